@@ -1,0 +1,185 @@
+/*
+ * rqb.h -- C ABI of the GB300 library for the blocked randomized QB scheme
+ * (randQB_b) of Martinsson & Voronin, "A randomized blocked algorithm for
+ * efficiently computing rank-revealing factorizations of matrices"
+ * (arXiv:1503.07157).
+ *
+ * Problem (Sec. 1.1 eq. (1); Sec. 1.2): given an m x n matrix A and a tolerance
+ * eps, find an orthonormal Q (m x k) and B = Q^T A (k x n) with
+ * ||A - Q B||_F <= eps, building Q and B b columns/rows at a time as in
+ * Fig. randQB_b:
+ *   (2)  Omega_i = randn(n, b)
+ *   (3)  Q_i = orth(A Omega_i)
+ *   (3') Q_i = orth(Q_i - sum_{j<i} Q_j Q_j^T Q_i)
+ *   (4)  B_i = Q_i^T A
+ *   (5)  A = A - Q_i B_i
+ *   (6)  stop once ||A||_F <= eps
+ *
+ * Conventions for every entry point:
+ *   - matrices are column-major; a leading dimension is in elements and must
+ *     be >= the row count;
+ *   - pointers are DEVICE pointers unless the name ends in _host;
+ *   - the element type of A, Q, B, Y, Omega is given by the handle's dtype:
+ *     RQB_F64 -> double, RQB_F32 -> float (BF16 input: Q, B, Y are float);
+ *   - every call returns an rqb_status; no exception crosses the ABI; the last
+ *     status is also kept in the handle (rqb_get_stats);
+ *   - all work is enqueued on the handle's stream (cfg.stream, a
+ *     cudaStream_t; NULL = the legacy default stream).  Calls that return
+ *     results to the host (k, stop decisions) synchronise that stream.
+ *   - Omega entry (r, c) is a function of (seed, r, c) only: Philox4x32-10
+ *     (Salmon et al., SC'11) at counter (r, c/2, 0, 0) with key (seed low
+ *     word, seed high word) gives two uniforms u1, u2 in (0, 1) and
+ *     Box-Muller gives sqrt(-2 ln u1) cos(2 pi u2) for even c and
+ *     sqrt(-2 ln u1) sin(2 pi u2) for odd c.  FP64 handles use 53-bit uniforms
+ *     and binary64 arithmetic; FP32 and BF16 handles use 23-bit uniforms and
+ *     binary32 arithmetic.  Block i uses global columns (i-1) b .. i b - 1, so
+ *     the blocks slice one fixed Omega (eq. OmegaBlock).
+ */
+#ifndef RQB_H
+#define RQB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RQB_OK = 0,
+    RQB_ERR_INVALID = 1,     /* bad size, leading dimension, pointer or config */
+    RQB_ERR_NONFINITE = 2,   /* NaN or Inf in A (detected through ||A||_F^2)   */
+    RQB_ERR_BREAKDOWN = 3,   /* Gram matrix of a panel not positive definite   */
+    RQB_ERR_OOM = 4,         /* device or pinned-host allocation failed        */
+    RQB_ERR_TIMEOUT = 5,     /* a bounded device wait gave up                  */
+    RQB_ERR_CUDA = 6,        /* a CUDA runtime call failed                     */
+    RQB_NOT_CONVERGED = 7,   /* k reached max_rank with ||A - QB||_F > eps;
+                                Q, B and k are still valid                      */
+    RQB_ERR_UNSUPPORTED = 8  /* valid request this build cannot serve          */
+} rqb_status;
+
+typedef enum { RQB_F64 = 0, RQB_F32 = 1, RQB_BF16 = 2 } rqb_dtype;
+
+/* Arithmetic of the n- and m-long products (sketch, B = Q^T A, downdate).
+ * NATIVE: the dtype's own arithmetic on the SIMT pipes (FP64 or FP32).
+ * Panel Gram matrices, Cholesky factors, re-projection coefficients and the
+ * Frobenius downdate are accumulated in FP64 in every mode. */
+typedef enum { RQB_PREC_NATIVE = 0, RQB_PREC_TF32X3 = 1, RQB_PREC_BF16 = 2 } rqb_prec;
+
+typedef struct {
+    int32_t dtype;       /* rqb_dtype                                           */
+    int32_t prec;        /* rqb_prec                                            */
+    int64_t max_rank;    /* rank cap; 0 = min(m, n)                             */
+    int32_t fixed_rank;  /* nonzero: ignore eps, run until k = max_rank (Sec. 4.1) */
+    int32_t power;       /* P of randQB_pb (Fig. randQB_pb); 0 = randQB_b       */
+    void* stream;        /* cudaStream_t                                        */
+    int32_t flags;       /* reserved, must be 0                                 */
+    int32_t reserved;
+} rqb_config;
+
+#define RQB_MAX_TRACKED_BLOCKS 512
+
+typedef struct {
+    int64_t k;            /* rank of the last factorization                    */
+    int64_t blocks;       /* number of blocks s                                */
+    int32_t status;       /* rqb_status of the last call                       */
+    int32_t direct_tests; /* blocks whose stop decision used the direct norm   */
+    double normA2;        /* ||A||_F^2 (FP64)                                  */
+    double eps;           /* tolerance of the last call                        */
+    /* per-block stopping quantities, first min(blocks, RQB_MAX_TRACKED_BLOCKS) */
+    double E[RQB_MAX_TRACKED_BLOCKS];  /* ||A||^2 - sum_{j<=i} ||B_j||^2       */
+    double D[RQB_MAX_TRACKED_BLOCKS];  /* direct ||A^(i)||_F^2 where computed,
+                                          else -1                              */
+    int32_t kernel_launches; /* kernels launched by the last call              */
+    int32_t reserved;
+} rqb_stats;
+
+typedef struct rqb_handle_s* rqb_handle;
+
+/* Create a handle on the current CUDA device.  cfg is copied.
+ * Errors: RQB_ERR_INVALID (null pointer, unknown dtype/prec, flags != 0),
+ *         RQB_ERR_UNSUPPORTED (dtype/prec pair not built), RQB_ERR_OOM. */
+int rqb_create(rqb_handle* h, const rqb_config* cfg);
+
+/* Release the handle and everything it owns (Q, B, workspace). */
+int rqb_destroy(rqb_handle h);
+
+/* randQB_b (Fig. randQB_b; with cfg.power > 0 randQB_pb, Fig. randQB_pb).
+ *   A      device, m x n, leading dim lda >= m, read only (the residual is
+ *          downdated in a handle-owned copy, eq. def3)
+ *   eps    absolute Frobenius tolerance, >= 0 (Sec. 1.1 eq. (1))
+ *   b      block size, 1 <= b <= 256
+ *   seed   Omega seed
+ * Outputs (handle-owned device buffers, valid until the next factor call on
+ * this handle or rqb_destroy):
+ *   *Q     m x k orthonormal, leading dim *ldq
+ *   *B     k x n, leading dim *ldb
+ *   *k     rank reached, a multiple of b except when capped by max_rank or
+ *          min(m, n) (the last block is then shrunk to fit)
+ * Stop rule: after B_i, E_i = ||A||_F^2 - sum_j ||B_j||_F^2 (FP64) is compared
+ * with eps^2 (Sec. 4.2 with Prop. 4.1(b)); when E_i is within the rounding
+ * band of the working precision around eps^2 the decision is taken on the
+ * directly computed ||A^(i)||_F^2 instead, as in line (6).
+ * Returns RQB_OK, RQB_NOT_CONVERGED, or an error. */
+int rqb_factor(rqb_handle h, const void* A, int64_t m, int64_t n, int64_t lda,
+               double eps, int64_t b, uint64_t seed,
+               const void** Q, int64_t* ldq, const void** B, int64_t* ldb, int64_t* k);
+
+/* As rqb_factor, with A, Q and B in HOST memory: A_host is copied to the
+ * device, factored, and Q (m x k into Q_host, leading dim ldq_host >= m) and
+ * B (k x n into B_host, leading dim ldb_host >= capacity) are copied back.
+ * Q_host must hold cap columns and B_host cap rows, cap = max_rank (or
+ * min(m, n)).  Pinned host buffers give the fastest copies. */
+int rqb_factor_host(rqb_handle h, const void* A_host, int64_t m, int64_t n, int64_t lda,
+                    double eps, int64_t b, uint64_t seed,
+                    void* Q_host, int64_t ldq_host, void* B_host, int64_t ldb_host, int64_t* k);
+
+/* Statistics of the last call on this handle. */
+int rqb_get_stats(rqb_handle h, rqb_stats* out);
+
+/* ------------------------------------------------------------------------
+ * Step-level entry points: single steps of Fig. randQB_b on caller buffers,
+ * for verification of each step against the oracle.
+ * ------------------------------------------------------------------------ */
+
+/* Omega block (line (2)): Omega (n x ncols, leading dim ldo >= n) receives
+ * global columns col0 .. col0 + ncols - 1 of the Omega defined above. */
+int rqb_omega(rqb_handle h, int64_t n, int64_t col0, int64_t ncols, uint64_t seed,
+              void* Omega, int64_t ldo);
+
+/* Sketch (line (3), product part): Y (m x ncols, leading dim ldy) = A Omega,
+ * Omega = global columns col0 .. col0 + ncols - 1, 1 <= ncols <= 256.
+ * If normA2 is non-NULL it receives ||A||_F^2 (FP64, host). */
+int rqb_sketch(rqb_handle h, const void* A, int64_t m, int64_t n, int64_t lda,
+               int64_t col0, int64_t ncols, uint64_t seed,
+               void* Y, int64_t ldy, double* normA2);
+
+/* Lines (3) and (3'): Qi (m x p, leading dim ldqi) = orth(Y) re-orthogonalised
+ * against Qbar (m x kprev, leading dim ldqb; may be NULL when kprev = 0), by
+ * CholeskyQR with FP64 Gram/Cholesky, the re-projection, and a second
+ * CholeskyQR; diag(R) > 0.  Returns RQB_ERR_BREAKDOWN when a Gram matrix is
+ * not numerically positive definite.  m >= p, 1 <= p <= 256. */
+int rqb_orth(rqb_handle h, const void* Y, int64_t m, int64_t p, int64_t ldy,
+             const void* Qbar, int64_t kprev, int64_t ldqb, void* Qi, int64_t ldqi);
+
+/* Line (4): Bi (p x n, leading dim ldbi) = Qi^T A with Qi m x p (ldqi),
+ * A m x n (lda).  If normB2 is non-NULL it receives ||Bi||_F^2 (FP64, host). */
+int rqb_project(rqb_handle h, const void* Qi, int64_t m, int64_t p, int64_t ldqi,
+                const void* A, int64_t n, int64_t lda, void* Bi, int64_t ldbi, double* normB2);
+
+/* Line (5) fused with line (3) of the next block: W (m x n, leading dim ldw)
+ * = A - Qi Bi (A may alias W exactly, for the in-place downdate), and
+ * Y (m x ncols, leading dim ldy) = W Omega(:, col0 : col0 + ncols).
+ * If normW2 is non-NULL it receives ||W||_F^2 (FP64, host). */
+int rqb_downdate_sketch(rqb_handle h, const void* A, int64_t lda, const void* Qi, int64_t ldqi,
+                        const void* Bi, int64_t ldbi, int64_t m, int64_t n, int64_t p,
+                        void* W, int64_t ldw, int64_t col0, int64_t ncols, uint64_t seed,
+                        void* Y, int64_t ldy, double* normW2);
+
+/* Human-readable name of a status code (static string). */
+const char* rqb_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RQB_H */

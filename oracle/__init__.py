@@ -1,0 +1,171 @@
+"""CPU FP64 oracle for blocked randomized QB (Martinsson & Voronin, arXiv:1503.07157).
+
+TEST INFRASTRUCTURE.  Only tests/, __graft_entry__.smoke() and bench.py's
+CPU-baseline leg import this package.  The product library never does.
+
+Thin ctypes wrapper over oracle/librqb_oracle.so (built from rqb_oracle.c);
+arrays are numpy float64, column-major (Fortran order).
+
+Functions and the passages they follow:
+  philox4x32_10  -- the counter-based generator of Salmon et al. (SC'11)
+  omega          -- Fig. randQB_b line (2), Omega_i = randn(n, b), indexed by
+                    global column so that blocks slice one Omega (eq. OmegaBlock)
+  orth           -- Sec. 2.4, unpivoted Householder QR with diag(R) >= 0
+  sketch         -- Fig. randQB_b line (3), A Omega_i
+  orth_reproject -- Fig. randQB_b lines (3) and (3')
+  randqb_b       -- Fig. randQB_b (power > 0: Fig. randQB_pb; skip_inner_orth:
+                    the Sec. 5.4 variant)
+  randqb         -- Fig. randQB (unblocked)
+  svd_values     -- singular values by one-sided Jacobi (for the Eckart-Young
+                    bound of eq. minerrors on small inputs)
+"""
+import ctypes
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        i64, u64, dbl, i32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int
+        P = ctypes.c_void_p
+        lib.orc_philox4x32_10.argtypes = [P, P, P]
+        lib.orc_omega.argtypes = [u64, ctypes.c_uint32, i64, i64, i64, i32, P, i64]
+        lib.orc_orth.argtypes = [P, i64, i64, i64, P, i64, P, i64]
+        lib.orc_randqb_b.argtypes = [P, i64, i64, i64, dbl, i64, u64, i64, i32, i32, i32, i32,
+                                     P, i64, P, i64, P]
+        lib.orc_randqb_b.restype = i32
+        lib.orc_randqb.argtypes = [P, i64, i64, i64, i64, u64, i32, P, i64, P, i64]
+        lib.orc_randqb.restype = i32
+        lib.orc_svd_values.argtypes = [P, i64, i64, i64, P]
+        lib.orc_sketch.argtypes = [P, i64, i64, i64, u64, i64, i64, i32, P, i64]
+        lib.orc_orth_reproject.argtypes = [P, i64, i64, i64, P, i64, i64, P, i64]
+        lib.orc_num_threads.restype = i32
+        _LIB = lib
+    return _LIB
+
+
+class _Res(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int64), ("blocks", ctypes.c_int64), ("status", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("normA2", ctypes.c_double),
+                ("E", ctypes.c_void_p), ("D", ctypes.c_void_p), ("max_blocks", ctypes.c_int64)]
+
+
+def _f64(a):
+    return np.asfortranarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def num_threads() -> int:
+    return int(_lib().orc_num_threads())
+
+
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def omega(seed: int, n: int, col0: int, ncols: int, prec: int = 64, stream: int = 0):
+    out = np.zeros((n, ncols), dtype=np.float64, order="F")
+    _lib().orc_omega(seed, stream, n, col0, ncols, prec, _ptr(out), n)
+    return out
+
+
+def orth(Y, return_r: bool = False):
+    Y = _f64(Y)
+    m, p = Y.shape
+    Q = np.zeros((m, p), order="F")
+    R = np.zeros((p, p), order="F")
+    _lib().orc_orth(_ptr(Y), m, p, m, _ptr(Q), m, _ptr(R), p)
+    return (Q, R) if return_r else Q
+
+
+def sketch(A, seed: int, col0: int, p: int, omega_prec: int = 64):
+    A = _f64(A)
+    m, n = A.shape
+    Y = np.zeros((m, p), order="F")
+    _lib().orc_sketch(_ptr(A), m, n, m, seed, col0, p, omega_prec, _ptr(Y), m)
+    return Y
+
+
+def orth_reproject(Y, Qbar):
+    Y = _f64(Y)
+    m, p = Y.shape
+    Qbar = _f64(Qbar) if Qbar is not None and Qbar.shape[1] > 0 else np.zeros((m, 0), order="F")
+    kprev = Qbar.shape[1]
+    Qi = np.zeros((m, p), order="F")
+    qb = Qbar if kprev > 0 else np.zeros((m, 1), order="F")
+    _lib().orc_orth_reproject(_ptr(Y), m, p, m, _ptr(qb), kprev, m, _ptr(Qi), m)
+    return Qi
+
+
+@dataclass
+class QBResult:
+    Q: np.ndarray
+    B: np.ndarray
+    k: int
+    blocks: int
+    status: int
+    normA2: float
+    E: np.ndarray = field(repr=False)   # running downdate after each block
+    D: np.ndarray = field(repr=False)   # direct ||A^(i)||_F^2 after each block
+
+    def residual_downdate(self) -> float:
+        return float(np.sqrt(max(self.E[-1], 0.0)))
+
+    def residual_direct(self) -> float:
+        return float(np.sqrt(self.D[-1]))
+
+
+def randqb_b(A, eps: float, b: int, seed: int = 0, max_rank: int = 0, fixed_rank: bool = False,
+             power: int = 0, skip_inner_orth: bool = False, omega_prec: int = 64) -> QBResult:
+    A = _f64(A)
+    m, n = A.shape
+    rmax = min(m, n)
+    kcap = rmax if (max_rank <= 0 or max_rank > rmax) else max_rank
+    Q = np.zeros((m, kcap), order="F")
+    B = np.zeros((kcap, n), order="F")
+    nbmax = (kcap + b - 1) // b + 1
+    E = np.zeros(nbmax)
+    D = np.zeros(nbmax)
+    res = _Res(0, 0, 0, 0, 0.0, E.ctypes.data, D.ctypes.data, nbmax)
+    rc = _lib().orc_randqb_b(_ptr(A), m, n, m, float(eps), b, seed, kcap, int(fixed_rank),
+                             int(power), int(skip_inner_orth), int(omega_prec),
+                             _ptr(Q), m, _ptr(B), kcap, ctypes.byref(res))
+    if rc != 0:
+        raise ValueError("orc_randqb_b: invalid arguments")
+    k, s = int(res.k), int(res.blocks)
+    return QBResult(Q=Q[:, :k].copy(order="F"), B=B[:k, :].copy(order="F"), k=k, blocks=s,
+                    status=int(res.status), normA2=float(res.normA2), E=E[:s].copy(), D=D[:s].copy())
+
+
+def randqb(A, l: int, seed: int = 0, omega_prec: int = 64):
+    A = _f64(A)
+    m, n = A.shape
+    Q = np.zeros((m, l), order="F")
+    B = np.zeros((l, n), order="F")
+    rc = _lib().orc_randqb(_ptr(A), m, n, m, l, seed, omega_prec, _ptr(Q), m, _ptr(B), l)
+    if rc != 0:
+        raise ValueError("orc_randqb: invalid arguments")
+    return Q, B
+
+
+def svd_values(A):
+    A = _f64(A)
+    m, n = A.shape
+    s = np.zeros(min(m, n))
+    _lib().orc_svd_values(_ptr(A), m, n, m, _ptr(s))
+    return s

@@ -1,0 +1,396 @@
+"""Benchmark of the randQB_b hot path on one GB300 (or N replicas under torchrun).
+
+One step = one full randQB_b factorization (Fig. randQB_b: every block's
+Omega, sketch, CholeskyQR2 with re-projection, B_i = Q_i^T A, downdate fused
+with the next sketch, stop test) of the benchmark workload, with A already
+resident in HBM.  Prints one JSON line.
+
+Workloads (--workload):
+  fp32  (default) 20000 x 16000 FP32, A = U diag(j^-1.5) V^T, b = 128,
+        eps = 1e-2 ||A||_F, Omega seed 0 -- the plain FP32 configuration
+  fp64  2000 x 1000 FP64, s_j = 10^(-8(j-1)/999), b = 50, eps = 1e-4 ||A||_F
+
+Metric: TFLOP/s of useful FLOPs (the algorithm's products counted once, no
+extra passes of split precision):
+  F = (6 s - 2) m n b + 2 m b^2 s (s - 1) + 6 m b^2 s
+for s blocks of width b (sketch of block 1, per block B_i and, except for the
+last block, the downdate and the next sketch; re-projection; CholeskyQR2).
+
+--impl reference times the CPU FP64 oracle on a bounded sample of the same
+workload recipe (the oracle is the reference arm: the paper has no code).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "fp32": dict(name="randQB_b FP32 20000x16000 s_j=j^-1.5 b=128 eps=1e-2||A||_F", m=20000, n=16000, b=128,
+                 eps_rel=1e-2, dtype="float32", spectrum="poly1.5"),
+    "fp64": dict(name="randQB_b FP64 2000x1000 s_j=10^(-8(j-1)/999) b=50 eps=1e-4||A||_F", m=2000, n=1000, b=50,
+                 eps_rel=1e-4, dtype="float64", spectrum="fp64cfg"),
+}
+METRIC = "randQB_b TFLOP/s & roofline fraction at matched eps; mixed/batched vs plain FP32"
+
+
+def useful_flops(m: int, n: int, b: int, s: int) -> float:
+    return (6 * s - 2) * m * n * b + 2.0 * m * b * b * s * (s - 1) + 6.0 * m * b * b * s
+
+
+def phase_flops(m: int, n: int, b: int, s: int) -> dict:
+    """Algorithmic FLOPs per launch of each step of the block loop."""
+    return {
+        "sketch": 2.0 * m * n * b,
+        "project": 2.0 * m * n * b,
+        "downdate": 4.0 * m * n * b,
+        "orth": (2.0 * m * b * b * s * (s - 1) + 6.0 * m * b * b * s) / max(s, 1),
+    }
+
+
+def spectrum(kind: str, r: int):
+    import inputs
+    if kind == "poly1.5":
+        return inputs.spectrum_poly(r)
+    if kind == "fp64cfg":
+        return inputs.spectrum_fp64_config(r)
+    raise ValueError(kind)
+
+
+def make_workload_device(w: dict, seed: int = 2):
+    """A on the current CUDA device, column-major, built by inputs.usv_torch."""
+    import numpy as np
+    import torch
+    import inputs
+    m, n = w["m"], w["n"]
+    s = spectrum(w["spectrum"], min(m, n))
+    dt = torch.float64 if w["dtype"] == "float64" else torch.float32
+    A = inputs.usv_torch(m, n, s, seed, device="cuda", dtype=dt)
+    normA = float(np.sqrt(np.sum(s.astype(np.float64) ** 2)))
+    return A, normA
+
+
+def make_sample_host(w: dict, frac: float, seed: int = 2):
+    """The workload recipe at frac x the size, FP64 numpy (oracle input)."""
+    import numpy as np
+    import inputs
+    m, n = max(8, int(w["m"] * frac)), max(8, int(w["n"] * frac))
+    s = spectrum(w["spectrum"], min(m, n))
+    A = inputs.usv(m, n, s, seed)
+    if w["dtype"] == "float32":
+        A = A.astype(np.float32).astype(np.float64)
+    return A
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling in the background."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 100):
+        self.gpu = gpu_index
+        self.period = period_ms
+        self.proc = None
+        self.file = None
+        self.marks = []
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", str(self.period)], stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def mark(self):
+        self.marks.append(time.time())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.strip().split(",") for r in self.file.read().splitlines() if r.strip()]
+        self.file.close()
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def alu_peak_tflops(dtype: str, num_sms: int, sm_mhz: float) -> float:
+    """SIMT peak from unit counts: FP32 128 lanes/SM, FP64 2 lanes/SM (1.25 TFLOP/s
+    nominal on 152 SMs at 2070 MHz), 2 FLOPs per fused multiply-add."""
+    lanes = 128 if dtype == "float32" else 2
+    return num_sms * lanes * 2.0 * sm_mhz * 1e6 / 1e12
+
+
+# ncu DRAM traffic of the dominant kernel per launch (bytes), keyed by workload;
+# from profiles/ (value is None when the kernel changed since the capture).
+NCU_TRAFFIC = {"fp32": None, "fp64": None}
+
+
+def oracle_baseline(w: dict, frac: float, repeats: int = 1) -> dict:
+    """Oracle randQB_b on the workload recipe at frac x size; TFLOP/s and cores."""
+    import oracle
+    A = make_sample_host(w, frac)
+    m, n = A.shape
+    nA = float((A * A).sum()) ** 0.5
+    eps = w["eps_rel"] * nA
+    prec = 64 if w["dtype"] == "float64" else 32
+    times = []
+    res = None
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        res = oracle.randqb_b(A, eps, w["b"], seed=0, omega_prec=prec)
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    F = useful_flops(m, n, w["b"], res.blocks)
+    return {"value": F / t / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"oracle randQB_b on the same recipe at {m}x{n} (frac {frac}), b={w['b']}, "
+                      f"eps={w['eps_rel']}||A||_F, k={res.k}, {t:.2f} s per run", "seconds": t}
+
+
+def run_ours(args, w: dict, rank: int, world: int, dist):
+    import torch
+    from paper_1503_07157_gb300 import build as _build
+    _build.build()
+    from paper_1503_07157_gb300 import rqb
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    A, normA = make_workload_device(w)
+    m, n, b = w["m"], w["n"], w["b"]
+    eps = w["eps_rel"] * normA
+    dt = torch.float64 if w["dtype"] == "float64" else torch.float32
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    h = rqb.Handle(dt, stream=stream, flags=rqb.RQB_FLAG_PHASE_TIMING)
+    for _ in range(args.warmup):
+        _, _, k, rc = h.rqb_factor(A, eps, b, seed=0)
+    st = h.rqb_get_stats()
+    s_blocks, k = st.blocks, st.k
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    phase_ms = [0.0] * rqb.RQB_NUM_PHASES
+    phase_calls = [0] * rqb.RQB_NUM_PHASES
+    launches = 0
+    clocks = ClockSampler(torch.cuda.current_device())
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    time.sleep(0.25)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        _, _, kk, rc = h.rqb_factor(A, eps, b, seed=0)
+        stt = h.rqb_get_stats()
+        for i in range(rqb.RQB_NUM_PHASES):
+            phase_ms[i] += stt.phase_ms[i]
+            phase_calls[i] += stt.phase_calls[i]
+        launches += stt.kernel_launches
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    F = useful_flops(m, n, b, s_blocks)
+    value = F * world / (ms * 1e-3) / 1e12
+
+    # roofline of the dominant step (its main kernel plus split reduction)
+    pf = phase_flops(m, n, b, s_blocks)
+    names = list(rqb.PHASES)
+    cand = [(phase_ms[i], names[i]) for i in range(len(names)) if names[i] in pf and phase_calls[i] > 0]
+    dom_ms, dom = max(cand)
+    idx = names.index(dom)
+    per_launch_ms = phase_ms[idx] / phase_calls[idx]
+    achieved = pf[dom] / (per_launch_ms * 1e-3) / 1e12
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(dev)
+    peak = alu_peak_tflops(w["dtype"], props.multi_processor_count, sm_max)
+    roofline = {"bound": "alu", "kernel": f"{dom} (k_gemm_{'nn' if dom == 'sketch' else 'tn'} + split reduction)"
+                if dom in ("sketch", "project") else dom,
+                "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(args.workload),
+                "peak_source": f"derived: {props.multi_processor_count} SMs x "
+                               f"{'128 FP32' if w['dtype'] == 'float32' else '2 FP64'} lanes x 2 x {sm_max:.0f} MHz",
+                "phase_ms_per_step": {names[i]: round(phase_ms[i] / args.steps, 4) for i in range(len(names))}}
+    return dict(h=h, A=A, eps=eps, value=value, ms=ms, F=F, k=k, s=s_blocks, clocks=clk, roofline=roofline,
+                launches=launches // max(args.steps, 1), stream=stream)
+
+
+def run_e2e(args, w: dict, res: dict) -> dict:
+    """Same metric through rqb_factor_host: pinned host A in, Q and B back to
+    pinned host buffers, all copies inside the timed region."""
+    import torch
+    from paper_1503_07157_gb300 import rqb
+    m, n, b = w["m"], w["n"], w["b"]
+    dt = res["A"].dtype
+    cap = min(m, n, args.e2e_max_rank)
+    A_host = torch.empty(n, m, dtype=dt, pin_memory=True).t()
+    A_host.copy_(res["A"])
+    Q_host = torch.empty(cap, m, dtype=dt, pin_memory=True).t()
+    B_host = torch.empty(n, cap, dtype=dt, pin_memory=True).t()
+    h = rqb.Handle(dt, stream=res["stream"], max_rank=cap)
+    times, k = [], 0
+    for i in range(args.warmup + max(1, args.e2e_steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k, rc = h.rqb_factor_host(A_host, res["eps"], b, 0, Q_host, B_host)
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            times.append(t1 - t0)
+    h.close()
+    t = statistics.median(times)
+    es = A_host.element_size()
+    return {"value": round(res["F"] / t / 1e12, 4), "unit": "TFLOP/s", "h2d_bytes_per_step": m * n * es,
+            "d2h_bytes_per_step": (m * k + k * n) * es, "ms_per_step": round(t * 1e3, 3),
+            "api": "rqb_factor_host (pinned host buffers)"}
+
+
+def init_dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world <= 1:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return rank, world, dist
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="fp32")
+    ap.add_argument("--sample-frac", type=float, default=0.3,
+                    help="size fraction of the oracle's bounded sample (CPU baseline / reference arm)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-max-rank", type=int, default=4096)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    w = WORKLOADS[args.workload]
+
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        if rank != 0:
+            return 0
+        return run_reference(args, w)
+
+    import torch
+    rank, world, dist = init_dist()
+    res = run_ours(args, w, rank, world, dist)
+    e2e = run_e2e(args, w, res) if rank == 0 else None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_baseline(w, args.sample_frac)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(res["value"], 4), "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(res["ms"], 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32" if
+            w["dtype"] == "float32" else "f64", "data": "synthetic (seeded A = U diag(s) V^T, U, V from QR of "
+            "Gaussian matrices; Omega Philox4x32-10 + Box-Muller)",
+            "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "b": w["b"], "eps_rel": w["eps_rel"],
+                       "k": res["k"], "blocks": res["s"], "useful_flops_per_step": res["F"],
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "input larger than L2 (A is %.2f GB)" % (w["m"] * w["n"] *
+                                                                       (4 if w["dtype"] == "float32" else 8) / 1e9)
+                       if w["m"] * w["n"] * 4 > 129e6 else "L2 not flushed: input fits in L2"},
+            "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": res["launches"]
+            * args.steps, "clocks": res["clocks"],
+        }
+        if cpu is not None:
+            cpu.pop("seconds", None)
+        print(json.dumps(line), flush=True)
+    res["h"].close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_reference(args, w: dict) -> int:
+    """The reference arm: the CPU FP64 oracle, as it stands, on the machine's host
+    cores; each step is one run on the bounded sample of the workload recipe."""
+    import oracle
+    A = make_sample_host(w, args.sample_frac)
+    m, n = A.shape
+    nA = float((A * A).sum()) ** 0.5
+    eps = w["eps_rel"] * nA
+    prec = 64 if w["dtype"] == "float64" else 32
+    steps = max(1, min(args.steps, 5))
+    warm = min(args.warmup, 1)
+    times, r = [], None
+    for i in range(warm + steps):
+        t0 = time.perf_counter()
+        r = oracle.randqb_b(A, eps, w["b"], seed=0, omega_prec=prec)
+        if i >= warm:
+            times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    F = useful_flops(m, n, w["b"], r.blocks)
+    val = F / t / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": round(val, 6), "unit": "TFLOP/s", "n_gpus": 0,
+            "steps": steps, "warmup": warm, "ms_per_step": round(t * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "sample": f"{m}x{n}", "k": r.k, "blocks": r.blocks},
+            "cpu_baseline": {"value": round(val, 6), "unit": "TFLOP/s", "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": f"same recipe at {m}x{n} (frac {args.sample_frac}); "
+                             f"steps capped at {steps}, warm-up at {warm} to bound CPU time"},
+            "e2e": {"value": round(val, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -73,9 +73,24 @@ typedef struct {
     int32_t fixed_rank;  /* nonzero: ignore eps, run until k = max_rank (Sec. 4.1) */
     int32_t power;       /* P of randQB_pb (Fig. randQB_pb); 0 = randQB_b       */
     void* stream;        /* cudaStream_t                                        */
-    int32_t flags;       /* reserved, must be 0                                 */
+    int32_t flags;       /* bit set of RQB_FLAG_*; other bits must be 0         */
     int32_t reserved;
 } rqb_config;
+
+/* cfg.flags: record CUDA events around each step of the block loop and
+ * report their durations in rqb_stats.phase_ms (costs a few microseconds of
+ * host time per step; no extra synchronisation beyond the per-block one). */
+#define RQB_FLAG_PHASE_TIMING 1
+
+/* Steps timed with RQB_FLAG_PHASE_TIMING (index into phase_ms/phase_calls). */
+typedef enum {
+    RQB_PHASE_SKETCH = 0,    /* line (3) first block: Omega_1 and A Omega_1, ||A||_F^2 */
+    RQB_PHASE_ORTH = 1,      /* lines (3), (3'): CholeskyQR2 with re-projection        */
+    RQB_PHASE_PROJECT = 2,   /* line (4): B_i = Q_i^T A, ||B_i||^2                     */
+    RQB_PHASE_DOWNDATE = 3,  /* line (5) fused with line (3) of the next block         */
+    RQB_PHASE_CONTROL = 4,   /* line (6): stop test and its host read-back             */
+    RQB_NUM_PHASES = 8
+} rqb_phase;
 
 #define RQB_MAX_TRACKED_BLOCKS 512
 
@@ -92,6 +107,8 @@ typedef struct {
                                           else -1                              */
     int32_t kernel_launches; /* kernels launched by the last call              */
     int32_t reserved;
+    double phase_ms[RQB_NUM_PHASES];     /* summed device time per step (ms)   */
+    int32_t phase_calls[RQB_NUM_PHASES]; /* times each step ran                */
 } rqb_stats;
 
 typedef struct rqb_handle_s* rqb_handle;

@@ -1,0 +1,699 @@
+// rqb_api.cu -- C ABI of the randQB_b library: handle, workspace, and the
+// block loop of Fig. randQB_b driving the SIMT kernels of rqb_kernels.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "rqb_engine.h"
+
+using namespace rqb;
+
+namespace {
+
+constexpr int kNrmCap = 8192;      // per-CTA FP64 partials
+constexpr int kScalars = 16;       // FP64 scalars on the device
+
+int round_up(int64_t v, int64_t q) { return (int)(((v + q - 1) / q) * q); }
+
+int pad_block(int64_t b) { return b <= 32 ? 32 : b <= 64 ? 64 : b <= 128 ? 128 : 256; }
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    int ensure(size_t need) {
+        if (need <= bytes) return RQB_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        if (cudaMalloc(&p, need) != cudaSuccess) {
+            cudaGetLastError();
+            return RQB_ERR_OOM;
+        }
+        bytes = need;
+        return RQB_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+// CUDA-event timing of the steps of the block loop (RQB_FLAG_PHASE_TIMING).
+// Pairs of events are recorded on the handle's stream and read after the
+// per-block synchronisation that the loop already performs.
+struct PhaseTimer {
+    static constexpr int kPairs = 16;
+    bool on = false;
+    bool pending = false;
+    int n = 0;
+    cudaEvent_t ev[2 * kPairs] = {};
+    int phase[kPairs] = {};
+    int create() {
+        for (int i = 0; i < 2 * kPairs; ++i)
+            if (cudaEventCreate(&ev[i]) != cudaSuccess) return RQB_ERR_CUDA;
+        on = true;
+        return RQB_OK;
+    }
+    void destroy() {
+        for (int i = 0; i < 2 * kPairs; ++i)
+            if (ev[i]) cudaEventDestroy(ev[i]);
+        on = false;
+    }
+    void begin(cudaStream_t s, int ph) {
+        if (!on || n >= kPairs) return;
+        cudaEventRecord(ev[2 * n], s);
+        phase[n] = ph;
+        pending = true;
+    }
+    void end(cudaStream_t s) {
+        if (!on || !pending) return;
+        cudaEventRecord(ev[2 * n + 1], s);
+        pending = false;
+        ++n;
+    }
+    // after the stream has been synchronised
+    void flush(rqb_stats* st) {
+        for (int i = 0; i < n; ++i) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]) == cudaSuccess) {
+                st->phase_ms[phase[i]] += ms;
+                st->phase_calls[phase[i]] += 1;
+            }
+        }
+        n = 0;
+    }
+};
+
+}  // namespace
+
+struct rqb_handle_s {
+    rqb_config cfg{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 1;
+    size_t esize = 4;          // bytes per element of A, Q, B
+    // device memory
+    DevBuf state;              // DevState + FP64 scalars + FP64 partials
+    DevBuf arena;              // Omega, Y, Y1, Gram, R, Rinv, C, partials
+    DevBuf q, b, w, ahost;     // outputs, residual copy, staging for host input
+    int64_t ldq = 0, ldb = 0, ldw = 0, kcap_alloc = 0;
+    // host mirror
+    DevState* hstate = nullptr;  // pinned
+    rqb_stats stats{};
+    int last_status = RQB_OK;
+    PhaseTimer timer;
+};
+
+namespace {
+
+template <typename T>
+struct Arena {
+    T* Om;          // n x bp row-major
+    T* Y;           // m x bp (ld m)
+    T* Y1;          // m x bp (ld m)
+    T* Rinv;        // bp x bp
+    T* Cc;          // kprev x bp
+    T* part;        // split partials
+    size_t part_cap;
+    double* G;      // bp x bp
+    double* R;      // bp x bp
+    double* Cd;     // kprev x bp
+    double* dpart;  // FP64 split partials
+    size_t dpart_cap;
+};
+
+struct Scal {
+    DevState* st;
+    double* s;       // kScalars
+    double* nrm;     // kNrmCap
+};
+
+Scal scalars(rqb_handle h) {
+    Scal r;
+    r.st = reinterpret_cast<DevState*>(h->state.p);
+    r.s = reinterpret_cast<double*>(reinterpret_cast<char*>(h->state.p) + 256);
+    r.nrm = r.s + kScalars;
+    return r;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+template <typename T>
+int ensure_arena(rqb_handle h, int64_t m, int64_t n, int bp, int64_t kprev_max, Arena<T>* out) {
+    const size_t part_cap = (size_t)16 * (size_t)std::max(m, n) * (size_t)bp;
+    const int64_t kp = std::max<int64_t>(kprev_max, 1);
+    const size_t dpart_cap = std::max<size_t>((size_t)128 * bp * bp, (size_t)8 * kp * bp);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+    const size_t oOm = take(sizeof(T) * (size_t)n * bp);
+    const size_t oY = take(sizeof(T) * (size_t)m * bp);
+    const size_t oY1 = take(sizeof(T) * (size_t)m * bp);
+    const size_t oRinv = take(sizeof(T) * (size_t)bp * bp);
+    const size_t oCc = take(sizeof(T) * (size_t)kp * bp);
+    const size_t oPart = take(sizeof(T) * part_cap);
+    const size_t oG = take(sizeof(double) * (size_t)bp * bp);
+    const size_t oR = take(sizeof(double) * (size_t)bp * bp);
+    const size_t oCd = take(sizeof(double) * (size_t)kp * bp);
+    const size_t oDp = take(sizeof(double) * dpart_cap);
+    int rc = h->arena.ensure(off);
+    if (rc != RQB_OK) return rc;
+    char* base = reinterpret_cast<char*>(h->arena.p);
+    out->Om = reinterpret_cast<T*>(base + oOm);
+    out->Y = reinterpret_cast<T*>(base + oY);
+    out->Y1 = reinterpret_cast<T*>(base + oY1);
+    out->Rinv = reinterpret_cast<T*>(base + oRinv);
+    out->Cc = reinterpret_cast<T*>(base + oCc);
+    out->part = reinterpret_cast<T*>(base + oPart);
+    out->part_cap = part_cap;
+    out->G = reinterpret_cast<double*>(base + oG);
+    out->R = reinterpret_cast<double*>(base + oR);
+    out->Cd = reinterpret_cast<double*>(base + oCd);
+    out->dpart = reinterpret_cast<double*>(base + oDp);
+    out->dpart_cap = std::max<size_t>(dpart_cap, 1);
+    return RQB_OK;
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return RQB_OK;
+    if (e == cudaErrorMemoryAllocation) return RQB_ERR_OOM;
+    return RQB_ERR_CUDA;
+}
+
+#define RQB_CK(call)                                    \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_status(e_);  \
+    } while (0)
+
+// Rounding band of the downdated E relative to ||A||^2 in the working precision.
+template <typename T> double band_rel();
+template <> double band_rel<double>() { return 64.0 * 1.1102230246251565e-16; }
+template <> double band_rel<float>() { return 32.0 * 5.9604644775390625e-08; }
+
+// Read the device state (synchronises the stream).
+int read_state(rqb_handle h, const Scal& sc) {
+    RQB_CK(cudaMemcpyAsync(h->hstate, sc.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    RQB_CK(cudaStreamSynchronize(h->stream));
+    h->timer.flush(&h->stats);
+    return h->hstate->err;
+}
+
+// Lines (3) and (3'): Qout (p columns, ld ldqo) from the panel Y (bp columns,
+// ld ldy; columns >= p are zero) and Qbar (kprev columns, ld ldqb).
+template <typename T>
+int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_t ldy, int64_t m, int p, int bp,
+                   const T* Qbar, int64_t kprev, int64_t ldqb, T* Qout, int64_t ldqo) {
+    // pass 1: CholeskyQR of Y, Y1 = Y R^{-1}
+    RQB_CK(gemm_tn_f64acc<T>(cx, m, bp, bp, Y, ldy, Y, ldy, ar.G, bp, ar.dpart, ar.dpart_cap));
+    RQB_CK(chol_inv<T>(cx, ar.G, bp, p, ar.R, ar.Rinv));
+    {
+        NNArgs<T> a;
+        a.m = m; a.K = bp; a.nc = bp; a.nout = bp;
+        a.X = Y; a.ldx = ldy;
+        a.C = ar.Rinv; a.csk = 1; a.csj = bp; a.c_rowmajor = false;
+        a.Out = ar.Y1; a.ldo = m;
+        RQB_CK(gemm_nn<T>(cx, a));
+    }
+    // line (3'): Y1 -= Qbar (Qbar^T Y1)
+    if (kprev > 0) {
+        RQB_CK(gemm_tn_f64acc<T>(cx, m, (int)kprev, bp, Qbar, ldqb, ar.Y1, m, ar.Cd, kprev, ar.dpart,
+                                 ar.dpart_cap));
+        RQB_CK((launch_reduce_split<double, T>(cx, kprev, bp, 1, ar.Cd, kprev, 0, ar.Cc, kprev, nullptr, 0,
+                                               nullptr)));
+        NNArgs<T> a;
+        a.m = m; a.K = kprev; a.nc = bp; a.nout = bp;
+        a.X = Qbar; a.ldx = ldqb;
+        a.C = ar.Cc; a.csk = 1; a.csj = kprev; a.c_rowmajor = false;
+        a.Out = ar.Y1; a.ldo = m;
+        a.Yin = ar.Y1; a.ldyin = m; a.alpha = T(-1); a.beta = T(1);
+        RQB_CK(gemm_nn<T>(cx, a));
+    }
+    // pass 2: CholeskyQR of Y1, Qout = Y1 R^{-1}
+    RQB_CK(gemm_tn_f64acc<T>(cx, m, bp, bp, ar.Y1, m, ar.Y1, m, ar.G, bp, ar.dpart, ar.dpart_cap));
+    RQB_CK(chol_inv<T>(cx, ar.G, bp, p, ar.R, ar.Rinv));
+    {
+        NNArgs<T> a;
+        a.m = m; a.K = bp; a.nc = bp; a.nout = p;
+        a.X = ar.Y1; a.ldx = m;
+        a.C = ar.Rinv; a.csk = 1; a.csj = bp; a.c_rowmajor = false;
+        a.Out = Qout; a.ldo = ldqo;
+        RQB_CK(gemm_nn<T>(cx, a));
+    }
+    return RQB_OK;
+}
+
+template <typename T>
+int factor_impl(rqb_handle h, const T* A, int64_t m, int64_t n, int64_t lda, double eps, int64_t b, uint64_t seed,
+                int64_t* k_out) {
+    const int64_t rmax = std::min(m, n);
+    const int64_t kcap = (h->cfg.max_rank > 0 && h->cfg.max_rank < rmax) ? h->cfg.max_rank : rmax;
+    const int bp = pad_block(b);
+    const int fixed = h->cfg.fixed_rank ? 1 : 0;
+    Arena<T> ar;
+    int rc = ensure_arena<T>(h, m, n, bp, kcap, &ar);
+    if (rc != RQB_OK) return rc;
+    // outputs
+    const int64_t ldq = round_up(m, 4), ldb = round_up(kcap, 4);
+    rc = h->q.ensure(sizeof(T) * (size_t)ldq * (size_t)kcap);
+    if (rc != RQB_OK) return rc;
+    rc = h->b.ensure(sizeof(T) * (size_t)ldb * (size_t)n);
+    if (rc != RQB_OK) return rc;
+    h->ldq = ldq;
+    h->ldb = ldb;
+    h->kcap_alloc = kcap;
+    T* Q = reinterpret_cast<T*>(h->q.p);
+    T* B = reinterpret_cast<T*>(h->b.p);
+
+    Scal sc = scalars(h);
+    Ctx cx;
+    cx.stream = h->stream;
+    cx.num_sms = h->num_sms;
+    cx.st = sc.st;
+    RQB_CK(cudaMemsetAsync(sc.st, 0, sizeof(DevState), h->stream));
+
+    const double eps2 = eps * eps;
+    const double tau_rel = band_rel<T>();
+    int64_t k = 0;
+    int blocks = 0, direct = 0;
+    int status = RQB_OK;
+    bool converged = false;
+
+    // block 1 sketch: Y = A Omega_1 with ||A||_F^2 on the same read
+    int p = (int)std::min<int64_t>(b, kcap);
+    h->timer.begin(h->stream, RQB_PHASE_SKETCH);
+    RQB_CK(launch_omega<T>(cx, n, 0, p, bp, seed, ar.Om, bp, 1));
+    {
+        NNArgs<T> a;
+        a.m = m; a.K = n; a.nc = bp; a.nout = bp;
+        a.X = A; a.ldx = lda;
+        a.C = ar.Om; a.csk = bp; a.csj = 1; a.c_rowmajor = true;
+        a.Out = ar.Y; a.ldo = m;
+        a.part = ar.part; a.part_cap = ar.part_cap; a.allow_split = 1;
+        a.nrm_part = sc.nrm; a.nrm_cap = kNrmCap; a.nrm_out = sc.s + 0;
+        RQB_CK(gemm_nn<T>(cx, a));
+    }
+    RQB_CK(launch_set_norm(cx, sc.s + 0));
+    h->timer.end(h->stream);
+
+    const T* Wsrc = A;
+    int64_t ldws = lda;
+    T* W = nullptr;
+    int64_t ldw = 0;
+    for (;;) {
+        p = (int)std::min<int64_t>(b, kcap - k);
+        T* Qi = Q + k * ldq;
+        T* Bi = B + k;
+        // lines (3), (3')
+        h->timer.begin(h->stream, RQB_PHASE_ORTH);
+        rc = orth_reproject<T>(h, cx, ar, ar.Y, m, m, p, bp, Q, k, ldq, Qi, ldq);
+        if (rc != RQB_OK) return rc;
+        h->timer.end(h->stream);
+        h->timer.begin(h->stream, RQB_PHASE_PROJECT);
+        // line (4): B_i = Q_i^T A, ||B_i||^2
+        RQB_CK(gemm_tn<T>(cx, m, p, n, Qi, ldq, Wsrc, ldws, Bi, ldb, ar.part, ar.part_cap, sc.nrm, kNrmCap,
+                          sc.s + 1));
+        h->timer.end(h->stream);
+        // line (6), downdate form of the test
+        h->timer.begin(h->stream, RQB_PHASE_CONTROL);
+        RQB_CK(launch_stop_after_b(cx, sc.s + 1, eps2, tau_rel, fixed));
+        h->timer.end(h->stream);
+        int err = read_state(h, sc);
+        if (err != RQB_OK) { status = err; break; }
+        const int flag = h->hstate->flag;
+        if (blocks < RQB_MAX_TRACKED_BLOCKS) {
+            h->stats.E[blocks] = h->hstate->E;
+            h->stats.D[blocks] = -1.0;
+        }
+        k += p;
+        blocks++;
+        if (flag == kStop) { converged = true; break; }
+        if (flag == kContinue && k >= kcap) break;
+        // line (5) fused with line (3) of the next block (or only the direct
+        // norm when the cap is reached with an ambiguous E)
+        const int pn = (int)std::min<int64_t>(b, std::max<int64_t>(kcap - k, 0));
+        if (!W) {
+            ldw = round_up(m, 4);
+            rc = h->w.ensure(sizeof(T) * (size_t)ldw * (size_t)n);
+            if (rc != RQB_OK) return rc;
+            W = reinterpret_cast<T*>(h->w.p);
+            h->ldw = ldw;
+        }
+        h->timer.begin(h->stream, RQB_PHASE_DOWNDATE);
+        RQB_CK(launch_omega<T>(cx, n, k, pn, bp, seed, ar.Om, bp, 1));
+        RQB_CK(downdate_sketch<T>(cx, m, n, p, bp, Wsrc, ldws, Qi, ldq, Bi, ldb, ar.Om, W, ldw, ar.Y, m, ar.part,
+                                  ar.part_cap, sc.nrm, kNrmCap, sc.s + 2));
+        h->timer.end(h->stream);
+        RQB_CK(launch_stop_direct(cx, sc.s + 2, eps2));
+        Wsrc = W;
+        ldws = ldw;
+        if (flag == kAmbiguous) {
+            err = read_state(h, sc);
+            if (err != RQB_OK) { status = err; break; }
+            direct++;
+            if (blocks - 1 < RQB_MAX_TRACKED_BLOCKS) h->stats.D[blocks - 1] = h->hstate->D;
+            if (h->hstate->flag == kStop) { converged = true; break; }
+        }
+        if (k >= kcap) break;
+    }
+    if (status == RQB_OK) {
+        int err = read_state(h, sc);
+        if (err != RQB_OK) status = err;
+    }
+    h->stats.k = k;
+    h->stats.blocks = blocks;
+    h->stats.direct_tests = direct;
+    h->stats.normA2 = h->hstate->normA2;
+    h->stats.eps = eps;
+    h->stats.kernel_launches = cx.launches;
+    *k_out = k;
+    if (status != RQB_OK) return status;
+    if (!fixed && !converged) return RQB_NOT_CONVERGED;
+    return RQB_OK;
+}
+
+int check_matrix(const void* p, int64_t m, int64_t n, int64_t ld) {
+    if (!p || m <= 0 || n <= 0 || ld < m) return RQB_ERR_INVALID;
+    return RQB_OK;
+}
+
+int max_block(const rqb_handle h) { return h->cfg.dtype == RQB_F64 ? 128 : 256; }
+
+int set_device(rqb_handle h) { return cudaSetDevice(h->device) == cudaSuccess ? RQB_OK : RQB_ERR_CUDA; }
+
+int finish(rqb_handle h, int rc) {
+    h->last_status = rc;
+    h->stats.status = rc;
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rqb_status_string(int status) {
+    switch (status) {
+        case RQB_OK: return "ok";
+        case RQB_ERR_INVALID: return "invalid argument";
+        case RQB_ERR_NONFINITE: return "non-finite value in A";
+        case RQB_ERR_BREAKDOWN: return "Gram matrix of a panel is not positive definite";
+        case RQB_ERR_OOM: return "out of memory";
+        case RQB_ERR_TIMEOUT: return "bounded device wait expired";
+        case RQB_ERR_CUDA: return "CUDA runtime error";
+        case RQB_NOT_CONVERGED: return "rank cap reached before the tolerance";
+        case RQB_ERR_UNSUPPORTED: return "unsupported configuration";
+        default: return "unknown status";
+    }
+}
+
+int rqb_create(rqb_handle* out, const rqb_config* cfg) {
+    if (!out || !cfg) return RQB_ERR_INVALID;
+    *out = nullptr;
+    if ((cfg->flags & ~RQB_FLAG_PHASE_TIMING) != 0 || cfg->max_rank < 0 || cfg->power < 0) return RQB_ERR_INVALID;
+    if (cfg->dtype != RQB_F64 && cfg->dtype != RQB_F32 && cfg->dtype != RQB_BF16) return RQB_ERR_INVALID;
+    if (cfg->prec != RQB_PREC_NATIVE && cfg->prec != RQB_PREC_TF32X3 && cfg->prec != RQB_PREC_BF16)
+        return RQB_ERR_INVALID;
+    if (cfg->prec != RQB_PREC_NATIVE || cfg->dtype == RQB_BF16 || cfg->power != 0) return RQB_ERR_UNSUPPORTED;
+    rqb_handle h = new (std::nothrow) rqb_handle_s();
+    if (!h) return RQB_ERR_OOM;
+    h->cfg = *cfg;
+    h->stream = reinterpret_cast<cudaStream_t>(cfg->stream);
+    h->esize = (cfg->dtype == RQB_F64) ? 8 : 4;
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return RQB_ERR_CUDA;
+    }
+    if (h->state.ensure(256 + sizeof(double) * (kScalars + kNrmCap)) != RQB_OK ||
+        cudaMallocHost(reinterpret_cast<void**>(&h->hstate), sizeof(DevState)) != cudaSuccess) {
+        cudaGetLastError();
+        h->state.release();
+        delete h;
+        return RQB_ERR_OOM;
+    }
+    std::memset(h->hstate, 0, sizeof(DevState));
+    if ((cfg->flags & RQB_FLAG_PHASE_TIMING) && h->timer.create() != RQB_OK) {
+        h->timer.destroy();
+        cudaGetLastError();
+        h->state.release();
+        cudaFreeHost(h->hstate);
+        delete h;
+        return RQB_ERR_CUDA;
+    }
+    *out = h;
+    return RQB_OK;
+}
+
+int rqb_destroy(rqb_handle h) {
+    if (!h) return RQB_ERR_INVALID;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    h->state.release();
+    h->arena.release();
+    h->q.release();
+    h->b.release();
+    h->w.release();
+    h->ahost.release();
+    if (h->hstate) cudaFreeHost(h->hstate);
+    h->timer.destroy();
+    delete h;
+    return RQB_OK;
+}
+
+int rqb_factor(rqb_handle h, const void* A, int64_t m, int64_t n, int64_t lda, double eps, int64_t b,
+               uint64_t seed, const void** Q, int64_t* ldq, const void** B, int64_t* ldb, int64_t* k) {
+    if (!h) return RQB_ERR_INVALID;
+    if (check_matrix(A, m, n, lda) != RQB_OK || !Q || !ldq || !B || !ldb || !k || b < 1 || b > max_block(h) ||
+        !(eps >= 0.0) || !std::isfinite(eps))
+        return finish(h, RQB_ERR_INVALID);
+    if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
+    std::memset(&h->stats, 0, sizeof(h->stats));
+    int64_t kk = 0;
+    int rc = (h->cfg.dtype == RQB_F64)
+                 ? factor_impl<double>(h, static_cast<const double*>(A), m, n, lda, eps, b, seed, &kk)
+                 : factor_impl<float>(h, static_cast<const float*>(A), m, n, lda, eps, b, seed, &kk);
+    *Q = h->q.p;
+    *ldq = h->ldq;
+    *B = h->b.p;
+    *ldb = h->ldb;
+    *k = kk;
+    return finish(h, rc);
+}
+
+int rqb_factor_host(rqb_handle h, const void* A_host, int64_t m, int64_t n, int64_t lda, double eps, int64_t b,
+                    uint64_t seed, void* Q_host, int64_t ldq_host, void* B_host, int64_t ldb_host, int64_t* k) {
+    if (!h) return RQB_ERR_INVALID;
+    const int64_t rmax = std::min(m, n);
+    const int64_t kcap = (h->cfg.max_rank > 0 && h->cfg.max_rank < rmax) ? h->cfg.max_rank : rmax;
+    if (check_matrix(A_host, m, n, lda) != RQB_OK || !Q_host || !B_host || !k || ldq_host < m ||
+        ldb_host < kcap)
+        return finish(h, RQB_ERR_INVALID);
+    if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
+    const size_t es = h->esize;
+    int rc = h->ahost.ensure(es * (size_t)m * (size_t)n);
+    if (rc != RQB_OK) return finish(h, rc);
+    if (cudaMemcpy2DAsync(h->ahost.p, es * m, A_host, es * lda, es * m, n, cudaMemcpyHostToDevice, h->stream) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return finish(h, RQB_ERR_CUDA);
+    }
+    const void *Qd, *Bd;
+    int64_t ldq, ldb, kk = 0;
+    rc = rqb_factor(h, h->ahost.p, m, n, m, eps, b, seed, &Qd, &ldq, &Bd, &ldb, &kk);
+    *k = kk;
+    if (rc != RQB_OK && rc != RQB_NOT_CONVERGED) return finish(h, rc);
+    if (kk > 0) {
+        if (cudaMemcpy2DAsync(Q_host, es * ldq_host, Qd, es * ldq, es * m, kk, cudaMemcpyDeviceToHost, h->stream) !=
+                cudaSuccess ||
+            cudaMemcpy2DAsync(B_host, es * ldb_host, Bd, es * ldb, es * kk, n, cudaMemcpyDeviceToHost, h->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return finish(h, RQB_ERR_CUDA);
+        }
+    }
+    return finish(h, rc);
+}
+
+int rqb_get_stats(rqb_handle h, rqb_stats* out) {
+    if (!h || !out) return RQB_ERR_INVALID;
+    *out = h->stats;
+    out->status = h->last_status;
+    return RQB_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// step-level entry points
+extern "C" int rqb_omega(rqb_handle h, int64_t n, int64_t col0, int64_t ncols, uint64_t seed, void* Omega, int64_t ldo) {
+    if (!h) return RQB_ERR_INVALID;
+    if (!Omega || n <= 0 || ncols <= 0 || col0 < 0 || ldo < n || ncols > (int64_t)1 << 30)
+        return finish(h, RQB_ERR_INVALID);
+    if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
+    Scal sc = scalars(h);
+    Ctx cx;
+    cx.stream = h->stream; cx.num_sms = h->num_sms; cx.st = sc.st;
+    cudaError_t e = (h->cfg.dtype == RQB_F64)
+                        ? launch_omega<double>(cx, n, col0, (int)ncols, (int)ncols, seed,
+                                               static_cast<double*>(Omega), 1, ldo)
+                        : launch_omega<float>(cx, n, col0, (int)ncols, (int)ncols, seed, static_cast<float*>(Omega),
+                                              1, ldo);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return finish(h, cuda_status(e));
+}
+
+namespace {
+template <typename T>
+int sketch_impl(rqb_handle h, const T* A, int64_t m, int64_t n, int64_t lda, int64_t col0, int p, uint64_t seed,
+                T* Y, int64_t ldy, double* normA2) {
+    const int bp = pad_block(p);
+    Arena<T> ar;
+    int rc = ensure_arena<T>(h, m, n, bp, 1, &ar);
+    if (rc != RQB_OK) return rc;
+    Scal sc = scalars(h);
+    Ctx cx;
+    cx.stream = h->stream; cx.num_sms = h->num_sms; cx.st = sc.st;
+    RQB_CK(launch_omega<T>(cx, n, col0, p, bp, seed, ar.Om, bp, 1));
+    NNArgs<T> a;
+    a.m = m; a.K = n; a.nc = bp; a.nout = p;
+    a.X = A; a.ldx = lda;
+    a.C = ar.Om; a.csk = bp; a.csj = 1; a.c_rowmajor = true;
+    a.Out = Y; a.ldo = ldy;
+    a.part = ar.part; a.part_cap = ar.part_cap; a.allow_split = 1;
+    if (normA2) { a.nrm_part = sc.nrm; a.nrm_cap = kNrmCap; a.nrm_out = sc.s + 0; }
+    RQB_CK(gemm_nn<T>(cx, a));
+    if (normA2) RQB_CK(cudaMemcpyAsync(normA2, sc.s + 0, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    RQB_CK(cudaStreamSynchronize(h->stream));
+    return RQB_OK;
+}
+
+template <typename T>
+int orth_impl(rqb_handle h, const T* Y, int64_t m, int p, int64_t ldy, const T* Qbar, int64_t kprev, int64_t ldqb,
+              T* Qi, int64_t ldqi) {
+    const int bp = pad_block(p);
+    Arena<T> ar;
+    int rc = ensure_arena<T>(h, m, 1, bp, kprev, &ar);
+    if (rc != RQB_OK) return rc;
+    Scal sc = scalars(h);
+    Ctx cx;
+    cx.stream = h->stream; cx.num_sms = h->num_sms; cx.st = sc.st;
+    RQB_CK(cudaMemsetAsync(sc.st, 0, sizeof(DevState), h->stream));
+    // panel copy with zero padding to bp columns: Y_pad = Y * [I_p 0]
+    RQB_CK(cudaMemsetAsync(ar.Y, 0, sizeof(T) * (size_t)m * bp, h->stream));
+    RQB_CK(cudaMemcpy2DAsync(ar.Y, sizeof(T) * m, Y, sizeof(T) * ldy, sizeof(T) * m, p, cudaMemcpyDeviceToDevice,
+                             h->stream));
+    rc = orth_reproject<T>(h, cx, ar, ar.Y, m, m, p, bp, Qbar, kprev, ldqb, Qi, ldqi);
+    if (rc != RQB_OK) return rc;
+    return read_state(h, sc);
+}
+
+template <typename T>
+int project_impl(rqb_handle h, const T* Qi, int64_t m, int p, int64_t ldqi, const T* A, int64_t n, int64_t lda,
+                 T* Bi, int64_t ldbi, double* normB2) {
+    const int bp = pad_block(p);
+    Arena<T> ar;
+    int rc = ensure_arena<T>(h, m, n, bp, 1, &ar);
+    if (rc != RQB_OK) return rc;
+    Scal sc = scalars(h);
+    Ctx cx;
+    cx.stream = h->stream; cx.num_sms = h->num_sms; cx.st = sc.st;
+    RQB_CK(gemm_tn<T>(cx, m, p, n, Qi, ldqi, A, lda, Bi, ldbi, ar.part, ar.part_cap, sc.nrm, kNrmCap, sc.s + 1));
+    if (normB2) RQB_CK(cudaMemcpyAsync(normB2, sc.s + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    RQB_CK(cudaStreamSynchronize(h->stream));
+    return RQB_OK;
+}
+
+template <typename T>
+int dd_impl(rqb_handle h, const T* A, int64_t lda, const T* Qi, int64_t ldqi, const T* Bi, int64_t ldbi, int64_t m,
+            int64_t n, int p, T* W, int64_t ldw, int64_t col0, int ncols, uint64_t seed, T* Y, int64_t ldy,
+            double* normW2) {
+    const int bp = pad_block(std::max(p, ncols));
+    Arena<T> ar;
+    int rc = ensure_arena<T>(h, m, n, bp, 1, &ar);
+    if (rc != RQB_OK) return rc;
+    Scal sc = scalars(h);
+    Ctx cx;
+    cx.stream = h->stream; cx.num_sms = h->num_sms; cx.st = sc.st;
+    RQB_CK(launch_omega<T>(cx, n, col0, ncols, bp, seed, ar.Om, bp, 1));
+    RQB_CK(downdate_sketch<T>(cx, m, n, p, bp, A, lda, Qi, ldqi, Bi, ldbi, ar.Om, W, ldw, ar.Y, m, ar.part,
+                              ar.part_cap, sc.nrm, kNrmCap, sc.s + 2));
+    RQB_CK(cudaMemcpy2DAsync(Y, sizeof(T) * ldy, ar.Y, sizeof(T) * m, sizeof(T) * m, ncols, cudaMemcpyDeviceToDevice,
+                             h->stream));
+    if (normW2) RQB_CK(cudaMemcpyAsync(normW2, sc.s + 2, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    RQB_CK(cudaStreamSynchronize(h->stream));
+    return RQB_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int rqb_sketch(rqb_handle h, const void* A, int64_t m, int64_t n, int64_t lda, int64_t col0, int64_t ncols,
+               uint64_t seed, void* Y, int64_t ldy, double* normA2) {
+    if (!h) return RQB_ERR_INVALID;
+    if (check_matrix(A, m, n, lda) != RQB_OK || !Y || ncols < 1 || ncols > 256 || ldy < m || col0 < 0 ||
+        (h->cfg.dtype == RQB_F64 && ncols > 128))
+        return finish(h, RQB_ERR_INVALID);
+    if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
+    int rc = (h->cfg.dtype == RQB_F64)
+                 ? sketch_impl<double>(h, static_cast<const double*>(A), m, n, lda, col0, (int)ncols, seed,
+                                       static_cast<double*>(Y), ldy, normA2)
+                 : sketch_impl<float>(h, static_cast<const float*>(A), m, n, lda, col0, (int)ncols, seed,
+                                      static_cast<float*>(Y), ldy, normA2);
+    return finish(h, rc);
+}
+
+int rqb_orth(rqb_handle h, const void* Y, int64_t m, int64_t p, int64_t ldy, const void* Qbar, int64_t kprev,
+             int64_t ldqb, void* Qi, int64_t ldqi) {
+    if (!h) return RQB_ERR_INVALID;
+    if (check_matrix(Y, m, p, ldy) != RQB_OK || !Qi || ldqi < m || p > m || p > max_block(h) || kprev < 0 ||
+        (kprev > 0 && (!Qbar || ldqb < m)) || kprev + p > m)
+        return finish(h, RQB_ERR_INVALID);
+    if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
+    int rc = (h->cfg.dtype == RQB_F64)
+                 ? orth_impl<double>(h, static_cast<const double*>(Y), m, (int)p, ldy,
+                                     static_cast<const double*>(Qbar), kprev, ldqb, static_cast<double*>(Qi), ldqi)
+                 : orth_impl<float>(h, static_cast<const float*>(Y), m, (int)p, ldy, static_cast<const float*>(Qbar),
+                                    kprev, ldqb, static_cast<float*>(Qi), ldqi);
+    return finish(h, rc);
+}
+
+int rqb_project(rqb_handle h, const void* Qi, int64_t m, int64_t p, int64_t ldqi, const void* A, int64_t n,
+                int64_t lda, void* Bi, int64_t ldbi, double* normB2) {
+    if (!h) return RQB_ERR_INVALID;
+    if (check_matrix(Qi, m, p, ldqi) != RQB_OK || check_matrix(A, m, n, lda) != RQB_OK || !Bi || ldbi < p ||
+        p > max_block(h))
+        return finish(h, RQB_ERR_INVALID);
+    if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
+    int rc = (h->cfg.dtype == RQB_F64)
+                 ? project_impl<double>(h, static_cast<const double*>(Qi), m, (int)p, ldqi,
+                                        static_cast<const double*>(A), n, lda, static_cast<double*>(Bi), ldbi, normB2)
+                 : project_impl<float>(h, static_cast<const float*>(Qi), m, (int)p, ldqi,
+                                       static_cast<const float*>(A), n, lda, static_cast<float*>(Bi), ldbi, normB2);
+    return finish(h, rc);
+}
+
+int rqb_downdate_sketch(rqb_handle h, const void* A, int64_t lda, const void* Qi, int64_t ldqi, const void* Bi,
+                        int64_t ldbi, int64_t m, int64_t n, int64_t p, void* W, int64_t ldw, int64_t col0,
+                        int64_t ncols, uint64_t seed, void* Y, int64_t ldy, double* normW2) {
+    if (!h) return RQB_ERR_INVALID;
+    if (check_matrix(A, m, n, lda) != RQB_OK || check_matrix(Qi, m, p, ldqi) != RQB_OK ||
+        check_matrix(Bi, p, n, ldbi) != RQB_OK || check_matrix(W, m, n, ldw) != RQB_OK || !Y || ldy < m ||
+        ncols < 1 || ncols > max_block(h) || p > max_block(h) || col0 < 0 ||
+        (A == W && lda != ldw))
+        return finish(h, RQB_ERR_INVALID);
+    if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
+    int rc = (h->cfg.dtype == RQB_F64)
+                 ? dd_impl<double>(h, static_cast<const double*>(A), lda, static_cast<const double*>(Qi), ldqi,
+                                   static_cast<const double*>(Bi), ldbi, m, n, (int)p, static_cast<double*>(W), ldw,
+                                   col0, (int)ncols, seed, static_cast<double*>(Y), ldy, normW2)
+                 : dd_impl<float>(h, static_cast<const float*>(A), lda, static_cast<const float*>(Qi), ldqi,
+                                  static_cast<const float*>(Bi), ldbi, m, n, (int)p, static_cast<float*>(W), ldw, col0,
+                                  (int)ncols, seed, static_cast<float*>(Y), ldy, normW2);
+    return finish(h, rc);
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+// rqb_engine.h -- host-side launchers of the SIMT kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "rqb_internal.cuh"
+
+namespace rqb {
+
+struct Ctx {
+    cudaStream_t stream = nullptr;
+    int num_sms = 1;
+    DevState* st = nullptr;
+    int launches = 0;
+};
+
+// Arguments of Out = alpha * X C + beta * Yin (see k_gemm_nn).
+template <typename T>
+struct NNArgs {
+    int64_t m = 0, K = 0;
+    int nc = 0, nout = 0;
+    const T* X = nullptr;
+    int64_t ldx = 0;
+    const T* C = nullptr;
+    int64_t csk = 0, csj = 0;
+    bool c_rowmajor = false;
+    T* Out = nullptr;
+    int64_t ldo = 0;
+    T* part = nullptr;          // split partials (only when alpha = 1, beta = 0)
+    size_t part_cap = 0;        // elements
+    const T* Yin = nullptr;
+    int64_t ldyin = 0;
+    T alpha = T(1), beta = T(0);
+    int allow_split = 0;
+    double* nrm_part = nullptr; // non-NULL: also ||X||_F^2 into *nrm_out
+    int nrm_cap = 0;
+    double* nrm_out = nullptr;
+};
+
+template <typename T>
+cudaError_t launch_omega(Ctx& cx, int64_t n, int64_t col0, int ncols, int ncols_pad, uint64_t seed, T* out,
+                         int64_t rs, int64_t cs);
+template <typename T>
+cudaError_t launch_sumsq(Ctx& cx, int64_t m, int64_t n, const T* X, int64_t ldx, double* part, int part_cap,
+                         double* out);
+cudaError_t launch_sum_doubles(Ctx& cx, const double* part, int count, double* out);
+template <typename TP, typename TO>
+cudaError_t launch_reduce_split(Ctx& cx, int64_t rows, int64_t cols, int splits, const TP* part, int64_t ldp,
+                                int64_t zstride, TO* out, int64_t ldo, double* sq_part, int sq_cap,
+                                double* sq_out);
+template <typename T>
+cudaError_t gemm_nn(Ctx& cx, const NNArgs<T>& a);
+template <typename T>
+cudaError_t gemm_tn(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, int64_t ldx, const T* Y, int64_t ldy,
+                    T* Out, int64_t ldo, T* part, size_t part_cap_elems, double* sq_part, int sq_cap,
+                    double* sq_out);
+template <typename T>
+cudaError_t gemm_tn_f64acc(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, int64_t ldx, const T* Y,
+                           int64_t ldy, double* Out, int64_t ldo, double* part, size_t part_cap_elems);
+template <typename T>
+cudaError_t chol_inv(Ctx& cx, const double* G, int bp, int p, double* R, T* Rinv);
+template <typename T>
+cudaError_t downdate_sketch(Ctx& cx, int64_t m, int64_t n, int p, int bp, const T* Wsrc, int64_t ldws,
+                            const T* Qi, int64_t ldq, const T* Bi, int64_t ldb, const T* Om, T* Wdst,
+                            int64_t ldwd, T* Y, int64_t ldy, T* part, size_t part_cap_elems, double* nrm_part,
+                            int nrm_cap, double* nrm_out);
+cudaError_t launch_set_norm(Ctx& cx, const double* nrm);
+cudaError_t launch_stop_after_b(Ctx& cx, const double* nb2, double eps2, double tau_rel, int fixed);
+cudaError_t launch_stop_direct(Ctx& cx, const double* d2, double eps2);
+
+}  // namespace rqb

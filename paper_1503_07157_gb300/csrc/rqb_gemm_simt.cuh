@@ -1,0 +1,404 @@
+// rqb_gemm_simt.cuh -- register-blocked SIMT GEMM tiles for the tall-skinny
+// products of randQB_b (FP32 and FP64 pipes).
+//
+// Two shapes cover every product of Fig. randQB_b:
+//   NN:  Out (m x N) = alpha * X (m x K) * C (K x N) + beta * Yin
+//        -- the sketch A Omega (line (3)), Q_i = Y R^{-1}, Y - Qbar C (line (3'))
+//   TN:  Out (P x Q) = X^T (P x m) * Y (m x Q), a reduction over the m rows
+//        -- B_i = Q_i^T A (line (4)), Gram matrices and Qbar^T Y of the panel
+// Both split the reduction dimension over gridDim.z; each split writes its
+// own partial (deterministic two-stage reduction, no float atomics).
+//
+// Every global access is bounds-checked per element or per 16-byte vector
+// (a vector is used only when it is aligned and entirely in range).
+#pragma once
+
+#include "rqb_internal.cuh"
+
+namespace rqb {
+
+// Thread tile: float threads own 8 x 8 outputs, double threads 4 x 4; each
+// thread's rows are two groups of TM/2 contiguous rows, BM/2 apart, and its
+// columns two groups of TN/2, BN/2 apart (conflict-free vector smem reads).
+template <typename T> struct SimtTile;
+template <> struct SimtTile<float> { static constexpr int TM = 8, TN = 8; };
+template <> struct SimtTile<double> { static constexpr int TM = 4, TN = 4; };
+
+template <typename T, int H> struct VecH;   // H contiguous elements
+template <> struct VecH<float, 4> { using type = float4; };
+template <> struct VecH<float, 2> { using type = float2; };
+template <> struct VecH<double, 2> { using type = double2; };
+
+template <typename T, int H>
+__device__ __forceinline__ void lds_vec(T (&dst)[H], const T* src) {
+    using V = typename VecH<T, H>::type;
+    const V v = *reinterpret_cast<const V*>(src);
+    const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+    for (int i = 0; i < H; ++i) dst[i] = e[i];
+}
+
+// Load V16 consecutive elements p[0..V16) of a contiguous run whose valid
+// length from p is `valid` (<= 0: all zeros).  Uses one 16-byte load when the
+// run is complete and p is aligned.
+template <typename T>
+__device__ __forceinline__ void ldg_run(T* dst, const T* p, int64_t valid) {
+    constexpr int V = Vec16<T>::N;
+    if (valid >= V && aligned16(p)) {
+        using VT = typename Vec16<T>::type;
+        const VT v = __ldg(reinterpret_cast<const VT*>(p));
+        const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+        for (int i = 0; i < V; ++i) dst[i] = e[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) dst[i] = (i < valid) ? __ldg(p + i) : T(0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// NN: Out[z] (rows r0.., cols) = alpha * sum_{k in split z} X(r,k) C(k,j) + beta * Yin(r,j)
+// C(k, j) = C[k * csk + j * csj]; C_ROWMAJOR selects csj == 1 (else csk == 1).
+// Columns j >= nc read C as zero; only columns j < nout and rows r < m are written.
+template <typename T, int BM, int BN, int BK, bool C_ROWMAJOR>
+struct GemmNN {
+    static constexpr int TM = SimtTile<T>::TM, TN = SimtTile<T>::TN;
+    static constexpr int NT = (BM / TM) * (BN / TN);
+    static constexpr int V = Vec16<T>::N;
+    static constexpr int XVEC = BM * BK / V;   // 16-byte vectors per X tile
+    static constexpr int CVEC = BK * BN / V;
+    static_assert(XVEC % NT == 0 || NT % XVEC == 0, "X tile split");
+    static constexpr int XPER = (XVEC + NT - 1) / NT;
+    static constexpr int CPER = (CVEC + NT - 1) / NT;
+    static constexpr int SMEM_ELEMS = 2 * BK * (BM + BN);
+};
+
+template <typename T, int BM, int BN, int BK, bool C_ROWMAJOR>
+__global__ void __launch_bounds__(GemmNN<T, BM, BN, BK, C_ROWMAJOR>::NT)
+k_gemm_nn(int64_t m, int64_t K, int64_t ksplit, int nc, int nout,
+          const T* __restrict__ X, int64_t ldx,
+          const T* __restrict__ C, int64_t csk, int64_t csj,
+          T* Out, int64_t ldo, int64_t out_zstride,
+          const T* Yin, int64_t ldyin, T alpha, T beta, double* __restrict__ nrm_part) {
+    using G = GemmNN<T, BM, BN, BK, C_ROWMAJOR>;
+    constexpr int TM = G::TM, TN = G::TN, NT = G::NT, V = G::V;
+    constexpr int HM = TM / 2, HN = TN / 2;
+    __shared__ __align__(16) T As[2][BK][BM];
+    __shared__ __align__(16) T Bs[2][BK][BN];
+
+    const int tid = threadIdx.x;
+    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+    const int64_t r0 = (int64_t)blockIdx.x * BM;
+    const int j0 = blockIdx.y * BN;
+    const int64_t kbeg = (int64_t)blockIdx.z * ksplit;
+    const int64_t kend = (kbeg + ksplit < K) ? kbeg + ksplit : K;
+
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+
+    T xa[G::XPER][V];
+    T cb[G::CPER][V];
+    // ||X||_F^2 of the tiles this CTA reads (only the blockIdx.y == 0 column
+    // of CTAs counts, so every element of X is counted once)
+    const bool do_norm = (nrm_part != nullptr) && (blockIdx.y == 0);
+    double nacc = 0.0;
+
+    // X tile: vector v covers rows rr..rr+V of column kk (BM/V vectors per column)
+    auto load_x = [&](int64_t k0) {
+#pragma unroll
+        for (int t = 0; t < G::XPER; ++t) {
+            const int v = tid + t * NT;
+            if (v < G::XVEC) {
+                const int kk = v / (BM / V);
+                const int rr = (v % (BM / V)) * V;
+                const int64_t k = k0 + kk, r = r0 + rr;
+                if (k < kend && r < m) ldg_run<T>(xa[t], X + r + k * ldx, m - r);
+                else {
+#pragma unroll
+                    for (int i = 0; i < V; ++i) xa[t][i] = T(0);
+                }
+                if (do_norm) {
+                    T sq = T(0);
+#pragma unroll
+                    for (int i = 0; i < V; ++i) sq = fma(xa[t][i], xa[t][i], sq);
+                    nacc += (double)sq;
+                }
+            }
+        }
+    };
+    auto store_x = [&](int buf) {
+#pragma unroll
+        for (int t = 0; t < G::XPER; ++t) {
+            const int v = tid + t * NT;
+            if (v < G::XVEC) {
+                const int kk = v / (BM / V);
+                const int rr = (v % (BM / V)) * V;
+#pragma unroll
+                for (int i = 0; i < V; ++i) As[buf][kk][rr + i] = xa[t][i];
+            }
+        }
+    };
+    auto load_c = [&](int64_t k0) {
+#pragma unroll
+        for (int t = 0; t < G::CPER; ++t) {
+            const int v = tid + t * NT;
+            if (v < G::CVEC) {
+                if (C_ROWMAJOR) {   // vector along j
+                    const int kk = v / (BN / V);
+                    const int jj = (v % (BN / V)) * V;
+                    const int64_t k = k0 + kk;
+                    const int j = j0 + jj;
+                    if (k < kend && j < nc) ldg_run<T>(cb[t], C + k * csk + j, nc - j);
+                    else {
+#pragma unroll
+                        for (int i = 0; i < V; ++i) cb[t][i] = T(0);
+                    }
+                } else {            // vector along k
+                    const int jj = v / (BK / V);
+                    const int kk = (v % (BK / V)) * V;
+                    const int64_t k = k0 + kk;
+                    const int j = j0 + jj;
+                    if (k < kend && j < nc) ldg_run<T>(cb[t], C + k + (int64_t)j * csj, kend - k);
+                    else {
+#pragma unroll
+                        for (int i = 0; i < V; ++i) cb[t][i] = T(0);
+                    }
+                }
+            }
+        }
+    };
+    auto store_c = [&](int buf) {
+#pragma unroll
+        for (int t = 0; t < G::CPER; ++t) {
+            const int v = tid + t * NT;
+            if (v < G::CVEC) {
+                if (C_ROWMAJOR) {
+                    const int kk = v / (BN / V);
+                    const int jj = (v % (BN / V)) * V;
+#pragma unroll
+                    for (int i = 0; i < V; ++i) Bs[buf][kk][jj + i] = cb[t][i];
+                } else {
+                    const int jj = v / (BK / V);
+                    const int kk = (v % (BK / V)) * V;
+#pragma unroll
+                    for (int i = 0; i < V; ++i) Bs[buf][kk + i][jj] = cb[t][i];
+                }
+            }
+        }
+    };
+
+    int buf = 0;
+    if (kbeg < kend) {
+        load_x(kbeg);
+        load_c(kbeg);
+        store_x(0);
+        store_c(0);
+    }
+    __syncthreads();
+    for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+        const bool more = (k0 + BK < kend);
+        if (more) {
+            load_x(k0 + BK);
+            load_c(k0 + BK);
+        }
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[TM], b[TN];
+            T a0[HM], a1[HM], b0[HN], b1[HN];
+            lds_vec<T, HM>(a0, &As[buf][kk][ty * HM]);
+            lds_vec<T, HM>(a1, &As[buf][kk][BM / 2 + ty * HM]);
+            lds_vec<T, HN>(b0, &Bs[buf][kk][tx * HN]);
+            lds_vec<T, HN>(b1, &Bs[buf][kk][BN / 2 + tx * HN]);
+#pragma unroll
+            for (int i = 0; i < HM; ++i) { a[i] = a0[i]; a[HM + i] = a1[i]; }
+#pragma unroll
+            for (int j = 0; j < HN; ++j) { b[j] = b0[j]; b[HN + j] = b1[j]; }
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        if (more) {
+            store_x(buf ^ 1);
+            store_c(buf ^ 1);
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+
+    if (nrm_part != nullptr) {   // uniform per CTA
+        __shared__ double red[NT / 32];
+        double v = nacc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) red[tid >> 5] = v;
+        __syncthreads();
+        if (tid == 0 && do_norm) {
+            double t = 0.0;
+            for (int w = 0; w < NT / 32; ++w) t += red[w];
+            nrm_part[blockIdx.x + (int64_t)gridDim.x * blockIdx.z] = t;
+        }
+    }
+
+    // epilogue
+    T* out = Out + (int64_t)blockIdx.z * out_zstride;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int64_t r = r0 + ((i < HM) ? (ty * HM + i) : (BM / 2 + ty * HM + (i - HM)));
+        if (r >= m) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int c = j0 + ((j < HN) ? (tx * HN + j) : (BN / 2 + tx * HN + (j - HN)));
+            if (c >= nout) continue;
+            T v = alpha * acc[i][j];
+            if (beta != T(0)) v = fma(beta, Yin[r + (int64_t)c * ldyin], v);
+            out[r + (int64_t)c * ldo] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// TN: Out[z] (p x q) = sum over rows r of split z of X(r, p) * Y(r, q).
+// X is m x pn (ldx), Y is m x qn (ldy); rows >= m and columns beyond pn/qn
+// read as zero; outputs with p < pn, q < qn are written, type Acc.
+// With PROMOTE > 0 (Acc = double, T = float) the FP32 tile accumulators are
+// added into FP64 accumulators every PROMOTE row-chunks of BK rows.
+template <typename T, typename Acc, int BP, int BQ, int BK, int TP, int TQ, int PROMOTE>
+__global__ void __launch_bounds__((BP / TP) * (BQ / TQ))
+k_gemm_tn(int64_t m, int pn, int64_t qn, int64_t rsplit,
+          const T* __restrict__ X, int64_t ldx,
+          const T* __restrict__ Y, int64_t ldy,
+          Acc* __restrict__ Out, int64_t ldo, int64_t out_zstride) {
+    constexpr int NT = (BP / TP) * (BQ / TQ);
+    constexpr int V = Vec16<T>::N;
+    constexpr int HP = TP / 2, HQ = TQ / 2;
+    constexpr int XVEC = BP * BK / V, YVEC = BQ * BK / V;
+    constexpr int XPER = (XVEC + NT - 1) / NT, YPER = (YVEC + NT - 1) / NT;
+    constexpr int PAD = 4;   // breaks the 4-way bank conflict of the transposed stores
+    __shared__ __align__(16) T Xs[2][BK][BP + PAD];
+    __shared__ __align__(16) T Ys[2][BK][BQ + PAD];
+
+    const int tid = threadIdx.x;
+    const int tq = tid % (BQ / TQ), tp = tid / (BQ / TQ);
+    const int p0 = blockIdx.x * BP;
+    const int64_t q0 = (int64_t)blockIdx.y * BQ;
+    const int64_t rbeg = (int64_t)blockIdx.z * rsplit;
+    const int64_t rend = (rbeg + rsplit < m) ? rbeg + rsplit : m;
+
+    T acc[TP][TQ];
+    Acc acc2[TP][TQ];
+#pragma unroll
+    for (int i = 0; i < TP; ++i)
+#pragma unroll
+        for (int j = 0; j < TQ; ++j) { acc[i][j] = T(0); acc2[i][j] = Acc(0); }
+
+    T xa[XPER][V], ya[YPER][V];
+    // vector v: column cc = v / (BK/V), rows kk..kk+V
+    auto load = [&](int64_t rr0) {
+#pragma unroll
+        for (int t = 0; t < XPER; ++t) {
+            const int v = tid + t * NT;
+            if (v < XVEC) {
+                const int cc = v / (BK / V), kk = (v % (BK / V)) * V;
+                const int p = p0 + cc;
+                const int64_t r = rr0 + kk;
+                if (p < pn && r < rend) ldg_run<T>(xa[t], X + r + (int64_t)p * ldx, rend - r);
+                else {
+#pragma unroll
+                    for (int i = 0; i < V; ++i) xa[t][i] = T(0);
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < YPER; ++t) {
+            const int v = tid + t * NT;
+            if (v < YVEC) {
+                const int cc = v / (BK / V), kk = (v % (BK / V)) * V;
+                const int64_t q = q0 + cc;
+                const int64_t r = rr0 + kk;
+                if (q < qn && r < rend) ldg_run<T>(ya[t], Y + r + q * ldy, rend - r);
+                else {
+#pragma unroll
+                    for (int i = 0; i < V; ++i) ya[t][i] = T(0);
+                }
+            }
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int t = 0; t < XPER; ++t) {
+            const int v = tid + t * NT;
+            if (v < XVEC) {
+                const int cc = v / (BK / V), kk = (v % (BK / V)) * V;
+#pragma unroll
+                for (int i = 0; i < V; ++i) Xs[buf][kk + i][cc] = xa[t][i];
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < YPER; ++t) {
+            const int v = tid + t * NT;
+            if (v < YVEC) {
+                const int cc = v / (BK / V), kk = (v % (BK / V)) * V;
+#pragma unroll
+                for (int i = 0; i < V; ++i) Ys[buf][kk + i][cc] = ya[t][i];
+            }
+        }
+    };
+
+    int buf = 0;
+    if (rbeg < rend) {
+        load(rbeg);
+        store(0);
+    }
+    __syncthreads();
+    int chunk = 0;
+    for (int64_t rr0 = rbeg; rr0 < rend; rr0 += BK) {
+        const bool more = (rr0 + BK < rend);
+        if (more) load(rr0 + BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[TP], b[TQ];
+            T a0[HP], a1[HP], b0[HQ], b1[HQ];
+            lds_vec<T, HP>(a0, &Xs[buf][kk][tp * HP]);
+            lds_vec<T, HP>(a1, &Xs[buf][kk][BP / 2 + tp * HP]);
+            lds_vec<T, HQ>(b0, &Ys[buf][kk][tq * HQ]);
+            lds_vec<T, HQ>(b1, &Ys[buf][kk][BQ / 2 + tq * HQ]);
+#pragma unroll
+            for (int i = 0; i < HP; ++i) { a[i] = a0[i]; a[HP + i] = a1[i]; }
+#pragma unroll
+            for (int j = 0; j < HQ; ++j) { b[j] = b0[j]; b[HQ + j] = b1[j]; }
+#pragma unroll
+            for (int i = 0; i < TP; ++i)
+#pragma unroll
+                for (int j = 0; j < TQ; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        if (PROMOTE > 0 && ++chunk == PROMOTE) {
+            chunk = 0;
+#pragma unroll
+            for (int i = 0; i < TP; ++i)
+#pragma unroll
+                for (int j = 0; j < TQ; ++j) { acc2[i][j] += (Acc)acc[i][j]; acc[i][j] = T(0); }
+        }
+        if (more) store(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+    }
+
+    Acc* out = Out + (int64_t)blockIdx.z * out_zstride;
+#pragma unroll
+    for (int i = 0; i < TP; ++i) {
+        const int p = p0 + ((i < HP) ? (tp * HP + i) : (BP / 2 + tp * HP + (i - HP)));
+        if (p >= pn) continue;
+#pragma unroll
+        for (int j = 0; j < TQ; ++j) {
+            const int64_t q = q0 + ((j < HQ) ? (tq * HQ + j) : (BQ / 2 + tq * HQ + (j - HQ)));
+            if (q >= qn) continue;
+            out[p + q * ldo] = (PROMOTE > 0) ? (acc2[i][j] + (Acc)acc[i][j]) : (Acc)acc[i][j];
+        }
+    }
+}
+
+}  // namespace rqb

@@ -1,0 +1,746 @@
+// rqb_kernels.cu -- SIMT kernels of the randQB_b hot path and their launchers.
+//
+// Steps of Fig. randQB_b and the kernels that carry them:
+//   line (2)   Omega_i = randn(n, b)             k_omega
+//   line (3)   A Omega_i (first block)           k_gemm_nn (+ ||A||_F^2 on the same read)
+//   line (3)/(3') orth + re-projection           CholeskyQR2: k_gemm_tn (FP64 Gram),
+//                                                k_cholesky (FP64), k_tri_inverse,
+//                                                k_gemm_nn (Y R^{-1}, Y - Qbar C)
+//   line (4)   B_i = Q_i^T A                     k_gemm_tn + k_reduce_split (+ ||B_i||^2)
+//   line (5)   A = A - Q_i B_i, fused with line (3) of block i+1:
+//                                                k_downdate_sketch (+ ||A^(i)||_F^2)
+//   line (6)   stop test                         k_stop_after_b / k_stop_direct
+#include <algorithm>
+#include <cstdio>
+
+#include "rqb_engine.h"
+#include "rqb_gemm_simt.cuh"
+
+namespace rqb {
+
+// ---------------------------------------------------------------------------
+// line (2): Omega entries; out[r * rs + c * cs] for r < n, c < ncols_pad,
+// columns c >= ncols are zero (padding of the block to the tile width).
+template <typename T>
+__global__ void k_omega(int64_t n, int64_t col0, int ncols, int ncols_pad, uint64_t seed,
+                        T* __restrict__ out, int64_t rs, int64_t cs) {
+    const int64_t total = n * (int64_t)ncols_pad;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r, c;
+        if (rs == 1) { r = e % n; c = e / n; }       // column-major target: walk rows
+        else { c = e % ncols_pad; r = e / ncols_pad; }
+        const T v = (c < ncols) ? gaussian<T>(seed, r, col0 + c) : T(0);
+        out[r * rs + c * cs] = v;
+    }
+}
+
+template <typename T>
+cudaError_t launch_omega(Ctx& cx, int64_t n, int64_t col0, int ncols, int ncols_pad, uint64_t seed,
+                         T* out, int64_t rs, int64_t cs) {
+    const int64_t total = n * (int64_t)ncols_pad;
+    int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)cx.num_sms * 8);
+    if (blocks < 1) blocks = 1;
+    k_omega<T><<<blocks, 256, 0, cx.stream>>>(n, col0, ncols, ncols_pad, seed, out, rs, cs);
+    cx.launches++;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic block reduction of one double per thread (fixed tree).
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < NT / 32; ++w) r += sh[w];
+    }
+    __syncthreads();
+    return r;  // valid in thread 0
+}
+
+// Sum of squares of an m x n matrix (FP64 accumulation), one partial per CTA.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sumsq(int64_t m, int64_t n, const T* __restrict__ X, int64_t ldx,
+                                               double* __restrict__ part) {
+    __shared__ double sh[8];
+    double acc = 0.0;
+    const int64_t total = m * n;
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < total; e += (int64_t)gridDim.x * 256) {
+        const int64_t r = e % m, c = e / m;
+        const double v = (double)X[r + c * ldx];
+        acc += v * v;
+    }
+    const double s = block_sum<256>(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// Sum `count` doubles in a fixed order into *out (single CTA).
+__global__ void __launch_bounds__(256) k_sum_doubles(const double* __restrict__ part, int count,
+                                                     double* __restrict__ out) {
+    __shared__ double sh[8];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < count; i += 256) acc += part[i];
+    const double s = block_sum<256>(acc, sh);
+    if (threadIdx.x == 0) *out = s;
+}
+
+cudaError_t launch_sum_doubles(Ctx& cx, const double* part, int count, double* out) {
+    k_sum_doubles<<<1, 256, 0, cx.stream>>>(part, count, out);
+    cx.launches++;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sumsq(Ctx& cx, int64_t m, int64_t n, const T* X, int64_t ldx, double* part, int part_cap,
+                         double* out) {
+    int blocks = std::min<int>(part_cap, cx.num_sms * 4);
+    blocks = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (m * n + 255) / 256));
+    k_sumsq<T><<<blocks, 256, 0, cx.stream>>>(m, n, X, ldx, part);
+    cx.launches++;
+    return launch_sum_doubles(cx, part, blocks, out);
+}
+
+// ---------------------------------------------------------------------------
+// Split reduction: out(r, c) = sum_z part[z](r, c) (FP64 sum in z order), for
+// r < rows, c < cols; optional sum of squares of the stored outputs, one
+// partial per CTA.
+template <typename TP, typename TO>
+__global__ void __launch_bounds__(256)
+k_reduce_split(int64_t rows, int64_t cols, int splits, const TP* __restrict__ part, int64_t ldp,
+               int64_t zstride, TO* __restrict__ out, int64_t ldo, double* __restrict__ sq_part) {
+    __shared__ double sh[8];
+    double sq = 0.0;
+    const int64_t total = rows * cols;
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < total; e += (int64_t)gridDim.x * 256) {
+        const int64_t r = e % rows, c = e / rows;
+        double s = 0.0;
+        for (int z = 0; z < splits; ++z) s += (double)part[z * zstride + r + c * ldp];
+        const TO v = (TO)s;
+        out[r + c * ldo] = v;
+        sq += (double)v * (double)v;
+    }
+    if (sq_part) {
+        const double t = block_sum<256>(sq, sh);
+        if (threadIdx.x == 0) sq_part[blockIdx.x] = t;
+    }
+}
+
+template <typename TP, typename TO>
+cudaError_t launch_reduce_split(Ctx& cx, int64_t rows, int64_t cols, int splits, const TP* part, int64_t ldp,
+                                int64_t zstride, TO* out, int64_t ldo, double* sq_part, int sq_cap,
+                                double* sq_out) {
+    int blocks = std::max<int64_t>(1, std::min<int64_t>((rows * cols + 255) / 256, (int64_t)cx.num_sms * 8));
+    if (sq_part) blocks = std::min(blocks, sq_cap);
+    k_reduce_split<TP, TO><<<blocks, 256, 0, cx.stream>>>(rows, cols, splits, part, ldp, zstride, out, ldo,
+                                                           sq_part);
+    cx.launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !sq_part) return e;
+    return launch_sum_doubles(cx, sq_part, blocks, sq_out);
+}
+
+// ---------------------------------------------------------------------------
+// CholeskyQR factor of the panel Gram matrix: G (bp x bp, FP64, symmetric;
+// only rows/cols < p are meaningful) = R^T R with R upper triangular and
+// diag(R) > 0; rows/cols >= p are set to the identity.  Right-looking
+// column algorithm in FP64, one CTA; the working copy lives in shared memory
+// when it fits, else in R itself (global).  A pivot <= tol * G_jj(original)
+// records RQB_ERR_BREAKDOWN.
+template <int NT>
+__global__ void __launch_bounds__(NT)
+k_cholesky(const double* __restrict__ G, int ldg, int bp, int p, double* __restrict__ R, int use_smem,
+           double tol, DevState* st) {
+    extern __shared__ __align__(16) double dsm[];
+    double* S = use_smem ? dsm : R;   // column-major bp x bp, ld = bp
+    __shared__ int bad;
+    __shared__ double rowj[256];
+    const int tid = threadIdx.x;
+    if (tid == 0) bad = 0;
+    for (int e = tid; e < bp * bp; e += NT) {
+        const int r = e % bp, c = e / bp;
+        double v;
+        if (r < p && c < p) v = (r <= c) ? G[r + c * ldg] : 0.0;
+        else v = (r == c) ? 1.0 : 0.0;
+        S[r + c * bp] = v;
+    }
+    __syncthreads();
+    for (int j = 0; j < p; ++j) {
+        if (tid == 0) {
+            const double d = S[j + j * bp];
+            const double ref = G[j + j * ldg];
+            if (!(d > tol * ref) || !(d > 0.0) || !isfinite(d)) {
+                bad = 1;
+                S[j + j * bp] = 1.0;
+            } else {
+                S[j + j * bp] = sqrt(d);
+            }
+        }
+        __syncthreads();
+        if (bad) break;
+        const double rjj = S[j + j * bp];
+        // row j of R, also staged contiguously for the trailing update
+        for (int c = j + 1 + tid; c < p; c += NT) {
+            const double v = S[j + c * bp] / rjj;
+            S[j + c * bp] = v;
+            rowj[c] = v;
+        }
+        __syncthreads();
+        // trailing update of the upper triangle: S[r][c] -= R[j][r] R[j][c], j < r <= c < p;
+        // one warp per column c (rows contiguous in the column-major layout)
+        const int lane = tid & 31, warp = tid >> 5;
+        for (int c = j + 1 + warp; c < p; c += NT / 32) {
+            const double rjc = rowj[c];
+            for (int r = j + 1 + lane; r <= c; r += 32) S[r + c * bp] -= rowj[r] * rjc;
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        if (tid == 0) record_error(st, RQB_ERR_BREAKDOWN);
+        return;
+    }
+    if (use_smem) {
+        for (int e = tid; e < bp * bp; e += NT) {
+            const int r = e % bp, c = e / bp;
+            R[e] = (r <= c) ? S[e] : 0.0;
+        }
+    } else {
+        for (int e = tid; e < bp * bp; e += NT) {
+            const int r = e % bp, c = e / bp;
+            if (r > c) R[e] = 0.0;
+        }
+    }
+}
+
+// Rinv (bp x bp, type T, column-major) = R^{-1} for upper-triangular R (FP64).
+// CTA c solves R x = e_c by column-oriented back substitution with the
+// leading (c+1) x (c+1) block of R staged in shared memory when it fits.
+template <typename T>
+__global__ void __launch_bounds__(128)
+k_tri_inverse(const double* __restrict__ R, int bp, T* __restrict__ Rinv, int smem_cols) {
+    extern __shared__ __align__(16) double dsm[];
+    const int c = blockIdx.x;
+    const int tid = threadIdx.x;
+    double* x = dsm;                 // bp entries: right-hand side / solution
+    double* Rs = dsm + bp;           // columns 0..c of R when staged (ld = bp)
+    const bool staged = (c < smem_cols);
+    if (staged) {
+        for (int e = tid; e < (c + 1) * bp; e += 128) Rs[e] = R[e];
+    }
+    for (int r = tid; r < bp; r += 128) x[r] = (r == c) ? 1.0 : 0.0;
+    __syncthreads();
+    const double* Rc = staged ? Rs : R;
+    for (int t = c; t >= 0; --t) {
+        const double xt = x[t] / Rc[t + t * bp];
+        __syncthreads();
+        if (tid == 0) x[t] = xt;
+        for (int r = tid; r < t; r += 128) x[r] -= Rc[r + t * bp] * xt;
+        __syncthreads();
+    }
+    for (int r = tid; r < bp; r += 128) Rinv[r + (int64_t)c * bp] = (T)((r <= c) ? x[r] : 0.0);
+}
+
+// ---------------------------------------------------------------------------
+// Stopping test (line (6)).  After B_i:  E -= ||B_i||^2 and
+//   E <= eps2 - tau  -> stop;  E > eps2 + tau -> continue;  else ambiguous
+// (decided on the direct norm after the downdate).  tau is the rounding band
+// of E in the working precision.
+__global__ void k_set_norm(DevState* st, const double* nrm) {
+    const double v = *nrm;
+    st->normA2 = v;
+    st->E = v;
+    st->flag = kContinue;
+    if (!isfinite(v)) record_error(st, RQB_ERR_NONFINITE);
+}
+
+__global__ void k_stop_after_b(DevState* st, const double* nb2, double eps2, double tau_rel, int fixed) {
+    const double tau = tau_rel * st->normA2;
+    const double b2 = *nb2;
+    st->normB2 = b2;
+    st->E -= b2;
+    st->D = -1.0;
+    if (!isfinite(b2)) record_error(st, RQB_ERR_NONFINITE);
+    const double E = st->E;
+    if (fixed) st->flag = kContinue;
+    else if (E <= eps2 - tau) st->flag = kStop;
+    else if (E > eps2 + tau) st->flag = kContinue;
+    else st->flag = kAmbiguous;
+}
+
+__global__ void k_stop_direct(DevState* st, const double* d2, double eps2) {
+    const double d = *d2;
+    st->D = d;
+    if (st->flag == kAmbiguous) st->flag = (d <= eps2) ? kStop : kContinue;
+}
+
+cudaError_t launch_set_norm(Ctx& cx, const double* nrm) {
+    k_set_norm<<<1, 1, 0, cx.stream>>>(cx.st, nrm);
+    cx.launches++;
+    return cudaGetLastError();
+}
+cudaError_t launch_stop_after_b(Ctx& cx, const double* nb2, double eps2, double tau_rel, int fixed) {
+    k_stop_after_b<<<1, 1, 0, cx.stream>>>(cx.st, nb2, eps2, tau_rel, fixed);
+    cx.launches++;
+    return cudaGetLastError();
+}
+cudaError_t launch_stop_direct(Ctx& cx, const double* d2, double eps2) {
+    k_stop_direct<<<1, 1, 0, cx.stream>>>(cx.st, d2, eps2);
+    cx.launches++;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// line (5) fused with line (3) of the next block.  CTA (x, z) owns rows
+// [x BM, x BM + BM) and the column range of split z.  Per column chunk of BC
+// columns:  Wn = Wsrc - Q_i B_i (GEMM 1, K = bp), stored to Wdst and, transposed,
+// to shared memory; then Yacc += Wn Omega_next(chunk, :) (GEMM 2, K = BC).
+// Also ||Wn||_F^2 (FP64 partial per CTA).
+template <typename T, int BM, int BN>
+struct DDCfg {
+    static constexpr int TM = SimtTile<T>::TM, TN = SimtTile<T>::TN;
+    static constexpr int NT = (BM / TM) * (BN / TN);
+    static constexpr int BC = 2 * NT * TM / BM;          // chunk columns: GEMM 1 thread tile TM x 2
+    static constexpr int TN1 = BM * BC / (NT * TM);      // == 2
+    static constexpr size_t SMEM = sizeof(T) * ((size_t)BN * BM + (size_t)BN * BC + (size_t)BC * BM +
+                                                (size_t)BC * BN);
+    static_assert(TN1 == 2, "GEMM 1 tile");
+};
+
+template <typename T, int BM, int BN>
+__global__ void __launch_bounds__(DDCfg<T, BM, BN>::NT)
+k_downdate_sketch(int64_t m, int64_t n, int p, int64_t csplit,
+                  const T* Wsrc, int64_t ldws, const T* __restrict__ Qi, int64_t ldq,
+                  const T* __restrict__ Bi, int64_t ldb, const T* __restrict__ Om /* n x BN row-major */,
+                  T* Wdst, int64_t ldwd, T* __restrict__ Ypart, int64_t ldyp, int64_t yzstride,
+                  double* __restrict__ nrm_part) {
+    using C = DDCfg<T, BM, BN>;
+    constexpr int TM = C::TM, TN = C::TN, NT = C::NT, BC = C::BC, V = Vec16<T>::N;
+    constexpr int HM = TM / 2, HN = TN / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* Qs = reinterpret_cast<T*>(smem_raw);   // [BN][BM]  Qs[t*BM + r] = Q(r0 + r, t)
+    T* Bs = Qs + BN * BM;                      // [BN][BC]  Bs[t*BC + c] = B(t, c0 + c)
+    T* Ws = Bs + BN * BC;                      // [BC][BM]  Ws[c*BM + r] = Wn(r0 + r, c0 + c)
+    T* Os = Ws + BC * BM;                      // [BC][BN]  Os[c*BN + j] = Omega(c0 + c, j)
+    __shared__ double red[NT / 32];
+
+    const int tid = threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.x * BM;
+    const int64_t cbeg = (int64_t)blockIdx.z * csplit;
+    const int64_t cend = (cbeg + csplit < n) ? cbeg + csplit : n;
+
+    // stage Q_i rows of this tile (once)
+    for (int v = tid; v < BN * (BM / V); v += NT) {
+        const int t = v / (BM / V), rr = (v % (BM / V)) * V;
+        const int64_t r = r0 + rr;
+        T tmp[V];
+        if (t < p && r < m) ldg_run<T>(tmp, Qi + r + (int64_t)t * ldq, m - r);
+        else {
+#pragma unroll
+            for (int i = 0; i < V; ++i) tmp[i] = T(0);
+        }
+#pragma unroll
+        for (int i = 0; i < V; ++i) Qs[t * BM + rr + i] = tmp[i];
+    }
+
+    // GEMM 2 (Y) thread tile
+    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+    // GEMM 1 (downdate) thread tile: TM rows x 2 columns (c = tx1, BC/2 + tx1)
+    const int tx1 = tid % (BC / 2), ty1 = tid / (BC / 2);
+
+    T yacc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) yacc[i][j] = T(0);
+    double nrm = 0.0;
+
+    for (int64_t c0 = cbeg; c0 < cend; c0 += BC) {
+        __syncthreads();   // previous chunk's readers of Bs/Ws/Os are done (and Qs staged)
+        // B_i chunk: column c of B is p contiguous entries
+        for (int v = tid; v < BC * (BN / V); v += NT) {
+            const int cc = v / (BN / V), tt = (v % (BN / V)) * V;
+            const int64_t c = c0 + cc;
+            T tmp[V];
+            if (c < cend && tt < p) ldg_run<T>(tmp, Bi + tt + c * ldb, p - tt);
+            else {
+#pragma unroll
+                for (int i = 0; i < V; ++i) tmp[i] = T(0);
+            }
+#pragma unroll
+            for (int i = 0; i < V; ++i) Bs[(tt + i) * BC + cc] = tmp[i];
+        }
+        // Omega chunk rows (row-major, BN per row)
+        for (int v = tid; v < BC * (BN / V); v += NT) {
+            const int cc = v / (BN / V), jj = (v % (BN / V)) * V;
+            const int64_t c = c0 + cc;
+            T tmp[V];
+            if (c < cend) ldg_run<T>(tmp, Om + c * BN + jj, BN - jj);
+            else {
+#pragma unroll
+                for (int i = 0; i < V; ++i) tmp[i] = T(0);
+            }
+#pragma unroll
+            for (int i = 0; i < V; ++i) Os[cc * BN + jj + i] = tmp[i];
+        }
+        __syncthreads();
+
+        // GEMM 1: P = Q_tile * B_chunk
+        T pacc[TM][2];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) { pacc[i][0] = T(0); pacc[i][1] = T(0); }
+        for (int t = 0; t < BN; ++t) {
+            T a0[HM], a1[HM];
+            lds_vec<T, HM>(a0, &Qs[t * BM + ty1 * HM]);
+            lds_vec<T, HM>(a1, &Qs[t * BM + BM / 2 + ty1 * HM]);
+            const T b0 = Bs[t * BC + tx1], b1 = Bs[t * BC + BC / 2 + tx1];
+#pragma unroll
+            for (int i = 0; i < HM; ++i) {
+                pacc[i][0] = fma(a0[i], b0, pacc[i][0]);
+                pacc[i][1] = fma(a0[i], b1, pacc[i][1]);
+                pacc[HM + i][0] = fma(a1[i], b0, pacc[HM + i][0]);
+                pacc[HM + i][1] = fma(a1[i], b1, pacc[HM + i][1]);
+            }
+        }
+        // Wn = Wsrc - P; store to Wdst and Ws; accumulate ||Wn||^2
+        T part_sq = T(0);
+#pragma unroll
+        for (int jc = 0; jc < 2; ++jc) {
+            const int cc = (jc == 0) ? tx1 : (BC / 2 + tx1);
+            const int64_t c = c0 + cc;
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                const int rr = (g == 0) ? ty1 * HM : (BM / 2 + ty1 * HM);
+                const int64_t r = r0 + rr;
+                T w[HM];
+                if (c < cend && r < m) {
+                    const T* src = Wsrc + r + c * ldws;
+                    if (r + HM <= m && aligned16(src) && HM * sizeof(T) == 16) {
+                        lds_vec<T, HM>(w, src);   // aligned 16-byte global load
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < HM; ++i) w[i] = (r + i < m) ? src[i] : T(0);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < HM; ++i) w[i] = T(0);
+                }
+#pragma unroll
+                for (int i = 0; i < HM; ++i) {
+                    w[i] -= pacc[g * HM + i][jc];
+                    if (!(c < cend && r + i < m)) w[i] = T(0);
+                    part_sq = fma(w[i], w[i], part_sq);
+                    Ws[cc * BM + rr + i] = w[i];
+                }
+                if (c < cend && r < m) {
+                    T* dst = Wdst + r + c * ldwd;
+                    if (r + HM <= m && aligned16(dst) && HM * sizeof(T) == 16) {
+                        using VT = typename VecH<T, HM>::type;
+                        *reinterpret_cast<VT*>(dst) = *reinterpret_cast<const VT*>(w);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < HM; ++i)
+                            if (r + i < m) dst[i] = w[i];
+                    }
+                }
+            }
+        }
+        nrm += (double)part_sq;
+        __syncthreads();
+
+        // GEMM 2: Yacc += Wn(chunk) * Omega(chunk, :)
+#pragma unroll 4
+        for (int kk = 0; kk < BC; ++kk) {
+            T a[TM], b[TN], a0[HM], a1[HM], b0[HN], b1[HN];
+            lds_vec<T, HM>(a0, &Ws[kk * BM + ty * HM]);
+            lds_vec<T, HM>(a1, &Ws[kk * BM + BM / 2 + ty * HM]);
+            lds_vec<T, HN>(b0, &Os[kk * BN + tx * HN]);
+            lds_vec<T, HN>(b1, &Os[kk * BN + BN / 2 + tx * HN]);
+#pragma unroll
+            for (int i = 0; i < HM; ++i) { a[i] = a0[i]; a[HM + i] = a1[i]; }
+#pragma unroll
+            for (int j = 0; j < HN; ++j) { b[j] = b0[j]; b[HN + j] = b1[j]; }
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) yacc[i][j] = fma(a[i], b[j], yacc[i][j]);
+        }
+    }
+
+    // Y partial of this split
+    T* yout = Ypart + (int64_t)blockIdx.z * yzstride;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int64_t r = r0 + ((i < HM) ? (ty * HM + i) : (BM / 2 + ty * HM + (i - HM)));
+        if (r >= m) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int c = (j < HN) ? (tx * HN + j) : (BN / 2 + tx * HN + (j - HN));
+            yout[r + (int64_t)c * ldyp] = yacc[i][j];
+        }
+    }
+    // ||Wn||^2 partial
+    double v = nrm;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int w = 0; w < NT / 32; ++w) s += red[w];
+        nrm_part[blockIdx.x + (int64_t)gridDim.x * blockIdx.z] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launch configuration helpers
+static int choose_splits(int64_t tiles, int64_t kdim, int64_t kmin, int max_splits, int slots) {
+    int best = 1;
+    double best_score = -1.0;
+    for (int s = 1; s <= max_splits; ++s) {
+        if (s > 1 && kdim / s < kmin) break;
+        const int64_t ctas = tiles * s;
+        const int64_t waves = (ctas + slots - 1) / slots;
+        const double eff = (double)ctas / (double)(waves * slots);
+        const double score = eff - 0.004 * s;
+        if (score > best_score + 1e-9) { best_score = score; best = s; }
+    }
+    return best;
+}
+
+template <typename K>
+static int occupancy(K kernel, int threads, size_t dyn_smem) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, dyn_smem) != cudaSuccess || nb < 1)
+        nb = 1;
+    return nb;
+}
+
+// Tile table ---------------------------------------------------------------
+// NN: float BM = 128 (64 for BN = 256), BN = bp; double BM = 64, BN = min(bp, 128).
+template <typename T> struct NNTile;
+template <> struct NNTile<float> { static constexpr int BK = 8; };
+template <> struct NNTile<double> { static constexpr int BK = 8; };
+
+template <typename T, int BM, int BN, bool ROWC>
+static cudaError_t nn_launch(Ctx& cx, const NNArgs<T>& a) {
+    using G = GemmNN<T, BM, BN, NNTile<T>::BK, ROWC>;
+    auto kern = k_gemm_nn<T, BM, BN, NNTile<T>::BK, ROWC>;
+    const int64_t mt = (a.m + BM - 1) / BM;
+    const int nt = (std::max(a.nc, a.nout) + BN - 1) / BN;
+    const int slots = cx.num_sms * occupancy(kern, G::NT, 0);
+    bool allow_split = a.allow_split && a.part && a.alpha == T(1) && a.beta == T(0);
+    int splits = 1;
+    if (allow_split) {
+        const int64_t per = a.m * (int64_t)nt * BN;
+        int64_t maxs = std::min<int64_t>(32, (int64_t)(a.part_cap / (size_t)std::max<int64_t>(per, 1)));
+        if (a.nrm_part) maxs = std::min<int64_t>(maxs, a.nrm_cap / std::max<int64_t>(mt, 1));
+        splits = choose_splits(mt * nt, a.K, 256, (int)std::max<int64_t>(1, maxs), slots);
+    }
+    int64_t ks = (a.K + splits - 1) / splits;
+    ks = ((ks + NNTile<T>::BK - 1) / NNTile<T>::BK) * NNTile<T>::BK;
+    if (ks < NNTile<T>::BK) ks = NNTile<T>::BK;
+    splits = (int)std::max<int64_t>(1, (a.K + ks - 1) / ks);
+    if (a.nrm_part && mt * splits > a.nrm_cap) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)mt, (unsigned)nt, (unsigned)splits);
+    if (splits == 1) {
+        kern<<<grid, G::NT, 0, cx.stream>>>(a.m, a.K, ks, a.nc, a.nout, a.X, a.ldx, a.C, a.csk, a.csj, a.Out,
+                                            a.ldo, 0, a.Yin, a.ldyin, a.alpha, a.beta, a.nrm_part);
+    } else {
+        // partial per split: m x (nt*BN), ld = m
+        kern<<<grid, G::NT, 0, cx.stream>>>(a.m, a.K, ks, a.nc, nt * BN, a.X, a.ldx, a.C, a.csk, a.csj, a.part,
+                                            a.m, a.m * (int64_t)nt * BN, nullptr, 0, T(1), T(0), a.nrm_part);
+    }
+    cx.launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (a.nrm_part) {
+        e = launch_sum_doubles(cx, a.nrm_part, (int)(mt * splits), a.nrm_out);
+        if (e != cudaSuccess) return e;
+    }
+    if (splits == 1) return cudaSuccess;
+    return launch_reduce_split<T, T>(cx, a.m, a.nout, splits, a.part, a.m, a.m * (int64_t)nt * BN, a.Out, a.ldo,
+                                     nullptr, 0, nullptr);
+}
+
+template <typename T>
+cudaError_t gemm_nn(Ctx& cx, const NNArgs<T>& a) {
+    const bool rowc = a.c_rowmajor;
+    const int bp = std::max(a.nc, a.nout);
+#define RQB_NN(BM_, BN_) return rowc ? nn_launch<T, BM_, BN_, true>(cx, a) : nn_launch<T, BM_, BN_, false>(cx, a)
+    if constexpr (sizeof(T) == 4) {
+        if (bp <= 32) { RQB_NN(128, 32); }
+        if (bp <= 64) { RQB_NN(128, 64); }
+        if (bp <= 128) { RQB_NN(128, 128); }
+        RQB_NN(64, 256);
+    } else {
+        if (bp <= 32) { RQB_NN(64, 32); }
+        if (bp <= 64) { RQB_NN(64, 64); }
+        RQB_NN(64, 128);
+    }
+#undef RQB_NN
+}
+
+// TN ----------------------------------------------------------------------
+template <typename T, typename Acc, int BP, int BQ, int BK, int TP, int TQ, int PROMOTE>
+static cudaError_t tn_launch(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, int64_t ldx, const T* Y,
+                             int64_t ldy, Acc* part, size_t part_cap_elems, int max_splits, int* splits_out) {
+    auto kern = k_gemm_tn<T, Acc, BP, BQ, BK, TP, TQ, PROMOTE>;
+    constexpr int NT = (BP / TP) * (BQ / TQ);
+    const int pt = (pn + BP - 1) / BP;
+    const int64_t qt = (qn + BQ - 1) / BQ;
+    const int slots = cx.num_sms * occupancy(kern, NT, 0);
+    const int64_t per = (int64_t)pn * qn;
+    if ((size_t)per > part_cap_elems) return cudaErrorInvalidValue;
+    int maxs = (int)std::min<int64_t>(max_splits, (int64_t)(part_cap_elems / (size_t)std::max<int64_t>(per, 1)));
+    maxs = std::max(1, maxs);
+    int splits = choose_splits((int64_t)pt * qt, m, 512, maxs, slots);
+    int64_t rs = (m + splits - 1) / splits;
+    rs = ((rs + BK - 1) / BK) * BK;
+    splits = (int)std::max<int64_t>(1, (m + rs - 1) / rs);
+    dim3 grid((unsigned)pt, (unsigned)qt, (unsigned)splits);
+    kern<<<grid, NT, 0, cx.stream>>>(m, pn, qn, rs, X, ldx, Y, ldy, part, pn, per);
+    cx.launches++;
+    *splits_out = splits;
+    return cudaGetLastError();
+}
+
+// Out (pn x qn, type TO, ld ldo) = X^T Y; optional ||Out||^2 into *sq_out.
+template <typename T>
+cudaError_t gemm_tn(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, int64_t ldx, const T* Y, int64_t ldy,
+                    T* Out, int64_t ldo, T* part, size_t part_cap_elems, double* sq_part, int sq_cap,
+                    double* sq_out) {
+    int splits = 1;
+    cudaError_t e;
+    if constexpr (sizeof(T) == 4) {
+        if (pn <= 32) e = tn_launch<T, T, 32, 128, 16, 8, 8, 0>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 64, &splits);
+        else if (pn <= 64) e = tn_launch<T, T, 64, 128, 16, 8, 8, 0>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 64, &splits);
+        else e = tn_launch<T, T, 128, 128, 16, 8, 8, 0>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 64, &splits);
+    } else {
+        if (pn <= 32) e = tn_launch<T, T, 32, 64, 8, 4, 4, 0>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 64, &splits);
+        else e = tn_launch<T, T, 64, 64, 8, 4, 4, 0>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 64, &splits);
+    }
+    if (e != cudaSuccess) return e;
+    return launch_reduce_split<T, T>(cx, pn, qn, splits, part, pn, (int64_t)pn * qn, Out, ldo, sq_part, sq_cap,
+                                     sq_out);
+}
+
+// Out (pn x qn, FP64, ld ldo) = X^T Y with FP64 accumulation across chunks.
+template <typename T>
+cudaError_t gemm_tn_f64acc(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, int64_t ldx, const T* Y,
+                           int64_t ldy, double* Out, int64_t ldo, double* part, size_t part_cap_elems) {
+    int splits = 1;
+    cudaError_t e;
+    if constexpr (sizeof(T) == 4) {
+        e = tn_launch<T, double, 64, 64, 16, 4, 4, 8>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 128, &splits);
+    } else {
+        e = tn_launch<T, double, 64, 64, 8, 4, 4, 0>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 128, &splits);
+    }
+    if (e != cudaSuccess) return e;
+    return launch_reduce_split<double, double>(cx, pn, qn, splits, part, pn, (int64_t)pn * qn, Out, ldo, nullptr,
+                                               0, nullptr);
+}
+
+// Cholesky + inverse -------------------------------------------------------
+template <typename T>
+cudaError_t chol_inv(Ctx& cx, const double* G, int bp, int p, double* R, T* Rinv) {
+    const size_t smem = sizeof(double) * (size_t)bp * bp;
+    const int use_smem = (smem <= 200 * 1024) ? 1 : 0;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_cholesky<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_tri_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    // relative pivot below which a panel column counts as dependent: FP64 data
+    // resolves pivots to ~1e-32, FP32 data (FP64 Gram) only to ~1e-15
+    const double tol = (sizeof(T) == 8) ? 1e-15 : 1e-12;
+    k_cholesky<512><<<1, 512, use_smem ? smem : 0, cx.stream>>>(G, bp, bp, p, R, use_smem, tol, cx.st);
+    cx.launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // stage columns 0..c of R for c < smem_cols: (c + 1) * bp + bp doubles <= 200 KB
+    const int smem_cols = (int)std::min<int64_t>(bp, (200 * 1024 / 8) / bp - 1);
+    const size_t smem2 = sizeof(double) * (size_t)(bp + (int64_t)bp * std::max(smem_cols, 1));
+    k_tri_inverse<T><<<bp, 128, smem2, cx.stream>>>(R, bp, Rinv, smem_cols);
+    cx.launches++;
+    return cudaGetLastError();
+}
+
+// Downdate + sketch ---------------------------------------------------------
+template <typename T, int BM, int BN>
+static cudaError_t dd_launch(Ctx& cx, int64_t m, int64_t n, int p, const T* Wsrc, int64_t ldws, const T* Qi,
+                             int64_t ldq, const T* Bi, int64_t ldb, const T* Om, T* Wdst, int64_t ldwd, T* Y,
+                             int64_t ldy, T* part, size_t part_cap_elems, double* nrm_part, int nrm_cap,
+                             double* nrm_out) {
+    using C = DDCfg<T, BM, BN>;
+    auto kern = k_downdate_sketch<T, BM, BN>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        attr = true;
+    }
+    const int64_t mt = (m + BM - 1) / BM;
+    const int slots = cx.num_sms * occupancy(kern, C::NT, C::SMEM);
+    const int64_t per = m * (int64_t)BN;
+    if ((size_t)per > part_cap_elems || mt > nrm_cap) return cudaErrorInvalidValue;
+    int maxs = (int)std::min<int64_t>(64, (int64_t)(part_cap_elems / (size_t)per));
+    maxs = std::min<int64_t>(maxs, nrm_cap / std::max<int64_t>(mt, 1));
+    maxs = std::max(1, maxs);
+    int splits = choose_splits(mt, n, 4 * C::BC, maxs, slots);
+    int64_t cs = (n + splits - 1) / splits;
+    cs = ((cs + C::BC - 1) / C::BC) * C::BC;
+    splits = (int)std::max<int64_t>(1, (n + cs - 1) / cs);
+    dim3 grid((unsigned)mt, 1, (unsigned)splits);
+    kern<<<grid, C::NT, C::SMEM, cx.stream>>>(m, n, p, cs, Wsrc, ldws, Qi, ldq, Bi, ldb, Om, Wdst, ldwd, part, m,
+                                              per, nrm_part);
+    cx.launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_sum_doubles(cx, nrm_part, (int)(mt * splits), nrm_out);
+    if (e != cudaSuccess) return e;
+    return launch_reduce_split<T, T>(cx, m, BN, splits, part, m, per, Y, ldy, nullptr, 0, nullptr);
+}
+
+template <typename T>
+cudaError_t downdate_sketch(Ctx& cx, int64_t m, int64_t n, int p, int bp, const T* Wsrc, int64_t ldws,
+                            const T* Qi, int64_t ldq, const T* Bi, int64_t ldb, const T* Om, T* Wdst,
+                            int64_t ldwd, T* Y, int64_t ldy, T* part, size_t part_cap_elems, double* nrm_part,
+                            int nrm_cap, double* nrm_out) {
+    if constexpr (sizeof(T) == 4) {
+        if (bp == 32) return dd_launch<T, 128, 32>(cx, m, n, p, Wsrc, ldws, Qi, ldq, Bi, ldb, Om, Wdst, ldwd, Y, ldy, part, part_cap_elems, nrm_part, nrm_cap, nrm_out);
+        if (bp == 64) return dd_launch<T, 128, 64>(cx, m, n, p, Wsrc, ldws, Qi, ldq, Bi, ldb, Om, Wdst, ldwd, Y, ldy, part, part_cap_elems, nrm_part, nrm_cap, nrm_out);
+        if (bp == 128) return dd_launch<T, 128, 128>(cx, m, n, p, Wsrc, ldws, Qi, ldq, Bi, ldb, Om, Wdst, ldwd, Y, ldy, part, part_cap_elems, nrm_part, nrm_cap, nrm_out);
+        if (bp == 256) return dd_launch<T, 64, 256>(cx, m, n, p, Wsrc, ldws, Qi, ldq, Bi, ldb, Om, Wdst, ldwd, Y, ldy, part, part_cap_elems, nrm_part, nrm_cap, nrm_out);
+    } else {
+        if (bp == 32) return dd_launch<T, 64, 32>(cx, m, n, p, Wsrc, ldws, Qi, ldq, Bi, ldb, Om, Wdst, ldwd, Y, ldy, part, part_cap_elems, nrm_part, nrm_cap, nrm_out);
+        if (bp == 64) return dd_launch<T, 64, 64>(cx, m, n, p, Wsrc, ldws, Qi, ldq, Bi, ldb, Om, Wdst, ldwd, Y, ldy, part, part_cap_elems, nrm_part, nrm_cap, nrm_out);
+        if (bp == 128) return dd_launch<T, 64, 128>(cx, m, n, p, Wsrc, ldws, Qi, ldq, Bi, ldb, Om, Wdst, ldwd, Y, ldy, part, part_cap_elems, nrm_part, nrm_cap, nrm_out);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Explicit instantiations ---------------------------------------------------
+#define RQB_INST(T)                                                                                              \
+    template cudaError_t launch_omega<T>(Ctx&, int64_t, int64_t, int, int, uint64_t, T*, int64_t, int64_t);       \
+    template cudaError_t launch_sumsq<T>(Ctx&, int64_t, int64_t, const T*, int64_t, double*, int, double*);       \
+    template cudaError_t gemm_nn<T>(Ctx&, const NNArgs<T>&);                                                      \
+    template cudaError_t gemm_tn<T>(Ctx&, int64_t, int, int64_t, const T*, int64_t, const T*, int64_t, T*,        \
+                                    int64_t, T*, size_t, double*, int, double*);                                 \
+    template cudaError_t gemm_tn_f64acc<T>(Ctx&, int64_t, int, int64_t, const T*, int64_t, const T*, int64_t,    \
+                                           double*, int64_t, double*, size_t);                                    \
+    template cudaError_t chol_inv<T>(Ctx&, const double*, int, int, double*, T*);                                 \
+    template cudaError_t downdate_sketch<T>(Ctx&, int64_t, int64_t, int, int, const T*, int64_t, const T*,        \
+                                            int64_t, const T*, int64_t, const T*, T*, int64_t, T*, int64_t, T*,   \
+                                            size_t, double*, int, double*);                                       \
+    template cudaError_t launch_reduce_split<double, T>(Ctx&, int64_t, int64_t, int, const double*, int64_t,      \
+                                                        int64_t, T*, int64_t, double*, int, double*);
+
+RQB_INST(float)
+RQB_INST(double)
+#undef RQB_INST
+
+}  // namespace rqb

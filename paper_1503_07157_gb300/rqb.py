@@ -1,0 +1,278 @@
+"""Python binding of librqb.so (include/rqb.h): argument marshalling only.
+
+Every numerical step runs in the CUDA library; this module converts torch
+tensors to pointers/leading dimensions, calls the C ABI entry point of the
+same name, and wraps returned device buffers as torch tensor views (through
+__cuda_array_interface__, no copy).  There is no CPU fallback: when the
+library is missing or cannot be loaded, every call raises.
+
+Matrices are column-major: a torch tensor M of shape (rows, cols) is passed
+with leading dimension M.stride(1) and must have M.stride(0) == 1 (use
+`colmajor(t)` to get such a tensor).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librqb.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "rqb.h")
+
+RQB_OK = 0
+RQB_ERR_INVALID = 1
+RQB_ERR_NONFINITE = 2
+RQB_ERR_BREAKDOWN = 3
+RQB_ERR_OOM = 4
+RQB_ERR_TIMEOUT = 5
+RQB_ERR_CUDA = 6
+RQB_NOT_CONVERGED = 7
+RQB_ERR_UNSUPPORTED = 8
+
+RQB_F64, RQB_F32, RQB_BF16 = 0, 1, 2
+RQB_PREC_NATIVE, RQB_PREC_TF32X3, RQB_PREC_BF16 = 0, 1, 2
+RQB_MAX_TRACKED_BLOCKS = 512
+RQB_FLAG_PHASE_TIMING = 1
+RQB_NUM_PHASES = 8
+PHASES = ("sketch", "orth", "project", "downdate", "control")
+
+
+class RqbError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+class rqb_config(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("prec", ctypes.c_int32), ("max_rank", ctypes.c_int64),
+                ("fixed_rank", ctypes.c_int32), ("power", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class rqb_stats(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int64), ("blocks", ctypes.c_int64), ("status", ctypes.c_int32),
+                ("direct_tests", ctypes.c_int32), ("normA2", ctypes.c_double), ("eps", ctypes.c_double),
+                ("E", ctypes.c_double * RQB_MAX_TRACKED_BLOCKS), ("D", ctypes.c_double * RQB_MAX_TRACKED_BLOCKS),
+                ("kernel_launches", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("phase_ms", ctypes.c_double * RQB_NUM_PHASES), ("phase_calls", ctypes.c_int32 * RQB_NUM_PHASES)]
+
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load librqb.so (built by paper_1503_07157_gb300.build); raise if absent."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1503_07157_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i64, u64, dbl, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int
+        PP, Pi64, Pd = ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)
+        sig = {
+            "rqb_create": [P, P],
+            "rqb_destroy": [P],
+            "rqb_factor": [P, P, i64, i64, i64, dbl, i64, u64, PP, Pi64, PP, Pi64, Pi64],
+            "rqb_factor_host": [P, P, i64, i64, i64, dbl, i64, u64, P, i64, P, i64, Pi64],
+            "rqb_get_stats": [P, P],
+            "rqb_omega": [P, i64, i64, i64, u64, P, i64],
+            "rqb_sketch": [P, P, i64, i64, i64, i64, i64, u64, P, i64, Pd],
+            "rqb_orth": [P, P, i64, i64, i64, P, i64, i64, P, i64],
+            "rqb_project": [P, P, i64, i64, i64, P, i64, i64, P, i64, Pd],
+            "rqb_downdate_sketch": [P, P, i64, P, i64, P, i64, i64, i64, i64, P, i64, i64, i64, u64, P, i64, Pd],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = i32
+        L.rqb_status_string.argtypes = [i32]
+        L.rqb_status_string.restype = ctypes.c_char_p
+        _LIB = L
+    return _LIB
+
+
+def status_string(status: int) -> str:
+    return lib().rqb_status_string(int(status)).decode()
+
+
+def declared_symbols(header: str = HEADER) -> list[str]:
+    """Names of the functions declared in include/rqb.h."""
+    text = open(header).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(rqb_\w+)\s*\(", text, flags=re.M)))
+
+
+def _check(rc: int, where: str, ok=(RQB_OK,)) -> int:
+    if rc not in ok:
+        raise RqbError(rc, where)
+    return rc
+
+
+def colmajor(t: torch.Tensor) -> torch.Tensor:
+    """Same values, column-major storage (stride(0) == 1)."""
+    if t.dim() != 2:
+        raise ValueError("expected a matrix")
+    if t.stride(0) == 1 and t.stride(1) >= max(1, t.shape[0]):
+        return t
+    return t.t().contiguous().t()
+
+
+def _ld(t: torch.Tensor) -> int:
+    if t.stride(0) != 1:
+        raise ValueError("matrix must be column-major (stride(0) == 1); use colmajor()")
+    return max(int(t.stride(1)), int(t.shape[0]), 1)
+
+
+def _dtype_code(dtype: torch.dtype) -> int:
+    return {torch.float64: RQB_F64, torch.float32: RQB_F32, torch.bfloat16: RQB_BF16}[dtype]
+
+
+class _CudaView:
+    def __init__(self, ptr, shape, strides, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "strides": tuple(strides), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3}
+
+
+def _view(ptr: int, rows: int, cols: int, ld: int, dtype: torch.dtype, device) -> torch.Tensor:
+    if rows == 0 or cols == 0 or not ptr:
+        return torch.empty((rows, cols), dtype=dtype, device=device)
+    es = torch.empty((), dtype=dtype).element_size()
+    ts = {torch.float64: "<f8", torch.float32: "<f4"}[dtype]
+    return torch.as_tensor(_CudaView(ptr, (rows, cols), (es, es * ld), ts), device=device)
+
+
+@dataclass
+class Stats:
+    k: int
+    blocks: int
+    status: int
+    direct_tests: int
+    normA2: float
+    eps: float
+    E: list
+    D: list
+    kernel_launches: int
+    phase_ms: list
+    phase_calls: list
+
+
+class Handle:
+    """Owns an rqb_handle on the current CUDA device and stream."""
+
+    def __init__(self, dtype: torch.dtype = torch.float32, prec: int = RQB_PREC_NATIVE, max_rank: int = 0,
+                 fixed_rank: bool = False, power: int = 0, stream: torch.cuda.Stream | None = None,
+                 flags: int = 0):
+        self.dtype = dtype
+        self.out_dtype = torch.float64 if dtype == torch.float64 else torch.float32
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        cfg = rqb_config(_dtype_code(dtype), prec, max_rank, int(fixed_rank), power,
+                         ctypes.c_void_p(s.cuda_stream), flags, 0)
+        h = ctypes.c_void_p()
+        _check(lib().rqb_create(ctypes.byref(h), ctypes.byref(cfg)), "rqb_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().rqb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- randQB_b ----------------------------------------------------------
+    def rqb_factor(self, A: torch.Tensor, eps: float, b: int, seed: int = 0, check: bool = True):
+        """Returns (Q view m x k, B view k x n, k, status); views are valid until the next call."""
+        m, n = A.shape
+        Qp, Bp = ctypes.c_void_p(), ctypes.c_void_p()
+        ldq, ldb, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        rc = lib().rqb_factor(self._h, ctypes.c_void_p(A.data_ptr()), m, n, _ld(A), float(eps), b, seed,
+                              ctypes.byref(Qp), ctypes.byref(ldq), ctypes.byref(Bp), ctypes.byref(ldb),
+                              ctypes.byref(k))
+        if check:
+            _check(rc, "rqb_factor", ok=(RQB_OK, RQB_NOT_CONVERGED))
+        kk = int(k.value)
+        Q = _view(Qp.value or 0, m, kk, int(ldq.value), self.out_dtype, self.device)
+        B = _view(Bp.value or 0, kk, n, int(ldb.value), self.out_dtype, self.device)
+        return Q, B, kk, rc
+
+    def rqb_factor_host(self, A_host: torch.Tensor, eps: float, b: int, seed: int, Q_host: torch.Tensor,
+                        B_host: torch.Tensor):
+        m, n = A_host.shape
+        k = ctypes.c_int64()
+        rc = lib().rqb_factor_host(self._h, ctypes.c_void_p(A_host.data_ptr()), m, n, _ld(A_host), float(eps), b,
+                                   seed, ctypes.c_void_p(Q_host.data_ptr()), _ld(Q_host),
+                                   ctypes.c_void_p(B_host.data_ptr()), _ld(B_host), ctypes.byref(k))
+        _check(rc, "rqb_factor_host", ok=(RQB_OK, RQB_NOT_CONVERGED))
+        return int(k.value), rc
+
+    def rqb_get_stats(self) -> Stats:
+        st = rqb_stats()
+        _check(lib().rqb_get_stats(self._h, ctypes.byref(st)), "rqb_get_stats")
+        nb = min(int(st.blocks), RQB_MAX_TRACKED_BLOCKS)
+        return Stats(int(st.k), int(st.blocks), int(st.status), int(st.direct_tests), float(st.normA2),
+                     float(st.eps), list(st.E[:nb]), list(st.D[:nb]), int(st.kernel_launches),
+                     list(st.phase_ms), list(st.phase_calls))
+
+    # -- steps ---------------------------------------------------------------
+    def rqb_omega(self, n: int, col0: int, ncols: int, seed: int) -> torch.Tensor:
+        out = colmajor(torch.empty(ncols, n, dtype=self.out_dtype, device=self.device).t())
+        _check(lib().rqb_omega(self._h, n, col0, ncols, seed, ctypes.c_void_p(out.data_ptr()), _ld(out)),
+               "rqb_omega")
+        return out
+
+    def rqb_sketch(self, A: torch.Tensor, col0: int, ncols: int, seed: int):
+        m, n = A.shape
+        Y = colmajor(torch.empty(ncols, m, dtype=self.out_dtype, device=self.device).t())
+        nrm = ctypes.c_double()
+        _check(lib().rqb_sketch(self._h, ctypes.c_void_p(A.data_ptr()), m, n, _ld(A), col0, ncols, seed,
+                                ctypes.c_void_p(Y.data_ptr()), _ld(Y), ctypes.byref(nrm)), "rqb_sketch")
+        return Y, float(nrm.value)
+
+    def rqb_orth(self, Y: torch.Tensor, Qbar: torch.Tensor | None):
+        m, p = Y.shape
+        Qi = colmajor(torch.empty(p, m, dtype=self.out_dtype, device=self.device).t())
+        if Qbar is None or Qbar.shape[1] == 0:
+            qp, kprev, ldqb = ctypes.c_void_p(0), 0, m
+        else:
+            qp, kprev, ldqb = ctypes.c_void_p(Qbar.data_ptr()), Qbar.shape[1], _ld(Qbar)
+        rc = lib().rqb_orth(self._h, ctypes.c_void_p(Y.data_ptr()), m, p, _ld(Y), qp, kprev, ldqb,
+                            ctypes.c_void_p(Qi.data_ptr()), _ld(Qi))
+        _check(rc, "rqb_orth")
+        return Qi
+
+    def rqb_project(self, Qi: torch.Tensor, A: torch.Tensor):
+        m, p = Qi.shape
+        n = A.shape[1]
+        Bi = colmajor(torch.empty(n, p, dtype=self.out_dtype, device=self.device).t())
+        nrm = ctypes.c_double()
+        _check(lib().rqb_project(self._h, ctypes.c_void_p(Qi.data_ptr()), m, p, _ld(Qi),
+                                 ctypes.c_void_p(A.data_ptr()), n, _ld(A), ctypes.c_void_p(Bi.data_ptr()), _ld(Bi),
+                                 ctypes.byref(nrm)), "rqb_project")
+        return Bi, float(nrm.value)
+
+    def rqb_downdate_sketch(self, A: torch.Tensor, Qi: torch.Tensor, Bi: torch.Tensor, W: torch.Tensor, col0: int,
+                            ncols: int, seed: int):
+        m, n = A.shape
+        p = Qi.shape[1]
+        Y = colmajor(torch.empty(ncols, m, dtype=self.out_dtype, device=self.device).t())
+        nrm = ctypes.c_double()
+        _check(lib().rqb_downdate_sketch(self._h, ctypes.c_void_p(A.data_ptr()), _ld(A),
+                                         ctypes.c_void_p(Qi.data_ptr()), _ld(Qi), ctypes.c_void_p(Bi.data_ptr()),
+                                         _ld(Bi), m, n, p, ctypes.c_void_p(W.data_ptr()), _ld(W), col0, ncols, seed,
+                                         ctypes.c_void_p(Y.data_ptr()), _ld(Y), ctypes.byref(nrm)),
+               "rqb_downdate_sketch")
+        return Y, float(nrm.value)

@@ -17,3 +17,16 @@ def pytest_configure(config):
 def orc():
     import oracle
     return oracle
+
+
+@pytest.fixture(scope="session")
+def rqb_lib():
+    """The CUDA library and its binding; builds librqb.so if needed."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1503_07157_gb300 import build
+    build.build()
+    from paper_1503_07157_gb300 import rqb
+    rqb.lib()
+    return rqb

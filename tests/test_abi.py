@@ -1,0 +1,54 @@
+"""The C-ABI library loads and exports every entry point include/rqb.h declares
+(no GPU needed: only symbol lookup, no compute call)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1503_07157_gb300 import build
+from paper_1503_07157_gb300 import rqb
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return rqb.lib()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = rqb.declared_symbols()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), f"librqb.so does not export {name}"
+
+
+def test_header_status_codes_match_binding():
+    text = open(rqb.HEADER).read()
+    codes = dict((k, int(v)) for k, v in re.findall(r"(RQB_[A-Z_]+)\s*=\s*(\d+)", text))
+    for k, v in codes.items():
+        if hasattr(rqb, k):
+            assert getattr(rqb, k) == v, k
+
+
+def test_status_strings(lib):
+    assert rqb.status_string(0) == "ok"
+    assert "invalid" in rqb.status_string(rqb.RQB_ERR_INVALID)
+    assert rqb.status_string(999) == "unknown status"
+
+
+def test_struct_layout_matches_header():
+    # rqb_config: 2 x int32, int64, 2 x int32, pointer, 2 x int32
+    assert ctypes.sizeof(rqb.rqb_config) == 40
+    assert ctypes.sizeof(rqb.rqb_stats) == (8 * 2 + 4 * 2 + 8 * 2 + 8 * 2 * rqb.RQB_MAX_TRACKED_BLOCKS + 8
+                                            + 8 * rqb.RQB_NUM_PHASES + 4 * rqb.RQB_NUM_PHASES)
+
+
+def test_null_handle_rejected_without_gpu(lib):
+    assert lib.rqb_destroy(None) == rqb.RQB_ERR_INVALID
+    assert lib.rqb_get_stats(None, None) == rqb.RQB_ERR_INVALID
+    assert lib.rqb_create(None, None) == rqb.RQB_ERR_INVALID
+
+
+def test_library_is_in_tree():
+    assert os.path.dirname(rqb.LIB_PATH) == os.path.dirname(os.path.abspath(rqb.__file__))

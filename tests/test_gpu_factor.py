@@ -1,0 +1,190 @@
+"""Parity of rqb_factor (Fig. randQB_b end to end) against the oracle.
+
+Bars (the same seeded A and the same Omega on both sides):
+  rank k              exact, unless the oracle's stopping quantity lies within
+                      the GPU's decision band of eps^2 (then one block away is valid)
+  residual r = ||A - QB||_F, both sides evaluated in FP64 from their own Q, B:
+                      FP64 |r_gpu - r_orc| <= 1e-10 r_orc
+                      FP32 |r_gpu - r_orc| <= 1e-5 ||A||_F
+  ||Q^T Q - I||_max   FP64 <= 1e-12, FP32 <= 1e-5
+  Q, B elementwise    FP64 (diag(R) > 0 makes Q unique): 1e-9, 1e-9 ||A||_F
+Edge cases: ragged sizes (b not dividing anything, m and n off the tiles),
+wide matrices, tiny matrices, padded leading dimension, rank caps
+(RQB_NOT_CONVERGED), fixed-rank mode, eps = 0, invalid arguments,
+rank-deficient panels (RQB_ERR_BREAKDOWN), non-finite input.
+"""
+import numpy as np
+import pytest
+import torch
+
+import inputs
+from parity_util import check_rank, orth_err, resid, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def _factor(rqb, A, eps, b, dtype, seed=0, lda=None, **cfg):
+    with rqb.Handle(dtype, **cfg) as h:
+        Q, B, k, rc = h.rqb_factor(to_dev(A, dtype, lda=lda), eps, b, seed)
+        st = h.rqb_get_stats()
+        return to_np(Q), to_np(B), k, rc, st
+
+
+def test_fp64_config(orc, rqb_lib):
+    """2000 x 1000, s_j = 10^(-8(j-1)/999), b = 50, eps = 1e-4 ||A||_F, Omega seed 0."""
+    A, meta = inputs.config_fp64()
+    eps, b = meta["eps"], meta["b"]
+    ro = orc.randqb_b(A, eps, b, seed=0)
+    Q, B, k, rc, st = _factor(rqb_lib, A, eps, b, torch.float64)
+    assert rc == rqb_lib.RQB_OK
+    assert k == ro.k == 600
+    r_g, r_o = resid(A, Q, B), resid(A, ro.Q, ro.B)
+    assert abs(r_g - r_o) <= 1e-10 * r_o
+    assert r_g <= eps
+    assert orth_err(Q) <= 1e-12
+    assert np.abs(Q - ro.Q).max() <= 1e-9
+    assert np.abs(B - ro.B).max() <= 1e-9 * np.sqrt(ro.normA2)
+    assert st.blocks == ro.blocks
+    assert abs(st.normA2 - ro.normA2) <= 1e-13 * ro.normA2
+    np.testing.assert_allclose(st.E, ro.E, rtol=0, atol=1e-13 * ro.normA2)
+
+
+@pytest.mark.parametrize("m,n,b,eps_rel", [(4000, 3200, 128, 1e-2), (4000, 3200, 128, 2e-3), (1037, 777, 37, 3e-3)])
+def test_fp32_poly_decay(orc, rqb_lib, m, n, b, eps_rel):
+    """Polynomial decay s_j = j^-1.5 (the FP32 workload's spectrum) at oracle-size."""
+    s = inputs.spectrum_poly(min(m, n))
+    A = inputs.usv(m, n, s, seed=m + n).astype(np.float32).astype(np.float64)
+    nA = np.linalg.norm(A)
+    eps = eps_rel * nA
+    ro = orc.randqb_b(A, eps, b, seed=0, omega_prec=32)
+    Q, B, k, rc, st = _factor(rqb_lib, A, eps, b, torch.float32)
+    assert rc == rqb_lib.RQB_OK
+    check_rank(k, ro, eps, b, rel_band=1e-3)
+    if k == ro.k:
+        assert abs(resid(A, Q, B) - resid(A, ro.Q, ro.B)) <= 1e-5 * nA
+    assert resid(A, Q, B) <= eps * (1 + 1e-4)
+    assert orth_err(Q) <= 1e-5
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("m,n,b", [(1037, 777, 37), (500, 1500, 64), (5, 3, 2), (97, 64, 8), (300, 300, 128)])
+def test_ragged_and_wide(orc, rqb_lib, dtype, m, n, b):
+    r = min(m, n)
+    A = inputs.usv(m, n, 0.93 ** np.arange(r), seed=m * 7 + n)
+    if dtype == torch.float32:
+        A = A.astype(np.float32).astype(np.float64)
+    nA = np.linalg.norm(A)
+    eps = 1e-2 * nA
+    prec = 64 if dtype == torch.float64 else 32
+    ro = orc.randqb_b(A, eps, b, seed=5, omega_prec=prec)
+    Q, B, k, rc, st = _factor(rqb_lib, A, eps, b, dtype, seed=5)
+    assert rc in (rqb_lib.RQB_OK, rqb_lib.RQB_NOT_CONVERGED)
+    check_rank(k, ro, eps, b, rel_band=1e-6 if dtype == torch.float64 else 1e-3)
+    if dtype == torch.float64:
+        assert abs(resid(A, Q, B) - resid(A, ro.Q, ro.B)) <= 1e-10 * max(resid(A, ro.Q, ro.B), 1e-300) + 1e-14 * nA
+        assert orth_err(Q) <= 1e-12
+    else:
+        assert abs(resid(A, Q, B) - resid(A, ro.Q, ro.B)) <= 1e-5 * nA
+        assert orth_err(Q) <= 1e-5
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_padded_leading_dimension(orc, rqb_lib, dtype):
+    A = inputs.usv(301, 257, 0.9 ** np.arange(257), seed=4)
+    if dtype == torch.float32:
+        A = A.astype(np.float32).astype(np.float64)
+    eps = 1e-3 * np.linalg.norm(A)
+    Q1, B1, k1, _, _ = _factor(rqb_lib, A, eps, 16, dtype, lda=333)
+    Q2, B2, k2, _, _ = _factor(rqb_lib, A, eps, 16, dtype)
+    assert k1 == k2
+    assert np.abs(Q1 - Q2).max() <= (1e-12 if dtype == torch.float64 else 1e-5)
+
+
+def test_rank_cap_not_converged(orc, rqb_lib):
+    A = inputs.usv(400, 300, 0.97 ** np.arange(300), seed=8)
+    Q, B, k, rc, st = _factor(rqb_lib, A, 1e-9, 16, torch.float64, max_rank=40)
+    ro = orc.randqb_b(A, 1e-9, 16, seed=0, max_rank=40)
+    assert rc == rqb_lib.RQB_NOT_CONVERGED and ro.status == 1
+    assert k == ro.k == 40 and st.blocks == 3      # 16 + 16 + 8
+    assert np.abs(Q - ro.Q).max() <= 1e-9
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_fixed_rank(orc, rqb_lib, dtype):
+    A = inputs.usv(600, 400, 0.95 ** np.arange(400), seed=9)
+    if dtype == torch.float32:
+        A = A.astype(np.float32).astype(np.float64)
+    Q, B, k, rc, st = _factor(rqb_lib, A, 1e9, 32, dtype, max_rank=100, fixed_rank=True)
+    prec = 64 if dtype == torch.float64 else 32
+    ro = orc.randqb_b(A, 1e9, 32, seed=0, max_rank=100, fixed_rank=True, omega_prec=prec)
+    assert rc == rqb_lib.RQB_OK and k == 100 == ro.k
+    tol = 1e-10 if dtype == torch.float64 else 1e-5
+    assert abs(resid(A, Q, B) - resid(A, ro.Q, ro.B)) <= tol * np.linalg.norm(A)
+
+
+def test_eps_zero_runs_to_full_rank(orc, rqb_lib):
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((120, 90))
+    Q, B, k, rc, st = _factor(rqb_lib, A, 0.0, 32, torch.float64)
+    assert k == 90 and st.blocks == 3
+    assert rc in (rqb_lib.RQB_OK, rqb_lib.RQB_NOT_CONVERGED)
+    assert resid(A, Q, B) <= 1e-12 * np.linalg.norm(A)
+    assert orth_err(Q) <= 1e-12
+
+
+def test_exact_rank_panel_breakdown(rqb_lib):
+    """A panel whose Gram matrix is singular (rank(A) = 7 < b = 10) reports
+    RQB_ERR_BREAKDOWN instead of producing a non-orthonormal Q."""
+    A = inputs.usv(120, 90, np.arange(7, 0, -1).astype(float), seed=41)
+    _, _, k, rc, _ = _factor(rqb_lib, A, 1e-12, 10, torch.float64)
+    assert rc == rqb_lib.RQB_ERR_BREAKDOWN
+
+
+def test_nonfinite_input(rqb_lib):
+    A = np.ones((64, 48))
+    A[3, 5] = np.nan
+    _, _, _, rc, _ = _factor(rqb_lib, A, 1e-3, 8, torch.float64)
+    assert rc == rqb_lib.RQB_ERR_NONFINITE
+
+
+def test_invalid_arguments(rqb_lib):
+    import ctypes
+    L = rqb_lib.lib()
+    with rqb_lib.Handle(torch.float64) as h:
+        A = torch.zeros(10, 8, dtype=torch.float64, device="cuda").t().contiguous().t()
+        Qp, Bp = ctypes.c_void_p(), ctypes.c_void_p()
+        l1, l2, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        args = lambda m, n, lda, eps, b: L.rqb_factor(h._h, ctypes.c_void_p(A.data_ptr()), m, n, lda, eps, b, 0,
+                                                      ctypes.byref(Qp), ctypes.byref(l1), ctypes.byref(Bp),
+                                                      ctypes.byref(l2), ctypes.byref(k))
+        assert args(10, 8, 9, 1.0, 2) == rqb_lib.RQB_ERR_INVALID      # lda < m
+        assert args(0, 8, 10, 1.0, 2) == rqb_lib.RQB_ERR_INVALID      # m = 0
+        assert args(10, 8, 10, -1.0, 2) == rqb_lib.RQB_ERR_INVALID    # eps < 0
+        assert args(10, 8, 10, 1.0, 0) == rqb_lib.RQB_ERR_INVALID     # b = 0
+        assert args(10, 8, 10, 1.0, 129) == rqb_lib.RQB_ERR_INVALID   # b > 128 (FP64)
+        assert args(10, 8, 10, float("nan"), 2) == rqb_lib.RQB_ERR_INVALID
+        assert h.rqb_get_stats().status == rqb_lib.RQB_ERR_INVALID
+
+
+def test_repeatable_bitwise(rqb_lib):
+    """Deterministic reductions: two runs give identical bits."""
+    A = inputs.usv(900, 700, 0.9 ** np.arange(700), seed=12).astype(np.float32).astype(np.float64)
+    eps = 1e-3 * np.linalg.norm(A)
+    Q1, B1, k1, _, _ = _factor(rqb_lib, A, eps, 32, torch.float32)
+    Q2, B2, k2, _, _ = _factor(rqb_lib, A, eps, 32, torch.float32)
+    assert k1 == k2 and np.array_equal(Q1, Q2) and np.array_equal(B1, B2)
+
+
+def test_host_entry_point(orc, rqb_lib):
+    A, meta = inputs.config_fp64()
+    eps, b = meta["eps"], meta["b"]
+    with rqb_lib.Handle(torch.float64) as h:
+        Ah = torch.as_tensor(A).t().contiguous().t().pin_memory()
+        cap = min(A.shape)
+        Qh = torch.zeros(cap, A.shape[0], dtype=torch.float64).t()
+        Bh = torch.zeros(A.shape[1], cap, dtype=torch.float64).t()
+        k, rc = h.rqb_factor_host(Ah, eps, b, 0, Qh, Bh)
+    ro = orc.randqb_b(A, eps, b, seed=0)
+    assert rc == rqb_lib.RQB_OK and k == ro.k
+    Q, B = Qh[:, :k].numpy(), Bh[:k, :].numpy()
+    assert abs(resid(A, Q, B) - resid(A, ro.Q, ro.B)) <= 1e-10 * resid(A, ro.Q, ro.B)

@@ -147,11 +147,25 @@ def _torch():
     return torch
 
 
+def _preload_torch_linalg(torch):
+    """torch loads its CUDA linear-algebra library lazily by soname; under a
+    profiler's injection that lookup can fail, so load it by path first."""
+    import ctypes
+    import os
+    path = os.path.join(os.path.dirname(torch.__file__), "lib", "libtorch_cuda_linalg.so")
+    if os.path.exists(path):
+        try:
+            ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
+        except OSError:
+            pass
+
+
 def usv_torch(m: int, n: int, s: np.ndarray, seed: int, device="cuda", dtype=None):
     """A = U diag(s) V^T built with torch on `device`; QR and GEMM run in FP32
     with TF32 disabled (FP64 when dtype is float64).  Returns an (m, n) tensor
     whose storage is column-major (a transposed view of a contiguous n x m)."""
     torch = _torch()
+    _preload_torch_linalg(torch)
     dtype = dtype or torch.float32
     r = len(s)
     g = torch.Generator(device=device)

@@ -207,7 +207,7 @@ template <typename T>
 int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_t ldy, int64_t m, int p, int bp,
                    const T* Qbar, int64_t kprev, int64_t ldqb, T* Qout, int64_t ldqo) {
     // pass 1: CholeskyQR of Y, Y1 = Y R^{-1}
-    RQB_CK(gemm_tn_f64acc<T>(cx, m, bp, bp, Y, ldy, Y, ldy, ar.G, bp, ar.dpart, ar.dpart_cap));
+    RQB_CK(gemm_tn_f64acc<T>(cx, m, bp, bp, Y, ldy, Y, ldy, ar.G, bp, ar.dpart, ar.dpart_cap, true));
     RQB_CK(chol_inv<T>(cx, ar.G, bp, p, ar.R, ar.Rinv));
     {
         NNArgs<T> a;
@@ -220,7 +220,7 @@ int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_
     // line (3'): Y1 -= Qbar (Qbar^T Y1)
     if (kprev > 0) {
         RQB_CK(gemm_tn_f64acc<T>(cx, m, (int)kprev, bp, Qbar, ldqb, ar.Y1, m, ar.Cd, kprev, ar.dpart,
-                                 ar.dpart_cap));
+                                 ar.dpart_cap, false));
         RQB_CK((launch_reduce_split<double, T>(cx, kprev, bp, 1, ar.Cd, kprev, 0, ar.Cc, kprev, nullptr, 0,
                                                nullptr)));
         NNArgs<T> a;
@@ -229,10 +229,11 @@ int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_
         a.C = ar.Cc; a.csk = 1; a.csj = kprev; a.c_rowmajor = false;
         a.Out = ar.Y1; a.ldo = m;
         a.Yin = ar.Y1; a.ldyin = m; a.alpha = T(-1); a.beta = T(1);
+        a.part = ar.part; a.part_cap = ar.part_cap; a.allow_split = 1;
         RQB_CK(gemm_nn<T>(cx, a));
     }
     // pass 2: CholeskyQR of Y1, Qout = Y1 R^{-1}
-    RQB_CK(gemm_tn_f64acc<T>(cx, m, bp, bp, ar.Y1, m, ar.Y1, m, ar.G, bp, ar.dpart, ar.dpart_cap));
+    RQB_CK(gemm_tn_f64acc<T>(cx, m, bp, bp, ar.Y1, m, ar.Y1, m, ar.G, bp, ar.dpart, ar.dpart_cap, false));
     RQB_CK(chol_inv<T>(cx, ar.G, bp, p, ar.R, ar.Rinv));
     {
         NNArgs<T> a;

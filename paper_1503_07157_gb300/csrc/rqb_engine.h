@@ -49,7 +49,8 @@ cudaError_t launch_sum_doubles(Ctx& cx, const double* part, int count, double* o
 template <typename TP, typename TO>
 cudaError_t launch_reduce_split(Ctx& cx, int64_t rows, int64_t cols, int splits, const TP* part, int64_t ldp,
                                 int64_t zstride, TO* out, int64_t ldo, double* sq_part, int sq_cap,
-                                double* sq_out);
+                                double* sq_out, double alpha = 1.0, double beta = 0.0, const TO* Yin = nullptr,
+                                int64_t ldyin = 0);
 template <typename T>
 cudaError_t gemm_nn(Ctx& cx, const NNArgs<T>& a);
 template <typename T>
@@ -58,7 +59,8 @@ cudaError_t gemm_tn(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, int64_t 
                     double* sq_out);
 template <typename T>
 cudaError_t gemm_tn_f64acc(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, int64_t ldx, const T* Y,
-                           int64_t ldy, double* Out, int64_t ldo, double* part, size_t part_cap_elems);
+                           int64_t ldy, double* Out, int64_t ldo, double* part, size_t part_cap_elems,
+                           bool exact);
 template <typename T>
 cudaError_t chol_inv(Ctx& cx, const double* G, int bp, int p, double* R, T* Rinv);
 template <typename T>

@@ -266,7 +266,22 @@ k_gemm_nn(int64_t m, int64_t K, int64_t ksplit, int nc, int nout,
 // read as zero; outputs with p < pn, q < qn are written, type Acc.
 // With PROMOTE > 0 (Acc = double, T = float) the FP32 tile accumulators are
 // added into FP64 accumulators every PROMOTE row-chunks of BK rows.
-template <typename T, typename Acc, int BP, int BQ, int BK, int TP, int TQ, int PROMOTE>
+// With COMP (T = float) every product is formed exactly as a pair
+// (a*b, fma(a, b, -a*b)) and summed with TwoSum into an unevaluated FP32 pair
+// (Knuth's error-free transformations), so the FP64 result carries about
+// 2^-46 relative error instead of 2^-24: the accuracy the Gram matrix of an
+// ill-conditioned panel needs before its Cholesky factorisation.
+__device__ __forceinline__ void exact_fma_acc(float a, float b, float& hi, float& lo) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bv = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+template <typename T, typename Acc, int BP, int BQ, int BK, int TP, int TQ, int PROMOTE, bool COMP = false>
 __global__ void __launch_bounds__((BP / TP) * (BQ / TQ))
 k_gemm_tn(int64_t m, int pn, int64_t qn, int64_t rsplit,
           const T* __restrict__ X, int64_t ldx,
@@ -289,11 +304,12 @@ k_gemm_tn(int64_t m, int pn, int64_t qn, int64_t rsplit,
     const int64_t rend = (rbeg + rsplit < m) ? rbeg + rsplit : m;
 
     T acc[TP][TQ];
+    T lo[TP][TQ];
     Acc acc2[TP][TQ];
 #pragma unroll
     for (int i = 0; i < TP; ++i)
 #pragma unroll
-        for (int j = 0; j < TQ; ++j) { acc[i][j] = T(0); acc2[i][j] = Acc(0); }
+        for (int j = 0; j < TQ; ++j) { acc[i][j] = T(0); lo[i][j] = T(0); acc2[i][j] = Acc(0); }
 
     T xa[XPER][V], ya[YPER][V];
     // vector v: column cc = v / (BK/V), rows kk..kk+V
@@ -370,17 +386,29 @@ k_gemm_tn(int64_t m, int pn, int64_t qn, int64_t rsplit,
             for (int i = 0; i < HP; ++i) { a[i] = a0[i]; a[HP + i] = a1[i]; }
 #pragma unroll
             for (int j = 0; j < HQ; ++j) { b[j] = b0[j]; b[HQ + j] = b1[j]; }
+            if constexpr (COMP) {
 #pragma unroll
-            for (int i = 0; i < TP; ++i)
+                for (int i = 0; i < TP; ++i)
 #pragma unroll
-                for (int j = 0; j < TQ; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                    for (int j = 0; j < TQ; ++j) exact_fma_acc(a[i], b[j], acc[i][j], lo[i][j]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < TP; ++i)
+#pragma unroll
+                    for (int j = 0; j < TQ; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
         }
         if (PROMOTE > 0 && ++chunk == PROMOTE) {
             chunk = 0;
 #pragma unroll
             for (int i = 0; i < TP; ++i)
 #pragma unroll
-                for (int j = 0; j < TQ; ++j) { acc2[i][j] += (Acc)acc[i][j]; acc[i][j] = T(0); }
+                for (int j = 0; j < TQ; ++j) {
+                    acc2[i][j] += (Acc)acc[i][j];
+                    if (COMP) acc2[i][j] += (Acc)lo[i][j];
+                    acc[i][j] = T(0);
+                    lo[i][j] = T(0);
+                }
         }
         if (more) store(buf ^ 1);
         __syncthreads();
@@ -396,9 +424,12 @@ k_gemm_tn(int64_t m, int pn, int64_t qn, int64_t rsplit,
         for (int j = 0; j < TQ; ++j) {
             const int64_t q = q0 + ((j < HQ) ? (tq * HQ + j) : (BQ / 2 + tq * HQ + (j - HQ)));
             if (q >= qn) continue;
-            out[p + q * ldo] = (PROMOTE > 0) ? (acc2[i][j] + (Acc)acc[i][j]) : (Acc)acc[i][j];
+            Acc v = (PROMOTE > 0) ? (acc2[i][j] + (Acc)acc[i][j]) : (Acc)acc[i][j];
+            if (COMP) v += (Acc)lo[i][j];
+            out[p + q * ldo] = v;
         }
     }
 }
 
 }  // namespace rqb
+

@@ -112,7 +112,8 @@ cudaError_t launch_sumsq(Ctx& cx, int64_t m, int64_t n, const T* X, int64_t ldx,
 template <typename TP, typename TO>
 __global__ void __launch_bounds__(256)
 k_reduce_split(int64_t rows, int64_t cols, int splits, const TP* __restrict__ part, int64_t ldp,
-               int64_t zstride, TO* __restrict__ out, int64_t ldo, double* __restrict__ sq_part) {
+               int64_t zstride, TO* out, int64_t ldo, double* __restrict__ sq_part, double alpha, double beta,
+               const TO* Yin, int64_t ldyin) {
     __shared__ double sh[8];
     double sq = 0.0;
     const int64_t total = rows * cols;
@@ -120,6 +121,8 @@ k_reduce_split(int64_t rows, int64_t cols, int splits, const TP* __restrict__ pa
         const int64_t r = e % rows, c = e / rows;
         double s = 0.0;
         for (int z = 0; z < splits; ++z) s += (double)part[z * zstride + r + c * ldp];
+        if (alpha != 1.0) s *= alpha;
+        if (beta != 0.0) s += beta * (double)Yin[r + c * ldyin];
         const TO v = (TO)s;
         out[r + c * ldo] = v;
         sq += (double)v * (double)v;
@@ -133,11 +136,11 @@ k_reduce_split(int64_t rows, int64_t cols, int splits, const TP* __restrict__ pa
 template <typename TP, typename TO>
 cudaError_t launch_reduce_split(Ctx& cx, int64_t rows, int64_t cols, int splits, const TP* part, int64_t ldp,
                                 int64_t zstride, TO* out, int64_t ldo, double* sq_part, int sq_cap,
-                                double* sq_out) {
+                                double* sq_out, double alpha, double beta, const TO* Yin, int64_t ldyin) {
     int blocks = std::max<int64_t>(1, std::min<int64_t>((rows * cols + 255) / 256, (int64_t)cx.num_sms * 8));
     if (sq_part) blocks = std::min(blocks, sq_cap);
     k_reduce_split<TP, TO><<<blocks, 256, 0, cx.stream>>>(rows, cols, splits, part, ldp, zstride, out, ldo,
-                                                           sq_part);
+                                                           sq_part, alpha, beta, Yin, ldyin);
     cx.launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !sq_part) return e;
@@ -528,31 +531,39 @@ template <> struct NNTile<double> { static constexpr int BK = 8; };
 template <typename T, int BM, int BN, bool ROWC>
 static cudaError_t nn_launch(Ctx& cx, const NNArgs<T>& a) {
     using G = GemmNN<T, BM, BN, NNTile<T>::BK, ROWC>;
-    auto kern = k_gemm_nn<T, BM, BN, NNTile<T>::BK, ROWC>;
+    using KernT = void (*)(int64_t, int64_t, int64_t, int, int, const T*, int64_t, const T*, int64_t, int64_t, T*,
+                           int64_t, int64_t, const T*, int64_t, T, T, double*);
+    KernT kern = k_gemm_nn<T, BM, BN, NNTile<T>::BK, ROWC>;
+    int threads = G::NT;
+    size_t dsmem = 0;
+    int64_t kalign = NNTile<T>::BK;
     const int64_t mt = (a.m + BM - 1) / BM;
     const int nt = (std::max(a.nc, a.nout) + BN - 1) / BN;
-    const int slots = cx.num_sms * occupancy(kern, G::NT, 0);
-    bool allow_split = a.allow_split && a.part && a.alpha == T(1) && a.beta == T(0);
+    const int slots = cx.num_sms * occupancy(kern, threads, dsmem);
+    // FP64 pipes are 64x slower than FP32 ones on this part: spread FP64
+    // products over more CTAs by splitting shorter reductions
+    constexpr int64_t kmin = (sizeof(T) == 8) ? 64 : 256;
+    bool allow_split = a.allow_split && a.part;
     int splits = 1;
     if (allow_split) {
         const int64_t per = a.m * (int64_t)nt * BN;
         int64_t maxs = std::min<int64_t>(32, (int64_t)(a.part_cap / (size_t)std::max<int64_t>(per, 1)));
         if (a.nrm_part) maxs = std::min<int64_t>(maxs, a.nrm_cap / std::max<int64_t>(mt, 1));
-        splits = choose_splits(mt * nt, a.K, 256, (int)std::max<int64_t>(1, maxs), slots);
+        splits = choose_splits(mt * nt, a.K, kmin, (int)std::max<int64_t>(1, maxs), slots);
     }
     int64_t ks = (a.K + splits - 1) / splits;
-    ks = ((ks + NNTile<T>::BK - 1) / NNTile<T>::BK) * NNTile<T>::BK;
-    if (ks < NNTile<T>::BK) ks = NNTile<T>::BK;
+    ks = ((ks + kalign - 1) / kalign) * kalign;
+    if (ks < kalign) ks = kalign;
     splits = (int)std::max<int64_t>(1, (a.K + ks - 1) / ks);
     if (a.nrm_part && mt * splits > a.nrm_cap) return cudaErrorInvalidValue;
     dim3 grid((unsigned)mt, (unsigned)nt, (unsigned)splits);
     if (splits == 1) {
-        kern<<<grid, G::NT, 0, cx.stream>>>(a.m, a.K, ks, a.nc, a.nout, a.X, a.ldx, a.C, a.csk, a.csj, a.Out,
-                                            a.ldo, 0, a.Yin, a.ldyin, a.alpha, a.beta, a.nrm_part);
+        kern<<<grid, threads, dsmem, cx.stream>>>(a.m, a.K, ks, a.nc, a.nout, a.X, a.ldx, a.C, a.csk, a.csj, a.Out,
+                                                  a.ldo, 0, a.Yin, a.ldyin, a.alpha, a.beta, a.nrm_part);
     } else {
         // partial per split: m x (nt*BN), ld = m
-        kern<<<grid, G::NT, 0, cx.stream>>>(a.m, a.K, ks, a.nc, nt * BN, a.X, a.ldx, a.C, a.csk, a.csj, a.part,
-                                            a.m, a.m * (int64_t)nt * BN, nullptr, 0, T(1), T(0), a.nrm_part);
+        kern<<<grid, threads, dsmem, cx.stream>>>(a.m, a.K, ks, a.nc, nt * BN, a.X, a.ldx, a.C, a.csk, a.csj, a.part,
+                                                  a.m, a.m * (int64_t)nt * BN, nullptr, 0, T(1), T(0), a.nrm_part);
     }
     cx.launches++;
     cudaError_t e = cudaGetLastError();
@@ -563,7 +574,7 @@ static cudaError_t nn_launch(Ctx& cx, const NNArgs<T>& a) {
     }
     if (splits == 1) return cudaSuccess;
     return launch_reduce_split<T, T>(cx, a.m, a.nout, splits, a.part, a.m, a.m * (int64_t)nt * BN, a.Out, a.ldo,
-                                     nullptr, 0, nullptr);
+                                     nullptr, 0, nullptr, (double)a.alpha, (double)a.beta, a.Yin, a.ldyin);
 }
 
 template <typename T>
@@ -585,10 +596,11 @@ cudaError_t gemm_nn(Ctx& cx, const NNArgs<T>& a) {
 }
 
 // TN ----------------------------------------------------------------------
-template <typename T, typename Acc, int BP, int BQ, int BK, int TP, int TQ, int PROMOTE>
+template <typename T, typename Acc, int BP, int BQ, int BK, int TP, int TQ, int PROMOTE, bool COMP = false>
 static cudaError_t tn_launch(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, int64_t ldx, const T* Y,
-                             int64_t ldy, Acc* part, size_t part_cap_elems, int max_splits, int* splits_out) {
-    auto kern = k_gemm_tn<T, Acc, BP, BQ, BK, TP, TQ, PROMOTE>;
+                             int64_t ldy, Acc* part, size_t part_cap_elems, int max_splits, int* splits_out,
+                             int64_t kmin = 512) {
+    auto kern = k_gemm_tn<T, Acc, BP, BQ, BK, TP, TQ, PROMOTE, COMP>;
     constexpr int NT = (BP / TP) * (BQ / TQ);
     const int pt = (pn + BP - 1) / BP;
     const int64_t qt = (qn + BQ - 1) / BQ;
@@ -597,7 +609,7 @@ static cudaError_t tn_launch(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X,
     if ((size_t)per > part_cap_elems) return cudaErrorInvalidValue;
     int maxs = (int)std::min<int64_t>(max_splits, (int64_t)(part_cap_elems / (size_t)std::max<int64_t>(per, 1)));
     maxs = std::max(1, maxs);
-    int splits = choose_splits((int64_t)pt * qt, m, 512, maxs, slots);
+    int splits = choose_splits((int64_t)pt * qt, m, kmin, maxs, slots);
     int64_t rs = (m + splits - 1) / splits;
     rs = ((rs + BK - 1) / BK) * BK;
     splits = (int)std::max<int64_t>(1, (m + rs - 1) / rs);
@@ -615,33 +627,40 @@ cudaError_t gemm_tn(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, int64_t 
                     double* sq_out) {
     int splits = 1;
     cudaError_t e;
+    constexpr int64_t kmin = (sizeof(T) == 8) ? 64 : 512;
     if constexpr (sizeof(T) == 4) {
-        if (pn <= 32) e = tn_launch<T, T, 32, 128, 16, 8, 8, 0>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 64, &splits);
-        else if (pn <= 64) e = tn_launch<T, T, 64, 128, 16, 8, 8, 0>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 64, &splits);
-        else e = tn_launch<T, T, 128, 128, 16, 8, 8, 0>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 64, &splits);
+        if (pn <= 32) e = tn_launch<T, T, 32, 128, 16, 8, 8, 0>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 64, &splits, kmin);
+        else if (pn <= 64) e = tn_launch<T, T, 64, 128, 16, 8, 8, 0>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 64, &splits, kmin);
+        else e = tn_launch<T, T, 128, 128, 16, 8, 8, 0>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 64, &splits, kmin);
     } else {
-        if (pn <= 32) e = tn_launch<T, T, 32, 64, 8, 4, 4, 0>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 64, &splits);
-        else e = tn_launch<T, T, 64, 64, 8, 4, 4, 0>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 64, &splits);
+        if (pn <= 32) e = tn_launch<T, T, 32, 64, 8, 4, 4, 0>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 64, &splits, kmin);
+        else e = tn_launch<T, T, 64, 64, 8, 4, 4, 0>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 64, &splits, kmin);
     }
     if (e != cudaSuccess) return e;
     return launch_reduce_split<T, T>(cx, pn, qn, splits, part, pn, (int64_t)pn * qn, Out, ldo, sq_part, sq_cap,
-                                     sq_out);
+                                     sq_out, 1.0, 0.0, nullptr, 0);
 }
 
 // Out (pn x qn, FP64, ld ldo) = X^T Y with FP64 accumulation across chunks.
 template <typename T>
 cudaError_t gemm_tn_f64acc(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, int64_t ldx, const T* Y,
-                           int64_t ldy, double* Out, int64_t ldo, double* part, size_t part_cap_elems) {
+                           int64_t ldy, double* Out, int64_t ldo, double* part, size_t part_cap_elems, bool exact) {
     int splits = 1;
     cudaError_t e;
     if constexpr (sizeof(T) == 4) {
-        e = tn_launch<T, double, 64, 64, 16, 4, 4, 8>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 128, &splits);
+        if (exact)
+            e = tn_launch<T, double, 64, 64, 16, 4, 4, 16, true>(cx, m, pn, qn, X, ldx, Y, ldy, part,
+                                                                 part_cap_elems, 128, &splits, 128);
+        else
+            e = tn_launch<T, double, 64, 64, 16, 4, 4, 8>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 128,
+                                                          &splits, 256);
     } else {
-        e = tn_launch<T, double, 64, 64, 8, 4, 4, 0>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 128, &splits);
+        e = tn_launch<T, double, 64, 64, 8, 4, 4, 0>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 128, &splits,
+                                                     32);
     }
     if (e != cudaSuccess) return e;
     return launch_reduce_split<double, double>(cx, pn, qn, splits, part, pn, (int64_t)pn * qn, Out, ldo, nullptr,
-                                               0, nullptr);
+                                               0, nullptr, 1.0, 0.0, nullptr, 0);
 }
 
 // Cholesky + inverse -------------------------------------------------------
@@ -655,9 +674,10 @@ cudaError_t chol_inv(Ctx& cx, const double* G, int bp, int p, double* R, T* Rinv
         cudaFuncSetAttribute(k_tri_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
-    // relative pivot below which a panel column counts as dependent: FP64 data
-    // resolves pivots to ~1e-32, FP32 data (FP64 Gram) only to ~1e-15
-    const double tol = (sizeof(T) == 8) ? 1e-15 : 1e-12;
+    // relative pivot below which a panel column counts as dependent: rounding
+    // of the panel itself leaves pivots of order u^2 (1e-32 for FP64 data,
+    // 4e-15 for FP32 data); CholeskyQR2 with an FP64 Gram handles anything above
+    const double tol = (sizeof(T) == 8) ? 1e-15 : 1e-14;
     k_cholesky<512><<<1, 512, use_smem ? smem : 0, cx.stream>>>(G, bp, bp, p, R, use_smem, tol, cx.st);
     cx.launches++;
     cudaError_t e = cudaGetLastError();
@@ -702,7 +722,8 @@ static cudaError_t dd_launch(Ctx& cx, int64_t m, int64_t n, int p, const T* Wsrc
     if (e != cudaSuccess) return e;
     e = launch_sum_doubles(cx, nrm_part, (int)(mt * splits), nrm_out);
     if (e != cudaSuccess) return e;
-    return launch_reduce_split<T, T>(cx, m, BN, splits, part, m, per, Y, ldy, nullptr, 0, nullptr);
+    return launch_reduce_split<T, T>(cx, m, BN, splits, part, m, per, Y, ldy, nullptr, 0, nullptr, 1.0, 0.0, nullptr,
+                                     0);
 }
 
 template <typename T>
@@ -731,13 +752,14 @@ cudaError_t downdate_sketch(Ctx& cx, int64_t m, int64_t n, int p, int bp, const 
     template cudaError_t gemm_tn<T>(Ctx&, int64_t, int, int64_t, const T*, int64_t, const T*, int64_t, T*,        \
                                     int64_t, T*, size_t, double*, int, double*);                                 \
     template cudaError_t gemm_tn_f64acc<T>(Ctx&, int64_t, int, int64_t, const T*, int64_t, const T*, int64_t,    \
-                                           double*, int64_t, double*, size_t);                                    \
+                                           double*, int64_t, double*, size_t, bool);                              \
     template cudaError_t chol_inv<T>(Ctx&, const double*, int, int, double*, T*);                                 \
     template cudaError_t downdate_sketch<T>(Ctx&, int64_t, int64_t, int, int, const T*, int64_t, const T*,        \
                                             int64_t, const T*, int64_t, const T*, T*, int64_t, T*, int64_t, T*,   \
                                             size_t, double*, int, double*);                                       \
     template cudaError_t launch_reduce_split<double, T>(Ctx&, int64_t, int64_t, int, const double*, int64_t,      \
-                                                        int64_t, T*, int64_t, double*, int, double*);
+                                                        int64_t, T*, int64_t, double*, int, double*, double,      \
+                                                        double, const T*, int64_t);
 
 RQB_INST(float)
 RQB_INST(double)

@@ -25,7 +25,7 @@ pytestmark = pytest.mark.gpu
 
 def _factor(rqb, A, eps, b, dtype, seed=0, lda=None, **cfg):
     with rqb.Handle(dtype, **cfg) as h:
-        Q, B, k, rc = h.rqb_factor(to_dev(A, dtype, lda=lda), eps, b, seed)
+        Q, B, k, rc = h.rqb_factor(to_dev(A, dtype, lda=lda), eps, b, seed, check=False)
         st = h.rqb_get_stats()
         return to_np(Q), to_np(B), k, rc, st
 

@@ -55,7 +55,9 @@ typedef enum {
     RQB_ERR_CUDA = 6,        /* a CUDA runtime call failed                     */
     RQB_NOT_CONVERGED = 7,   /* k reached max_rank with ||A - QB||_F > eps;
                                 Q, B and k are still valid                      */
-    RQB_ERR_UNSUPPORTED = 8  /* valid request this build cannot serve          */
+    RQB_ERR_UNSUPPORTED = 8, /* valid request this build cannot serve          */
+    RQB_ERR_SCRATCH_LIMIT = 9 /* request exceeds the fixed scratch of
+                                 rqb_sketch_noalloc                              */
 } rqb_status;
 
 typedef enum { RQB_F64 = 0, RQB_F32 = 1, RQB_BF16 = 2 } rqb_dtype;
@@ -192,6 +194,39 @@ int rqb_downdate_sketch(rqb_handle h, const void* A, int64_t lda, const void* Qi
                         const void* Bi, int64_t ldbi, int64_t m, int64_t n, int64_t p,
                         void* W, int64_t ldw, int64_t col0, int64_t ncols, uint64_t seed,
                         void* Y, int64_t ldy, double* normW2);
+
+/* ------------------------------------------------------------------------
+ * Allocation-free sketch.  The paper has no counterpart: this entry point
+ * exists for callers of this library that cannot allocate device memory --
+ * code that runs where the allocator must not be touched (a real-time loop,
+ * a host callback, a process whose memory pool owns the whole device) or
+ * whose allocator is capped by someone else.
+ *
+ * rqb_sketch_noalloc computes the same Y = A Omega(:, col0 : col0 + ncols)
+ * (and optionally ||A||_F^2) as rqb_sketch, without a handle and without
+ * calling cudaMalloc, cudaFree or any allocating library routine.  Its
+ * scratch -- the Omega block, the split-K partial sums and the FP64 norm
+ * partials -- is one static device array of RQB_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading this library keeps until the process exits.
+ *   dtype  RQB_F32 or RQB_F64 (element type of A and Y)
+ *   A, Y   device, column-major; lda >= m, ldy >= m
+ *   ncols  1..256 (FP32) or 1..128 (FP64)
+ *   normA2 host pointer or NULL; when non-NULL the call synchronises stream
+ *   stream cudaStream_t (NULL: legacy default stream)
+ * Errors: RQB_ERR_INVALID (bad argument), RQB_ERR_SCRATCH_LIMIT when the
+ * Omega block (n * ncols rounded up to 32/64/128/256 columns) or the row
+ * tiles (m / 128 > 8192) do not fit the fixed scratch -- nothing is launched
+ * then; RQB_ERR_CUDA on a runtime error.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents: calls that overlap on the GPU (different streams, or
+ * different host threads on one device) race on it and must be serialised by
+ * the caller. */
+#define RQB_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int rqb_sketch_noalloc(int32_t dtype, const void* A, int64_t m, int64_t n, int64_t lda,
+                       int64_t col0, int64_t ncols, uint64_t seed, void* Y, int64_t ldy,
+                       double* normA2, void* stream);
 
 /* Human-readable name of a status code (static string). */
 const char* rqb_status_string(int status);

@@ -405,6 +405,7 @@ const char* rqb_status_string(int status) {
         case RQB_ERR_CUDA: return "CUDA runtime error";
         case RQB_NOT_CONVERGED: return "rank cap reached before the tolerance";
         case RQB_ERR_UNSUPPORTED: return "unsupported configuration";
+        case RQB_ERR_SCRATCH_LIMIT: return "request exceeds the fixed scratch of rqb_sketch_noalloc";
         default: return "unknown status";
     }
 }

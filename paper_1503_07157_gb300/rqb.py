@@ -32,6 +32,7 @@ RQB_ERR_TIMEOUT = 5
 RQB_ERR_CUDA = 6
 RQB_NOT_CONVERGED = 7
 RQB_ERR_UNSUPPORTED = 8
+RQB_ERR_SCRATCH_LIMIT = 9
 
 RQB_F64, RQB_F32, RQB_BF16 = 0, 1, 2
 RQB_PREC_NATIVE, RQB_PREC_TF32X3, RQB_PREC_BF16 = 0, 1, 2
@@ -84,6 +85,7 @@ def lib() -> ctypes.CDLL:
             "rqb_orth": [P, P, i64, i64, i64, P, i64, i64, P, i64],
             "rqb_project": [P, P, i64, i64, i64, P, i64, i64, P, i64, Pd],
             "rqb_downdate_sketch": [P, P, i64, P, i64, P, i64, i64, i64, i64, P, i64, i64, i64, u64, P, i64, Pd],
+            "rqb_sketch_noalloc": [ctypes.c_int32, P, i64, i64, i64, i64, i64, u64, P, i64, Pd, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -276,3 +278,16 @@ class Handle:
                                          ctypes.c_void_p(Y.data_ptr()), _ld(Y), ctypes.byref(nrm)),
                "rqb_downdate_sketch")
         return Y, float(nrm.value)
+
+
+def rqb_sketch_noalloc(A: torch.Tensor, col0: int, ncols: int, seed: int, Y: torch.Tensor,
+                       stream: torch.cuda.Stream | None = None, want_norm: bool = True):
+    """Y (caller-allocated, m x ncols, column-major) = A Omega(:, col0:col0+ncols)
+    without any device allocation inside the library; returns (status, ||A||_F^2 or None)."""
+    m, n = A.shape
+    s = stream if stream is not None else torch.cuda.current_stream()
+    nrm = ctypes.c_double()
+    rc = lib().rqb_sketch_noalloc(_dtype_code(A.dtype), ctypes.c_void_p(A.data_ptr()), m, n, _ld(A), col0, ncols,
+                                  seed, ctypes.c_void_p(Y.data_ptr()), _ld(Y),
+                                  ctypes.byref(nrm) if want_norm else None, ctypes.c_void_p(s.cuda_stream))
+    return rc, (float(nrm.value) if want_norm else None)

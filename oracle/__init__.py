@@ -18,6 +18,9 @@ Functions and the passages they follow:
   randqb         -- Fig. randQB (unblocked)
   svd_values     -- singular values by one-sided Jacobi (for the Eckart-Young
                     bound of eq. minerrors on small inputs)
+  qqta_adjoint   -- gradient through the fixed-rank map A -> Q Q^T A with Omega
+                    held fixed (derived from the projector onto R(A Omega),
+                    Sec. 4.1 / Prop. 4.1(c)); the paper itself has no derivatives
 """
 import ctypes
 from dataclasses import dataclass, field
@@ -48,6 +51,8 @@ def _lib():
         lib.orc_sketch.argtypes = [P, i64, i64, i64, u64, i64, i64, i32, P, i64]
         lib.orc_orth_reproject.argtypes = [P, i64, i64, i64, P, i64, i64, P, i64]
         lib.orc_num_threads.restype = i32
+        lib.orc_qqta_adjoint.argtypes = [P, i64, i64, i64, P, i64, P, i64, i64, u64, i32, P, i64, P, i64]
+        lib.orc_qqta_adjoint.restype = i32
         _LIB = lib
     return _LIB
 
@@ -169,3 +174,16 @@ def svd_values(A):
     s = np.zeros(min(m, n))
     _lib().orc_svd_values(_ptr(A), m, n, m, _ptr(s))
     return s
+
+
+def qqta_adjoint(A, Q, B, G, seed: int = 0, omega_prec: int = 64):
+    """dL/dA for X = Q Q^T A (fixed Omega) given G = dL/dX and the forward's Q, B."""
+    A, Q, B, G = _f64(A), _f64(Q), _f64(B), _f64(G)
+    m, n = A.shape
+    k = Q.shape[1]
+    dA = np.zeros((m, n), order="F")
+    rc = _lib().orc_qqta_adjoint(_ptr(A), m, n, m, _ptr(Q), m, _ptr(B), k, k, seed, omega_prec,
+                                 _ptr(G), m, _ptr(dA), m)
+    if rc != 0:
+        raise ValueError("orc_qqta_adjoint: singular B Omega or bad rank")
+    return dA

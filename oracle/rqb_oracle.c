@@ -411,3 +411,98 @@ int orc_svd_values(const double* A, int64_t m, int64_t n, int64_t lda, double* s
     free(U);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Derivative of the fixed-rank map A -> X = Q Q^T A, Q = orth(A Omega) with
+ * Omega (n x k, the first k global columns) held fixed.  Q Q^T is the
+ * orthogonal projector P onto R(Y), Y = A Omega, whatever the blocking
+ * (Sec. 4.1, Prop. 4.1(c)).  Differentiating P = Y (Y^T Y)^{-1} Y^T gives
+ *   dL/dA = P G + (I - P)(G A^T + A G^T) Y^{+T} Omega^T,
+ * and with Y = Q R, R = Q^T A Omega = B Omega, Y^{+T} = Q R^{-T}, A^T Q = B^T:
+ *   dL/dA = Q (Q^T G) + (I - Q Q^T)(G B^T + A (G^T Q)) R^{-T} Omega^T.
+ * G = dL/dX (m x n); Q (m x k) and B (k x n) are the forward's factors. */
+
+/* X (k x nrhs) = M^{-1} Rhs for a k x k matrix M: Gaussian elimination with
+ * partial pivoting (no structure of M assumed). */
+static int solve_left(const double* M, int64_t k, const double* Rhs, int64_t nrhs, double* X) {
+    double* Lu = (double*)malloc(sizeof(double) * (size_t)k * (size_t)k);
+    memcpy(Lu, M, sizeof(double) * (size_t)k * (size_t)k);
+    memcpy(X, Rhs, sizeof(double) * (size_t)k * (size_t)nrhs);
+    int ok = 1;
+    for (int64_t c = 0; c < k && ok; ++c) {
+        int64_t p = c;
+        for (int64_t r = c + 1; r < k; ++r)
+            if (fabs(Lu[r + c * k]) > fabs(Lu[p + c * k])) p = r;
+        if (Lu[p + c * k] == 0.0) { ok = 0; break; }
+        if (p != c) {
+            for (int64_t j = 0; j < k; ++j) { double t = Lu[c + j * k]; Lu[c + j * k] = Lu[p + j * k]; Lu[p + j * k] = t; }
+            for (int64_t j = 0; j < nrhs; ++j) { double t = X[c + j * k]; X[c + j * k] = X[p + j * k]; X[p + j * k] = t; }
+        }
+        for (int64_t r = c + 1; r < k; ++r) {
+            const double f = Lu[r + c * k] / Lu[c + c * k];
+            for (int64_t j = c; j < k; ++j) Lu[r + j * k] -= f * Lu[c + j * k];
+            for (int64_t j = 0; j < nrhs; ++j) X[r + j * k] -= f * X[c + j * k];
+        }
+    }
+    if (ok) {
+        for (int64_t j = 0; j < nrhs; ++j)
+            for (int64_t r = k - 1; r >= 0; --r) {
+                double s = X[r + j * k];
+                for (int64_t t = r + 1; t < k; ++t) s -= Lu[r + t * k] * X[t + j * k];
+                X[r + j * k] = s / Lu[r + r * k];
+            }
+    }
+    free(Lu);
+    return ok ? 0 : -1;
+}
+
+int orc_qqta_adjoint(const double* A, int64_t m, int64_t n, int64_t lda, const double* Q, int64_t ldq,
+                     const double* B, int64_t ldb, int64_t k, uint64_t seed, int omega_prec,
+                     const double* G, int64_t ldg, double* dA, int64_t ldda) {
+    if (k <= 0 || k > m || k > n) return -1;
+    double* Om = (double*)malloc(sizeof(double) * (size_t)n * (size_t)k);
+    double* R = (double*)malloc(sizeof(double) * (size_t)k * (size_t)k);
+    double* QtG = (double*)malloc(sizeof(double) * (size_t)k * (size_t)n);
+    double* Bt = (double*)malloc(sizeof(double) * (size_t)n * (size_t)k);
+    double* M1 = (double*)malloc(sizeof(double) * (size_t)m * (size_t)k);
+    double* GtQ = (double*)malloc(sizeof(double) * (size_t)n * (size_t)k);
+    double* T1 = (double*)malloc(sizeof(double) * (size_t)m * (size_t)k);
+    double* QtM = (double*)malloc(sizeof(double) * (size_t)k * (size_t)k);
+    double* M1t = (double*)malloc(sizeof(double) * (size_t)k * (size_t)m);
+    double* Nt = (double*)malloc(sizeof(double) * (size_t)k * (size_t)m);
+    double* Omt = (double*)malloc(sizeof(double) * (size_t)k * (size_t)n);
+    double* T2 = (double*)malloc(sizeof(double) * (size_t)m * (size_t)n);
+    orc_omega(seed, 0u, n, 0, k, omega_prec, Om, n);
+    mm_nn(k, k, n, B, ldb, Om, n, R, k);                       /* R = B Omega            */
+    mm_tn(m, k, n, Q, ldq, G, ldg, QtG, k);                    /* Q^T G                  */
+    mm_nn(m, n, k, Q, ldq, QtG, k, dA, ldda);                  /* dA = Q (Q^T G)         */
+    for (int64_t c = 0; c < k; ++c)
+        for (int64_t r = 0; r < n; ++r) Bt[r + c * n] = B[c + r * ldb];
+    mm_nn(m, k, n, G, ldg, Bt, n, M1, m);                      /* M1 = G B^T             */
+    mm_tn(m, n, k, G, ldg, Q, ldq, GtQ, n);                    /* G^T Q                  */
+    mm_nn(m, k, n, A, lda, GtQ, n, T1, m);                     /* A (G^T Q)              */
+    for (int64_t c = 0; c < k; ++c)
+        for (int64_t r = 0; r < m; ++r) M1[r + c * m] += T1[r + c * m];
+    mm_tn(m, k, k, Q, ldq, M1, m, QtM, k);                     /* Q^T M1                 */
+    mm_nn(m, k, k, Q, ldq, QtM, k, T1, m);
+    for (int64_t c = 0; c < k; ++c)
+        for (int64_t r = 0; r < m; ++r) M1[r + c * m] -= T1[r + c * m];   /* (I - QQ^T) M1 */
+    /* N = M1 R^{-T}  <=>  R N^T = M1^T */
+    for (int64_t c = 0; c < k; ++c)
+        for (int64_t r = 0; r < m; ++r) M1t[c + r * k] = M1[r + c * m];
+    int rc = solve_left(R, k, M1t, m, Nt);
+    if (rc == 0) {
+        for (int64_t c = 0; c < n; ++c)
+            for (int64_t r = 0; r < k; ++r) Omt[r + c * k] = Om[c + r * n];
+        /* T2 = N Omega^T with N = Nt^T (m x k) */
+        double* Nm = T1;
+        for (int64_t c = 0; c < k; ++c)
+            for (int64_t r = 0; r < m; ++r) Nm[r + c * m] = Nt[c + r * k];
+        mm_nn(m, n, k, Nm, m, Omt, k, T2, m);
+        for (int64_t c = 0; c < n; ++c)
+            for (int64_t r = 0; r < m; ++r) dA[r + c * ldda] += T2[r + c * m];
+    }
+    free(Om); free(R); free(QtG); free(Bt); free(M1); free(GtQ); free(T1); free(QtM);
+    free(M1t); free(Nt); free(Omt); free(T2);
+    return rc;
+}

@@ -97,6 +97,16 @@ void orc_orth_reproject(const double* Y, int64_t m, int64_t p, int64_t ldy,
                         const double* Qbar, int64_t kprev, int64_t ldqb,
                         double* Qi, int64_t ldqi);
 
+/* Gradient of L(X) with respect to A for the fixed-rank map X = Q Q^T A,
+ * Q = orth(A Omega) with Omega (first k global columns of the Gaussian matrix)
+ * held fixed: dA = Q (Q^T G) + (I - Q Q^T)(G B^T + A (G^T Q)) R^{-T} Omega^T,
+ * R = B Omega, from differentiating the projector onto R(A Omega).
+ * Q (m x k), B (k x n) are the forward's factors; G = dL/dX (m x n).
+ * Returns 0, or -1 when R is singular or k is out of range. */
+int orc_qqta_adjoint(const double* A, int64_t m, int64_t n, int64_t lda, const double* Q, int64_t ldq,
+                     const double* B, int64_t ldb, int64_t k, uint64_t seed, int omega_prec,
+                     const double* G, int64_t ldg, double* dA, int64_t ldda);
+
 /* Number of OpenMP threads the oracle's parallel loops use (1 without OpenMP). */
 int orc_num_threads(void);
 

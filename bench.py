@@ -42,6 +42,9 @@ WORKLOADS = {
     "fp64": dict(name="randQB_b FP64 2000x1000 s_j=10^(-8(j-1)/999) b=50 eps=1e-4||A||_F", m=2000, n=1000, b=50,
                  eps_rel=1e-4, dtype="float64", spectrum="fp64cfg"),
 }
+WORKLOADS["batched"] = dict(name="randQB_b batched FP32: 512 matrices, m~U[256,4096], n~U[128,min(m,2048)], "
+                                 "s_j=exp(-j/r), r~U[10,200], b=32, eps_t=1e-3||A_t||_F",
+                            m=0, n=0, b=32, eps_rel=1e-3, dtype="float32", spectrum="exp", count=512)
 METRIC = "randQB_b TFLOP/s & roofline fraction at matched eps; mixed/batched vs plain FP32"
 
 
@@ -292,6 +295,107 @@ def run_e2e(args, w: dict, res: dict) -> dict:
             "api": "rqb_factor_host (pinned host buffers)"}
 
 
+def make_batch_device(count: int, seed: int = 0):
+    import numpy as np
+    import torch
+    import inputs
+    cases = inputs.batched_sizes(count, seed=seed)
+    mats, eps = [], []
+    for i, c in enumerate(cases):
+        s = inputs.spectrum_exp(min(c.m, c.n), c.rate)
+        A = inputs.usv_torch(c.m, c.n, s, 1000 + i, device="cuda", dtype=torch.float32)
+        mats.append(A)
+        eps.append(1e-3 * float(np.sqrt(np.sum(s ** 2))))
+    return mats, eps, cases
+
+
+def run_batched(args, w: dict, rank: int, world: int, dist):
+    """Config-4 workload: one rqb_factor_batched call per step (one graph launch)."""
+    import torch
+    from paper_1503_07157_gb300 import build as _build
+    _build.build()
+    from paper_1503_07157_gb300 import rqb
+    mats, eps, cases = make_batch_device(w["count"])
+    b = w["b"]
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    h = rqb.Handle(torch.float32, stream=stream)
+    for _ in range(args.warmup):
+        out = h.rqb_factor_batched(mats, eps, b, seed=0)
+    ks = [o[2] for o in out]
+    sts = [o[3] for o in out]
+    F = sum(useful_flops(c.m, c.n, b, (k + b - 1) // b) for c, k in zip(cases, ks))
+    clocks = ClockSampler(torch.cuda.current_device())
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.25)
+    kern_ms = 0.0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        h.rqb_factor_batched(mats, eps, b, seed=0)
+        kern_ms += h.rqb_get_stats().phase_ms[0]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    kern_ms /= args.steps
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    peak = alu_peak_tflops("float32", props.multi_processor_count, float(peaks.get("sm_max_mhz", 2070.0)))
+    achieved = F / (kern_ms * 1e-3) / 1e12
+    # the same matrices through a loop of single-matrix rqb_factor calls (one pass)
+    h1 = rqb.Handle(torch.float32, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for A, e in zip(mats, eps):
+        h1.rqb_factor(A, e, b, 0, check=False)
+    torch.cuda.synchronize()
+    loop_ms = (time.perf_counter() - t0) * 1e3
+    h1.close()
+    roofline = {"bound": "alu", "kernel": "k_batched (persistent, one launch per step)", "achieved": round(achieved, 3),
+                "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
+                               f"{float(peaks.get('sm_max_mhz', 2070.0)):.0f} MHz"}
+    # e2e: pinned host inputs in, Q and B back to pinned host, inside the timed region
+    hosts = [torch.empty(A.shape[1], A.shape[0], dtype=torch.float32, pin_memory=True).t() for A in mats]
+    for hA, A in zip(hosts, mats):
+        hA.copy_(A)
+    dev = [torch.empty_like(A).t().contiguous().t() for A in mats]
+    e2e_times = []
+    h2d = sum(A.numel() * 4 for A in mats)
+    d2h = 0
+    for it in range(args.warmup + max(1, args.e2e_steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for d_, hA in zip(dev, hosts):
+                d_.copy_(hA, non_blocking=True)
+        out2 = h.rqb_factor_batched(dev, eps, b, seed=0)
+        with torch.cuda.stream(stream):
+            qb = [(Q.to("cpu", non_blocking=True), B.to("cpu", non_blocking=True)) for Q, B, _, _ in out2]
+        stream.synchronize()
+        t1 = time.perf_counter()
+        if it >= args.warmup:
+            e2e_times.append(t1 - t0)
+            d2h = sum(q.numel() * 4 + bb.numel() * 4 for q, bb in qb)
+    te = statistics.median(e2e_times)
+    e2e = {"value": round(F / te / 1e12, 4), "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h), "ms_per_step": round(te * 1e3, 3),
+           "api": "pinned host copies + rqb_factor_batched"}
+    h.close()
+    return dict(value=F * world / (ms * 1e-3) / 1e12, ms=ms, F=F, clocks=clk, roofline=roofline, e2e=e2e,
+                launches=2, extra={"count": len(mats), "k_mean": float(sum(ks)) / len(ks), "k_max": max(ks),
+                                   "status_ok": int(sum(1 for s_ in sts if s_ == 0)),
+                                   "loop_of_single_calls_ms": round(loop_ms, 2)})
+
+
 def init_dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -330,6 +434,8 @@ def main():
 
     import torch
     rank, world, dist = init_dist()
+    if args.workload == "batched":
+        return main_batched(args, w, rank, world, dist)
     res = run_ours(args, w, rank, world, dist)
     e2e = run_e2e(args, w, res) if rank == 0 else None
     cpu = None
@@ -360,10 +466,63 @@ def main():
     return 0
 
 
+def main_batched(args, w, rank, world, dist) -> int:
+    res = run_batched(args, w, rank, world, dist)
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = oracle_baseline_batched(w, args.sample_frac)
+        line = {"metric": METRIC, "value": round(res["value"], 4), "unit": "TFLOP/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(res["ms"], 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded A_t = U diag(s) V^T; sizes drawn from seed 0)",
+                "config": dict({"workload": w["name"], "b": w["b"], "eps_rel": w["eps_rel"],
+                                "useful_flops_per_step": res["F"],
+                                "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                                "l2": "inputs larger than L2 (4.9 GB in total)"}, **res["extra"]),
+                "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"],
+                "gpu_launches": res["launches"] * args.steps, "clocks": res["clocks"]}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def oracle_baseline_batched(w: dict, frac: float) -> dict:
+    """Oracle on the first matrices of the batch recipe (bounded sample)."""
+    import numpy as np
+    import oracle
+    import inputs
+    cases = inputs.batched_sizes(w["count"], seed=0)
+    t_tot, F = 0.0, 0.0
+    used = 0
+    for i, c in enumerate(cases):
+        if t_tot > 10.0:
+            break
+        A = inputs.usv(c.m, c.n, inputs.spectrum_exp(min(c.m, c.n), c.rate), 1000 + i).astype(np.float32).astype(np.float64)
+        eps = 1e-3 * float(np.linalg.norm(A))
+        t0 = time.perf_counter()
+        r = oracle.randqb_b(A, eps, w["b"], seed=0, omega_prec=32)
+        t_tot += time.perf_counter() - t0
+        F += useful_flops(c.m, c.n, w["b"], r.blocks)
+        used += 1
+    return {"value": F / t_tot / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"oracle randQB_b on the first {used} matrices of the batch recipe ({t_tot:.1f} s)"}
+
+
 def run_reference(args, w: dict) -> int:
     """The reference arm: the CPU FP64 oracle, as it stands, on the machine's host
     cores; each step is one run on the bounded sample of the workload recipe."""
     import oracle
+    if args.workload == "batched":
+        cb = oracle_baseline_batched(w, args.sample_frac)
+        line = {"impl": "reference", "metric": METRIC, "value": round(cb["value"], 6), "unit": "TFLOP/s",
+                "n_gpus": 0, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": w["name"]},
+                "cpu_baseline": cb, "e2e": {"value": round(cb["value"], 6), "unit": "TFLOP/s",
+                                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
     A = make_sample_host(w, args.sample_frac)
     m, n = A.shape
     nA = float((A * A).sum()) ** 0.5

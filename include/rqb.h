@@ -153,6 +153,41 @@ int rqb_factor_host(rqb_handle h, const void* A_host, int64_t m, int64_t n, int6
                     double eps, int64_t b, uint64_t seed,
                     void* Q_host, int64_t ldq_host, void* B_host, int64_t ldb_host, int64_t* k);
 
+/* randQB_b for `count` independent FP32 matrices of any sizes in one
+ * persistent launch (captured in a CUDA graph): each CTA takes the next matrix
+ * (largest m n first) from a device work counter and runs Fig. randQB_b on it
+ * end to end, so no CTA ever waits on another.  Per matrix t (host arrays):
+ *   A[t]   device pointer, m[t] x n[t], leading dim lda[t] >= m[t]
+ *   eps[t] absolute tolerance
+ * Shared: b (1 <= b <= 32), seed (each matrix uses the same Omega stream, its
+ * own columns), the handle's max_rank (0 = min(m, n)).  Outputs (host arrays,
+ * device pointers valid until the next batched call or rqb_destroy):
+ *   Q[t], ldq[t], B[t], ldb[t], k[t], status[t] (RQB_OK, RQB_NOT_CONVERGED,
+ *   RQB_ERR_BREAKDOWN or RQB_ERR_NONFINITE per matrix).
+ * The handle must be FP32 with power = 0.  Returns RQB_OK when the launch ran
+ * (per-matrix results in status), else an error. */
+int rqb_factor_batched(rqb_handle h, int64_t count, const void* const* A, const int64_t* m,
+                       const int64_t* n, const int64_t* lda, const double* eps, int64_t b,
+                       uint64_t seed, const void** Q, int64_t* ldq, const void** B, int64_t* ldb,
+                       int64_t* k, int* status);
+
+/* X (m x n, leading dim ldx, device) = Q B of the last factorization on this
+ * handle, i.e. the approximation Q Q^T A (Prop. 4.1(b)). */
+int rqb_reconstruct(rqb_handle h, void* X, int64_t ldx);
+
+/* Adjoint of the last factorization on this handle, seen as the map
+ * A -> X = Q Q^T A with Omega (the first k global columns) held fixed.  The
+ * paper gives no derivatives; Q Q^T is the projector onto R(A Omega) (Sec. 4.1,
+ * Prop. 4.1(c)), and differentiating it gives
+ *   dL/dA = Q (Q^T G) + (I - Q Q^T)(G B^T + A (G^T Q)) R^{-T} Omega^T,
+ *   R = B Omega (upper triangular by Prop. 4.1(c)),
+ * computed from the stored Q, B and the regenerated Omega (no panel factors
+ * are kept).  G = dL_dX (m x n, leading dim ldg), dL_dA (m x n, leading dim
+ * ldda, caller-owned, overwritten).  The A passed to the factorization must
+ * still be valid and unchanged.  Errors: RQB_ERR_INVALID (no factorization on
+ * the handle, bad leading dimension), RQB_ERR_UNSUPPORTED (power > 0). */
+int rqb_backward(rqb_handle h, const void* dL_dX, int64_t ldg, void* dL_dA, int64_t ldda);
+
 /* Statistics of the last call on this handle. */
 int rqb_get_stats(rqb_handle h, rqb_stats* out);
 

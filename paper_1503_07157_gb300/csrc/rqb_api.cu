@@ -10,6 +10,15 @@
 
 using namespace rqb;
 
+namespace rqb {
+namespace batched {
+int factor_batched(cudaStream_t stream, int num_sms, int64_t count, const void* const* A, const int64_t* m,
+                   const int64_t* n, const int64_t* lda, const double* eps, int64_t b, uint64_t seed, int64_t max_rank,
+                   const void** Q, int64_t* ldq, const void** B, int64_t* ldb, int64_t* k, int* status, void** outbuf,
+                   size_t* outbytes, void** workbuf, size_t* workbytes, float* ms, int* launches);
+}
+}  // namespace rqb
+
 namespace {
 
 constexpr int kNrmCap = 8192;      // per-CTA FP64 partials
@@ -105,6 +114,16 @@ struct rqb_handle_s {
     rqb_stats stats{};
     int last_status = RQB_OK;
     PhaseTimer timer;
+    // the last factorization, for rqb_reconstruct / rqb_backward
+    const void* last_A = nullptr;
+    int64_t last_m = 0, last_n = 0, last_lda = 0, last_k = 0, last_b = 0;
+    uint64_t last_seed = 0;
+    bool have_factor = false;
+    DevBuf adj;                // workspace of rqb_backward
+    void* bat_out = nullptr;   // outputs of rqb_factor_batched
+    size_t bat_out_bytes = 0;
+    void* bat_work = nullptr;  // its descriptors and per-CTA scratch
+    size_t bat_work_bytes = 0;
 };
 
 namespace {
@@ -113,7 +132,10 @@ template <typename T>
 struct Arena {
     T* Om;          // n x bp row-major
     T* Y;           // m x bp (ld m)
-    T* Y1;          // m x bp (ld m)
+    T* Y1;          // max(m, n) x bp: panel scratch of orth_reproject
+    T* Qt;          // m x bp (ld m): power-scheme panel
+    T* Z;           // n x bp (ld n): A^T Q of the power scheme
+    T* Zq;          // n x bp (ld n): orth(A^T Q)
     T* Rinv;        // bp x bp
     T* Cc;          // kprev x bp
     T* part;        // split partials
@@ -150,7 +172,10 @@ int ensure_arena(rqb_handle h, int64_t m, int64_t n, int bp, int64_t kprev_max, 
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
     const size_t oOm = take(sizeof(T) * (size_t)n * bp);
     const size_t oY = take(sizeof(T) * (size_t)m * bp);
-    const size_t oY1 = take(sizeof(T) * (size_t)m * bp);
+    const size_t oY1 = take(sizeof(T) * (size_t)std::max(m, n) * bp);
+    const size_t oQt = take(sizeof(T) * (size_t)m * bp);
+    const size_t oZ = take(sizeof(T) * (size_t)n * bp);
+    const size_t oZq = take(sizeof(T) * (size_t)n * bp);
     const size_t oRinv = take(sizeof(T) * (size_t)bp * bp);
     const size_t oCc = take(sizeof(T) * (size_t)kp * bp);
     const size_t oPart = take(sizeof(T) * part_cap);
@@ -164,6 +189,9 @@ int ensure_arena(rqb_handle h, int64_t m, int64_t n, int bp, int64_t kprev_max, 
     out->Om = reinterpret_cast<T*>(base + oOm);
     out->Y = reinterpret_cast<T*>(base + oY);
     out->Y1 = reinterpret_cast<T*>(base + oY1);
+    out->Qt = reinterpret_cast<T*>(base + oQt);
+    out->Z = reinterpret_cast<T*>(base + oZ);
+    out->Zq = reinterpret_cast<T*>(base + oZq);
     out->Rinv = reinterpret_cast<T*>(base + oRinv);
     out->Cc = reinterpret_cast<T*>(base + oCc);
     out->part = reinterpret_cast<T*>(base + oPart);
@@ -208,7 +236,7 @@ int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_
                    const T* Qbar, int64_t kprev, int64_t ldqb, T* Qout, int64_t ldqo) {
     // pass 1: CholeskyQR of Y, Y1 = Y R^{-1}
     RQB_CK(gemm_tn_f64acc<T>(cx, m, bp, bp, Y, ldy, Y, ldy, ar.G, bp, ar.dpart, ar.dpart_cap, true));
-    RQB_CK(chol_inv<T>(cx, ar.G, bp, p, ar.R, ar.Rinv));
+    RQB_CK(chol_inv<T>(cx, ar.G, bp, p, ar.R, ar.Rinv, true, ar.dpart, ar.dpart_cap));
     {
         NNArgs<T> a;
         a.m = m; a.K = bp; a.nc = bp; a.nout = bp;
@@ -234,7 +262,7 @@ int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_
     }
     // pass 2: CholeskyQR of Y1, Qout = Y1 R^{-1}
     RQB_CK(gemm_tn_f64acc<T>(cx, m, bp, bp, ar.Y1, m, ar.Y1, m, ar.G, bp, ar.dpart, ar.dpart_cap, false));
-    RQB_CK(chol_inv<T>(cx, ar.G, bp, p, ar.R, ar.Rinv));
+    RQB_CK(chol_inv<T>(cx, ar.G, bp, p, ar.R, ar.Rinv, sizeof(T) == 8, ar.dpart, ar.dpart_cap));
     {
         NNArgs<T> a;
         a.m = m; a.K = bp; a.nc = bp; a.nout = p;
@@ -244,6 +272,38 @@ int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_
         RQB_CK(gemm_nn<T>(cx, a));
     }
     return RQB_OK;
+}
+
+// Fig. randQB_pb lines (3)-(8) for block i: Q_i = orth(A Omega_i); P times
+// Q_i = orth(A^T Q_i), Q_i = orth(A Q_i), on the current (downdated) A; then
+// line (8): Q_i = orth(Q_i - Qbar Qbar^T Q_i), written to Qi.  ar.Y holds
+// A Omega_i on entry; its columns >= p are zero.
+template <typename T>
+int power_panel(rqb_handle h, Ctx& cx, const Arena<T>& ar, int64_t m, int64_t n, int p, int bp, const T* W,
+                int64_t ldw, const T* Qbar, int64_t kprev, int64_t ldqb, T* Qi) {
+    RQB_CK(cudaMemsetAsync(ar.Qt, 0, sizeof(T) * (size_t)m * bp, h->stream));
+    RQB_CK(cudaMemsetAsync(ar.Z, 0, sizeof(T) * (size_t)n * bp, h->stream));
+    RQB_CK(cudaMemsetAsync(ar.Zq, 0, sizeof(T) * (size_t)n * bp, h->stream));
+    int rc = orth_reproject<T>(h, cx, ar, ar.Y, m, m, p, bp, nullptr, 0, m, ar.Qt, m);     // line (3)
+    if (rc != RQB_OK) return rc;
+    for (int j = 0; j < h->cfg.power; ++j) {
+        // line (5): Z = A^T Q_i (n x p), Q_i' = orth(Z)
+        RQB_CK(gemm_tn<T>(cx, m, (int)n, p, W, ldw, ar.Qt, m, ar.Z, n, ar.part, ar.part_cap, nullptr, 0, nullptr));
+        rc = orth_reproject<T>(h, cx, ar, ar.Z, n, n, p, bp, nullptr, 0, n, ar.Zq, n);
+        if (rc != RQB_OK) return rc;
+        // line (6): Y = A Q_i', Q_i = orth(Y)
+        NNArgs<T> a;
+        a.m = m; a.K = n; a.nc = bp; a.nout = bp;
+        a.X = W; a.ldx = ldw;
+        a.C = ar.Zq; a.csk = 1; a.csj = n; a.c_rowmajor = false;
+        a.Out = ar.Y; a.ldo = m;
+        a.part = ar.part; a.part_cap = ar.part_cap; a.allow_split = 1;
+        RQB_CK(gemm_nn<T>(cx, a));
+        rc = orth_reproject<T>(h, cx, ar, ar.Y, m, m, p, bp, nullptr, 0, m, ar.Qt, m);
+        if (rc != RQB_OK) return rc;
+    }
+    // line (8): re-projection against the earlier blocks and a final orth
+    return orth_reproject<T>(h, cx, ar, ar.Qt, m, m, p, bp, Qbar, kprev, ldqb, Qi, ldqb);
 }
 
 template <typename T>
@@ -309,8 +369,13 @@ int factor_impl(rqb_handle h, const T* A, int64_t m, int64_t n, int64_t lda, dou
         T* Bi = B + k;
         // lines (3), (3')
         h->timer.begin(h->stream, RQB_PHASE_ORTH);
-        rc = orth_reproject<T>(h, cx, ar, ar.Y, m, m, p, bp, Q, k, ldq, Qi, ldq);
-        if (rc != RQB_OK) return rc;
+        if (h->cfg.power == 0) {
+            rc = orth_reproject<T>(h, cx, ar, ar.Y, m, m, p, bp, Q, k, ldq, Qi, ldq);
+            if (rc != RQB_OK) return rc;
+        } else {
+            rc = power_panel<T>(h, cx, ar, m, n, p, bp, Wsrc, ldws, Q, k, ldq, Qi);
+            if (rc != RQB_OK) return rc;
+        }
         h->timer.end(h->stream);
         h->timer.begin(h->stream, RQB_PHASE_PROJECT);
         // line (4): B_i = Q_i^T A, ||B_i||^2
@@ -417,7 +482,8 @@ int rqb_create(rqb_handle* out, const rqb_config* cfg) {
     if (cfg->dtype != RQB_F64 && cfg->dtype != RQB_F32 && cfg->dtype != RQB_BF16) return RQB_ERR_INVALID;
     if (cfg->prec != RQB_PREC_NATIVE && cfg->prec != RQB_PREC_TF32X3 && cfg->prec != RQB_PREC_BF16)
         return RQB_ERR_INVALID;
-    if (cfg->prec != RQB_PREC_NATIVE || cfg->dtype == RQB_BF16 || cfg->power != 0) return RQB_ERR_UNSUPPORTED;
+    if (cfg->prec != RQB_PREC_NATIVE || cfg->dtype == RQB_BF16) return RQB_ERR_UNSUPPORTED;
+    if (cfg->power > 8) return RQB_ERR_INVALID;
     rqb_handle h = new (std::nothrow) rqb_handle_s();
     if (!h) return RQB_ERR_OOM;
     h->cfg = *cfg;
@@ -459,6 +525,9 @@ int rqb_destroy(rqb_handle h) {
     h->b.release();
     h->w.release();
     h->ahost.release();
+    h->adj.release();
+    if (h->bat_out) cudaFree(h->bat_out);
+    if (h->bat_work) cudaFree(h->bat_work);
     if (h->hstate) cudaFreeHost(h->hstate);
     h->timer.destroy();
     delete h;
@@ -482,6 +551,9 @@ int rqb_factor(rqb_handle h, const void* A, int64_t m, int64_t n, int64_t lda, d
     *B = h->b.p;
     *ldb = h->ldb;
     *k = kk;
+    h->have_factor = (rc == RQB_OK || rc == RQB_NOT_CONVERGED) && kk > 0;
+    h->last_A = A;
+    h->last_m = m; h->last_n = n; h->last_lda = lda; h->last_k = kk; h->last_b = b; h->last_seed = seed;
     return finish(h, rc);
 }
 
@@ -699,3 +771,182 @@ int rqb_downdate_sketch(rqb_handle h, const void* A, int64_t lda, const void* Qi
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// X = Q B, and the adjoint of A -> Q Q^T A (fixed Omega)
+namespace {
+
+template <typename T>
+int reconstruct_impl(rqb_handle h, T* X, int64_t ldx) {
+    Scal sc = scalars(h);
+    Ctx cx;
+    cx.stream = h->stream; cx.num_sms = h->num_sms; cx.st = sc.st;
+    NNArgs<T> a;
+    a.m = h->last_m; a.K = h->last_k; a.nc = (int)h->last_n; a.nout = (int)h->last_n;
+    a.X = reinterpret_cast<const T*>(h->q.p); a.ldx = h->ldq;
+    a.C = reinterpret_cast<const T*>(h->b.p); a.csk = 1; a.csj = h->ldb; a.c_rowmajor = false;
+    a.Out = X; a.ldo = ldx;
+    RQB_CK(gemm_nn<T>(cx, a));
+    RQB_CK(cudaStreamSynchronize(h->stream));
+    return RQB_OK;
+}
+
+// dA = Q (Q^T G) + (I - Q Q^T)(G B^T + A (G^T Q)) R^{-T} Omega^T,  R = B Omega
+template <typename T>
+int backward_impl(rqb_handle h, const T* G, int64_t ldg, T* dA, int64_t ldda) {
+    const int64_t m = h->last_m, n = h->last_n, k = h->last_k;
+    const T* A = reinterpret_cast<const T*>(h->last_A);
+    const int64_t lda = h->last_lda;
+    const T* Q = reinterpret_cast<const T*>(h->q.p);
+    const T* B = reinterpret_cast<const T*>(h->b.p);
+    const int64_t ldq = h->ldq, ldb = h->ldb;
+    // workspace
+    const size_t part_cap = std::max<size_t>((size_t)4 * k * std::max(m, n), (size_t)8 * m * 256);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+    const size_t oOm = take(sizeof(T) * n * k), oR = take(sizeof(T) * k * k), oRd = take(sizeof(double) * k * k);
+    const size_t oRi = take(sizeof(T) * k * k), oQtG = take(sizeof(T) * k * n), oM1 = take(sizeof(T) * m * k);
+    const size_t oGtQ = take(sizeof(T) * n * k), oQtM = take(sizeof(T) * k * k), oN = take(sizeof(T) * m * k);
+    const size_t oP = take(sizeof(T) * part_cap);
+    int rc = h->adj.ensure(off);
+    if (rc != RQB_OK) return rc;
+    char* base = reinterpret_cast<char*>(h->adj.p);
+    T* Om = reinterpret_cast<T*>(base + oOm);
+    T* R = reinterpret_cast<T*>(base + oR);
+    double* Rd = reinterpret_cast<double*>(base + oRd);
+    T* Rinv = reinterpret_cast<T*>(base + oRi);
+    T* QtG = reinterpret_cast<T*>(base + oQtG);
+    T* M1 = reinterpret_cast<T*>(base + oM1);
+    T* GtQ = reinterpret_cast<T*>(base + oGtQ);
+    T* QtM = reinterpret_cast<T*>(base + oQtM);
+    T* Nm = reinterpret_cast<T*>(base + oN);
+    T* part = reinterpret_cast<T*>(base + oP);
+    Scal sc = scalars(h);
+    Ctx cx;
+    cx.stream = h->stream; cx.num_sms = h->num_sms; cx.st = sc.st;
+
+    // Omega (n x k, row-major) and R = B Omega, R^{-1}
+    RQB_CK(launch_omega<T>(cx, n, 0, (int)k, (int)k, h->last_seed, Om, k, 1));
+    {
+        NNArgs<T> a;
+        a.m = k; a.K = n; a.nc = (int)k; a.nout = (int)k;
+        a.X = B; a.ldx = ldb;
+        a.C = Om; a.csk = k; a.csj = 1; a.c_rowmajor = true;
+        a.Out = R; a.ldo = k;
+        a.part = part; a.part_cap = part_cap; a.allow_split = 1;
+        RQB_CK(gemm_nn<T>(cx, a));
+    }
+    RQB_CK(launch_to_double<T>(cx, k, k, R, k, Rd, k));
+    RQB_CK(tri_inverse<T>(cx, Rd, (int)k, Rinv));
+    // dA = Q (Q^T G)
+    RQB_CK(gemm_tn<T>(cx, m, (int)k, n, Q, ldq, G, ldg, QtG, k, part, part_cap, nullptr, 0, nullptr));
+    {
+        NNArgs<T> a;
+        a.m = m; a.K = k; a.nc = (int)n; a.nout = (int)n;
+        a.X = Q; a.ldx = ldq;
+        a.C = QtG; a.csk = 1; a.csj = k; a.c_rowmajor = false;
+        a.Out = dA; a.ldo = ldda;
+        RQB_CK(gemm_nn<T>(cx, a));
+    }
+    // M1 = G B^T + A (G^T Q)
+    {
+        NNArgs<T> a;
+        a.m = m; a.K = n; a.nc = (int)k; a.nout = (int)k;
+        a.X = G; a.ldx = ldg;
+        a.C = B; a.csk = ldb; a.csj = 1; a.c_rowmajor = true;   // C(c, j) = B(j, c)
+        a.Out = M1; a.ldo = m;
+        a.part = part; a.part_cap = part_cap; a.allow_split = 1;
+        RQB_CK(gemm_nn<T>(cx, a));
+    }
+    RQB_CK(gemm_tn<T>(cx, m, (int)n, k, G, ldg, Q, ldq, GtQ, n, part, part_cap, nullptr, 0, nullptr));
+    {
+        NNArgs<T> a;
+        a.m = m; a.K = n; a.nc = (int)k; a.nout = (int)k;
+        a.X = A; a.ldx = lda;
+        a.C = GtQ; a.csk = 1; a.csj = n; a.c_rowmajor = false;
+        a.Out = M1; a.ldo = m;
+        a.Yin = M1; a.ldyin = m; a.alpha = T(1); a.beta = T(1);
+        a.part = part; a.part_cap = part_cap; a.allow_split = 1;
+        RQB_CK(gemm_nn<T>(cx, a));
+    }
+    // M1 -= Q (Q^T M1)
+    RQB_CK(gemm_tn<T>(cx, m, (int)k, k, Q, ldq, M1, m, QtM, k, part, part_cap, nullptr, 0, nullptr));
+    {
+        NNArgs<T> a;
+        a.m = m; a.K = k; a.nc = (int)k; a.nout = (int)k;
+        a.X = Q; a.ldx = ldq;
+        a.C = QtM; a.csk = 1; a.csj = k; a.c_rowmajor = false;
+        a.Out = M1; a.ldo = m;
+        a.Yin = M1; a.ldyin = m; a.alpha = T(-1); a.beta = T(1);
+        a.part = part; a.part_cap = part_cap; a.allow_split = 1;
+        RQB_CK(gemm_nn<T>(cx, a));
+    }
+    // N = M1 R^{-T};  dA += N Omega^T
+    {
+        NNArgs<T> a;
+        a.m = m; a.K = k; a.nc = (int)k; a.nout = (int)k;
+        a.X = M1; a.ldx = m;
+        a.C = Rinv; a.csk = k; a.csj = 1; a.c_rowmajor = true;  // C(c, j) = Rinv(j, c)
+        a.Out = Nm; a.ldo = m;
+        RQB_CK(gemm_nn<T>(cx, a));
+    }
+    {
+        NNArgs<T> a;
+        a.m = m; a.K = k; a.nc = (int)n; a.nout = (int)n;
+        a.X = Nm; a.ldx = m;
+        a.C = Om; a.csk = 1; a.csj = k; a.c_rowmajor = false;   // C(c, j) = Omega(j, c)
+        a.Out = dA; a.ldo = ldda;
+        a.Yin = dA; a.ldyin = ldda; a.alpha = T(1); a.beta = T(1);
+        RQB_CK(gemm_nn<T>(cx, a));
+    }
+    int err = read_state(h, sc);
+    return err;
+}
+
+}  // namespace
+
+extern "C" int rqb_reconstruct(rqb_handle h, void* X, int64_t ldx) {
+    if (!h) return RQB_ERR_INVALID;
+    if (!h->have_factor || !X || ldx < h->last_m) return finish(h, RQB_ERR_INVALID);
+    if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
+    int rc = (h->cfg.dtype == RQB_F64) ? reconstruct_impl<double>(h, static_cast<double*>(X), ldx)
+                                       : reconstruct_impl<float>(h, static_cast<float*>(X), ldx);
+    return finish(h, rc);
+}
+
+extern "C" int rqb_backward(rqb_handle h, const void* dL_dX, int64_t ldg, void* dL_dA, int64_t ldda) {
+    if (!h) return RQB_ERR_INVALID;
+    if (!h->have_factor || !dL_dX || !dL_dA || ldg < h->last_m || ldda < h->last_m) return finish(h, RQB_ERR_INVALID);
+    if (h->cfg.power != 0) return finish(h, RQB_ERR_UNSUPPORTED);
+    if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
+    RQB_CK(cudaMemsetAsync(scalars(h).st, 0, sizeof(DevState), h->stream));
+    int rc = (h->cfg.dtype == RQB_F64)
+                 ? backward_impl<double>(h, static_cast<const double*>(dL_dX), ldg, static_cast<double*>(dL_dA), ldda)
+                 : backward_impl<float>(h, static_cast<const float*>(dL_dX), ldg, static_cast<float*>(dL_dA), ldda);
+    return finish(h, rc);
+}
+
+extern "C" int rqb_factor_batched(rqb_handle h, int64_t count, const void* const* A, const int64_t* m,
+                                  const int64_t* n, const int64_t* lda, const double* eps, int64_t b, uint64_t seed,
+                                  const void** Q, int64_t* ldq, const void** B, int64_t* ldb, int64_t* k,
+                                  int* status) {
+    if (!h) return RQB_ERR_INVALID;
+    if (count < 1 || !A || !m || !n || !lda || !eps || !Q || !ldq || !B || !ldb || !k || !status || b < 1 || b > 32)
+        return finish(h, RQB_ERR_INVALID);
+    for (int64_t t = 0; t < count; ++t)
+        if (check_matrix(A[t], m[t], n[t], lda[t]) != RQB_OK || !(eps[t] >= 0.0) || !std::isfinite(eps[t]))
+            return finish(h, RQB_ERR_INVALID);
+    if (h->cfg.dtype != RQB_F32 || h->cfg.power != 0) return finish(h, RQB_ERR_UNSUPPORTED);
+    if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
+    std::memset(&h->stats, 0, sizeof(h->stats));
+    float ms = 0.f;
+    int launches = 0;
+    int rc = rqb::batched::factor_batched(h->stream, h->num_sms, count, A, m, n, lda, eps, b, seed, h->cfg.max_rank,
+                                          Q, ldq, B, ldb, k, status, &h->bat_out, &h->bat_out_bytes, &h->bat_work,
+                                          &h->bat_work_bytes, &ms, &launches);
+    h->have_factor = false;
+    h->stats.kernel_launches = launches;
+    h->stats.phase_ms[RQB_PHASE_SKETCH] = ms;   // the whole persistent launch
+    h->stats.phase_calls[RQB_PHASE_SKETCH] = 1;
+    return finish(h, rc);
+}

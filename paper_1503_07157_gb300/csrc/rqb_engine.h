@@ -62,12 +62,18 @@ cudaError_t gemm_tn_f64acc(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, i
                            int64_t ldy, double* Out, int64_t ldo, double* part, size_t part_cap_elems,
                            bool exact);
 template <typename T>
-cudaError_t chol_inv(Ctx& cx, const double* G, int bp, int p, double* R, T* Rinv);
+cudaError_t chol_inv(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, bool fp64_factor, double* scratch,
+                     size_t scratch_doubles);
 template <typename T>
 cudaError_t downdate_sketch(Ctx& cx, int64_t m, int64_t n, int p, int bp, const T* Wsrc, int64_t ldws,
                             const T* Qi, int64_t ldq, const T* Bi, int64_t ldb, const T* Om, T* Wdst,
                             int64_t ldwd, T* Y, int64_t ldy, T* part, size_t part_cap_elems, double* nrm_part,
                             int nrm_cap, double* nrm_out);
+template <typename T>
+cudaError_t tri_inverse(Ctx& cx, const double* R, int kdim, T* Rinv);
+template <typename T>
+cudaError_t launch_to_double(Ctx& cx, int64_t rows, int64_t cols, const T* src, int64_t lds, double* dst,
+                             int64_t ldd);
 cudaError_t launch_set_norm(Ctx& cx, const double* nrm);
 cudaError_t launch_stop_after_b(Ctx& cx, const double* nb2, double eps2, double tau_rel, int fixed);
 cudaError_t launch_stop_direct(Ctx& cx, const double* d2, double eps2);

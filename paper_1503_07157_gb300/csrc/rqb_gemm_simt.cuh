@@ -74,7 +74,8 @@ struct GemmNN {
 };
 
 template <typename T, int BM, int BN, int BK, bool C_ROWMAJOR>
-__global__ void __launch_bounds__(GemmNN<T, BM, BN, BK, C_ROWMAJOR>::NT)
+__global__ void __launch_bounds__(GemmNN<T, BM, BN, BK, C_ROWMAJOR>::NT,
+                                  (sizeof(T) == 4 && GemmNN<T, BM, BN, BK, C_ROWMAJOR>::NT >= 256) ? 2 : 1)
 k_gemm_nn(int64_t m, int64_t K, int64_t ksplit, int nc, int nout,
           const T* __restrict__ X, int64_t ldx,
           const T* __restrict__ C, int64_t csk, int64_t csj,
@@ -282,7 +283,7 @@ __device__ __forceinline__ void exact_fma_acc(float a, float b, float& hi, float
 }
 
 template <typename T, typename Acc, int BP, int BQ, int BK, int TP, int TQ, int PROMOTE, bool COMP = false>
-__global__ void __launch_bounds__((BP / TP) * (BQ / TQ))
+__global__ void __launch_bounds__((BP / TP) * (BQ / TQ), ((BP / TP) * (BQ / TQ) >= 256 && TP * TQ == 64) ? 2 : 1)
 k_gemm_tn(int64_t m, int pn, int64_t qn, int64_t rsplit,
           const T* __restrict__ X, int64_t ldx,
           const T* __restrict__ Y, int64_t ldy,

@@ -150,55 +150,38 @@ cudaError_t launch_reduce_split(Ctx& cx, int64_t rows, int64_t cols, int splits,
 // ---------------------------------------------------------------------------
 // CholeskyQR factor of the panel Gram matrix: G (bp x bp, FP64, symmetric;
 // only rows/cols < p are meaningful) = R^T R with R upper triangular and
-// diag(R) > 0; rows/cols >= p are set to the identity.  Right-looking
-// column algorithm in FP64, one CTA; the working copy lives in shared memory
-// when it fits, else in R itself (global).  A pivot <= tol * G_jj(original)
-// records RQB_ERR_BREAKDOWN.
-template <int NT>
-__global__ void __launch_bounds__(NT)
-k_cholesky(const double* __restrict__ G, int ldg, int bp, int p, double* __restrict__ R, int use_smem,
+// diag(R) > 0; rows/cols >= p are set to the identity.  One CTA of 256
+// threads, working precision W (FP64 for the first CholeskyQR pass, whose Gram
+// may be ill-conditioned; FP32 for the second, whose Gram is I + O(u kappa)).
+// The upper triangle is kept row-major, in shared memory when the square fits,
+// else in a global scratch of bp x bp elements.  Thread (ty, tx) of a 16 x 16 grid owns the entries
+// (r, c) with r = ty, c = tx (mod 16); step j subtracts S[j][r] S[j][c] / d_j
+// from each owned S[r][c] (j < r <= c) using the unscaled pivot row, so a
+// step needs one barrier; rows are scaled by d_j^{-1/2} at the end.  A pivot
+// <= tol * G_jj records RQB_ERR_BREAKDOWN.
+template <typename W>
+__global__ void __launch_bounds__(256)
+k_cholesky(const double* __restrict__ G, int bp, int p, double* __restrict__ R, int in_smem, void* scratch,
            double tol, DevState* st) {
-    extern __shared__ __align__(16) double dsm[];
-    double* S = use_smem ? dsm : R;   // column-major bp x bp, ld = bp
-    __shared__ int bad;
-    __shared__ double rowj[256];
-    const int tid = threadIdx.x;
-    if (tid == 0) bad = 0;
-    for (int e = tid; e < bp * bp; e += NT) {
-        const int r = e % bp, c = e / bp;
-        double v;
-        if (r < p && c < p) v = (r <= c) ? G[r + c * ldg] : 0.0;
-        else v = (r == c) ? 1.0 : 0.0;
-        S[r + c * bp] = v;
-    }
+    extern __shared__ __align__(16) unsigned char chol_smem[];
+    __shared__ double refd[256];
+    __shared__ double rdiag[256];
+    W* S = in_smem ? reinterpret_cast<W*>(chol_smem) : reinterpret_cast<W*>(scratch);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    for (int r = tid; r < p; r += 256) refd[r] = G[r + (int64_t)r * bp];
+    for (int r = ty; r < p; r += 16)
+        for (int c = r + ((tx - r) % 16 + 16) % 16; c < p; c += 16) S[(int64_t)r * bp + c] = (W)G[r + (int64_t)c * bp];
     __syncthreads();
+    bool bad = false;
     for (int j = 0; j < p; ++j) {
-        if (tid == 0) {
-            const double d = S[j + j * bp];
-            const double ref = G[j + j * ldg];
-            if (!(d > tol * ref) || !(d > 0.0) || !isfinite(d)) {
-                bad = 1;
-                S[j + j * bp] = 1.0;
-            } else {
-                S[j + j * bp] = sqrt(d);
-            }
-        }
-        __syncthreads();
-        if (bad) break;
-        const double rjj = S[j + j * bp];
-        // row j of R, also staged contiguously for the trailing update
-        for (int c = j + 1 + tid; c < p; c += NT) {
-            const double v = S[j + c * bp] / rjj;
-            S[j + c * bp] = v;
-            rowj[c] = v;
-        }
-        __syncthreads();
-        // trailing update of the upper triangle: S[r][c] -= R[j][r] R[j][c], j < r <= c < p;
-        // one warp per column c (rows contiguous in the column-major layout)
-        const int lane = tid & 31, warp = tid >> 5;
-        for (int c = j + 1 + warp; c < p; c += NT / 32) {
-            const double rjc = rowj[c];
-            for (int r = j + 1 + lane; r <= c; r += 32) S[r + c * bp] -= rowj[r] * rjc;
+        const W d = S[(int64_t)j * bp + j];
+        if (!((double)d > tol * refd[j]) || !isfinite((double)d)) { bad = true; break; }   // uniform
+        const W invd = W(1) / d;
+        const W* Sj = S + (int64_t)j * bp;
+        for (int r = j + 1 + ((ty - (j + 1)) % 16 + 16) % 16; r < p; r += 16) {
+            const W f = Sj[r] * invd;
+            W* Sr = S + (int64_t)r * bp;
+            for (int c = r + ((tx - r) % 16 + 16) % 16; c < p; c += 16) Sr[c] -= f * Sj[c];
         }
         __syncthreads();
     }
@@ -206,45 +189,54 @@ k_cholesky(const double* __restrict__ G, int ldg, int bp, int p, double* __restr
         if (tid == 0) record_error(st, RQB_ERR_BREAKDOWN);
         return;
     }
-    if (use_smem) {
-        for (int e = tid; e < bp * bp; e += NT) {
-            const int r = e % bp, c = e / bp;
-            R[e] = (r <= c) ? S[e] : 0.0;
+    // R (column-major, FP64): R[r][c] = S[r][c] / sqrt(d_r), identity beyond p.
+    for (int r = tid; r < p; r += 256) rdiag[r] = sqrt((double)S[(int64_t)r * bp + r]);
+    __syncthreads();
+    for (int e = tid; e < bp * bp; e += 256) {
+        const int r = e % bp, c = e / bp;
+        double v = 0.0;
+        if (r < p && c < p) {
+            if (r < c) v = (double)S[(int64_t)r * bp + c] / rdiag[r];
+            else if (r == c) v = rdiag[r];
+        } else if (r == c) {
+            v = 1.0;
         }
-    } else {
-        for (int e = tid; e < bp * bp; e += NT) {
-            const int r = e % bp, c = e / bp;
-            if (r > c) R[e] = 0.0;
-        }
+        R[e] = v;
     }
 }
 
 // Rinv (bp x bp, type T, column-major) = R^{-1} for upper-triangular R (FP64).
-// CTA c solves R x = e_c by column-oriented back substitution with the
-// leading (c+1) x (c+1) block of R staged in shared memory when it fits.
+// One warp per column c solves R x = e_c by column-oriented back substitution
+// (x_t = x_t / R_tt, then x_r -= R_rt x_t for r < t), warp-synchronous, with
+// the CTA's leading block of R and the reciprocal diagonal in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(128)
-k_tri_inverse(const double* __restrict__ R, int bp, T* __restrict__ Rinv, int smem_cols) {
+k_tri_inverse(const double* __restrict__ R, int bp, T* __restrict__ Rinv, int staged_cols) {
     extern __shared__ __align__(16) double dsm[];
-    const int c = blockIdx.x;
-    const int tid = threadIdx.x;
-    double* x = dsm;                 // bp entries: right-hand side / solution
-    double* Rs = dsm + bp;           // columns 0..c of R when staged (ld = bp)
-    const bool staged = (c < smem_cols);
-    if (staged) {
-        for (int e = tid; e < (c + 1) * bp; e += 128) Rs[e] = R[e];
-    }
-    for (int r = tid; r < bp; r += 128) x[r] = (r == c) ? 1.0 : 0.0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cmax = min(bp - 1, (int)blockIdx.x * 4 + 3);
+    const int c = blockIdx.x * 4 + warp;
+    double* invd = dsm;                  // bp
+    double* xs = dsm + bp;               // 4 x bp
+    double* Rs = dsm + 5 * bp;           // columns 0..cmax of R (ld bp), when staged
+    const bool staged = (cmax < staged_cols);
+    for (int t = threadIdx.x; t <= cmax; t += 128) invd[t] = 1.0 / R[t + (int64_t)t * bp];
+    if (staged)
+        for (int e = threadIdx.x; e < (cmax + 1) * bp; e += 128) Rs[e] = R[e];
     __syncthreads();
+    if (c >= bp) return;
     const double* Rc = staged ? Rs : R;
+    double* x = xs + warp * bp;
+    for (int r = lane; r <= c; r += 32) x[r] = (r == c) ? 1.0 : 0.0;
+    __syncwarp();
     for (int t = c; t >= 0; --t) {
-        const double xt = x[t] / Rc[t + t * bp];
-        __syncthreads();
-        if (tid == 0) x[t] = xt;
-        for (int r = tid; r < t; r += 128) x[r] -= Rc[r + t * bp] * xt;
-        __syncthreads();
+        const double xt = x[t] * invd[t];
+        for (int r = lane; r < t; r += 32) x[r] -= Rc[r + (int64_t)t * bp] * xt;
+        __syncwarp();
+        if (lane == 0) x[t] = xt;
+        __syncwarp();
     }
-    for (int r = tid; r < bp; r += 128) Rinv[r + (int64_t)c * bp] = (T)((r <= c) ? x[r] : 0.0);
+    for (int r = lane; r < bp; r += 32) Rinv[r + (int64_t)c * bp] = (T)((r <= c) ? x[r] : 0.0);
 }
 
 // ---------------------------------------------------------------------------
@@ -501,15 +493,18 @@ k_downdate_sketch(int64_t m, int64_t n, int p, int64_t csplit,
 // ---------------------------------------------------------------------------
 // Launch configuration helpers
 static int choose_splits(int64_t tiles, int64_t kdim, int64_t kmin, int max_splits, int slots) {
+    // Largest wave efficiency ctas / (waves * slots); a larger split count is
+    // taken only when it improves the efficiency by more than 1 % (relative),
+    // so grids smaller than one wave grow until the reduction length per split
+    // reaches kmin, and full grids keep the fewest splits.
     int best = 1;
-    double best_score = -1.0;
+    double best_eff = -1.0;
     for (int s = 1; s <= max_splits; ++s) {
         if (s > 1 && kdim / s < kmin) break;
         const int64_t ctas = tiles * s;
         const int64_t waves = (ctas + slots - 1) / slots;
         const double eff = (double)ctas / (double)(waves * slots);
-        const double score = eff - 0.004 * s;
-        if (score > best_score + 1e-9) { best_score = score; best = s; }
+        if (eff > best_eff * 1.01) { best_eff = eff; best = s; }
     }
     return best;
 }
@@ -664,13 +659,14 @@ cudaError_t gemm_tn_f64acc(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, i
 }
 
 // Cholesky + inverse -------------------------------------------------------
+// fp64_factor: FP64 Cholesky (first CholeskyQR pass); else FP32 (second pass).
 template <typename T>
-cudaError_t chol_inv(Ctx& cx, const double* G, int bp, int p, double* R, T* Rinv) {
-    const size_t smem = sizeof(double) * (size_t)bp * bp;
-    const int use_smem = (smem <= 200 * 1024) ? 1 : 0;
+cudaError_t chol_inv(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, bool fp64_factor, double* scratch,
+                     size_t scratch_doubles) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_cholesky<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_cholesky<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_cholesky<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(k_tri_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
@@ -678,14 +674,62 @@ cudaError_t chol_inv(Ctx& cx, const double* G, int bp, int p, double* R, T* Rinv
     // of the panel itself leaves pivots of order u^2 (1e-32 for FP64 data,
     // 4e-15 for FP32 data); CholeskyQR2 with an FP64 Gram handles anything above
     const double tol = (sizeof(T) == 8) ? 1e-15 : 1e-14;
-    k_cholesky<512><<<1, 512, use_smem ? smem : 0, cx.stream>>>(G, bp, bp, p, R, use_smem, tol, cx.st);
+    const size_t sq = (size_t)bp * bp;
+    if (scratch_doubles < sq) return cudaErrorInvalidValue;
+    if (fp64_factor) {
+        const int in_smem = (sizeof(double) * sq <= 200 * 1024) ? 1 : 0;
+        k_cholesky<double><<<1, 256, in_smem ? sizeof(double) * sq : 0, cx.stream>>>(G, bp, p, R, in_smem, scratch,
+                                                                                     tol, cx.st);
+    } else {
+        const int in_smem = (sizeof(float) * sq <= 200 * 1024) ? 1 : 0;
+        k_cholesky<float><<<1, 256, in_smem ? sizeof(float) * sq : 0, cx.stream>>>(G, bp, p, R, in_smem, scratch,
+                                                                                   tol, cx.st);
+    }
     cx.launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // stage columns 0..c of R for c < smem_cols: (c + 1) * bp + bp doubles <= 200 KB
-    const int smem_cols = (int)std::min<int64_t>(bp, (200 * 1024 / 8) / bp - 1);
-    const size_t smem2 = sizeof(double) * (size_t)(bp + (int64_t)bp * std::max(smem_cols, 1));
-    k_tri_inverse<T><<<bp, 128, smem2, cx.stream>>>(R, bp, Rinv, smem_cols);
+    // stage columns 0..cmax of R when (cmax + 1) * bp + 5 bp doubles <= 200 KB
+    const int staged_cols = (int)std::min<int64_t>(bp, (200 * 1024 / 8) / bp - 5);
+    const int cmax_all = std::min(bp, staged_cols);
+    const size_t smem2 = sizeof(double) * (size_t)(5 * bp + (int64_t)bp * std::max(cmax_all, 1));
+    k_tri_inverse<T><<<(bp + 3) / 4, 128, smem2, cx.stream>>>(R, bp, Rinv, staged_cols);
+    cx.launches++;
+    return cudaGetLastError();
+}
+
+// Upper-triangular inverse of a kdim x kdim FP64 matrix (entries below the
+// diagonal are ignored), result in T.
+template <typename T>
+cudaError_t tri_inverse(Ctx& cx, const double* R, int kdim, T* Rinv) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_tri_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    const int staged_cols = (int)std::min<int64_t>(kdim, std::max<int64_t>(0, (200 * 1024 / 8) / kdim - 5));
+    const int cmax_all = std::min(kdim, staged_cols);
+    const size_t smem2 = sizeof(double) * (size_t)(5 * (int64_t)kdim + (int64_t)kdim * std::max(cmax_all, 1));
+    if (smem2 > 200 * 1024) return cudaErrorInvalidValue;
+    k_tri_inverse<T><<<(kdim + 3) / 4, 128, smem2, cx.stream>>>(R, kdim, Rinv, staged_cols);
+    cx.launches++;
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_to_double(int64_t rows, int64_t cols, const T* __restrict__ src, int64_t lds,
+                            double* __restrict__ dst, int64_t ldd) {
+    const int64_t total = rows * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e % rows, c = e / rows;
+        dst[r + c * ldd] = (double)src[r + c * lds];
+    }
+}
+
+template <typename T>
+cudaError_t launch_to_double(Ctx& cx, int64_t rows, int64_t cols, const T* src, int64_t lds, double* dst,
+                             int64_t ldd) {
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows * cols + 255) / 256, cx.num_sms * 4));
+    k_to_double<T><<<blocks, 256, 0, cx.stream>>>(rows, cols, src, lds, dst, ldd);
     cx.launches++;
     return cudaGetLastError();
 }
@@ -753,7 +797,7 @@ cudaError_t downdate_sketch(Ctx& cx, int64_t m, int64_t n, int p, int bp, const 
                                     int64_t, T*, size_t, double*, int, double*);                                 \
     template cudaError_t gemm_tn_f64acc<T>(Ctx&, int64_t, int, int64_t, const T*, int64_t, const T*, int64_t,    \
                                            double*, int64_t, double*, size_t, bool);                              \
-    template cudaError_t chol_inv<T>(Ctx&, const double*, int, int, double*, T*);                                 \
+    template cudaError_t chol_inv<T>(Ctx&, double*, int, int, double*, T*, bool, double*, size_t);               \
     template cudaError_t downdate_sketch<T>(Ctx&, int64_t, int64_t, int, int, const T*, int64_t, const T*,        \
                                             int64_t, const T*, int64_t, const T*, T*, int64_t, T*, int64_t, T*,   \
                                             size_t, double*, int, double*);                                       \
@@ -763,6 +807,10 @@ cudaError_t downdate_sketch(Ctx& cx, int64_t m, int64_t n, int p, int bp, const 
 
 RQB_INST(float)
 RQB_INST(double)
+template cudaError_t tri_inverse<float>(Ctx&, const double*, int, float*);
+template cudaError_t tri_inverse<double>(Ctx&, const double*, int, double*);
+template cudaError_t launch_to_double<float>(Ctx&, int64_t, int64_t, const float*, int64_t, double*, int64_t);
+template cudaError_t launch_to_double<double>(Ctx&, int64_t, int64_t, const double*, int64_t, double*, int64_t);
 #undef RQB_INST
 
 }  // namespace rqb

@@ -86,6 +86,9 @@ def lib() -> ctypes.CDLL:
             "rqb_project": [P, P, i64, i64, i64, P, i64, i64, P, i64, Pd],
             "rqb_downdate_sketch": [P, P, i64, P, i64, P, i64, i64, i64, i64, P, i64, i64, i64, u64, P, i64, Pd],
             "rqb_sketch_noalloc": [ctypes.c_int32, P, i64, i64, i64, i64, i64, u64, P, i64, Pd, P],
+            "rqb_reconstruct": [P, P, i64],
+            "rqb_factor_batched": [P, i64, P, P, P, P, P, i64, u64, P, P, P, P, P, P],
+            "rqb_backward": [P, P, i64, P, i64],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -221,6 +224,39 @@ class Handle:
         _check(rc, "rqb_factor_host", ok=(RQB_OK, RQB_NOT_CONVERGED))
         return int(k.value), rc
 
+    def rqb_reconstruct(self, m: int, n: int) -> torch.Tensor:
+        X = colmajor(torch.empty(n, m, dtype=self.out_dtype, device=self.device).t())
+        _check(lib().rqb_reconstruct(self._h, ctypes.c_void_p(X.data_ptr()), _ld(X)), "rqb_reconstruct")
+        return X
+
+    def rqb_backward(self, G: torch.Tensor) -> torch.Tensor:
+        m, n = G.shape
+        G = colmajor(G.to(self.out_dtype))
+        dA = colmajor(torch.empty(n, m, dtype=self.out_dtype, device=self.device).t())
+        _check(lib().rqb_backward(self._h, ctypes.c_void_p(G.data_ptr()), _ld(G), ctypes.c_void_p(dA.data_ptr()),
+                                  _ld(dA)), "rqb_backward")
+        return dA
+
+    def rqb_factor_batched(self, As: list, eps: list, b: int, seed: int = 0):
+        """As: column-major FP32 device matrices.  Returns [(Q view, B view, k, status)]."""
+        cnt = len(As)
+        Ap = (ctypes.c_void_p * cnt)(*[ctypes.c_void_p(a.data_ptr()) for a in As])
+        mm = (ctypes.c_int64 * cnt)(*[a.shape[0] for a in As])
+        nn = (ctypes.c_int64 * cnt)(*[a.shape[1] for a in As])
+        ld = (ctypes.c_int64 * cnt)(*[_ld(a) for a in As])
+        ee = (ctypes.c_double * cnt)(*[float(e) for e in eps])
+        Qp, Bp = (ctypes.c_void_p * cnt)(), (ctypes.c_void_p * cnt)()
+        lq, lb, kk = (ctypes.c_int64 * cnt)(), (ctypes.c_int64 * cnt)(), (ctypes.c_int64 * cnt)()
+        st = (ctypes.c_int * cnt)()
+        _check(lib().rqb_factor_batched(self._h, cnt, Ap, mm, nn, ld, ee, b, seed, Qp, lq, Bp, lb, kk, st),
+               "rqb_factor_batched")
+        out = []
+        for t in range(cnt):
+            k = int(kk[t])
+            out.append((_view(Qp[t] or 0, mm[t], k, int(lq[t]), torch.float32, self.device),
+                        _view(Bp[t] or 0, k, nn[t], int(lb[t]), torch.float32, self.device), k, int(st[t])))
+        return out
+
     def rqb_get_stats(self) -> Stats:
         st = rqb_stats()
         _check(lib().rqb_get_stats(self._h, ctypes.byref(st)), "rqb_get_stats")
@@ -291,3 +327,29 @@ def rqb_sketch_noalloc(A: torch.Tensor, col0: int, ncols: int, seed: int, Y: tor
                                   seed, ctypes.c_void_p(Y.data_ptr()), _ld(Y),
                                   ctypes.byref(nrm) if want_norm else None, ctypes.c_void_p(s.cuda_stream))
     return rc, (float(nrm.value) if want_norm else None)
+
+
+class QQtA(torch.autograd.Function):
+    """X = Q Q^T A with Q from fixed-rank randQB_b (k = max_rank, Omega from
+    `seed`); backward through rqb_backward.  Each call owns a handle, so
+    several nodes of one graph do not share factorization state."""
+
+    @staticmethod
+    def forward(ctx, A: torch.Tensor, k: int, b: int, seed: int):
+        A = colmajor(A.detach())
+        h = Handle(A.dtype, max_rank=k, fixed_rank=True)
+        h.rqb_factor(A, 0.0, b, seed)
+        X = h.rqb_reconstruct(*A.shape)
+        ctx.save_for_backward(A)
+        ctx.h = h
+        return X
+
+    @staticmethod
+    def backward(ctx, G: torch.Tensor):
+        dA = ctx.h.rqb_backward(G)
+        return dA, None, None, None
+
+
+def qqta(A: torch.Tensor, k: int, b: int, seed: int = 0) -> torch.Tensor:
+    """Differentiable fixed-rank approximation Q Q^T A (Omega held fixed)."""
+    return QQtA.apply(A, k, b, seed)

@@ -1,0 +1,86 @@
+"""rqb_factor_batched: many FP32 matrices of uneven sizes in one persistent launch.
+
+Each matrix is compared with the oracle (randQB_b, same seed, binary32 Omega):
+rank exact (or one block away inside the decision band), |r_gpu - r_orc| <=
+1e-5 ||A_t||_F, ||Q^T Q - I||_max <= 1e-5; a matrix with a NaN reports
+RQB_ERR_NONFINITE without affecting the others; results equal those of the
+single-matrix entry point on the same inputs (same rank, residuals within 1e-5).
+"""
+import numpy as np
+import pytest
+import torch
+
+import inputs
+from parity_util import check_rank, orth_err, resid, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(seed=0):
+    rng = np.random.default_rng(seed)
+    mats = []
+    shapes = [(900, 600, 40), (257, 129, 10), (513, 513, 25), (64, 300, 8), (5, 3, 2), (1000, 33, 30),
+              (777, 400, 60), (300, 299, 5), (128, 128, 12), (640, 480, 20), (33, 31, 15), (1500, 700, 50)]
+    for i, (m, n, r) in enumerate(shapes):
+        s = inputs.spectrum_exp(min(m, n), r)
+        A = inputs.usv(m, n, s, seed=100 + i).astype(np.float32).astype(np.float64)
+        eps = (1e-3 if i % 2 == 0 else 1e-2) * np.linalg.norm(A)
+        mats.append((A, eps))
+    return mats
+
+
+@pytest.mark.parametrize("b", [32, 20])
+def test_batched_matches_oracle(orc, rqb_lib, b):
+    mats = _batch()
+    devs = [to_dev(A, torch.float32) for A, _ in mats]
+    with rqb_lib.Handle(torch.float32) as h:
+        out = h.rqb_factor_batched(devs, [e for _, e in mats], b, seed=9)
+        res = [(to_np(Q), to_np(B), k, st) for Q, B, k, st in out]
+    for (A, eps), (Q, B, k, st) in zip(mats, res):
+        ro = orc.randqb_b(A, eps, b, seed=9, omega_prec=32)
+        nA = np.linalg.norm(A)
+        assert st in (rqb_lib.RQB_OK, rqb_lib.RQB_NOT_CONVERGED), st
+        check_rank(k, ro, eps, b, rel_band=1e-3)
+        if k == ro.k:
+            assert abs(resid(A, Q, B) - resid(A, ro.Q, ro.B)) <= 1e-5 * nA
+        if st == rqb_lib.RQB_OK:
+            assert resid(A, Q, B) <= eps * (1 + 1e-4)
+        assert orth_err(Q) <= 1e-5
+
+
+def test_batched_equals_single(rqb_lib):
+    mats = _batch(seed=1)[:6]
+    devs = [to_dev(A, torch.float32) for A, _ in mats]
+    with rqb_lib.Handle(torch.float32) as h:
+        out = h.rqb_factor_batched(devs, [e for _, e in mats], 32, seed=4)
+        res = [(to_np(Q), to_np(B), k, st) for Q, B, k, st in out]
+    with rqb_lib.Handle(torch.float32) as h1:
+        for (A, eps), d, (Q, B, k, st) in zip(mats, devs, res):
+            Q1, B1, k1, rc1 = h1.rqb_factor(d, eps, 32, 4, check=False)
+            assert k1 == k and rc1 == st
+            assert abs(resid(A, Q, B) - resid(A, to_np(Q1), to_np(B1))) <= 1e-5 * np.linalg.norm(A)
+
+
+def test_batched_nonfinite_isolated(rqb_lib):
+    mats = _batch(seed=2)[:4]
+    A_bad = mats[1][0].copy()
+    A_bad[3, 2] = np.nan
+    mats[1] = (A_bad, mats[1][1])
+    devs = [to_dev(A, torch.float32) for A, _ in mats]
+    with rqb_lib.Handle(torch.float32) as h:
+        out = h.rqb_factor_batched(devs, [e for _, e in mats], 32, seed=4)
+    sts = [st for _, _, _, st in out]
+    assert sts[1] == rqb_lib.RQB_ERR_NONFINITE
+    assert all(s == rqb_lib.RQB_OK for i, s in enumerate(sts) if i != 1)
+
+
+def test_batched_rejects_bad_arguments(rqb_lib):
+    with rqb_lib.Handle(torch.float64) as h:
+        A = to_dev(np.ones((8, 4)), torch.float64)
+        with pytest.raises(rqb_lib.RqbError) as e:
+            h.rqb_factor_batched([A], [1.0], 4)
+        assert e.value.status == rqb_lib.RQB_ERR_UNSUPPORTED
+    with rqb_lib.Handle(torch.float32) as h:
+        A = to_dev(np.ones((8, 4)), torch.float32)
+        with pytest.raises(rqb_lib.RqbError):
+            h.rqb_factor_batched([A], [1.0], 33)

@@ -188,3 +188,41 @@ def test_host_entry_point(orc, rqb_lib):
     assert rc == rqb_lib.RQB_OK and k == ro.k
     Q, B = Qh[:, :k].numpy(), Bh[:k, :].numpy()
     assert abs(resid(A, Q, B) - resid(A, ro.Q, ro.B)) <= 1e-10 * resid(A, ro.Q, ro.B)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("P", [1, 2])
+def test_power_scheme_fixed_rank(orc, rqb_lib, dtype, P):
+    """randQB_pb (Fig. randQB_pb) at fixed rank on the Matrix 2 spectrum (slow decay)."""
+    m, n, b, k = 700, 500, 32, 96
+    s = (1.0 + 200.0 * np.arange(n)) ** -0.5
+    A = inputs.usv(m, n, s, seed=77)
+    if dtype == torch.float32:
+        A = A.astype(np.float32).astype(np.float64)
+    prec = 64 if dtype == torch.float64 else 32
+    ro = orc.randqb_b(A, 0.0, b, seed=3, max_rank=k, fixed_rank=True, power=P, omega_prec=prec)
+    Q, B, kk, rc, st = _factor(rqb_lib, A, 0.0, b, dtype, seed=3, max_rank=k, fixed_rank=True, power=P)
+    assert rc == rqb_lib.RQB_OK and kk == k == ro.k
+    nA = np.linalg.norm(A)
+    if dtype == torch.float64:
+        assert abs(resid(A, Q, B) - resid(A, ro.Q, ro.B)) <= 1e-10 * resid(A, ro.Q, ro.B)
+        assert orth_err(Q) <= 1e-12
+        assert np.abs(Q - ro.Q).max() <= 1e-8
+    else:
+        assert abs(resid(A, Q, B) - resid(A, ro.Q, ro.B)) <= 1e-5 * nA
+        assert orth_err(Q) <= 1e-5
+    # the power scheme beats P = 0 at the same rank (Sec. 5.1)
+    r0 = orc.randqb_b(A, 0.0, b, seed=3, max_rank=k, fixed_rank=True, power=0, omega_prec=prec)
+    assert resid(A, Q, B) < resid(A, r0.Q, r0.B)
+
+
+def test_power_scheme_adaptive(orc, rqb_lib):
+    m, n, b = 900, 600, 40
+    s = inputs.spectrum_poly(n)
+    A = inputs.usv(m, n, s, seed=78)
+    eps = 5e-3 * np.linalg.norm(A)
+    ro = orc.randqb_b(A, eps, b, seed=1, power=1)
+    Q, B, k, rc, st = _factor(rqb_lib, A, eps, b, torch.float64, seed=1, power=1)
+    assert rc == rqb_lib.RQB_OK
+    check_rank(k, ro, eps, b, rel_band=1e-6)
+    assert abs(resid(A, Q, B) - resid(A, ro.Q, ro.B)) <= 1e-10 * resid(A, ro.Q, ro.B)

@@ -9,7 +9,9 @@ arrays are numpy float64, column-major (Fortran order).
 Functions and the passages they follow:
   philox4x32_10  -- the counter-based generator of Salmon et al. (SC'11)
   omega          -- Fig. randQB_b line (2), Omega_i = randn(n, b), indexed by
-                    global column so that blocks slice one Omega (eq. OmegaBlock)
+                    global column so that blocks slice one Omega (eq. OmegaBlock);
+                    prec 64, 32 or 19 (binary32 draw rounded to TF32)
+  round_tf32     -- rounding to 11 significant bits, ties away from zero
   orth           -- Sec. 2.4, unpivoted Householder QR with diag(R) >= 0
   sketch         -- Fig. randQB_b line (3), A Omega_i
   orth_reproject -- Fig. randQB_b lines (3) and (3')
@@ -53,6 +55,8 @@ def _lib():
         lib.orc_num_threads.restype = i32
         lib.orc_qqta_adjoint.argtypes = [P, i64, i64, i64, P, i64, P, i64, i64, u64, i32, P, i64, P, i64]
         lib.orc_qqta_adjoint.restype = i32
+        lib.orc_round_tf32.argtypes = [dbl]
+        lib.orc_round_tf32.restype = dbl
         _LIB = lib
     return _LIB
 
@@ -81,6 +85,10 @@ def philox4x32_10(ctr, key):
     out = np.zeros(4, dtype=np.uint32)
     _lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
     return out
+
+
+def round_tf32(x: float) -> float:
+    return float(_lib().orc_round_tf32(float(x)))
 
 
 def omega(seed: int, n: int, col0: int, ncols: int, prec: int = 64, stream: int = 0):

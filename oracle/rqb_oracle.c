@@ -67,20 +67,33 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
  * uniforms u1, u2 in (0, 1); Box-Muller turns them into the pair
  * sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2), of which column c takes the first
  * entry when c is even and the second when c is odd. */
+/* Round x to 11 significant bits (the TF32 format: 10 fraction bits), to
+ * nearest with ties away from zero: with x = f 2^e, 1/2 <= |f| < 1, the
+ * result is round(f 2^11) 2^(e - 11).  Exact in binary64. */
+double orc_round_tf32(double x) {
+    if (x == 0.0 || !isfinite(x)) return x;
+    int e;
+    double f = frexp(x, &e);
+    double s = ldexp(fabs(f), 11);
+    double r = floor(s + 0.5);
+    return ldexp(f < 0 ? -r : r, e - 11);
+}
+
 static double orc_omega_entry(uint64_t seed, uint32_t stream, int64_t r, int64_t c, int prec) {
     const double PI = 3.14159265358979323846;
     uint32_t ctr[4] = {(uint32_t)r, (uint32_t)(c >> 1), stream, 0u};
     uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
     uint32_t x[4];
     orc_philox4x32_10(ctr, key, x);
-    if (prec == 32) {
-        /* binary32 evaluation: 23-bit uniforms (j + 1/2) 2^-23, exact in float */
+    if (prec == 32 || prec == 19) {
+        /* binary32 evaluation: 23-bit uniforms (j + 1/2) 2^-23, exact in float;
+         * prec 19 then rounds the binary32 value to TF32 */
         float u1 = ((float)(x[0] >> 9) + 0.5f) * 0x1p-23f;
         float u2 = ((float)(x[2] >> 9) + 0.5f) * 0x1p-23f;
         double rad = sqrt(-2.0 * log((double)u1));
         double ang = 2.0 * PI * (double)u2;
         double z = (c & 1) ? rad * sin(ang) : rad * cos(ang);
-        return (double)(float)z;
+        return prec == 19 ? orc_round_tf32((double)(float)z) : (double)(float)z;
     }
     /* binary64: 53-bit uniforms ((x0 >> 5) 2^26 + (x1 >> 6) + 1/2) 2^-53 */
     double u1 = ((double)(x[0] >> 5) * 67108864.0 + (double)(x[1] >> 6) + 0.5) * 0x1p-53;

@@ -27,13 +27,19 @@ extern "C" {
  * definition.  ctr: 4 words, key: 2 words, out: 4 words. */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
+/* x rounded to 11 significant bits (TF32: 10 fraction bits), to nearest,
+ * ties away from zero. */
+double orc_round_tf32(double x);
+
 /* Gaussian test matrix Omega (Fig. randQB_b, line (2): Omega_i = randn(n, b)).
  * Writes the n x ncols block whose first column is global column col0 of the
  * infinite Gaussian matrix defined by (seed, stream).  Entry (r, c) depends
  * only on (seed, stream, r, c), so a block is a slice of one fixed Omega as in
  * eq. (OmegaBlock).  prec = 64: Box-Muller in binary64 from 53-bit uniforms.
  * prec = 32: the binary32 evaluation (23-bit uniforms, result rounded to
- * float, returned widened to double).  out is n x ncols, leading dim ldo. */
+ * float, returned widened to double).  prec = 19: the prec-32 value rounded
+ * to TF32 by orc_round_tf32, so that a tensor-core product with Omega as an
+ * operand is exact.  out is n x ncols, leading dim ldo. */
 void orc_omega(uint64_t seed, uint32_t stream, int64_t n, int64_t col0,
                int64_t ncols, int prec, double* out, int64_t ldo);
 
@@ -66,7 +72,7 @@ typedef struct {
  *   power  P of randQB_pb (0 gives randQB_b)
  *   skip_inner_orth  nonzero: the Sec. 5.4 variant that applies the powers
  *          without the intermediate orth() calls
- *   omega_prec  64 or 32, see orc_omega
+ *   omega_prec  64, 32 or 19, see orc_omega
  *   Q      m x max_rank output, leading dim ldq
  *   B      max_rank x n output, leading dim ldb
  * Returns 0 on success, -1 on invalid arguments. */

@@ -72,7 +72,7 @@ def test_philox_bits_uniform_and_avalanche(orc):
     assert abs(np.mean(flips) - 64.0) < 2.0
 
 
-@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("prec", [64, 32, 19])
 def test_omega_gaussian_moments_and_ks(orc, prec):
     from scipy import stats
     Om = orc.omega(seed=12345, n=4000, col0=0, ncols=256, prec=prec)
@@ -90,7 +90,7 @@ def test_omega_gaussian_moments_and_ks(orc, prec):
     assert abs(c) < 5 / np.sqrt(N)
 
 
-@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("prec", [64, 32, 19])
 def test_omega_blocks_slice_one_matrix(orc, prec):
     full = orc.omega(seed=99, n=300, col0=0, ncols=37, prec=prec)
     for c0, w in [(0, 5), (5, 3), (7, 12), (19, 18), (36, 1)]:
@@ -110,3 +110,33 @@ def test_omega_fp32_is_fp32_evaluation_of_same_draw(orc):
     diff = np.abs(a - b)
     assert np.median(diff / np.maximum(np.abs(a), 1e-3)) < 1e-6
     assert np.quantile(diff, 0.999) < 2e-5
+
+
+def test_round_tf32_closed_forms(orc):
+    """11 significant bits, nearest, ties away from zero (cases fixed by the format)."""
+    r = orc.round_tf32
+    u = 2.0 ** -10                       # TF32 spacing on [1, 2)
+    assert r(1.0) == 1.0 and r(0.0) == 0.0 and r(-3.0) == -3.0
+    assert r(1.0 + u / 2) == 1.0 + u     # tie -> away from zero
+    assert r(-(1.0 + u / 2)) == -(1.0 + u)
+    assert r(1.0 + 3 * u / 2) == 1.0 + 2 * u
+    assert r(1.0 + u / 4) == 1.0 and r(1.0 + 3 * u / 4) == 1.0 + u
+    assert r(2.0 - u / 4) == 2.0         # carry into the next binade
+    assert r(0.75 * 2.0 ** -30) == 0.75 * 2.0 ** -30
+    x = (1.0 + 5 * u + u / 2) * 2.0 ** 40
+    assert r(x) == (1.0 + 6 * u) * 2.0 ** 40
+
+
+def test_omega_tf32_is_rounded_fp32_draw(orc):
+    """prec 19 = the binary32 draw rounded to 11 significant bits: every value is
+    representable in TF32 and within half a TF32 ulp of the binary32 value."""
+    a = orc.omega(seed=5, n=2000, col0=0, ncols=64, prec=32)
+    b = orc.omega(seed=5, n=2000, col0=0, ncols=64, prec=19)
+    nz = a != 0
+    e = np.floor(np.log2(np.abs(a[nz]))) + 1          # 2^(e-1) <= |a| < 2^e
+    assert np.all(np.abs(b[nz] - a[nz]) <= 2.0 ** (e - 12) * (1 + 1e-12))
+    scaled = b[nz] * 2.0 ** (11 - e)
+    ok = np.abs(scaled - np.round(scaled)) == 0
+    # values rounded up to 2^e carry one binade; they are powers of two
+    assert np.all(ok | (np.abs(b[nz]) == 2.0 ** e))
+    assert np.mean(b != a) > 0.99

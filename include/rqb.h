@@ -197,7 +197,9 @@ int rqb_get_stats(rqb_handle h, rqb_stats* out);
  * ------------------------------------------------------------------------ */
 
 /* Omega block (line (2)): Omega (n x ncols, leading dim ldo >= n) receives
- * global columns col0 .. col0 + ncols - 1 of the Omega defined above. */
+ * global columns col0 .. col0 + ncols - 1 of the Omega defined above, in the
+ * form the handle's products use (binary64, binary32, or for RQB_PREC_TF32X3
+ * the binary32 value rounded to TF32). */
 int rqb_omega(rqb_handle h, int64_t n, int64_t col0, int64_t ncols, uint64_t seed,
               void* Omega, int64_t ldo);
 

@@ -1,12 +1,15 @@
 // rqb_api.cu -- C ABI of the randQB_b library: handle, workspace, and the
-// block loop of Fig. randQB_b driving the SIMT kernels of rqb_kernels.cu.
+// block loop of Fig. randQB_b driving the SIMT kernels of rqb_kernels.cu and,
+// for RQB_PREC_TF32X3, the split-TF32 tensor-core products of rqb_tc.cu.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 
 #include "rqb_engine.h"
+#include "rqb_tc.h"
 
 using namespace rqb;
 
@@ -120,6 +123,7 @@ struct rqb_handle_s {
     uint64_t last_seed = 0;
     bool have_factor = false;
     DevBuf adj;                // workspace of rqb_backward
+    DevBuf tcbuf;              // operand copies and partials of the tensor-core products
     void* bat_out = nullptr;   // outputs of rqb_factor_batched
     size_t bat_out_bytes = 0;
     void* bat_work = nullptr;  // its descriptors and per-CTA scratch
@@ -204,6 +208,46 @@ int ensure_arena(rqb_handle h, int64_t m, int64_t n, int bp, int64_t kprev_max, 
     return RQB_OK;
 }
 
+// Workspace of the split-TF32 products: Omega_i in K-major order, the split
+// copies of Q_i and B_i, and the stream-K partial accumulators.
+struct TcArena {
+    float* Om;       // n x bp, ld ldom
+    int64_t ldom;
+    float* Qhi;      // m x bp, ld ldql
+    float* Qlo;
+    int64_t ldql;
+    float* Qt;       // m x bp row-major
+    float* Qtl;
+    float* Bs;       // bp x n, ld bp
+    float* Bsl;
+    float* part;
+    size_t part_cap;
+};
+
+int ensure_tc(rqb_handle h, int64_t m, int64_t n, int bp, TcArena* out) {
+    const int64_t ldom = round_up(n, 4), ldql = round_up(m, 4);
+    const size_t part = tc::partial_floats(m, n, bp, h->num_sms);
+    size_t off = 0;
+    auto take = [&](size_t floats) { size_t o = off; off = align256(off + 4 * floats); return o; };
+    const size_t oOm = take((size_t)ldom * bp);
+    const size_t oQh = take((size_t)ldql * bp), oQl = take((size_t)ldql * bp);
+    const size_t oQt = take((size_t)m * bp), oQtl = take((size_t)m * bp);
+    const size_t oBs = take((size_t)n * bp), oBsl = take((size_t)n * bp);
+    const size_t oP = take(part);
+    int rc = h->tcbuf.ensure(off);
+    if (rc != RQB_OK) return rc;
+    char* base = reinterpret_cast<char*>(h->tcbuf.p);
+    auto at = [&](size_t o) { return reinterpret_cast<float*>(base + o); };
+    out->Om = at(oOm); out->ldom = ldom;
+    out->Qhi = at(oQh); out->Qlo = at(oQl); out->ldql = ldql;
+    out->Qt = at(oQt); out->Qtl = at(oQtl);
+    out->Bs = at(oBs); out->Bsl = at(oBsl);
+    out->part = at(oP); out->part_cap = part;
+    return RQB_OK;
+}
+
+bool tma_ok(const void* p, int64_t ld) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0 && ld % 4 == 0; }
+
 int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return RQB_OK;
     if (e == cudaErrorMemoryAllocation) return RQB_ERR_OOM;
@@ -220,6 +264,8 @@ int cuda_status(cudaError_t e) {
 template <typename T> double band_rel();
 template <> double band_rel<double>() { return 64.0 * 1.1102230246251565e-16; }
 template <> double band_rel<float>() { return 32.0 * 5.9604644775390625e-08; }
+// split-TF32 products keep about 21 bits per term: 4 * 2^-20
+constexpr double kBandTf32x3 = 3.814697265625e-06;
 
 // Read the device state (synchronises the stream).
 int read_state(rqb_handle h, const Scal& sc) {
@@ -306,9 +352,136 @@ int power_panel(rqb_handle h, Ctx& cx, const Arena<T>& ar, int64_t m, int64_t n,
     return orth_reproject<T>(h, cx, ar, ar.Qt, m, m, p, bp, Qbar, kprev, ldqb, Qi, ldqb);
 }
 
+// Fig. randQB_b with the split-TF32 products (RQB_PREC_TF32X3, FP32 data):
+// line (3) sketch and line (4) projection stream-K on tcgen05, line (5) the
+// tensor-core update W <- W - Q_i B_i, then the next sketch of the updated
+// W; the panel of lines (3)/(3') and the stopping test as in factor_impl.
+int factor_tc(rqb_handle h, const float* A, int64_t m, int64_t n, int64_t lda, double eps, int64_t b, uint64_t seed,
+              int64_t* k_out) {
+    const int64_t rmax = std::min(m, n);
+    const int64_t kcap = (h->cfg.max_rank > 0 && h->cfg.max_rank < rmax) ? h->cfg.max_rank : rmax;
+    const int bp = pad_block(b);
+    const int fixed = h->cfg.fixed_rank ? 1 : 0;
+    Arena<float> ar;
+    int rc = ensure_arena<float>(h, m, n, bp, kcap, &ar);
+    if (rc != RQB_OK) return rc;
+    TcArena ta;
+    rc = ensure_tc(h, m, n, bp, &ta);
+    if (rc != RQB_OK) return rc;
+    const int64_t ldq = round_up(m, 4), ldb = round_up(kcap, 4), ldw = round_up(m, 4);
+    if ((rc = h->q.ensure(sizeof(float) * (size_t)ldq * (size_t)kcap)) != RQB_OK) return rc;
+    if ((rc = h->b.ensure(sizeof(float) * (size_t)ldb * (size_t)n)) != RQB_OK) return rc;
+    if ((rc = h->w.ensure(sizeof(float) * (size_t)ldw * (size_t)n)) != RQB_OK) return rc;
+    h->ldq = ldq;
+    h->ldb = ldb;
+    h->ldw = ldw;
+    h->kcap_alloc = kcap;
+    float* Q = reinterpret_cast<float*>(h->q.p);
+    float* B = reinterpret_cast<float*>(h->b.p);
+    float* W = reinterpret_cast<float*>(h->w.p);
+
+    Scal sc = scalars(h);
+    Ctx cx;
+    cx.stream = h->stream;
+    cx.num_sms = h->num_sms;
+    cx.st = sc.st;
+    RQB_CK(cudaMemsetAsync(sc.st, 0, sizeof(DevState), h->stream));
+
+    const double eps2 = eps * eps;
+    int64_t k = 0;
+    int blocks = 0, direct = 0;
+    int status = RQB_OK;
+    bool converged = false;
+
+    // A as the first W: read in place when TMA can address it, else copied
+    const float* Wsrc = A;
+    int64_t ldws = lda;
+    h->timer.begin(h->stream, RQB_PHASE_SKETCH);
+    if (!tma_ok(A, lda)) {
+        RQB_CK(cudaMemcpy2DAsync(W, sizeof(float) * ldw, A, sizeof(float) * lda, sizeof(float) * m, n,
+                                 cudaMemcpyDeviceToDevice, h->stream));
+        Wsrc = W;
+        ldws = ldw;
+    }
+    int p = (int)std::min<int64_t>(b, kcap);
+    RQB_CK(launch_sumsq<float>(cx, m, n, Wsrc, ldws, sc.nrm, kNrmCap, sc.s + 0));
+    RQB_CK(launch_set_norm(cx, sc.s + 0));
+    RQB_CK(tc::omega(cx, n, 0, p, bp, seed, ta.Om, ta.ldom));
+    RQB_CK(tc::sketch(cx, Wsrc, ldws, m, n, ta.Om, ta.ldom, bp, ar.Y, m, ta.part, ta.part_cap));
+    h->timer.end(h->stream);
+
+    for (;;) {
+        p = (int)std::min<int64_t>(b, kcap - k);
+        float* Qi = Q + k * ldq;
+        float* Bi = B + k;
+        h->timer.begin(h->stream, RQB_PHASE_ORTH);
+        rc = (h->cfg.power == 0) ? orth_reproject<float>(h, cx, ar, ar.Y, m, m, p, bp, Q, k, ldq, Qi, ldq)
+                                 : power_panel<float>(h, cx, ar, m, n, p, bp, Wsrc, ldws, Q, k, ldq, Qi);
+        if (rc != RQB_OK) return rc;
+        RQB_CK(tc::split_q(cx, Qi, ldq, m, p, bp, ta.Qhi, ta.Qlo, ta.ldql, ta.Qt, ta.Qtl));
+        h->timer.end(h->stream);
+        h->timer.begin(h->stream, RQB_PHASE_PROJECT);
+        RQB_CK(tc::project(cx, Wsrc, ldws, m, n, ta.Qhi, ta.Qlo, ta.ldql, p, bp, Bi, ldb, ta.Bs, ta.Bsl, ta.part,
+                           ta.part_cap, sc.nrm, kNrmCap, sc.s + 1));
+        h->timer.end(h->stream);
+        h->timer.begin(h->stream, RQB_PHASE_CONTROL);
+        RQB_CK(launch_stop_after_b(cx, sc.s + 1, eps2, kBandTf32x3, fixed));
+        h->timer.end(h->stream);
+        int err = read_state(h, sc);
+        if (err != RQB_OK) { status = err; break; }
+        const int flag = h->hstate->flag;
+        if (blocks < RQB_MAX_TRACKED_BLOCKS) {
+            h->stats.E[blocks] = h->hstate->E;
+            h->stats.D[blocks] = -1.0;
+        }
+        k += p;
+        blocks++;
+        if (flag == kStop) { converged = true; break; }
+        if (flag == kContinue && k >= kcap) break;
+        const int pn = (int)std::min<int64_t>(b, std::max<int64_t>(kcap - k, 0));
+        // line (5) with ||A^(i)||_F^2 on the same pass; the split-TF32 products
+        // carry a rounding of E far above eps^2 at small eps, so the stop is
+        // decided on the direct norm (line (6))
+        h->timer.begin(h->stream, RQB_PHASE_DOWNDATE);
+        RQB_CK(tc::update(cx, Wsrc, ldws, W, ldw, m, n, ta.Qt, ta.Qtl, ta.Bs, ta.Bsl, bp, sc.nrm, kNrmCap, sc.s + 2));
+        h->timer.end(h->stream);
+        Wsrc = W;
+        ldws = ldw;
+        RQB_CK(launch_stop_direct(cx, sc.s + 2, eps2, true));
+        err = read_state(h, sc);
+        if (err != RQB_OK) { status = err; break; }
+        if (flag == kAmbiguous) direct++;
+        if (blocks - 1 < RQB_MAX_TRACKED_BLOCKS) h->stats.D[blocks - 1] = h->hstate->D;
+        if (!fixed && h->hstate->flag == kStop) { converged = true; break; }
+        if (k >= kcap) break;
+        h->timer.begin(h->stream, RQB_PHASE_SKETCH);
+        RQB_CK(tc::omega(cx, n, k, pn, bp, seed, ta.Om, ta.ldom));
+        RQB_CK(tc::sketch(cx, W, ldw, m, n, ta.Om, ta.ldom, bp, ar.Y, m, ta.part, ta.part_cap));
+        h->timer.end(h->stream);
+    }
+    if (status == RQB_OK) {
+        int err = read_state(h, sc);
+        if (err != RQB_OK) status = err;
+    }
+    h->stats.k = k;
+    h->stats.blocks = blocks;
+    h->stats.direct_tests = direct;
+    h->stats.normA2 = h->hstate->normA2;
+    h->stats.eps = eps;
+    h->stats.kernel_launches = cx.launches;
+    *k_out = k;
+    if (status != RQB_OK) return status;
+    if (!fixed && !converged) return RQB_NOT_CONVERGED;
+    return RQB_OK;
+}
+
 template <typename T>
 int factor_impl(rqb_handle h, const T* A, int64_t m, int64_t n, int64_t lda, double eps, int64_t b, uint64_t seed,
                 int64_t* k_out) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (h->cfg.prec == RQB_PREC_TF32X3 && tc::shape_ok(m, n))
+            return factor_tc(h, A, m, n, lda, eps, b, seed, k_out);
+    }
     const int64_t rmax = std::min(m, n);
     const int64_t kcap = (h->cfg.max_rank > 0 && h->cfg.max_rank < rmax) ? h->cfg.max_rank : rmax;
     const int bp = pad_block(b);
@@ -482,7 +655,9 @@ int rqb_create(rqb_handle* out, const rqb_config* cfg) {
     if (cfg->dtype != RQB_F64 && cfg->dtype != RQB_F32 && cfg->dtype != RQB_BF16) return RQB_ERR_INVALID;
     if (cfg->prec != RQB_PREC_NATIVE && cfg->prec != RQB_PREC_TF32X3 && cfg->prec != RQB_PREC_BF16)
         return RQB_ERR_INVALID;
-    if (cfg->prec != RQB_PREC_NATIVE || cfg->dtype == RQB_BF16) return RQB_ERR_UNSUPPORTED;
+    if (cfg->dtype == RQB_BF16 || cfg->prec == RQB_PREC_BF16 ||
+        (cfg->prec == RQB_PREC_TF32X3 && cfg->dtype != RQB_F32))
+        return RQB_ERR_UNSUPPORTED;
     if (cfg->power > 8) return RQB_ERR_INVALID;
     rqb_handle h = new (std::nothrow) rqb_handle_s();
     if (!h) return RQB_ERR_OOM;
@@ -526,6 +701,7 @@ int rqb_destroy(rqb_handle h) {
     h->w.release();
     h->ahost.release();
     h->adj.release();
+    h->tcbuf.release();
     if (h->bat_out) cudaFree(h->bat_out);
     if (h->bat_work) cudaFree(h->bat_work);
     if (h->hstate) cudaFreeHost(h->hstate);
@@ -611,11 +787,13 @@ extern "C" int rqb_omega(rqb_handle h, int64_t n, int64_t col0, int64_t ncols, u
     Scal sc = scalars(h);
     Ctx cx;
     cx.stream = h->stream; cx.num_sms = h->num_sms; cx.st = sc.st;
-    cudaError_t e = (h->cfg.dtype == RQB_F64)
-                        ? launch_omega<double>(cx, n, col0, (int)ncols, (int)ncols, seed,
-                                               static_cast<double*>(Omega), 1, ldo)
-                        : launch_omega<float>(cx, n, col0, (int)ncols, (int)ncols, seed, static_cast<float*>(Omega),
-                                              1, ldo);
+    cudaError_t e;
+    if (h->cfg.dtype == RQB_F64)
+        e = launch_omega<double>(cx, n, col0, (int)ncols, (int)ncols, seed, static_cast<double*>(Omega), 1, ldo);
+    else if (h->cfg.prec == RQB_PREC_TF32X3)
+        e = tc::omega(cx, n, col0, (int)ncols, (int)ncols, seed, static_cast<float*>(Omega), ldo);
+    else
+        e = launch_omega<float>(cx, n, col0, (int)ncols, (int)ncols, seed, static_cast<float*>(Omega), 1, ldo);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     return finish(h, cuda_status(e));
 }
@@ -701,6 +879,99 @@ int dd_impl(rqb_handle h, const T* A, int64_t lda, const T* Qi, int64_t ldqi, co
     RQB_CK(cudaStreamSynchronize(h->stream));
     return RQB_OK;
 }
+// Step entry points of a TF32X3 handle.
+bool use_tc(const rqb_handle h, int64_t m, int64_t n) {
+    return h->cfg.dtype == RQB_F32 && h->cfg.prec == RQB_PREC_TF32X3 && tc::shape_ok(m, n);
+}
+
+// X itself when TMA can address it, else a copy in the handle's W buffer.
+int tma_source(rqb_handle h, const float* X, int64_t ldx, int64_t m, int64_t n, const float** out, int64_t* ldout) {
+    if (tma_ok(X, ldx)) {
+        *out = X;
+        *ldout = ldx;
+        return RQB_OK;
+    }
+    const int64_t ldw = round_up(m, 4);
+    int rc = h->w.ensure(sizeof(float) * (size_t)ldw * (size_t)n);
+    if (rc != RQB_OK) return rc;
+    RQB_CK(cudaMemcpy2DAsync(h->w.p, sizeof(float) * ldw, X, sizeof(float) * ldx, sizeof(float) * m, n,
+                             cudaMemcpyDeviceToDevice, h->stream));
+    *out = reinterpret_cast<const float*>(h->w.p);
+    *ldout = ldw;
+    return RQB_OK;
+}
+
+int sketch_tc(rqb_handle h, const float* A, int64_t m, int64_t n, int64_t lda, int64_t col0, int p, uint64_t seed,
+              float* Y, int64_t ldy, double* normA2) {
+    const int bp = pad_block(p);
+    Arena<float> ar;
+    TcArena ta;
+    int rc = ensure_arena<float>(h, m, n, bp, 1, &ar);
+    if (rc == RQB_OK) rc = ensure_tc(h, m, n, bp, &ta);
+    if (rc != RQB_OK) return rc;
+    Scal sc = scalars(h);
+    Ctx cx;
+    cx.stream = h->stream; cx.num_sms = h->num_sms; cx.st = sc.st;
+    RQB_CK(cudaMemsetAsync(sc.st, 0, sizeof(DevState), h->stream));
+    const float* X;
+    int64_t ldx;
+    if ((rc = tma_source(h, A, lda, m, n, &X, &ldx)) != RQB_OK) return rc;
+    if (normA2) RQB_CK(launch_sumsq<float>(cx, m, n, X, ldx, sc.nrm, kNrmCap, sc.s + 0));
+    RQB_CK(tc::omega(cx, n, col0, p, bp, seed, ta.Om, ta.ldom));
+    RQB_CK(tc::sketch(cx, X, ldx, m, n, ta.Om, ta.ldom, bp, ar.Y, m, ta.part, ta.part_cap));
+    RQB_CK(cudaMemcpy2DAsync(Y, sizeof(float) * ldy, ar.Y, sizeof(float) * m, sizeof(float) * m, p,
+                             cudaMemcpyDeviceToDevice, h->stream));
+    if (normA2) RQB_CK(cudaMemcpyAsync(normA2, sc.s + 0, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return read_state(h, sc);
+}
+
+int project_tc(rqb_handle h, const float* Qi, int64_t m, int p, int64_t ldqi, const float* A, int64_t n, int64_t lda,
+               float* Bi, int64_t ldbi, double* normB2) {
+    const int bp = pad_block(p);
+    TcArena ta;
+    int rc = ensure_tc(h, m, n, bp, &ta);
+    if (rc != RQB_OK) return rc;
+    Scal sc = scalars(h);
+    Ctx cx;
+    cx.stream = h->stream; cx.num_sms = h->num_sms; cx.st = sc.st;
+    RQB_CK(cudaMemsetAsync(sc.st, 0, sizeof(DevState), h->stream));
+    const float* X;
+    int64_t ldx;
+    if ((rc = tma_source(h, A, lda, m, n, &X, &ldx)) != RQB_OK) return rc;
+    RQB_CK(tc::split_q(cx, Qi, ldqi, m, p, bp, ta.Qhi, ta.Qlo, ta.ldql, ta.Qt, ta.Qtl));
+    RQB_CK(tc::project(cx, X, ldx, m, n, ta.Qhi, ta.Qlo, ta.ldql, p, bp, Bi, ldbi, ta.Bs, ta.Bsl, ta.part,
+                       ta.part_cap, sc.nrm, kNrmCap, sc.s + 1));
+    if (normB2) RQB_CK(cudaMemcpyAsync(normB2, sc.s + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return read_state(h, sc);
+}
+
+int dd_tc(rqb_handle h, const float* A, int64_t lda, const float* Qi, int64_t ldqi, const float* Bi, int64_t ldbi,
+          int64_t m, int64_t n, int p, float* W, int64_t ldw, int64_t col0, int ncols, uint64_t seed, float* Y,
+          int64_t ldy, double* normW2) {
+    const int bpu = pad_block(p), bps = pad_block(ncols);
+    Arena<float> ar;
+    TcArena ta;
+    int rc = ensure_arena<float>(h, m, n, bps, 1, &ar);
+    if (rc == RQB_OK) rc = ensure_tc(h, m, n, std::max(bpu, bps), &ta);
+    if (rc != RQB_OK) return rc;
+    Scal sc = scalars(h);
+    Ctx cx;
+    cx.stream = h->stream; cx.num_sms = h->num_sms; cx.st = sc.st;
+    RQB_CK(cudaMemsetAsync(sc.st, 0, sizeof(DevState), h->stream));
+    RQB_CK(tc::split_q(cx, Qi, ldqi, m, p, bpu, ta.Qhi, ta.Qlo, ta.ldql, ta.Qt, ta.Qtl));
+    RQB_CK(tc::stage_b(cx, Bi, ldbi, p, n, bpu, ta.Bs, ta.Bsl));
+    RQB_CK(tc::update(cx, A, lda, W, ldw, m, n, ta.Qt, ta.Qtl, ta.Bs, ta.Bsl, bpu, sc.nrm, kNrmCap,
+                      normW2 ? sc.s + 2 : nullptr));
+    const float* X;
+    int64_t ldx;
+    if ((rc = tma_source(h, W, ldw, m, n, &X, &ldx)) != RQB_OK) return rc;
+    RQB_CK(tc::omega(cx, n, col0, ncols, bps, seed, ta.Om, ta.ldom));
+    RQB_CK(tc::sketch(cx, X, ldx, m, n, ta.Om, ta.ldom, bps, ar.Y, m, ta.part, ta.part_cap));
+    RQB_CK(cudaMemcpy2DAsync(Y, sizeof(float) * ldy, ar.Y, sizeof(float) * m, sizeof(float) * m, ncols,
+                             cudaMemcpyDeviceToDevice, h->stream));
+    if (normW2) RQB_CK(cudaMemcpyAsync(normW2, sc.s + 2, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return read_state(h, sc);
+}
 }  // namespace
 
 extern "C" {
@@ -712,6 +983,9 @@ int rqb_sketch(rqb_handle h, const void* A, int64_t m, int64_t n, int64_t lda, i
         (h->cfg.dtype == RQB_F64 && ncols > 128))
         return finish(h, RQB_ERR_INVALID);
     if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
+    if (use_tc(h, m, n))
+        return finish(h, sketch_tc(h, static_cast<const float*>(A), m, n, lda, col0, (int)ncols, seed,
+                                   static_cast<float*>(Y), ldy, normA2));
     int rc = (h->cfg.dtype == RQB_F64)
                  ? sketch_impl<double>(h, static_cast<const double*>(A), m, n, lda, col0, (int)ncols, seed,
                                        static_cast<double*>(Y), ldy, normA2)
@@ -742,6 +1016,9 @@ int rqb_project(rqb_handle h, const void* Qi, int64_t m, int64_t p, int64_t ldqi
         p > max_block(h))
         return finish(h, RQB_ERR_INVALID);
     if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
+    if (use_tc(h, m, n))
+        return finish(h, project_tc(h, static_cast<const float*>(Qi), m, (int)p, ldqi, static_cast<const float*>(A),
+                                    n, lda, static_cast<float*>(Bi), ldbi, normB2));
     int rc = (h->cfg.dtype == RQB_F64)
                  ? project_impl<double>(h, static_cast<const double*>(Qi), m, (int)p, ldqi,
                                         static_cast<const double*>(A), n, lda, static_cast<double*>(Bi), ldbi, normB2)
@@ -760,6 +1037,10 @@ int rqb_downdate_sketch(rqb_handle h, const void* A, int64_t lda, const void* Qi
         (A == W && lda != ldw))
         return finish(h, RQB_ERR_INVALID);
     if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
+    if (use_tc(h, m, n))
+        return finish(h, dd_tc(h, static_cast<const float*>(A), lda, static_cast<const float*>(Qi), ldqi,
+                               static_cast<const float*>(Bi), ldbi, m, n, (int)p, static_cast<float*>(W), ldw, col0,
+                               (int)ncols, seed, static_cast<float*>(Y), ldy, normW2));
     int rc = (h->cfg.dtype == RQB_F64)
                  ? dd_impl<double>(h, static_cast<const double*>(A), lda, static_cast<const double*>(Qi), ldqi,
                                    static_cast<const double*>(Bi), ldbi, m, n, (int)p, static_cast<double*>(W), ldw,

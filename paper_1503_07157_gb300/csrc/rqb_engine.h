@@ -76,6 +76,6 @@ cudaError_t launch_to_double(Ctx& cx, int64_t rows, int64_t cols, const T* src, 
                              int64_t ldd);
 cudaError_t launch_set_norm(Ctx& cx, const double* nrm);
 cudaError_t launch_stop_after_b(Ctx& cx, const double* nb2, double eps2, double tau_rel, int fixed);
-cudaError_t launch_stop_direct(Ctx& cx, const double* d2, double eps2);
+cudaError_t launch_stop_direct(Ctx& cx, const double* d2, double eps2, bool always = false);
 
 }  // namespace rqb

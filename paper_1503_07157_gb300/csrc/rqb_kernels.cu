@@ -266,10 +266,12 @@ __global__ void k_stop_after_b(DevState* st, const double* nb2, double eps2, dou
     else st->flag = kAmbiguous;
 }
 
-__global__ void k_stop_direct(DevState* st, const double* d2, double eps2) {
+// always = 0: decide only when the downdate test was ambiguous; always = 1:
+// decide on the direct norm whenever the downdate test did not stop.
+__global__ void k_stop_direct(DevState* st, const double* d2, double eps2, int always) {
     const double d = *d2;
     st->D = d;
-    if (st->flag == kAmbiguous) st->flag = (d <= eps2) ? kStop : kContinue;
+    if (st->flag == kAmbiguous || (always && st->flag != kStop)) st->flag = (d <= eps2) ? kStop : kContinue;
 }
 
 cudaError_t launch_set_norm(Ctx& cx, const double* nrm) {
@@ -282,8 +284,8 @@ cudaError_t launch_stop_after_b(Ctx& cx, const double* nb2, double eps2, double 
     cx.launches++;
     return cudaGetLastError();
 }
-cudaError_t launch_stop_direct(Ctx& cx, const double* d2, double eps2) {
-    k_stop_direct<<<1, 1, 0, cx.stream>>>(cx.st, d2, eps2);
+cudaError_t launch_stop_direct(Ctx& cx, const double* d2, double eps2, bool always) {
+    k_stop_direct<<<1, 1, 0, cx.stream>>>(cx.st, d2, eps2, always ? 1 : 0);
     cx.launches++;
     return cudaGetLastError();
 }

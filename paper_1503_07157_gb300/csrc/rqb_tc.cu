@@ -1,0 +1,775 @@
+// rqb_tc.cu -- split-TF32 tensor-core kernels of randQB_b (RQB_PREC_TF32X3).
+//
+// The three products of a block of Fig. randQB_b that touch all of A run on
+// tcgen05 with FP32 accumulators in TMEM, operands staged by TMA:
+//   sketch   Y = W Omega_i        line (3), Omega_i rounded to TF32 (exact),
+//                                 W split into hi + lo: 2 MMA passes
+//   project  B_i^T = W^T Q_i      line (4), W and Q_i split: 3 passes
+//   update   W <- W - Q_i B_i     line (5), Q_i and B_i split: 3 passes
+// A split FP32 value x = hi + lo has hi = x (the MMA reads its TF32 part)
+// and lo = rna_tf32(x - trunc_tf32(x)); the products hi*hi + hi*lo + lo*hi
+// keep about 21 bits of each term.  The panel (Gram, Cholesky, re-projection) and the
+// stopping test stay on the SIMT kernels with FP64 accumulation.
+//
+// Sketch and project reduce over a long K (n or m), so they run stream-K:
+// one CTA per SM walks a contiguous range of (tile, K-chunk) units, writes
+// one partial accumulator per tile segment it touches, and a second kernel
+// sums the partials of each tile in CTA order (deterministic).  The update
+// has K = b and walks whole output tiles.
+//
+// Warp roles in each CTA: warp 0 issues TMA loads, warp 1 owns TMEM and
+// issues the MMAs (one thread), the remaining warps split operands into the
+// MMA layout and drain accumulators.  Every wait is bounded (rqb_tc.cuh); on
+// expiry the CTA drains its copies and MMAs, frees TMEM and records
+// RQB_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "rqb_engine.h"
+#include "rqb_internal.cuh"
+#include "rqb_tc.cuh"
+#include "rqb_tc.h"
+
+namespace rqb {
+namespace tc {
+namespace {
+
+enum Role { kSketch = 0, kProject = 1 };
+
+struct StreamKParams {
+    CUtensorMap mx;    // W: sketch box {128 rows, 32 cols}, no swizzle; project box {32 rows, 128 cols}, SW128
+    CUtensorMap mw;    // Omega (sketch) or Q_i (project): box {32, np}, SW128
+    CUtensorMap mwl;   // lo part of Q_i (project)
+    float* part;       // P * G partial accumulators of 128 x np floats
+    DevState* st;
+    long long U;       // units = tiles * C
+    int C;             // K chunks per tile
+    int P;             // CTAs
+    int G;             // partial slots per CTA
+    int np;            // MMA N
+};
+
+struct UpdateParams {
+    CUtensorMap mqt, mqtl;  // Q_i^T row-major (bp x m as {bp, m}), box {32, 128}
+    CUtensorMap mbs, mbsl;  // B_i staged column-major (bp x n), box {32, NJ}
+    const float* Wsrc;
+    float* Wdst;
+    DevState* st;
+    double* sq_part;        // per-CTA ||W_dst||_F^2 partials (FP64), or null
+    long long ldws, ldwd, m, n;
+    int RT, CT, C;
+};
+
+__device__ __forceinline__ long long unit_begin(long long U, int P, int p) { return U * p / P; }
+
+// ---------------------------------------------------------------------------
+// Stream-K sketch / project.
+//
+// The tensor core accumulates in FP32 with a one-sided rounding, so a long
+// chain of MMAs into one accumulator drifts toward zero in proportion to its
+// length (measured: about 2^-25.5 of the value per MMA, 2e-6 after 96
+// MMAs).  The chain is therefore cut every kPeriod K-chunks (24 MMAs for the
+// projection, 16 for the sketch): the MMA
+// alternates between two TMEM accumulators, and the eight epilogue warps add
+// each finished period into FP32 running sums in registers (round to
+// nearest), which are written out at the end of a tile segment.
+constexpr int kPeriod = 2;
+
+template <int ROLE, int NP>
+struct StreamKCfg {
+    static constexpr int S = (ROLE == kProject && NP > 128) ? 2 : 3;   // TMA stages
+    static constexpr uint32_t kW = (uint32_t)NP * 128u;                 // Omega / Q tile bytes
+    static constexpr uint32_t kCv = ROLE == kSketch ? 2 * kTileBytes : kTileBytes;  // one conversion slot
+    static constexpr size_t kSmem =
+        (size_t)S * (kTileBytes + kW) + (ROLE == kProject ? (size_t)S * kW : 0) + 2 * (size_t)kCv + 1024;
+};
+
+template <int ROLE, int NP>
+__global__ void __launch_bounds__(320, 1) k_streamk(const __grid_constant__ StreamKParams p) {
+    using Cfg = StreamKCfg<ROLE, NP>;
+    constexpr int S = Cfg::S;
+    constexpr uint32_t kW = Cfg::kW;
+    constexpr int kHalf = NP / 2;          // accumulator columns per epilogue warp
+    __shared__ __align__(8) uint64_t full[S], empty[S], cvfull[2], cvempty[2], accfull[2], accempty[2], drain;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    extern __shared__ uint8_t dsm[];
+    uint8_t* base = dsm + (((smem_u32(dsm) + 1023u) & ~1023u) - smem_u32(dsm));
+    uint8_t* sX = base;
+    uint8_t* sW = sX + S * kTileBytes;
+    uint8_t* sWl = sW + S * kW;
+    uint8_t* sCv = (ROLE == kProject) ? sWl + S * kW : sWl;   // sketch: 2 x (hi, lo); project: 2 x lo
+    constexpr uint32_t ncols = 2u * (uint32_t)NP;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int* ab = &abort_flag;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&cvfull[s], 8); mbar_init(&cvempty[s], 1);
+            mbar_init(&accfull[s], 1); mbar_init(&accempty[s], 8);
+        }
+        mbar_init(&drain, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+        prefetch_map(&p.mx);
+        prefetch_map(&p.mw);
+        if (ROLE == kProject) prefetch_map(&p.mwl);
+    }
+    if (warp == 1) tmem_alloc(&tmem_base, ncols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const long long u0 = unit_begin(p.U, p.P, blockIdx.x), u1 = unit_begin(p.U, p.P, blockIdx.x + 1);
+    // unit u is chunk kc = u % C of tile u / C; a period ends at every kPeriod-th
+    // chunk of a tile, at the tile's last chunk and at the end of the CTA's range
+    auto seg_end = [&](long long u) { return u + 1 == u1 || (u + 1) % p.C == 0; };
+    auto period_end = [&](long long u) { return seg_end(u) || ((u % p.C) + 1) % kPeriod == 0; };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            long long q = 0;
+            for (long long u = u0; u < u1; ++u, ++q) {
+                const int s = (int)(q % S);
+                const uint32_t r = (uint32_t)(q / S);
+                if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1u, ab)) break;
+                const int t = (int)(u / p.C), kc = (int)(u % p.C);
+                if (ROLE == kSketch) {
+                    mbar_arrive_expect_tx(&full[s], kTileBytes + kW);
+                    tma_load_2d(sX + s * kTileBytes, &p.mx, t * kBM, kc * kKC, &full[s]);
+                    tma_load_2d(sW + s * kW, &p.mw, kc * kKC, 0, &full[s]);
+                } else {
+                    mbar_arrive_expect_tx(&full[s], kTileBytes + 2u * kW);
+                    tma_load_2d(sX + s * kTileBytes, &p.mx, kc * kKC, t * kBM, &full[s]);
+                    tma_load_2d(sW + s * kW, &p.mw, kc * kKC, 0, &full[s]);
+                    tma_load_2d(sWl + s * kW, &p.mwl, kc * kKC, 0, &full[s]);
+                }
+            }
+            // the last loads issued must land before the CTA's shared memory is released
+            for (long long qq = (q > S ? q - S : 0); qq < q; ++qq)
+                mbar_wait(&full[qq % S], (uint32_t)(qq / S) & 1u, ab, false);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_tf32(NP);
+            int g = 0;             // periods issued
+            bool first = true;     // next chunk starts a period
+            long long q = 0;
+            for (long long u = u0; u < u1; ++u, ++q) {
+                const int s = (int)(q % S), cs = (int)(q & 1);
+                const uint32_t r = (uint32_t)(q / S), cr = (uint32_t)(q >> 1);
+                if (!mbar_wait(&full[s], r & 1u, ab)) break;
+                if (!mbar_wait(&cvfull[cs], cr & 1u, ab)) break;
+                const int abuf = g & 1, use = g >> 1;
+                if (first && use > 0 && !mbar_wait(&accempty[abuf], (uint32_t)(use - 1) & 1u, ab)) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(abuf * NP);
+                if (ROLE == kSketch) {
+                    const uint32_t a0 = smem_u32(sCv + cs * Cfg::kCv), a1 = a0 + kTileBytes;
+                    const uint32_t b0 = smem_u32(sW + s * kW);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_tf32(d, desc_k_sw128(a0 + kk * 32), desc_k_sw128(b0 + kk * 32), idesc,
+                                 (first && kk == 0) ? 0u : 1u);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_tf32(d, desc_k_sw128(a1 + kk * 32), desc_k_sw128(b0 + kk * 32), idesc, 1u);
+                } else {
+                    const uint32_t a0 = smem_u32(sX + s * kTileBytes), a1 = smem_u32(sCv + cs * Cfg::kCv);
+                    const uint32_t b0 = smem_u32(sW + s * kW), b1 = smem_u32(sWl + s * kW);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_tf32(d, desc_k_sw128(a0 + kk * 32), desc_k_sw128(b0 + kk * 32), idesc,
+                                 (first && kk == 0) ? 0u : 1u);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_tf32(d, desc_k_sw128(a0 + kk * 32), desc_k_sw128(b1 + kk * 32), idesc, 1u);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_tf32(d, desc_k_sw128(a1 + kk * 32), desc_k_sw128(b0 + kk * 32), idesc, 1u);
+                }
+                mma_commit(&empty[s]);
+                mma_commit(&cvempty[cs]);
+                if (period_end(u)) {
+                    mma_commit(&accfull[abuf]);
+                    ++g;
+                    first = true;
+                } else {
+                    first = false;
+                }
+            }
+            // every MMA issued has completed before TMEM is released
+            mma_commit(&drain);
+            mbar_wait(&drain, 0, ab, false);
+        }
+    } else {
+        const int ct = threadIdx.x - 64;          // 0..255
+        const int e = warp - 2;                   // 0..7
+        const int quarter = warp & 3;             // TMEM lanes this warp may read
+        const int half = e >> 2;                  // accumulator columns [half NP/2, (half+1) NP/2)
+        const int row = quarter * 32 + lane;      // accumulator row held by this thread
+        float acc[kHalf];
+#pragma unroll
+        for (int i = 0; i < kHalf; ++i) acc[i] = 0.f;
+        int g = 0;
+        long long q = 0;
+        for (long long u = u0; u < u1; ++u, ++q) {
+            const int s = (int)(q % S), cs = (int)(q & 1);
+            const uint32_t r = (uint32_t)(q / S), cr = (uint32_t)(q >> 1);
+            bool ok = mbar_wait(&full[s], r & 1u, ab);
+            if (ok && cr > 0) ok = mbar_wait(&cvempty[cs], (cr - 1) & 1u, ab);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            if (ROLE == kSketch) {
+                // raw tile [32 cols][128 rows] -> K-major rows (hi, lo): thread ct
+                // converts columns [16 h, 16 h + 16) of row ct % 128, h = ct / 128
+                const int rr = ct & (kBM - 1), h = ct >> 7;
+                const float* raw = reinterpret_cast<const float*>(sX + s * kTileBytes);
+                float x[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) x[j] = raw[(16 * h + j) * kBM + rr];
+                uint8_t* hi = sCv + cs * Cfg::kCv;
+                uint8_t* lo = hi + kTileBytes;
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    const int c = 4 * h + c4;
+                    const uint32_t off = (uint32_t)rr * 128u + ((uint32_t)(c ^ (rr & 7)) << 4);
+                    *reinterpret_cast<float4*>(hi + off) =
+                        make_float4(x[4 * c4], x[4 * c4 + 1], x[4 * c4 + 2], x[4 * c4 + 3]);
+                    *reinterpret_cast<float4*>(lo + off) =
+                        make_float4(tf32_lo(x[4 * c4]), tf32_lo(x[4 * c4 + 1]), tf32_lo(x[4 * c4 + 2]),
+                                    tf32_lo(x[4 * c4 + 3]));
+                }
+            } else {
+                const float4* src = reinterpret_cast<const float4*>(sX + s * kTileBytes);
+                float4* dst = reinterpret_cast<float4*>(sCv + cs * Cfg::kCv);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float4 v = src[ct + 256 * i];
+                    dst[ct + 256 * i] = make_float4(tf32_lo(v.x), tf32_lo(v.y), tf32_lo(v.z), tf32_lo(v.w));
+                }
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&cvfull[cs]);
+            if (period_end(u)) {
+                const int abuf = g & 1, use = g >> 1;
+                const bool okw = mbar_wait(&accfull[abuf], (uint32_t)use & 1u, ab);
+                if (!__all_sync(0xffffffffu, okw)) break;
+                tc_fence_after();
+                const uint32_t tl =
+                    tmem + (uint32_t)(abuf * NP + half * kHalf) + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll
+                for (int c0 = 0; c0 < kHalf; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tl + (uint32_t)c0, v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) acc[c0 + i] += v[i];
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&accempty[abuf]);
+                ++g;
+                if (seg_end(u)) {
+                    const int seg = (int)(u / p.C - u0 / p.C);
+                    float* slot = p.part + ((size_t)blockIdx.x * p.G + seg) * (size_t)kBM * NP;
+                    if (ROLE == kSketch) {
+#pragma unroll
+                        for (int i = 0; i < kHalf; ++i) slot[(size_t)(half * kHalf + i) * kBM + row] = acc[i];
+                    } else {
+                        float4* d4 = reinterpret_cast<float4*>(slot + (size_t)row * NP + half * kHalf);
+#pragma unroll
+                        for (int i = 0; i < kHalf / 4; ++i)
+                            d4[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < kHalf; ++i) acc[i] = 0.f;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, ncols);
+    if (threadIdx.x == 0 && abort_flag) record_error(p.st, RQB_ERR_TIMEOUT);
+}
+
+// ---------------------------------------------------------------------------
+// Update W_dst = W_src - Q_i B_i on 128 x NJ output tiles, K = bp in chunks of
+// 32: D = Q_i^T-tile (M = rows) x B_i-tile (N = columns), three passes.
+// Warps 2..9 drain the accumulator: thread (quarter, lane) owns row
+// 32 quarter + lane, and the two warps of a quarter split the NJ columns.
+template <int NJ, int S>
+__global__ void __launch_bounds__(320, 1) k_update(const __grid_constant__ UpdateParams p) {
+    __shared__ __align__(8) uint64_t full[S], empty[S], accfull[2], accempty[2], drain;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ double red[8];
+    extern __shared__ uint8_t dsm[];
+    uint8_t* base = dsm + (((smem_u32(dsm) + 1023u) & ~1023u) - smem_u32(dsm));
+    constexpr uint32_t kB = (uint32_t)NJ * 128u;           // one B tile (NJ rows x 128 B)
+    constexpr uint32_t kStage = 2u * kTileBytes + 2u * kB;
+    constexpr uint32_t kCols = 2u * NJ;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int* ab = &abort_flag;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int s = 0; s < 2; ++s) { mbar_init(&accfull[s], 1); mbar_init(&accempty[s], 8); }
+        mbar_init(&drain, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+        prefetch_map(&p.mqt);
+        prefetch_map(&p.mqtl);
+        prefetch_map(&p.mbs);
+        prefetch_map(&p.mbsl);
+    }
+    if (warp == 1) tmem_alloc(&tmem_base, kCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const int T = p.RT * p.CT;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            long long q = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < T && !stop; t += gridDim.x) {
+                const int rt = t / p.CT, ctile = t % p.CT;
+                for (int kc = 0; kc < p.C; ++kc, ++q) {
+                    const int s = (int)(q % S);
+                    const uint32_t r = (uint32_t)(q / S);
+                    if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1u, ab)) { stop = true; break; }
+                    uint8_t* st = base + s * kStage;
+                    mbar_arrive_expect_tx(&full[s], kStage);
+                    tma_load_2d(st, &p.mqt, kc * kKC, rt * kBM, &full[s]);
+                    tma_load_2d(st + kTileBytes, &p.mqtl, kc * kKC, rt * kBM, &full[s]);
+                    tma_load_2d(st + 2 * kTileBytes, &p.mbs, kc * kKC, ctile * NJ, &full[s]);
+                    tma_load_2d(st + 2 * kTileBytes + kB, &p.mbsl, kc * kKC, ctile * NJ, &full[s]);
+                }
+            }
+            for (long long qq = (q > S ? q - S : 0); qq < q; ++qq)
+                mbar_wait(&full[qq % S], (uint32_t)(qq / S) & 1u, ab, false);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_tf32(NJ);
+            long long q = 0;
+            int g = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < T && !stop; t += gridDim.x, ++g) {
+                const int abuf = g & 1, use = g >> 1;
+                if (use > 0 && !mbar_wait(&accempty[abuf], (uint32_t)(use - 1) & 1u, ab)) break;
+                const uint32_t d = tmem + (uint32_t)(abuf * NJ);
+                for (int kc = 0; kc < p.C; ++kc, ++q) {
+                    const int s = (int)(q % S);
+                    const uint32_t r = (uint32_t)(q / S);
+                    if (!mbar_wait(&full[s], r & 1u, ab)) { stop = true; break; }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(base + s * kStage), a1 = a0 + kTileBytes;
+                    const uint32_t b0 = a0 + 2 * kTileBytes, b1 = b0 + kB;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_tf32(d, desc_k_sw128(a0 + kk * 32), desc_k_sw128(b0 + kk * 32), idesc,
+                                 (kc == 0 && kk == 0) ? 0u : 1u);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_tf32(d, desc_k_sw128(a0 + kk * 32), desc_k_sw128(b1 + kk * 32), idesc, 1u);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_tf32(d, desc_k_sw128(a1 + kk * 32), desc_k_sw128(b0 + kk * 32), idesc, 1u);
+                    mma_commit(&empty[s]);
+                }
+                if (stop) break;
+                mma_commit(&accfull[abuf]);
+            }
+            mma_commit(&drain);
+            mbar_wait(&drain, 0, ab, false);
+        }
+    } else {
+        const int e = warp - 2;               // 0..7
+        const int quarter = warp & 3;
+        const int half = e >> 2;
+        constexpr int kHalf = NJ / 2;
+        double sq = 0.0;   // ||W_dst||_F^2 of the elements this thread wrote
+        int g = 0;
+        for (int t = blockIdx.x; t < T; t += gridDim.x, ++g) {
+            const int abuf = g & 1, use = g >> 1;
+            const bool okw = mbar_wait(&accfull[abuf], (uint32_t)use & 1u, ab);
+            if (!__all_sync(0xffffffffu, okw)) break;
+            tc_fence_after();
+            const int rt = t / p.CT, ctile = t % p.CT;
+            const long long r = (long long)rt * kBM + quarter * 32 + lane;
+            const long long j0 = (long long)ctile * NJ + half * kHalf;
+            const bool rok = r < p.m;
+            const float* src = p.Wsrc + r;
+            float* dst = p.Wdst + r;
+            const uint32_t tl = tmem + (uint32_t)(abuf * NJ + half * kHalf) + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+            for (int c0 = 0; c0 < kHalf; c0 += 32) {
+                float w[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const long long j = j0 + c0 + i;
+                    w[i] = (rok && j < p.n) ? __ldcs(src + j * p.ldws) : 0.f;
+                }
+                float v0[16], v1[16];
+                tmem_ld16(tl + (uint32_t)c0, v0);
+                tmem_ld16(tl + (uint32_t)(c0 + 16), v1);
+                float sq32 = 0.f;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const long long j = j0 + c0 + i;
+                    const float d = w[i] - (i < 16 ? v0[i] : v1[i - 16]);
+                    if (rok && j < p.n) {
+                        dst[j * p.ldwd] = d;
+                        sq32 = fmaf(d, d, sq32);
+                    }
+                }
+                sq += (double)sq32;
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accempty[abuf]);
+        }
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (lane == 0) red[e] = sq;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, kCols);
+    if (threadIdx.x == 0) {
+        if (abort_flag) record_error(p.st, RQB_ERR_TIMEOUT);
+        if (p.sq_part) {
+            double t = 0.0;
+            for (int i = 0; i < 8; ++i) t += red[i];
+            p.sq_part[blockIdx.x] = t;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Small kernels around the products.
+
+// Omega_i in the K-major layout of the sketch: out[j + c ldo] = rna_tf32 of the
+// binary32 Gaussian (j, col0 + c) for c < p, zero for p <= c < bp.
+__global__ void k_omega_tf32(long long n, long long col0, int p, int bp, uint64_t seed, float* __restrict__ out,
+                             long long ldo) {
+    const long long total = n * bp;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long j = e % n;
+        const int c = (int)(e / n);
+        out[j + c * ldo] = c < p ? tf32_rna(gaussian_f32(seed, j, col0 + c)) : 0.f;
+    }
+}
+
+// From Q_i (m x p, column-major, ld ldq): Qhi = Q_i and its lo part Qlo
+// (column-major, ld ldql, bp columns), Qt = Q_i^T as row-major m x bp and
+// its lo part Qtl; columns p..bp-1 are zero.  32 x 32 tiles transposed
+// through shared memory.
+__global__ void k_split_q(const float* __restrict__ Qi, long long ldq, long long m, int p, int bp,
+                          float* __restrict__ Qhi, float* __restrict__ Qlo, long long ldql, float* __restrict__ Qt,
+                          float* __restrict__ Qtl) {
+    __shared__ float tile[32][33];
+    const long long r0 = (long long)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+    for (int i = ty; i < 32; i += 8) {
+        const long long r = r0 + tx;
+        const int c = c0 + i;
+        float v = 0.f;
+        if (r < m && c < p) v = Qi[r + c * ldq];
+        if (r < m) {
+            Qhi[r + c * ldql] = v;
+            Qlo[r + c * ldql] = tf32_lo(v);
+        }
+        tile[i][tx] = v;
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        const long long r = r0 + i;
+        const int c = c0 + tx;
+        if (r < m) {
+            const float v = tile[tx][i];
+            Qt[r * bp + c] = v;
+            Qtl[r * bp + c] = tf32_lo(v);
+        }
+    }
+}
+
+// Bs / Bsl (np x n, ld np) from B_i (p x n, ld ldbi); rows p..np-1 zero.
+__global__ void k_stage_b(const float* __restrict__ Bi, long long ldbi, int p, long long n, int np,
+                          float* __restrict__ Bs, float* __restrict__ Bsl) {
+    const long long total = n * np;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e % np);
+        const long long j = e / np;
+        const float v = c < p ? Bi[c + j * ldbi] : 0.f;
+        Bs[e] = v;
+        Bsl[e] = tf32_lo(v);
+    }
+}
+
+__device__ __forceinline__ int first_cta(long long x, long long U, int P) {
+    int p = (int)((x * P) / U);
+    while (p + 1 < P && unit_begin(U, P, p + 1) <= x) ++p;
+    while (p > 0 && unit_begin(U, P, p) > x) --p;
+    return p;
+}
+
+// Y[r + c ldy] (r < m, c < np) = sum over the CTAs covering tile r / 128 of
+// their partials, in CTA order.  One CTA per tile.
+__global__ void k_reduce_sketch(const float* __restrict__ part, long long U, int C, int P, int G, int np, long long m,
+                                float* __restrict__ Y, long long ldy) {
+    const int t = blockIdx.x;
+    const long long x0 = (long long)t * C, x1 = x0 + C;
+    const int q0 = first_cta(x0, U, P);
+    for (int idx = threadIdx.x; idx < np * kBM; idx += blockDim.x) {   // c * 128 + row
+        const int c = idx / kBM, rl = idx % kBM;
+        const long long r = (long long)t * kBM + rl;
+        if (r >= m) continue;
+        double acc = 0.0;
+        for (int q = q0; q < P && unit_begin(U, P, q) < x1; ++q) {
+            const int seg = (int)(t - unit_begin(U, P, q) / C);
+            acc += (double)part[((size_t)q * G + seg) * (size_t)kBM * np + idx];
+        }
+        Y[r + c * ldy] = (float)acc;
+    }
+}
+
+// B_i: B[c + j ldb] (c < pcols) and the staged split copy Bs / Bsl (np x n,
+// column-major, ld np) from the partials of the projection; ||B_i||_F^2 of
+// the tile into sq_part[tile] (FP64).  One CTA per tile of 128 columns.
+__global__ void k_reduce_project(const float* __restrict__ part, long long U, int C, int P, int G, int np, int pcols,
+                                 long long n, float* __restrict__ B, long long ldb, float* __restrict__ Bs,
+                                 float* __restrict__ Bsl, double* __restrict__ sq_part) {
+    __shared__ double red[32];
+    const int t = blockIdx.x;
+    const long long x0 = (long long)t * C, x1 = x0 + C;
+    const int q0 = first_cta(x0, U, P);
+    double sq = 0.0;
+    for (int idx = threadIdx.x; idx < np * kBM; idx += blockDim.x) {   // jl * np + c
+        const int jl = idx / np, c = idx % np;
+        const long long j = (long long)t * kBM + jl;
+        if (j >= n) continue;
+        double acc = 0.0;
+        for (int q = q0; q < P && unit_begin(U, P, q) < x1; ++q) {
+            const int seg = (int)(t - unit_begin(U, P, q) / C);
+            acc += (double)part[((size_t)q * G + seg) * (size_t)kBM * np + idx];
+        }
+        const float v = (float)acc;
+        Bs[c + j * np] = v;
+        Bsl[c + j * np] = tf32_lo(v);
+        if (c < pcols) {
+            B[c + j * ldb] = v;
+            sq += (double)v * (double)v;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        sq_part[t] = s;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side.
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+    });
+    return fn;
+}
+
+// FP32 2-D map: `inner` contiguous elements per line, `outer` lines `ld`
+// elements apart; boxes of box_inner x box_outer, zero fill out of bounds.
+cudaError_t make_map(CUtensorMap* map, const float* base, long long inner, long long outer, long long ld,
+                     int box_inner, int box_outer, bool swizzle128) {
+    EncodeTiledFn enc = encoder();
+    if (!enc) return cudaErrorNotSupported;
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0 || ((ld * 4) & 15) != 0 || inner < box_inner ||
+        outer < box_outer)
+        return cudaErrorInvalidValue;
+    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+    const cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+constexpr int kUpdNJ = 128, kUpdStages = 3;
+constexpr size_t kUpdSmem = (size_t)kUpdStages * (2 * kTileBytes + 2 * kUpdNJ * 128) + 1024;
+
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int ROLE, int NP>
+cudaError_t launch_streamk_np(Ctx& cx, const StreamKParams& p) {
+    constexpr size_t smem = StreamKCfg<ROLE, NP>::kSmem;
+    cudaError_t e = allow_smem(k_streamk<ROLE, NP>, smem);
+    if (e != cudaSuccess) return e;
+    k_streamk<ROLE, NP><<<p.P, 320, smem, cx.stream>>>(p);
+    cx.launches++;
+    return cudaGetLastError();
+}
+
+template <int ROLE>
+cudaError_t launch_streamk(Ctx& cx, const StreamKParams& p, int np) {
+    switch (np) {
+        case 32: return launch_streamk_np<ROLE, 32>(cx, p);
+        case 64: return launch_streamk_np<ROLE, 64>(cx, p);
+        case 128: return launch_streamk_np<ROLE, 128>(cx, p);
+        case 256: return launch_streamk_np<ROLE, 256>(cx, p);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+struct Plan {
+    long long U;
+    int tiles, C, P, G;
+};
+
+Plan plan(long long tiles, long long C, int sms) {
+    Plan pl;
+    pl.tiles = (int)tiles;
+    pl.C = (int)C;
+    pl.U = tiles * C;
+    pl.P = (int)std::min<long long>(sms, pl.U);
+    const long long maxlen = (pl.U + pl.P - 1) / pl.P;
+    pl.G = (int)((maxlen - 1) / C + 2);
+    return pl;
+}
+
+}  // namespace
+
+bool shape_ok(long long m, long long n) { return m >= 128 && n >= 256; }
+
+size_t partial_floats(long long m, long long n, int np, int sms) {
+    const Plan a = plan((m + kBM - 1) / kBM, (n + kKC - 1) / kKC, sms);   // sketch
+    const Plan b = plan((n + kBM - 1) / kBM, (m + kKC - 1) / kKC, sms);
+    return (size_t)std::max(a.P * a.G, b.P * b.G) * kBM * np;
+}
+
+cudaError_t omega(Ctx& cx, long long n, long long col0, int p, int np, uint64_t seed, float* out, long long ldo) {
+    const long long total = n * np;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * cx.num_sms);
+    k_omega_tf32<<<blocks, 256, 0, cx.stream>>>(n, col0, p, np, seed, out, ldo);
+    cx.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t split_q(Ctx& cx, const float* Qi, long long ldq, long long m, int p, int np, float* Qhi, float* Qlo,
+                    long long ldql, float* Qt, float* Qtl) {
+    dim3 grid((unsigned)((m + 31) / 32), (unsigned)(np / 32));
+    k_split_q<<<grid, 256, 0, cx.stream>>>(Qi, ldq, m, p, np, Qhi, Qlo, ldql, Qt, Qtl);
+    cx.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t stage_b(Ctx& cx, const float* Bi, long long ldbi, int p, long long n, int np, float* Bs, float* Bsl) {
+    const long long total = n * np;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * cx.num_sms);
+    k_stage_b<<<blocks, 256, 0, cx.stream>>>(Bi, ldbi, p, n, np, Bs, Bsl);
+    cx.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t sketch(Ctx& cx, const float* X, long long ldx, long long m, long long n, const float* Om, long long ldom,
+                   int np, float* Y, long long ldy, float* part, size_t part_cap) {
+    StreamKParams p;
+    cudaError_t e;
+    if ((e = make_map(&p.mx, X, m, n, ldx, kBM, kKC, false)) != cudaSuccess) return e;
+    if ((e = make_map(&p.mw, Om, n, np, ldom, kKC, np, true)) != cudaSuccess) return e;
+    p.mwl = p.mw;
+    const Plan pl = plan((m + kBM - 1) / kBM, (n + kKC - 1) / kKC, cx.num_sms);
+    if ((size_t)pl.P * pl.G * kBM * np > part_cap) return cudaErrorInvalidValue;
+    p.part = part;
+    p.st = cx.st;
+    p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
+    if ((e = launch_streamk<kSketch>(cx, p, np)) != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_reduce_sketch<<<pl.tiles, 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, m, Y, ldy);
+    cx.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t project(Ctx& cx, const float* X, long long ldx, long long m, long long n, const float* Qhi,
+                    const float* Qlo, long long ldql, int pcols, int np, float* B, long long ldb, float* Bs,
+                    float* Bsl, float* part, size_t part_cap, double* sq_part, int sq_cap, double* sq_out) {
+    StreamKParams p;
+    cudaError_t e;
+    if ((e = make_map(&p.mx, X, m, n, ldx, kKC, kBM, true)) != cudaSuccess) return e;
+    if ((e = make_map(&p.mw, Qhi, m, np, ldql, kKC, np, true)) != cudaSuccess) return e;
+    if ((e = make_map(&p.mwl, Qlo, m, np, ldql, kKC, np, true)) != cudaSuccess) return e;
+    const Plan pl = plan((n + kBM - 1) / kBM, (m + kKC - 1) / kKC, cx.num_sms);
+    if ((size_t)pl.P * pl.G * kBM * np > part_cap || pl.tiles > sq_cap) return cudaErrorInvalidValue;
+    p.part = part;
+    p.st = cx.st;
+    p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
+    if ((e = launch_streamk<kProject>(cx, p, np)) != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_reduce_project<<<pl.tiles, 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, pcols, n, B, ldb, Bs, Bsl,
+                                                      sq_part);
+    cx.launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_sum_doubles(cx, sq_part, pl.tiles, sq_out);
+}
+
+cudaError_t update(Ctx& cx, const float* Wsrc, long long ldws, float* Wdst, long long ldwd, long long m,
+                   long long n, const float* Qt, const float* Qtl, const float* Bs, const float* Bsl, int np,
+                   double* sq_part, int sq_cap, double* sq_out) {
+    UpdateParams p;
+    cudaError_t e;
+    if ((e = make_map(&p.mqt, Qt, np, m, np, kKC, kBM, true)) != cudaSuccess) return e;
+    if ((e = make_map(&p.mqtl, Qtl, np, m, np, kKC, kBM, true)) != cudaSuccess) return e;
+    if ((e = make_map(&p.mbs, Bs, np, n, np, kKC, kUpdNJ, true)) != cudaSuccess) return e;
+    if ((e = make_map(&p.mbsl, Bsl, np, n, np, kKC, kUpdNJ, true)) != cudaSuccess) return e;
+    p.Wsrc = Wsrc; p.Wdst = Wdst; p.st = cx.st;
+    p.sq_part = sq_out ? sq_part : nullptr;
+    p.ldws = ldws; p.ldwd = ldwd; p.m = m; p.n = n;
+    p.RT = (int)((m + kBM - 1) / kBM);
+    p.CT = (int)((n + kUpdNJ - 1) / kUpdNJ);
+    p.C = np / kKC;
+    const long long T = (long long)p.RT * p.CT;
+    const int grid = (int)std::min<long long>(cx.num_sms, T);
+    if (sq_out && grid > sq_cap) return cudaErrorInvalidValue;
+    if ((e = allow_smem(k_update<kUpdNJ, kUpdStages>, kUpdSmem)) != cudaSuccess) return e;
+    k_update<kUpdNJ, kUpdStages><<<grid, 320, kUpdSmem, cx.stream>>>(p);
+    cx.launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return sq_out ? launch_sum_doubles(cx, sq_part, grid, sq_out) : cudaSuccess;
+}
+
+}  // namespace tc
+}  // namespace rqb

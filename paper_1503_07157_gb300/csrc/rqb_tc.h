@@ -1,0 +1,54 @@
+// rqb_tc.h -- host launchers of the split-TF32 tensor-core kernels (internal).
+//
+// All matrices FP32 and column-major unless stated; np is the padded block
+// width (32, 64, 128 or 256) and the MMA N.  Every pointer that feeds a
+// tensor map must be 16-byte aligned with a leading dimension that is a
+// multiple of 4; the launchers return cudaErrorInvalidValue otherwise.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "rqb_engine.h"
+
+namespace rqb {
+namespace tc {
+
+// The tensor-core path needs m >= 128 and n >= 256 (one full TMA box).
+bool shape_ok(long long m, long long n);
+
+// Floats of partial-accumulator scratch the sketch and the projection need.
+size_t partial_floats(long long m, long long n, int np, int sms);
+
+// Omega_i (n x np, ld ldo): columns col0 .. col0+p-1 of the binary32
+// Gaussian rounded to TF32; columns p .. np-1 zero.
+cudaError_t omega(Ctx& cx, long long n, long long col0, int p, int np, uint64_t seed, float* out, long long ldo);
+
+// Split copies of Q_i (m x p, ld ldq): Qhi / Qlo (ld ldql, np columns) and
+// the row-major transpose pair Qt / Qtl (m x np).
+cudaError_t split_q(Ctx& cx, const float* Qi, long long ldq, long long m, int p, int np, float* Qhi, float* Qlo,
+                    long long ldql, float* Qt, float* Qtl);
+
+// Bs / Bsl (np x n, ld np): B_i (p x n, ld ldbi) and its lo part, zero rows
+// p .. np-1 (the staged form the update reads).
+cudaError_t stage_b(Ctx& cx, const float* Bi, long long ldbi, int p, long long n, int np, float* Bs, float* Bsl);
+
+// Y (m x np, ld ldy) = X (m x n, ld ldx) Omega (n x np, ld ldom).
+cudaError_t sketch(Ctx& cx, const float* X, long long ldx, long long m, long long n, const float* Om, long long ldom,
+                   int np, float* Y, long long ldy, float* part, size_t part_cap);
+
+// B (pcols x n, ld ldb) = Q_i^T X and the staged split copy Bs / Bsl
+// (np x n, ld np); ||B||_F^2 into *sq_out.
+cudaError_t project(Ctx& cx, const float* X, long long ldx, long long m, long long n, const float* Qhi,
+                    const float* Qlo, long long ldql, int pcols, int np, float* B, long long ldb, float* Bs,
+                    float* Bsl, float* part, size_t part_cap, double* sq_part, int sq_cap, double* sq_out);
+
+// Wdst = Wsrc - Q_i B_i (m x n); Wdst may equal Wsrc.  With sq_out,
+// ||Wdst||_F^2 (FP64, summed from one partial per CTA in sq_part) too.
+cudaError_t update(Ctx& cx, const float* Wsrc, long long ldws, float* Wdst, long long ldwd, long long m,
+                   long long n, const float* Qt, const float* Qtl, const float* Bs, const float* Bsl, int np,
+                   double* sq_part, int sq_cap, double* sq_out);
+
+}  // namespace tc
+}  // namespace rqb

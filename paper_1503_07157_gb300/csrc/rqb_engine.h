@@ -65,6 +65,9 @@ template <typename T>
 cudaError_t chol_inv(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, bool fp64_factor, double* scratch,
                      size_t scratch_doubles);
 template <typename T>
+cudaError_t chol_inv_blocked(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, double tol, double* scratch,
+                             size_t scratch_doubles);
+template <typename T>
 cudaError_t downdate_sketch(Ctx& cx, int64_t m, int64_t n, int p, int bp, const T* Wsrc, int64_t ldws,
                             const T* Qi, int64_t ldq, const T* Bi, int64_t ldb, const T* Om, T* Wdst,
                             int64_t ldwd, T* Y, int64_t ldy, T* part, size_t part_cap_elems, double* nrm_part,

@@ -678,6 +678,9 @@ cudaError_t chol_inv(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, bool
     const double tol = (sizeof(T) == 8) ? 1e-15 : 1e-14;
     const size_t sq = (size_t)bp * bp;
     if (scratch_doubles < sq) return cudaErrorInvalidValue;
+    // a Gram wider than 128 does not fit one CTA's shared memory: blocked
+    // FP64 factorization over many CTAs (both passes)
+    if (bp > 128) return chol_inv_blocked<T>(cx, G, bp, p, R, Rinv, tol, scratch, scratch_doubles);
     if (fp64_factor) {
         const int in_smem = (sizeof(double) * sq <= 200 * 1024) ? 1 : 0;
         k_cholesky<double><<<1, 256, in_smem ? sizeof(double) * sq : 0, cx.stream>>>(G, bp, p, R, in_smem, scratch,

@@ -9,6 +9,15 @@ Workloads (--workload):
   fp32  (default) 20000 x 16000 FP32, A = U diag(j^-1.5) V^T, b = 128,
         eps = 1e-2 ||A||_F, Omega seed 0 -- the plain FP32 configuration
   fp64  2000 x 1000 FP64, s_j = 10^(-8(j-1)/999), b = 50, eps = 1e-4 ||A||_F
+  mixed 32768 x 16384 FP32 on the split-TF32 tensor-core path (RQB_PREC_TF32X3),
+        s_j = 10^(-4 j / 2000) for j <= 2000 then 1e-6, b = 256,
+        eps = 1e-3 ||A||_F; the plain FP32 path is timed on the same matrix at
+        the same eps (matched-eps comparison)
+  batched  512 FP32 matrices of uneven sizes, b = 32, eps_t = 1e-3 ||A_t||_F,
+        one rqb_factor_batched call per step
+
+The default run also measures the mixed and batched forms (a few steps each,
+--no-forms skips them) and reports them under "forms" in the same line.
 
 Metric: TFLOP/s of useful FLOPs (the algorithm's products counted once, no
 extra passes of split precision):
@@ -42,6 +51,9 @@ WORKLOADS = {
     "fp64": dict(name="randQB_b FP64 2000x1000 s_j=10^(-8(j-1)/999) b=50 eps=1e-4||A||_F", m=2000, n=1000, b=50,
                  eps_rel=1e-4, dtype="float64", spectrum="fp64cfg"),
 }
+WORKLOADS["mixed"] = dict(name="randQB_b split-TF32 32768x16384 s_j=10^(-4j/2000) (j<=2000) then 1e-6 b=256 "
+                               "eps=1e-3||A||_F", m=32768, n=16384, b=256, eps_rel=1e-3, dtype="float32",
+                          spectrum="mixed", prec="tf32x3")
 WORKLOADS["batched"] = dict(name="randQB_b batched FP32: 512 matrices, m~U[256,4096], n~U[128,min(m,2048)], "
                                  "s_j=exp(-j/r), r~U[10,200], b=32, eps_t=1e-3||A_t||_F",
                             m=0, n=0, b=32, eps_rel=1e-3, dtype="float32", spectrum="exp", count=512)
@@ -50,6 +62,11 @@ METRIC = "randQB_b TFLOP/s & roofline fraction at matched eps; mixed/batched vs 
 
 def useful_flops(m: int, n: int, b: int, s: int) -> float:
     return (6 * s - 2) * m * n * b + 2.0 * m * b * b * s * (s - 1) + 6.0 * m * b * b * s
+
+
+# MMA passes of each split-TF32 product: the sketch reads Omega as exact TF32
+# (hi + lo of A), the projection and the update split both operands
+TC_PASSES = {"sketch": 2, "project": 3, "downdate": 3}
 
 
 def phase_flops(m: int, n: int, b: int, s: int) -> dict:
@@ -68,6 +85,8 @@ def spectrum(kind: str, r: int):
         return inputs.spectrum_poly(r)
     if kind == "fp64cfg":
         return inputs.spectrum_fp64_config(r)
+    if kind == "mixed":
+        return inputs.spectrum_mixed_config(r)
     raise ValueError(kind)
 
 
@@ -202,9 +221,10 @@ def run_ours(args, w: dict, rank: int, world: int, dist):
     m, n, b = w["m"], w["n"], w["b"]
     eps = w["eps_rel"] * normA
     dt = torch.float64 if w["dtype"] == "float64" else torch.float32
+    prec = rqb.RQB_PREC_TF32X3 if w.get("prec") == "tf32x3" else rqb.RQB_PREC_NATIVE
     stream = torch.cuda.Stream()
     torch.cuda.synchronize()
-    h = rqb.Handle(dt, stream=stream, flags=rqb.RQB_FLAG_PHASE_TIMING)
+    h = rqb.Handle(dt, prec=prec, stream=stream, flags=rqb.RQB_FLAG_PHASE_TIMING)
     for _ in range(args.warmup):
         _, _, k, rc = h.rqb_factor(A, eps, b, seed=0)
     st = h.rqb_get_stats()
@@ -243,27 +263,72 @@ def run_ours(args, w: dict, rank: int, world: int, dist):
     F = useful_flops(m, n, b, s_blocks)
     value = F * world / (ms * 1e-3) / 1e12
 
-    # roofline of the dominant step (its main kernel plus split reduction)
+    # roofline of the dominant product step (its main kernel plus split reduction)
     pf = phase_flops(m, n, b, s_blocks)
     names = list(rqb.PHASES)
-    cand = [(phase_ms[i], names[i]) for i in range(len(names)) if names[i] in pf and phase_calls[i] > 0]
-    dom_ms, dom = max(cand)
-    idx = names.index(dom)
-    per_launch_ms = phase_ms[idx] / phase_calls[idx]
-    achieved = pf[dom] / (per_launch_ms * 1e-3) / 1e12
+    per_step = {names[i]: round(phase_ms[i] / args.steps, 4) for i in range(len(names))}
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(dev)
-    peak = alu_peak_tflops(w["dtype"], props.multi_processor_count, sm_max)
-    roofline = {"bound": "alu", "kernel": f"{dom} (k_gemm_{'nn' if dom == 'sketch' else 'tn'} + split reduction)"
-                if dom in ("sketch", "project") else dom,
-                "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(args.workload),
-                "peak_source": f"derived: {props.multi_processor_count} SMs x "
-                               f"{'128 FP32' if w['dtype'] == 'float32' else '2 FP64'} lanes x 2 x {sm_max:.0f} MHz",
-                "phase_ms_per_step": {names[i]: round(phase_ms[i] / args.steps, 4) for i in range(len(names))}}
+    if prec == rqb.RQB_PREC_TF32X3:
+        cand = [(phase_ms[i], names[i]) for i in range(len(names)) if names[i] in TC_PASSES and phase_calls[i] > 0]
+        dom_ms, dom = max(cand)
+        idx = names.index(dom)
+        per_launch_ms = phase_ms[idx] / phase_calls[idx]
+        passes = TC_PASSES[dom]
+        executed = passes * pf[dom]
+        achieved = executed / (per_launch_ms * 1e-3) / 1e12
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        peak = bf16 / 2.0
+        kern = {"sketch": "k_streamk<sketch> + k_reduce_sketch", "project": "k_streamk<project> + k_reduce_project",
+                "downdate": "k_update"}[dom]
+        roofline = {"bound": "tensor", "kernel": kern, "achieved": round(achieved, 3), "peak": round(peak, 3),
+                    "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(args.workload),
+                    "peak_source": f"measured bf16 burst {bf16} TFLOP/s (MEASURED_PEAKS.json) x 1/2 "
+                                   f"(nominal TF32:BF16 dense ratio), of measured",
+                    "flops_per_launch": executed, "mma_passes": passes,
+                    "useful_tflops": round(pf[dom] / (per_launch_ms * 1e-3) / 1e12, 3),
+                    "hbm_gbs": round((2 if dom == "downdate" else 1) * m * n * 4 / (per_launch_ms * 1e-3) / 1e9, 1),
+                    "phase_ms_per_step": per_step}
+    else:
+        cand = [(phase_ms[i], names[i]) for i in range(len(names)) if names[i] in pf and phase_calls[i] > 0]
+        dom_ms, dom = max(cand)
+        idx = names.index(dom)
+        per_launch_ms = phase_ms[idx] / phase_calls[idx]
+        achieved = pf[dom] / (per_launch_ms * 1e-3) / 1e12
+        peak = alu_peak_tflops(w["dtype"], props.multi_processor_count, sm_max)
+        roofline = {"bound": "alu",
+                    "kernel": f"{dom} (k_gemm_{'nn' if dom == 'sketch' else 'tn'} + split reduction)"
+                    if dom in ("sketch", "project") else dom,
+                    "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+                    "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(args.workload),
+                    "peak_source": f"derived: {props.multi_processor_count} SMs x "
+                                   f"{'128 FP32' if w['dtype'] == 'float32' else '2 FP64'} lanes x 2 x {sm_max:.0f} MHz",
+                    "phase_ms_per_step": per_step}
     return dict(h=h, A=A, eps=eps, value=value, ms=ms, F=F, k=k, s=s_blocks, clocks=clk, roofline=roofline,
                 launches=launches // max(args.steps, 1), stream=stream)
+
+
+def run_plain_matched(args, w: dict, res: dict, steps: int = 2) -> dict:
+    """The plain FP32 path (RQB_PREC_NATIVE) on the same matrix at the same eps."""
+    import torch
+    from paper_1503_07157_gb300 import rqb
+    m, n, b = w["m"], w["n"], w["b"]
+    h = rqb.Handle(torch.float32, stream=res["stream"])
+    _, _, k, rc = h.rqb_factor(res["A"], res["eps"], b, seed=0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(res["stream"])
+    for _ in range(steps):
+        _, _, k, rc = h.rqb_factor(res["A"], res["eps"], b, seed=0)
+    ev1.record(res["stream"])
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    s_blocks = h.rqb_get_stats().blocks
+    h.close()
+    F = useful_flops(m, n, b, s_blocks)
+    return {"impl": "plain FP32 (RQB_PREC_NATIVE)", "ms_per_step": round(ms, 3), "value": round(F / (ms * 1e-3) / 1e12, 4),
+            "unit": "TFLOP/s", "k": k, "steps": steps, "speedup_of_mixed": round(ms / res["ms"], 3)}
 
 
 def run_e2e(args, w: dict, res: dict) -> dict:
@@ -278,7 +343,8 @@ def run_e2e(args, w: dict, res: dict) -> dict:
     A_host.copy_(res["A"])
     Q_host = torch.empty(cap, m, dtype=dt, pin_memory=True).t()
     B_host = torch.empty(n, cap, dtype=dt, pin_memory=True).t()
-    h = rqb.Handle(dt, stream=res["stream"], max_rank=cap)
+    prec = rqb.RQB_PREC_TF32X3 if w.get("prec") == "tf32x3" else rqb.RQB_PREC_NATIVE
+    h = rqb.Handle(dt, prec=prec, stream=res["stream"], max_rank=cap)
     times, k = [], 0
     for i in range(args.warmup + max(1, args.e2e_steps)):
         torch.cuda.synchronize()
@@ -309,7 +375,7 @@ def make_batch_device(count: int, seed: int = 0):
     return mats, eps, cases
 
 
-def run_batched(args, w: dict, rank: int, world: int, dist):
+def run_batched(args, w: dict, rank: int, world: int, dist, do_e2e: bool = True):
     """Config-4 workload: one rqb_factor_batched call per step (one graph launch)."""
     import torch
     from paper_1503_07157_gb300 import build as _build
@@ -363,6 +429,12 @@ def run_batched(args, w: dict, rank: int, world: int, dist):
                 "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
                 "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
                                f"{float(peaks.get('sm_max_mhz', 2070.0)):.0f} MHz"}
+    if not do_e2e:
+        h.close()
+        return dict(value=F * world / (ms * 1e-3) / 1e12, ms=ms, F=F, clocks=clk, roofline=roofline, e2e=None,
+                    launches=2, extra={"count": len(mats), "k_mean": float(sum(ks)) / len(ks), "k_max": max(ks),
+                                       "status_ok": int(sum(1 for s_ in sts if s_ == 0)),
+                                       "loop_of_single_calls_ms": round(loop_ms, 2)})
     # e2e: pinned host inputs in, Q and B back to pinned host, inside the timed region
     hosts = [torch.empty(A.shape[1], A.shape[0], dtype=torch.float32, pin_memory=True).t() for A in mats]
     for hA, A in zip(hosts, mats):
@@ -421,6 +493,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--e2e-max-rank", type=int, default=4096)
+    ap.add_argument("--no-forms", action="store_true",
+                    help="default workload only: skip the mixed and batched forms")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -438,6 +512,10 @@ def main():
         return main_batched(args, w, rank, world, dist)
     res = run_ours(args, w, rank, world, dist)
     e2e = run_e2e(args, w, res) if rank == 0 else None
+    matched = run_plain_matched(args, w, res) if (rank == 0 and w.get("prec") == "tf32x3") else None
+    forms = None
+    if args.workload == "fp32" and not args.no_forms:
+        forms = run_forms(args, rank, world, dist)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_baseline(w, args.sample_frac)
@@ -457,6 +535,10 @@ def main():
             "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": res["launches"]
             * args.steps, "clocks": res["clocks"],
         }
+        if matched is not None:
+            line["plain_fp32_matched_eps"] = matched
+        if forms is not None:
+            line["forms"] = forms
         if cpu is not None:
             cpu.pop("seconds", None)
         print(json.dumps(line), flush=True)
@@ -464,6 +546,37 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_forms(args, rank: int, world: int, dist) -> dict:
+    """The mixed (split-TF32) and batched forms, a few steps each, for the
+    default line: value, ms, roofline, and the plain FP32 comparison."""
+    import copy
+    import gc
+    import torch
+    out = {}
+    a = copy.copy(args)
+    a.steps, a.warmup = 5, 3
+    wm = WORKLOADS["mixed"]
+    r = run_ours(a, wm, rank, world, dist)
+    out["mixed"] = {"workload": wm["name"], "value": round(r["value"], 4), "unit": "TFLOP/s",
+                    "ms_per_step": round(r["ms"], 3), "steps": a.steps, "k": r["k"], "blocks": r["s"],
+                    "roofline": r["roofline"], "plain_fp32_matched_eps": run_plain_matched(a, wm, r) if rank == 0
+                    else None}
+    r["h"].close()
+    del r
+    gc.collect()
+    torch.cuda.empty_cache()
+    wb = WORKLOADS["batched"]
+    a.steps = 2
+    rb = run_batched(a, wb, rank, world, dist, do_e2e=False)
+    out["batched"] = dict({"workload": wb["name"], "value": round(rb["value"], 4), "unit": "TFLOP/s",
+                           "ms_per_step": round(rb["ms"], 3), "steps": a.steps, "roofline": rb["roofline"]},
+                          **rb["extra"])
+    out["batched"]["speedup_vs_loop_of_single_calls"] = round(rb["extra"]["loop_of_single_calls_ms"] / rb["ms"], 3)
+    gc.collect()
+    torch.cuda.empty_cache()
+    return out
 
 
 def main_batched(args, w, rank, world, dist) -> int:

@@ -65,8 +65,10 @@ template <typename T>
 cudaError_t chol_inv(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, bool fp64_factor, double* scratch,
                      size_t scratch_doubles);
 template <typename T>
+cudaError_t upper_inverse(Ctx& cx, const double* R, int bp, T* Rinv);
+template <typename T>
 cudaError_t chol_inv_blocked(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, double tol, double* scratch,
-                             size_t scratch_doubles);
+                             size_t scratch_doubles, bool fp64);
 template <typename T>
 cudaError_t downdate_sketch(Ctx& cx, int64_t m, int64_t n, int p, int bp, const T* Wsrc, int64_t ldws,
                             const T* Qi, int64_t ldq, const T* Bi, int64_t ldb, const T* Om, T* Wdst,

@@ -67,13 +67,36 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_sumsq(int64_t m, int64_t n, const T* __restrict__ X, int64_t ldx,
                                                double* __restrict__ part) {
+    // one warp per column at a time (coalesced rows); FP32 data: each square
+    // is split exactly into p + e (e = fma(v, v, -p)) and summed with
+    // compensated FP32 adds, promoted to FP64 every 64 rows per lane
     __shared__ double sh[8];
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5), nw = (int64_t)gridDim.x * 8;
     double acc = 0.0;
-    const int64_t total = m * n;
-    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < total; e += (int64_t)gridDim.x * 256) {
-        const int64_t r = e % m, c = e / m;
-        const double v = (double)X[r + c * ldx];
-        acc += v * v;
+    for (int64_t c = gw; c < n; c += nw) {
+        const T* col = X + c * ldx;
+        if (sizeof(T) == 8) {
+            for (int64_t r = lane; r < m; r += 32) {
+                const double v = (double)col[r];
+                acc = fma(v, v, acc);
+            }
+        } else {
+            for (int64_t r0 = 0; r0 < m; r0 += 32 * 64) {
+                float hi = 0.f, lo = 0.f;
+                const int64_t r1 = r0 + 32 * 64 < m ? r0 + 32 * 64 : m;
+                for (int64_t r = r0 + lane; r < r1; r += 32) {
+                    const float v = (float)col[r];
+                    const float p2 = __fmul_rn(v, v);     // rounded square, never contracted
+                    const float e2 = fmaf(v, v, -p2);     // its exact error
+                    const float t = __fadd_rn(hi, p2);    // TwoSum(hi, p2)
+                    const float bp = __fsub_rn(t, hi);
+                    lo += __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p2, bp)) + e2;
+                    hi = t;
+                }
+                acc += (double)hi + (double)lo;
+            }
+        }
     }
     const double s = block_sum<256>(acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
@@ -153,12 +176,15 @@ cudaError_t launch_reduce_split(Ctx& cx, int64_t rows, int64_t cols, int splits,
 // diag(R) > 0; rows/cols >= p are set to the identity.  One CTA of 256
 // threads, working precision W (FP64 for the first CholeskyQR pass, whose Gram
 // may be ill-conditioned; FP32 for the second, whose Gram is I + O(u kappa)).
-// The upper triangle is kept row-major, in shared memory when the square fits,
-// else in a global scratch of bp x bp elements.  Thread (ty, tx) of a 16 x 16 grid owns the entries
-// (r, c) with r = ty, c = tx (mod 16); step j subtracts S[j][r] S[j][c] / d_j
-// from each owned S[r][c] (j < r <= c) using the unscaled pivot row, so a
-// step needs one barrier; rows are scaled by d_j^{-1/2} at the end.  A pivot
-// <= tol * G_jj records RQB_ERR_BREAKDOWN.
+// The upper triangle is kept row-major and packed (row r holds columns
+// r .. bp-1), in shared memory when it fits, else in a global scratch.
+// Thread (ty, tx) of a 16 x 16 grid owns the entries (r, c) with r = ty,
+// c = tx (mod 16); step j subtracts S[j][r] S[j][c] / d_j from each owned
+// S[r][c] (j < r <= c) using the unscaled pivot row, so a step needs one
+// barrier; rows are scaled by d_j^{-1/2} at the end.  A pivot <= tol * G_jj
+// records RQB_ERR_BREAKDOWN.
+__device__ __forceinline__ int64_t packed_row(int r, int bp) { return (int64_t)r * bp - (int64_t)r * (r + 1) / 2; }
+
 template <typename W>
 __global__ void __launch_bounds__(256)
 k_cholesky(const double* __restrict__ G, int bp, int p, double* __restrict__ R, int in_smem, void* scratch,
@@ -169,18 +195,20 @@ k_cholesky(const double* __restrict__ G, int bp, int p, double* __restrict__ R, 
     W* S = in_smem ? reinterpret_cast<W*>(chol_smem) : reinterpret_cast<W*>(scratch);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     for (int r = tid; r < p; r += 256) refd[r] = G[r + (int64_t)r * bp];
-    for (int r = ty; r < p; r += 16)
-        for (int c = r + ((tx - r) % 16 + 16) % 16; c < p; c += 16) S[(int64_t)r * bp + c] = (W)G[r + (int64_t)c * bp];
+    for (int r = ty; r < p; r += 16) {
+        W* Sr = S + packed_row(r, bp);
+        for (int c = r + ((tx - r) % 16 + 16) % 16; c < p; c += 16) Sr[c] = (W)G[r + (int64_t)c * bp];
+    }
     __syncthreads();
     bool bad = false;
     for (int j = 0; j < p; ++j) {
-        const W d = S[(int64_t)j * bp + j];
+        const W* Sj = S + packed_row(j, bp);
+        const W d = Sj[j];
         if (!((double)d > tol * refd[j]) || !isfinite((double)d)) { bad = true; break; }   // uniform
         const W invd = W(1) / d;
-        const W* Sj = S + (int64_t)j * bp;
         for (int r = j + 1 + ((ty - (j + 1)) % 16 + 16) % 16; r < p; r += 16) {
             const W f = Sj[r] * invd;
-            W* Sr = S + (int64_t)r * bp;
+            W* Sr = S + packed_row(r, bp);
             for (int c = r + ((tx - r) % 16 + 16) % 16; c < p; c += 16) Sr[c] -= f * Sj[c];
         }
         __syncthreads();
@@ -190,13 +218,13 @@ k_cholesky(const double* __restrict__ G, int bp, int p, double* __restrict__ R, 
         return;
     }
     // R (column-major, FP64): R[r][c] = S[r][c] / sqrt(d_r), identity beyond p.
-    for (int r = tid; r < p; r += 256) rdiag[r] = sqrt((double)S[(int64_t)r * bp + r]);
+    for (int r = tid; r < p; r += 256) rdiag[r] = sqrt((double)S[packed_row(r, bp) + r]);
     __syncthreads();
     for (int e = tid; e < bp * bp; e += 256) {
         const int r = e % bp, c = e / bp;
         double v = 0.0;
         if (r < p && c < p) {
-            if (r < c) v = (double)S[(int64_t)r * bp + c] / rdiag[r];
+            if (r < c) v = (double)S[packed_row(r, bp) + c] / rdiag[r];
             else if (r == c) v = rdiag[r];
         } else if (r == c) {
             v = 1.0;
@@ -677,18 +705,19 @@ cudaError_t chol_inv(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, bool
     // 4e-15 for FP32 data); CholeskyQR2 with an FP64 Gram handles anything above
     const double tol = (sizeof(T) == 8) ? 1e-15 : 1e-14;
     const size_t sq = (size_t)bp * bp;
+    const size_t packed = (size_t)bp * (bp + 1) / 2;
     if (scratch_doubles < sq) return cudaErrorInvalidValue;
-    // a Gram wider than 128 does not fit one CTA's shared memory: blocked
-    // FP64 factorization over many CTAs (both passes)
-    if (bp > 128) return chol_inv_blocked<T>(cx, G, bp, p, R, Rinv, tol, scratch, scratch_doubles);
+    // a Gram wider than 128: blocked over many CTAs (one CTA's shared memory
+    // does not hold an FP64 one, and one SM's FP64 rate would bound it)
+    if (bp > 128) return chol_inv_blocked<T>(cx, G, bp, p, R, Rinv, tol, scratch, scratch_doubles, fp64_factor);
     if (fp64_factor) {
-        const int in_smem = (sizeof(double) * sq <= 200 * 1024) ? 1 : 0;
-        k_cholesky<double><<<1, 256, in_smem ? sizeof(double) * sq : 0, cx.stream>>>(G, bp, p, R, in_smem, scratch,
-                                                                                     tol, cx.st);
+        const int in_smem = (sizeof(double) * packed <= 200 * 1024) ? 1 : 0;
+        k_cholesky<double><<<1, 256, in_smem ? sizeof(double) * packed : 0, cx.stream>>>(G, bp, p, R, in_smem,
+                                                                                         scratch, tol, cx.st);
     } else {
-        const int in_smem = (sizeof(float) * sq <= 200 * 1024) ? 1 : 0;
-        k_cholesky<float><<<1, 256, in_smem ? sizeof(float) * sq : 0, cx.stream>>>(G, bp, p, R, in_smem, scratch,
-                                                                                   tol, cx.st);
+        const int in_smem = (sizeof(float) * packed <= 200 * 1024) ? 1 : 0;
+        k_cholesky<float><<<1, 256, in_smem ? sizeof(float) * packed : 0, cx.stream>>>(G, bp, p, R, in_smem,
+                                                                                       scratch, tol, cx.st);
     }
     cx.launches++;
     cudaError_t e = cudaGetLastError();

@@ -63,7 +63,9 @@ struct UpdateParams {
     int RT, CT, C;
 };
 
-__device__ __forceinline__ long long unit_begin(long long U, int P, int p) { return U * p / P; }
+__host__ __device__ __forceinline__ long long unit_begin(long long U, int P, int p) { return U * p / P; }
+
+constexpr int kMaxCover = 64;   // CTAs that may share one tile
 
 // ---------------------------------------------------------------------------
 // Stream-K sketch / project.
@@ -524,47 +526,72 @@ __device__ __forceinline__ int first_cta(long long x, long long U, int P) {
     return p;
 }
 
+// Offsets (in floats) of the partial slots that hold tile t, in CTA order,
+// into off[0 .. count); computed once per CTA by thread 0.  The host plan
+// keeps the number of CTAs covering one tile at most kMaxCover.
+
+__device__ __forceinline__ int tile_slots(long long U, int C, int P, int G, int np, int t, size_t* off) {
+    const long long x0 = (long long)t * C, x1 = x0 + C;
+    int count = 0;
+    for (int q = first_cta(x0, U, P); q < P && count < kMaxCover; ++q) {
+        const long long ub = unit_begin(U, P, q);
+        if (ub >= x1) break;
+        const int seg = (int)(t - ub / C);
+        off[count++] = ((size_t)q * G + seg) * (size_t)kBM * np;
+    }
+    return count;
+}
+
 // Y[r + c ldy] (r < m, c < np) = sum over the CTAs covering tile r / 128 of
-// their partials, in CTA order.  One CTA per tile.
+// their partials, in CTA order (FP32, at most a few terms, round to nearest).
+// One CTA per tile.
+constexpr int kReduceSlices = 8;   // CTAs per tile in the reductions
+
 __global__ void k_reduce_sketch(const float* __restrict__ part, long long U, int C, int P, int G, int np, long long m,
                                 float* __restrict__ Y, long long ldy) {
+    __shared__ size_t off[kMaxCover];
+    __shared__ int count;
     const int t = blockIdx.x;
-    const long long x0 = (long long)t * C, x1 = x0 + C;
-    const int q0 = first_cta(x0, U, P);
-    for (int idx = threadIdx.x; idx < np * kBM; idx += blockDim.x) {   // c * 128 + row
+    if (threadIdx.x == 0) count = tile_slots(U, C, P, G, np, t, off);
+    __syncthreads();
+    const int nc = count;
+    const int span = np * kBM / kReduceSlices;
+    const int i0 = blockIdx.y * span;
+#pragma unroll 4
+    for (int idx = i0 + threadIdx.x; idx < i0 + span; idx += blockDim.x) {   // c * 128 + row
         const int c = idx / kBM, rl = idx % kBM;
         const long long r = (long long)t * kBM + rl;
         if (r >= m) continue;
-        double acc = 0.0;
-        for (int q = q0; q < P && unit_begin(U, P, q) < x1; ++q) {
-            const int seg = (int)(t - unit_begin(U, P, q) / C);
-            acc += (double)part[((size_t)q * G + seg) * (size_t)kBM * np + idx];
-        }
-        Y[r + c * ldy] = (float)acc;
+        float acc = 0.f;
+        for (int q = 0; q < nc; ++q) acc += part[off[q] + idx];
+        Y[r + c * ldy] = acc;
     }
 }
 
 // B_i: B[c + j ldb] (c < pcols) and the staged split copy Bs / Bsl (np x n,
 // column-major, ld np) from the partials of the projection; ||B_i||_F^2 of
-// the tile into sq_part[tile] (FP64).  One CTA per tile of 128 columns.
+// the tile into sq_part[tile * 8 + slice] (FP64).  Eight CTAs per tile of 128
+// columns.
 __global__ void k_reduce_project(const float* __restrict__ part, long long U, int C, int P, int G, int np, int pcols,
                                  long long n, float* __restrict__ B, long long ldb, float* __restrict__ Bs,
                                  float* __restrict__ Bsl, double* __restrict__ sq_part) {
+    __shared__ size_t off[kMaxCover];
+    __shared__ int count;
     __shared__ double red[32];
     const int t = blockIdx.x;
-    const long long x0 = (long long)t * C, x1 = x0 + C;
-    const int q0 = first_cta(x0, U, P);
+    if (threadIdx.x == 0) count = tile_slots(U, C, P, G, np, t, off);
+    __syncthreads();
+    const int nc = count;
     double sq = 0.0;
-    for (int idx = threadIdx.x; idx < np * kBM; idx += blockDim.x) {   // jl * np + c
+    const int span = np * kBM / kReduceSlices;
+    const int i0 = blockIdx.y * span;
+#pragma unroll 4
+    for (int idx = i0 + threadIdx.x; idx < i0 + span; idx += blockDim.x) {   // jl * np + c
         const int jl = idx / np, c = idx % np;
         const long long j = (long long)t * kBM + jl;
         if (j >= n) continue;
-        double acc = 0.0;
-        for (int q = q0; q < P && unit_begin(U, P, q) < x1; ++q) {
-            const int seg = (int)(t - unit_begin(U, P, q) / C);
-            acc += (double)part[((size_t)q * G + seg) * (size_t)kBM * np + idx];
-        }
-        const float v = (float)acc;
+        float v = 0.f;
+        for (int q = 0; q < nc; ++q) v += part[off[q] + idx];
         Bs[c + j * np] = v;
         Bsl[c + j * np] = tf32_lo(v);
         if (c < pcols) {
@@ -578,7 +605,7 @@ __global__ void k_reduce_project(const float* __restrict__ part, long long U, in
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        sq_part[t] = s;
+        sq_part[(size_t)t * kReduceSlices + blockIdx.y] = s;
     }
 }
 
@@ -665,7 +692,10 @@ Plan plan(long long tiles, long long C, int sms) {
     pl.tiles = (int)tiles;
     pl.C = (int)C;
     pl.U = tiles * C;
-    pl.P = (int)std::min<long long>(sms, pl.U);
+    // every CTA covers at least minlen = floor(U / P) units, so a tile of C
+    // units meets at most ceil(C / minlen) + 1 CTAs: keep that <= kMaxCover
+    const long long minlen = (C + kMaxCover - 2) / (kMaxCover - 1);
+    pl.P = (int)std::max<long long>(1, std::min<long long>({(long long)sms, pl.U, pl.U / minlen}));
     const long long maxlen = (pl.U + pl.P - 1) / pl.P;
     pl.G = (int)((maxlen - 1) / C + 2);
     return pl;
@@ -719,7 +749,8 @@ cudaError_t sketch(Ctx& cx, const float* X, long long ldx, long long m, long lon
     p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
     if ((e = launch_streamk<kSketch>(cx, p, np)) != cudaSuccess) return e;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_reduce_sketch<<<pl.tiles, 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, m, Y, ldy);
+    k_reduce_sketch<<<dim3(pl.tiles, kReduceSlices), 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, m, Y,
+                                                                           ldy);
     cx.launches++;
     return cudaGetLastError();
 }
@@ -733,17 +764,17 @@ cudaError_t project(Ctx& cx, const float* X, long long ldx, long long m, long lo
     if ((e = make_map(&p.mw, Qhi, m, np, ldql, kKC, np, true)) != cudaSuccess) return e;
     if ((e = make_map(&p.mwl, Qlo, m, np, ldql, kKC, np, true)) != cudaSuccess) return e;
     const Plan pl = plan((n + kBM - 1) / kBM, (m + kKC - 1) / kKC, cx.num_sms);
-    if ((size_t)pl.P * pl.G * kBM * np > part_cap || pl.tiles > sq_cap) return cudaErrorInvalidValue;
+    if ((size_t)pl.P * pl.G * kBM * np > part_cap || pl.tiles * kReduceSlices > sq_cap) return cudaErrorInvalidValue;
     p.part = part;
     p.st = cx.st;
     p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
     if ((e = launch_streamk<kProject>(cx, p, np)) != cudaSuccess) return e;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_reduce_project<<<pl.tiles, 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, pcols, n, B, ldb, Bs, Bsl,
-                                                      sq_part);
+    k_reduce_project<<<dim3(pl.tiles, kReduceSlices), 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, pcols,
+                                                                            n, B, ldb, Bs, Bsl, sq_part);
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return launch_sum_doubles(cx, sq_part, pl.tiles, sq_out);
+    return launch_sum_doubles(cx, sq_part, pl.tiles * kReduceSlices, sq_out);
 }
 
 cudaError_t update(Ctx& cx, const float* Wsrc, long long ldws, float* Wdst, long long ldwd, long long m,

@@ -1,0 +1,53 @@
+"""Split-TF32 factorizations for ncu captures of the tensor-core path.
+
+  --case small  8192 x 8192 FP32 (256 MB, larger than L2), the mixed spectrum,
+                b = 256, fixed rank 512 (two blocks): one launch each of the
+                stream-K sketch and projection and of the update per block;
+                for --set full captures of one kernel.
+  --case mixed  the 32768 x 16384 split-TF32 workload (b = 256, eps =
+                1e-3 ||A||_F): one warm-up factorization, then one inside
+                cudaProfilerStart/Stop, for launch lists taken with
+                ncu --profile-from-start off.
+Usage: python -m paper_1503_07157_gb300.profile_case [--case small|mixed]
+"""
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", choices=["small", "mixed"], default="small")
+    args = ap.parse_args()
+    import torch
+    import inputs
+    from paper_1503_07157_gb300 import build, rqb
+    build.build()
+    if args.case == "small":
+        m = n = 8192
+        s = inputs.spectrum_mixed_config(min(m, n), knee=2000)
+        A = inputs.usv_torch(m, n, s, 3, device="cuda", dtype=torch.float32)
+        torch.cuda.synchronize()
+        with rqb.Handle(torch.float32, prec=rqb.RQB_PREC_TF32X3, max_rank=512, fixed_rank=True) as h:
+            _, _, k, rc = h.rqb_factor(A, 0.0, 256, 0, check=False)
+            torch.cuda.synchronize()
+    else:
+        A, meta = inputs.config_mixed_torch()
+        torch.cuda.synchronize()
+        with rqb.Handle(torch.float32, prec=rqb.RQB_PREC_TF32X3) as h:
+            h.rqb_factor(A, meta["eps"], meta["b"], 0, check=False)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+            _, _, k, rc = h.rqb_factor(A, meta["eps"], meta["b"], 0, check=False)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
+    print("case", args.case, "rc", rc, "k", k, flush=True)
+    return 0 if rc == rqb.RQB_OK else 1
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -65,7 +65,9 @@ def useful_flops(m: int, n: int, b: int, s: int) -> float:
 
 
 # MMA passes of each split-TF32 product: the sketch reads Omega as exact TF32
-# (hi + lo of A), the projection and the update split both operands
+# (hi + lo of A), the projection and the update split both operands.  On the
+# split-TF32 path every product phase is one m x n x b product (the update
+# is not fused with the next sketch), 2 m n b useful FLOPs per launch.
 TC_PASSES = {"sketch": 2, "project": 3, "downdate": 3}
 
 
@@ -185,8 +187,10 @@ def alu_peak_tflops(dtype: str, num_sms: int, sm_mhz: float) -> float:
 
 
 # ncu DRAM traffic of the dominant kernel per launch (bytes), keyed by workload;
-# from profiles/ (value is None when the kernel changed since the capture).
-NCU_TRAFFIC = {"fp32": None, "fp64": None}
+# from profiles/ (None when the kernel changed since the capture or when the
+# workload's dominant kernel was captured only on a smaller case).
+#   fp32: k_gemm_nn sketch, 20000 x 16000, dram read 1.295 GB + write 0.145 GB
+NCU_TRAFFIC = {"fp32": 1.440e9, "fp64": None, "mixed": None}
 
 
 def oracle_baseline(w: dict, frac: float, repeats: int = 1) -> dict:
@@ -255,13 +259,9 @@ def run_ours(args, w: dict, rank: int, world: int, dist):
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, dev)
     F = useful_flops(m, n, b, s_blocks)
-    value = F * world / (ms * 1e-3) / 1e12
+    value = aggregate_value(F, world, ms)
 
     # roofline of the dominant product step (its main kernel plus split reduction)
     pf = phase_flops(m, n, b, s_blocks)
@@ -276,7 +276,8 @@ def run_ours(args, w: dict, rank: int, world: int, dist):
         idx = names.index(dom)
         per_launch_ms = phase_ms[idx] / phase_calls[idx]
         passes = TC_PASSES[dom]
-        executed = passes * pf[dom]
+        useful = 2.0 * m * n * b
+        executed = passes * useful
         achieved = executed / (per_launch_ms * 1e-3) / 1e12
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
         peak = bf16 / 2.0
@@ -287,7 +288,7 @@ def run_ours(args, w: dict, rank: int, world: int, dist):
                     "peak_source": f"measured bf16 burst {bf16} TFLOP/s (MEASURED_PEAKS.json) x 1/2 "
                                    f"(nominal TF32:BF16 dense ratio), of measured",
                     "flops_per_launch": executed, "mma_passes": passes,
-                    "useful_tflops": round(pf[dom] / (per_launch_ms * 1e-3) / 1e12, 3),
+                    "useful_tflops": round(useful / (per_launch_ms * 1e-3) / 1e12, 3),
                     "hbm_gbs": round((2 if dom == "downdate" else 1) * m * n * 4 / (per_launch_ms * 1e-3) / 1e9, 1),
                     "phase_ms_per_step": per_step}
     else:
@@ -406,11 +407,7 @@ def run_batched(args, w: dict, rank: int, world: int, dist, do_e2e: bool = True)
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, torch.device("cuda", torch.cuda.current_device()))
     kern_ms /= args.steps
     peaks = measured_peaks()
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
@@ -431,7 +428,7 @@ def run_batched(args, w: dict, rank: int, world: int, dist, do_e2e: bool = True)
                                f"{float(peaks.get('sm_max_mhz', 2070.0)):.0f} MHz"}
     if not do_e2e:
         h.close()
-        return dict(value=F * world / (ms * 1e-3) / 1e12, ms=ms, F=F, clocks=clk, roofline=roofline, e2e=None,
+        return dict(value=aggregate_value(F, world, ms), ms=ms, F=F, clocks=clk, roofline=roofline, e2e=None,
                     launches=2, extra={"count": len(mats), "k_mean": float(sum(ks)) / len(ks), "k_max": max(ks),
                                        "status_ok": int(sum(1 for s_ in sts if s_ == 0)),
                                        "loop_of_single_calls_ms": round(loop_ms, 2)})
@@ -462,10 +459,25 @@ def run_batched(args, w: dict, rank: int, world: int, dist, do_e2e: bool = True)
            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(te * 1e3, 3),
            "api": "pinned host copies + rqb_factor_batched"}
     h.close()
-    return dict(value=F * world / (ms * 1e-3) / 1e12, ms=ms, F=F, clocks=clk, roofline=roofline, e2e=e2e,
+    return dict(value=aggregate_value(F, world, ms), ms=ms, F=F, clocks=clk, roofline=roofline, e2e=e2e,
                 launches=2, extra={"count": len(mats), "k_mean": float(sum(ks)) / len(ks), "k_max": max(ks),
                                    "status_ok": int(sum(1 for s_ in sts if s_ == 0)),
                                    "loop_of_single_calls_ms": round(loop_ms, 2)})
+
+
+def max_over_ranks(ms: float, dist, device=None) -> float:
+    """The slowest replica's time: the maximum of a per-rank value over all ranks."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(flops_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job TFLOP/s: the work of all replicas over the slowest replica's time."""
+    return flops_per_rank * world / (ms * 1e-3) / 1e12
 
 
 def init_dist():

@@ -8,7 +8,11 @@
                 1e-3 ||A||_F): one warm-up factorization, then one inside
                 cudaProfilerStart/Stop, for launch lists taken with
                 ncu --profile-from-start off.
-Usage: python -m paper_1503_07157_gb300.profile_case [--case small|mixed]
+  --case fp32   the same for the 20000 x 16000 plain FP32 workload (b = 128,
+                eps = 1e-2 ||A||_F)
+  --case fp64   the same for the 2000 x 1000 FP64 workload (b = 50,
+                eps = 1e-4 ||A||_F)
+Usage: python -m paper_1503_07157_gb300.profile_case [--case small|mixed|fp32|fp64]
 """
 import argparse
 import os
@@ -21,7 +25,7 @@ if ROOT not in sys.path:
 
 def main() -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["small", "mixed"], default="small")
+    ap.add_argument("--case", choices=["small", "mixed", "fp32", "fp64"], default="small")
     args = ap.parse_args()
     import torch
     import inputs
@@ -36,13 +40,24 @@ def main() -> int:
             _, _, k, rc = h.rqb_factor(A, 0.0, 256, 0, check=False)
             torch.cuda.synchronize()
     else:
-        A, meta = inputs.config_mixed_torch()
+        import numpy as np
+        if args.case == "mixed":
+            A, meta = inputs.config_mixed_torch()
+            dt, prec, eps, b = torch.float32, rqb.RQB_PREC_TF32X3, meta["eps"], meta["b"]
+        elif args.case == "fp32":
+            s = inputs.spectrum_poly(16000)
+            A = inputs.usv_torch(20000, 16000, s, 2, device="cuda", dtype=torch.float32)
+            dt, prec, eps, b = torch.float32, rqb.RQB_PREC_NATIVE, 1e-2 * float(np.sqrt(np.sum(s ** 2))), 128
+        else:
+            s = inputs.spectrum_fp64_config(1000)
+            A = inputs.usv_torch(2000, 1000, s, 2, device="cuda", dtype=torch.float64)
+            dt, prec, eps, b = torch.float64, rqb.RQB_PREC_NATIVE, 1e-4 * float(np.sqrt(np.sum(s ** 2))), 50
         torch.cuda.synchronize()
-        with rqb.Handle(torch.float32, prec=rqb.RQB_PREC_TF32X3) as h:
-            h.rqb_factor(A, meta["eps"], meta["b"], 0, check=False)
+        with rqb.Handle(dt, prec=prec) as h:
+            h.rqb_factor(A, eps, b, 0, check=False)
             torch.cuda.synchronize()
             torch.cuda.profiler.start()
-            _, _, k, rc = h.rqb_factor(A, meta["eps"], meta["b"], 0, check=False)
+            _, _, k, rc = h.rqb_factor(A, eps, b, 0, check=False)
             torch.cuda.synchronize()
             torch.cuda.profiler.stop()
     print("case", args.case, "rc", rc, "k", k, flush=True)

@@ -83,6 +83,15 @@ typedef struct {
  * report their durations in rqb_stats.phase_ms (costs a few microseconds of
  * host time per step; no extra synchronisation beyond the per-block one). */
 #define RQB_FLAG_PHASE_TIMING 1
+/* With power > 0: the Sec. 5.4 variant of the power scheme, which forms
+ * Y = (A A^T)^power A Omega_i by plain products and orthonormalises once
+ * (no orth between the products of Fig. randQB_pb).  Cheaper per block; the
+ * unblocked scheme then stalls near sigma_1 eps_mach^(1/(2 power + 1))
+ * (Sec. 5.4), the blocked one reaches full precision (Sec. 6.3).  The panel
+ * is still orthonormalised by CholeskyQR2, so a Y whose condition number
+ * exceeds about u^(-1/2) of the Gram's precision reports
+ * RQB_ERR_BREAKDOWN. */
+#define RQB_FLAG_SKIP_INNER_ORTH 2
 
 /* Steps timed with RQB_FLAG_PHASE_TIMING (index into phase_ms/phase_calls). */
 typedef enum {

@@ -330,6 +330,22 @@ int power_panel(rqb_handle h, Ctx& cx, const Arena<T>& ar, int64_t m, int64_t n,
     RQB_CK(cudaMemsetAsync(ar.Qt, 0, sizeof(T) * (size_t)m * bp, h->stream));
     RQB_CK(cudaMemsetAsync(ar.Z, 0, sizeof(T) * (size_t)n * bp, h->stream));
     RQB_CK(cudaMemsetAsync(ar.Zq, 0, sizeof(T) * (size_t)n * bp, h->stream));
+    if (h->cfg.flags & RQB_FLAG_SKIP_INNER_ORTH) {
+        // Sec. 5.4 variant: Y <- A (A^T Y), power times, then one orth with
+        // the re-projection against the earlier blocks
+        for (int j = 0; j < h->cfg.power; ++j) {
+            RQB_CK(gemm_tn<T>(cx, m, (int)n, p, W, ldw, ar.Y, m, ar.Z, n, ar.part, ar.part_cap, nullptr, 0,
+                              nullptr));
+            NNArgs<T> a;
+            a.m = m; a.K = n; a.nc = bp; a.nout = bp;
+            a.X = W; a.ldx = ldw;
+            a.C = ar.Z; a.csk = 1; a.csj = n; a.c_rowmajor = false;
+            a.Out = ar.Y; a.ldo = m;
+            a.part = ar.part; a.part_cap = ar.part_cap; a.allow_split = 1;
+            RQB_CK(gemm_nn<T>(cx, a));
+        }
+        return orth_reproject<T>(h, cx, ar, ar.Y, m, m, p, bp, Qbar, kprev, ldqb, Qi, ldqb);
+    }
     int rc = orth_reproject<T>(h, cx, ar, ar.Y, m, m, p, bp, nullptr, 0, m, ar.Qt, m);     // line (3)
     if (rc != RQB_OK) return rc;
     for (int j = 0; j < h->cfg.power; ++j) {
@@ -651,7 +667,9 @@ const char* rqb_status_string(int status) {
 int rqb_create(rqb_handle* out, const rqb_config* cfg) {
     if (!out || !cfg) return RQB_ERR_INVALID;
     *out = nullptr;
-    if ((cfg->flags & ~RQB_FLAG_PHASE_TIMING) != 0 || cfg->max_rank < 0 || cfg->power < 0) return RQB_ERR_INVALID;
+    if ((cfg->flags & ~(RQB_FLAG_PHASE_TIMING | RQB_FLAG_SKIP_INNER_ORTH)) != 0 || cfg->max_rank < 0 ||
+        cfg->power < 0)
+        return RQB_ERR_INVALID;
     if (cfg->dtype != RQB_F64 && cfg->dtype != RQB_F32 && cfg->dtype != RQB_BF16) return RQB_ERR_INVALID;
     if (cfg->prec != RQB_PREC_NATIVE && cfg->prec != RQB_PREC_TF32X3 && cfg->prec != RQB_PREC_BF16)
         return RQB_ERR_INVALID;

@@ -226,3 +226,48 @@ def test_power_scheme_adaptive(orc, rqb_lib):
     assert rc == rqb_lib.RQB_OK
     check_rank(k, ro, eps, b, rel_band=1e-6)
     assert abs(resid(A, Q, B) - resid(A, ro.Q, ro.B)) <= 1e-10 * resid(A, ro.Q, ro.B)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("P", [1, 2])
+def test_power_scheme_without_inner_orth(orc, rqb_lib, dtype, P):
+    """Sec. 5.4 variant (RQB_FLAG_SKIP_INNER_ORTH): Y = (A A^T)^P A Omega_i and one
+    orth per block.  Slow decay s_j = (1 + j)^(-1/2), so the panel's condition
+    number, which grows as (sigma_1 / sigma_b)^(2P+1) within a block, stays inside
+    CholeskyQR2's range; compared with the oracle's variant on the same Omega."""
+    m, n, b, k = 700, 500, 32, 128
+    s = (1.0 + np.arange(n)) ** -0.5
+    A = inputs.usv(m, n, s, seed=79)
+    if dtype == torch.float32:
+        A = A.astype(np.float32).astype(np.float64)
+    prec = 64 if dtype == torch.float64 else 32
+    ro = orc.randqb_b(A, 0.0, b, seed=3, max_rank=k, fixed_rank=True, power=P, skip_inner_orth=True,
+                      omega_prec=prec)
+    Q, B, kk, rc, st = _factor(rqb_lib, A, 0.0, b, dtype, seed=3, max_rank=k, fixed_rank=True, power=P,
+                               flags=rqb_lib.RQB_FLAG_SKIP_INNER_ORTH)
+    assert rc == rqb_lib.RQB_OK and kk == k == ro.k
+    nA = np.linalg.norm(A)
+    if dtype == torch.float64:
+        assert abs(resid(A, Q, B) - resid(A, ro.Q, ro.B)) <= 1e-9 * resid(A, ro.Q, ro.B)
+        assert orth_err(Q) <= 1e-12
+    else:
+        assert abs(resid(A, Q, B) - resid(A, ro.Q, ro.B)) <= 1e-5 * nA
+        assert orth_err(Q) <= 1e-5
+    # blocked: skipping the inner orth loses nothing against Fig. randQB_pb (Sec. 6.3)
+    rf = orc.randqb_b(A, 0.0, b, seed=3, max_rank=k, fixed_rank=True, power=P, omega_prec=prec)
+    assert abs(resid(A, Q, B) - resid(A, rf.Q, rf.B)) <= 1e-3 * resid(A, rf.Q, rf.B)
+
+
+def test_power_scheme_without_inner_orth_adaptive(orc, rqb_lib):
+    m, n, b = 900, 600, 40
+    s = (1.0 + np.arange(n)) ** -1.0
+    A = inputs.usv(m, n, s, seed=80)
+    eps = 5e-2 * np.linalg.norm(A)
+    ro = orc.randqb_b(A, eps, b, seed=1, power=1, skip_inner_orth=True)
+    Q, B, k, rc, st = _factor(rqb_lib, A, eps, b, torch.float64, seed=1, power=1,
+                              flags=rqb_lib.RQB_FLAG_SKIP_INNER_ORTH)
+    assert rc == rqb_lib.RQB_OK
+    check_rank(k, ro, eps, b, rel_band=1e-6)
+    if k == ro.k:
+        assert abs(resid(A, Q, B) - resid(A, ro.Q, ro.B)) <= 1e-9 * resid(A, ro.Q, ro.B)
+    assert orth_err(Q) <= 1e-12

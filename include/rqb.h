@@ -162,10 +162,12 @@ int rqb_factor_host(rqb_handle h, const void* A_host, int64_t m, int64_t n, int6
                     double eps, int64_t b, uint64_t seed,
                     void* Q_host, int64_t ldq_host, void* B_host, int64_t ldb_host, int64_t* k);
 
-/* randQB_b for `count` independent FP32 matrices of any sizes in one
- * persistent launch (captured in a CUDA graph): each CTA takes the next matrix
- * (largest m n first) from a device work counter and runs Fig. randQB_b on it
- * end to end, so no CTA ever waits on another.  Per matrix t (host arrays):
+/* randQB_b (Fig. randQB_b) for `count` independent FP32 matrices of any
+ * sizes.  All matrices advance block by block together: block i of every
+ * still-active matrix is one sequence of grouped launches covering the tiles
+ * of all of them (largest matrices first), with each matrix's k, E_i and stop
+ * decision kept on the device; blocks run in chunks of eight, each chunk one
+ * captured CUDA graph.  Per matrix t (host arrays):
  *   A[t]   device pointer, m[t] x n[t], leading dim lda[t] >= m[t]
  *   eps[t] absolute tolerance
  * Shared: b (1 <= b <= 32), seed (each matrix uses the same Omega stream, its
@@ -173,8 +175,9 @@ int rqb_factor_host(rqb_handle h, const void* A_host, int64_t m, int64_t n, int6
  * device pointers valid until the next batched call or rqb_destroy):
  *   Q[t], ldq[t], B[t], ldb[t], k[t], status[t] (RQB_OK, RQB_NOT_CONVERGED,
  *   RQB_ERR_BREAKDOWN or RQB_ERR_NONFINITE per matrix).
- * The handle must be FP32 with power = 0.  Returns RQB_OK when the launch ran
- * (per-matrix results in status), else an error. */
+ * The handle must be FP32 with power = 0.  Workspace: a residual copy of
+ * every matrix (sum of m[t] n[t] floats) besides the outputs.  Returns RQB_OK
+ * when the launches ran (per-matrix results in status), else an error. */
 int rqb_factor_batched(rqb_handle h, int64_t count, const void* const* A, const int64_t* m,
                        const int64_t* n, const int64_t* lda, const double* eps, int64_t b,
                        uint64_t seed, const void** Q, int64_t* ldq, const void** B, int64_t* ldb,

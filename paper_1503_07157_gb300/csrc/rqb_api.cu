@@ -1245,7 +1245,7 @@ extern "C" int rqb_factor_batched(rqb_handle h, int64_t count, const void* const
                                           &h->bat_work_bytes, &ms, &launches);
     h->have_factor = false;
     h->stats.kernel_launches = launches;
-    h->stats.phase_ms[RQB_PHASE_SKETCH] = ms;   // the whole persistent launch
+    h->stats.phase_ms[RQB_PHASE_SKETCH] = ms;   // the whole batch
     h->stats.phase_calls[RQB_PHASE_SKETCH] = 1;
     return finish(h, rc);
 }

@@ -1,18 +1,27 @@
-// rqb_batched.cu -- randQB_b for many independent matrices of uneven sizes in
-// one persistent launch (FP32, block size b <= 32).
+// rqb_batched.cu -- randQB_b for many independent FP32 matrices of uneven
+// sizes (block size b <= 32), grouped by block index.
 //
-// Each CTA repeatedly takes the next matrix from a device work counter (the
-// host orders the matrices by decreasing m n, so the largest start first) and
-// runs the whole of Fig. randQB_b on it with CTA-level tile routines:
-//   line (2)  Omega_i into an L2-resident per-CTA buffer (Philox + Box-Muller)
-//   line (3)  Y = A Omega_i (first block; later blocks from the fused pass)
-//   (3), (3') CholeskyQR2 with re-projection, Gram in FP32 pairs promoted to
-//             FP64, Cholesky in FP64
-//   line (4)  B_i = Q_i^T A, ||B_i||^2 in FP64
-//   line (6)  stop on E_i <= eps^2 outside the FP32 rounding band, else on
-//             the direct ||A^(i)||^2 of the fused pass
-//   line (5)  A - Q_i B_i fused with the next block's sketch
-// Nothing waits on another CTA, so there is no inter-CTA synchronisation.
+// All matrices advance through the blocks of Fig. randQB_b together: block i
+// of every still-active matrix is one sequence of grouped launches, each of
+// which covers the tiles of all active matrices (work-item tables built once
+// on the host), so a large matrix spreads over many SMs while small ones fill
+// the rest of the GPU.  Per block i:
+//   line (2)   Omega_i: every matrix uses global columns i b .. i b + 31 of one
+//              Omega (its first n_t rows), drawn once per block
+//   line (3)   Y = A Omega_1 (block 1; later blocks come out of the update)
+//   (3), (3')  CholeskyQR2 with re-projection: exact FP32 Gram promoted to
+//              FP64 and FP64 Cholesky per matrix (one CTA each), Y R^-1 and
+//              Y - Qbar C on 128-row tiles, C = Qbar^T Y on 128-column tiles
+//              with FP64 accumulation
+//   line (4)   B_i = Q_i^T A^(i-1) on 128-column tiles, ||B_i||^2 (FP64)
+//   line (6)   per-matrix test on E_i outside the FP32 rounding band, else on
+//              the direct ||A^(i)||^2 of the update
+//   line (5)   A^(i) = A^(i-1) - Q_i B_i fused with the next block's sketch
+// The per-matrix state (k, E, flags, status) lives on the device; the items of
+// finished matrices return at once.  Blocks are launched in chunks of eight,
+// each chunk captured into one CUDA graph; the host reads the number of
+// active matrices between chunks.  Partial sums are combined per matrix in a
+// fixed order, so results are bitwise repeatable.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -24,26 +33,12 @@ namespace rqb {
 namespace batched {
 
 constexpr int NT = 256;          // threads per CTA
-constexpr int BP = 32;           // padded block width
-constexpr int RB = 256;          // rows per row tile
-constexpr int KC = 16;           // reduction chunk
-
-struct MatDesc {
-    const float* A;
-    float* W;        // residual copy (ld ldw)
-    float* Q;        // m x kcap (ld ldq)
-    float* B;        // kcap x n (ld ldb)
-    int64_t m, n, lda, ldw, ldq, ldb, kcap;
-    double eps2;
-};
-
-struct MatOut {
-    int64_t k;
-    int32_t status;
-    int32_t blocks;
-    double normA2;
-    double E;
-};
+constexpr int BP = 32;           // padded block width (b <= 32)
+constexpr int RB = 256;          // staging rows of the per-matrix Gram
+constexpr int KC = 16;
+constexpr int TR = 128;          // rows per row item
+constexpr int TC = 128;          // columns per column item
+constexpr int KCH = 32;          // reduction chunk of the grouped products
 
 struct Smem {
     float tA[KC][RB + 4];        // X chunk: KC reduction rows x RB outputs
@@ -67,136 +62,40 @@ __device__ __forceinline__ double cta_sum(double v, Smem& s) {
     return t;   // every thread gets the same value
 }
 
-// Out (rows x nout, ld ldo) = alpha * X (rows x K) * C (K x BP) + beta * Yin,
-// C(k, j) = C[k * csk + j * csj].  Thread (ty, tx): rows ty*8..+7, cols tx*4..+3
-// of each 256-row tile.  Optionally ||X||_F^2 into *nrm (FP64, CTA-uniform).
-__device__ void cta_nn(Smem& s, int64_t rows, int64_t K, const float* X, int64_t ldx, const float* C, int64_t csk,
-                       int64_t csj, float* Out, int64_t ldo, int nout, float alpha, float beta, const float* Yin,
-                       int64_t ldyin, double* nrm) {
-    const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
-    double nacc = 0.0;
-    const bool want_norm = (nrm != nullptr);
-    for (int64_t r0 = 0; r0 < rows; r0 += RB) {
-        float acc[8][4];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-        for (int64_t k0 = 0; k0 < K; k0 += KC) {
-            // X chunk: KC columns x RB rows (column-major runs of RB rows)
-            float sq = 0.f;
-            for (int v = tid; v < KC * RB; v += NT) {
-                const int kk = v / RB, rr = v % RB;
-                const int64_t r = r0 + rr, k = k0 + kk;
-                const float x = (r < rows && k < K) ? X[r + k * ldx] : 0.f;
-                s.tA[kk][rr] = x;
-                sq = fmaf(x, x, sq);
-            }
-            if (want_norm) nacc += (double)sq;
-            for (int v = tid; v < KC * BP; v += NT) {
-                const int kk = v / BP, j = v % BP;
-                const int64_t k = k0 + kk;
-                s.tB[kk][j] = (k < K) ? C[k * csk + j * csj] : 0.f;
-            }
-            __syncthreads();
-#pragma unroll 4
-            for (int kk = 0; kk < KC; ++kk) {
-                float a[8], b[4];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) a[i] = s.tA[kk][ty * 8 + i];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) b[j] = s.tB[kk][tx * 4 + j];
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-            }
-            __syncthreads();
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int64_t r = r0 + ty * 8 + i;
-            if (r >= rows) continue;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = tx * 4 + j;
-                if (c >= nout) continue;
-                float v = alpha * acc[i][j];
-                if (beta != 0.f) v = fmaf(beta, Yin[r + (int64_t)c * ldyin], v);
-                Out[r + (int64_t)c * ldo] = v;
-            }
-        }
-    }
-    __syncthreads();   // Out is read by the next routine
-    if (nrm) {
-        const double t = cta_sum(nacc, s);
-        if (threadIdx.x == 0) *nrm = t;
-        __syncthreads();
-    }
-}
 
-// Out (P x BP, FP64, ld ldo) = X^T Y over `rows` rows; X rows x P (ld ldx),
-// Y rows x BP (ld ldy).  FP32 products summed over 128-row chunks, promoted
-// to FP64 after each chunk.  Thread (ty, tx): P entries ty*8..+7 of each 256-wide
-// P tile, columns tx*4..+3.
-__device__ void cta_tn(Smem& s, int64_t rows, int64_t P, const float* X, int64_t ldx, const float* Y, int64_t ldy,
-                       double* Out, int64_t ldo) {
-    const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
-    for (int64_t p0 = 0; p0 < P; p0 += RB) {
-        double acc2[8][4];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc2[i][j] = 0.0;
-        float acc[8][4];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-        int chunk = 0;
-        for (int64_t k0 = 0; k0 < rows; k0 += KC) {
-            for (int v = tid; v < KC * RB; v += NT) {
-                const int pp = v / KC, kk = v % KC;      // column-major runs of KC rows
-                const int64_t pc = p0 + pp, r = k0 + kk;
-                s.tA[kk][pp] = (pc < P && r < rows) ? X[r + pc * ldx] : 0.f;
-            }
-            for (int v = tid; v < KC * BP; v += NT) {
-                const int j = v / KC, kk = v % KC;
-                const int64_t r = k0 + kk;
-                s.tB[kk][j] = (r < rows) ? Y[r + (int64_t)j * ldy] : 0.f;
-            }
-            __syncthreads();
-#pragma unroll 4
-            for (int kk = 0; kk < KC; ++kk) {
-                float a[8], b[4];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) a[i] = s.tA[kk][ty * 8 + i];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) b[j] = s.tB[kk][tx * 4 + j];
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-            }
-            if (++chunk == 8 || k0 + KC >= rows) {   // promote every 128 rows
-                chunk = 0;
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) { acc2[i][j] += (double)acc[i][j]; acc[i][j] = 0.f; }
-            }
-            __syncthreads();
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int64_t pc = p0 + ty * 8 + i;
-            if (pc >= P) continue;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) Out[pc + (int64_t)(tx * 4 + j) * ldo] = acc2[i][j];
-        }
-    }
-    __syncthreads();
-}
+
+// Per-matrix descriptors (built on the host) and device state.
+struct GMat {
+    const float* A;      // caller's matrix (ld lda)
+    float* W;            // residual A^(i) (ld ldw)
+    float* Q;            // m x kcap output (ld ldq)
+    float* B;            // kcap x n output (ld ldb)
+    float* Y;            // m x BP panel (ld ldw)
+    float* Y1;           // m x BP panel scratch (ld ldw)
+    float* Cc;           // kcap x BP re-projection coefficients (ld kcap)
+    float* Rinv;         // BP x BP, row-major
+    int64_t m, n, lda, ldw, ldq, ldb, kcap;
+    double eps2;
+    int rows_begin, rows_end;   // items of this matrix in the row table
+    int proj_begin, proj_end;   // ... in the projection table
+};
+
+struct GState {
+    double normA2, E, tau, D;
+    int64_t k;           // columns of Q done before the current block
+    int64_t knext;       // k + p once the current block is accepted
+    int p;               // width of the current block
+    int active;          // still factoring
+    int pending;         // the current block's update must run
+    int flag;            // stop decision of the current block (StopFlag)
+    int status;
+    int blocks;
+};
+
+struct Item {
+    int t;               // matrix
+    int tile;            // row tile (rows 128 tile ..) or column tile
+};
 
 // s.G (BP x BP, FP64) = Y^T Y over `rows` rows with error-free FP32
 // accumulation (exact products, TwoSum into an FP32 pair, promoted to FP64
@@ -289,254 +188,489 @@ __device__ bool cta_chol_inv(Smem& s, int p, double tol) {
     return true;
 }
 
-// Omega_i (n x BP, row-major, columns >= p zero): global columns col0 .. col0 + p - 1.
-__device__ void cta_omega(int64_t n, int64_t col0, int p, uint64_t seed, float* Om) {
-    for (int64_t e = threadIdx.x; e < n * BP; e += NT) {
-        const int64_t r = e / BP;
-        const int c = (int)(e % BP);
-        Om[e] = (c < p) ? gaussian_f32(seed, r, col0 + c) : 0.f;
-    }
-    __syncthreads();
-}
 
-// Line (5) fused with line (3) of the next block:  Wdst = Wsrc - Q_i B_i over the
-// whole matrix and Y (m x BP) = Wdst Omega; returns ||Wdst||_F^2 (CTA-uniform).
-// Per 256-row tile: Q_i rows staged in shared memory; per KC-column chunk the
-// rank-p update is formed (thread: rows ty*8..+7, columns tx*2..+1 of the
-// chunk), written back, staged transposed and multiplied by the Omega chunk.
-__device__ double cta_downdate_sketch(Smem& s, float (*Qs)[RB + 4], float (*Bs)[KC + 1], int64_t m, int64_t n, int p,
-                                      const float* Wsrc, int64_t ldws, const float* Qi, int64_t ldq, const float* Bi,
-                                      int64_t ldb, const float* Om, float* Wdst, int64_t ldwd, float* Y) {
+// ---------------------------------------------------------------------------
+// Row items: 128-row tiles, output 128 x BP.  Thread (ty, tx) owns rows
+// ty*4 .. +3 and columns tx*4 .. +3 of the tile.
+
+// acc += X(r0 .. r0+127, 0 .. K) C(0 .. K, 0 .. BP), X column-major (ld ldx),
+// C(k, j) = C[k * csk + j * csj]; sq (if non-null) += sum of the squares of
+// the X entries this thread loaded.
+__device__ __forceinline__ void rows_product(float (&acc)[4][4], int64_t rows, int64_t r0, int64_t K, const float* X,
+                                             int64_t ldx, const float* C, int64_t csk, int64_t csj,
+                                             float (*Xs)[TR + 4], float (*Cs)[BP + 4], double* sq) {
     const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
-    double nacc = 0.0;
-    for (int64_t r0 = 0; r0 < m; r0 += RB) {
-        for (int v = tid; v < BP * RB; v += NT) {
-            const int t = v / RB, rr = v % RB;
-            const int64_t r = r0 + rr;
-            Qs[t][rr] = (t < p && r < m) ? Qi[r + (int64_t)t * ldq] : 0.f;
-        }
-        float yacc[8][4];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) yacc[i][j] = 0.f;
-        for (int64_t c0 = 0; c0 < n; c0 += KC) {
-            for (int v = tid; v < BP * KC; v += NT) {
-                const int cc = v / BP, t = v % BP;
-                const int64_t c = c0 + cc;
-                Bs[t][cc] = (t < p && c < n) ? Bi[t + c * ldb] : 0.f;
-            }
-            for (int v = tid; v < KC * BP; v += NT) {
-                const int cc = v / BP, j = v % BP;
-                const int64_t c = c0 + cc;
-                s.tB[cc][j] = (c < n) ? Om[c * BP + j] : 0.f;
-            }
-            __syncthreads();
-            float pacc[8][2];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) { pacc[i][0] = 0.f; pacc[i][1] = 0.f; }
-            for (int t = 0; t < BP; ++t) {
-                const float b0 = Bs[t][tx * 2], b1 = Bs[t][tx * 2 + 1];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float a = Qs[t][ty * 8 + i];
-                    pacc[i][0] = fmaf(a, b0, pacc[i][0]);
-                    pacc[i][1] = fmaf(a, b1, pacc[i][1]);
+    const bool vec = ((reinterpret_cast<uintptr_t>(X) & 15u) == 0) && (ldx % 4 == 0);
+    for (int64_t k0 = 0; k0 < K; k0 += KCH) {
+        __syncthreads();
+        float sqf = 0.f;
+        for (int v = tid; v < KCH * (TR / 4); v += NT) {
+            const int kk = v / (TR / 4), rr = (v % (TR / 4)) * 4;
+            const int64_t k = k0 + kk, r = r0 + rr;
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k < K && r < rows) {
+                const float* src = X + r + k * ldx;
+                if (vec && r + 4 <= rows) {
+                    x = *reinterpret_cast<const float4*>(src);
+                } else {
+                    x.x = src[0];
+                    if (r + 1 < rows) x.y = src[1];
+                    if (r + 2 < rows) x.z = src[2];
+                    if (r + 3 < rows) x.w = src[3];
                 }
             }
-            float sq = 0.f;
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int cc = tx * 2 + j;
-                const int64_t c = c0 + cc;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int rr = ty * 8 + i;
-                    const int64_t r = r0 + rr;
-                    float w = 0.f;
-                    if (r < m && c < n) {
-                        w = Wsrc[r + c * ldws] - pacc[i][j];
-                        Wdst[r + c * ldwd] = w;
-                    }
-                    sq = fmaf(w, w, sq);
-                    s.tA[cc][rr] = w;
-                }
-            }
-            nacc += (double)sq;
-            __syncthreads();
-#pragma unroll 4
-            for (int kk = 0; kk < KC; ++kk) {
-                float a[8], b[4];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) a[i] = s.tA[kk][ty * 8 + i];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) b[j] = s.tB[kk][tx * 4 + j];
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) yacc[i][j] = fmaf(a[i], b[j], yacc[i][j]);
-            }
-            __syncthreads();
+            *reinterpret_cast<float4*>(&Xs[kk][rr]) = x;
+            sqf = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, sqf))));
         }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int64_t r = r0 + ty * 8 + i;
-            if (r >= m) continue;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) Y[r + (int64_t)(tx * 4 + j) * m] = yacc[i][j];
+        if (sq) *sq += (double)sqf;
+        for (int e = tid; e < KCH * BP; e += NT) {
+            const int kk = e / BP, j = e % BP;
+            const int64_t k = k0 + kk;
+            Cs[kk][j] = (k < K) ? C[k * csk + (int64_t)j * csj] : 0.f;
         }
         __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < KCH; ++kk) {
+            const float4 a = *reinterpret_cast<const float4*>(&Xs[kk][ty * 4]);
+            const float4 b = *reinterpret_cast<const float4*>(&Cs[kk][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
     }
-    return cta_sum(nacc, s);
 }
 
-// B_i (p x n, written into B at row offset, ld ldb) = Q_i^T W; returns ||B_i||^2.
-// Thread (ty, tx): W columns ty*8..+7 of each 256-column tile, rows tx*4..+3 of B_i.
-__device__ double cta_project(Smem& s, int64_t m, int64_t n, int p, const float* Qi, int64_t ldq, const float* W,
-                              int64_t ldw, float* Bi, int64_t ldb) {
+// Out(r, j) = sub ? Out(r, j) - acc : acc for rows < `rows`, columns < BP;
+// columns >= ncols are written as zero.
+__device__ __forceinline__ void rows_store(const float (&acc)[4][4], int64_t rows, int64_t r0, float* Out, int64_t ldo,
+                                           int ncols, bool sub) {
     const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
-    double nb = 0.0;
-    for (int64_t c0 = 0; c0 < n; c0 += RB) {
-        float acc[8][4];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 4; ++i) {
+        const int64_t r = r0 + ty * 4 + i;
+        if (r >= rows) continue;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-        for (int64_t k0 = 0; k0 < m; k0 += KC) {
-            for (int v = tid; v < KC * RB; v += NT) {
-                const int cc = v / KC, kk = v % KC;
-                const int64_t c = c0 + cc, r = k0 + kk;
-                s.tA[kk][cc] = (c < n && r < m) ? W[r + c * ldw] : 0.f;
-            }
-            for (int v = tid; v < KC * BP; v += NT) {
-                const int j = v / KC, kk = v % KC;
-                const int64_t r = k0 + kk;
-                s.tB[kk][j] = (j < p && r < m) ? Qi[r + (int64_t)j * ldq] : 0.f;
-            }
-            __syncthreads();
-#pragma unroll 4
-            for (int kk = 0; kk < KC; ++kk) {
-                float a[8], b[4];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) a[i] = s.tA[kk][ty * 8 + i];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) b[j] = s.tB[kk][tx * 4 + j];
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-            }
-            __syncthreads();
+        for (int j = 0; j < 4; ++j) {
+            const int c = tx * 4 + j;
+            float* o = Out + r + (int64_t)c * ldo;
+            *o = (c < ncols) ? (sub ? *o - acc[i][j] : acc[i][j]) : 0.f;
         }
+    }
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int64_t c = c0 + ty * 8 + i;
-            if (c >= n) continue;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < NT / 32; ++w) t += red[w];
+    return t;
+}
+
+enum RowOp { kRowSketch0 = 0, kRowMulR1 = 1, kRowSubQC = 2, kRowMulR2 = 3 };
+
+// kRowSketch0  Y = A Omega_1 (columns >= p zero), part = ||A tile||_F^2
+// kRowMulR1    Y1 = Y R^-1
+// kRowSubQC    Y1 -= Qbar C (k > 0)
+// kRowMulR2    Q_i = Y1 R^-1 (columns k .. k + p of Q)
+template <int OP>
+__global__ void __launch_bounds__(NT) k_rows(const GMat* __restrict__ mats, const GState* __restrict__ st,
+                                             const Item* __restrict__ items, int b, const float* __restrict__ Om,
+                                             double* __restrict__ part) {
+    __shared__ __align__(16) float Xs[KCH][TR + 4];
+    __shared__ __align__(16) float Cs[KCH][BP + 4];
+    __shared__ double red[NT / 32];
+    const Item it = items[blockIdx.x];
+    const GMat& d = mats[it.t];
+    const int64_t r0 = (int64_t)it.tile * TR;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    if (OP == kRowSketch0) {
+        const int p = (int)min((int64_t)b, d.kcap);
+        double sq = 0.0;
+        rows_product(acc, d.m, r0, d.n, d.A, d.lda, Om, BP, 1, Xs, Cs, &sq);
+        rows_store(acc, d.m, r0, d.Y, d.ldw, p, false);
+        const double t = block_sum_d(sq, red);
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
+        return;
+    }
+    const GState s = st[it.t];
+    if (!s.active) return;
+    if (OP == kRowMulR1) {
+        rows_product(acc, d.m, r0, BP, d.Y, d.ldw, d.Rinv, BP, 1, Xs, Cs, nullptr);
+        rows_store(acc, d.m, r0, d.Y1, d.ldw, BP, false);
+    } else if (OP == kRowSubQC) {
+        if (s.k == 0) return;
+        rows_product(acc, d.m, r0, s.k, d.Q, d.ldq, d.Cc, 1, d.kcap, Xs, Cs, nullptr);
+        rows_store(acc, d.m, r0, d.Y1, d.ldw, BP, true);
+    } else {
+        rows_product(acc, d.m, r0, BP, d.Y1, d.ldw, d.Rinv, BP, 1, Xs, Cs, nullptr);
+        // Q has kcap columns: only the p columns of this block are written
+        const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
+        float* Qi = d.Q + s.k * d.ldq;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t r = r0 + ty * 4 + i;
+            if (r >= d.m) continue;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int t = tx * 4 + j;
-                if (t >= p) continue;
-                Bi[t + c * ldb] = acc[i][j];
-                nb += (double)acc[i][j] * (double)acc[i][j];
+                const int c = tx * 4 + j;
+                if (c < s.p) Qi[r + (int64_t)c * d.ldq] = acc[i][j];
             }
         }
     }
-    return cta_sum(nb, s);
 }
 
-// Per-CTA global scratch for the matrix being factored.
-struct SlotBuf {
-    float* Om;   // n_max x BP row-major
-    float* Y;    // m_max x BP
-    float* Y1;   // m_max x BP
-    float* W;    // m_max x n_max residual (ld m)
-    float* Cc;   // kcap_max x BP
-    double* Cd;  // kcap_max x BP
-};
-
-// Lines (3), (3'): Qout (p columns) from Y (BP columns, zero beyond p) and
-// Qbar (kprev columns): CholeskyQR, re-projection, CholeskyQR.
-__device__ bool cta_panel(Smem& s, int64_t m, int p, const float* Y, float* Y1, const float* Qbar, int64_t kprev,
-                          int64_t ldq, double* Cd, float* Cc, float* Qout) {
-    cta_gram_exact(s, m, Y, m);
-    if (!cta_chol_inv(s, p, 1e-14)) return false;
-    cta_nn(s, m, BP, Y, m, &s.Rinv[0][0], BP + 1, 1, Y1, m, BP, 1.f, 0.f, nullptr, 0, nullptr);
-    if (kprev > 0) {
-        cta_tn(s, m, kprev, Qbar, ldq, Y1, m, Cd, kprev);
-        for (int64_t e = threadIdx.x; e < kprev * BP; e += NT) Cc[e] = (float)Cd[e];
-        __syncthreads();
-        cta_nn(s, m, kprev, Qbar, ldq, Cc, 1, kprev, Y1, m, BP, -1.f, 1.f, Y1, m, nullptr);
+// Line (5) fused with the next sketch on one 128-row tile:
+//   W(rows, :) = Wsrc(rows, :) - Q_i(rows, :) B_i,  Y(rows, :) = W(rows, :) Omega_{i+1}
+// column chunk by column chunk; part = ||W(rows, :)||_F^2.  Wsrc is A in the
+// first block.  Runs for matrices whose block i was accepted or is ambiguous.
+__global__ void __launch_bounds__(NT) k_rows_update(const GMat* __restrict__ mats, const GState* __restrict__ st,
+                                                    const Item* __restrict__ items, int b, int first,
+                                                    const float* __restrict__ Om_next, double* __restrict__ part) {
+    __shared__ __align__(16) float Qs[BP][TR + 4];    // Qs[t][r] = Q_i(r0 + r, t)
+    __shared__ __align__(16) float Bs[BP][KCH + 4];   // Bs[t][c] = B_i(t, c0 + c)
+    __shared__ __align__(16) float Ws[KCH][TR + 4];   // Ws[c][r] = W(r0 + r, c0 + c)
+    __shared__ __align__(16) float Os[KCH][BP + 4];   // Os[c][j] = Omega_{i+1}(c0 + c, j)
+    __shared__ double red[NT / 32];
+    const Item it = items[blockIdx.x];
+    const GState s = st[it.t];
+    if (!s.pending) return;
+    const GMat& d = mats[it.t];
+    const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
+    const int64_t m = d.m, n = d.n, r0 = (int64_t)it.tile * TR;
+    const float* Wsrc = first ? d.A : d.W;
+    const int64_t ldws = first ? d.lda : d.ldw;
+    const bool vsrc = ((reinterpret_cast<uintptr_t>(Wsrc) & 15u) == 0) && (ldws % 4 == 0);
+    const float* Qi = d.Q + s.k * d.ldq;
+    const float* Bi = d.B + s.k;
+    const int p = s.p;
+    const int pn = (int)max((int64_t)0, min((int64_t)b, d.kcap - s.knext));
+    for (int v = tid; v < BP * (TR / 4); v += NT) {
+        const int t = v / (TR / 4), rr = (v % (TR / 4)) * 4;
+        const int64_t r = r0 + rr;
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t < p && r < m) {
+            const float* src = Qi + r + (int64_t)t * d.ldq;
+            if (r + 4 <= m) {
+                q = *reinterpret_cast<const float4*>(src);   // ldq is a multiple of 4
+            } else {
+                q.x = src[0];
+                if (r + 1 < m) q.y = src[1];
+                if (r + 2 < m) q.z = src[2];
+            }
+        }
+        *reinterpret_cast<float4*>(&Qs[t][rr]) = q;
     }
-    cta_gram_exact(s, m, Y1, m);
-    if (!cta_chol_inv(s, p, 1e-14)) return false;
-    cta_nn(s, m, BP, Y1, m, &s.Rinv[0][0], BP + 1, 1, Qout, ldq, p, 1.f, 0.f, nullptr, 0, nullptr);
-    return true;
+    float yacc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) yacc[i][j] = 0.f;
+    double sq = 0.0;
+    for (int64_t c0 = 0; c0 < n; c0 += KCH) {
+        __syncthreads();
+        for (int e = tid; e < KCH * BP; e += NT) {
+            const int c = e / BP, t = e % BP;
+            const int64_t cc = c0 + c;
+            Bs[t][c] = (t < p && cc < n) ? Bi[t + cc * d.ldb] : 0.f;
+            Os[c][t] = (cc < n) ? Om_next[cc * BP + t] : 0.f;
+        }
+        for (int v = tid; v < KCH * (TR / 4); v += NT) {
+            const int c = v / (TR / 4), rr = (v % (TR / 4)) * 4;
+            const int64_t cc = c0 + c, r = r0 + rr;
+            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (cc < n && r < m) {
+                const float* src = Wsrc + r + cc * ldws;
+                if (vsrc && r + 4 <= m) {
+                    w = *reinterpret_cast<const float4*>(src);
+                } else {
+                    w.x = src[0];
+                    if (r + 1 < m) w.y = src[1];
+                    if (r + 2 < m) w.z = src[2];
+                    if (r + 3 < m) w.w = src[3];
+                }
+            }
+            *reinterpret_cast<float4*>(&Ws[c][rr]) = w;
+        }
+        __syncthreads();
+        // P = Q_i(tile) B_i(:, chunk); W = Wsrc - P on this thread's 4 x 4 entries
+        float pacc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) pacc[i][j] = 0.f;
+#pragma unroll 8
+        for (int t = 0; t < BP; ++t) {
+            const float4 a = *reinterpret_cast<const float4*>(&Qs[t][ty * 4]);
+            const float4 bb = *reinterpret_cast<const float4*>(&Bs[t][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) pacc[i][j] = fmaf(av[i], bv[j], pacc[i][j]);
+        }
+        float sqf = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = tx * 4 + j;
+            const int64_t cc = c0 + c;
+            float w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                w[i] = Ws[c][ty * 4 + i] - pacc[i][j];
+                if (cc >= n || r0 + ty * 4 + i >= m) w[i] = 0.f;
+                sqf = fmaf(w[i], w[i], sqf);
+                Ws[c][ty * 4 + i] = w[i];
+            }
+            if (cc < n) {
+                const int64_t r = r0 + ty * 4;
+                float* dst = d.W + r + cc * d.ldw;
+                if (r + 4 <= m) {
+                    *reinterpret_cast<float4*>(dst) = make_float4(w[0], w[1], w[2], w[3]);   // ldw % 4 == 0
+                } else {
+                    for (int i = 0; i < 4; ++i)
+                        if (r + i < m) dst[i] = w[i];
+                }
+            }
+        }
+        sq += (double)sqf;
+        __syncthreads();
+        // Y += W(tile, chunk) Omega_{i+1}(chunk, :)
+#pragma unroll 8
+        for (int c = 0; c < KCH; ++c) {
+            const float4 a = *reinterpret_cast<const float4*>(&Ws[c][ty * 4]);
+            const float4 o = *reinterpret_cast<const float4*>(&Os[c][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, ov[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) yacc[i][j] = fmaf(av[i], ov[j], yacc[i][j]);
+        }
+    }
+    rows_store(yacc, m, r0, d.Y, d.ldw, pn, false);
+    const double t = block_sum_d(sq, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-__global__ void __launch_bounds__(NT, 1)
-k_batched(const MatDesc* __restrict__ descs, const int* __restrict__ order, int count, const SlotBuf* __restrict__ slots,
-          MatOut* __restrict__ outs, int b, uint64_t seed, int* counter) {
-    extern __shared__ __align__(16) float dyn[];
-    float (*Qs)[RB + 4] = reinterpret_cast<float (*)[RB + 4]>(dyn);
-    float (*Bs)[KC + 1] = reinterpret_cast<float (*)[KC + 1]>(dyn + BP * (RB + 4));
+// ---------------------------------------------------------------------------
+// Column items: out(j, c) for j < BP and 128 columns c, reduced over the m rows:
+//   kColProject  B_i(j, c) = sum_r Q_i(r, j) Wsrc(r, c), part = ||B_i tile||^2
+//   kColReproj   C(c, j)   = sum_r Qbar(r, c) Y1(r, j), FP64 accumulation
+// Thread (tj, lane) owns j = tj*4 .. +3 and c = lane + 32 q, q < 4.
+enum ColOp { kColProject = 0, kColReproj = 1 };
+
+template <int OP>
+__global__ void __launch_bounds__(NT) k_cols(const GMat* __restrict__ mats, const GState* __restrict__ st,
+                                             const Item* __restrict__ items, int first, double* __restrict__ part) {
+    __shared__ float Ps[KCH][BP + 1];    // Ps[r][j]: Q_i or Y1 rows of the chunk
+    __shared__ float Vs[KCH][TC + 1];    // Vs[r][c]: Wsrc or Qbar columns of the tile
+    __shared__ double red[NT / 32];
+    const Item it = items[blockIdx.x];
+    const GState s = st[it.t];
+    if (!s.active) return;
+    if (OP == kColReproj && s.k == 0) return;
+    const GMat& d = mats[it.t];
+    const int64_t c0 = (int64_t)it.tile * TC;
+    const int64_t ncols = (OP == kColProject) ? d.n : s.k;
+    if (c0 >= ncols) return;
+    const float* P = (OP == kColProject) ? d.Q + s.k * d.ldq : d.Y1;
+    const int64_t ldp = (OP == kColProject) ? d.ldq : d.ldw;
+    const int pw = (OP == kColProject) ? s.p : BP;
+    const float* V = (OP == kColProject) ? (first ? d.A : d.W) : d.Q;
+    const int64_t ldv = (OP == kColProject) ? (first ? d.lda : d.ldw) : d.ldq;
+    const int64_t m = d.m;
+    const int tid = threadIdx.x, tj = tid >> 5, lane = tid & 31;
+    float acc[4][4];
+    double acc2[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { acc[i][q] = 0.f; acc2[i][q] = 0.0; }
+    for (int64_t r0 = 0; r0 < m; r0 += KCH) {
+        __syncthreads();
+        for (int e = tid; e < KCH * BP; e += NT) {         // 32 rows of each of the BP columns
+            const int j = e / KCH, rr = e % KCH;
+            const int64_t r = r0 + rr;
+            Ps[rr][j] = (j < pw && r < m) ? P[r + (int64_t)j * ldp] : 0.f;
+        }
+        for (int e = tid; e < KCH * TC; e += NT) {         // 32 rows of each of the 128 columns
+            const int c = e / KCH, rr = e % KCH;
+            const int64_t r = r0 + rr, cc = c0 + c;
+            Vs[rr][c] = (cc < ncols && r < m) ? V[r + cc * ldv] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int rr = 0; rr < KCH; ++rr) {
+            float a[4], v[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = Ps[rr][tj * 4 + i];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = Vs[rr][lane + 32 * q];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[i][q] = fmaf(a[i], v[q], acc[i][q]);
+        }
+        if (OP == kColReproj) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) { acc2[i][q] += (double)acc[i][q]; acc[i][q] = 0.f; }
+        }
+    }
+    double sq = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int j = tj * 4 + i;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t cc = c0 + lane + 32 * q;
+            if (cc >= ncols) continue;
+            if (OP == kColProject) {
+                if (j < s.p) {
+                    const float bv = acc[i][q];
+                    d.B[(s.k + j) + cc * d.ldb] = bv;
+                    sq += (double)bv * (double)bv;
+                }
+            } else {
+                d.Cc[cc + (int64_t)j * d.kcap] = (float)acc2[i][q];
+            }
+        }
+    }
+    if (OP == kColProject) {
+        const double t = block_sum_d(sq, red);
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Matrix items: one CTA per matrix.
+//   kMatInit    ||A||^2 from the first sketch's partials; state of block 1
+//   kMatPanel1  exact Gram of Y, FP64 Cholesky, R^-1 (first CholeskyQR pass)
+//   kMatPanel2  the same for Y1 (second pass)
+//   kMatStop    E_i -= ||B_i||^2 and the decision of line (6)
+//   kMatDirect  inside the band: the direct ||A^(i)||^2 of the update decides;
+//               advance to the next block
+enum MatOp { kMatInit = 0, kMatPanel1 = 1, kMatPanel2 = 2, kMatStop = 3, kMatDirect = 4 };
+
+template <int OP>
+__global__ void __launch_bounds__(NT, 1) k_mat(const GMat* __restrict__ mats, GState* __restrict__ st, int b,
+                                               const double* __restrict__ rows_part,
+                                               const double* __restrict__ proj_part) {
     __shared__ Smem s;
-    __shared__ int cur;
-    const SlotBuf sl = slots[blockIdx.x];
+    const int t = blockIdx.x;
+    const GMat& d = mats[t];
+    GState g = st[t];
     const double tau_rel = 32.0 * 5.9604644775390625e-08;   // FP32 rounding band of E
-    for (;;) {
-        if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
-        __syncthreads();
-        const int idx = cur;
-        __syncthreads();
-        if (idx >= count) break;
-        const int t = order[idx];
-        const MatDesc d = descs[t];
-        const int64_t m = d.m, n = d.n, kcap = d.kcap;
-        int p = (int)min((int64_t)b, kcap);
-        cta_omega(n, 0, p, seed, sl.Om);
-        cta_nn(s, m, n, d.A, d.lda, sl.Om, BP, 1, sl.Y, m, BP, 1.f, 0.f, nullptr, 0, &s.scal[0]);
-        const double N0 = s.scal[0];
-        double E = N0;
-        const double tau = tau_rel * N0;
-        int64_t k = 0;
-        int blocks = 0, status = RQB_NOT_CONVERGED;
-        const float* Wsrc = d.A;
-        int64_t ldws = d.lda;
-        if (!isfinite(N0)) status = RQB_ERR_NONFINITE;
-        while (status == RQB_NOT_CONVERGED) {
-            p = (int)min((int64_t)b, kcap - k);
-            float* Qi = d.Q + k * d.ldq;
-            float* Bi = d.B + k;
-            if (!cta_panel(s, m, p, sl.Y, sl.Y1, d.Q, k, d.ldq, sl.Cd, sl.Cc, Qi)) {
-                status = RQB_ERR_BREAKDOWN;
-                break;
-            }
-            const double nb = cta_project(s, m, n, p, Qi, d.ldq, Wsrc, ldws, Bi, d.ldb);
-            E -= nb;
-            k += p;
-            ++blocks;
-            const int flag = (E <= d.eps2 - tau) ? kStop : (E > d.eps2 + tau) ? kContinue : kAmbiguous;
-            if (flag == kStop) { status = RQB_OK; break; }
-            if (flag == kContinue && k >= kcap) break;
-            const int pn = (int)min((int64_t)b, max((int64_t)0, kcap - k));
-            cta_omega(n, k, pn, seed, sl.Om);
-            const double D = cta_downdate_sketch(s, Qs, Bs, m, n, p, Wsrc, ldws, Qi, d.ldq, Bi, d.ldb, sl.Om, sl.W, m,
-                                                 sl.Y);
-            Wsrc = sl.W;
-            ldws = m;
-            if (flag == kAmbiguous && D <= d.eps2) { status = RQB_OK; break; }
-            if (k >= kcap) break;
-        }
+    if (OP == kMatInit) {
         if (threadIdx.x == 0) {
-            MatOut o;
-            o.k = k; o.status = status; o.blocks = blocks; o.normA2 = N0; o.E = E;
-            outs[t] = o;
+            double nrm = 0.0;
+            for (int i = d.rows_begin; i < d.rows_end; ++i) nrm += rows_part[i];
+            g.normA2 = nrm;
+            g.E = nrm;
+            g.tau = tau_rel * nrm;
+            g.D = -1.0;
+            g.k = 0;
+            g.knext = 0;
+            g.p = (int)min((int64_t)b, d.kcap);
+            g.pending = 0;
+            g.flag = kContinue;
+            g.blocks = 0;
+            g.active = isfinite(nrm) ? 1 : 0;
+            g.status = isfinite(nrm) ? RQB_NOT_CONVERGED : RQB_ERR_NONFINITE;
+            st[t] = g;
         }
-        __syncthreads();
+        return;
+    }
+    if (!g.active) return;
+    if (OP == kMatPanel1 || OP == kMatPanel2) {
+        cta_gram_exact(s, d.m, OP == kMatPanel1 ? d.Y : d.Y1, d.ldw);
+        const bool ok = cta_chol_inv(s, g.p, 1e-14);
+        if (!ok) {
+            if (threadIdx.x == 0) {
+                g.status = RQB_ERR_BREAKDOWN;
+                g.active = 0;
+                g.pending = 0;
+                st[t] = g;
+            }
+            return;
+        }
+        for (int e = threadIdx.x; e < BP * BP; e += NT) d.Rinv[e] = s.Rinv[e / BP][e % BP];
+        return;
+    }
+    if (threadIdx.x != 0) return;
+    if (OP == kMatStop) {
+        double nb = 0.0;
+        for (int i = d.proj_begin; i < d.proj_end; ++i) nb += proj_part[i];
+        g.E -= nb;
+        g.blocks += 1;
+        g.knext = g.k + g.p;
+        g.flag = (g.E <= d.eps2 - g.tau) ? kStop : (g.E > d.eps2 + g.tau) ? kContinue : kAmbiguous;
+        if (g.flag == kStop) {
+            g.status = RQB_OK;
+            g.active = 0;
+            g.pending = 0;
+            g.k = g.knext;
+        } else if (g.flag == kContinue && g.knext >= d.kcap) {
+            g.active = 0;             // rank cap reached: RQB_NOT_CONVERGED
+            g.pending = 0;
+            g.k = g.knext;
+        } else {
+            g.pending = 1;
+        }
+        st[t] = g;
+        return;
+    }
+    // kMatDirect
+    if (!g.pending) return;
+    double dn = 0.0;
+    for (int i = d.rows_begin; i < d.rows_end; ++i) dn += rows_part[i];
+    g.D = dn;
+    g.k = g.knext;
+    g.pending = 0;
+    if (g.flag == kAmbiguous && dn <= d.eps2) {
+        g.status = RQB_OK;
+        g.active = 0;
+    } else if (g.k >= d.kcap) {
+        g.active = 0;
+    } else {
+        g.p = (int)min((int64_t)b, d.kcap - g.k);
+    }
+    st[t] = g;
+}
+
+// Omega (n_max x BP, row-major): global columns col0 .. col0 + b - 1, zero beyond b.
+__global__ void k_omega_rows(int64_t n_max, int64_t col0, int b, uint64_t seed, float* __restrict__ Om) {
+    const int64_t total = n_max * BP;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / BP;
+        const int c = (int)(e % BP);
+        Om[e] = (c < b) ? gaussian_f32(seed, r, col0 + c) : 0.f;
     }
 }
 
-constexpr size_t kDynSmem = sizeof(float) * ((size_t)BP * (RB + 4) + (size_t)BP * (KC + 1));
+__global__ void k_count_active(const GState* __restrict__ st, int count, int* __restrict__ out) {
+    __shared__ int sh[NT / 32];
+    int c = 0;
+    for (int t = threadIdx.x; t < count; t += NT) c += st[t].active;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < NT / 32; ++w) tot += sh[w];
+        *out = tot;
+    }
+}
 
 }  // namespace batched
 }  // namespace rqb
@@ -559,72 +693,155 @@ static int grow(void** buf, size_t* bytes, size_t need) {
     return RQB_OK;
 }
 
+namespace {
+
+constexpr int kChunk = 8;   // blocks per captured graph
+
+struct Tables {
+    const GMat* mats;
+    GState* st;
+    const Item* rows;
+    const Item* proj;
+    const Item* reproj;
+    int nrows, nproj, nreproj, count;
+    double* rows_part;
+    double* proj_part;
+    float* Om[2];
+    int64_t n_max;
+};
+
+// The launches of block i (0-based) of every active matrix.
+cudaError_t launch_block(cudaStream_t cs, const Tables& T, int i, int b, uint64_t seed, int* launches) {
+    const int first = (i == 0) ? 1 : 0;
+    const float* Om = T.Om[i & 1];
+    float* Om_next = T.Om[(i + 1) & 1];
+    k_mat<kMatPanel1><<<T.count, NT, 0, cs>>>(T.mats, T.st, b, T.rows_part, T.proj_part);
+    k_rows<kRowMulR1><<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, b, Om, nullptr);
+    int nl = 2;
+    if (i > 0) {
+        k_cols<kColReproj><<<T.nreproj, NT, 0, cs>>>(T.mats, T.st, T.reproj, first, nullptr);
+        k_rows<kRowSubQC><<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, b, Om, nullptr);
+        nl += 2;
+    }
+    k_mat<kMatPanel2><<<T.count, NT, 0, cs>>>(T.mats, T.st, b, T.rows_part, T.proj_part);
+    k_rows<kRowMulR2><<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, b, Om, nullptr);
+    k_cols<kColProject><<<T.nproj, NT, 0, cs>>>(T.mats, T.st, T.proj, first, T.proj_part);
+    k_mat<kMatStop><<<T.count, NT, 0, cs>>>(T.mats, T.st, b, T.rows_part, T.proj_part);
+    const int64_t tot = T.n_max * BP;
+    k_omega_rows<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, cs>>>(T.n_max, (int64_t)(i + 1) * b, b,
+                                                                                 seed, Om_next);
+    k_rows_update<<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, b, first, Om_next, T.rows_part);
+    k_mat<kMatDirect><<<T.count, NT, 0, cs>>>(T.mats, T.st, b, T.rows_part, T.proj_part);
+    nl += 7;
+    *launches += nl;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 int factor_batched(cudaStream_t stream, int num_sms, int64_t count, const void* const* A, const int64_t* m,
                    const int64_t* n, const int64_t* lda, const double* eps, int64_t b, uint64_t seed, int64_t max_rank,
                    const void** Q, int64_t* ldq, const void** B, int64_t* ldb, int64_t* k, int* status, void** outbuf,
                    size_t* outbytes, void** workbuf, size_t* workbytes, float* ms, int* launches) {
-    // output layout and sizes
-    std::vector<MatDesc> d((size_t)count);
+    (void)num_sms;
+    // largest matrices first: their items are scheduled first in every launch
+    std::vector<int> order((size_t)count);
+    for (int64_t t = 0; t < count; ++t) order[(size_t)t] = (int)t;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return m[x] * n[x] > m[y] * n[y]; });
+
+    // outputs: Q_t (ldq x kcap), B_t (ldb x n) per matrix
+    std::vector<GMat> d((size_t)count);
     std::vector<size_t> qoff((size_t)count), boff((size_t)count);
     size_t total = 0;
-    int64_t m_max = 1, n_max = 1, kcap_max = 1;
+    int64_t n_max = 1, max_blocks = 1;
     for (int64_t t = 0; t < count; ++t) {
         const int64_t r = std::min(m[t], n[t]);
         const int64_t kc = (max_rank > 0 && max_rank < r) ? max_rank : r;
-        MatDesc& x = d[(size_t)t];
+        GMat& x = d[(size_t)t];
         x.A = static_cast<const float*>(A[t]);
         x.m = m[t]; x.n = n[t]; x.lda = lda[t]; x.kcap = kc;
         x.ldq = ((m[t] + 3) / 4) * 4;
         x.ldb = ((kc + 3) / 4) * 4;
-        x.ldw = m[t];
+        x.ldw = ((m[t] + 3) / 4) * 4;
         x.eps2 = eps[t] * eps[t];
         qoff[(size_t)t] = total; total = al256(total + sizeof(float) * (size_t)x.ldq * (size_t)kc);
         boff[(size_t)t] = total; total = al256(total + sizeof(float) * (size_t)x.ldb * (size_t)n[t]);
-        m_max = std::max(m_max, m[t]); n_max = std::max(n_max, n[t]); kcap_max = std::max(kcap_max, kc);
+        n_max = std::max(n_max, n[t]);
+        max_blocks = std::max(max_blocks, (kc + b - 1) / b);
     }
     int rc = grow(outbuf, outbytes, total);
     if (rc != RQB_OK) return rc;
     char* ob = static_cast<char*>(*outbuf);
-    for (int64_t t = 0; t < count; ++t) {
-        d[(size_t)t].Q = reinterpret_cast<float*>(ob + qoff[(size_t)t]);
-        d[(size_t)t].B = reinterpret_cast<float*>(ob + boff[(size_t)t]);
-        d[(size_t)t].W = nullptr;
+    // work items, in decreasing matrix size
+    std::vector<Item> rows, proj, reproj;
+    for (int t : order) {
+        GMat& x = d[(size_t)t];
+        x.Q = reinterpret_cast<float*>(ob + qoff[(size_t)t]);
+        x.B = reinterpret_cast<float*>(ob + boff[(size_t)t]);
+        x.rows_begin = (int)rows.size();
+        for (int64_t i = 0; i < (x.m + TR - 1) / TR; ++i) rows.push_back(Item{t, (int)i});
+        x.rows_end = (int)rows.size();
+        x.proj_begin = (int)proj.size();
+        for (int64_t i = 0; i < (x.n + TC - 1) / TC; ++i) proj.push_back(Item{t, (int)i});
+        x.proj_end = (int)proj.size();
+        for (int64_t i = 0; i < (x.kcap + TC - 1) / TC; ++i) reproj.push_back(Item{t, (int)i});
     }
-    // work layout: descriptors, order, outputs, counter, slot table, slot arrays
-    const int nslots = std::max(1, num_sms);
+    // work layout: descriptors, state, item tables, partials, Omega x 2,
+    // then per matrix W, Y, Y1, Cc, Rinv
     size_t w = 0;
-    const size_t oDesc = w; w = al256(w + sizeof(MatDesc) * (size_t)count);
-    const size_t oOrder = w; w = al256(w + sizeof(int) * (size_t)count);
-    const size_t oOuts = w; w = al256(w + sizeof(MatOut) * (size_t)count);
+    const size_t oDesc = w; w = al256(w + sizeof(GMat) * (size_t)count);
+    const size_t oSt = w; w = al256(w + sizeof(GState) * (size_t)count);
+    const size_t oRows = w; w = al256(w + sizeof(Item) * rows.size());
+    const size_t oProj = w; w = al256(w + sizeof(Item) * proj.size());
+    const size_t oRep = w; w = al256(w + sizeof(Item) * reproj.size());
+    const size_t oRp = w; w = al256(w + sizeof(double) * rows.size());
+    const size_t oPp = w; w = al256(w + sizeof(double) * proj.size());
     const size_t oCnt = w; w = al256(w + sizeof(int));
-    const size_t oSlots = w; w = al256(w + sizeof(SlotBuf) * (size_t)nslots);
-    const size_t per_slot = al256(sizeof(float) * (size_t)n_max * BP) + 2 * al256(sizeof(float) * (size_t)m_max * BP) +
-                            al256(sizeof(float) * (size_t)m_max * (size_t)n_max) +
-                            al256(sizeof(float) * (size_t)kcap_max * BP) + al256(sizeof(double) * (size_t)kcap_max * BP);
-    const size_t oSlotData = w; w += per_slot * (size_t)nslots;
+    const size_t oOm0 = w; w = al256(w + sizeof(float) * (size_t)n_max * BP);
+    const size_t oOm1 = w; w = al256(w + sizeof(float) * (size_t)n_max * BP);
+    std::vector<size_t> oW((size_t)count);
+    for (int64_t t = 0; t < count; ++t) {
+        const GMat& x = d[(size_t)t];
+        oW[(size_t)t] = w;
+        w = al256(w + sizeof(float) * (size_t)x.ldw * (size_t)x.n);          // W
+        w = al256(w + sizeof(float) * (size_t)x.ldw * BP);                    // Y
+        w = al256(w + sizeof(float) * (size_t)x.ldw * BP);                    // Y1
+        w = al256(w + sizeof(float) * (size_t)x.kcap * BP);                   // Cc
+        w = al256(w + sizeof(float) * BP * BP);                               // Rinv
+    }
     rc = grow(workbuf, workbytes, w);
     if (rc != RQB_OK) return rc;
     char* wb = static_cast<char*>(*workbuf);
-    std::vector<SlotBuf> sl((size_t)nslots);
-    for (int i = 0; i < nslots; ++i) {
-        char* p = wb + oSlotData + per_slot * (size_t)i;
-        sl[(size_t)i].Om = reinterpret_cast<float*>(p); p += al256(sizeof(float) * (size_t)n_max * BP);
-        sl[(size_t)i].Y = reinterpret_cast<float*>(p); p += al256(sizeof(float) * (size_t)m_max * BP);
-        sl[(size_t)i].Y1 = reinterpret_cast<float*>(p); p += al256(sizeof(float) * (size_t)m_max * BP);
-        sl[(size_t)i].W = reinterpret_cast<float*>(p); p += al256(sizeof(float) * (size_t)m_max * (size_t)n_max);
-        sl[(size_t)i].Cc = reinterpret_cast<float*>(p); p += al256(sizeof(float) * (size_t)kcap_max * BP);
-        sl[(size_t)i].Cd = reinterpret_cast<double*>(p);
+    for (int64_t t = 0; t < count; ++t) {
+        GMat& x = d[(size_t)t];
+        char* p = wb + oW[(size_t)t];
+        x.W = reinterpret_cast<float*>(p); p += al256(sizeof(float) * (size_t)x.ldw * (size_t)x.n);
+        x.Y = reinterpret_cast<float*>(p); p += al256(sizeof(float) * (size_t)x.ldw * BP);
+        x.Y1 = reinterpret_cast<float*>(p); p += al256(sizeof(float) * (size_t)x.ldw * BP);
+        x.Cc = reinterpret_cast<float*>(p); p += al256(sizeof(float) * (size_t)x.kcap * BP);
+        x.Rinv = reinterpret_cast<float*>(p);
     }
-    // largest matrices first (longest-processing-time order)
-    std::vector<int> order((size_t)count);
-    for (int64_t t = 0; t < count; ++t) order[(size_t)t] = (int)t;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int x, int y) { return m[x] * n[x] > m[y] * n[y]; });
+    Tables T;
+    T.mats = reinterpret_cast<const GMat*>(wb + oDesc);
+    T.st = reinterpret_cast<GState*>(wb + oSt);
+    T.rows = reinterpret_cast<const Item*>(wb + oRows);
+    T.proj = reinterpret_cast<const Item*>(wb + oProj);
+    T.reproj = reinterpret_cast<const Item*>(wb + oRep);
+    T.nrows = (int)rows.size();
+    T.nproj = (int)proj.size();
+    T.nreproj = (int)reproj.size();
+    T.count = (int)count;
+    T.rows_part = reinterpret_cast<double*>(wb + oRp);
+    T.proj_part = reinterpret_cast<double*>(wb + oPp);
+    T.Om[0] = reinterpret_cast<float*>(wb + oOm0);
+    T.Om[1] = reinterpret_cast<float*>(wb + oOm1);
+    T.n_max = n_max;
+    int* dcount = reinterpret_cast<int*>(wb + oCnt);
+
     cudaStream_t cs = nullptr;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return RQB_ERR_CUDA;
     cudaEvent_t e0 = nullptr, e1 = nullptr, dep = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    int nl = 0;
     rc = RQB_OK;
     do {
         if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
@@ -633,37 +850,57 @@ int factor_batched(cudaStream_t stream, int num_sms, int64_t count, const void* 
         if (cudaEventRecord(dep, stream) != cudaSuccess || cudaStreamWaitEvent(cs, dep, 0) != cudaSuccess) {
             rc = RQB_ERR_CUDA; break;
         }
-        if (cudaMemcpyAsync(wb + oDesc, d.data(), sizeof(MatDesc) * (size_t)count, cudaMemcpyHostToDevice, cs) !=
+        if (cudaMemcpyAsync(wb + oDesc, d.data(), sizeof(GMat) * (size_t)count, cudaMemcpyHostToDevice, cs) !=
                 cudaSuccess ||
-            cudaMemcpyAsync(wb + oOrder, order.data(), sizeof(int) * (size_t)count, cudaMemcpyHostToDevice, cs) !=
+            cudaMemcpyAsync(wb + oRows, rows.data(), sizeof(Item) * rows.size(), cudaMemcpyHostToDevice, cs) !=
                 cudaSuccess ||
-            cudaMemcpyAsync(wb + oSlots, sl.data(), sizeof(SlotBuf) * (size_t)nslots, cudaMemcpyHostToDevice, cs) !=
+            cudaMemcpyAsync(wb + oProj, proj.data(), sizeof(Item) * proj.size(), cudaMemcpyHostToDevice, cs) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(wb + oRep, reproj.data(), sizeof(Item) * reproj.size(), cudaMemcpyHostToDevice, cs) !=
                 cudaSuccess) { rc = RQB_ERR_CUDA; break; }
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem);
-            attr = true;
+        if (cudaEventRecord(e0, cs) != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
+        // block 1's sketch and the initial state
+        const int64_t tot = n_max * BP;
+        k_omega_rows<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, cs>>>(n_max, 0, (int)b, seed,
+                                                                                     T.Om[0]);
+        k_rows<kRowSketch0><<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, (int)b, T.Om[0], T.rows_part);
+        k_mat<kMatInit><<<T.count, NT, 0, cs>>>(T.mats, T.st, (int)b, T.rows_part, T.proj_part);
+        nl += 3;
+        if (cudaGetLastError() != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
+        // blocks in chunks of kChunk, each chunk one captured graph
+        for (int i0 = 0; i0 < (int)max_blocks && rc == RQB_OK; i0 += kChunk) {
+            const int i1 = std::min<int>((int)max_blocks, i0 + kChunk);
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
+            cudaError_t le = cudaSuccess;
+            for (int i = i0; i < i1 && le == cudaSuccess; ++i) le = launch_block(cs, T, i, (int)b, seed, &nl);
+            if (le == cudaSuccess) k_count_active<<<1, NT, 0, cs>>>(T.st, T.count, dcount);
+            if (cudaStreamEndCapture(cs, &graph) != cudaSuccess || !graph || le != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                rc = RQB_ERR_CUDA;
+                break;
+            }
+            nl += 1;
+            int active = 0;
+            if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess || cudaGraphLaunch(exec, cs) != cudaSuccess ||
+                cudaMemcpyAsync(&active, dcount, sizeof(int), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+                cudaStreamSynchronize(cs) != cudaSuccess)
+                rc = RQB_ERR_CUDA;
+            if (exec) cudaGraphExecDestroy(exec);
+            cudaGraphDestroy(graph);
+            if (rc == RQB_OK && active == 0) break;
         }
-        // one launch (counter reset + persistent kernel) captured into a graph
-        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
-        cudaMemsetAsync(wb + oCnt, 0, sizeof(int), cs);
-        k_batched<<<nslots, NT, kDynSmem, cs>>>(reinterpret_cast<const MatDesc*>(wb + oDesc),
-                                                reinterpret_cast<const int*>(wb + oOrder), (int)count,
-                                                reinterpret_cast<const SlotBuf*>(wb + oSlots),
-                                                reinterpret_cast<MatOut*>(wb + oOuts), (int)b, seed,
-                                                reinterpret_cast<int*>(wb + oCnt));
-        if (cudaStreamEndCapture(cs, &graph) != cudaSuccess || !graph) { rc = RQB_ERR_CUDA; break; }
-        if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
-        if (cudaEventRecord(e0, cs) != cudaSuccess || cudaGraphLaunch(exec, cs) != cudaSuccess ||
-            cudaEventRecord(e1, cs) != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
-        std::vector<MatOut> outs((size_t)count);
-        if (cudaMemcpyAsync(outs.data(), wb + oOuts, sizeof(MatOut) * (size_t)count, cudaMemcpyDeviceToHost, cs) !=
+        if (rc != RQB_OK) break;
+        if (cudaEventRecord(e1, cs) != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
+        std::vector<GState> outs((size_t)count);
+        if (cudaMemcpyAsync(outs.data(), wb + oSt, sizeof(GState) * (size_t)count, cudaMemcpyDeviceToHost, cs) !=
                 cudaSuccess ||
             cudaStreamSynchronize(cs) != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
         float t_ms = 0.f;
         cudaEventElapsedTime(&t_ms, e0, e1);
         if (ms) *ms = t_ms;
-        if (launches) *launches = 2;
+        if (launches) *launches = nl;
         for (int64_t t = 0; t < count; ++t) {
             Q[t] = d[(size_t)t].Q; ldq[t] = d[(size_t)t].ldq;
             B[t] = d[(size_t)t].B; ldb[t] = d[(size_t)t].ldb;
@@ -671,8 +908,6 @@ int factor_batched(cudaStream_t stream, int num_sms, int64_t count, const void* 
         }
     } while (0);
     if (rc != RQB_OK) cudaGetLastError();
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (dep) cudaEventDestroy(dep);

@@ -12,6 +12,8 @@
                 eps = 1e-2 ||A||_F)
   --case fp64   the same for the 2000 x 1000 FP64 workload (b = 50,
                 eps = 1e-4 ||A||_F)
+  --case batched  the same for the 512-matrix batch (b = 32, eps_t =
+                1e-3 ||A_t||_F) through rqb_factor_batched
 Usage: python -m paper_1503_07157_gb300.profile_case [--case small|mixed|fp32|fp64]
 """
 import argparse
@@ -25,7 +27,7 @@ if ROOT not in sys.path:
 
 def main() -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["small", "mixed", "fp32", "fp64"], default="small")
+    ap.add_argument("--case", choices=["small", "mixed", "fp32", "fp64", "batched"], default="small")
     args = ap.parse_args()
     import torch
     import inputs
@@ -39,6 +41,24 @@ def main() -> int:
         with rqb.Handle(torch.float32, prec=rqb.RQB_PREC_TF32X3, max_rank=512, fixed_rank=True) as h:
             _, _, k, rc = h.rqb_factor(A, 0.0, 256, 0, check=False)
             torch.cuda.synchronize()
+    elif args.case == "batched":
+        import numpy as np
+        cases = inputs.batched_sizes(512, seed=0)
+        mats, eps = [], []
+        for i, c in enumerate(cases):
+            s = inputs.spectrum_exp(min(c.m, c.n), c.rate)
+            mats.append(inputs.usv_torch(c.m, c.n, s, 1000 + i, device="cuda", dtype=torch.float32))
+            eps.append(1e-3 * float(np.sqrt(np.sum(s ** 2))))
+        torch.cuda.synchronize()
+        with rqb.Handle(torch.float32) as h:
+            h.rqb_factor_batched(mats, eps, 32, seed=0)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+            out = h.rqb_factor_batched(mats, eps, 32, seed=0)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
+        k = sum(o[2] for o in out)
+        rc = 0 if all(o[3] == rqb.RQB_OK for o in out) else 1
     else:
         import numpy as np
         if args.case == "mixed":

@@ -34,15 +34,12 @@ namespace batched {
 
 constexpr int NT = 256;          // threads per CTA
 constexpr int BP = 32;           // padded block width (b <= 32)
-constexpr int RB = 256;          // staging rows of the per-matrix Gram
-constexpr int KC = 16;
 constexpr int TR = 128;          // rows per row item
-constexpr int TC = 128;          // columns per column item
+constexpr int TC = 256;          // columns per projection item
+constexpr int TCR = 128;         // columns per re-projection item
 constexpr int KCH = 32;          // reduction chunk of the grouped products
 
 struct Smem {
-    float tA[KC][RB + 4];        // X chunk: KC reduction rows x RB outputs
-    float tB[KC][BP + 4];        // C chunk: KC x BP
     double G[BP][BP + 1];        // Gram / Cholesky work (FP64)
     float Rinv[BP][BP + 1];      // R^{-1}
     double red[NT / 32];
@@ -96,44 +93,6 @@ struct Item {
     int t;               // matrix
     int tile;            // row tile (rows 128 tile ..) or column tile
 };
-
-// s.G (BP x BP, FP64) = Y^T Y over `rows` rows with error-free FP32
-// accumulation (exact products, TwoSum into an FP32 pair, promoted to FP64
-// every 256 rows).  Thread (ti, tj): entries ti*2..+1 x tj*2..+1.
-__device__ void cta_gram_exact(Smem& s, int64_t rows, const float* Y, int64_t ldy) {
-    const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
-    constexpr int CH = 120;   // CH x (BP + 1) floats fit in tA (KC x (RB + 4))
-    static_assert(CH * (BP + 1) <= KC * (RB + 4), "Gram staging must fit in tA");
-    float (*tY)[BP + 1] = reinterpret_cast<float (*)[BP + 1]>(&s.tA[0][0]);
-    double acc2[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
-    for (int64_t r0 = 0; r0 < rows; r0 += CH) {
-        for (int v = tid; v < CH * BP; v += NT) {
-            const int j = v / CH, rr = v % CH;
-            const int64_t r = r0 + rr;
-            tY[rr][j] = (r < rows) ? Y[r + (int64_t)j * ldy] : 0.f;
-        }
-        __syncthreads();
-        float hi[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, lo[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-        for (int rr = 0; rr < CH; ++rr) {
-            const float a0 = tY[rr][ti * 2], a1 = tY[rr][ti * 2 + 1];
-            const float b0 = tY[rr][tj * 2], b1 = tY[rr][tj * 2 + 1];
-            exact_fma_acc(a0, b0, hi[0][0], lo[0][0]);
-            exact_fma_acc(a0, b1, hi[0][1], lo[0][1]);
-            exact_fma_acc(a1, b0, hi[1][0], lo[1][0]);
-            exact_fma_acc(a1, b1, hi[1][1], lo[1][1]);
-        }
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 2; ++j) acc2[i][j] += (double)hi[i][j] + (double)lo[i][j];
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) s.G[ti * 2 + i][tj * 2 + j] = acc2[i][j];
-    __syncthreads();
-}
 
 // Cholesky of s.G (p x p valid, identity beyond), then s.Rinv = R^{-1} (FP32).
 // Returns false (CTA-uniform) on a pivot <= tol * G_jj.
@@ -270,6 +229,23 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
     return t;
 }
 
+// Rows r .. r + 3 of one column: src points at row r, rem = rows left (m - r);
+// a 16-byte load when vec (aligned column, ld a multiple of 4) and rem >= 4.
+__device__ __forceinline__ float4 load_rows4(const float* src, int64_t rem, bool valid, bool vec) {
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!valid || rem <= 0) return x;
+    if (vec && rem >= 4) return *reinterpret_cast<const float4*>(src);
+    x.x = src[0];
+    if (rem > 1) x.y = src[1];
+    if (rem > 2) x.z = src[2];
+    if (rem > 3) x.w = src[3];
+    return x;
+}
+
+__device__ __forceinline__ bool vec_ok(const float* p, int64_t ld) {
+    return ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) && (ld % 4 == 0);
+}
+
 enum RowOp { kRowSketch0 = 0, kRowMulR1 = 1, kRowSubQC = 2, kRowMulR2 = 3 };
 
 // kRowSketch0  Y = A Omega_1 (columns >= p zero), part = ||A tile||_F^2
@@ -374,32 +350,43 @@ __global__ void __launch_bounds__(NT) k_rows_update(const GMat* __restrict__ mat
 #pragma unroll
         for (int j = 0; j < 4; ++j) yacc[i][j] = 0.f;
     double sq = 0.0;
+    // the next column chunk (W, B_i, Omega) is loaded into registers while the
+    // current one is used
+    constexpr int WQ = KCH * (TR / 4) / NT;    // float4 of W per thread (4)
+    constexpr int SQ = KCH * BP / NT;          // B_i and Omega entries per thread (4)
+    float4 wr[WQ];
+    float br[SQ], orr[SQ];
+    auto load = [&](int64_t c0) {
+#pragma unroll
+        for (int u = 0; u < SQ; ++u) {
+            const int e = tid + u * NT, c = e / BP, t = e % BP;
+            const int64_t cc = c0 + c;
+            br[u] = (t < p && cc < n) ? Bi[t + cc * d.ldb] : 0.f;
+            orr[u] = (cc < n) ? Om_next[cc * BP + t] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < WQ; ++u) {
+            const int v = tid + u * NT, c = v / (TR / 4), rr = (v % (TR / 4)) * 4;
+            const int64_t cc = c0 + c, r = r0 + rr;
+            wr[u] = load_rows4(Wsrc + r + cc * ldws, m - r, cc < n, vsrc);
+        }
+    };
+    load(0);
     for (int64_t c0 = 0; c0 < n; c0 += KCH) {
         __syncthreads();
-        for (int e = tid; e < KCH * BP; e += NT) {
-            const int c = e / BP, t = e % BP;
-            const int64_t cc = c0 + c;
-            Bs[t][c] = (t < p && cc < n) ? Bi[t + cc * d.ldb] : 0.f;
-            Os[c][t] = (cc < n) ? Om_next[cc * BP + t] : 0.f;
+#pragma unroll
+        for (int u = 0; u < SQ; ++u) {
+            const int e = tid + u * NT, c = e / BP, t = e % BP;
+            Bs[t][c] = br[u];
+            Os[c][t] = orr[u];
         }
-        for (int v = tid; v < KCH * (TR / 4); v += NT) {
-            const int c = v / (TR / 4), rr = (v % (TR / 4)) * 4;
-            const int64_t cc = c0 + c, r = r0 + rr;
-            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (cc < n && r < m) {
-                const float* src = Wsrc + r + cc * ldws;
-                if (vsrc && r + 4 <= m) {
-                    w = *reinterpret_cast<const float4*>(src);
-                } else {
-                    w.x = src[0];
-                    if (r + 1 < m) w.y = src[1];
-                    if (r + 2 < m) w.z = src[2];
-                    if (r + 3 < m) w.w = src[3];
-                }
-            }
-            *reinterpret_cast<float4*>(&Ws[c][rr]) = w;
+#pragma unroll
+        for (int u = 0; u < WQ; ++u) {
+            const int v = tid + u * NT, c = v / (TR / 4), rr = (v % (TR / 4)) * 4;
+            *reinterpret_cast<float4*>(&Ws[c][rr]) = wr[u];
         }
         __syncthreads();
+        if (c0 + KCH < n) load(c0 + KCH);
         // P = Q_i(tile) B_i(:, chunk); W = Wsrc - P on this thread's 4 x 4 entries
         float pacc[4][4];
 #pragma unroll
@@ -460,24 +447,29 @@ __global__ void __launch_bounds__(NT) k_rows_update(const GMat* __restrict__ mat
 }
 
 // ---------------------------------------------------------------------------
-// Column items: out(j, c) for j < BP and 128 columns c, reduced over the m rows:
-//   kColProject  B_i(j, c) = sum_r Q_i(r, j) Wsrc(r, c), part = ||B_i tile||^2
-//   kColReproj   C(c, j)   = sum_r Qbar(r, c) Y1(r, j), FP64 accumulation
-// Thread (tj, lane) owns j = tj*4 .. +3 and c = lane + 32 q, q < 4.
+// Column items: out(j, c) for j < BP and W columns c of the item, reduced over
+// the m rows:
+//   kColProject  B_i(j, c) = sum_r Q_i(r, j) Wsrc(r, c), 256 columns per item,
+//                part = ||B_i tile||^2
+//   kColReproj   C(c, j)   = sum_r Qbar(r, c) Y1(r, j), 128 columns per item,
+//                FP32 partials promoted to FP64 every 128 rows
+// Thread (tj, lane) owns j = tj*4 .. +3 and c = lane + 32 q.
 enum ColOp { kColProject = 0, kColReproj = 1 };
 
 template <int OP>
 __global__ void __launch_bounds__(NT) k_cols(const GMat* __restrict__ mats, const GState* __restrict__ st,
                                              const Item* __restrict__ items, int first, double* __restrict__ part) {
+    constexpr int W = (OP == kColProject) ? TC : TCR;   // columns per item
+    constexpr int NQ = W / 32;                           // column slots per thread
     __shared__ float Ps[KCH][BP + 1];    // Ps[r][j]: Q_i or Y1 rows of the chunk
-    __shared__ float Vs[KCH][TC + 1];    // Vs[r][c]: Wsrc or Qbar columns of the tile
+    __shared__ float Vs[KCH][W + 1];     // Vs[r][c]: Wsrc or Qbar columns of the item
     __shared__ double red[NT / 32];
     const Item it = items[blockIdx.x];
     const GState s = st[it.t];
     if (!s.active) return;
     if (OP == kColReproj && s.k == 0) return;
     const GMat& d = mats[it.t];
-    const int64_t c0 = (int64_t)it.tile * TC;
+    const int64_t c0 = (int64_t)it.tile * W;
     const int64_t ncols = (OP == kColProject) ? d.n : s.k;
     if (c0 >= ncols) return;
     const float* P = (OP == kColProject) ? d.Q + s.k * d.ldq : d.Y1;
@@ -487,42 +479,71 @@ __global__ void __launch_bounds__(NT) k_cols(const GMat* __restrict__ mats, cons
     const int64_t ldv = (OP == kColProject) ? (first ? d.lda : d.ldw) : d.ldq;
     const int64_t m = d.m;
     const int tid = threadIdx.x, tj = tid >> 5, lane = tid & 31;
-    float acc[4][4];
-    double acc2[4][4];
+    float acc[4][NQ];
+    double acc2[4][OP == kColReproj ? NQ : 1];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) { acc[i][q] = 0.f; acc2[i][q] = 0.0; }
+        for (int q = 0; q < NQ; ++q) acc[i][q] = 0.f;
+    if (OP == kColReproj) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int q = 0; q < (OP == kColReproj ? NQ : 1); ++q) acc2[i][q] = 0.0;
+    }
+    // staging: float4 e of a chunk covers rows 4 (e % 8) .. +3 of column e / 8;
+    // the next chunk is loaded into registers while the current one is used
+    constexpr int VQ = (KCH / 4) * W / NT;
+    const bool pvec = vec_ok(P, ldp), vvec = vec_ok(V, ldv);
+    float4 pr, vr[VQ];
+    auto load = [&](int64_t r0) {
+        {
+            const int j = tid / (KCH / 4), rq = (tid % (KCH / 4)) * 4;
+            pr = load_rows4(P + (r0 + rq) + (int64_t)j * ldp, m - r0 - rq, j < pw, pvec);
+        }
+#pragma unroll
+        for (int u = 0; u < VQ; ++u) {
+            const int e = tid + u * NT, c = e / (KCH / 4), rq = (e % (KCH / 4)) * 4;
+            const int64_t cc = c0 + c;
+            vr[u] = load_rows4(V + (r0 + rq) + cc * ldv, m - r0 - rq, cc < ncols, vvec);
+        }
+    };
+    load(0);
+    int chunk = 0;
     for (int64_t r0 = 0; r0 < m; r0 += KCH) {
         __syncthreads();
-        for (int e = tid; e < KCH * BP; e += NT) {         // 32 rows of each of the BP columns
-            const int j = e / KCH, rr = e % KCH;
-            const int64_t r = r0 + rr;
-            Ps[rr][j] = (j < pw && r < m) ? P[r + (int64_t)j * ldp] : 0.f;
+        {
+            const int j = tid / (KCH / 4), rq = (tid % (KCH / 4)) * 4;
+            Ps[rq][j] = pr.x; Ps[rq + 1][j] = pr.y; Ps[rq + 2][j] = pr.z; Ps[rq + 3][j] = pr.w;
         }
-        for (int e = tid; e < KCH * TC; e += NT) {         // 32 rows of each of the 128 columns
-            const int c = e / KCH, rr = e % KCH;
-            const int64_t r = r0 + rr, cc = c0 + c;
-            Vs[rr][c] = (cc < ncols && r < m) ? V[r + cc * ldv] : 0.f;
+#pragma unroll
+        for (int u = 0; u < VQ; ++u) {
+            const int e = tid + u * NT, c = e / (KCH / 4), rq = (e % (KCH / 4)) * 4;
+            Vs[rq][c] = vr[u].x; Vs[rq + 1][c] = vr[u].y; Vs[rq + 2][c] = vr[u].z; Vs[rq + 3][c] = vr[u].w;
         }
         __syncthreads();
-#pragma unroll 8
+        if (r0 + KCH < m) load(r0 + KCH);
+#pragma unroll 4
         for (int rr = 0; rr < KCH; ++rr) {
-            float a[4], v[4];
+            float a[4], v[NQ];
 #pragma unroll
             for (int i = 0; i < 4; ++i) a[i] = Ps[rr][tj * 4 + i];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = Vs[rr][lane + 32 * q];
+            for (int q = 0; q < NQ; ++q) v[q] = Vs[rr][lane + 32 * q];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[i][q] = fmaf(a[i], v[q], acc[i][q]);
+                for (int q = 0; q < NQ; ++q) acc[i][q] = fmaf(a[i], v[q], acc[i][q]);
         }
-        if (OP == kColReproj) {
+        if (OP == kColReproj && (++chunk == 4 || r0 + KCH >= m)) {
+            chunk = 0;
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) { acc2[i][q] += (double)acc[i][q]; acc[i][q] = 0.f; }
+                for (int q = 0; q < (OP == kColReproj ? NQ : 1); ++q) {
+                    acc2[i][q] += (double)acc[i][q];
+                    acc[i][q] = 0.f;
+                }
         }
     }
     double sq = 0.0;
@@ -530,7 +551,7 @@ __global__ void __launch_bounds__(NT) k_cols(const GMat* __restrict__ mats, cons
     for (int i = 0; i < 4; ++i) {
         const int j = tj * 4 + i;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < NQ; ++q) {
             const int64_t cc = c0 + lane + 32 * q;
             if (cc >= ncols) continue;
             if (OP == kColProject) {
@@ -540,7 +561,7 @@ __global__ void __launch_bounds__(NT) k_cols(const GMat* __restrict__ mats, cons
                     sq += (double)bv * (double)bv;
                 }
             } else {
-                d.Cc[cc + (int64_t)j * d.kcap] = (float)acc2[i][q];
+                d.Cc[cc + (int64_t)j * d.kcap] = (float)acc2[i][OP == kColReproj ? q : 0];
             }
         }
     }
@@ -550,10 +571,50 @@ __global__ void __launch_bounds__(NT) k_cols(const GMat* __restrict__ mats, cons
     }
 }
 
+// Exact Gram partials of one 128-row tile of Y (SRC = 0) or Y1 (SRC = 1):
+// gpart[item][r][c] = sum over the tile's rows of Y(., r) Y(., c), products
+// split exactly and summed with TwoSum in FP32 pairs, promoted to FP64.
+// Thread (ti, tj) of a 16 x 16 grid owns entries (2 ti .. +1, 2 tj .. +1).
+template <int SRC>
+__global__ void __launch_bounds__(NT) k_rows_gram(const GMat* __restrict__ mats, const GState* __restrict__ st,
+                                                  const Item* __restrict__ items, double* __restrict__ gpart) {
+    __shared__ float Ys[TR][BP + 1];
+    const Item it = items[blockIdx.x];
+    const GState s = st[it.t];
+    if (!s.active) return;
+    const GMat& d = mats[it.t];
+    const float* Y = (SRC == 0) ? d.Y : d.Y1;
+    const int64_t r0 = (int64_t)it.tile * TR;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < TR * BP; e += NT) {
+        const int j = e / TR, rr = e % TR;
+        const int64_t r = r0 + rr;
+        Ys[rr][j] = (r < d.m) ? Y[r + (int64_t)j * d.ldw] : 0.f;
+    }
+    __syncthreads();
+    const int ti = tid >> 4, tj = tid & 15;
+    float hi[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, lo[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 4
+    for (int rr = 0; rr < TR; ++rr) {
+        const float a0 = Ys[rr][ti * 2], a1 = Ys[rr][ti * 2 + 1];
+        const float b0 = Ys[rr][tj * 2], b1 = Ys[rr][tj * 2 + 1];
+        exact_fma_acc(a0, b0, hi[0][0], lo[0][0]);
+        exact_fma_acc(a0, b1, hi[0][1], lo[0][1]);
+        exact_fma_acc(a1, b0, hi[1][0], lo[1][0]);
+        exact_fma_acc(a1, b1, hi[1][1], lo[1][1]);
+    }
+    double* g = gpart + (size_t)blockIdx.x * (BP * BP);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) g[(ti * 2 + i) * BP + tj * 2 + j] = (double)hi[i][j] + (double)lo[i][j];
+}
+
 // ---------------------------------------------------------------------------
 // Matrix items: one CTA per matrix.
 //   kMatInit    ||A||^2 from the first sketch's partials; state of block 1
-//   kMatPanel1  exact Gram of Y, FP64 Cholesky, R^-1 (first CholeskyQR pass)
+//   kMatPanel1  Gram of Y from its tiles' exact partials (fixed order), FP64
+//               Cholesky, R^-1 (first CholeskyQR pass)
 //   kMatPanel2  the same for Y1 (second pass)
 //   kMatStop    E_i -= ||B_i||^2 and the decision of line (6)
 //   kMatDirect  inside the band: the direct ||A^(i)||^2 of the update decides;
@@ -563,7 +624,8 @@ enum MatOp { kMatInit = 0, kMatPanel1 = 1, kMatPanel2 = 2, kMatStop = 3, kMatDir
 template <int OP>
 __global__ void __launch_bounds__(NT, 1) k_mat(const GMat* __restrict__ mats, GState* __restrict__ st, int b,
                                                const double* __restrict__ rows_part,
-                                               const double* __restrict__ proj_part) {
+                                               const double* __restrict__ proj_part,
+                                               const double* __restrict__ gpart) {
     __shared__ Smem s;
     const int t = blockIdx.x;
     const GMat& d = mats[t];
@@ -591,7 +653,12 @@ __global__ void __launch_bounds__(NT, 1) k_mat(const GMat* __restrict__ mats, GS
     }
     if (!g.active) return;
     if (OP == kMatPanel1 || OP == kMatPanel2) {
-        cta_gram_exact(s, d.m, OP == kMatPanel1 ? d.Y : d.Y1, d.ldw);
+        for (int e = threadIdx.x; e < BP * BP; e += NT) {
+            double acc = 0.0;
+            for (int i = d.rows_begin; i < d.rows_end; ++i) acc += gpart[(size_t)i * (BP * BP) + e];
+            s.G[e / BP][e % BP] = acc;
+        }
+        __syncthreads();
         const bool ok = cta_chol_inv(s, g.p, 1e-14);
         if (!ok) {
             if (threadIdx.x == 0) {
@@ -706,6 +773,7 @@ struct Tables {
     int nrows, nproj, nreproj, count;
     double* rows_part;
     double* proj_part;
+    double* gpart;       // BP x BP exact Gram partial per row item
     float* Om[2];
     int64_t n_max;
 };
@@ -715,24 +783,26 @@ cudaError_t launch_block(cudaStream_t cs, const Tables& T, int i, int b, uint64_
     const int first = (i == 0) ? 1 : 0;
     const float* Om = T.Om[i & 1];
     float* Om_next = T.Om[(i + 1) & 1];
-    k_mat<kMatPanel1><<<T.count, NT, 0, cs>>>(T.mats, T.st, b, T.rows_part, T.proj_part);
+    k_rows_gram<0><<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, T.gpart);
+    k_mat<kMatPanel1><<<T.count, NT, 0, cs>>>(T.mats, T.st, b, T.rows_part, T.proj_part, T.gpart);
     k_rows<kRowMulR1><<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, b, Om, nullptr);
-    int nl = 2;
+    int nl = 3;
     if (i > 0) {
         k_cols<kColReproj><<<T.nreproj, NT, 0, cs>>>(T.mats, T.st, T.reproj, first, nullptr);
         k_rows<kRowSubQC><<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, b, Om, nullptr);
         nl += 2;
     }
-    k_mat<kMatPanel2><<<T.count, NT, 0, cs>>>(T.mats, T.st, b, T.rows_part, T.proj_part);
+    k_rows_gram<1><<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, T.gpart);
+    k_mat<kMatPanel2><<<T.count, NT, 0, cs>>>(T.mats, T.st, b, T.rows_part, T.proj_part, T.gpart);
     k_rows<kRowMulR2><<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, b, Om, nullptr);
     k_cols<kColProject><<<T.nproj, NT, 0, cs>>>(T.mats, T.st, T.proj, first, T.proj_part);
-    k_mat<kMatStop><<<T.count, NT, 0, cs>>>(T.mats, T.st, b, T.rows_part, T.proj_part);
+    k_mat<kMatStop><<<T.count, NT, 0, cs>>>(T.mats, T.st, b, T.rows_part, T.proj_part, T.gpart);
     const int64_t tot = T.n_max * BP;
     k_omega_rows<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, cs>>>(T.n_max, (int64_t)(i + 1) * b, b,
                                                                                  seed, Om_next);
     k_rows_update<<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, b, first, Om_next, T.rows_part);
-    k_mat<kMatDirect><<<T.count, NT, 0, cs>>>(T.mats, T.st, b, T.rows_part, T.proj_part);
-    nl += 7;
+    k_mat<kMatDirect><<<T.count, NT, 0, cs>>>(T.mats, T.st, b, T.rows_part, T.proj_part, T.gpart);
+    nl += 8;
     *launches += nl;
     return cudaGetLastError();
 }
@@ -784,7 +854,7 @@ int factor_batched(cudaStream_t stream, int num_sms, int64_t count, const void* 
         x.proj_begin = (int)proj.size();
         for (int64_t i = 0; i < (x.n + TC - 1) / TC; ++i) proj.push_back(Item{t, (int)i});
         x.proj_end = (int)proj.size();
-        for (int64_t i = 0; i < (x.kcap + TC - 1) / TC; ++i) reproj.push_back(Item{t, (int)i});
+        for (int64_t i = 0; i < (x.kcap + TCR - 1) / TCR; ++i) reproj.push_back(Item{t, (int)i});
     }
     // work layout: descriptors, state, item tables, partials, Omega x 2,
     // then per matrix W, Y, Y1, Cc, Rinv
@@ -796,6 +866,7 @@ int factor_batched(cudaStream_t stream, int num_sms, int64_t count, const void* 
     const size_t oRep = w; w = al256(w + sizeof(Item) * reproj.size());
     const size_t oRp = w; w = al256(w + sizeof(double) * rows.size());
     const size_t oPp = w; w = al256(w + sizeof(double) * proj.size());
+    const size_t oGp = w; w = al256(w + sizeof(double) * BP * BP * rows.size());
     const size_t oCnt = w; w = al256(w + sizeof(int));
     const size_t oOm0 = w; w = al256(w + sizeof(float) * (size_t)n_max * BP);
     const size_t oOm1 = w; w = al256(w + sizeof(float) * (size_t)n_max * BP);
@@ -833,6 +904,7 @@ int factor_batched(cudaStream_t stream, int num_sms, int64_t count, const void* 
     T.count = (int)count;
     T.rows_part = reinterpret_cast<double*>(wb + oRp);
     T.proj_part = reinterpret_cast<double*>(wb + oPp);
+    T.gpart = reinterpret_cast<double*>(wb + oGp);
     T.Om[0] = reinterpret_cast<float*>(wb + oOm0);
     T.Om[1] = reinterpret_cast<float*>(wb + oOm1);
     T.n_max = n_max;
@@ -864,7 +936,7 @@ int factor_batched(cudaStream_t stream, int num_sms, int64_t count, const void* 
         k_omega_rows<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, cs>>>(n_max, 0, (int)b, seed,
                                                                                      T.Om[0]);
         k_rows<kRowSketch0><<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, (int)b, T.Om[0], T.rows_part);
-        k_mat<kMatInit><<<T.count, NT, 0, cs>>>(T.mats, T.st, (int)b, T.rows_part, T.proj_part);
+        k_mat<kMatInit><<<T.count, NT, 0, cs>>>(T.mats, T.st, (int)b, T.rows_part, T.proj_part, T.gpart);
         nl += 3;
         if (cudaGetLastError() != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
         // blocks in chunks of kChunk, each chunk one captured graph

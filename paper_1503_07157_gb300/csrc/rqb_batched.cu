@@ -94,54 +94,58 @@ struct Item {
     int tile;            // row tile (rows 128 tile ..) or column tile
 };
 
-// Cholesky of s.G (p x p valid, identity beyond), then s.Rinv = R^{-1} (FP32).
+// Cholesky of s.G (p x p valid, identity beyond): G = L L^T with L and L^{-1}
+// formed together in shared memory (right-looking; at step j the pivot column
+// of L and row j of L^{-1} are scaled by 1 / l_jj, then the trailing part of L
+// is updated and column j eliminated from the rows of L^{-1} below j, all
+// entries in parallel).  s.Rinv = R^{-1} = (L^{-1})^T (FP32) for R = L^T.
 // Returns false (CTA-uniform) on a pivot <= tol * G_jj.
 __device__ bool cta_chol_inv(Smem& s, int p, double tol) {
     const int tid = threadIdx.x;
     __shared__ double diag0[BP];
+    __shared__ double L[BP][BP + 1];
+    __shared__ double Li[BP][BP + 1];
+    __shared__ double inv[BP];
+    __shared__ int fail;
     for (int r = tid; r < BP; r += NT) diag0[r] = (r < p) ? s.G[r][r] : 1.0;
-    // identity beyond p
     for (int e = tid; e < BP * BP; e += NT) {
         const int r = e / BP, c = e % BP;
-        if (r >= p || c >= p) s.G[r][c] = (r == c) ? 1.0 : 0.0;
+        double v = (r < p && c < p) ? s.G[r][c] : (r == c ? 1.0 : 0.0);
+        L[r][c] = (r >= c) ? v : 0.0;
+        Li[r][c] = (r == c) ? 1.0 : 0.0;
     }
+    if (tid == 0) fail = 0;
     __syncthreads();
-    bool ok = true;
-    for (int j = 0; j < p; ++j) {
-        const double d = s.G[j][j];
-        if (!(d > tol * diag0[j]) || !isfinite(d)) { ok = false; break; }
-        const double invd = 1.0 / d;
-        for (int e = tid; e < BP * BP; e += NT) {     // upper triangle r <= c, both > j
-            const int r = e / BP, c = e % BP;
-            if (r > j && c >= r && c < p) s.G[r][c] -= s.G[j][r] * s.G[j][c] * invd;
+    for (int j = 0; j < BP; ++j) {
+        if (tid == 0) {
+            double d = L[j][j];
+            if (!(d > tol * diag0[j]) || !isfinite(d)) {
+                fail = 1;
+                d = 1.0;
+            }
+            const double l = sqrt(d);
+            L[j][j] = l;
+            inv[j] = 1.0 / l;
+        }
+        __syncthreads();
+        const double ij = inv[j];
+        if (tid < BP) {
+            if (tid > j) L[tid][j] *= ij;
+        } else if (tid < 2 * BP) {
+            if (tid - BP <= j) Li[j][tid - BP] *= ij;
+        }
+        __syncthreads();
+        for (int e = tid; e < BP * BP; e += NT) {
+            const int r = e % BP, c = e / BP;
+            if (c > j && r >= c) L[r][c] -= L[r][j] * L[c][j];
+            else if (r > j && c <= j) Li[r][c] -= L[r][j] * Li[j][c];
         }
         __syncthreads();
     }
-    if (!ok) return false;
-    // R[r][c] = G[r][c] / sqrt(d_r) (upper), stored back in s.G
-    __shared__ double rd[BP];
-    for (int r = tid; r < BP; r += NT) rd[r] = sqrt(s.G[r][r]);
-    __syncthreads();
+    if (fail) return false;
     for (int e = tid; e < BP * BP; e += NT) {
         const int r = e / BP, c = e % BP;
-        double v = 0.0;
-        if (c > r) v = s.G[r][c] / rd[r];
-        else if (c == r) v = rd[r];
-        s.G[r][c] = v;   // each entry read and written by its own thread
-    }
-    __syncthreads();
-    // inverse: thread c < BP solves R x = e_c (column c of R^{-1})
-    if (tid < BP) {
-        const int c = tid;
-        double x[BP];
-#pragma unroll
-        for (int r = 0; r < BP; ++r) x[r] = (r == c) ? 1.0 : 0.0;
-        for (int t = c; t >= 0; --t) {
-            const double xt = x[t] / s.G[t][t];
-            x[t] = xt;
-            for (int r = 0; r < t; ++r) x[r] -= s.G[r][t] * xt;
-        }
-        for (int r = 0; r < BP; ++r) s.Rinv[r][c] = (r <= c) ? (float)x[r] : 0.f;
+        s.Rinv[r][c] = (float)Li[c][r];   // R^{-1} = (L^{-1})^T, upper
     }
     __syncthreads();
     return true;
@@ -307,14 +311,20 @@ __global__ void __launch_bounds__(NT) k_rows(const GMat* __restrict__ mats, cons
 //   W(rows, :) = Wsrc(rows, :) - Q_i(rows, :) B_i,  Y(rows, :) = W(rows, :) Omega_{i+1}
 // column chunk by column chunk; part = ||W(rows, :)||_F^2.  Wsrc is A in the
 // first block.  Runs for matrices whose block i was accepted or is ambiguous.
-__global__ void __launch_bounds__(NT) k_rows_update(const GMat* __restrict__ mats, const GState* __restrict__ st,
-                                                    const Item* __restrict__ items, int b, int first,
-                                                    const float* __restrict__ Om_next, double* __restrict__ part) {
+// 128 threads; thread (ty, tx) owns rows ty*8 .. +7 and columns tx + 8 j
+// (j < 4) of both products: the element-wise update then reads and writes its
+// 8 contiguous rows of a column with conflict-free 16-byte accesses.  The
+// next column chunk is loaded into registers while the current one is used.
+constexpr int NTU = 128;
+
+__global__ void __launch_bounds__(NTU) k_rows_update(const GMat* __restrict__ mats, const GState* __restrict__ st,
+                                                     const Item* __restrict__ items, int b, int first,
+                                                     const float* __restrict__ Om_next, double* __restrict__ part) {
     __shared__ __align__(16) float Qs[BP][TR + 4];    // Qs[t][r] = Q_i(r0 + r, t)
-    __shared__ __align__(16) float Bs[BP][KCH + 4];   // Bs[t][c] = B_i(t, c0 + c)
+    __shared__ float Bs[BP][KCH + 1];                 // Bs[t][c] = B_i(t, c0 + c)
     __shared__ __align__(16) float Ws[KCH][TR + 4];   // Ws[c][r] = W(r0 + r, c0 + c)
-    __shared__ __align__(16) float Os[KCH][BP + 4];   // Os[c][j] = Omega_{i+1}(c0 + c, j)
-    __shared__ double red[NT / 32];
+    __shared__ float Os[KCH][BP + 1];                 // Os[c][j] = Omega_{i+1}(c0 + c, j)
+    __shared__ double red[NTU / 32];
     const Item it = items[blockIdx.x];
     const GState s = st[it.t];
     if (!s.pending) return;
@@ -323,106 +333,102 @@ __global__ void __launch_bounds__(NT) k_rows_update(const GMat* __restrict__ mat
     const int64_t m = d.m, n = d.n, r0 = (int64_t)it.tile * TR;
     const float* Wsrc = first ? d.A : d.W;
     const int64_t ldws = first ? d.lda : d.ldw;
-    const bool vsrc = ((reinterpret_cast<uintptr_t>(Wsrc) & 15u) == 0) && (ldws % 4 == 0);
+    const bool vsrc = vec_ok(Wsrc, ldws);
     const float* Qi = d.Q + s.k * d.ldq;
     const float* Bi = d.B + s.k;
     const int p = s.p;
     const int pn = (int)max((int64_t)0, min((int64_t)b, d.kcap - s.knext));
-    for (int v = tid; v < BP * (TR / 4); v += NT) {
+    for (int v = tid; v < BP * (TR / 4); v += NTU) {
         const int t = v / (TR / 4), rr = (v % (TR / 4)) * 4;
         const int64_t r = r0 + rr;
-        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (t < p && r < m) {
-            const float* src = Qi + r + (int64_t)t * d.ldq;
-            if (r + 4 <= m) {
-                q = *reinterpret_cast<const float4*>(src);   // ldq is a multiple of 4
-            } else {
-                q.x = src[0];
-                if (r + 1 < m) q.y = src[1];
-                if (r + 2 < m) q.z = src[2];
-            }
-        }
-        *reinterpret_cast<float4*>(&Qs[t][rr]) = q;
+        *reinterpret_cast<float4*>(&Qs[t][rr]) = load_rows4(Qi + r + (int64_t)t * d.ldq, m - r, t < p, true);
     }
-    float yacc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) yacc[i][j] = 0.f;
-    double sq = 0.0;
-    // the next column chunk (W, B_i, Omega) is loaded into registers while the
-    // current one is used
-    constexpr int WQ = KCH * (TR / 4) / NT;    // float4 of W per thread (4)
-    constexpr int SQ = KCH * BP / NT;          // B_i and Omega entries per thread (4)
+    constexpr int WQ = KCH * (TR / 4) / NTU;   // float4 of W per thread (8)
+    constexpr int SQ = KCH * BP / NTU;         // B_i and Omega entries per thread (8)
     float4 wr[WQ];
     float br[SQ], orr[SQ];
     auto load = [&](int64_t c0) {
 #pragma unroll
         for (int u = 0; u < SQ; ++u) {
-            const int e = tid + u * NT, c = e / BP, t = e % BP;
+            const int e = tid + u * NTU, c = e / BP, t = e % BP;
             const int64_t cc = c0 + c;
             br[u] = (t < p && cc < n) ? Bi[t + cc * d.ldb] : 0.f;
             orr[u] = (cc < n) ? Om_next[cc * BP + t] : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < WQ; ++u) {
-            const int v = tid + u * NT, c = v / (TR / 4), rr = (v % (TR / 4)) * 4;
+            const int v = tid + u * NTU, c = v / (TR / 4), rr = (v % (TR / 4)) * 4;
             const int64_t cc = c0 + c, r = r0 + rr;
             wr[u] = load_rows4(Wsrc + r + cc * ldws, m - r, cc < n, vsrc);
         }
     };
+    float yacc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) yacc[i][j] = 0.f;
+    double sq = 0.0;
     load(0);
     for (int64_t c0 = 0; c0 < n; c0 += KCH) {
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < SQ; ++u) {
-            const int e = tid + u * NT, c = e / BP, t = e % BP;
+            const int e = tid + u * NTU, c = e / BP, t = e % BP;
             Bs[t][c] = br[u];
             Os[c][t] = orr[u];
         }
 #pragma unroll
         for (int u = 0; u < WQ; ++u) {
-            const int v = tid + u * NT, c = v / (TR / 4), rr = (v % (TR / 4)) * 4;
+            const int v = tid + u * NTU, c = v / (TR / 4), rr = (v % (TR / 4)) * 4;
             *reinterpret_cast<float4*>(&Ws[c][rr]) = wr[u];
         }
         __syncthreads();
         if (c0 + KCH < n) load(c0 + KCH);
-        // P = Q_i(tile) B_i(:, chunk); W = Wsrc - P on this thread's 4 x 4 entries
-        float pacc[4][4];
+        // P = Q_i(tile) B_i(:, chunk)
+        float pacc[8][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 8; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) pacc[i][j] = 0.f;
 #pragma unroll 8
         for (int t = 0; t < BP; ++t) {
-            const float4 a = *reinterpret_cast<const float4*>(&Qs[t][ty * 4]);
-            const float4 bb = *reinterpret_cast<const float4*>(&Bs[t][tx * 4]);
-            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {bb.x, bb.y, bb.z, bb.w};
+            const float4 a0 = *reinterpret_cast<const float4*>(&Qs[t][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&Qs[t][ty * 8 + 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            float bv[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[t][tx + 8 * j];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) pacc[i][j] = fmaf(av[i], bv[j], pacc[i][j]);
         }
+        // W = Wsrc - P on this thread's entries: shared copy, global store, ||W||^2
         float sqf = 0.f;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int c = tx * 4 + j;
+            const int c = tx + 8 * j;
             const int64_t cc = c0 + c;
-            float w[4];
+            float* ws = &Ws[c][ty * 8];
+            const float4 w0 = *reinterpret_cast<const float4*>(ws);
+            const float4 w1 = *reinterpret_cast<const float4*>(ws + 4);
+            float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                w[i] = Ws[c][ty * 4 + i] - pacc[i][j];
-                if (cc >= n || r0 + ty * 4 + i >= m) w[i] = 0.f;
+            for (int i = 0; i < 8; ++i) {
+                w[i] -= pacc[i][j];
+                if (cc >= n || r0 + ty * 8 + i >= m) w[i] = 0.f;
                 sqf = fmaf(w[i], w[i], sqf);
-                Ws[c][ty * 4 + i] = w[i];
             }
+            *reinterpret_cast<float4*>(ws) = make_float4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<float4*>(ws + 4) = make_float4(w[4], w[5], w[6], w[7]);
             if (cc < n) {
-                const int64_t r = r0 + ty * 4;
+                const int64_t r = r0 + ty * 8;
                 float* dst = d.W + r + cc * d.ldw;
-                if (r + 4 <= m) {
-                    *reinterpret_cast<float4*>(dst) = make_float4(w[0], w[1], w[2], w[3]);   // ldw % 4 == 0
+                if (r + 8 <= m) {   // ldw % 4 == 0: two aligned 16-byte stores
+                    *reinterpret_cast<float4*>(dst) = make_float4(w[0], w[1], w[2], w[3]);
+                    *reinterpret_cast<float4*>(dst + 4) = make_float4(w[4], w[5], w[6], w[7]);
                 } else {
-                    for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < 8; ++i)
                         if (r + i < m) dst[i] = w[i];
                 }
             }
@@ -432,18 +438,37 @@ __global__ void __launch_bounds__(NT) k_rows_update(const GMat* __restrict__ mat
         // Y += W(tile, chunk) Omega_{i+1}(chunk, :)
 #pragma unroll 8
         for (int c = 0; c < KCH; ++c) {
-            const float4 a = *reinterpret_cast<const float4*>(&Ws[c][ty * 4]);
-            const float4 o = *reinterpret_cast<const float4*>(&Os[c][tx * 4]);
-            const float av[4] = {a.x, a.y, a.z, a.w}, ov[4] = {o.x, o.y, o.z, o.w};
+            const float4 a0 = *reinterpret_cast<const float4*>(&Ws[c][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&Ws[c][ty * 8 + 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            float ov[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) ov[j] = Os[c][tx + 8 * j];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) yacc[i][j] = fmaf(av[i], ov[j], yacc[i][j]);
         }
     }
-    rows_store(yacc, m, r0, d.Y, d.ldw, pn, false);
-    const double t = block_sum_d(sq, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = t;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t r = r0 + ty * 8 + i;
+        if (r >= m) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = tx + 8 * j;
+            d.Y[r + (int64_t)c * d.ldw] = (c < pn) ? yacc[i][j] : 0.f;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if ((tid & 31) == 0) red[tid >> 5] = sq;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < NTU / 32; ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -461,7 +486,7 @@ __global__ void __launch_bounds__(NT) k_cols(const GMat* __restrict__ mats, cons
                                              const Item* __restrict__ items, int first, double* __restrict__ part) {
     constexpr int W = (OP == kColProject) ? TC : TCR;   // columns per item
     constexpr int NQ = W / 32;                           // column slots per thread
-    __shared__ float Ps[KCH][BP + 1];    // Ps[r][j]: Q_i or Y1 rows of the chunk
+    __shared__ __align__(16) float Ps[KCH][BP + 4];   // Ps[r][j]: Q_i or Y1 rows of the chunk
     __shared__ float Vs[KCH][W + 1];     // Vs[r][c]: Wsrc or Qbar columns of the item
     __shared__ double red[NT / 32];
     const Item it = items[blockIdx.x];
@@ -525,9 +550,9 @@ __global__ void __launch_bounds__(NT) k_cols(const GMat* __restrict__ mats, cons
         if (r0 + KCH < m) load(r0 + KCH);
 #pragma unroll 4
         for (int rr = 0; rr < KCH; ++rr) {
-            float a[4], v[NQ];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = Ps[rr][tj * 4 + i];
+            const float4 a4 = *reinterpret_cast<const float4*>(&Ps[rr][tj * 4]);   // warp-uniform: broadcast
+            const float a[4] = {a4.x, a4.y, a4.z, a4.w};
+            float v[NQ];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) v[q] = Vs[rr][lane + 32 * q];
 #pragma unroll
@@ -800,7 +825,7 @@ cudaError_t launch_block(cudaStream_t cs, const Tables& T, int i, int b, uint64_
     const int64_t tot = T.n_max * BP;
     k_omega_rows<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, cs>>>(T.n_max, (int64_t)(i + 1) * b, b,
                                                                                  seed, Om_next);
-    k_rows_update<<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, b, first, Om_next, T.rows_part);
+    k_rows_update<<<T.nrows, NTU, 0, cs>>>(T.mats, T.st, T.rows, b, first, Om_next, T.rows_part);
     k_mat<kMatDirect><<<T.count, NT, 0, cs>>>(T.mats, T.st, b, T.rows_part, T.proj_part, T.gpart);
     nl += 8;
     *launches += nl;

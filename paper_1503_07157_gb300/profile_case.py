@@ -14,6 +14,8 @@
                 eps = 1e-4 ||A||_F)
   --case batched  the same for the 512-matrix batch (b = 32, eps_t =
                 1e-3 ||A_t||_F) through rqb_factor_batched
+  --case batched64  the first 64 matrices of that batch (about 0.6 GB), for
+                --set full captures of the grouped kernels
 Usage: python -m paper_1503_07157_gb300.profile_case [--case small|mixed|fp32|fp64]
 """
 import argparse
@@ -27,7 +29,7 @@ if ROOT not in sys.path:
 
 def main() -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["small", "mixed", "fp32", "fp64", "batched"], default="small")
+    ap.add_argument("--case", choices=["small", "mixed", "fp32", "fp64", "batched", "batched64"], default="small")
     args = ap.parse_args()
     import torch
     import inputs
@@ -41,9 +43,9 @@ def main() -> int:
         with rqb.Handle(torch.float32, prec=rqb.RQB_PREC_TF32X3, max_rank=512, fixed_rank=True) as h:
             _, _, k, rc = h.rqb_factor(A, 0.0, 256, 0, check=False)
             torch.cuda.synchronize()
-    elif args.case == "batched":
+    elif args.case in ("batched", "batched64"):
         import numpy as np
-        cases = inputs.batched_sizes(512, seed=0)
+        cases = inputs.batched_sizes(512, seed=0)[: (512 if args.case == "batched" else 64)]
         mats, eps = [], []
         for i, c in enumerate(cases):
             s = inputs.spectrum_exp(min(c.m, c.n), c.rate)

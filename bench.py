@@ -15,6 +15,10 @@ Workloads (--workload):
         the same eps (matched-eps comparison)
   batched  512 FP32 matrices of uneven sizes, b = 32, eps_t = 1e-3 ||A_t||_F,
         one rqb_factor_batched call per step
+  adjoint  8192 x 4096 FP32 (N(0,1)/sqrt(4096) plus a planted rank-64 part of
+        norm 10), fixed rank k = 256, b = 64: per step the forward
+        factorization, X = Q B, G = 2 (X - T) and the hand-written backward
+        dL/dA of L = ||Q Q^T A - T||_F^2
 
 The default run also measures the mixed and batched forms (a few steps each,
 --no-forms skips them) and reports them under "forms" in the same line.
@@ -54,6 +58,8 @@ WORKLOADS = {
 WORKLOADS["mixed"] = dict(name="randQB_b split-TF32 32768x16384 s_j=10^(-4j/2000) (j<=2000) then 1e-6 b=256 "
                                "eps=1e-3||A||_F", m=32768, n=16384, b=256, eps_rel=1e-3, dtype="float32",
                           spectrum="mixed", prec="tf32x3")
+WORKLOADS["adjoint"] = dict(name="randQB_b fixed-rank forward + adjoint, 8192x4096 FP32, k=256, b=64", m=8192,
+                            n=4096, b=64, k=256, eps_rel=0.0, dtype="float32", spectrum="adjoint")
 WORKLOADS["batched"] = dict(name="randQB_b batched FP32: 512 matrices, m~U[256,4096], n~U[128,min(m,2048)], "
                                  "s_j=exp(-j/r), r~U[10,200], b=32, eps_t=1e-3||A_t||_F",
                             m=0, n=0, b=32, eps_rel=1e-3, dtype="float32", spectrum="exp", count=512)
@@ -310,6 +316,65 @@ def run_ours(args, w: dict, rank: int, world: int, dist):
                 launches=launches // max(args.steps, 1), stream=stream)
 
 
+def adjoint_flops(m: int, n: int, k: int) -> float:
+    """Useful FLOPs of rqb_backward: R = B Omega, Q^T G, Q (Q^T G), G B^T,
+    G^T Q, A (G^T Q), Q^T M, Q (Q^T M), M R^-T, N Omega^T."""
+    return 12.0 * m * n * k + 6.0 * m * k * k + 2.0 * n * k * k
+
+
+def run_adjoint(args, w: dict, rank: int, world: int, dist) -> dict:
+    """Config-5 workload: forward at fixed rank, X = Q B, G = 2 (X - T), backward."""
+    import torch
+    import inputs
+    from paper_1503_07157_gb300 import build as _build
+    _build.build()
+    from paper_1503_07157_gb300 import rqb
+    m, n, b, k = w["m"], w["n"], w["b"], w["k"]
+    A_np, T_np, _ = inputs.config_adjoint_np(m=m, n=n, seed=5, rank=64, norm=10.0)
+    A = torch.as_tensor(A_np.T, dtype=torch.float32, device="cuda").t()
+    T = torch.as_tensor(T_np.T, dtype=torch.float32, device="cuda").t()
+    del A_np, T_np
+    stream = torch.cuda.Stream()
+    h = rqb.Handle(torch.float32, stream=stream, max_rank=k, fixed_rank=True)
+
+    def step():
+        h.rqb_factor(A, 0.0, b, seed=0)
+        X = h.rqb_reconstruct(m, n)
+        with torch.cuda.stream(stream):
+            G = 2.0 * (X - T)
+        return h.rqb_backward(G)
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(torch.cuda.current_device())
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.25)
+    launches = 0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+        launches += h.rqb_get_stats().kernel_launches
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, torch.device("cuda", torch.cuda.current_device()))
+    s_blocks = k // b
+    F = useful_flops(m, n, b, s_blocks) + 2.0 * m * n * k + adjoint_flops(m, n, k)   # forward, X = Q B, backward
+    h.close()
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    peak = alu_peak_tflops("float32", props.multi_processor_count, float(peaks.get("sm_max_mhz", 2070.0)))
+    value = aggregate_value(F, world, ms)
+    return dict(value=value, ms=ms, F=F, clocks=clk, launches=launches // max(args.steps, 1),
+                roofline={"bound": "alu", "kernel": "whole step (SIMT GEMMs of forward and backward)",
+                          "achieved": round(F / (ms * 1e-3) / 1e12, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+                          "frac": round(F / (ms * 1e-3) / 1e12 / peak, 4), "traffic": None,
+                          "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
+                                         f"{float(peaks.get('sm_max_mhz', 2070.0)):.0f} MHz"})
+
+
 def run_plain_matched(args, w: dict, res: dict, steps: int = 2) -> dict:
     """The plain FP32 path (RQB_PREC_NATIVE) on the same matrix at the same eps."""
     import torch
@@ -526,6 +591,22 @@ def main():
     rank, world, dist = init_dist()
     if args.workload == "batched":
         return main_batched(args, w, rank, world, dist)
+    if args.workload == "adjoint":
+        r = run_adjoint(args, w, rank, world, dist)
+        if rank == 0:
+            line = {"metric": METRIC, "value": round(r["value"], 4), "unit": "TFLOP/s", "n_gpus": world,
+                    "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["ms"], 3),
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                    "data": "synthetic (N(0,1)/sqrt(n) plus a planted rank-64 part; T ~ N(0,1))",
+                    "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "b": w["b"], "k": w["k"],
+                               "useful_flops_per_step": r["F"], "parallelism": f"replicas x{world}" if world > 1
+                               else "single GPU", "l2": "inputs larger than L2 (A is 0.13 GB, T and G too)"},
+                    "roofline": r["roofline"], "cpu_baseline": None, "e2e": None,
+                    "gpu_launches": r["launches"] * args.steps, "clocks": r["clocks"]}
+            print(json.dumps(line), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
     res = run_ours(args, w, rank, world, dist)
     e2e = run_e2e(args, w, res) if rank == 0 else None
     matched = run_plain_matched(args, w, res) if (rank == 0 and w.get("prec") == "tf32x3") else None
@@ -592,6 +673,11 @@ def run_forms(args, rank: int, world: int, dist) -> dict:
     out["batched"]["speedup_vs_loop_of_single_calls"] = round(rb["extra"]["loop_of_single_calls_ms"] / rb["ms"], 3)
     gc.collect()
     torch.cuda.empty_cache()
+    wa = WORKLOADS["adjoint"]
+    a.steps = 10
+    ra = run_adjoint(a, wa, rank, world, dist)
+    out["adjoint"] = {"workload": wa["name"], "value": round(ra["value"], 4), "unit": "TFLOP/s",
+                      "ms_per_step": round(ra["ms"], 3), "steps": a.steps, "roofline": ra["roofline"]}
     return out
 
 

@@ -10,13 +10,16 @@ Functions and the passages they follow:
   philox4x32_10  -- the counter-based generator of Salmon et al. (SC'11)
   omega          -- Fig. randQB_b line (2), Omega_i = randn(n, b), indexed by
                     global column so that blocks slice one Omega (eq. OmegaBlock);
-                    prec 64, 32 or 19 (binary32 draw rounded to TF32)
+                    prec 64, 32, 19 (binary32 draw rounded to TF32) or 8
+                    (rounded to BF16)
   round_tf32     -- rounding to 11 significant bits, ties away from zero
+  round_bf16     -- rounding to 8 significant bits, ties to even
   orth           -- Sec. 2.4, unpivoted Householder QR with diag(R) >= 0
   sketch         -- Fig. randQB_b line (3), A Omega_i
   orth_reproject -- Fig. randQB_b lines (3) and (3')
   randqb_b       -- Fig. randQB_b (power > 0: Fig. randQB_pb; skip_inner_orth:
-                    the Sec. 5.4 variant)
+                    the Sec. 5.4 variant; storage_prec 16: the residual kept
+                    in BF16, stopping on its direct norm)
   randqb         -- Fig. randQB (unblocked)
   svd_values     -- singular values by one-sided Jacobi (for the Eckart-Young
                     bound of eq. minerrors on small inputs)
@@ -57,6 +60,11 @@ def _lib():
         lib.orc_qqta_adjoint.restype = i32
         lib.orc_round_tf32.argtypes = [dbl]
         lib.orc_round_tf32.restype = dbl
+        lib.orc_round_bf16.argtypes = [dbl]
+        lib.orc_round_bf16.restype = dbl
+        lib.orc_randqb_b_store.argtypes = [P, i64, i64, i64, dbl, i64, u64, i64, i32, i32, i32, i32, i32,
+                                           P, i64, P, i64, P]
+        lib.orc_randqb_b_store.restype = i32
         _LIB = lib
     return _LIB
 
@@ -89,6 +97,10 @@ def philox4x32_10(ctr, key):
 
 def round_tf32(x: float) -> float:
     return float(_lib().orc_round_tf32(float(x)))
+
+
+def round_bf16(x: float) -> float:
+    return float(_lib().orc_round_bf16(float(x)))
 
 
 def omega(seed: int, n: int, col0: int, ncols: int, prec: int = 64, stream: int = 0):
@@ -144,7 +156,7 @@ class QBResult:
 
 
 def randqb_b(A, eps: float, b: int, seed: int = 0, max_rank: int = 0, fixed_rank: bool = False,
-             power: int = 0, skip_inner_orth: bool = False, omega_prec: int = 64) -> QBResult:
+             power: int = 0, skip_inner_orth: bool = False, omega_prec: int = 64, storage_prec: int = 64) -> QBResult:
     A = _f64(A)
     m, n = A.shape
     rmax = min(m, n)
@@ -155,9 +167,9 @@ def randqb_b(A, eps: float, b: int, seed: int = 0, max_rank: int = 0, fixed_rank
     E = np.zeros(nbmax)
     D = np.zeros(nbmax)
     res = _Res(0, 0, 0, 0, 0.0, E.ctypes.data, D.ctypes.data, nbmax)
-    rc = _lib().orc_randqb_b(_ptr(A), m, n, m, float(eps), b, seed, kcap, int(fixed_rank),
-                             int(power), int(skip_inner_orth), int(omega_prec),
-                             _ptr(Q), m, _ptr(B), kcap, ctypes.byref(res))
+    rc = _lib().orc_randqb_b_store(_ptr(A), m, n, m, float(eps), b, seed, kcap, int(fixed_rank),
+                                   int(power), int(skip_inner_orth), int(omega_prec), int(storage_prec),
+                                   _ptr(Q), m, _ptr(B), kcap, ctypes.byref(res))
     if rc != 0:
         raise ValueError("orc_randqb_b: invalid arguments")
     k, s = int(res.k), int(res.blocks)

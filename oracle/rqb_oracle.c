@@ -79,21 +79,34 @@ double orc_round_tf32(double x) {
     return ldexp(f < 0 ? -r : r, e - 11);
 }
 
+/* Round x to 8 significant bits (the BF16 format: 7 fraction bits), to
+ * nearest with ties to even: with x = f 2^e, 1/2 <= |f| < 1, the result is
+ * rint(f 2^8) 2^(e - 8) (rint rounds half to even).  Exact in binary64. */
+double orc_round_bf16(double x) {
+    if (x == 0.0 || !isfinite(x)) return x;
+    int e;
+    double f = frexp(x, &e);
+    double r = rint(ldexp(fabs(f), 8));
+    return ldexp(f < 0 ? -r : r, e - 8);
+}
+
 static double orc_omega_entry(uint64_t seed, uint32_t stream, int64_t r, int64_t c, int prec) {
     const double PI = 3.14159265358979323846;
     uint32_t ctr[4] = {(uint32_t)r, (uint32_t)(c >> 1), stream, 0u};
     uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
     uint32_t x[4];
     orc_philox4x32_10(ctr, key, x);
-    if (prec == 32 || prec == 19) {
+    if (prec == 32 || prec == 19 || prec == 8) {
         /* binary32 evaluation: 23-bit uniforms (j + 1/2) 2^-23, exact in float;
-         * prec 19 then rounds the binary32 value to TF32 */
+         * prec 19 then rounds the binary32 value to TF32, prec 8 to BF16 */
         float u1 = ((float)(x[0] >> 9) + 0.5f) * 0x1p-23f;
         float u2 = ((float)(x[2] >> 9) + 0.5f) * 0x1p-23f;
         double rad = sqrt(-2.0 * log((double)u1));
         double ang = 2.0 * PI * (double)u2;
         double z = (c & 1) ? rad * sin(ang) : rad * cos(ang);
-        return prec == 19 ? orc_round_tf32((double)(float)z) : (double)(float)z;
+        if (prec == 19) return orc_round_tf32((double)(float)z);
+        if (prec == 8) return orc_round_bf16((double)(float)z);
+        return (double)(float)z;
     }
     /* binary64: 53-bit uniforms ((x0 >> 5) 2^26 + (x1 >> 6) + 1/2) 2^-53 */
     double u1 = ((double)(x[0] >> 5) * 67108864.0 + (double)(x[1] >> 6) + 0.5) * 0x1p-53;
@@ -269,7 +282,17 @@ int orc_randqb_b(const double* A, int64_t m, int64_t n, int64_t lda,
                  int fixed_rank, int power, int skip_inner_orth, int omega_prec,
                  double* Q, int64_t ldq, double* B, int64_t ldb,
                  orc_qb_result* res) {
+    return orc_randqb_b_store(A, m, n, lda, eps, b, seed, max_rank, fixed_rank, power, skip_inner_orth,
+                              omega_prec, 64, Q, ldq, B, ldb, res);
+}
+
+int orc_randqb_b_store(const double* A, int64_t m, int64_t n, int64_t lda,
+                       double eps, int64_t b, uint64_t seed, int64_t max_rank,
+                       int fixed_rank, int power, int skip_inner_orth, int omega_prec,
+                       int storage_prec, double* Q, int64_t ldq, double* B, int64_t ldb,
+                       orc_qb_result* res) {
     if (m <= 0 || n <= 0 || b <= 0 || lda < m || eps < 0.0 || power < 0 || !res) return -1;
+    if (storage_prec != 64 && storage_prec != 16) return -1;
     const int64_t rmax = (m < n) ? m : n;
     int64_t kcap = (max_rank <= 0 || max_rank > rmax) ? rmax : max_rank;
     if (ldq < m || ldb < kcap) return -1;
@@ -331,19 +354,28 @@ int orc_randqb_b(const double* A, int64_t m, int64_t n, int64_t lda,
                 W[r + c * m] -= s;
             }
         }
+        /* a residual stored in BF16 is rounded after every downdate */
+        if (storage_prec == 16) {
+#pragma omp parallel for schedule(static)
+            for (int64_t c = 0; c < n; ++c)
+                for (int64_t r = 0; r < m; ++r) W[r + c * m] = orc_round_bf16(W[r + c * m]);
+        }
         /* (8) Q = [Q_1 ... Q_i], B = [B_1; ...; B_i]. */
         for (int64_t c = 0; c < bi; ++c)
             for (int64_t r = 0; r < m; ++r) Q[r + (k + c) * ldq] = Qi[r + c * m];
         for (int64_t c = 0; c < n; ++c)
             for (int64_t r = 0; r < bi; ++r) B[k + r + c * ldb] = Bi[r + c * bi];
+        const double Dcur = frob2(m, n, W, m);
         if (blocks < res->max_blocks) {
             if (res->E) res->E[blocks] = E;
-            if (res->D) res->D[blocks] = frob2(m, n, W, m);
+            if (res->D) res->D[blocks] = Dcur;
         }
         k += bi;
         blocks += 1;
-        /* (6) stop once the residual norm is within tolerance. */
-        if (!fixed_rank && E <= eps2) {
+        /* (6) stop once the residual norm is within tolerance: E_i (exact
+         * arithmetic: E_i = ||A^(i)||^2); a rounded residual no longer follows
+         * E_i, so the stored residual's own norm decides. */
+        if (!fixed_rank && ((storage_prec == 64) ? E : Dcur) <= eps2) {
             converged = 1;
             break;
         }

@@ -31,6 +31,10 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
  * ties away from zero. */
 double orc_round_tf32(double x);
 
+/* x rounded to 8 significant bits (BF16: 7 fraction bits), to nearest, ties
+ * to even. */
+double orc_round_bf16(double x);
+
 /* Gaussian test matrix Omega (Fig. randQB_b, line (2): Omega_i = randn(n, b)).
  * Writes the n x ncols block whose first column is global column col0 of the
  * infinite Gaussian matrix defined by (seed, stream).  Entry (r, c) depends
@@ -39,7 +43,8 @@ double orc_round_tf32(double x);
  * prec = 32: the binary32 evaluation (23-bit uniforms, result rounded to
  * float, returned widened to double).  prec = 19: the prec-32 value rounded
  * to TF32 by orc_round_tf32, so that a tensor-core product with Omega as an
- * operand is exact.  out is n x ncols, leading dim ldo. */
+ * operand is exact; prec = 8: rounded to BF16 by orc_round_bf16.  out is
+ * n x ncols, leading dim ldo. */
 void orc_omega(uint64_t seed, uint32_t stream, int64_t n, int64_t col0,
                int64_t ncols, int prec, double* out, int64_t ldo);
 
@@ -72,7 +77,7 @@ typedef struct {
  *   power  P of randQB_pb (0 gives randQB_b)
  *   skip_inner_orth  nonzero: the Sec. 5.4 variant that applies the powers
  *          without the intermediate orth() calls
- *   omega_prec  64, 32 or 19, see orc_omega
+ *   omega_prec  64, 32, 19 or 8, see orc_omega
  *   Q      m x max_rank output, leading dim ldq
  *   B      max_rank x n output, leading dim ldb
  * Returns 0 on success, -1 on invalid arguments. */
@@ -81,6 +86,17 @@ int orc_randqb_b(const double* A, int64_t m, int64_t n, int64_t lda,
                  int fixed_rank, int power, int skip_inner_orth, int omega_prec,
                  double* Q, int64_t ldq, double* B, int64_t ldb,
                  orc_qb_result* res);
+
+/* orc_randqb_b with the residual stored in a narrower format: storage_prec
+ * 64 is orc_randqb_b; 16 rounds the residual to BF16 (orc_round_bf16) after
+ * every downdate (line (5)), as a path that keeps A^(i) in BF16 does, and
+ * then stops on the stored residual's norm D_i <= eps^2 (line (6)), since a
+ * rounded residual no longer satisfies ||A^(i)||^2 = E_i. */
+int orc_randqb_b_store(const double* A, int64_t m, int64_t n, int64_t lda,
+                       double eps, int64_t b, uint64_t seed, int64_t max_rank,
+                       int fixed_rank, int power, int skip_inner_orth, int omega_prec,
+                       int storage_prec, double* Q, int64_t ldq, double* B, int64_t ldb,
+                       orc_qb_result* res);
 
 /* Unblocked randQB (Fig. randQB): Omega = the first l global columns,
  * Q = orth(A Omega), B = Q^T A.  Q is m x l, B is l x n. */

@@ -13,6 +13,10 @@ Workloads (--workload):
         s_j = 10^(-4 j / 2000) for j <= 2000 then 1e-6, b = 256,
         eps = 1e-3 ||A||_F; the plain FP32 path is timed on the same matrix at
         the same eps (matched-eps comparison)
+  bf16  the mixed recipe stored in BF16 (RQB_BF16: A and the residual in BF16,
+        BF16 tensor-core products, Q and B in FP32), eps = 1e-2 ||A||_F; the
+        plain FP32 and split-TF32 paths are timed on the same (BF16-exact)
+        matrix at the same eps
   batched  512 FP32 matrices of uneven sizes, b = 32, eps_t = 1e-3 ||A_t||_F,
         one rqb_factor_batched call per step
   adjoint  8192 x 4096 FP32 (N(0,1)/sqrt(4096) plus a planted rank-64 part of
@@ -58,6 +62,9 @@ WORKLOADS = {
 WORKLOADS["mixed"] = dict(name="randQB_b split-TF32 32768x16384 s_j=10^(-4j/2000) (j<=2000) then 1e-6 b=256 "
                                "eps=1e-3||A||_F", m=32768, n=16384, b=256, eps_rel=1e-3, dtype="float32",
                           spectrum="mixed", prec="tf32x3")
+WORKLOADS["bf16"] = dict(name="randQB_b BF16 storage 32768x16384 s_j=10^(-4j/2000) (j<=2000) then 1e-6 b=256 "
+                              "eps=1e-2||A||_F", m=32768, n=16384, b=256, eps_rel=1e-2, dtype="bfloat16",
+                         spectrum="mixed", prec="bf16")
 WORKLOADS["adjoint"] = dict(name="randQB_b fixed-rank forward + adjoint, 8192x4096 FP32, k=256, b=64", m=8192,
                             n=4096, b=64, k=256, eps_rel=0.0, dtype="float32", spectrum="adjoint")
 WORKLOADS["batched"] = dict(name="randQB_b batched FP32: 512 matrices, m~U[256,4096], n~U[128,min(m,2048)], "
@@ -75,6 +82,9 @@ def useful_flops(m: int, n: int, b: int, s: int) -> float:
 # split-TF32 path every product phase is one m x n x b product (the update
 # is not fused with the next sketch), 2 m n b useful FLOPs per launch.
 TC_PASSES = {"sketch": 2, "project": 3, "downdate": 3}
+# BF16 storage: Omega and W are exact BF16 (one pass), Q_i is split (two),
+# Q_i and B_i are split in the update (three).
+TC_PASSES16 = {"sketch": 1, "project": 2, "downdate": 3}
 
 
 def phase_flops(m: int, n: int, b: int, s: int) -> dict:
@@ -108,6 +118,12 @@ def make_workload_device(w: dict, seed: int = 2):
     dt = torch.float64 if w["dtype"] == "float64" else torch.float32
     A = inputs.usv_torch(m, n, s, seed, device="cuda", dtype=dt)
     normA = float(np.sqrt(np.sum(s.astype(np.float64) ** 2)))
+    if w["dtype"] == "bfloat16":
+        Ab = torch.empty(n, m, dtype=torch.bfloat16, device="cuda").t()
+        Ab.copy_(A)
+        del A
+        torch.cuda.empty_cache()
+        return Ab, normA
     return A, normA
 
 
@@ -120,6 +136,9 @@ def make_sample_host(w: dict, frac: float, seed: int = 2):
     A = inputs.usv(m, n, s, seed)
     if w["dtype"] == "float32":
         A = A.astype(np.float32).astype(np.float64)
+    if w["dtype"] == "bfloat16":
+        import oracle
+        A = oracle.round_bf16_array(A)
     return A
 
 
@@ -199,6 +218,15 @@ def alu_peak_tflops(dtype: str, num_sms: int, sm_mhz: float) -> float:
 NCU_TRAFFIC = {"fp32": 1.440e9, "fp64": None, "mixed": None}
 
 
+def oracle_modes(w: dict) -> tuple[int, int]:
+    """Omega precision and residual storage of the oracle run matching a workload."""
+    if w["dtype"] == "float64":
+        return 64, 64
+    if w["dtype"] == "bfloat16":
+        return 8, 16
+    return 32, 64
+
+
 def oracle_baseline(w: dict, frac: float, repeats: int = 1) -> dict:
     """Oracle randQB_b on the workload recipe at frac x size; TFLOP/s and cores."""
     import oracle
@@ -206,12 +234,12 @@ def oracle_baseline(w: dict, frac: float, repeats: int = 1) -> dict:
     m, n = A.shape
     nA = float((A * A).sum()) ** 0.5
     eps = w["eps_rel"] * nA
-    prec = 64 if w["dtype"] == "float64" else 32
+    prec, store = oracle_modes(w)
     times = []
     res = None
     for _ in range(repeats):
         t0 = time.perf_counter()
-        res = oracle.randqb_b(A, eps, w["b"], seed=0, omega_prec=prec)
+        res = oracle.randqb_b(A, eps, w["b"], seed=0, omega_prec=prec, storage_prec=store)
         times.append(time.perf_counter() - t0)
     t = statistics.median(times)
     F = useful_flops(m, n, w["b"], res.blocks)
@@ -230,8 +258,8 @@ def run_ours(args, w: dict, rank: int, world: int, dist):
     A, normA = make_workload_device(w)
     m, n, b = w["m"], w["n"], w["b"]
     eps = w["eps_rel"] * normA
-    dt = torch.float64 if w["dtype"] == "float64" else torch.float32
-    prec = rqb.RQB_PREC_TF32X3 if w.get("prec") == "tf32x3" else rqb.RQB_PREC_NATIVE
+    dt = {"float64": torch.float64, "float32": torch.float32, "bfloat16": torch.bfloat16}[w["dtype"]]
+    prec = {"tf32x3": rqb.RQB_PREC_TF32X3, "bf16": rqb.RQB_PREC_BF16}.get(w.get("prec"), rqb.RQB_PREC_NATIVE)
     stream = torch.cuda.Stream()
     torch.cuda.synchronize()
     h = rqb.Handle(dt, prec=prec, stream=stream, flags=rqb.RQB_FLAG_PHASE_TIMING)
@@ -276,26 +304,31 @@ def run_ours(args, w: dict, rank: int, world: int, dist):
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(dev)
-    if prec == rqb.RQB_PREC_TF32X3:
-        cand = [(phase_ms[i], names[i]) for i in range(len(names)) if names[i] in TC_PASSES and phase_calls[i] > 0]
+    if prec in (rqb.RQB_PREC_TF32X3, rqb.RQB_PREC_BF16):
+        is16 = prec == rqb.RQB_PREC_BF16
+        table = TC_PASSES16 if is16 else TC_PASSES
+        cand = [(phase_ms[i], names[i]) for i in range(len(names)) if names[i] in table and phase_calls[i] > 0]
         dom_ms, dom = max(cand)
         idx = names.index(dom)
         per_launch_ms = phase_ms[idx] / phase_calls[idx]
-        passes = TC_PASSES[dom]
+        passes = table[dom]
         useful = 2.0 * m * n * b
         executed = passes * useful
         achieved = executed / (per_launch_ms * 1e-3) / 1e12
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
-        peak = bf16 / 2.0
-        kern = {"sketch": "k_streamk<sketch> + k_reduce_sketch", "project": "k_streamk<project> + k_reduce_project",
-                "downdate": "k_update"}[dom]
+        peak = bf16 if is16 else bf16 / 2.0
+        sfx = "16" if is16 else ""
+        kern = {"sketch": f"k_streamk{sfx}<sketch> + k_reduce_sketch",
+                "project": f"k_streamk{sfx}<project> + k_reduce_project{sfx}", "downdate": f"k_update{sfx}"}[dom]
+        es = 2 if is16 else 4
         roofline = {"bound": "tensor", "kernel": kern, "achieved": round(achieved, 3), "peak": round(peak, 3),
                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(args.workload),
-                    "peak_source": f"measured bf16 burst {bf16} TFLOP/s (MEASURED_PEAKS.json) x 1/2 "
-                                   f"(nominal TF32:BF16 dense ratio), of measured",
+                    "peak_source": (f"measured bf16 burst {bf16} TFLOP/s (MEASURED_PEAKS.json), of measured" if is16
+                                    else f"measured bf16 burst {bf16} TFLOP/s (MEASURED_PEAKS.json) x 1/2 "
+                                         f"(nominal TF32:BF16 dense ratio), of measured"),
                     "flops_per_launch": executed, "mma_passes": passes,
                     "useful_tflops": round(useful / (per_launch_ms * 1e-3) / 1e12, 3),
-                    "hbm_gbs": round((2 if dom == "downdate" else 1) * m * n * 4 / (per_launch_ms * 1e-3) / 1e9, 1),
+                    "hbm_gbs": round((2 if dom == "downdate" else 1) * m * n * es / (per_launch_ms * 1e-3) / 1e9, 1),
                     "phase_ms_per_step": per_step}
     else:
         cand = [(phase_ms[i], names[i]) for i in range(len(names)) if names[i] in pf and phase_calls[i] > 0]
@@ -375,26 +408,35 @@ def run_adjoint(args, w: dict, rank: int, world: int, dist) -> dict:
                                          f"{float(peaks.get('sm_max_mhz', 2070.0)):.0f} MHz"})
 
 
-def run_plain_matched(args, w: dict, res: dict, steps: int = 2) -> dict:
-    """The plain FP32 path (RQB_PREC_NATIVE) on the same matrix at the same eps."""
+def run_plain_matched(args, w: dict, res: dict, steps: int = 2, prec: int | None = None) -> dict:
+    """The plain FP32 path (RQB_PREC_NATIVE; or the split-TF32 path with prec)
+    on the same matrix (widened to FP32 for a BF16 workload) at the same eps."""
     import torch
     from paper_1503_07157_gb300 import rqb
     m, n, b = w["m"], w["n"], w["b"]
-    h = rqb.Handle(torch.float32, stream=res["stream"])
-    _, _, k, rc = h.rqb_factor(res["A"], res["eps"], b, seed=0)
+    prec = rqb.RQB_PREC_NATIVE if prec is None else prec
+    A = res["A"]
+    if A.dtype != torch.float32:
+        A32 = torch.empty(n, m, dtype=torch.float32, device=A.device).t()
+        A32.copy_(A)
+        A = A32
+    h = rqb.Handle(torch.float32, prec=prec, stream=res["stream"])
+    _, _, k, rc = h.rqb_factor(A, res["eps"], b, seed=0)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(res["stream"])
     for _ in range(steps):
-        _, _, k, rc = h.rqb_factor(res["A"], res["eps"], b, seed=0)
+        _, _, k, rc = h.rqb_factor(A, res["eps"], b, seed=0)
     ev1.record(res["stream"])
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / steps
     s_blocks = h.rqb_get_stats().blocks
     h.close()
+    del A
     F = useful_flops(m, n, b, s_blocks)
-    return {"impl": "plain FP32 (RQB_PREC_NATIVE)", "ms_per_step": round(ms, 3), "value": round(F / (ms * 1e-3) / 1e12, 4),
-            "unit": "TFLOP/s", "k": k, "steps": steps, "speedup_of_mixed": round(ms / res["ms"], 3)}
+    name = "split-TF32 (RQB_PREC_TF32X3)" if prec == rqb.RQB_PREC_TF32X3 else "plain FP32 (RQB_PREC_NATIVE)"
+    return {"impl": name, "ms_per_step": round(ms, 3), "value": round(F / (ms * 1e-3) / 1e12, 4),
+            "unit": "TFLOP/s", "k": k, "steps": steps, "speedup_of_form": round(ms / res["ms"], 3)}
 
 
 def run_e2e(args, w: dict, res: dict) -> dict:
@@ -404,12 +446,13 @@ def run_e2e(args, w: dict, res: dict) -> dict:
     from paper_1503_07157_gb300 import rqb
     m, n, b = w["m"], w["n"], w["b"]
     dt = res["A"].dtype
+    dto = torch.float64 if dt == torch.float64 else torch.float32
     cap = min(m, n, args.e2e_max_rank)
     A_host = torch.empty(n, m, dtype=dt, pin_memory=True).t()
     A_host.copy_(res["A"])
-    Q_host = torch.empty(cap, m, dtype=dt, pin_memory=True).t()
-    B_host = torch.empty(n, cap, dtype=dt, pin_memory=True).t()
-    prec = rqb.RQB_PREC_TF32X3 if w.get("prec") == "tf32x3" else rqb.RQB_PREC_NATIVE
+    Q_host = torch.empty(cap, m, dtype=dto, pin_memory=True).t()
+    B_host = torch.empty(n, cap, dtype=dto, pin_memory=True).t()
+    prec = {"tf32x3": rqb.RQB_PREC_TF32X3, "bf16": rqb.RQB_PREC_BF16}.get(w.get("prec"), rqb.RQB_PREC_NATIVE)
     h = rqb.Handle(dt, prec=prec, stream=res["stream"], max_rank=cap)
     times, k = [], 0
     for i in range(args.warmup + max(1, args.e2e_steps)):
@@ -421,9 +464,9 @@ def run_e2e(args, w: dict, res: dict) -> dict:
             times.append(t1 - t0)
     h.close()
     t = statistics.median(times)
-    es = A_host.element_size()
+    es, eo = A_host.element_size(), Q_host.element_size()
     return {"value": round(res["F"] / t / 1e12, 4), "unit": "TFLOP/s", "h2d_bytes_per_step": m * n * es,
-            "d2h_bytes_per_step": (m * k + k * n) * es, "ms_per_step": round(t * 1e3, 3),
+            "d2h_bytes_per_step": (m * k + k * n) * eo, "ms_per_step": round(t * 1e3, 3),
             "api": "rqb_factor_host (pinned host buffers)"}
 
 
@@ -609,7 +652,11 @@ def main():
         return 0
     res = run_ours(args, w, rank, world, dist)
     e2e = run_e2e(args, w, res) if rank == 0 else None
-    matched = run_plain_matched(args, w, res) if (rank == 0 and w.get("prec") == "tf32x3") else None
+    matched = run_plain_matched(args, w, res) if (rank == 0 and w.get("prec") in ("tf32x3", "bf16")) else None
+    matched_tc = None
+    if rank == 0 and w.get("prec") == "bf16":
+        from paper_1503_07157_gb300 import rqb as _rqb
+        matched_tc = run_plain_matched(args, w, res, prec=_rqb.RQB_PREC_TF32X3)
     forms = None
     if args.workload == "fp32" and not args.no_forms:
         forms = run_forms(args, rank, world, dist)
@@ -620,20 +667,24 @@ def main():
         line = {
             "metric": METRIC, "value": round(res["value"], 4), "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(res["ms"], 4),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32" if
-            w["dtype"] == "float32" else "f64", "data": "synthetic (seeded A = U diag(s) V^T, U, V from QR of "
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"float32": "f32", "float64": "f64", "bfloat16": "bf16 (A, W; FP32 accumulate, FP32 Q/B)"}[
+                w["dtype"]], "data": "synthetic (seeded A = U diag(s) V^T, U, V from QR of "
             "Gaussian matrices; Omega Philox4x32-10 + Box-Muller)",
             "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "b": w["b"], "eps_rel": w["eps_rel"],
                        "k": res["k"], "blocks": res["s"], "useful_flops_per_step": res["F"],
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "input larger than L2 (A is %.2f GB)" % (w["m"] * w["n"] *
-                                                                       (4 if w["dtype"] == "float32" else 8) / 1e9)
+                                                                       {"float32": 4, "float64": 8, "bfloat16": 2}[
+                                                                           w["dtype"]] / 1e9)
                        if w["m"] * w["n"] * 4 > 129e6 else "L2 not flushed: input fits in L2"},
             "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": res["launches"]
             * args.steps, "clocks": res["clocks"],
         }
         if matched is not None:
             line["plain_fp32_matched_eps"] = matched
+        if matched_tc is not None:
+            line["split_tf32_matched_eps"] = matched_tc
         if forms is not None:
             line["forms"] = forms
         if cpu is not None:
@@ -660,6 +711,16 @@ def run_forms(args, rank: int, world: int, dist) -> dict:
                     "ms_per_step": round(r["ms"], 3), "steps": a.steps, "k": r["k"], "blocks": r["s"],
                     "roofline": r["roofline"], "plain_fp32_matched_eps": run_plain_matched(a, wm, r) if rank == 0
                     else None}
+    r["h"].close()
+    del r
+    gc.collect()
+    torch.cuda.empty_cache()
+    w16 = WORKLOADS["bf16"]
+    r = run_ours(a, w16, rank, world, dist)
+    out["bf16"] = {"workload": w16["name"], "value": round(r["value"], 4), "unit": "TFLOP/s",
+                   "ms_per_step": round(r["ms"], 3), "steps": a.steps, "k": r["k"], "blocks": r["s"],
+                   "roofline": r["roofline"],
+                   "plain_fp32_matched_eps": run_plain_matched(a, w16, r) if rank == 0 else None}
     r["h"].close()
     del r
     gc.collect()
@@ -742,13 +803,13 @@ def run_reference(args, w: dict) -> int:
     m, n = A.shape
     nA = float((A * A).sum()) ** 0.5
     eps = w["eps_rel"] * nA
-    prec = 64 if w["dtype"] == "float64" else 32
+    prec, store = oracle_modes(w)
     steps = max(1, min(args.steps, 5))
     warm = min(args.warmup, 1)
     times, r = [], None
     for i in range(warm + steps):
         t0 = time.perf_counter()
-        r = oracle.randqb_b(A, eps, w["b"], seed=0, omega_prec=prec)
+        r = oracle.randqb_b(A, eps, w["b"], seed=0, omega_prec=prec, storage_prec=store)
         if i >= warm:
             times.append(time.perf_counter() - t0)
     t = sum(times) / len(times)

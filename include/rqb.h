@@ -64,6 +64,14 @@ typedef enum { RQB_F64 = 0, RQB_F32 = 1, RQB_BF16 = 2 } rqb_dtype;
 
 /* Arithmetic of the n- and m-long products (sketch, B = Q^T A, downdate).
  * NATIVE: the dtype's own arithmetic on the SIMT pipes (FP64 or FP32).
+ * TF32X3 (FP32 handles): tensor-core products with FP32 operands split into
+ *   TF32 hi + lo parts (2 or 3 MMA passes), FP32 accumulation.
+ * BF16 (BF16 handles; NATIVE means the same there): A and the downdated
+ *   residual are stored in BF16 and the products run on BF16 tensor-core
+ *   MMAs with FP32 accumulation -- W Omega exactly (Omega rounded to BF16),
+ *   Q_i^T W and Q_i B_i with Q_i and B_i split into BF16 hi + lo parts.  Each
+ *   downdate rounds the new residual to BF16 (nearest even).  Q, B and Y are
+ *   FP32.
  * Panel Gram matrices, Cholesky factors, re-projection coefficients and the
  * Frobenius downdate are accumulated in FP64 in every mode. */
 typedef enum { RQB_PREC_NATIVE = 0, RQB_PREC_TF32X3 = 1, RQB_PREC_BF16 = 2 } rqb_prec;
@@ -126,7 +134,9 @@ typedef struct rqb_handle_s* rqb_handle;
 
 /* Create a handle on the current CUDA device.  cfg is copied.
  * Errors: RQB_ERR_INVALID (null pointer, unknown dtype/prec, flags != 0),
- *         RQB_ERR_UNSUPPORTED (dtype/prec pair not built), RQB_ERR_OOM. */
+ *         RQB_ERR_UNSUPPORTED (dtype/prec pair not built: TF32X3 needs
+ *         RQB_F32, RQB_PREC_BF16 needs RQB_BF16, and a BF16 handle needs
+ *         power = 0), RQB_ERR_OOM. */
 int rqb_create(rqb_handle* h, const rqb_config* cfg);
 
 /* Release the handle and everything it owns (Q, B, workspace). */
@@ -147,7 +157,11 @@ int rqb_destroy(rqb_handle h);
  * Stop rule: after B_i, E_i = ||A||_F^2 - sum_j ||B_j||_F^2 (FP64) is compared
  * with eps^2 (Sec. 4.2 with Prop. 4.1(b)); when E_i is within the rounding
  * band of the working precision around eps^2 the decision is taken on the
- * directly computed ||A^(i)||_F^2 instead, as in line (6).
+ * directly computed ||A^(i)||_F^2 instead, as in line (6).  BF16 handles
+ * (A in BF16, Q and B returned in FP32) need m >= 128 and n >= 256
+ * (RQB_ERR_UNSUPPORTED otherwise) and decide every block on the direct
+ * ||A^(i)||_F^2 of the stored (rounded) residual, since the BF16 rounding of
+ * each downdate moves the residual away from E_i; stats.E still reports E_i.
  * Returns RQB_OK, RQB_NOT_CONVERGED, or an error. */
 int rqb_factor(rqb_handle h, const void* A, int64_t m, int64_t n, int64_t lda,
                double eps, int64_t b, uint64_t seed,
@@ -197,7 +211,8 @@ int rqb_reconstruct(rqb_handle h, void* X, int64_t ldx);
  * are kept).  G = dL_dX (m x n, leading dim ldg), dL_dA (m x n, leading dim
  * ldda, caller-owned, overwritten).  The A passed to the factorization must
  * still be valid and unchanged.  Errors: RQB_ERR_INVALID (no factorization on
- * the handle, bad leading dimension), RQB_ERR_UNSUPPORTED (power > 0). */
+ * the handle, bad leading dimension), RQB_ERR_UNSUPPORTED (power > 0 or a
+ * BF16 handle). */
 int rqb_backward(rqb_handle h, const void* dL_dX, int64_t ldg, void* dL_dA, int64_t ldda);
 
 /* Statistics of the last call on this handle. */
@@ -205,13 +220,17 @@ int rqb_get_stats(rqb_handle h, rqb_stats* out);
 
 /* ------------------------------------------------------------------------
  * Step-level entry points: single steps of Fig. randQB_b on caller buffers,
- * for verification of each step against the oracle.
+ * for verification of each step against the oracle.  On a BF16 handle A and
+ * W are BF16 and Y, Qi, Bi, Qbar FP32; sketch, project and downdate need
+ * m >= 128 and n >= 256 there (RQB_ERR_UNSUPPORTED otherwise), and the
+ * downdate stores W = rn_bf16(A - Qi Bi) (normW2 of the stored values).
  * ------------------------------------------------------------------------ */
 
 /* Omega block (line (2)): Omega (n x ncols, leading dim ldo >= n) receives
  * global columns col0 .. col0 + ncols - 1 of the Omega defined above, in the
  * form the handle's products use (binary64, binary32, or for RQB_PREC_TF32X3
- * the binary32 value rounded to TF32). */
+ * the binary32 value rounded to TF32; for BF16 handles rounded to BF16 and
+ * written as floats). */
 int rqb_omega(rqb_handle h, int64_t n, int64_t col0, int64_t ncols, uint64_t seed,
               void* Omega, int64_t ldo);
 

@@ -62,6 +62,7 @@ def _lib():
         lib.orc_round_tf32.restype = dbl
         lib.orc_round_bf16.argtypes = [dbl]
         lib.orc_round_bf16.restype = dbl
+        lib.orc_round_bf16_n.argtypes = [P, P, i64]
         lib.orc_randqb_b_store.argtypes = [P, i64, i64, i64, dbl, i64, u64, i64, i32, i32, i32, i32, i32,
                                            P, i64, P, i64, P]
         lib.orc_randqb_b_store.restype = i32
@@ -101,6 +102,13 @@ def round_tf32(x: float) -> float:
 
 def round_bf16(x: float) -> float:
     return float(_lib().orc_round_bf16(float(x)))
+
+
+def round_bf16_array(x) -> np.ndarray:
+    """Elementwise round_bf16 of an array (same shape, float64)."""
+    a = np.array(x, dtype=np.float64, order="F", copy=True)
+    _lib().orc_round_bf16_n(_ptr(a), _ptr(a), a.size)
+    return a
 
 
 def omega(seed: int, n: int, col0: int, ncols: int, prec: int = 64, stream: int = 0):

@@ -90,6 +90,11 @@ double orc_round_bf16(double x) {
     return ldexp(f < 0 ? -r : r, e - 8);
 }
 
+/* y[i] = orc_round_bf16(x[i]) for i < count (x and y may alias). */
+void orc_round_bf16_n(const double* x, double* y, int64_t count) {
+    for (int64_t i = 0; i < count; ++i) y[i] = orc_round_bf16(x[i]);
+}
+
 static double orc_omega_entry(uint64_t seed, uint32_t stream, int64_t r, int64_t c, int prec) {
     const double PI = 3.14159265358979323846;
     uint32_t ctr[4] = {(uint32_t)r, (uint32_t)(c >> 1), stream, 0u};

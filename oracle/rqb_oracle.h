@@ -34,6 +34,8 @@ double orc_round_tf32(double x);
 /* x rounded to 8 significant bits (BF16: 7 fraction bits), to nearest, ties
  * to even. */
 double orc_round_bf16(double x);
+/* elementwise orc_round_bf16 of count values (x and y may alias) */
+void orc_round_bf16_n(const double* x, double* y, int64_t count);
 
 /* Gaussian test matrix Omega (Fig. randQB_b, line (2): Omega_i = randn(n, b)).
  * Writes the n x ncols block whose first column is global column col0 of the

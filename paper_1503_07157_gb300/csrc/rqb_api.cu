@@ -106,7 +106,7 @@ struct rqb_handle_s {
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 1;
-    size_t esize = 4;          // bytes per element of A, Q, B
+    size_t esize = 4;          // bytes per element of A (Q and B: 8 for FP64, else 4)
     // device memory
     DevBuf state;              // DevState + FP64 scalars + FP64 partials
     DevBuf arena;              // Omega, Y, Y1, Gram, R, Rinv, C, partials
@@ -491,6 +491,156 @@ int factor_tc(rqb_handle h, const float* A, int64_t m, int64_t n, int64_t lda, d
     return RQB_OK;
 }
 
+// Workspace of the BF16 products: Omega_i and the BF16 hi / lo splits of Q_i
+// and B_i, and the stream-K partials (FP32).
+struct TcArena16 {
+    __nv_bfloat16* Om;     // n x bp, ld ldom
+    int64_t ldom;
+    __nv_bfloat16* Qhi;    // m x bp, ld ldql
+    __nv_bfloat16* Qlo;
+    int64_t ldql;
+    __nv_bfloat16* Qt;     // m x bp row-major
+    __nv_bfloat16* Qtl;
+    __nv_bfloat16* Bs;     // bp x n, ld bp
+    __nv_bfloat16* Bsl;
+    float* part;
+    size_t part_cap;
+};
+
+int ensure_tc16(rqb_handle h, int64_t m, int64_t n, int bp, TcArena16* out) {
+    const int64_t ldom = round_up(n, 8), ldql = round_up(m, 8);
+    const size_t part = tc::partial_floats16(m, n, bp, h->num_sms);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+    const size_t oOm = take(2 * (size_t)ldom * bp);
+    const size_t oQh = take(2 * (size_t)ldql * bp), oQl = take(2 * (size_t)ldql * bp);
+    const size_t oQt = take(2 * (size_t)m * bp), oQtl = take(2 * (size_t)m * bp);
+    const size_t oBs = take(2 * (size_t)n * bp), oBsl = take(2 * (size_t)n * bp);
+    const size_t oP = take(4 * part);
+    int rc = h->tcbuf.ensure(off);
+    if (rc != RQB_OK) return rc;
+    char* base = reinterpret_cast<char*>(h->tcbuf.p);
+    auto at = [&](size_t o) { return reinterpret_cast<__nv_bfloat16*>(base + o); };
+    out->Om = at(oOm); out->ldom = ldom;
+    out->Qhi = at(oQh); out->Qlo = at(oQl); out->ldql = ldql;
+    out->Qt = at(oQt); out->Qtl = at(oQtl);
+    out->Bs = at(oBs); out->Bsl = at(oBsl);
+    out->part = reinterpret_cast<float*>(base + oP); out->part_cap = part;
+    return RQB_OK;
+}
+
+bool tma_ok16(const void* p, int64_t ld) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0 && ld % 8 == 0; }
+
+// Fig. randQB_b with A and the residual stored in BF16 (RQB_BF16): the
+// sketch, projection and update run on kind::f16 MMAs; Q_i and B_i are FP32
+// (CholeskyQR2 panel on the FP32 SIMT kernels).  The update rounds the new
+// residual to BF16, so E_i no longer tracks the stored residual: the stop
+// test of line (6) is decided on the direct ||A^(i)||_F^2 of the stored
+// values, summed by the update itself, every block.
+int factor_bf16(rqb_handle h, const __nv_bfloat16* A, int64_t m, int64_t n, int64_t lda, double eps, int64_t b,
+                uint64_t seed, int64_t* k_out) {
+    const int64_t rmax = std::min(m, n);
+    const int64_t kcap = (h->cfg.max_rank > 0 && h->cfg.max_rank < rmax) ? h->cfg.max_rank : rmax;
+    const int bp = tc::pad_block16((int)b);
+    const int fixed = h->cfg.fixed_rank ? 1 : 0;
+    Arena<float> ar;
+    int rc = ensure_arena<float>(h, m, n, bp, kcap, &ar);
+    if (rc != RQB_OK) return rc;
+    TcArena16 ta;
+    rc = ensure_tc16(h, m, n, bp, &ta);
+    if (rc != RQB_OK) return rc;
+    const int64_t ldq = round_up(m, 4), ldb = round_up(kcap, 4), ldw = round_up(m, 8);
+    if ((rc = h->q.ensure(sizeof(float) * (size_t)ldq * (size_t)kcap)) != RQB_OK) return rc;
+    if ((rc = h->b.ensure(sizeof(float) * (size_t)ldb * (size_t)n)) != RQB_OK) return rc;
+    if ((rc = h->w.ensure(2 * (size_t)ldw * (size_t)n)) != RQB_OK) return rc;
+    h->ldq = ldq;
+    h->ldb = ldb;
+    h->ldw = ldw;
+    h->kcap_alloc = kcap;
+    float* Q = reinterpret_cast<float*>(h->q.p);
+    float* B = reinterpret_cast<float*>(h->b.p);
+    __nv_bfloat16* W = reinterpret_cast<__nv_bfloat16*>(h->w.p);
+
+    Scal sc = scalars(h);
+    Ctx cx;
+    cx.stream = h->stream;
+    cx.num_sms = h->num_sms;
+    cx.st = sc.st;
+    RQB_CK(cudaMemsetAsync(sc.st, 0, sizeof(DevState), h->stream));
+
+    const double eps2 = eps * eps;
+    int64_t k = 0;
+    int blocks = 0;
+    int status = RQB_OK;
+    bool converged = false;
+
+    const __nv_bfloat16* Wsrc = A;
+    int64_t ldws = lda;
+    h->timer.begin(h->stream, RQB_PHASE_SKETCH);
+    if (!tma_ok16(A, lda)) {
+        RQB_CK(cudaMemcpy2DAsync(W, 2 * ldw, A, 2 * lda, 2 * m, n, cudaMemcpyDeviceToDevice, h->stream));
+        Wsrc = W;
+        ldws = ldw;
+    }
+    int p = (int)std::min<int64_t>(b, kcap);
+    RQB_CK(launch_sumsq<__nv_bfloat16>(cx, m, n, Wsrc, ldws, sc.nrm, kNrmCap, sc.s + 0));
+    RQB_CK(launch_set_norm(cx, sc.s + 0));
+    RQB_CK(tc::omega16(cx, n, 0, p, bp, seed, ta.Om, ta.ldom));
+    RQB_CK(tc::sketch16(cx, Wsrc, ldws, m, n, ta.Om, ta.ldom, bp, ar.Y, m, ta.part, ta.part_cap));
+    h->timer.end(h->stream);
+
+    for (;;) {
+        p = (int)std::min<int64_t>(b, kcap - k);
+        float* Qi = Q + k * ldq;
+        float* Bi = B + k;
+        h->timer.begin(h->stream, RQB_PHASE_ORTH);
+        rc = orth_reproject<float>(h, cx, ar, ar.Y, m, m, p, bp, Q, k, ldq, Qi, ldq);
+        if (rc != RQB_OK) return rc;
+        RQB_CK(tc::split_q16(cx, Qi, ldq, m, p, bp, ta.Qhi, ta.Qlo, ta.ldql, ta.Qt, ta.Qtl));
+        h->timer.end(h->stream);
+        h->timer.begin(h->stream, RQB_PHASE_PROJECT);
+        RQB_CK(tc::project16(cx, Wsrc, ldws, m, n, ta.Qhi, ta.Qlo, ta.ldql, p, bp, Bi, ldb, ta.Bs, ta.Bsl, ta.part,
+                             ta.part_cap, sc.nrm, kNrmCap, sc.s + 1));
+        // E_i bookkeeping only (reported in the statistics)
+        RQB_CK(launch_stop_after_b(cx, sc.s + 1, eps2, 0.0, 1));
+        h->timer.end(h->stream);
+        h->timer.begin(h->stream, RQB_PHASE_DOWNDATE);
+        RQB_CK(tc::update16(cx, Wsrc, ldws, W, ldw, m, n, ta.Qt, ta.Qtl, ta.Bs, ta.Bsl, bp, sc.nrm, kNrmCap,
+                            sc.s + 2));
+        h->timer.end(h->stream);
+        Wsrc = W;
+        ldws = ldw;
+        h->timer.begin(h->stream, RQB_PHASE_CONTROL);
+        RQB_CK(launch_stop_direct(cx, sc.s + 2, eps2, true));
+        h->timer.end(h->stream);
+        const int err = read_state(h, sc);
+        if (err != RQB_OK) { status = err; break; }
+        if (blocks < RQB_MAX_TRACKED_BLOCKS) {
+            h->stats.E[blocks] = h->hstate->E;
+            h->stats.D[blocks] = h->hstate->D;
+        }
+        k += p;
+        blocks++;
+        if (!fixed && h->hstate->flag == kStop) { converged = true; break; }
+        if (k >= kcap) break;
+        const int pn = (int)std::min<int64_t>(b, kcap - k);
+        h->timer.begin(h->stream, RQB_PHASE_SKETCH);
+        RQB_CK(tc::omega16(cx, n, k, pn, bp, seed, ta.Om, ta.ldom));
+        RQB_CK(tc::sketch16(cx, W, ldw, m, n, ta.Om, ta.ldom, bp, ar.Y, m, ta.part, ta.part_cap));
+        h->timer.end(h->stream);
+    }
+    h->stats.k = k;
+    h->stats.blocks = blocks;
+    h->stats.direct_tests = blocks;
+    h->stats.normA2 = h->hstate->normA2;
+    h->stats.eps = eps;
+    h->stats.kernel_launches = cx.launches;
+    *k_out = k;
+    if (status != RQB_OK) return status;
+    if (!fixed && !converged) return RQB_NOT_CONVERGED;
+    return RQB_OK;
+}
+
 template <typename T>
 int factor_impl(rqb_handle h, const T* A, int64_t m, int64_t n, int64_t lda, double eps, int64_t b, uint64_t seed,
                 int64_t* k_out) {
@@ -673,15 +823,15 @@ int rqb_create(rqb_handle* out, const rqb_config* cfg) {
     if (cfg->dtype != RQB_F64 && cfg->dtype != RQB_F32 && cfg->dtype != RQB_BF16) return RQB_ERR_INVALID;
     if (cfg->prec != RQB_PREC_NATIVE && cfg->prec != RQB_PREC_TF32X3 && cfg->prec != RQB_PREC_BF16)
         return RQB_ERR_INVALID;
-    if (cfg->dtype == RQB_BF16 || cfg->prec == RQB_PREC_BF16 ||
-        (cfg->prec == RQB_PREC_TF32X3 && cfg->dtype != RQB_F32))
+    if ((cfg->prec == RQB_PREC_TF32X3 && cfg->dtype != RQB_F32) ||
+        (cfg->prec == RQB_PREC_BF16 && cfg->dtype != RQB_BF16) || (cfg->dtype == RQB_BF16 && cfg->power != 0))
         return RQB_ERR_UNSUPPORTED;
     if (cfg->power > 8) return RQB_ERR_INVALID;
     rqb_handle h = new (std::nothrow) rqb_handle_s();
     if (!h) return RQB_ERR_OOM;
     h->cfg = *cfg;
     h->stream = reinterpret_cast<cudaStream_t>(cfg->stream);
-    h->esize = (cfg->dtype == RQB_F64) ? 8 : 4;
+    h->esize = (cfg->dtype == RQB_F64) ? 8 : (cfg->dtype == RQB_BF16) ? 2 : 4;
     if (cudaGetDevice(&h->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
         cudaGetLastError();
@@ -737,9 +887,14 @@ int rqb_factor(rqb_handle h, const void* A, int64_t m, int64_t n, int64_t lda, d
     if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
     std::memset(&h->stats, 0, sizeof(h->stats));
     int64_t kk = 0;
-    int rc = (h->cfg.dtype == RQB_F64)
-                 ? factor_impl<double>(h, static_cast<const double*>(A), m, n, lda, eps, b, seed, &kk)
-                 : factor_impl<float>(h, static_cast<const float*>(A), m, n, lda, eps, b, seed, &kk);
+    int rc;
+    if (h->cfg.dtype == RQB_BF16)
+        rc = tc::shape_ok(m, n) ? factor_bf16(h, static_cast<const __nv_bfloat16*>(A), m, n, lda, eps, b, seed, &kk)
+                                : RQB_ERR_UNSUPPORTED;
+    else if (h->cfg.dtype == RQB_F64)
+        rc = factor_impl<double>(h, static_cast<const double*>(A), m, n, lda, eps, b, seed, &kk);
+    else
+        rc = factor_impl<float>(h, static_cast<const float*>(A), m, n, lda, eps, b, seed, &kk);
     *Q = h->q.p;
     *ldq = h->ldq;
     *B = h->b.p;
@@ -760,7 +915,7 @@ int rqb_factor_host(rqb_handle h, const void* A_host, int64_t m, int64_t n, int6
         ldb_host < kcap)
         return finish(h, RQB_ERR_INVALID);
     if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
-    const size_t es = h->esize;
+    const size_t es = h->esize, eo = (h->cfg.dtype == RQB_F64) ? 8 : 4;
     int rc = h->ahost.ensure(es * (size_t)m * (size_t)n);
     if (rc != RQB_OK) return finish(h, rc);
     if (cudaMemcpy2DAsync(h->ahost.p, es * m, A_host, es * lda, es * m, n, cudaMemcpyHostToDevice, h->stream) !=
@@ -774,9 +929,9 @@ int rqb_factor_host(rqb_handle h, const void* A_host, int64_t m, int64_t n, int6
     *k = kk;
     if (rc != RQB_OK && rc != RQB_NOT_CONVERGED) return finish(h, rc);
     if (kk > 0) {
-        if (cudaMemcpy2DAsync(Q_host, es * ldq_host, Qd, es * ldq, es * m, kk, cudaMemcpyDeviceToHost, h->stream) !=
+        if (cudaMemcpy2DAsync(Q_host, eo * ldq_host, Qd, eo * ldq, eo * m, kk, cudaMemcpyDeviceToHost, h->stream) !=
                 cudaSuccess ||
-            cudaMemcpy2DAsync(B_host, es * ldb_host, Bd, es * ldb, es * kk, n, cudaMemcpyDeviceToHost, h->stream) !=
+            cudaMemcpy2DAsync(B_host, eo * ldb_host, Bd, eo * ldb, eo * kk, n, cudaMemcpyDeviceToHost, h->stream) !=
                 cudaSuccess ||
             cudaStreamSynchronize(h->stream) != cudaSuccess) {
             cudaGetLastError();
@@ -810,6 +965,8 @@ extern "C" int rqb_omega(rqb_handle h, int64_t n, int64_t col0, int64_t ncols, u
         e = launch_omega<double>(cx, n, col0, (int)ncols, (int)ncols, seed, static_cast<double*>(Omega), 1, ldo);
     else if (h->cfg.prec == RQB_PREC_TF32X3)
         e = tc::omega(cx, n, col0, (int)ncols, (int)ncols, seed, static_cast<float*>(Omega), ldo);
+    else if (h->cfg.dtype == RQB_BF16)
+        e = tc::omega16_f32(cx, n, col0, (int)ncols, (int)ncols, seed, static_cast<float*>(Omega), ldo);
     else
         e = launch_omega<float>(cx, n, col0, (int)ncols, (int)ncols, seed, static_cast<float*>(Omega), 1, ldo);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -990,6 +1147,95 @@ int dd_tc(rqb_handle h, const float* A, int64_t lda, const float* Qi, int64_t ld
     if (normW2) RQB_CK(cudaMemcpyAsync(normW2, sc.s + 2, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     return read_state(h, sc);
 }
+
+// Step entry points of a BF16 handle (A and W in BF16; Q, B, Y in FP32).
+int tma_source16(rqb_handle h, const __nv_bfloat16* X, int64_t ldx, int64_t m, int64_t n,
+                 const __nv_bfloat16** out, int64_t* ldout) {
+    if (tma_ok16(X, ldx)) {
+        *out = X;
+        *ldout = ldx;
+        return RQB_OK;
+    }
+    const int64_t ldw = round_up(m, 8);
+    int rc = h->w.ensure(2 * (size_t)ldw * (size_t)n);
+    if (rc != RQB_OK) return rc;
+    RQB_CK(cudaMemcpy2DAsync(h->w.p, 2 * ldw, X, 2 * ldx, 2 * m, n, cudaMemcpyDeviceToDevice, h->stream));
+    *out = reinterpret_cast<const __nv_bfloat16*>(h->w.p);
+    *ldout = ldw;
+    return RQB_OK;
+}
+
+int sketch_bf16(rqb_handle h, const __nv_bfloat16* A, int64_t m, int64_t n, int64_t lda, int64_t col0, int p,
+                uint64_t seed, float* Y, int64_t ldy, double* normA2) {
+    const int bp = tc::pad_block16(p);
+    Arena<float> ar;
+    TcArena16 ta;
+    int rc = ensure_arena<float>(h, m, n, bp, 1, &ar);
+    if (rc == RQB_OK) rc = ensure_tc16(h, m, n, bp, &ta);
+    if (rc != RQB_OK) return rc;
+    Scal sc = scalars(h);
+    Ctx cx;
+    cx.stream = h->stream; cx.num_sms = h->num_sms; cx.st = sc.st;
+    RQB_CK(cudaMemsetAsync(sc.st, 0, sizeof(DevState), h->stream));
+    const __nv_bfloat16* X;
+    int64_t ldx;
+    if ((rc = tma_source16(h, A, lda, m, n, &X, &ldx)) != RQB_OK) return rc;
+    if (normA2) RQB_CK(launch_sumsq<__nv_bfloat16>(cx, m, n, X, ldx, sc.nrm, kNrmCap, sc.s + 0));
+    RQB_CK(tc::omega16(cx, n, col0, p, bp, seed, ta.Om, ta.ldom));
+    RQB_CK(tc::sketch16(cx, X, ldx, m, n, ta.Om, ta.ldom, bp, ar.Y, m, ta.part, ta.part_cap));
+    RQB_CK(cudaMemcpy2DAsync(Y, sizeof(float) * ldy, ar.Y, sizeof(float) * m, sizeof(float) * m, p,
+                             cudaMemcpyDeviceToDevice, h->stream));
+    if (normA2) RQB_CK(cudaMemcpyAsync(normA2, sc.s + 0, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return read_state(h, sc);
+}
+
+int project_bf16(rqb_handle h, const float* Qi, int64_t m, int p, int64_t ldqi, const __nv_bfloat16* A, int64_t n,
+                 int64_t lda, float* Bi, int64_t ldbi, double* normB2) {
+    const int bp = tc::pad_block16(p);
+    TcArena16 ta;
+    int rc = ensure_tc16(h, m, n, bp, &ta);
+    if (rc != RQB_OK) return rc;
+    Scal sc = scalars(h);
+    Ctx cx;
+    cx.stream = h->stream; cx.num_sms = h->num_sms; cx.st = sc.st;
+    RQB_CK(cudaMemsetAsync(sc.st, 0, sizeof(DevState), h->stream));
+    const __nv_bfloat16* X;
+    int64_t ldx;
+    if ((rc = tma_source16(h, A, lda, m, n, &X, &ldx)) != RQB_OK) return rc;
+    RQB_CK(tc::split_q16(cx, Qi, ldqi, m, p, bp, ta.Qhi, ta.Qlo, ta.ldql, ta.Qt, ta.Qtl));
+    RQB_CK(tc::project16(cx, X, ldx, m, n, ta.Qhi, ta.Qlo, ta.ldql, p, bp, Bi, ldbi, ta.Bs, ta.Bsl, ta.part,
+                         ta.part_cap, sc.nrm, kNrmCap, sc.s + 1));
+    if (normB2) RQB_CK(cudaMemcpyAsync(normB2, sc.s + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return read_state(h, sc);
+}
+
+int dd_bf16(rqb_handle h, const __nv_bfloat16* A, int64_t lda, const float* Qi, int64_t ldqi, const float* Bi,
+            int64_t ldbi, int64_t m, int64_t n, int p, __nv_bfloat16* W, int64_t ldw, int64_t col0, int ncols,
+            uint64_t seed, float* Y, int64_t ldy, double* normW2) {
+    const int bpu = tc::pad_block16(p), bps = tc::pad_block16(ncols);
+    Arena<float> ar;
+    TcArena16 ta;
+    int rc = ensure_arena<float>(h, m, n, bps, 1, &ar);
+    if (rc == RQB_OK) rc = ensure_tc16(h, m, n, std::max(bpu, bps), &ta);
+    if (rc != RQB_OK) return rc;
+    Scal sc = scalars(h);
+    Ctx cx;
+    cx.stream = h->stream; cx.num_sms = h->num_sms; cx.st = sc.st;
+    RQB_CK(cudaMemsetAsync(sc.st, 0, sizeof(DevState), h->stream));
+    RQB_CK(tc::split_q16(cx, Qi, ldqi, m, p, bpu, ta.Qhi, ta.Qlo, ta.ldql, ta.Qt, ta.Qtl));
+    RQB_CK(tc::stage_b16(cx, Bi, ldbi, p, n, bpu, ta.Bs, ta.Bsl));
+    RQB_CK(tc::update16(cx, A, lda, W, ldw, m, n, ta.Qt, ta.Qtl, ta.Bs, ta.Bsl, bpu, sc.nrm, kNrmCap,
+                        normW2 ? sc.s + 2 : nullptr));
+    const __nv_bfloat16* X;
+    int64_t ldx;
+    if ((rc = tma_source16(h, W, ldw, m, n, &X, &ldx)) != RQB_OK) return rc;
+    RQB_CK(tc::omega16(cx, n, col0, ncols, bps, seed, ta.Om, ta.ldom));
+    RQB_CK(tc::sketch16(cx, X, ldx, m, n, ta.Om, ta.ldom, bps, ar.Y, m, ta.part, ta.part_cap));
+    RQB_CK(cudaMemcpy2DAsync(Y, sizeof(float) * ldy, ar.Y, sizeof(float) * m, sizeof(float) * m, ncols,
+                             cudaMemcpyDeviceToDevice, h->stream));
+    if (normW2) RQB_CK(cudaMemcpyAsync(normW2, sc.s + 2, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return read_state(h, sc);
+}
 }  // namespace
 
 extern "C" {
@@ -1001,6 +1247,10 @@ int rqb_sketch(rqb_handle h, const void* A, int64_t m, int64_t n, int64_t lda, i
         (h->cfg.dtype == RQB_F64 && ncols > 128))
         return finish(h, RQB_ERR_INVALID);
     if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
+    if (h->cfg.dtype == RQB_BF16)
+        return finish(h, !tc::shape_ok(m, n) ? RQB_ERR_UNSUPPORTED
+                                             : sketch_bf16(h, static_cast<const __nv_bfloat16*>(A), m, n, lda, col0,
+                                                           (int)ncols, seed, static_cast<float*>(Y), ldy, normA2));
     if (use_tc(h, m, n))
         return finish(h, sketch_tc(h, static_cast<const float*>(A), m, n, lda, col0, (int)ncols, seed,
                                    static_cast<float*>(Y), ldy, normA2));
@@ -1034,6 +1284,12 @@ int rqb_project(rqb_handle h, const void* Qi, int64_t m, int64_t p, int64_t ldqi
         p > max_block(h))
         return finish(h, RQB_ERR_INVALID);
     if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
+    if (h->cfg.dtype == RQB_BF16)
+        return finish(h, !tc::shape_ok(m, n)
+                             ? RQB_ERR_UNSUPPORTED
+                             : project_bf16(h, static_cast<const float*>(Qi), m, (int)p, ldqi,
+                                            static_cast<const __nv_bfloat16*>(A), n, lda, static_cast<float*>(Bi),
+                                            ldbi, normB2));
     if (use_tc(h, m, n))
         return finish(h, project_tc(h, static_cast<const float*>(Qi), m, (int)p, ldqi, static_cast<const float*>(A),
                                     n, lda, static_cast<float*>(Bi), ldbi, normB2));
@@ -1055,6 +1311,13 @@ int rqb_downdate_sketch(rqb_handle h, const void* A, int64_t lda, const void* Qi
         (A == W && lda != ldw))
         return finish(h, RQB_ERR_INVALID);
     if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
+    if (h->cfg.dtype == RQB_BF16)
+        return finish(h, !tc::shape_ok(m, n)
+                             ? RQB_ERR_UNSUPPORTED
+                             : dd_bf16(h, static_cast<const __nv_bfloat16*>(A), lda, static_cast<const float*>(Qi),
+                                       ldqi, static_cast<const float*>(Bi), ldbi, m, n, (int)p,
+                                       static_cast<__nv_bfloat16*>(W), ldw, col0, (int)ncols, seed,
+                                       static_cast<float*>(Y), ldy, normW2));
     if (use_tc(h, m, n))
         return finish(h, dd_tc(h, static_cast<const float*>(A), lda, static_cast<const float*>(Qi), ldqi,
                                static_cast<const float*>(Bi), ldbi, m, n, (int)p, static_cast<float*>(W), ldw, col0,
@@ -1216,7 +1479,7 @@ extern "C" int rqb_reconstruct(rqb_handle h, void* X, int64_t ldx) {
 extern "C" int rqb_backward(rqb_handle h, const void* dL_dX, int64_t ldg, void* dL_dA, int64_t ldda) {
     if (!h) return RQB_ERR_INVALID;
     if (!h->have_factor || !dL_dX || !dL_dA || ldg < h->last_m || ldda < h->last_m) return finish(h, RQB_ERR_INVALID);
-    if (h->cfg.power != 0) return finish(h, RQB_ERR_UNSUPPORTED);
+    if (h->cfg.power != 0 || h->cfg.dtype == RQB_BF16) return finish(h, RQB_ERR_UNSUPPORTED);
     if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
     RQB_CK(cudaMemsetAsync(scalars(h).st, 0, sizeof(DevState), h->stream));
     int rc = (h->cfg.dtype == RQB_F64)

@@ -10,6 +10,8 @@
 //   line (5)   A = A - Q_i B_i, fused with line (3) of block i+1:
 //                                                k_downdate_sketch (+ ||A^(i)||_F^2)
 //   line (6)   stop test                         k_stop_after_b / k_stop_direct
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cstdio>
 
@@ -67,7 +69,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_sumsq(int64_t m, int64_t n, const T* __restrict__ X, int64_t ldx,
                                                double* __restrict__ part) {
-    // one warp per column at a time (coalesced rows); FP32 data: each square
+    // one warp per column at a time (coalesced rows); FP32 or BF16 data: each square
     // is split exactly into p + e (e = fma(v, v, -p)) and summed with
     // compensated FP32 adds, promoted to FP64 every 64 rows per lane
     __shared__ double sh[8];
@@ -76,7 +78,7 @@ __global__ void __launch_bounds__(256) k_sumsq(int64_t m, int64_t n, const T* __
     double acc = 0.0;
     for (int64_t c = gw; c < n; c += nw) {
         const T* col = X + c * ldx;
-        if (sizeof(T) == 8) {
+        if constexpr (sizeof(T) == 8) {
             for (int64_t r = lane; r < m; r += 32) {
                 const double v = (double)col[r];
                 acc = fma(v, v, acc);
@@ -86,7 +88,7 @@ __global__ void __launch_bounds__(256) k_sumsq(int64_t m, int64_t n, const T* __
                 float hi = 0.f, lo = 0.f;
                 const int64_t r1 = r0 + 32 * 64 < m ? r0 + 32 * 64 : m;
                 for (int64_t r = r0 + lane; r < r1; r += 32) {
-                    const float v = (float)col[r];
+                    const float v = static_cast<float>(col[r]);
                     const float p2 = __fmul_rn(v, v);     // rounded square, never contracted
                     const float e2 = fmaf(v, v, -p2);     // its exact error
                     const float t = __fadd_rn(hi, p2);    // TwoSum(hi, p2)
@@ -841,6 +843,8 @@ cudaError_t downdate_sketch(Ctx& cx, int64_t m, int64_t n, int p, int bp, const 
 
 RQB_INST(float)
 RQB_INST(double)
+template cudaError_t launch_sumsq<__nv_bfloat16>(Ctx&, int64_t, int64_t, const __nv_bfloat16*, int64_t, double*, int,
+                                                 double*);
 template cudaError_t tri_inverse<float>(Ctx&, const double*, int, float*);
 template cudaError_t tri_inverse<double>(Ctx&, const double*, int, double*);
 template cudaError_t launch_to_double<float>(Ctx&, int64_t, int64_t, const float*, int64_t, double*, int64_t);

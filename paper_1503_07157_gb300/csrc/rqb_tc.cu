@@ -23,6 +23,7 @@
 // expiry the CTA drains its copies and MMAs, frees TMEM and records
 // RQB_ERR_TIMEOUT.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -290,6 +291,173 @@ __global__ void __launch_bounds__(320, 1) k_streamk(const __grid_constant__ Stre
 #pragma unroll
                     for (int i = 0; i < kHalf; ++i) acc[i] = 0.f;
                 }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, ncols);
+    if (threadIdx.x == 0 && abort_flag) record_error(p.st, RQB_ERR_TIMEOUT);
+}
+
+// ---------------------------------------------------------------------------
+// BF16 storage path (A and its residual in BF16, products on kind::f16 with
+// FP32 accumulation).  A 128-row x 128-byte tile holds 64 BF16 of K and an MMA
+// step covers K = 16, so a chunk is four MMAs as in the TF32 kernels.
+//   sketch   Y = W Omega_i: W read MN-major straight from TMA (two 64-row
+//            boxes), Omega_i in BF16 (exact), one pass
+//   project  B_i^T = W^T Q_i: W K-major, Q_i split into BF16 hi + lo, two passes
+constexpr int kKC16 = 64;    // K per chunk of the BF16 kernels
+
+template <int ROLE, int NP>
+struct StreamK16Cfg {
+    static constexpr int S = (ROLE == kProject && NP > 128) ? 2 : 4;    // TMA stages
+    static constexpr uint32_t kW = (uint32_t)NP * 128u;                  // Omega / Q tile bytes
+    static constexpr uint32_t kStage = kTileBytes + (ROLE == kProject ? 2u : 1u) * kW;
+    static constexpr size_t kSmem = (size_t)S * kStage + 1024;
+};
+
+template <int ROLE, int NP>
+__global__ void __launch_bounds__(320, 1) k_streamk16(const __grid_constant__ StreamKParams p) {
+    using Cfg = StreamK16Cfg<ROLE, NP>;
+    constexpr int S = Cfg::S;
+    constexpr uint32_t kW = Cfg::kW, kStage = Cfg::kStage;
+    constexpr int kHalf = NP / 2;
+    __shared__ __align__(8) uint64_t full[S], empty[S], accfull[2], accempty[2], drain;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    extern __shared__ uint8_t dsm[];
+    uint8_t* base = dsm + (((smem_u32(dsm) + 1023u) & ~1023u) - smem_u32(dsm));
+    constexpr uint32_t ncols = 2u * (uint32_t)NP;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int* ab = &abort_flag;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int s = 0; s < 2; ++s) { mbar_init(&accfull[s], 1); mbar_init(&accempty[s], 8); }
+        mbar_init(&drain, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+        prefetch_map(&p.mx);
+        prefetch_map(&p.mw);
+        if (ROLE == kProject) prefetch_map(&p.mwl);
+    }
+    if (warp == 1) tmem_alloc(&tmem_base, ncols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const long long u0 = unit_begin(p.U, p.P, blockIdx.x), u1 = unit_begin(p.U, p.P, blockIdx.x + 1);
+    auto seg_end = [&](long long u) { return u + 1 == u1 || (u + 1) % p.C == 0; };
+    auto period_end = [&](long long u) { return seg_end(u) || ((u % p.C) + 1) % kPeriod == 0; };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            long long q = 0;
+            for (long long u = u0; u < u1; ++u, ++q) {
+                const int s = (int)(q % S);
+                const uint32_t r = (uint32_t)(q / S);
+                if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1u, ab)) break;
+                const int t = (int)(u / p.C), kc = (int)(u % p.C);
+                uint8_t* st = base + s * kStage;
+                if (ROLE == kSketch) {
+                    mbar_arrive_expect_tx(&full[s], kTileBytes + kW);
+                    tma_load_2d(st, &p.mx, t * kBM, kc * kKC16, &full[s]);
+                    tma_load_2d(st + kTileBytes / 2, &p.mx, t * kBM + 64, kc * kKC16, &full[s]);
+                    tma_load_2d(st + kTileBytes, &p.mw, kc * kKC16, 0, &full[s]);
+                } else {
+                    mbar_arrive_expect_tx(&full[s], kTileBytes + 2u * kW);
+                    tma_load_2d(st, &p.mx, kc * kKC16, t * kBM, &full[s]);
+                    tma_load_2d(st + kTileBytes, &p.mw, kc * kKC16, 0, &full[s]);
+                    tma_load_2d(st + kTileBytes + kW, &p.mwl, kc * kKC16, 0, &full[s]);
+                }
+            }
+            for (long long qq = (q > S ? q - S : 0); qq < q; ++qq)
+                mbar_wait(&full[qq % S], (uint32_t)(qq / S) & 1u, ab, false);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(NP, ROLE == kSketch ? 1 : 0);
+            int g = 0;
+            bool first = true;
+            long long q = 0;
+            for (long long u = u0; u < u1; ++u, ++q) {
+                const int s = (int)(q % S);
+                const uint32_t r = (uint32_t)(q / S);
+                if (!mbar_wait(&full[s], r & 1u, ab)) break;
+                const int abuf = g & 1, use = g >> 1;
+                if (first && use > 0 && !mbar_wait(&accempty[abuf], (uint32_t)(use - 1) & 1u, ab)) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(abuf * NP);
+                const uint32_t a0 = smem_u32(base + s * kStage), b0 = a0 + kTileBytes;
+                if (ROLE == kSketch) {
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_bf16(d, desc_mn_sw128(a0 + kk * 2048, kTileBytes / 2), desc_k_sw128(b0 + kk * 32), idesc,
+                                 (first && kk == 0) ? 0u : 1u);
+                } else {
+                    const uint32_t b1 = b0 + kW;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_bf16(d, desc_k_sw128(a0 + kk * 32), desc_k_sw128(b0 + kk * 32), idesc,
+                                 (first && kk == 0) ? 0u : 1u);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_bf16(d, desc_k_sw128(a0 + kk * 32), desc_k_sw128(b1 + kk * 32), idesc, 1u);
+                }
+                mma_commit(&empty[s]);
+                if (period_end(u)) {
+                    mma_commit(&accfull[abuf]);
+                    ++g;
+                    first = true;
+                } else {
+                    first = false;
+                }
+            }
+            mma_commit(&drain);
+            mbar_wait(&drain, 0, ab, false);
+        }
+    } else {
+        const int e = warp - 2;
+        const int quarter = warp & 3;
+        const int half = e >> 2;
+        const int row = quarter * 32 + lane;
+        float acc[kHalf];
+#pragma unroll
+        for (int i = 0; i < kHalf; ++i) acc[i] = 0.f;
+        int g = 0;
+        for (long long u = u0; u < u1; ++u) {
+            if (!period_end(u)) continue;
+            const int abuf = g & 1, use = g >> 1;
+            const bool okw = mbar_wait(&accfull[abuf], (uint32_t)use & 1u, ab);
+            if (!__all_sync(0xffffffffu, okw)) break;
+            tc_fence_after();
+            const uint32_t tl = tmem + (uint32_t)(abuf * NP + half * kHalf) + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll
+            for (int c0 = 0; c0 < kHalf; c0 += 16) {
+                float v[16];
+                tmem_ld16(tl + (uint32_t)c0, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) acc[c0 + i] += v[i];
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accempty[abuf]);
+            ++g;
+            if (seg_end(u)) {
+                const int seg = (int)(u / p.C - u0 / p.C);
+                float* slot = p.part + ((size_t)blockIdx.x * p.G + seg) * (size_t)kBM * NP;
+                if (ROLE == kSketch) {
+#pragma unroll
+                    for (int i = 0; i < kHalf; ++i) slot[(size_t)(half * kHalf + i) * kBM + row] = acc[i];
+                } else {
+                    float4* d4 = reinterpret_cast<float4*>(slot + (size_t)row * NP + half * kHalf);
+#pragma unroll
+                    for (int i = 0; i < kHalf / 4; ++i)
+                        d4[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
+                }
+#pragma unroll
+                for (int i = 0; i < kHalf; ++i) acc[i] = 0.f;
             }
         }
     }
@@ -609,6 +777,272 @@ __global__ void k_reduce_project(const float* __restrict__ part, long long U, in
     }
 }
 
+// ---------------------------------------------------------------------------
+// BF16 update: Wdst = round_bf16(Wsrc - Q_i B_i) on 128 x NJ tiles, K = bp in
+// chunks of 64; Q_i^T and B_i split into BF16 hi + lo, three passes (the
+// lo x lo term is below 2^-17 of the product).  ||Wdst||_F^2 of the rounded
+// values (exact FP32 squares) per CTA.
+struct UpdateParams16 {
+    CUtensorMap mqt, mqtl;  // Q_i^T hi / lo, row-major m x bp (as {bp, m}), box {64, 128}
+    CUtensorMap mbs, mbsl;  // B_i hi / lo, bp x n column-major, box {64, NJ}
+    const __nv_bfloat16* Wsrc;
+    __nv_bfloat16* Wdst;
+    DevState* st;
+    double* sq_part;
+    long long ldws, ldwd, m, n;
+    int RT, CT, C;
+};
+
+template <int NJ, int S>
+__global__ void __launch_bounds__(320, 1) k_update16(const __grid_constant__ UpdateParams16 p) {
+    __shared__ __align__(8) uint64_t full[S], empty[S], accfull[2], accempty[2], drain;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ double red[8];
+    extern __shared__ uint8_t dsm[];
+    uint8_t* base = dsm + (((smem_u32(dsm) + 1023u) & ~1023u) - smem_u32(dsm));
+    constexpr uint32_t kB = (uint32_t)NJ * 128u;
+    constexpr uint32_t kStage = 2u * kTileBytes + 2u * kB;
+    constexpr uint32_t kCols = 2u * NJ;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int* ab = &abort_flag;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int s = 0; s < 2; ++s) { mbar_init(&accfull[s], 1); mbar_init(&accempty[s], 8); }
+        mbar_init(&drain, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+        prefetch_map(&p.mqt);
+        prefetch_map(&p.mqtl);
+        prefetch_map(&p.mbs);
+        prefetch_map(&p.mbsl);
+    }
+    if (warp == 1) tmem_alloc(&tmem_base, kCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const int T = p.RT * p.CT;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            long long q = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < T && !stop; t += gridDim.x) {
+                const int rt = t / p.CT, ctile = t % p.CT;
+                for (int kc = 0; kc < p.C; ++kc, ++q) {
+                    const int s = (int)(q % S);
+                    const uint32_t r = (uint32_t)(q / S);
+                    if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1u, ab)) { stop = true; break; }
+                    uint8_t* st = base + s * kStage;
+                    mbar_arrive_expect_tx(&full[s], kStage);
+                    tma_load_2d(st, &p.mqt, kc * kKC16, rt * kBM, &full[s]);
+                    tma_load_2d(st + kTileBytes, &p.mqtl, kc * kKC16, rt * kBM, &full[s]);
+                    tma_load_2d(st + 2 * kTileBytes, &p.mbs, kc * kKC16, ctile * NJ, &full[s]);
+                    tma_load_2d(st + 2 * kTileBytes + kB, &p.mbsl, kc * kKC16, ctile * NJ, &full[s]);
+                }
+            }
+            for (long long qq = (q > S ? q - S : 0); qq < q; ++qq)
+                mbar_wait(&full[qq % S], (uint32_t)(qq / S) & 1u, ab, false);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(NJ, 0);
+            long long q = 0;
+            int g = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < T && !stop; t += gridDim.x, ++g) {
+                const int abuf = g & 1, use = g >> 1;
+                if (use > 0 && !mbar_wait(&accempty[abuf], (uint32_t)(use - 1) & 1u, ab)) break;
+                const uint32_t d = tmem + (uint32_t)(abuf * NJ);
+                for (int kc = 0; kc < p.C; ++kc, ++q) {
+                    const int s = (int)(q % S);
+                    const uint32_t r = (uint32_t)(q / S);
+                    if (!mbar_wait(&full[s], r & 1u, ab)) { stop = true; break; }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(base + s * kStage), a1 = a0 + kTileBytes;
+                    const uint32_t b0 = a0 + 2 * kTileBytes, b1 = b0 + kB;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_bf16(d, desc_k_sw128(a0 + kk * 32), desc_k_sw128(b0 + kk * 32), idesc,
+                                 (kc == 0 && kk == 0) ? 0u : 1u);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_bf16(d, desc_k_sw128(a0 + kk * 32), desc_k_sw128(b1 + kk * 32), idesc, 1u);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_bf16(d, desc_k_sw128(a1 + kk * 32), desc_k_sw128(b0 + kk * 32), idesc, 1u);
+                    mma_commit(&empty[s]);
+                }
+                if (stop) break;
+                mma_commit(&accfull[abuf]);
+            }
+            mma_commit(&drain);
+            mbar_wait(&drain, 0, ab, false);
+        }
+    } else {
+        const int e = warp - 2;
+        const int quarter = warp & 3;
+        const int half = e >> 2;
+        constexpr int kHalf = NJ / 2;
+        double sq = 0.0;
+        int g = 0;
+        for (int t = blockIdx.x; t < T; t += gridDim.x, ++g) {
+            const int abuf = g & 1, use = g >> 1;
+            const bool okw = mbar_wait(&accfull[abuf], (uint32_t)use & 1u, ab);
+            if (!__all_sync(0xffffffffu, okw)) break;
+            tc_fence_after();
+            const int rt = t / p.CT, ctile = t % p.CT;
+            const long long r = (long long)rt * kBM + quarter * 32 + lane;
+            const long long j0 = (long long)ctile * NJ + half * kHalf;
+            const bool rok = r < p.m;
+            const unsigned short* src = reinterpret_cast<const unsigned short*>(p.Wsrc) + r;
+            __nv_bfloat16* dst = p.Wdst + r;
+            const uint32_t tl = tmem + (uint32_t)(abuf * NJ + half * kHalf) + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+            for (int c0 = 0; c0 < kHalf; c0 += 32) {
+                float w[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const long long j = j0 + c0 + i;
+                    w[i] = (rok && j < p.n) ? __bfloat162float(__ushort_as_bfloat16(__ldcs(src + j * p.ldws))) : 0.f;
+                }
+                float v0[16], v1[16];
+                tmem_ld16(tl + (uint32_t)c0, v0);
+                tmem_ld16(tl + (uint32_t)(c0 + 16), v1);
+                float sq32 = 0.f;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const long long j = j0 + c0 + i;
+                    const __nv_bfloat16 o = __float2bfloat16_rn(w[i] - (i < 16 ? v0[i] : v1[i - 16]));
+                    if (rok && j < p.n) {
+                        dst[j * p.ldwd] = o;
+                        const float of = __bfloat162float(o);
+                        sq32 = fmaf(of, of, sq32);
+                    }
+                }
+                sq += (double)sq32;
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accempty[abuf]);
+        }
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (lane == 0) red[e] = sq;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, kCols);
+    if (threadIdx.x == 0) {
+        if (abort_flag) record_error(p.st, RQB_ERR_TIMEOUT);
+        if (p.sq_part) {
+            double t = 0.0;
+            for (int i = 0; i < 8; ++i) t += red[i];
+            p.sq_part[blockIdx.x] = t;
+        }
+    }
+}
+
+// x = hi + lo with hi = rn_bf16(x) and lo = rn_bf16(x - hi) (x - hi is exact
+// in FP32): the pair holds x to 2^-18 relative.
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// Omega_i for the BF16 products: the binary32 Gaussian (j, col0 + c) rounded
+// to BF16 (nearest even), out[j + c ldo] for c < p, zero for p <= c < bp.
+// OutT = __nv_bfloat16 (the MMA operand) or float (the same values widened).
+template <typename OutT>
+__global__ void k_omega_bf16(long long n, long long col0, int p, int bp, uint64_t seed, OutT* __restrict__ out,
+                             long long ldo) {
+    const long long total = n * bp;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long j = e % n;
+        const int c = (int)(e / n);
+        const __nv_bfloat16 v = __float2bfloat16_rn(c < p ? gaussian_f32(seed, j, col0 + c) : 0.f);
+        if constexpr (sizeof(OutT) == 2) out[j + c * ldo] = v;
+        else out[j + c * ldo] = __bfloat162float(v);
+    }
+}
+
+// BF16 splits of Q_i (m x p, ld ldq): Qhi / Qlo column-major (ld ldql, bp
+// columns) and the row-major transpose pair Qt / Qtl (m x bp).
+__global__ void k_split_q16(const float* __restrict__ Qi, long long ldq, long long m, int p, int bp,
+                            __nv_bfloat16* __restrict__ Qhi, __nv_bfloat16* __restrict__ Qlo, long long ldql,
+                            __nv_bfloat16* __restrict__ Qt, __nv_bfloat16* __restrict__ Qtl) {
+    __shared__ float tile[32][33];
+    const long long r0 = (long long)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int i = ty; i < 32; i += 8) {
+        const long long r = r0 + tx;
+        const int c = c0 + i;
+        float v = 0.f;
+        if (r < m && c < p) v = Qi[r + c * ldq];
+        if (r < m) split_bf16(v, Qhi[r + c * ldql], Qlo[r + c * ldql]);
+        tile[i][tx] = v;
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        const long long r = r0 + i;
+        const int c = c0 + tx;
+        if (r < m) split_bf16(tile[tx][i], Qt[r * bp + c], Qtl[r * bp + c]);
+    }
+}
+
+// Bs / Bsl (bp x n, ld bp, BF16 hi / lo) from B_i (p x n, ld ldbi).
+__global__ void k_stage_b16(const float* __restrict__ Bi, long long ldbi, int p, long long n, int bp,
+                            __nv_bfloat16* __restrict__ Bs, __nv_bfloat16* __restrict__ Bsl) {
+    const long long total = n * bp;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e % bp);
+        const long long j = e / bp;
+        split_bf16(c < p ? Bi[c + j * ldbi] : 0.f, Bs[e], Bsl[e]);
+    }
+}
+
+// As k_reduce_project, with the staged copy of B_i split into BF16 hi / lo.
+__global__ void k_reduce_project16(const float* __restrict__ part, long long U, int C, int P, int G, int np,
+                                   int pcols, long long n, float* __restrict__ B, long long ldb,
+                                   __nv_bfloat16* __restrict__ Bs, __nv_bfloat16* __restrict__ Bsl,
+                                   double* __restrict__ sq_part) {
+    __shared__ size_t off[kMaxCover];
+    __shared__ int count;
+    __shared__ double red[32];
+    const int t = blockIdx.x;
+    if (threadIdx.x == 0) count = tile_slots(U, C, P, G, np, t, off);
+    __syncthreads();
+    const int nc = count;
+    double sq = 0.0;
+    const int span = np * kBM / kReduceSlices;
+    const int i0 = blockIdx.y * span;
+#pragma unroll 4
+    for (int idx = i0 + threadIdx.x; idx < i0 + span; idx += blockDim.x) {
+        const int jl = idx / np, c = idx % np;
+        const long long j = (long long)t * kBM + jl;
+        if (j >= n) continue;
+        float v = 0.f;
+        for (int q = 0; q < nc; ++q) v += part[off[q] + idx];
+        split_bf16(v, Bs[c + j * np], Bsl[c + j * np]);
+        if (c < pcols) {
+            B[c + j * ldb] = v;
+            sq += (double)v * (double)v;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        sq_part[(size_t)t * kReduceSlices + blockIdx.y] = s;
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -633,24 +1067,37 @@ EncodeTiledFn encoder() {
     return fn;
 }
 
-// FP32 2-D map: `inner` contiguous elements per line, `outer` lines `ld`
-// elements apart; boxes of box_inner x box_outer, zero fill out of bounds.
-cudaError_t make_map(CUtensorMap* map, const float* base, long long inner, long long outer, long long ld,
-                     int box_inner, int box_outer, bool swizzle128) {
+// 2-D map of esize-byte elements: `inner` contiguous elements per line,
+// `outer` lines `ld` elements apart; boxes of box_inner x box_outer, zero
+// fill out of bounds.  The base must be 16-byte aligned and the line pitch a
+// multiple of 16 bytes.
+cudaError_t make_map_t(CUtensorMap* map, const void* base, CUtensorMapDataType dt, int esize, long long inner,
+                       long long outer, long long ld, int box_inner, int box_outer, bool swizzle128) {
     EncodeTiledFn enc = encoder();
     if (!enc) return cudaErrorNotSupported;
-    if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0 || ((ld * 4) & 15) != 0 || inner < box_inner ||
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0 || ((ld * esize) & 15) != 0 || inner < box_inner ||
         outer < box_outer)
         return cudaErrorInvalidValue;
     const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
-    const cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ld * esize)};
     const cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
     const cuuint32_t es[2] = {1, 1};
-    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE,
+    const CUresult r = enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                            swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t make_map(CUtensorMap* map, const float* base, long long inner, long long outer, long long ld,
+                     int box_inner, int box_outer, bool swizzle128) {
+    return make_map_t(map, base, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, inner, outer, ld, box_inner, box_outer,
+                      swizzle128);
+}
+
+cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, long long inner, long long outer, long long ld,
+                     int box_inner, int box_outer, bool swizzle128) {
+    return make_map_t(map, base, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, inner, outer, ld, box_inner, box_outer,
+                      swizzle128);
 }
 
 constexpr int kUpdNJ = 128, kUpdStages = 3;
@@ -681,6 +1128,28 @@ cudaError_t launch_streamk(Ctx& cx, const StreamKParams& p, int np) {
         default: return cudaErrorInvalidValue;
     }
 }
+
+template <int ROLE, int NP>
+cudaError_t launch_streamk16_np(Ctx& cx, const StreamKParams& p) {
+    constexpr size_t smem = StreamK16Cfg<ROLE, NP>::kSmem;
+    cudaError_t e = allow_smem(k_streamk16<ROLE, NP>, smem);
+    if (e != cudaSuccess) return e;
+    k_streamk16<ROLE, NP><<<p.P, 320, smem, cx.stream>>>(p);
+    cx.launches++;
+    return cudaGetLastError();
+}
+
+template <int ROLE>
+cudaError_t launch_streamk16(Ctx& cx, const StreamKParams& p, int np) {
+    switch (np) {
+        case 64: return launch_streamk16_np<ROLE, 64>(cx, p);
+        case 128: return launch_streamk16_np<ROLE, 128>(cx, p);
+        case 256: return launch_streamk16_np<ROLE, 256>(cx, p);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+constexpr size_t kUpd16Smem = (size_t)kUpdStages * (2 * kTileBytes + 2 * kUpdNJ * 128) + 1024;
 
 struct Plan {
     long long U;
@@ -797,6 +1266,119 @@ cudaError_t update(Ctx& cx, const float* Wsrc, long long ldws, float* Wdst, long
     if (sq_out && grid > sq_cap) return cudaErrorInvalidValue;
     if ((e = allow_smem(k_update<kUpdNJ, kUpdStages>, kUpdSmem)) != cudaSuccess) return e;
     k_update<kUpdNJ, kUpdStages><<<grid, 320, kUpdSmem, cx.stream>>>(p);
+    cx.launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return sq_out ? launch_sum_doubles(cx, sq_part, grid, sq_out) : cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// BF16 storage path.
+int pad_block16(int b) { return b <= 64 ? 64 : b <= 128 ? 128 : 256; }
+
+size_t partial_floats16(long long m, long long n, int np, int sms) {
+    const Plan a = plan((m + kBM - 1) / kBM, (n + kKC16 - 1) / kKC16, sms);
+    const Plan b = plan((n + kBM - 1) / kBM, (m + kKC16 - 1) / kKC16, sms);
+    return (size_t)std::max(a.P * a.G, b.P * b.G) * kBM * np;
+}
+
+cudaError_t omega16(Ctx& cx, long long n, long long col0, int p, int np, uint64_t seed, __nv_bfloat16* out,
+                    long long ldo) {
+    const long long total = n * np;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * cx.num_sms);
+    k_omega_bf16<__nv_bfloat16><<<blocks, 256, 0, cx.stream>>>(n, col0, p, np, seed, out, ldo);
+    cx.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t omega16_f32(Ctx& cx, long long n, long long col0, int p, int np, uint64_t seed, float* out,
+                        long long ldo) {
+    const long long total = n * np;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * cx.num_sms);
+    k_omega_bf16<float><<<blocks, 256, 0, cx.stream>>>(n, col0, p, np, seed, out, ldo);
+    cx.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t split_q16(Ctx& cx, const float* Qi, long long ldq, long long m, int p, int np, __nv_bfloat16* Qhi,
+                      __nv_bfloat16* Qlo, long long ldql, __nv_bfloat16* Qt, __nv_bfloat16* Qtl) {
+    dim3 grid((unsigned)((m + 31) / 32), (unsigned)(np / 32));
+    k_split_q16<<<grid, 256, 0, cx.stream>>>(Qi, ldq, m, p, np, Qhi, Qlo, ldql, Qt, Qtl);
+    cx.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t stage_b16(Ctx& cx, const float* Bi, long long ldbi, int p, long long n, int np, __nv_bfloat16* Bs,
+                      __nv_bfloat16* Bsl) {
+    const long long total = n * np;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * cx.num_sms);
+    k_stage_b16<<<blocks, 256, 0, cx.stream>>>(Bi, ldbi, p, n, np, Bs, Bsl);
+    cx.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t sketch16(Ctx& cx, const __nv_bfloat16* X, long long ldx, long long m, long long n,
+                     const __nv_bfloat16* Om, long long ldom, int np, float* Y, long long ldy, float* part,
+                     size_t part_cap) {
+    StreamKParams p;
+    cudaError_t e;
+    if ((e = make_map(&p.mx, X, m, n, ldx, 64, kKC16, true)) != cudaSuccess) return e;
+    if ((e = make_map(&p.mw, Om, n, np, ldom, kKC16, np, true)) != cudaSuccess) return e;
+    p.mwl = p.mw;
+    const Plan pl = plan((m + kBM - 1) / kBM, (n + kKC16 - 1) / kKC16, cx.num_sms);
+    if ((size_t)pl.P * pl.G * kBM * np > part_cap) return cudaErrorInvalidValue;
+    p.part = part;
+    p.st = cx.st;
+    p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
+    if ((e = launch_streamk16<kSketch>(cx, p, np)) != cudaSuccess) return e;
+    k_reduce_sketch<<<dim3(pl.tiles, kReduceSlices), 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, m, Y,
+                                                                           ldy);
+    cx.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t project16(Ctx& cx, const __nv_bfloat16* X, long long ldx, long long m, long long n,
+                      const __nv_bfloat16* Qhi, const __nv_bfloat16* Qlo, long long ldql, int pcols, int np, float* B,
+                      long long ldb, __nv_bfloat16* Bs, __nv_bfloat16* Bsl, float* part, size_t part_cap,
+                      double* sq_part, int sq_cap, double* sq_out) {
+    StreamKParams p;
+    cudaError_t e;
+    if ((e = make_map(&p.mx, X, m, n, ldx, kKC16, kBM, true)) != cudaSuccess) return e;
+    if ((e = make_map(&p.mw, Qhi, m, np, ldql, kKC16, np, true)) != cudaSuccess) return e;
+    if ((e = make_map(&p.mwl, Qlo, m, np, ldql, kKC16, np, true)) != cudaSuccess) return e;
+    const Plan pl = plan((n + kBM - 1) / kBM, (m + kKC16 - 1) / kKC16, cx.num_sms);
+    if ((size_t)pl.P * pl.G * kBM * np > part_cap || pl.tiles * kReduceSlices > sq_cap) return cudaErrorInvalidValue;
+    p.part = part;
+    p.st = cx.st;
+    p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
+    if ((e = launch_streamk16<kProject>(cx, p, np)) != cudaSuccess) return e;
+    k_reduce_project16<<<dim3(pl.tiles, kReduceSlices), 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np,
+                                                                              pcols, n, B, ldb, Bs, Bsl, sq_part);
+    cx.launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_sum_doubles(cx, sq_part, pl.tiles * kReduceSlices, sq_out);
+}
+
+cudaError_t update16(Ctx& cx, const __nv_bfloat16* Wsrc, long long ldws, __nv_bfloat16* Wdst, long long ldwd,
+                     long long m, long long n, const __nv_bfloat16* Qt, const __nv_bfloat16* Qtl,
+                     const __nv_bfloat16* Bs, const __nv_bfloat16* Bsl, int np, double* sq_part, int sq_cap,
+                     double* sq_out) {
+    UpdateParams16 p;
+    cudaError_t e;
+    if ((e = make_map(&p.mqt, Qt, np, m, np, kKC16, kBM, true)) != cudaSuccess) return e;
+    if ((e = make_map(&p.mqtl, Qtl, np, m, np, kKC16, kBM, true)) != cudaSuccess) return e;
+    if ((e = make_map(&p.mbs, Bs, np, n, np, kKC16, kUpdNJ, true)) != cudaSuccess) return e;
+    if ((e = make_map(&p.mbsl, Bsl, np, n, np, kKC16, kUpdNJ, true)) != cudaSuccess) return e;
+    p.Wsrc = Wsrc; p.Wdst = Wdst; p.st = cx.st;
+    p.sq_part = sq_out ? sq_part : nullptr;
+    p.ldws = ldws; p.ldwd = ldwd; p.m = m; p.n = n;
+    p.RT = (int)((m + kBM - 1) / kBM);
+    p.CT = (int)((n + kUpdNJ - 1) / kUpdNJ);
+    p.C = np / kKC16;
+    const long long T = (long long)p.RT * p.CT;
+    const int grid = (int)std::min<long long>(cx.num_sms, T);
+    if (sq_out && grid > sq_cap) return cudaErrorInvalidValue;
+    if ((e = allow_smem(k_update16<kUpdNJ, kUpdStages>, kUpd16Smem)) != cudaSuccess) return e;
+    k_update16<kUpdNJ, kUpdStages><<<grid, 320, kUpd16Smem, cx.stream>>>(p);
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return sq_out ? launch_sum_doubles(cx, sq_part, grid, sq_out) : cudaSuccess;

@@ -6,6 +6,7 @@
 // multiple of 4; the launchers return cudaErrorInvalidValue otherwise.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -49,6 +50,52 @@ cudaError_t project(Ctx& cx, const float* X, long long ldx, long long m, long lo
 cudaError_t update(Ctx& cx, const float* Wsrc, long long ldws, float* Wdst, long long ldwd, long long m,
                    long long n, const float* Qt, const float* Qtl, const float* Bs, const float* Bsl, int np,
                    double* sq_part, int sq_cap, double* sq_out);
+
+// ---------------------------------------------------------------------------
+// BF16 storage path (A and the residual W in BF16; kind::f16 MMAs with FP32
+// accumulation).  np is 64, 128 or 256; BF16 tensor-map sources need a
+// 16-byte aligned base and a leading dimension that is a multiple of 8.
+
+// Block width padded to the BF16 MMA chunk (64 values of K).
+int pad_block16(int b);
+
+// Floats of partial-accumulator scratch of sketch16 / project16.
+size_t partial_floats16(long long m, long long n, int np, int sms);
+
+// Omega_i (n x np, ld ldo): the binary32 Gaussian rounded to BF16; columns
+// p .. np-1 zero.  omega16_f32 writes the same values as floats.
+cudaError_t omega16(Ctx& cx, long long n, long long col0, int p, int np, uint64_t seed, __nv_bfloat16* out,
+                    long long ldo);
+cudaError_t omega16_f32(Ctx& cx, long long n, long long col0, int p, int np, uint64_t seed, float* out,
+                        long long ldo);
+
+// BF16 hi / lo splits of Q_i: column-major Qhi / Qlo (ld ldql) and the
+// row-major transpose pair Qt / Qtl (m x np).
+cudaError_t split_q16(Ctx& cx, const float* Qi, long long ldq, long long m, int p, int np, __nv_bfloat16* Qhi,
+                      __nv_bfloat16* Qlo, long long ldql, __nv_bfloat16* Qt, __nv_bfloat16* Qtl);
+
+// Bs / Bsl (np x n, ld np): BF16 hi / lo split of B_i, zero rows p .. np-1.
+cudaError_t stage_b16(Ctx& cx, const float* Bi, long long ldbi, int p, long long n, int np, __nv_bfloat16* Bs,
+                      __nv_bfloat16* Bsl);
+
+// Y (m x np, FP32) = X (BF16) Omega (BF16): exact products, FP32 sums.
+cudaError_t sketch16(Ctx& cx, const __nv_bfloat16* X, long long ldx, long long m, long long n,
+                     const __nv_bfloat16* Om, long long ldom, int np, float* Y, long long ldy, float* part,
+                     size_t part_cap);
+
+// B (pcols x n, FP32) = Q_i^T X with Q_i as its BF16 split, the staged split
+// copy Bs / Bsl of B, and ||B||_F^2 into *sq_out.
+cudaError_t project16(Ctx& cx, const __nv_bfloat16* X, long long ldx, long long m, long long n,
+                      const __nv_bfloat16* Qhi, const __nv_bfloat16* Qlo, long long ldql, int pcols, int np, float* B,
+                      long long ldb, __nv_bfloat16* Bs, __nv_bfloat16* Bsl, float* part, size_t part_cap,
+                      double* sq_part, int sq_cap, double* sq_out);
+
+// Wdst = rn_bf16(Wsrc - Q_i B_i); Wdst may equal Wsrc.  With sq_out,
+// ||Wdst||_F^2 of the stored values.
+cudaError_t update16(Ctx& cx, const __nv_bfloat16* Wsrc, long long ldws, __nv_bfloat16* Wdst, long long ldwd,
+                     long long m, long long n, const __nv_bfloat16* Qt, const __nv_bfloat16* Qtl,
+                     const __nv_bfloat16* Bs, const __nv_bfloat16* Bsl, int np, double* sq_part, int sq_cap,
+                     double* sq_out);
 
 }  // namespace tc
 }  // namespace rqb

@@ -132,6 +132,12 @@ def _ld(t: torch.Tensor) -> int:
     return max(int(t.stride(1)), int(t.shape[0]), 1)
 
 
+def _need(t: torch.Tensor, dtype: torch.dtype, what: str) -> None:
+    """The library reads t as `dtype`: refuse a tensor of another element type."""
+    if t.dtype != dtype:
+        raise TypeError(f"{what}: expected {dtype}, got {t.dtype}")
+
+
 def _dtype_code(dtype: torch.dtype) -> int:
     return {torch.float64: RQB_F64, torch.float32: RQB_F32, torch.bfloat16: RQB_BF16}[dtype]
 
@@ -202,6 +208,7 @@ class Handle:
     # -- randQB_b ----------------------------------------------------------
     def rqb_factor(self, A: torch.Tensor, eps: float, b: int, seed: int = 0, check: bool = True):
         """Returns (Q view m x k, B view k x n, k, status); views are valid until the next call."""
+        _need(A, self.dtype, "rqb_factor A")
         m, n = A.shape
         Qp, Bp = ctypes.c_void_p(), ctypes.c_void_p()
         ldq, ldb, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
@@ -217,6 +224,9 @@ class Handle:
 
     def rqb_factor_host(self, A_host: torch.Tensor, eps: float, b: int, seed: int, Q_host: torch.Tensor,
                         B_host: torch.Tensor):
+        _need(A_host, self.dtype, "rqb_factor_host A")
+        _need(Q_host, self.out_dtype, "rqb_factor_host Q")
+        _need(B_host, self.out_dtype, "rqb_factor_host B")
         m, n = A_host.shape
         k = ctypes.c_int64()
         rc = lib().rqb_factor_host(self._h, ctypes.c_void_p(A_host.data_ptr()), m, n, _ld(A_host), float(eps), b,
@@ -274,6 +284,7 @@ class Handle:
         return out
 
     def rqb_sketch(self, A: torch.Tensor, col0: int, ncols: int, seed: int):
+        _need(A, self.dtype, "rqb_sketch A")
         m, n = A.shape
         Y = colmajor(torch.empty(ncols, m, dtype=self.out_dtype, device=self.device).t())
         nrm = ctypes.c_double()
@@ -282,6 +293,9 @@ class Handle:
         return Y, float(nrm.value)
 
     def rqb_orth(self, Y: torch.Tensor, Qbar: torch.Tensor | None):
+        _need(Y, self.out_dtype, "rqb_orth Y")
+        if Qbar is not None:
+            _need(Qbar, self.out_dtype, "rqb_orth Qbar")
         m, p = Y.shape
         Qi = colmajor(torch.empty(p, m, dtype=self.out_dtype, device=self.device).t())
         if Qbar is None or Qbar.shape[1] == 0:
@@ -294,6 +308,8 @@ class Handle:
         return Qi
 
     def rqb_project(self, Qi: torch.Tensor, A: torch.Tensor):
+        _need(Qi, self.out_dtype, "rqb_project Qi")
+        _need(A, self.dtype, "rqb_project A")
         m, p = Qi.shape
         n = A.shape[1]
         Bi = colmajor(torch.empty(n, p, dtype=self.out_dtype, device=self.device).t())
@@ -305,6 +321,10 @@ class Handle:
 
     def rqb_downdate_sketch(self, A: torch.Tensor, Qi: torch.Tensor, Bi: torch.Tensor, W: torch.Tensor, col0: int,
                             ncols: int, seed: int):
+        _need(A, self.dtype, "rqb_downdate_sketch A")
+        _need(W, self.dtype, "rqb_downdate_sketch W")
+        _need(Qi, self.out_dtype, "rqb_downdate_sketch Qi")
+        _need(Bi, self.out_dtype, "rqb_downdate_sketch Bi")
         m, n = A.shape
         p = Qi.shape[1]
         Y = colmajor(torch.empty(ncols, m, dtype=self.out_dtype, device=self.device).t())

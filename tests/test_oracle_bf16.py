@@ -67,3 +67,13 @@ def test_storage_64_is_plain_oracle(orc):
     a = orc.randqb_b(A, 1e-3 * np.linalg.norm(A), 20, seed=1)
     c = orc.randqb_b(A, 1e-3 * np.linalg.norm(A), 20, seed=1, storage_prec=64)
     assert a.k == c.k and np.array_equal(a.Q, c.Q) and np.array_equal(a.B, c.B)
+
+
+def test_round_bf16_array_matches_scalar(orc):
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((37, 11)) * 10.0 ** rng.integers(-30, 30, size=(37, 11))
+    x[0, 0], x[1, 0], x[2, 0] = 1.0 + 2.0 ** -8, -(1.0 + 3 * 2.0 ** -8), 0.0
+    y = orc.round_bf16_array(x)
+    assert y.shape == x.shape
+    assert np.array_equal(y, np.vectorize(orc.round_bf16)(x))
+    assert y[0, 0] == 1.0 and y[1, 0] == -(1.0 + 2.0 ** -6) and y[2, 0] == 0.0

@@ -125,7 +125,7 @@ typedef struct {
     double D[RQB_MAX_TRACKED_BLOCKS];  /* direct ||A^(i)||_F^2 where computed,
                                           else -1                              */
     int32_t kernel_launches; /* kernels launched by the last call              */
-    int32_t reserved;
+    int32_t svd_sweeps;      /* Jacobi sweeps of the last rqb_svd              */
     double phase_ms[RQB_NUM_PHASES];     /* summed device time per step (ms)   */
     int32_t phase_calls[RQB_NUM_PHASES]; /* times each step ran                */
 } rqb_stats;
@@ -214,6 +214,24 @@ int rqb_reconstruct(rqb_handle h, void* X, int64_t ldx);
  * the handle, bad leading dimension), RQB_ERR_UNSUPPORTED (power > 0 or a
  * BF16 handle). */
 int rqb_backward(rqb_handle h, const void* dL_dX, int64_t ldg, void* dL_dA, int64_t ldda);
+
+/* Low-rank SVD from the last factorization on this handle (Sec. 2,
+ * "Computing the low rank SVD"): with the full SVD of the k x n factor
+ * B = U_hat D V_hat^T, the rank-r factors are U_r = Q U_hat(:, 1:r),
+ * Sigma_r = D(1:r, 1:r) and V_r = V_hat(:, 1:r), so A ~ U_r Sigma_r V_r^T.
+ * B's SVD is taken from G = B B^T (k x k; FP64 sums of exact products) by
+ * cyclic Jacobi rotations in FP64 until a sweep rotates nothing (a rotation
+ * is skipped when |g_pq| <= 1e-15 sqrt(g_pp g_qq)); sigma_i = sqrt(lambda_i),
+ * U_hat = the eigenvectors, V_r^T = Sigma_r^-1 U_hat(:, 1:r)^T B.
+ *   r      1 <= r <= k of the last factorization
+ *   U      device, m x r, leading dim ldu >= m (handle's output type)
+ *   S      HOST, r doubles, descending
+ *   Vt     device, r x n = V_r^T, leading dim ldvt >= r (a row for a zero
+ *          singular value is zero)
+ * Cost: O(k^2 n) for G and O(k^3) per Jacobi sweep (typically 6-10 sweeps);
+ * stats.svd_sweeps reports the sweeps.  Errors: RQB_ERR_INVALID (no
+ * factorization, bad r or leading dimension), RQB_ERR_NONFINITE, RQB_ERR_OOM. */
+int rqb_svd(rqb_handle h, int64_t r, void* U, int64_t ldu, double* S, void* Vt, int64_t ldvt);
 
 /* Statistics of the last call on this handle. */
 int rqb_get_stats(rqb_handle h, rqb_stats* out);

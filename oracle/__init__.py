@@ -63,6 +63,8 @@ def _lib():
         lib.orc_round_bf16.argtypes = [dbl]
         lib.orc_round_bf16.restype = dbl
         lib.orc_round_bf16_n.argtypes = [P, P, i64]
+        lib.orc_rsvd.argtypes = [P, i64, i64, i64, P, i64, i64, i64, P, i64, P, P, i64]
+        lib.orc_rsvd.restype = i32
         lib.orc_randqb_b_store.argtypes = [P, i64, i64, i64, dbl, i64, u64, i64, i32, i32, i32, i32, i32,
                                            P, i64, P, i64, P]
         lib.orc_randqb_b_store.restype = i32
@@ -202,6 +204,20 @@ def svd_values(A):
     s = np.zeros(min(m, n))
     _lib().orc_svd_values(_ptr(A), m, n, m, _ptr(s))
     return s
+
+
+def rsvd(Q, B, r: int):
+    """Rank-r SVD of Q B (Sec. 2): returns U (m x r), S (r,), Vt (r x n)."""
+    Q, B = _f64(Q), _f64(B)
+    m, k = Q.shape
+    n = B.shape[1]
+    U = np.zeros((m, r), order="F")
+    S = np.zeros(r)
+    Vt = np.zeros((r, n), order="F")
+    rc = _lib().orc_rsvd(_ptr(Q), m, k, m, _ptr(B), n, k, r, _ptr(U), m, _ptr(S), _ptr(Vt), r)
+    if rc != 0:
+        raise ValueError("orc_rsvd: invalid arguments")
+    return U, S, Vt
 
 
 def qqta_adjoint(A, Q, B, G, seed: int = 0, omega_prec: int = 64):

@@ -462,6 +462,85 @@ int orc_svd_values(const double* A, int64_t m, int64_t n, int64_t lda, double* s
     return 0;
 }
 
+/* Low-rank SVD from Q (m x k) and B (k x n) (Sec. 2, computing the low rank
+ * SVD): the full SVD B = Uh D Vh^T, then U_r = Q Uh(:, 1:r), S = D(1:r) and
+ * Vt = Vh(:, 1:r)^T.  B's SVD by one-sided (Hestenes) Jacobi on X = B^T
+ * (n x k): column rotations X J make the columns of X orthogonal, so
+ * B^T = (X J) J^T, sigma_i = ||(X J)_i||, Vh_i = (X J)_i / sigma_i and Uh = J.
+ * Needs k <= n.  S in decreasing order; a zero sigma gives a zero Vt row. */
+int orc_rsvd(const double* Q, int64_t m, int64_t k, int64_t ldq, const double* B, int64_t n, int64_t ldb,
+             int64_t r, double* U, int64_t ldu, double* S, double* Vt, int64_t ldvt) {
+    if (k < 1 || r < 1 || r > k || k > n || ldq < m || ldb < k || ldu < m || ldvt < r) return -1;
+    double* X = (double*)malloc(sizeof(double) * (size_t)n * (size_t)k);
+    double* J = (double*)malloc(sizeof(double) * (size_t)k * (size_t)k);
+    double* sig = (double*)malloc(sizeof(double) * (size_t)k);
+    int64_t* ord = (int64_t*)malloc(sizeof(int64_t) * (size_t)k);
+    for (int64_t c = 0; c < k; ++c)
+        for (int64_t j = 0; j < n; ++j) X[j + c * n] = B[c + j * ldb];
+    for (int64_t c = 0; c < k; ++c)
+        for (int64_t i = 0; i < k; ++i) J[i + c * k] = (i == c) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int64_t i = 0; i < k - 1; ++i) {
+            for (int64_t j = i + 1; j < k; ++j) {
+                double* xi = X + i * n;
+                double* xj = X + j * n;
+                double a = 0.0, bb = 0.0, g = 0.0;
+                for (int64_t t = 0; t < n; ++t) {
+                    a += xi[t] * xi[t];
+                    bb += xj[t] * xj[t];
+                    g += xi[t] * xj[t];
+                }
+                if (g == 0.0) continue;
+                double rel = fabs(g) / sqrt(a * bb);
+                if (rel > off) off = rel;
+                if (rel < 1e-15) continue;
+                double zeta = (bb - a) / (2.0 * g);
+                double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+                for (int64_t q = 0; q < n; ++q) {
+                    double x = xi[q], y = xj[q];
+                    xi[q] = cs * x - sn * y;
+                    xj[q] = sn * x + cs * y;
+                }
+                double* ji = J + i * k;
+                double* jj = J + j * k;
+                for (int64_t q = 0; q < k; ++q) {
+                    double x = ji[q], y = jj[q];
+                    ji[q] = cs * x - sn * y;
+                    jj[q] = sn * x + cs * y;
+                }
+            }
+        }
+        if (off < 1e-15) break;
+    }
+    for (int64_t c = 0; c < k; ++c) {
+        double s2 = 0.0;
+        for (int64_t t = 0; t < n; ++t) s2 += X[t + c * n] * X[t + c * n];
+        sig[c] = sqrt(s2);
+        ord[c] = c;
+    }
+    /* insertion sort of the indices by decreasing sigma (stable) */
+    for (int64_t i = 1; i < k; ++i) {
+        int64_t v = ord[i];
+        int64_t j = i - 1;
+        while (j >= 0 && sig[ord[j]] < sig[v]) { ord[j + 1] = ord[j]; --j; }
+        ord[j + 1] = v;
+    }
+    for (int64_t c = 0; c < r; ++c) {
+        const int64_t o = ord[c];
+        S[c] = sig[o];
+        for (int64_t i = 0; i < m; ++i) {
+            double acc = 0.0;
+            for (int64_t t = 0; t < k; ++t) acc += Q[i + t * ldq] * J[t + o * k];
+            U[i + c * ldu] = acc;
+        }
+        for (int64_t j = 0; j < n; ++j) Vt[c + j * ldvt] = sig[o] > 0.0 ? X[j + o * n] / sig[o] : 0.0;
+    }
+    free(X); free(J); free(sig); free(ord);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Derivative of the fixed-rank map A -> X = Q Q^T A, Q = orth(A Omega) with
  * Omega (n x k, the first k global columns) held fixed.  Q Q^T is the

@@ -110,6 +110,13 @@ int orc_randqb(const double* A, int64_t m, int64_t n, int64_t lda, int64_t l,
  * sorted in decreasing order; sigma has min(m, n) entries. */
 int orc_svd_values(const double* A, int64_t m, int64_t n, int64_t lda, double* sigma);
 
+/* Low-rank SVD from a QB factorization (Sec. 2): B = Uh D Vh^T by one-sided
+ * Jacobi on B^T; U = Q Uh(:, 1:r) (m x r), S = D(1:r) decreasing, Vt =
+ * Vh(:, 1:r)^T (r x n).  Needs 1 <= r <= k <= n.  Returns 0, or -1 on bad
+ * arguments. */
+int orc_rsvd(const double* Q, int64_t m, int64_t k, int64_t ldq, const double* B, int64_t n, int64_t ldb,
+             int64_t r, double* U, int64_t ldu, double* S, double* Vt, int64_t ldvt);
+
 /* One step of the blocked scheme, exposed for step-level checks:
  *   orc_sketch:  Y = A Omega(:, col0 : col0 + p), Y is m x p.
  *   orc_orth_reproject: lines (3) and (3') of Fig. randQB_b,

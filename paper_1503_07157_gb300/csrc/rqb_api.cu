@@ -124,6 +124,7 @@ struct rqb_handle_s {
     bool have_factor = false;
     DevBuf adj;                // workspace of rqb_backward
     DevBuf tcbuf;              // operand copies and partials of the tensor-core products
+    DevBuf svdbuf;             // workspace of rqb_svd
     void* bat_out = nullptr;   // outputs of rqb_factor_batched
     size_t bat_out_bytes = 0;
     void* bat_work = nullptr;  // its descriptors and per-CTA scratch
@@ -870,6 +871,7 @@ int rqb_destroy(rqb_handle h) {
     h->ahost.release();
     h->adj.release();
     h->tcbuf.release();
+    h->svdbuf.release();
     if (h->bat_out) cudaFree(h->bat_out);
     if (h->bat_work) cudaFree(h->bat_work);
     if (h->hstate) cudaFreeHost(h->hstate);
@@ -1473,6 +1475,32 @@ extern "C" int rqb_reconstruct(rqb_handle h, void* X, int64_t ldx) {
     if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
     int rc = (h->cfg.dtype == RQB_F64) ? reconstruct_impl<double>(h, static_cast<double*>(X), ldx)
                                        : reconstruct_impl<float>(h, static_cast<float*>(X), ldx);
+    return finish(h, rc);
+}
+
+extern "C" int rqb_svd(rqb_handle h, int64_t r, void* U, int64_t ldu, double* S, void* Vt, int64_t ldvt) {
+    if (!h) return RQB_ERR_INVALID;
+    if (!h->have_factor || r < 1 || r > h->last_k || r > (int64_t)1 << 30 || !U || !S || !Vt || ldu < h->last_m ||
+        ldvt < r)
+        return finish(h, RQB_ERR_INVALID);
+    if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
+    const int k = (int)h->last_k;
+    int rc = h->svdbuf.ensure(svd_scratch_bytes(h->last_m, h->last_n, k, (int)r));
+    if (rc != RQB_OK) return finish(h, rc);
+    Scal sc = scalars(h);
+    Ctx cx;
+    cx.stream = h->stream; cx.num_sms = h->num_sms; cx.st = sc.st;
+    int sweeps = 0;
+    if (h->cfg.dtype == RQB_F64)
+        rc = svd_lowrank<double>(cx, h->last_m, h->last_n, k, (int)r, static_cast<const double*>(h->q.p), h->ldq,
+                                 static_cast<const double*>(h->b.p), h->ldb, static_cast<double*>(U), ldu, S,
+                                 static_cast<double*>(Vt), ldvt, h->svdbuf.p, h->svdbuf.bytes, &sweeps);
+    else
+        rc = svd_lowrank<float>(cx, h->last_m, h->last_n, k, (int)r, static_cast<const float*>(h->q.p), h->ldq,
+                                static_cast<const float*>(h->b.p), h->ldb, static_cast<float*>(U), ldu, S,
+                                static_cast<float*>(Vt), ldvt, h->svdbuf.p, h->svdbuf.bytes, &sweeps);
+    h->stats.kernel_launches = cx.launches;
+    h->stats.svd_sweeps = sweeps;
     return finish(h, rc);
 }
 

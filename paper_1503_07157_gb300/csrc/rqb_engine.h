@@ -83,4 +83,12 @@ cudaError_t launch_set_norm(Ctx& cx, const double* nrm);
 cudaError_t launch_stop_after_b(Ctx& cx, const double* nb2, double eps2, double tau_rel, int fixed);
 cudaError_t launch_stop_direct(Ctx& cx, const double* d2, double eps2, bool always = false);
 
+// Low-rank SVD of Q B (rqb_svd.cu): U (m x r), S_host (r, descending),
+// Vt (r x n); returns an rqb_status.
+size_t svd_scratch_bytes(int64_t m, int64_t n, int k, int r);
+template <typename T>
+int svd_lowrank(Ctx& cx, int64_t m, int64_t n, int k, int r, const T* Q, int64_t ldq, const T* B, int64_t ldb,
+                T* U, int64_t ldu, double* S_host, T* Vt, int64_t ldvt, void* scratch, size_t scratch_bytes,
+                int* sweeps_out);
+
 }  // namespace rqb

@@ -59,7 +59,7 @@ class rqb_stats(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int64), ("blocks", ctypes.c_int64), ("status", ctypes.c_int32),
                 ("direct_tests", ctypes.c_int32), ("normA2", ctypes.c_double), ("eps", ctypes.c_double),
                 ("E", ctypes.c_double * RQB_MAX_TRACKED_BLOCKS), ("D", ctypes.c_double * RQB_MAX_TRACKED_BLOCKS),
-                ("kernel_launches", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int32), ("svd_sweeps", ctypes.c_int32),
                 ("phase_ms", ctypes.c_double * RQB_NUM_PHASES), ("phase_calls", ctypes.c_int32 * RQB_NUM_PHASES)]
 
 
@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
             "rqb_reconstruct": [P, P, i64],
             "rqb_factor_batched": [P, i64, P, P, P, P, P, i64, u64, P, P, P, P, P, P],
             "rqb_backward": [P, P, i64, P, i64],
+            "rqb_svd": [P, i64, P, i64, Pd, P, i64],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -218,6 +219,7 @@ class Handle:
         if check:
             _check(rc, "rqb_factor", ok=(RQB_OK, RQB_NOT_CONVERGED))
         kk = int(k.value)
+        self._last_shape = (m, n)
         Q = _view(Qp.value or 0, m, kk, int(ldq.value), self.out_dtype, self.device)
         B = _view(Bp.value or 0, kk, n, int(ldb.value), self.out_dtype, self.device)
         return Q, B, kk, rc
@@ -233,6 +235,7 @@ class Handle:
                                    seed, ctypes.c_void_p(Q_host.data_ptr()), _ld(Q_host),
                                    ctypes.c_void_p(B_host.data_ptr()), _ld(B_host), ctypes.byref(k))
         _check(rc, "rqb_factor_host", ok=(RQB_OK, RQB_NOT_CONVERGED))
+        self._last_shape = (m, n)
         return int(k.value), rc
 
     def rqb_reconstruct(self, m: int, n: int) -> torch.Tensor:
@@ -247,6 +250,21 @@ class Handle:
         _check(lib().rqb_backward(self._h, ctypes.c_void_p(G.data_ptr()), _ld(G), ctypes.c_void_p(dA.data_ptr()),
                                   _ld(dA)), "rqb_backward")
         return dA
+
+    def rqb_svd(self, r: int):
+        """Rank-r SVD of the last factorization: (U m x r, S numpy (r,), Vt r x n, Jacobi sweeps)."""
+        st = rqb_stats()
+        _check(lib().rqb_get_stats(self._h, ctypes.byref(st)), "rqb_get_stats")
+        m, n = self._last_shape
+        U = colmajor(torch.empty(r, m, dtype=self.out_dtype, device=self.device).t())
+        Vt = colmajor(torch.empty(n, r, dtype=self.out_dtype, device=self.device).t())
+        S = (ctypes.c_double * r)()
+        _check(lib().rqb_svd(self._h, r, ctypes.c_void_p(U.data_ptr()), _ld(U),
+                             ctypes.cast(S, ctypes.POINTER(ctypes.c_double)), ctypes.c_void_p(Vt.data_ptr()),
+                             _ld(Vt)), "rqb_svd")
+        lib().rqb_get_stats(self._h, ctypes.byref(st))
+        import numpy as np
+        return U, np.array(S[:], dtype=np.float64), Vt, int(st.svd_sweeps)
 
     def rqb_factor_batched(self, As: list, eps: list, b: int, seed: int = 0):
         """As: column-major FP32 device matrices.  Returns [(Q view, B view, k, status)]."""

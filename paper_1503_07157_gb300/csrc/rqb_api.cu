@@ -1226,11 +1226,24 @@ int dd_bf16(rqb_handle h, const __nv_bfloat16* A, int64_t lda, const float* Qi, 
     RQB_CK(cudaMemsetAsync(sc.st, 0, sizeof(DevState), h->stream));
     RQB_CK(tc::split_q16(cx, Qi, ldqi, m, p, bpu, ta.Qhi, ta.Qlo, ta.ldql, ta.Qt, ta.Qtl));
     RQB_CK(tc::stage_b16(cx, Bi, ldbi, p, n, bpu, ta.Bs, ta.Bsl));
-    RQB_CK(tc::update16(cx, A, lda, W, ldw, m, n, ta.Qt, ta.Qtl, ta.Bs, ta.Bsl, bpu, sc.nrm, kNrmCap,
+    // the update reads and writes W through TMA: unaligned operands go
+    // through aligned copies (A into the handle's W buffer, the result into
+    // the adjoint workspace, copied out afterwards)
+    const __nv_bfloat16* Ax;
+    int64_t ldax;
+    if ((rc = tma_source16(h, A, lda, m, n, &Ax, &ldax)) != RQB_OK) return rc;
+    __nv_bfloat16* X = W;
+    int64_t ldx = ldw;
+    const bool copy_out = !tma_ok16(W, ldw);
+    if (copy_out) {
+        ldx = round_up(m, 8);
+        if ((rc = h->adj.ensure(2 * (size_t)ldx * (size_t)n)) != RQB_OK) return rc;
+        X = reinterpret_cast<__nv_bfloat16*>(h->adj.p);
+    }
+    RQB_CK(tc::update16(cx, Ax, ldax, X, ldx, m, n, ta.Qt, ta.Qtl, ta.Bs, ta.Bsl, bpu, sc.nrm, kNrmCap,
                         normW2 ? sc.s + 2 : nullptr));
-    const __nv_bfloat16* X;
-    int64_t ldx;
-    if ((rc = tma_source16(h, W, ldw, m, n, &X, &ldx)) != RQB_OK) return rc;
+    if (copy_out)
+        RQB_CK(cudaMemcpy2DAsync(W, 2 * ldw, X, 2 * ldx, 2 * m, n, cudaMemcpyDeviceToDevice, h->stream));
     RQB_CK(tc::omega16(cx, n, col0, ncols, bps, seed, ta.Om, ta.ldom));
     RQB_CK(tc::sketch16(cx, X, ldx, m, n, ta.Om, ta.ldom, bps, ar.Y, m, ta.part, ta.part_cap));
     RQB_CK(cudaMemcpy2DAsync(Y, sizeof(float) * ldy, ar.Y, sizeof(float) * m, sizeof(float) * m, ncols,

@@ -780,22 +780,26 @@ __global__ void k_reduce_project(const float* __restrict__ part, long long U, in
 // ---------------------------------------------------------------------------
 // BF16 update: Wdst = round_bf16(Wsrc - Q_i B_i) on 128 x NJ tiles, K = bp in
 // chunks of 64; Q_i^T and B_i split into BF16 hi + lo, three passes (the
-// lo x lo term is below 2^-17 of the product).  ||Wdst||_F^2 of the rounded
-// values (exact FP32 squares) per CTA.
+// lo x lo term is below 2^-17 of the product).  The W tile travels by TMA in
+// both directions: warp 10 loads tile g of Wsrc into one of two W buffers,
+// the eight epilogue warps replace it in shared memory by the rounded
+// difference, and one thread stores it with a TMA store.  ||Wdst||_F^2 of
+// the rounded values (exact FP32 squares) per CTA.
 struct UpdateParams16 {
     CUtensorMap mqt, mqtl;  // Q_i^T hi / lo, row-major m x bp (as {bp, m}), box {64, 128}
     CUtensorMap mbs, mbsl;  // B_i hi / lo, bp x n column-major, box {64, NJ}
-    const __nv_bfloat16* Wsrc;
-    __nv_bfloat16* Wdst;
+    CUtensorMap mws, mwd;   // Wsrc / Wdst, m x n column-major, box {128 rows, NJ columns}, no swizzle
     DevState* st;
     double* sq_part;
-    long long ldws, ldwd, m, n;
+    long long m, n;
     int RT, CT, C;
 };
 
+constexpr int kUpd16Threads = 352;   // warps 0 (operand TMA), 1 (MMA), 2..9 (epilogue), 10 (W loads)
+
 template <int NJ, int S>
-__global__ void __launch_bounds__(320, 1) k_update16(const __grid_constant__ UpdateParams16 p) {
-    __shared__ __align__(8) uint64_t full[S], empty[S], accfull[2], accempty[2], drain;
+__global__ void __launch_bounds__(kUpd16Threads, 1) k_update16(const __grid_constant__ UpdateParams16 p) {
+    __shared__ __align__(8) uint64_t full[S], empty[S], accfull[2], accempty[2], wfull[2], wempty[2], drain;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     __shared__ double red[8];
@@ -803,12 +807,17 @@ __global__ void __launch_bounds__(320, 1) k_update16(const __grid_constant__ Upd
     uint8_t* base = dsm + (((smem_u32(dsm) + 1023u) & ~1023u) - smem_u32(dsm));
     constexpr uint32_t kB = (uint32_t)NJ * 128u;
     constexpr uint32_t kStage = 2u * kTileBytes + 2u * kB;
+    constexpr uint32_t kWTile = (uint32_t)kBM * NJ * 2u;   // one BF16 W tile
+    uint8_t* wbuf = base + S * kStage;
     constexpr uint32_t kCols = 2u * NJ;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     volatile int* ab = &abort_flag;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        for (int s = 0; s < 2; ++s) { mbar_init(&accfull[s], 1); mbar_init(&accempty[s], 8); }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&accfull[s], 1); mbar_init(&accempty[s], 8);
+            mbar_init(&wfull[s], 1); mbar_init(&wempty[s], 1);
+        }
         mbar_init(&drain, 1);
         abort_flag = 0;
         fence_mbar_init();
@@ -816,6 +825,8 @@ __global__ void __launch_bounds__(320, 1) k_update16(const __grid_constant__ Upd
         prefetch_map(&p.mqtl);
         prefetch_map(&p.mbs);
         prefetch_map(&p.mbsl);
+        prefetch_map(&p.mws);
+        prefetch_map(&p.mwd);
     }
     if (warp == 1) tmem_alloc(&tmem_base, kCols);
     tc_fence_before();
@@ -844,6 +855,18 @@ __global__ void __launch_bounds__(320, 1) k_update16(const __grid_constant__ Upd
             }
             for (long long qq = (q > S ? q - S : 0); qq < q; ++qq)
                 mbar_wait(&full[qq % S], (uint32_t)(qq / S) & 1u, ab, false);
+        }
+    } else if (warp == 10) {
+        if (lane == 0) {
+            int g = 0;
+            for (int t = blockIdx.x; t < T; t += gridDim.x, ++g) {
+                const int b = g & 1, use = g >> 1;
+                if (use > 0 && !mbar_wait(&wempty[b], (uint32_t)(use - 1) & 1u, ab)) break;
+                mbar_arrive_expect_tx(&wfull[b], kWTile);
+                tma_load_2d(wbuf + b * kWTile, &p.mws, (t / p.CT) * kBM, (t % p.CT) * NJ, &wfull[b]);
+            }
+            for (int gg = (g > 2 ? g - 2 : 0); gg < g; ++gg)
+                mbar_wait(&wfull[gg & 1], (uint32_t)(gg >> 1) & 1u, ab, false);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -885,48 +908,61 @@ __global__ void __launch_bounds__(320, 1) k_update16(const __grid_constant__ Upd
         const int quarter = warp & 3;
         const int half = e >> 2;
         constexpr int kHalf = NJ / 2;
+        const bool issuer = (warp == 2 && lane == 0);
+        const int row = quarter * 32 + lane;          // tile row of this thread
         double sq = 0.0;
         int g = 0;
         for (int t = blockIdx.x; t < T; t += gridDim.x, ++g) {
             const int abuf = g & 1, use = g >> 1;
-            const bool okw = mbar_wait(&accfull[abuf], (uint32_t)use & 1u, ab);
-            if (!__all_sync(0xffffffffu, okw)) break;
+            bool okw = mbar_wait(&accfull[abuf], (uint32_t)use & 1u, ab);
+            if (okw) okw = mbar_wait(&wfull[abuf], (uint32_t)use & 1u, ab);
+            // all eight warps leave together (the named barrier below counts them)
+            named_barrier(1, 256);
+            if (*ab || !okw) break;
             tc_fence_after();
             const int rt = t / p.CT, ctile = t % p.CT;
-            const long long r = (long long)rt * kBM + quarter * 32 + lane;
+            const long long r = (long long)rt * kBM + row;
             const long long j0 = (long long)ctile * NJ + half * kHalf;
             const bool rok = r < p.m;
-            const unsigned short* src = reinterpret_cast<const unsigned short*>(p.Wsrc) + r;
-            __nv_bfloat16* dst = p.Wdst + r;
+            // W tile column-major: element (row, col) at col * 256 + row * 2
+            unsigned short* wt = reinterpret_cast<unsigned short*>(wbuf + abuf * kWTile) + row;
             const uint32_t tl = tmem + (uint32_t)(abuf * NJ + half * kHalf) + ((uint32_t)(quarter * 32) << 16);
+            float sq32 = 0.f;
 #pragma unroll 1
-            for (int c0 = 0; c0 < kHalf; c0 += 32) {
-                float w[32];
+            for (int c0 = 0; c0 < kHalf; c0 += 16) {
+                float v[16];
+                tmem_ld16(tl + (uint32_t)c0, v);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const long long j = j0 + c0 + i;
-                    w[i] = (rok && j < p.n) ? __bfloat162float(__ushort_as_bfloat16(__ldcs(src + j * p.ldws))) : 0.f;
-                }
-                float v0[16], v1[16];
-                tmem_ld16(tl + (uint32_t)c0, v0);
-                tmem_ld16(tl + (uint32_t)(c0 + 16), v1);
-                float sq32 = 0.f;
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const long long j = j0 + c0 + i;
-                    const __nv_bfloat16 o = __float2bfloat16_rn(w[i] - (i < 16 ? v0[i] : v1[i - 16]));
-                    if (rok && j < p.n) {
-                        dst[j * p.ldwd] = o;
+                for (int i = 0; i < 16; ++i) {
+                    const int cl = half * kHalf + c0 + i;
+                    const float w = __bfloat162float(__ushort_as_bfloat16(wt[cl * kBM]));
+                    const __nv_bfloat16 o = __float2bfloat16_rn(w - v[i]);
+                    wt[cl * kBM] = __bfloat16_as_ushort(o);
+                    if (rok && j0 + c0 + i < p.n) {
                         const float of = __bfloat162float(o);
                         sq32 = fmaf(of, of, sq32);
                     }
                 }
-                sq += (double)sq32;
+                if ((c0 & 31) == 16) {
+                    sq += (double)sq32;
+                    sq32 = 0.f;
+                }
             }
+            sq += (double)sq32;
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&accempty[abuf]);
+            fence_async_smem();
+            named_barrier(1, 256);
+            if (issuer) {
+                tma_store_2d(&p.mwd, rt * kBM, ctile * NJ, wbuf + abuf * kWTile);
+                bulk_commit();
+                // the previous tile's store has read its buffer: hand it back
+                bulk_wait_read<1>();
+                if (g > 0) mbar_arrive(&wempty[abuf ^ 1]);
+            }
         }
+        if (issuer) bulk_wait<0>();
         for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
         if (lane == 0) red[e] = sq;
     }
@@ -1149,7 +1185,9 @@ cudaError_t launch_streamk16(Ctx& cx, const StreamKParams& p, int np) {
     }
 }
 
-constexpr size_t kUpd16Smem = (size_t)kUpdStages * (2 * kTileBytes + 2 * kUpdNJ * 128) + 1024;
+constexpr int kUpd16Stages = 2;
+constexpr size_t kUpd16Smem =
+    (size_t)kUpd16Stages * (2 * kTileBytes + 2 * kUpdNJ * 128) + 2 * (size_t)kBM * kUpdNJ * 2 + 1024;
 
 struct Plan {
     long long U;
@@ -1368,17 +1406,19 @@ cudaError_t update16(Ctx& cx, const __nv_bfloat16* Wsrc, long long ldws, __nv_bf
     if ((e = make_map(&p.mqtl, Qtl, np, m, np, kKC16, kBM, true)) != cudaSuccess) return e;
     if ((e = make_map(&p.mbs, Bs, np, n, np, kKC16, kUpdNJ, true)) != cudaSuccess) return e;
     if ((e = make_map(&p.mbsl, Bsl, np, n, np, kKC16, kUpdNJ, true)) != cudaSuccess) return e;
-    p.Wsrc = Wsrc; p.Wdst = Wdst; p.st = cx.st;
+    if ((e = make_map(&p.mws, Wsrc, m, n, ldws, kBM, kUpdNJ, false)) != cudaSuccess) return e;
+    if ((e = make_map(&p.mwd, Wdst, m, n, ldwd, kBM, kUpdNJ, false)) != cudaSuccess) return e;
+    p.st = cx.st;
     p.sq_part = sq_out ? sq_part : nullptr;
-    p.ldws = ldws; p.ldwd = ldwd; p.m = m; p.n = n;
+    p.m = m; p.n = n;
     p.RT = (int)((m + kBM - 1) / kBM);
     p.CT = (int)((n + kUpdNJ - 1) / kUpdNJ);
     p.C = np / kKC16;
     const long long T = (long long)p.RT * p.CT;
     const int grid = (int)std::min<long long>(cx.num_sms, T);
     if (sq_out && grid > sq_cap) return cudaErrorInvalidValue;
-    if ((e = allow_smem(k_update16<kUpdNJ, kUpdStages>, kUpd16Smem)) != cudaSuccess) return e;
-    k_update16<kUpdNJ, kUpdStages><<<grid, 320, kUpd16Smem, cx.stream>>>(p);
+    if ((e = allow_smem(k_update16<kUpdNJ, kUpd16Stages>, kUpd16Smem)) != cudaSuccess) return e;
+    k_update16<kUpdNJ, kUpd16Stages><<<grid, kUpd16Threads, kUpd16Smem, cx.stream>>>(p);
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return sq_out ? launch_sum_doubles(cx, sq_part, grid, sq_out) : cudaSuccess;

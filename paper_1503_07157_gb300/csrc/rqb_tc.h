@@ -90,7 +90,8 @@ cudaError_t project16(Ctx& cx, const __nv_bfloat16* X, long long ldx, long long 
                       long long ldb, __nv_bfloat16* Bs, __nv_bfloat16* Bsl, float* part, size_t part_cap,
                       double* sq_part, int sq_cap, double* sq_out);
 
-// Wdst = rn_bf16(Wsrc - Q_i B_i); Wdst may equal Wsrc.  With sq_out,
+// Wdst = rn_bf16(Wsrc - Q_i B_i); Wdst may equal Wsrc (both TMA-addressable:
+// 16-byte aligned, leading dimension a multiple of 8).  With sq_out,
 // ||Wdst||_F^2 of the stored values.
 cudaError_t update16(Ctx& cx, const __nv_bfloat16* Wsrc, long long ldws, __nv_bfloat16* Wdst, long long ldwd,
                      long long m, long long n, const __nv_bfloat16* Qt, const __nv_bfloat16* Qtl,

@@ -125,6 +125,7 @@ struct rqb_handle_s {
     DevBuf adj;                // workspace of rqb_backward
     DevBuf tcbuf;              // operand copies and partials of the tensor-core products
     DevBuf svdbuf;             // workspace of rqb_svd
+    DevBuf pcbuf;              // workspace of the tensor-core re-projection
     void* bat_out = nullptr;   // outputs of rqb_factor_batched
     size_t bat_out_bytes = 0;
     void* bat_work = nullptr;  // its descriptors and per-CTA scratch
@@ -150,6 +151,7 @@ struct Arena {
     double* Cd;     // kprev x bp
     double* dpart;  // FP64 split partials
     size_t dpart_cap;
+    const tc::ReprojScratch* rp = nullptr;  // set: line (3') on the tensor core
 };
 
 struct Scal {
@@ -247,6 +249,30 @@ int ensure_tc(rqb_handle h, int64_t m, int64_t n, int bp, TcArena* out) {
     return RQB_OK;
 }
 
+// Workspace of the split-TF32 re-projection (line (3')) for panels of bp
+// columns against up to kcap earlier columns.
+int ensure_reproj(rqb_handle h, int64_t m, int64_t kcap, int bp, tc::ReprojScratch* w) {
+    const int64_t ldyl = round_up(m, 4), ldom = round_up(kcap, 4);
+    const size_t part = tc::partial_floats(m, std::max<int64_t>(kcap, 256), bp, h->num_sms);
+    size_t off = 0;
+    auto take = [&](size_t floats) { size_t o = off; off = align256(off + 4 * floats); return o; };
+    const size_t oYh = take((size_t)ldyl * bp), oYl = take((size_t)ldyl * bp);
+    const size_t oCt = take((size_t)bp * kcap), oOm = take((size_t)ldom * bp);
+    const size_t oBs = take((size_t)bp * kcap), oBsl = take((size_t)bp * kcap);
+    const size_t oP = take(part);
+    int rc = h->pcbuf.ensure(off);
+    if (rc != RQB_OK) return rc;
+    char* base = reinterpret_cast<char*>(h->pcbuf.p);
+    auto at = [&](size_t o) { return reinterpret_cast<float*>(base + o); };
+    Scal sc = scalars(h);
+    w->Yhi = at(oYh); w->Ylo = at(oYl); w->ldyl = ldyl;
+    w->Ct = at(oCt); w->Om = at(oOm); w->ldom = ldom;
+    w->Bs = at(oBs); w->Bsl = at(oBsl);
+    w->part = at(oP); w->part_cap = part;
+    w->sq_part = sc.nrm; w->sq_cap = kNrmCap; w->sq_out = sc.s + 8;
+    return RQB_OK;
+}
+
 bool tma_ok(const void* p, int64_t ld) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0 && ld % 4 == 0; }
 
 int cuda_status(cudaError_t e) {
@@ -293,7 +319,14 @@ int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_
         RQB_CK(gemm_nn<T>(cx, a));
     }
     // line (3'): Y1 -= Qbar (Qbar^T Y1)
-    if (kprev > 0) {
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if (kprev > 0 && ar.rp && tc::reproject_ok(m, kprev) && tma_ok(Qbar, ldqb)) {
+            RQB_CK(tc::reproject(cx, Qbar, ldqb, m, kprev, ar.Y1, m, bp, *ar.rp));
+            done = true;
+        }
+    }
+    if (kprev > 0 && !done) {
         RQB_CK(gemm_tn_f64acc<T>(cx, m, (int)kprev, bp, Qbar, ldqb, ar.Y1, m, ar.Cd, kprev, ar.dpart,
                                  ar.dpart_cap, false));
         RQB_CK((launch_reduce_split<double, T>(cx, kprev, bp, 1, ar.Cd, kprev, 0, ar.Cc, kprev, nullptr, 0,
@@ -385,6 +418,9 @@ int factor_tc(rqb_handle h, const float* A, int64_t m, int64_t n, int64_t lda, d
     TcArena ta;
     rc = ensure_tc(h, m, n, bp, &ta);
     if (rc != RQB_OK) return rc;
+    tc::ReprojScratch rp;
+    if ((rc = ensure_reproj(h, m, kcap, bp, &rp)) != RQB_OK) return rc;
+    ar.rp = &rp;
     const int64_t ldq = round_up(m, 4), ldb = round_up(kcap, 4), ldw = round_up(m, 4);
     if ((rc = h->q.ensure(sizeof(float) * (size_t)ldq * (size_t)kcap)) != RQB_OK) return rc;
     if ((rc = h->b.ensure(sizeof(float) * (size_t)ldb * (size_t)n)) != RQB_OK) return rc;
@@ -550,6 +586,9 @@ int factor_bf16(rqb_handle h, const __nv_bfloat16* A, int64_t m, int64_t n, int6
     TcArena16 ta;
     rc = ensure_tc16(h, m, n, bp, &ta);
     if (rc != RQB_OK) return rc;
+    tc::ReprojScratch rp;
+    if ((rc = ensure_reproj(h, m, kcap, bp, &rp)) != RQB_OK) return rc;
+    ar.rp = &rp;
     const int64_t ldq = round_up(m, 4), ldb = round_up(kcap, 4), ldw = round_up(m, 8);
     if ((rc = h->q.ensure(sizeof(float) * (size_t)ldq * (size_t)kcap)) != RQB_OK) return rc;
     if ((rc = h->b.ensure(sizeof(float) * (size_t)ldb * (size_t)n)) != RQB_OK) return rc;
@@ -872,6 +911,7 @@ int rqb_destroy(rqb_handle h) {
     h->adj.release();
     h->tcbuf.release();
     h->svdbuf.release();
+    h->pcbuf.release();
     if (h->bat_out) cudaFree(h->bat_out);
     if (h->bat_work) cudaFree(h->bat_work);
     if (h->hstate) cudaFreeHost(h->hstate);
@@ -1007,6 +1047,12 @@ int orth_impl(rqb_handle h, const T* Y, int64_t m, int p, int64_t ldy, const T* 
     Arena<T> ar;
     int rc = ensure_arena<T>(h, m, 1, bp, kprev, &ar);
     if (rc != RQB_OK) return rc;
+    tc::ReprojScratch rp;
+    if (std::is_same<T, float>::value && (h->cfg.prec == RQB_PREC_TF32X3 || h->cfg.dtype == RQB_BF16) &&
+        tc::reproject_ok(m, kprev)) {
+        if ((rc = ensure_reproj(h, m, kprev, bp, &rp)) != RQB_OK) return rc;
+        ar.rp = &rp;
+    }
     Scal sc = scalars(h);
     Ctx cx;
     cx.stream = h->stream; cx.num_sms = h->num_sms; cx.st = sc.st;

@@ -661,6 +661,7 @@ __global__ void k_split_q(const float* __restrict__ Qi, long long ldq, long long
         }
         tile[i][tx] = v;
     }
+    if (Qt == nullptr) return;     // column-major copies only
     __syncthreads();
     for (int i = ty; i < 32; i += 8) {
         const long long r = r0 + i;
@@ -670,6 +671,25 @@ __global__ void k_split_q(const float* __restrict__ Qi, long long ldq, long long
             Qt[r * bp + c] = v;
             Qtl[r * bp + c] = tf32_lo(v);
         }
+    }
+}
+
+// Omega-layout copy of the re-projection coefficients: Om[j + c ldo] =
+// rna_tf32(Ct[c + j ldc]) for j < kprev, c < np (Ct is C^T, np x kprev).
+__global__ void k_ct_to_omega(const float* __restrict__ Ct, long long ldc, long long kprev, int np,
+                              float* __restrict__ Om, long long ldo) {
+    __shared__ float tile[32][33];
+    const long long j0 = (long long)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int i = ty; i < 32; i += 8) {
+        const long long j = j0 + i;
+        if (j < kprev) tile[i][tx] = Ct[(c0 + tx) + j * ldc];
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        const long long j = j0 + tx;
+        if (j < kprev) Om[j + (long long)(c0 + i) * ldo] = tf32_rna(tile[tx][i]);
     }
 }
 
@@ -711,12 +731,12 @@ __device__ __forceinline__ int tile_slots(long long U, int C, int P, int G, int 
 }
 
 // Y[r + c ldy] (r < m, c < np) = sum over the CTAs covering tile r / 128 of
-// their partials, in CTA order (FP32, at most a few terms, round to nearest).
-// One CTA per tile.
+// their partials, in CTA order (FP32, at most a few terms, round to nearest);
+// with sub, Y = sub - that sum (sub may alias Y).  One CTA per tile.
 constexpr int kReduceSlices = 8;   // CTAs per tile in the reductions
 
 __global__ void k_reduce_sketch(const float* __restrict__ part, long long U, int C, int P, int G, int np, long long m,
-                                float* __restrict__ Y, long long ldy) {
+                                float* Y, long long ldy, const float* sub) {
     __shared__ size_t off[kMaxCover];
     __shared__ int count;
     const int t = blockIdx.x;
@@ -732,7 +752,7 @@ __global__ void k_reduce_sketch(const float* __restrict__ part, long long U, int
         if (r >= m) continue;
         float acc = 0.f;
         for (int q = 0; q < nc; ++q) acc += part[off[q] + idx];
-        Y[r + c * ldy] = acc;
+        Y[r + c * ldy] = sub ? sub[r + c * ldy] - acc : acc;
     }
 }
 
@@ -1257,7 +1277,28 @@ cudaError_t sketch(Ctx& cx, const float* X, long long ldx, long long m, long lon
     if ((e = launch_streamk<kSketch>(cx, p, np)) != cudaSuccess) return e;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_reduce_sketch<<<dim3(pl.tiles, kReduceSlices), 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, m, Y,
-                                                                           ldy);
+                                                                           ldy, nullptr);
+    cx.launches++;
+    return cudaGetLastError();
+}
+
+// Y = sub - X Omega (sub may alias Y), otherwise as sketch().
+cudaError_t sketch_sub(Ctx& cx, const float* X, long long ldx, long long m, long long n, const float* Om,
+                       long long ldom, int np, float* Y, long long ldy, const float* sub, float* part,
+                       size_t part_cap) {
+    StreamKParams p;
+    cudaError_t e;
+    if ((e = make_map(&p.mx, X, m, n, ldx, kBM, kKC, false)) != cudaSuccess) return e;
+    if ((e = make_map(&p.mw, Om, n, np, ldom, kKC, np, true)) != cudaSuccess) return e;
+    p.mwl = p.mw;
+    const Plan pl = plan((m + kBM - 1) / kBM, (n + kKC - 1) / kKC, cx.num_sms);
+    if ((size_t)pl.P * pl.G * kBM * np > part_cap) return cudaErrorInvalidValue;
+    p.part = part;
+    p.st = cx.st;
+    p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
+    if ((e = launch_streamk<kSketch>(cx, p, np)) != cudaSuccess) return e;
+    k_reduce_sketch<<<dim3(pl.tiles, kReduceSlices), 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, m, Y,
+                                                                           ldy, sub);
     cx.launches++;
     return cudaGetLastError();
 }
@@ -1369,7 +1410,7 @@ cudaError_t sketch16(Ctx& cx, const __nv_bfloat16* X, long long ldx, long long m
     p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
     if ((e = launch_streamk16<kSketch>(cx, p, np)) != cudaSuccess) return e;
     k_reduce_sketch<<<dim3(pl.tiles, kReduceSlices), 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, m, Y,
-                                                                           ldy);
+                                                                           ldy, nullptr);
     cx.launches++;
     return cudaGetLastError();
 }
@@ -1422,6 +1463,30 @@ cudaError_t update16(Ctx& cx, const __nv_bfloat16* Wsrc, long long ldws, __nv_bf
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return sq_out ? launch_sum_doubles(cx, sq_part, grid, sq_out) : cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Line (3'): Y <- Y - Qbar (Qbar^T Y) with the split-TF32 products.
+bool reproject_ok(long long m, long long kprev) { return m >= 128 && kprev >= 128; }
+
+cudaError_t reproject(Ctx& cx, const float* Qbar, long long ldq, long long m, long long kprev, float* Y,
+                      long long ldy, int np, const ReprojScratch& w) {
+    cudaError_t e;
+    // C^T = Y^T Qbar (np x kprev): the projection kernel with X = Qbar and Y in
+    // the place of Q_i
+    dim3 g1((unsigned)((m + 31) / 32), (unsigned)(np / 32));
+    k_split_q<<<g1, 256, 0, cx.stream>>>(Y, ldy, m, np, np, w.Yhi, w.Ylo, w.ldyl, nullptr, nullptr);
+    cx.launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = project(cx, Qbar, ldq, m, kprev, w.Yhi, w.Ylo, w.ldyl, np, np, w.Ct, np, w.Bs, w.Bsl, w.part,
+                     w.part_cap, w.sq_part, w.sq_cap, w.sq_out)) != cudaSuccess)
+        return e;
+    // C in the sketch's Omega layout (rounded to TF32), then Y -= Qbar C
+    dim3 g2((unsigned)((kprev + 31) / 32), (unsigned)(np / 32));
+    k_ct_to_omega<<<g2, 256, 0, cx.stream>>>(w.Ct, np, kprev, np, w.Om, w.ldom);
+    cx.launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return sketch_sub(cx, Qbar, ldq, m, kprev, w.Om, w.ldom, np, Y, ldy, Y, w.part, w.part_cap);
 }
 
 }  // namespace tc

@@ -51,6 +51,32 @@ cudaError_t update(Ctx& cx, const float* Wsrc, long long ldws, float* Wdst, long
                    long long n, const float* Qt, const float* Qtl, const float* Bs, const float* Bsl, int np,
                    double* sq_part, int sq_cap, double* sq_out);
 
+// Workspace of reproject (FP32): Y's split (m x np, ld ldyl), C^T (np x kprev),
+// C in Omega layout (kprev x np, ld ldom), staging Bs / Bsl (np x kprev),
+// stream-K partials, FP64 norm partials.
+struct ReprojScratch {
+    float* Yhi;
+    float* Ylo;
+    long long ldyl;
+    float* Ct;
+    float* Om;
+    long long ldom;
+    float* Bs;
+    float* Bsl;
+    float* part;
+    size_t part_cap;
+    double* sq_part;
+    int sq_cap;
+    double* sq_out;
+};
+
+// Line (3') on the tensor core: Y (m x np) <- Y - Qbar (Qbar^T Y), Qbar
+// m x kprev (ld ldq), both products split-TF32 (C rounded to TF32 for the
+// second); needs reproject_ok(m, kprev).
+bool reproject_ok(long long m, long long kprev);
+cudaError_t reproject(Ctx& cx, const float* Qbar, long long ldq, long long m, long long kprev, float* Y,
+                      long long ldy, int np, const ReprojScratch& w);
+
 // ---------------------------------------------------------------------------
 // BF16 storage path (A and the residual W in BF16; kind::f16 MMAs with FP32
 // accumulation).  np is 64, 128 or 256; BF16 tensor-map sources need a

@@ -96,6 +96,22 @@ def test_downdate_sketch(orc, htc, m, n, p, ncols, inplace):
     assert abs(nw2 - np.sum(Wo * Wo)) <= 10 * TOL_STEP * np.sum(A * A)
 
 
+@pytest.mark.parametrize("m,p,kprev", [(4000, 128, 256), (3000, 256, 512), (1037, 37, 130), (4100, 64, 1000)])
+def test_orth_tensor_core_reprojection(orc, htc, m, p, kprev):
+    """kprev >= 128: line (3') runs on the tensor core (split-TF32 C = Qbar^T Y,
+    C rounded to TF32 for Y -= Qbar C); the panel stays orthonormal and
+    orthogonal to Qbar at the FP32 level and matches the oracle's Q_i."""
+    rng = np.random.default_rng(m + 2 * p + kprev)
+    Qbar = _f32(np.linalg.qr(rng.standard_normal((m, kprev)))[0])
+    Y = rng.standard_normal((m, p)) @ np.diag(np.logspace(0, -2, p))
+    Y = _f32(Y - (1 - 1e-3) * Qbar @ (Qbar.T @ Y))     # mostly, not exactly, orthogonal to Qbar
+    Qi = to_np(htc.rqb_orth(to_dev(Y, torch.float32), to_dev(Qbar, torch.float32)))
+    Qo = orc.orth_reproject(Y, Qbar)
+    assert orth_err(Qi) <= 1e-5
+    assert np.abs(Qbar.T @ Qi).max() <= 1e-5
+    assert np.abs(Qi - Qo).max() <= 1e-3
+
+
 def _factor(rqb, A, eps, b, seed, **kw):
     with rqb.Handle(torch.float32, prec=rqb.RQB_PREC_TF32X3, **kw) as h:
         Q, B, k, rc = h.rqb_factor(to_dev(A, torch.float32), eps, b, seed, check=False)

@@ -257,8 +257,9 @@ int ensure_reproj(rqb_handle h, int64_t m, int64_t kcap, int bp, tc::ReprojScrat
     size_t off = 0;
     auto take = [&](size_t floats) { size_t o = off; off = align256(off + 4 * floats); return o; };
     const size_t oYh = take((size_t)ldyl * bp), oYl = take((size_t)ldyl * bp);
+    const size_t kb = (size_t)std::max<int64_t>(kcap, bp);
     const size_t oCt = take((size_t)bp * kcap), oOm = take((size_t)ldom * bp);
-    const size_t oBs = take((size_t)bp * kcap), oBsl = take((size_t)bp * kcap);
+    const size_t oBs = take((size_t)bp * kb), oBsl = take((size_t)bp * kb);
     const size_t oP = take(part);
     int rc = h->pcbuf.ensure(off);
     if (rc != RQB_OK) return rc;
@@ -308,9 +309,16 @@ template <typename T>
 int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_t ldy, int64_t m, int p, int bp,
                    const T* Qbar, int64_t kprev, int64_t ldqb, T* Qout, int64_t ldqo) {
     // pass 1: CholeskyQR of Y, Y1 = Y R^{-1}
-    RQB_CK(gemm_tn_f64acc<T>(cx, m, bp, bp, Y, ldy, Y, ldy, ar.G, bp, ar.dpart, ar.dpart_cap, true));
+    RQB_CK(gemm_tn_f64acc<T>(cx, m, bp, bp, Y, ldy, Y, ldy, ar.G, bp, ar.dpart, ar.dpart_cap, true, true));
     RQB_CK(chol_inv<T>(cx, ar.G, bp, p, ar.R, ar.Rinv, true, ar.dpart, ar.dpart_cap));
-    {
+    bool tc1 = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if (ar.rp && m <= ar.rp->ldyl && tc::product_ok(m, bp, m, ar.Y1)) {
+            RQB_CK(tc::product(cx, Y, ldy, m, ar.Rinv, bp, bp, ar.Y1, m, *ar.rp));
+            tc1 = true;
+        }
+    }
+    if (!tc1) {
         NNArgs<T> a;
         a.m = m; a.K = bp; a.nc = bp; a.nout = bp;
         a.X = Y; a.ldx = ldy;
@@ -321,7 +329,7 @@ int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_
     // line (3'): Y1 -= Qbar (Qbar^T Y1)
     bool done = false;
     if constexpr (std::is_same<T, float>::value) {
-        if (kprev > 0 && ar.rp && tc::reproject_ok(m, kprev) && tma_ok(Qbar, ldqb)) {
+        if (kprev > 0 && ar.rp && m <= ar.rp->ldyl && tc::reproject_ok(m, kprev) && tma_ok(Qbar, ldqb)) {
             RQB_CK(tc::reproject(cx, Qbar, ldqb, m, kprev, ar.Y1, m, bp, *ar.rp));
             done = true;
         }
@@ -341,9 +349,17 @@ int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_
         RQB_CK(gemm_nn<T>(cx, a));
     }
     // pass 2: CholeskyQR of Y1, Qout = Y1 R^{-1}
-    RQB_CK(gemm_tn_f64acc<T>(cx, m, bp, bp, ar.Y1, m, ar.Y1, m, ar.G, bp, ar.dpart, ar.dpart_cap, false));
+    RQB_CK(gemm_tn_f64acc<T>(cx, m, bp, bp, ar.Y1, m, ar.Y1, m, ar.G, bp, ar.dpart, ar.dpart_cap, false, true));
     RQB_CK(chol_inv<T>(cx, ar.G, bp, p, ar.R, ar.Rinv, sizeof(T) == 8, ar.dpart, ar.dpart_cap));
-    {
+    bool tc2 = false;
+    if constexpr (std::is_same<T, float>::value) {
+        // full-width panels only: the product writes all bp columns
+        if (ar.rp && m <= ar.rp->ldyl && p == bp && tc::product_ok(m, bp, ldqo, Qout)) {
+            RQB_CK(tc::product(cx, ar.Y1, m, m, ar.Rinv, bp, bp, Qout, ldqo, *ar.rp));
+            tc2 = true;
+        }
+    }
+    if (!tc2) {
         NNArgs<T> a;
         a.m = m; a.K = bp; a.nc = bp; a.nout = p;
         a.X = ar.Y1; a.ldx = m;
@@ -419,7 +435,7 @@ int factor_tc(rqb_handle h, const float* A, int64_t m, int64_t n, int64_t lda, d
     rc = ensure_tc(h, m, n, bp, &ta);
     if (rc != RQB_OK) return rc;
     tc::ReprojScratch rp;
-    if ((rc = ensure_reproj(h, m, kcap, bp, &rp)) != RQB_OK) return rc;
+    if ((rc = ensure_reproj(h, h->cfg.power > 0 ? std::max(m, n) : m, kcap, bp, &rp)) != RQB_OK) return rc;
     ar.rp = &rp;
     const int64_t ldq = round_up(m, 4), ldb = round_up(kcap, 4), ldw = round_up(m, 4);
     if ((rc = h->q.ensure(sizeof(float) * (size_t)ldq * (size_t)kcap)) != RQB_OK) return rc;
@@ -587,7 +603,7 @@ int factor_bf16(rqb_handle h, const __nv_bfloat16* A, int64_t m, int64_t n, int6
     rc = ensure_tc16(h, m, n, bp, &ta);
     if (rc != RQB_OK) return rc;
     tc::ReprojScratch rp;
-    if ((rc = ensure_reproj(h, m, kcap, bp, &rp)) != RQB_OK) return rc;
+    if ((rc = ensure_reproj(h, h->cfg.power > 0 ? std::max(m, n) : m, kcap, bp, &rp)) != RQB_OK) return rc;
     ar.rp = &rp;
     const int64_t ldq = round_up(m, 4), ldb = round_up(kcap, 4), ldw = round_up(m, 8);
     if ((rc = h->q.ensure(sizeof(float) * (size_t)ldq * (size_t)kcap)) != RQB_OK) return rc;
@@ -1183,11 +1199,25 @@ int dd_tc(rqb_handle h, const float* A, int64_t lda, const float* Qi, int64_t ld
     RQB_CK(cudaMemsetAsync(sc.st, 0, sizeof(DevState), h->stream));
     RQB_CK(tc::split_q(cx, Qi, ldqi, m, p, bpu, ta.Qhi, ta.Qlo, ta.ldql, ta.Qt, ta.Qtl));
     RQB_CK(tc::stage_b(cx, Bi, ldbi, p, n, bpu, ta.Bs, ta.Bsl));
-    RQB_CK(tc::update(cx, A, lda, W, ldw, m, n, ta.Qt, ta.Qtl, ta.Bs, ta.Bsl, bpu, sc.nrm, kNrmCap,
+    // the update reads and writes W through TMA: unaligned operands go
+    // through aligned copies (A into the handle's W buffer, the result into
+    // the adjoint workspace, copied out afterwards)
+    const float* Ax;
+    int64_t ldax;
+    if ((rc = tma_source(h, A, lda, m, n, &Ax, &ldax)) != RQB_OK) return rc;
+    float* X = W;
+    int64_t ldx = ldw;
+    const bool copy_out = !tma_ok(W, ldw);
+    if (copy_out) {
+        ldx = round_up(m, 4);
+        if ((rc = h->adj.ensure(sizeof(float) * (size_t)ldx * (size_t)n)) != RQB_OK) return rc;
+        X = reinterpret_cast<float*>(h->adj.p);
+    }
+    RQB_CK(tc::update(cx, Ax, ldax, X, ldx, m, n, ta.Qt, ta.Qtl, ta.Bs, ta.Bsl, bpu, sc.nrm, kNrmCap,
                       normW2 ? sc.s + 2 : nullptr));
-    const float* X;
-    int64_t ldx;
-    if ((rc = tma_source(h, W, ldw, m, n, &X, &ldx)) != RQB_OK) return rc;
+    if (copy_out)
+        RQB_CK(cudaMemcpy2DAsync(W, sizeof(float) * ldw, X, sizeof(float) * ldx, sizeof(float) * m, n,
+                                 cudaMemcpyDeviceToDevice, h->stream));
     RQB_CK(tc::omega(cx, n, col0, ncols, bps, seed, ta.Om, ta.ldom));
     RQB_CK(tc::sketch(cx, X, ldx, m, n, ta.Om, ta.ldom, bps, ar.Y, m, ta.part, ta.part_cap));
     RQB_CK(cudaMemcpy2DAsync(Y, sizeof(float) * ldy, ar.Y, sizeof(float) * m, sizeof(float) * m, ncols,

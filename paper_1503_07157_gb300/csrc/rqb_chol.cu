@@ -6,13 +6,15 @@
 // n^3/3 = 5.6 M FP64 multiply-adds, which one SM (two FP64 FMAs per clock on
 // this part) needs about 1.4 ms for.  Here the factorization G = L L^T is
 // blocked in 32 x 32 tiles and spread over many CTAs:
-//   panel k   every CTA factors the diagonal tile G_kk and inverts L_kk in
-//             shared memory; CTA 0 stores L_kk, the others the 8-row strips
-//             of L_ik = G_ik L_kk^{-T} below it
+//   panel k   every CTA factors the diagonal tile G_kk and inverts L_kk (FP32:
+//             one warp, rows in registers and shuffles; FP64: the whole CTA
+//             on the tile in shared memory, which keeps all four FP64 pipes
+//             of the SM busy); CTA 0 stores L_kk and L_kk^{-1}, the others the
+//             8-row strips of L_ik = G_ik L_kk^{-T} below it
 //   update k  G_ij -= L_ik L_jk^T for every tile k < j <= i, one CTA per
 //             8-row strip
-// R = L^T in FP64; R^{-1} is formed in the output type from R staged
-// (packed) in shared memory, one warp per column.
+// R = L^T in FP64.  Each panel also keeps L_kk^{-1}, from which R^{-1} =
+// (L^{-1})^T is formed by block forward substitution in the output type.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,56 +41,135 @@ __global__ void k_chol_init(double* __restrict__ G, int bp, int p, double* __res
     }
 }
 
+// 1 / sqrt(d) for d > 0 in FP64: the FP32 estimate refined by three Newton
+// steps y <- y (3 - d y^2) / 2 (each squares the relative error: 2^-23 ->
+// 2^-45 -> 2^-89), so the pivot's serial chain costs a few dependent FP64
+// multiply-adds instead of an FP64 square root and division.  Pivots outside
+// the FP32 range take the FP64 library route.
+__device__ __forceinline__ double rsqrt_fp64(double d) {
+    if (!(d > 1e-36 && d < 1e36)) return 1.0 / sqrt(d);
+    double y = (double)rsqrtf((float)d);
+    const double h = 0.5 * d;
+#pragma unroll
+    for (int it = 0; it < 3; ++it) y = y * fma(-h, y * y, 1.5);
+    return y;
+}
+
+// Factor the 32 x 32 diagonal tile in one warp: lane i holds row i of D
+// (-> L_kk) and of the identity (-> L_kk^{-1}) in registers; step j takes the
+// pivot from lane j, scales column j, and applies the rank-1 update to the
+// trailing rows and the elimination to the rows of L^{-1} with values
+// broadcast by shuffles (fully unrolled, so the rows stay in registers).
 template <typename W>
-__global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G, double* __restrict__ L, int bp,
-                                                    int k, const double* __restrict__ dG, double tol,
-                                                    DevState* st) {
-    __shared__ W D[kNb][kNb + 1];    // G_kk -> L_kk (lower)
-    __shared__ W Di[kNb][kNb + 1];   // I -> L_kk^{-1} (lower)
+__device__ __forceinline__ bool warp_chol32(W (&d)[kNb], W (&di)[kNb], int lane, const double* __restrict__ dG,
+                                            int k0, double tol) {
+    bool fail = false;
+#pragma unroll 32
+    for (int j = 0; j < kNb; ++j) {
+        W piv = __shfl_sync(0xffffffffu, d[j], j);
+        if (!((double)piv > tol * dG[k0 + j]) || !isfinite((double)piv)) {
+            fail = true;
+            piv = W(1);
+        }
+        const W inv = W(1) / sqrt(piv);
+        const bool me = (lane == j), below = (lane > j);
+        d[j] = me ? piv * inv : (below ? d[j] * inv : d[j]);
+#pragma unroll 32
+        for (int t = 0; t < kNb; ++t)
+            if (t <= j) di[t] = me ? di[t] * inv : di[t];
+        const W lij = below ? d[j] : W(0);   // L[lane][j]
+#pragma unroll 32
+        for (int c = 0; c < kNb; ++c) {
+            if (c > j) {
+                const W lcj = __shfl_sync(0xffffffffu, d[j], c);
+                d[c] = (lane >= c) ? d[c] - lij * lcj : d[c];
+            }
+        }
+#pragma unroll 32
+        for (int t = 0; t < kNb; ++t) {
+            if (t <= j) {
+                const W xjt = __shfl_sync(0xffffffffu, di[t], j);
+                di[t] = below ? di[t] - lij * xjt : di[t];
+            }
+        }
+    }
+    return fail;
+}
+
+template <typename W>
+__global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G, double* __restrict__ L,
+                                                    double* __restrict__ Linv, int bp, int k,
+                                                    const double* __restrict__ dG, double tol, DevState* st) {
+    __shared__ W D[kNb][kNb + 1];    // L_kk (lower)
+    __shared__ W Di[kNb][kNb + 1];   // L_kk^{-1} (lower)
     __shared__ W inv[kNb];
     __shared__ int fail;
     const int tid = threadIdx.x;
     const int k0 = k * kNb;
-    for (int e = tid; e < kNb * kNb; e += 256) {
-        const int r = e & (kNb - 1), c = e / kNb;
-        D[r][c] = (r >= c) ? (W)G[(k0 + r) + (int64_t)(k0 + c) * bp] : W(0);
-        Di[r][c] = (r == c) ? W(1) : W(0);
-    }
-    if (tid == 0) fail = 0;
-    __syncthreads();
-    // step j: pivot; scale column j of L and row j of L^{-1} by 1 / l_jj;
-    // update the trailing part of L and eliminate column j from the rows of
-    // L^{-1} below j (forward substitution applied to all columns at once)
-    for (int j = 0; j < kNb; ++j) {
-        if (tid == 0) {
-            W d = D[j][j];
-            if (!((double)d > tol * dG[k0 + j]) || !isfinite((double)d)) {
-                fail = 1;
-                d = W(1);
+    if constexpr (sizeof(W) == 4) {
+        // FP32: one warp, rows in registers
+        if (tid < 32) {
+            W d[kNb], di[kNb];
+#pragma unroll
+            for (int c = 0; c < kNb; ++c) {
+                d[c] = (tid >= c) ? (W)G[(k0 + tid) + (int64_t)(k0 + c) * bp] : W(0);
+                di[c] = (tid == c) ? W(1) : W(0);
             }
-            const W l = sqrt(d);
-            D[j][j] = l;
-            inv[j] = W(1) / l;
+            const bool f = warp_chol32<W>(d, di, tid, dG, k0, tol);
+#pragma unroll
+            for (int c = 0; c < kNb; ++c) {
+                D[tid][c] = (tid >= c) ? d[c] : W(0);
+                Di[tid][c] = (tid >= c) ? di[c] : W(0);
+            }
+            if (tid == 0) fail = f ? 1 : 0;
         }
         __syncthreads();
-        const W ij = inv[j];
-        if (tid < kNb) {
-            if (tid > j) D[tid][j] *= ij;
-        } else if (tid < 2 * kNb) {
-            if (tid - kNb <= j) Di[j][tid - kNb] *= ij;
-        }
-        __syncthreads();
+    } else {
+        // FP64: the FP64 pipes of all four SM sub-partitions, tile in shared
+        // memory; step j pivots, scales column j of L and row j of L^{-1},
+        // updates the trailing part of L and eliminates column j from the rows
+        // of L^{-1} below j
         for (int e = tid; e < kNb * kNb; e += 256) {
             const int r = e & (kNb - 1), c = e / kNb;
-            if (c > j && r >= c) D[r][c] -= D[r][j] * D[c][j];
-            else if (r > j && c <= j) Di[r][c] -= D[r][j] * Di[j][c];
+            D[r][c] = (r >= c) ? (W)G[(k0 + r) + (int64_t)(k0 + c) * bp] : W(0);
+            Di[r][c] = (r == c) ? W(1) : W(0);
         }
+        if (tid == 0) fail = 0;
         __syncthreads();
+        for (int j = 0; j < kNb; ++j) {
+            if (tid == 0) {
+                W d = D[j][j];
+                if (!((double)d > tol * dG[k0 + j]) || !isfinite((double)d)) {
+                    fail = 1;
+                    d = W(1);
+                }
+                const W y = rsqrt_fp64(d);
+                D[j][j] = d * y;
+                inv[j] = y;
+            }
+            __syncthreads();
+            const W ij = inv[j];
+            if (tid < kNb) {
+                if (tid > j) D[tid][j] *= ij;
+            } else if (tid < 2 * kNb) {
+                if (tid - kNb <= j) Di[j][tid - kNb] *= ij;
+            }
+            __syncthreads();
+            for (int e = tid; e < kNb * kNb; e += 256) {
+                const int r = e & (kNb - 1), c = e / kNb;
+                if (c > j && r >= c) D[r][c] -= D[r][j] * D[c][j];
+                else if (r > j && c <= j) Di[r][c] -= D[r][j] * Di[j][c];
+            }
+            __syncthreads();
+        }
     }
     if (blockIdx.x == 0) {
         for (int e = tid; e < kNb * kNb; e += 256) {
             const int r = e & (kNb - 1), c = e / kNb;
-            if (r >= c) L[(k0 + r) + (int64_t)(k0 + c) * bp] = (double)D[r][c];
+            if (r >= c) {
+                L[(k0 + r) + (int64_t)(k0 + c) * bp] = (double)D[r][c];
+                Linv[(k0 + r) + (int64_t)(k0 + c) * bp] = (double)Di[r][c];
+            }
         }
         if (tid == 0 && fail) record_error(st, RQB_ERR_BREAKDOWN);
         return;
@@ -174,6 +255,70 @@ __global__ void __launch_bounds__(256) k_upper_inverse(const double* __restrict_
     for (int r = lane; r < bp; r += 32) Rinv[c + (int64_t)r * bp] = (T)((r >= c) ? x[r] : W(0));
 }
 
+// Rinv = R^{-1} = (L^{-1})^T from the tiles of L and the inverses of its
+// diagonal tiles (written by the panels): CTA j forms column block j of
+// X = L^{-1} down the block rows, X_jj = L_jj^{-1} and
+// X_ij = -L_ii^{-1} sum_{j <= t < i} L_it X_tj (block forward substitution),
+// in working type W with the block row of L staged in shared memory, and
+// stores it transposed.
+template <typename T, typename W>
+__global__ void __launch_bounds__(256) k_linv_blocked(const double* __restrict__ L, const double* __restrict__ Linv,
+                                                      int bp, T* __restrict__ Rinv) {
+    extern __shared__ __align__(16) unsigned char linv_smem[];
+    W* X = reinterpret_cast<W*>(linv_smem);          // bp x 32, column block j of L^{-1}, ld bp
+    W* Lr = X + (size_t)bp * kNb;                     // 32 x bp block row of L, ld 33 (row-padded)
+    W* S = Lr + (size_t)bp * (kNb + 1);               // 32 x 32 partial sum, ld 33
+    W* Di = S + (size_t)kNb * (kNb + 1);              // 32 x 32 L_ii^{-1}, ld 33
+    const int j = blockIdx.x, nblk = bp / kNb;
+    const int tid = threadIdx.x;
+    const int j0 = j * kNb;
+    for (int e = tid; e < bp * kNb; e += 256) {
+        const int r = e % bp, c = e / bp;
+        X[r + (size_t)c * bp] = (r >= j0 && r < j0 + kNb && r - j0 >= c) ? (W)Linv[r + (int64_t)(j0 + c) * bp] : W(0);
+    }
+    const int r = tid & 31, cg = tid >> 5;    // output row r, columns cg + 8 q
+    for (int i = j + 1; i < nblk; ++i) {
+        const int i0 = i * kNb, len = i0 - j0;
+        __syncthreads();     // X rows of block i-1 complete; Lr, Di free
+        for (int e = tid; e < kNb * len; e += 256) {
+            const int rr = e & (kNb - 1), t = e >> 5;
+            Lr[t * (kNb + 1) + rr] = (W)L[(i0 + rr) + (int64_t)(j0 + t) * bp];
+        }
+        for (int e = tid; e < kNb * kNb; e += 256) {
+            const int rr = e & (kNb - 1), t = e >> 5;
+            Di[t * (kNb + 1) + rr] = (W)Linv[(i0 + rr) + (int64_t)(i0 + t) * bp];
+        }
+        __syncthreads();
+        W acc[4] = {W(0), W(0), W(0), W(0)};
+        for (int t0 = 0; t0 < len; t0 += kNb) {
+#pragma unroll 8
+            for (int t = t0; t < t0 + kNb; ++t) {
+                const W l = Lr[t * (kNb + 1) + r];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[q] += l * X[(j0 + t) + (size_t)(cg + 8 * q) * bp];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) S[r + (cg + 8 * q) * (kNb + 1)] = acc[q];
+        __syncthreads();
+        W out[4] = {W(0), W(0), W(0), W(0)};
+#pragma unroll 8
+        for (int t = 0; t < kNb; ++t) {
+            const W dv = (t <= r) ? Di[t * (kNb + 1) + r] : W(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) out[q] += dv * S[t + (cg + 8 * q) * (kNb + 1)];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) X[(i0 + r) + (size_t)(cg + 8 * q) * bp] = -out[q];
+    }
+    __syncthreads();
+    // Rinv(c, r) = X(r, c): row j0 + c of Rinv, columns r >= j0
+    for (int e = tid; e < bp * kNb; e += 256) {
+        const int c = e % kNb, rr = e / kNb;
+        Rinv[(j0 + c) + (int64_t)rr * bp] = (T)X[rr + (size_t)c * bp];
+    }
+}
+
 }  // namespace
 
 // Rinv (T) = R^{-1} for an upper-triangular FP64 R (bp x bp, column-major);
@@ -194,24 +339,28 @@ cudaError_t upper_inverse(Ctx& cx, const double* R, int bp, T* Rinv) {
 }
 
 // G (bp x bp, FP64, overwritten) = R^T R; R (FP64) and Rinv (T).  scratch:
-// bp * bp + bp doubles (L and the diagonal of G).  fp64: working precision
-// of the factorization (FP32 serves the second CholeskyQR pass, whose Gram
-// is I + O(u kappa)); the factors are stored in FP64 either way.
+// 2 bp^2 + bp doubles (L, the inverses of its diagonal tiles, and the
+// diagonal of G).  fp64: working precision of the factorization (FP32 serves
+// the second CholeskyQR pass, whose Gram is I + O(u kappa)); the factors are
+// stored in FP64 either way; R^{-1} is formed in T.
 template <typename T>
 cudaError_t chol_inv_blocked(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, double tol, double* scratch,
                              size_t scratch_doubles, bool fp64) {
-    if (bp % kNb != 0 || scratch_doubles < (size_t)bp * bp + bp) return cudaErrorInvalidValue;
+    if (bp % kNb != 0 || scratch_doubles < 2 * (size_t)bp * bp + bp) return cudaErrorInvalidValue;
     double* L = scratch;
-    double* dG = scratch + (size_t)bp * bp;
+    double* Linv = scratch + (size_t)bp * bp;
+    double* dG = Linv + (size_t)bp * bp;
     const int nblk = bp / kNb;
     k_chol_init<<<std::max(1, bp * bp / 256), 256, 0, cx.stream>>>(G, bp, p, dG, L);
     cx.launches++;
     for (int k = 0; k < nblk; ++k) {
         const int below = nblk - k - 1;
         if (fp64)
-            k_chol_panel<double><<<1 + below * (kNb / kStrip), 256, 0, cx.stream>>>(G, L, bp, k, dG, tol, cx.st);
+            k_chol_panel<double><<<1 + below * (kNb / kStrip), 256, 0, cx.stream>>>(G, L, Linv, bp, k, dG, tol,
+                                                                                    cx.st);
         else
-            k_chol_panel<float><<<1 + below * (kNb / kStrip), 256, 0, cx.stream>>>(G, L, bp, k, dG, tol, cx.st);
+            k_chol_panel<float><<<1 + below * (kNb / kStrip), 256, 0, cx.stream>>>(G, L, Linv, bp, k, dG, tol,
+                                                                                   cx.st);
         cx.launches++;
         if (below > 0) {
             const int pairs = below * (below + 1) / 2;
@@ -224,9 +373,16 @@ cudaError_t chol_inv_blocked(Ctx& cx, double* G, int bp, int p, double* R, T* Ri
     }
     k_chol_transpose<<<std::max(1, bp * bp / 256), 256, 0, cx.stream>>>(L, bp, R);
     cx.launches++;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return upper_inverse<T>(cx, R, bp, Rinv);
+    using Wi = T;
+    const size_t smem = sizeof(Wi) * ((size_t)bp * kNb + (size_t)bp * (kNb + 1) + 2 * (size_t)kNb * (kNb + 1));
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_linv_blocked<T, Wi>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    k_linv_blocked<T, Wi><<<nblk, 256, smem, cx.stream>>>(L, Linv, bp, Rinv);
+    cx.launches++;
+    return cudaGetLastError();
 }
 
 template cudaError_t upper_inverse<float>(Ctx&, const double*, int, float*);

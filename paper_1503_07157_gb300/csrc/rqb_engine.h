@@ -50,7 +50,7 @@ template <typename TP, typename TO>
 cudaError_t launch_reduce_split(Ctx& cx, int64_t rows, int64_t cols, int splits, const TP* part, int64_t ldp,
                                 int64_t zstride, TO* out, int64_t ldo, double* sq_part, int sq_cap,
                                 double* sq_out, double alpha = 1.0, double beta = 0.0, const TO* Yin = nullptr,
-                                int64_t ldyin = 0);
+                                int64_t ldyin = 0, int sym = 0);
 template <typename T>
 cudaError_t gemm_nn(Ctx& cx, const NNArgs<T>& a);
 template <typename T>
@@ -60,7 +60,7 @@ cudaError_t gemm_tn(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, int64_t 
 template <typename T>
 cudaError_t gemm_tn_f64acc(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, int64_t ldx, const T* Y,
                            int64_t ldy, double* Out, int64_t ldo, double* part, size_t part_cap_elems,
-                           bool exact);
+                           bool exact, bool sym = false);
 template <typename T>
 cudaError_t chol_inv(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, bool fp64_factor, double* scratch,
                      size_t scratch_doubles);

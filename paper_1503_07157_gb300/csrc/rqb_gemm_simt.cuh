@@ -287,7 +287,10 @@ __global__ void __launch_bounds__((BP / TP) * (BQ / TQ), ((BP / TP) * (BQ / TQ) 
 k_gemm_tn(int64_t m, int pn, int64_t qn, int64_t rsplit,
           const T* __restrict__ X, int64_t ldx,
           const T* __restrict__ Y, int64_t ldy,
-          Acc* __restrict__ Out, int64_t ldo, int64_t out_zstride) {
+          Acc* __restrict__ Out, int64_t ldo, int64_t out_zstride, int sym) {
+    // sym (X = Y, a Gram matrix): tiles strictly above the diagonal are left
+    // to the reduction, which reads their mirror image
+    if (sym && (int64_t)blockIdx.x * BP + BP <= (int64_t)blockIdx.y * BQ) return;
     constexpr int NT = (BP / TP) * (BQ / TQ);
     constexpr int V = Vec16<T>::N;
     constexpr int HP = TP / 2, HQ = TQ / 2;

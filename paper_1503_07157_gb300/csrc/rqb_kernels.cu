@@ -83,6 +83,38 @@ __global__ void __launch_bounds__(256) k_sumsq(int64_t m, int64_t n, const T* __
                 const double v = (double)col[r];
                 acc = fma(v, v, acc);
             }
+        } else if (sizeof(T) == 2 && (ldx & 7) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+            // BF16 with 16-byte aligned columns: eight values per lane and
+            // load; a BF16 square is exact in FP32, summed with TwoSum
+            const int64_t m8 = m & ~(int64_t)7;
+            for (int64_t r0 = 0; r0 < m; r0 += 32 * 8 * 16) {
+                float hi = 0.f, lo = 0.f;
+                const int64_t r1 = r0 + 32 * 8 * 16 < m ? r0 + 32 * 8 * 16 : m;
+                for (int64_t r = r0 + 8 * lane; r < r1; r += 32 * 8) {
+                    float v[8];
+                    if (r + 8 <= m8) {
+                        const uint4 u = __ldcs(reinterpret_cast<const uint4*>(col + r));
+                        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            v[2 * i] = __uint_as_float(w[i] << 16);
+                            v[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) v[i] = (r + i < m) ? static_cast<float>(col[r + i]) : 0.f;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float p2 = __fmul_rn(v[i], v[i]);
+                        const float t = __fadd_rn(hi, p2);
+                        const float bp = __fsub_rn(t, hi);
+                        lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p2, bp)));
+                        hi = t;
+                    }
+                }
+                acc += (double)hi + (double)lo;
+            }
         } else {
             for (int64_t r0 = 0; r0 < m; r0 += 32 * 64) {
                 float hi = 0.f, lo = 0.f;
@@ -138,14 +170,16 @@ template <typename TP, typename TO>
 __global__ void __launch_bounds__(256)
 k_reduce_split(int64_t rows, int64_t cols, int splits, const TP* __restrict__ part, int64_t ldp,
                int64_t zstride, TO* out, int64_t ldo, double* __restrict__ sq_part, double alpha, double beta,
-               const TO* Yin, int64_t ldyin) {
+               const TO* Yin, int64_t ldyin, int sym) {
     __shared__ double sh[8];
     double sq = 0.0;
     const int64_t total = rows * cols;
     for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < total; e += (int64_t)gridDim.x * 256) {
         const int64_t r = e % rows, c = e / rows;
+        // sym: the upper triangle is the mirror of the lower one
+        const int64_t pe = (sym && r < c) ? c + r * ldp : r + c * ldp;
         double s = 0.0;
-        for (int z = 0; z < splits; ++z) s += (double)part[z * zstride + r + c * ldp];
+        for (int z = 0; z < splits; ++z) s += (double)part[z * zstride + pe];
         if (alpha != 1.0) s *= alpha;
         if (beta != 0.0) s += beta * (double)Yin[r + c * ldyin];
         const TO v = (TO)s;
@@ -161,11 +195,11 @@ k_reduce_split(int64_t rows, int64_t cols, int splits, const TP* __restrict__ pa
 template <typename TP, typename TO>
 cudaError_t launch_reduce_split(Ctx& cx, int64_t rows, int64_t cols, int splits, const TP* part, int64_t ldp,
                                 int64_t zstride, TO* out, int64_t ldo, double* sq_part, int sq_cap,
-                                double* sq_out, double alpha, double beta, const TO* Yin, int64_t ldyin) {
+                                double* sq_out, double alpha, double beta, const TO* Yin, int64_t ldyin, int sym) {
     int blocks = std::max<int64_t>(1, std::min<int64_t>((rows * cols + 255) / 256, (int64_t)cx.num_sms * 8));
     if (sq_part) blocks = std::min(blocks, sq_cap);
     k_reduce_split<TP, TO><<<blocks, 256, 0, cx.stream>>>(rows, cols, splits, part, ldp, zstride, out, ldo,
-                                                           sq_part, alpha, beta, Yin, ldyin);
+                                                           sq_part, alpha, beta, Yin, ldyin, sym);
     cx.launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !sq_part) return e;
@@ -626,7 +660,7 @@ cudaError_t gemm_nn(Ctx& cx, const NNArgs<T>& a) {
 template <typename T, typename Acc, int BP, int BQ, int BK, int TP, int TQ, int PROMOTE, bool COMP = false>
 static cudaError_t tn_launch(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, int64_t ldx, const T* Y,
                              int64_t ldy, Acc* part, size_t part_cap_elems, int max_splits, int* splits_out,
-                             int64_t kmin = 512) {
+                             int64_t kmin = 512, int sym = 0) {
     auto kern = k_gemm_tn<T, Acc, BP, BQ, BK, TP, TQ, PROMOTE, COMP>;
     constexpr int NT = (BP / TP) * (BQ / TQ);
     const int pt = (pn + BP - 1) / BP;
@@ -636,12 +670,14 @@ static cudaError_t tn_launch(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X,
     if ((size_t)per > part_cap_elems) return cudaErrorInvalidValue;
     int maxs = (int)std::min<int64_t>(max_splits, (int64_t)(part_cap_elems / (size_t)std::max<int64_t>(per, 1)));
     maxs = std::max(1, maxs);
-    int splits = choose_splits((int64_t)pt * qt, m, kmin, maxs, slots);
+    // tiles that do work (the lower triangle of tiles for a Gram)
+    const int64_t work_tiles = sym ? (int64_t)pt * (pt + 1) / 2 : (int64_t)pt * qt;
+    int splits = choose_splits(work_tiles, m, kmin, maxs, slots);
     int64_t rs = (m + splits - 1) / splits;
     rs = ((rs + BK - 1) / BK) * BK;
     splits = (int)std::max<int64_t>(1, (m + rs - 1) / rs);
     dim3 grid((unsigned)pt, (unsigned)qt, (unsigned)splits);
-    kern<<<grid, NT, 0, cx.stream>>>(m, pn, qn, rs, X, ldx, Y, ldy, part, pn, per);
+    kern<<<grid, NT, 0, cx.stream>>>(m, pn, qn, rs, X, ldx, Y, ldy, part, pn, per, sym);
     cx.launches++;
     *splits_out = splits;
     return cudaGetLastError();
@@ -669,25 +705,29 @@ cudaError_t gemm_tn(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, int64_t 
 }
 
 // Out (pn x qn, FP64, ld ldo) = X^T Y with FP64 accumulation across chunks.
+// sym: X and Y are the same matrix (a Gram matrix): only the lower triangle
+// of tiles is computed and the upper one mirrored.
 template <typename T>
 cudaError_t gemm_tn_f64acc(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, int64_t ldx, const T* Y,
-                           int64_t ldy, double* Out, int64_t ldo, double* part, size_t part_cap_elems, bool exact) {
+                           int64_t ldy, double* Out, int64_t ldo, double* part, size_t part_cap_elems, bool exact,
+                           bool sym) {
     int splits = 1;
     cudaError_t e;
+    const int sy = (sym && X == Y && ldx == ldy && pn == qn) ? 1 : 0;
     if constexpr (sizeof(T) == 4) {
         if (exact)
             e = tn_launch<T, double, 64, 64, 16, 4, 4, 16, true>(cx, m, pn, qn, X, ldx, Y, ldy, part,
-                                                                 part_cap_elems, 128, &splits, 128);
+                                                                 part_cap_elems, 128, &splits, 128, sy);
         else
             e = tn_launch<T, double, 64, 64, 16, 4, 4, 8>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 128,
-                                                          &splits, 256);
+                                                          &splits, 256, sy);
     } else {
         e = tn_launch<T, double, 64, 64, 8, 4, 4, 0>(cx, m, pn, qn, X, ldx, Y, ldy, part, part_cap_elems, 128, &splits,
-                                                     32);
+                                                     32, sy);
     }
     if (e != cudaSuccess) return e;
     return launch_reduce_split<double, double>(cx, pn, qn, splits, part, pn, (int64_t)pn * qn, Out, ldo, nullptr,
-                                               0, nullptr, 1.0, 0.0, nullptr, 0);
+                                               0, nullptr, 1.0, 0.0, nullptr, 0, sy);
 }
 
 // Cholesky + inverse -------------------------------------------------------
@@ -832,14 +872,14 @@ cudaError_t downdate_sketch(Ctx& cx, int64_t m, int64_t n, int p, int bp, const 
     template cudaError_t gemm_tn<T>(Ctx&, int64_t, int, int64_t, const T*, int64_t, const T*, int64_t, T*,        \
                                     int64_t, T*, size_t, double*, int, double*);                                 \
     template cudaError_t gemm_tn_f64acc<T>(Ctx&, int64_t, int, int64_t, const T*, int64_t, const T*, int64_t,    \
-                                           double*, int64_t, double*, size_t, bool);                              \
+                                           double*, int64_t, double*, size_t, bool, bool);                        \
     template cudaError_t chol_inv<T>(Ctx&, double*, int, int, double*, T*, bool, double*, size_t);               \
     template cudaError_t downdate_sketch<T>(Ctx&, int64_t, int64_t, int, int, const T*, int64_t, const T*,        \
                                             int64_t, const T*, int64_t, const T*, T*, int64_t, T*, int64_t, T*,   \
                                             size_t, double*, int, double*);                                       \
     template cudaError_t launch_reduce_split<double, T>(Ctx&, int64_t, int64_t, int, const double*, int64_t,      \
                                                         int64_t, T*, int64_t, double*, int, double*, double,      \
-                                                        double, const T*, int64_t);
+                                                        double, const T*, int64_t, int);
 
 RQB_INST(float)
 RQB_INST(double)

@@ -242,7 +242,7 @@ int svd_lowrank(Ctx& cx, int64_t m, int64_t n, int k, int r, const T* Q, int64_t
         k_transpose<T><<<grid, 256, 0, cx.stream>>>(k, n, B, ldb, Bt, n);
         cx.launches++;
         SVD_CK(cudaGetLastError());
-        SVD_CK(gemm_tn_f64acc<T>(cx, n, k, k, Bt, n, Bt, n, G, k, gpart, (size_t)k * k * 8, true));
+        SVD_CK(gemm_tn_f64acc<T>(cx, n, k, k, Bt, n, Bt, n, G, k, gpart, (size_t)k * k * 8, true, true));
     }
     k_jacobi_init<<<grid_for((int64_t)kk * kk, cx.num_sms), 256, 0, cx.stream>>>(G, k, k, kk, G0, G1);
     cx.launches++;

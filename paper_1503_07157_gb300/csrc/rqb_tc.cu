@@ -53,17 +53,6 @@ struct StreamKParams {
     int np;            // MMA N
 };
 
-struct UpdateParams {
-    CUtensorMap mqt, mqtl;  // Q_i^T row-major (bp x m as {bp, m}), box {32, 128}
-    CUtensorMap mbs, mbsl;  // B_i staged column-major (bp x n), box {32, NJ}
-    const float* Wsrc;
-    float* Wdst;
-    DevState* st;
-    double* sq_part;        // per-CTA ||W_dst||_F^2 partials (FP64), or null
-    long long ldws, ldwd, m, n;
-    int RT, CT, C;
-};
-
 __host__ __device__ __forceinline__ long long unit_begin(long long U, int P, int p) { return U * p / P; }
 
 constexpr int kMaxCover = 64;   // CTAs that may share one tile
@@ -472,10 +461,31 @@ __global__ void __launch_bounds__(320, 1) k_streamk16(const __grid_constant__ St
 // Update W_dst = W_src - Q_i B_i on 128 x NJ output tiles, K = bp in chunks of
 // 32: D = Q_i^T-tile (M = rows) x B_i-tile (N = columns), three passes.
 // Warps 2..9 drain the accumulator: thread (quarter, lane) owns row
-// 32 quarter + lane, and the two warps of a quarter split the NJ columns.
+// 32 quarter + lane, and the two warps of a quarter split the NJ columns
+// into halves.  W travels by TMA in both directions, one half tile
+// (128 x NJ/2 FP32) at a time through a ring of three buffers: warp 10 loads
+// half tile h = 2 g + half of the CTA's g-th tile into buffer h mod 3, the
+// four warps of that half replace it by the difference in shared memory and
+// one of them stores it (TMA store) and hands the buffer back once the store
+// has read it.  ||W_dst||_F^2 per CTA on the same pass.
+struct UpdateParams {
+    CUtensorMap mqt, mqtl;  // Q_i^T row-major (bp x m as {bp, m}), box {32, 128}
+    CUtensorMap mbs, mbsl;  // B_i staged column-major (bp x n), box {32, NJ}
+    CUtensorMap mws, mwd;   // W_src / W_dst, m x n column-major, box {128 rows, NJ / 2 columns}
+    DevState* st;
+    double* sq_part;        // per-CTA ||W_dst||_F^2 partials (FP64), or null
+    long long m, n;
+    int RT, CT, C;
+    int sub;                // 1: W_dst = W_src - Q_i B_i; 0: W_dst = Q_i B_i (W_src unused)
+};
+
+constexpr int kUpdThreads = 352;   // warps 0 (operand TMA), 1 (MMA), 2..9 (epilogue), 10 (W loads)
+constexpr int kWRing = 3;          // half-tile W buffers
+
 template <int NJ, int S>
-__global__ void __launch_bounds__(320, 1) k_update(const __grid_constant__ UpdateParams p) {
-    __shared__ __align__(8) uint64_t full[S], empty[S], accfull[2], accempty[2], drain;
+__global__ void __launch_bounds__(kUpdThreads, 1) k_update(const __grid_constant__ UpdateParams p) {
+    __shared__ __align__(8) uint64_t full[S], empty[S], accfull[2], accempty[2], wfull[kWRing], wempty[kWRing],
+        drain;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     __shared__ double red[8];
@@ -483,12 +493,16 @@ __global__ void __launch_bounds__(320, 1) k_update(const __grid_constant__ Updat
     uint8_t* base = dsm + (((smem_u32(dsm) + 1023u) & ~1023u) - smem_u32(dsm));
     constexpr uint32_t kB = (uint32_t)NJ * 128u;           // one B tile (NJ rows x 128 B)
     constexpr uint32_t kStage = 2u * kTileBytes + 2u * kB;
+    constexpr int kHalf = NJ / 2;
+    constexpr uint32_t kWHalf = (uint32_t)kBM * kHalf * 4u;  // one FP32 half tile
+    uint8_t* wbuf = base + S * kStage;
     constexpr uint32_t kCols = 2u * NJ;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     volatile int* ab = &abort_flag;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
         for (int s = 0; s < 2; ++s) { mbar_init(&accfull[s], 1); mbar_init(&accempty[s], 8); }
+        for (int s = 0; s < kWRing; ++s) { mbar_init(&wfull[s], 1); mbar_init(&wempty[s], 1); }
         mbar_init(&drain, 1);
         abort_flag = 0;
         fence_mbar_init();
@@ -496,6 +510,8 @@ __global__ void __launch_bounds__(320, 1) k_update(const __grid_constant__ Updat
         prefetch_map(&p.mqtl);
         prefetch_map(&p.mbs);
         prefetch_map(&p.mbsl);
+        prefetch_map(&p.mws);
+        prefetch_map(&p.mwd);
     }
     if (warp == 1) tmem_alloc(&tmem_base, kCols);
     tc_fence_before();
@@ -524,6 +540,28 @@ __global__ void __launch_bounds__(320, 1) k_update(const __grid_constant__ Updat
             }
             for (long long qq = (q > S ? q - S : 0); qq < q; ++qq)
                 mbar_wait(&full[qq % S], (uint32_t)(qq / S) & 1u, ab, false);
+        }
+    } else if (warp == 10) {
+        if (lane == 0) {
+            long long h = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < T && !stop; t += gridDim.x) {
+                for (int hf = 0; hf < 2; ++hf, ++h) {
+                    const int b = (int)(h % kWRing);
+                    const uint32_t use = (uint32_t)(h / kWRing);
+                    if (use > 0 && !mbar_wait(&wempty[b], (use - 1) & 1u, ab)) { stop = true; break; }
+                    if (p.sub) {
+                        mbar_arrive_expect_tx(&wfull[b], kWHalf);
+                        tma_load_2d(wbuf + b * kWHalf, &p.mws, (t / p.CT) * kBM, (t % p.CT) * NJ + hf * kHalf,
+                                    &wfull[b]);
+                    } else {
+                        mbar_arrive(&wfull[b]);     // the buffer is free; nothing to load
+                    }
+                }
+            }
+            if (p.sub)
+                for (long long hh = (h > kWRing ? h - kWRing : 0); hh < h; ++hh)
+                    mbar_wait(&wfull[hh % kWRing], (uint32_t)(hh / kWRing) & 1u, ab, false);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -564,48 +602,53 @@ __global__ void __launch_bounds__(320, 1) k_update(const __grid_constant__ Updat
         const int e = warp - 2;               // 0..7
         const int quarter = warp & 3;
         const int half = e >> 2;
-        constexpr int kHalf = NJ / 2;
-        double sq = 0.0;   // ||W_dst||_F^2 of the elements this thread wrote
+        const bool issuer = (lane == 0 && (e & 3) == 0);
+        const int row = quarter * 32 + lane;
+        double sq = 0.0;
         int g = 0;
         for (int t = blockIdx.x; t < T; t += gridDim.x, ++g) {
             const int abuf = g & 1, use = g >> 1;
-            const bool okw = mbar_wait(&accfull[abuf], (uint32_t)use & 1u, ab);
-            if (!__all_sync(0xffffffffu, okw)) break;
+            const long long h = 2LL * g + half;
+            const int b = (int)(h % kWRing);
+            bool okw = mbar_wait(&accfull[abuf], (uint32_t)use & 1u, ab);
+            if (okw) okw = mbar_wait(&wfull[b], (uint32_t)(h / kWRing) & 1u, ab);
+            // the four warps of this half leave together (the barrier counts them)
+            named_barrier(1 + half, 128);
+            if (*ab || !okw) break;
             tc_fence_after();
             const int rt = t / p.CT, ctile = t % p.CT;
-            const long long r = (long long)rt * kBM + quarter * 32 + lane;
+            const long long r = (long long)rt * kBM + row;
             const long long j0 = (long long)ctile * NJ + half * kHalf;
             const bool rok = r < p.m;
-            const float* src = p.Wsrc + r;
-            float* dst = p.Wdst + r;
+            // half tile column-major: element (row, col) at col * 512 + row * 4
+            float* wt = reinterpret_cast<float*>(wbuf + b * kWHalf) + row;
             const uint32_t tl = tmem + (uint32_t)(abuf * NJ + half * kHalf) + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
-            for (int c0 = 0; c0 < kHalf; c0 += 32) {
-                float w[32];
+            for (int c0 = 0; c0 < kHalf; c0 += 16) {
+                float v[16];
+                tmem_ld16(tl + (uint32_t)c0, v);
+                float sq16 = 0.f;
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const long long j = j0 + c0 + i;
-                    w[i] = (rok && j < p.n) ? __ldcs(src + j * p.ldws) : 0.f;
+                for (int i = 0; i < 16; ++i) {
+                    const float d = p.sub ? wt[(c0 + i) * kBM] - v[i] : v[i];
+                    wt[(c0 + i) * kBM] = d;
+                    if (rok && j0 + c0 + i < p.n) sq16 = fmaf(d, d, sq16);
                 }
-                float v0[16], v1[16];
-                tmem_ld16(tl + (uint32_t)c0, v0);
-                tmem_ld16(tl + (uint32_t)(c0 + 16), v1);
-                float sq32 = 0.f;
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const long long j = j0 + c0 + i;
-                    const float d = w[i] - (i < 16 ? v0[i] : v1[i - 16]);
-                    if (rok && j < p.n) {
-                        dst[j * p.ldwd] = d;
-                        sq32 = fmaf(d, d, sq32);
-                    }
-                }
-                sq += (double)sq32;
+                sq += (double)sq16;
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&accempty[abuf]);
+            fence_async_smem();
+            named_barrier(1 + half, 128);
+            if (issuer) {
+                tma_store_2d(&p.mwd, rt * kBM, ctile * NJ + half * kHalf, wbuf + b * kWHalf);
+                bulk_commit();
+                bulk_wait_read<0>();
+                mbar_arrive(&wempty[b]);
+            }
         }
+        if (issuer) bulk_wait<0>();
         for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
         if (lane == 0) red[e] = sq;
     }
@@ -655,7 +698,7 @@ __global__ void k_split_q(const float* __restrict__ Qi, long long ldq, long long
         const int c = c0 + i;
         float v = 0.f;
         if (r < m && c < p) v = Qi[r + c * ldq];
-        if (r < m) {
+        if (r < m && Qhi) {
             Qhi[r + c * ldql] = v;
             Qlo[r + c * ldql] = tf32_lo(v);
         }
@@ -733,7 +776,7 @@ __device__ __forceinline__ int tile_slots(long long U, int C, int P, int G, int 
 // Y[r + c ldy] (r < m, c < np) = sum over the CTAs covering tile r / 128 of
 // their partials, in CTA order (FP32, at most a few terms, round to nearest);
 // with sub, Y = sub - that sum (sub may alias Y).  One CTA per tile.
-constexpr int kReduceSlices = 8;   // CTAs per tile in the reductions
+constexpr int kReduceSlices = 8;   // least CTAs per tile in the reductions (gridDim.y)
 
 __global__ void k_reduce_sketch(const float* __restrict__ part, long long U, int C, int P, int G, int np, long long m,
                                 float* Y, long long ldy, const float* sub) {
@@ -743,7 +786,7 @@ __global__ void k_reduce_sketch(const float* __restrict__ part, long long U, int
     if (threadIdx.x == 0) count = tile_slots(U, C, P, G, np, t, off);
     __syncthreads();
     const int nc = count;
-    const int span = np * kBM / kReduceSlices;
+    const int span = np * kBM / (int)gridDim.y;
     const int i0 = blockIdx.y * span;
 #pragma unroll 4
     for (int idx = i0 + threadIdx.x; idx < i0 + span; idx += blockDim.x) {   // c * 128 + row
@@ -771,7 +814,7 @@ __global__ void k_reduce_project(const float* __restrict__ part, long long U, in
     __syncthreads();
     const int nc = count;
     double sq = 0.0;
-    const int span = np * kBM / kReduceSlices;
+    const int span = np * kBM / (int)gridDim.y;
     const int i0 = blockIdx.y * span;
 #pragma unroll 4
     for (int idx = i0 + threadIdx.x; idx < i0 + span; idx += blockDim.x) {   // jl * np + c
@@ -793,7 +836,7 @@ __global__ void k_reduce_project(const float* __restrict__ part, long long U, in
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        sq_part[(size_t)t * kReduceSlices + blockIdx.y] = s;
+        sq_part[(size_t)t * gridDim.y + blockIdx.y] = s;
     }
 }
 
@@ -1074,7 +1117,7 @@ __global__ void k_reduce_project16(const float* __restrict__ part, long long U, 
     __syncthreads();
     const int nc = count;
     double sq = 0.0;
-    const int span = np * kBM / kReduceSlices;
+    const int span = np * kBM / (int)gridDim.y;
     const int i0 = blockIdx.y * span;
 #pragma unroll 4
     for (int idx = i0 + threadIdx.x; idx < i0 + span; idx += blockDim.x) {
@@ -1095,7 +1138,7 @@ __global__ void k_reduce_project16(const float* __restrict__ part, long long U, 
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        sq_part[(size_t)t * kReduceSlices + blockIdx.y] = s;
+        sq_part[(size_t)t * gridDim.y + blockIdx.y] = s;
     }
 }
 
@@ -1156,8 +1199,9 @@ cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, long long inne
                       swizzle128);
 }
 
-constexpr int kUpdNJ = 128, kUpdStages = 3;
-constexpr size_t kUpdSmem = (size_t)kUpdStages * (2 * kTileBytes + 2 * kUpdNJ * 128) + 1024;
+constexpr int kUpdNJ = 128, kUpdStages = 2;
+constexpr size_t kUpdSmem =
+    (size_t)kUpdStages * (2 * kTileBytes + 2 * kUpdNJ * 128) + (size_t)kWRing * kBM * (kUpdNJ / 2) * 4 + 1024;
 
 template <typename K>
 cudaError_t allow_smem(K kernel, size_t bytes) {
@@ -1228,6 +1272,14 @@ Plan plan(long long tiles, long long C, int sms) {
     return pl;
 }
 
+// CTAs per tile of the reductions: at least kReduceSlices, more (up to 64)
+// when there are few tiles, so that the reduction still fills the GPU.
+int reduce_slices(int tiles, int sms) {
+    int sl = kReduceSlices;
+    while (sl < 64 && (long long)tiles * sl < 4LL * sms) sl *= 2;
+    return sl;
+}
+
 }  // namespace
 
 bool shape_ok(long long m, long long n) { return m >= 128 && n >= 256; }
@@ -1276,7 +1328,8 @@ cudaError_t sketch(Ctx& cx, const float* X, long long ldx, long long m, long lon
     p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
     if ((e = launch_streamk<kSketch>(cx, p, np)) != cudaSuccess) return e;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_reduce_sketch<<<dim3(pl.tiles, kReduceSlices), 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, m, Y,
+    const dim3 rgrid(pl.tiles, reduce_slices(pl.tiles, cx.num_sms));
+    k_reduce_sketch<<<rgrid, 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, m, Y,
                                                                            ldy, nullptr);
     cx.launches++;
     return cudaGetLastError();
@@ -1297,7 +1350,8 @@ cudaError_t sketch_sub(Ctx& cx, const float* X, long long ldx, long long m, long
     p.st = cx.st;
     p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
     if ((e = launch_streamk<kSketch>(cx, p, np)) != cudaSuccess) return e;
-    k_reduce_sketch<<<dim3(pl.tiles, kReduceSlices), 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, m, Y,
+    const dim3 rgrid(pl.tiles, reduce_slices(pl.tiles, cx.num_sms));
+    k_reduce_sketch<<<rgrid, 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, m, Y,
                                                                            ldy, sub);
     cx.launches++;
     return cudaGetLastError();
@@ -1312,31 +1366,39 @@ cudaError_t project(Ctx& cx, const float* X, long long ldx, long long m, long lo
     if ((e = make_map(&p.mw, Qhi, m, np, ldql, kKC, np, true)) != cudaSuccess) return e;
     if ((e = make_map(&p.mwl, Qlo, m, np, ldql, kKC, np, true)) != cudaSuccess) return e;
     const Plan pl = plan((n + kBM - 1) / kBM, (m + kKC - 1) / kKC, cx.num_sms);
-    if ((size_t)pl.P * pl.G * kBM * np > part_cap || pl.tiles * kReduceSlices > sq_cap) return cudaErrorInvalidValue;
+    const int sl = reduce_slices(pl.tiles, cx.num_sms);
+    if ((size_t)pl.P * pl.G * kBM * np > part_cap || pl.tiles * sl > sq_cap) return cudaErrorInvalidValue;
     p.part = part;
     p.st = cx.st;
     p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
     if ((e = launch_streamk<kProject>(cx, p, np)) != cudaSuccess) return e;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_reduce_project<<<dim3(pl.tiles, kReduceSlices), 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, pcols,
+    k_reduce_project<<<dim3(pl.tiles, sl), 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, pcols,
                                                                             n, B, ldb, Bs, Bsl, sq_part);
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return launch_sum_doubles(cx, sq_part, pl.tiles * kReduceSlices, sq_out);
+    return launch_sum_doubles(cx, sq_part, pl.tiles * sl, sq_out);
 }
 
-cudaError_t update(Ctx& cx, const float* Wsrc, long long ldws, float* Wdst, long long ldwd, long long m,
-                   long long n, const float* Qt, const float* Qtl, const float* Bs, const float* Bsl, int np,
-                   double* sq_part, int sq_cap, double* sq_out) {
+cudaError_t update_impl(Ctx& cx, const float* Wsrc, long long ldws, float* Wdst, long long ldwd, long long m,
+                        long long n, const float* Qt, const float* Qtl, const float* Bs, const float* Bsl, int np,
+                        double* sq_part, int sq_cap, double* sq_out, int sub) {
     UpdateParams p;
     cudaError_t e;
+    p.sub = sub;
+    if (!sub) {
+        Wsrc = Wdst;     // the source map is not read
+        ldws = ldwd;
+    }
     if ((e = make_map(&p.mqt, Qt, np, m, np, kKC, kBM, true)) != cudaSuccess) return e;
     if ((e = make_map(&p.mqtl, Qtl, np, m, np, kKC, kBM, true)) != cudaSuccess) return e;
     if ((e = make_map(&p.mbs, Bs, np, n, np, kKC, kUpdNJ, true)) != cudaSuccess) return e;
     if ((e = make_map(&p.mbsl, Bsl, np, n, np, kKC, kUpdNJ, true)) != cudaSuccess) return e;
-    p.Wsrc = Wsrc; p.Wdst = Wdst; p.st = cx.st;
+    if ((e = make_map(&p.mws, Wsrc, m, n, ldws, kBM, kUpdNJ / 2, false)) != cudaSuccess) return e;
+    if ((e = make_map(&p.mwd, Wdst, m, n, ldwd, kBM, kUpdNJ / 2, false)) != cudaSuccess) return e;
+    p.st = cx.st;
     p.sq_part = sq_out ? sq_part : nullptr;
-    p.ldws = ldws; p.ldwd = ldwd; p.m = m; p.n = n;
+    p.m = m; p.n = n;
     p.RT = (int)((m + kBM - 1) / kBM);
     p.CT = (int)((n + kUpdNJ - 1) / kUpdNJ);
     p.C = np / kKC;
@@ -1344,10 +1406,36 @@ cudaError_t update(Ctx& cx, const float* Wsrc, long long ldws, float* Wdst, long
     const int grid = (int)std::min<long long>(cx.num_sms, T);
     if (sq_out && grid > sq_cap) return cudaErrorInvalidValue;
     if ((e = allow_smem(k_update<kUpdNJ, kUpdStages>, kUpdSmem)) != cudaSuccess) return e;
-    k_update<kUpdNJ, kUpdStages><<<grid, 320, kUpdSmem, cx.stream>>>(p);
+    k_update<kUpdNJ, kUpdStages><<<grid, kUpdThreads, kUpdSmem, cx.stream>>>(p);
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return sq_out ? launch_sum_doubles(cx, sq_part, grid, sq_out) : cudaSuccess;
+}
+
+cudaError_t update(Ctx& cx, const float* Wsrc, long long ldws, float* Wdst, long long ldwd, long long m,
+                   long long n, const float* Qt, const float* Qtl, const float* Bs, const float* Bsl, int np,
+                   double* sq_part, int sq_cap, double* sq_out) {
+    return update_impl(cx, Wsrc, ldws, Wdst, ldwd, m, n, Qt, Qtl, Bs, Bsl, np, sq_part, sq_cap, sq_out, 1);
+}
+
+// Out (m x np, ld ldo) = Y (m x np, ld ldy) C (np x np, ld ldc), split-TF32.
+bool product_ok(long long m, int np, long long ldo, const float* Out) {
+    return m >= 128 && np >= kUpdNJ && (ldo % 4) == 0 && (reinterpret_cast<uintptr_t>(Out) & 15u) == 0;
+}
+
+cudaError_t product(Ctx& cx, const float* Y, long long ldy, long long m, const float* C, long long ldc, int np,
+                    float* Out, long long ldo, const ReprojScratch& w) {
+    cudaError_t e;
+    dim3 g1((unsigned)((m + 31) / 32), (unsigned)(np / 32));
+    k_split_q<<<g1, 256, 0, cx.stream>>>(Y, ldy, m, np, np, nullptr, nullptr, 0, w.Yhi, w.Ylo);
+    cx.launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const long long total = (long long)np * np;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * cx.num_sms);
+    k_stage_b<<<blocks, 256, 0, cx.stream>>>(C, ldc, np, np, np, w.Bs, w.Bsl);
+    cx.launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return update_impl(cx, nullptr, 0, Out, ldo, m, np, w.Yhi, w.Ylo, w.Bs, w.Bsl, np, nullptr, 0, nullptr, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -1409,7 +1497,8 @@ cudaError_t sketch16(Ctx& cx, const __nv_bfloat16* X, long long ldx, long long m
     p.st = cx.st;
     p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
     if ((e = launch_streamk16<kSketch>(cx, p, np)) != cudaSuccess) return e;
-    k_reduce_sketch<<<dim3(pl.tiles, kReduceSlices), 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, m, Y,
+    const dim3 rgrid(pl.tiles, reduce_slices(pl.tiles, cx.num_sms));
+    k_reduce_sketch<<<rgrid, 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, m, Y,
                                                                            ldy, nullptr);
     cx.launches++;
     return cudaGetLastError();
@@ -1425,16 +1514,17 @@ cudaError_t project16(Ctx& cx, const __nv_bfloat16* X, long long ldx, long long 
     if ((e = make_map(&p.mw, Qhi, m, np, ldql, kKC16, np, true)) != cudaSuccess) return e;
     if ((e = make_map(&p.mwl, Qlo, m, np, ldql, kKC16, np, true)) != cudaSuccess) return e;
     const Plan pl = plan((n + kBM - 1) / kBM, (m + kKC16 - 1) / kKC16, cx.num_sms);
-    if ((size_t)pl.P * pl.G * kBM * np > part_cap || pl.tiles * kReduceSlices > sq_cap) return cudaErrorInvalidValue;
+    const int sl = reduce_slices(pl.tiles, cx.num_sms);
+    if ((size_t)pl.P * pl.G * kBM * np > part_cap || pl.tiles * sl > sq_cap) return cudaErrorInvalidValue;
     p.part = part;
     p.st = cx.st;
     p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
     if ((e = launch_streamk16<kProject>(cx, p, np)) != cudaSuccess) return e;
-    k_reduce_project16<<<dim3(pl.tiles, kReduceSlices), 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np,
+    k_reduce_project16<<<dim3(pl.tiles, sl), 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np,
                                                                               pcols, n, B, ldb, Bs, Bsl, sq_part);
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return launch_sum_doubles(cx, sq_part, pl.tiles * kReduceSlices, sq_out);
+    return launch_sum_doubles(cx, sq_part, pl.tiles * sl, sq_out);
 }
 
 cudaError_t update16(Ctx& cx, const __nv_bfloat16* Wsrc, long long ldws, __nv_bfloat16* Wdst, long long ldwd,

@@ -74,6 +74,14 @@ struct ReprojScratch {
 // m x kprev (ld ldq), both products split-TF32 (C rounded to TF32 for the
 // second); needs reproject_ok(m, kprev).
 bool reproject_ok(long long m, long long kprev);
+
+// Out (m x np, ld ldo) = Y (m x np, ld ldy) C (np x np, ld ldc) with the
+// split-TF32 update kernel (both operands split, three passes); uses
+// w.Yhi / w.Ylo (m x np) and w.Bs / w.Bsl (np x np).  Out must be
+// TMA-addressable and np >= 128 (product_ok).
+bool product_ok(long long m, int np, long long ldo, const float* Out);
+cudaError_t product(Ctx& cx, const float* Y, long long ldy, long long m, const float* C, long long ldc, int np,
+                    float* Out, long long ldo, const ReprojScratch& w);
 cudaError_t reproject(Ctx& cx, const float* Qbar, long long ldq, long long m, long long kprev, float* Y,
                       long long ldy, int np, const ReprojScratch& w);
 

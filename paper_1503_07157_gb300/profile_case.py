@@ -12,6 +12,10 @@
                 eps = 1e-2 ||A||_F)
   --case fp64   the same for the 2000 x 1000 FP64 workload (b = 50,
                 eps = 1e-4 ||A||_F)
+  --case bf16   the same for the BF16 storage leg (the mixed matrix stored
+                in BF16, b = 256, eps = 1e-2 ||A||_F)
+  --case small16  8192 x 8192 BF16 (128 MB), fixed rank 512 (two blocks), for
+                --set full captures of the BF16 kernels
   --case batched  the same for the 512-matrix batch (b = 32, eps_t =
                 1e-3 ||A_t||_F) through rqb_factor_batched
   --case batched64  the first 64 matrices of that batch (about 0.6 GB), for
@@ -29,7 +33,7 @@ if ROOT not in sys.path:
 
 def main() -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["small", "mixed", "fp32", "fp64", "batched", "batched64"], default="small")
+    ap.add_argument("--case", choices=["small", "small16", "mixed", "bf16", "fp32", "fp64", "batched", "batched64"], default="small")
     args = ap.parse_args()
     import torch
     import inputs
@@ -41,6 +45,17 @@ def main() -> int:
         A = inputs.usv_torch(m, n, s, 3, device="cuda", dtype=torch.float32)
         torch.cuda.synchronize()
         with rqb.Handle(torch.float32, prec=rqb.RQB_PREC_TF32X3, max_rank=512, fixed_rank=True) as h:
+            _, _, k, rc = h.rqb_factor(A, 0.0, 256, 0, check=False)
+            torch.cuda.synchronize()
+    elif args.case == "small16":
+        m = n = 8192
+        s = inputs.spectrum_mixed_config(min(m, n), knee=2000)
+        A32 = inputs.usv_torch(m, n, s, 3, device="cuda", dtype=torch.float32)
+        A = torch.empty(n, m, dtype=torch.bfloat16, device="cuda").t()
+        A.copy_(A32)
+        del A32
+        torch.cuda.synchronize()
+        with rqb.Handle(torch.bfloat16, max_rank=512, fixed_rank=True) as h:
             _, _, k, rc = h.rqb_factor(A, 0.0, 256, 0, check=False)
             torch.cuda.synchronize()
     elif args.case in ("batched", "batched64"):
@@ -63,9 +78,15 @@ def main() -> int:
         rc = 0 if all(o[3] == rqb.RQB_OK for o in out) else 1
     else:
         import numpy as np
-        if args.case == "mixed":
+        if args.case in ("mixed", "bf16"):
             A, meta = inputs.config_mixed_torch()
             dt, prec, eps, b = torch.float32, rqb.RQB_PREC_TF32X3, meta["eps"], meta["b"]
+            if args.case == "bf16":
+                Ab = torch.empty(A.shape[1], A.shape[0], dtype=torch.bfloat16, device="cuda").t()
+                Ab.copy_(A)
+                del A
+                torch.cuda.empty_cache()
+                A, dt, prec, eps = Ab, torch.bfloat16, rqb.RQB_PREC_BF16, 10 * meta["eps"]
         elif args.case == "fp32":
             s = inputs.spectrum_poly(16000)
             A = inputs.usv_torch(20000, 16000, s, 2, device="cuda", dtype=torch.float32)

@@ -128,6 +128,10 @@ typedef struct {
     int32_t svd_sweeps;      /* Jacobi sweeps of the last rqb_svd              */
     double phase_ms[RQB_NUM_PHASES];     /* summed device time per step (ms)   */
     int32_t phase_calls[RQB_NUM_PHASES]; /* times each step ran                */
+    int32_t gram_fallbacks; /* tensor-core handles: panels whose first Gram was
+                               recomputed with exact products (section of
+                               rqb_factor)                                     */
+    int32_t reserved2;
 } rqb_stats;
 
 typedef struct rqb_handle_s* rqb_handle;
@@ -162,6 +166,12 @@ int rqb_destroy(rqb_handle h);
  * (RQB_ERR_UNSUPPORTED otherwise) and decide every block on the direct
  * ||A^(i)||_F^2 of the stored (rounded) residual, since the BF16 rounding of
  * each downdate moves the residual away from E_i; stats.E still reports E_i.
+ * On split-TF32 and BF16 handles the first CholeskyQR pass of a panel takes
+ * its Gram from split-TF32 tensor-core products (relative error ~1e-7); when
+ * the FP64 Cholesky of it breaks down or its pivots put kappa(G) above 1e5,
+ * the Gram is recomputed with exact products and FP64 sums
+ * (stats.gram_fallbacks counts those panels).  The second pass always uses an
+ * FP64-accumulated Gram.
  * Returns RQB_OK, RQB_NOT_CONVERGED, or an error. */
 int rqb_factor(rqb_handle h, const void* A, int64_t m, int64_t n, int64_t lda,
                double eps, int64_t b, uint64_t seed,

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <type_traits>
+#include <vector>
 
 #include "rqb_engine.h"
 #include "rqb_tc.h"
@@ -258,7 +259,7 @@ int ensure_reproj(rqb_handle h, int64_t m, int64_t kcap, int bp, tc::ReprojScrat
     auto take = [&](size_t floats) { size_t o = off; off = align256(off + 4 * floats); return o; };
     const size_t oYh = take((size_t)ldyl * bp), oYl = take((size_t)ldyl * bp);
     const size_t kb = (size_t)std::max<int64_t>(kcap, bp);
-    const size_t oCt = take((size_t)bp * kcap), oOm = take((size_t)ldom * bp);
+    const size_t oCt = take((size_t)bp * kb), oOm = take((size_t)ldom * bp);
     const size_t oBs = take((size_t)bp * kb), oBsl = take((size_t)bp * kb);
     const size_t oP = take(part);
     int rc = h->pcbuf.ensure(off);
@@ -308,9 +309,43 @@ int read_state(rqb_handle h, const Scal& sc) {
 template <typename T>
 int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_t ldy, int64_t m, int p, int bp,
                    const T* Qbar, int64_t kprev, int64_t ldqb, T* Qout, int64_t ldqo) {
-    // pass 1: CholeskyQR of Y, Y1 = Y R^{-1}
-    RQB_CK(gemm_tn_f64acc<T>(cx, m, bp, bp, Y, ldy, Y, ldy, ar.G, bp, ar.dpart, ar.dpart_cap, true, true));
-    RQB_CK(chol_inv<T>(cx, ar.G, bp, p, ar.R, ar.Rinv, true, ar.dpart, ar.dpart_cap));
+    // pass 1: CholeskyQR of Y, Y1 = Y R^{-1}.  On the tensor-core handles the
+    // Gram is first taken from the split-TF32 products (relative error
+    // ~1e-7): pass 1 only has to leave Y1 well conditioned for pass 2, which
+    // it does while kappa(Y)^2 * 1e-7 << 1.  The FP64 Cholesky of that Gram
+    // runs on a scratch state; when it breaks down or its pivots put
+    // kappa(G) above 1e5, the Gram is recomputed with exact products and FP64
+    // sums and factored again.
+    bool pass1 = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if (ar.rp && m <= ar.rp->ldyl && tc::gram_ok(m, bp, ldy, Y)) {
+            RQB_CK(tc::gram(cx, Y, ldy, m, bp, *ar.rp));
+            RQB_CK(launch_to_double<float>(cx, bp, bp, ar.rp->Ct, bp, ar.G, bp));
+            DevState* st2 = reinterpret_cast<DevState*>(reinterpret_cast<char*>(h->state.p) + 128);
+            RQB_CK(cudaMemsetAsync(st2, 0, sizeof(DevState), h->stream));
+            Ctx cx2 = cx;
+            cx2.st = st2;
+            RQB_CK(chol_inv<T>(cx2, ar.G, bp, p, ar.R, ar.Rinv, true, ar.dpart, ar.dpart_cap));
+            cx.launches = cx2.launches;
+            DevState hs;
+            std::vector<double> diag((size_t)bp);
+            RQB_CK(cudaMemcpyAsync(&hs, st2, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+            RQB_CK(cudaMemcpy2DAsync(diag.data(), sizeof(double), ar.R, sizeof(double) * (bp + 1), sizeof(double),
+                                     bp, cudaMemcpyDeviceToHost, h->stream));
+            RQB_CK(cudaStreamSynchronize(h->stream));
+            double lo = HUGE_VAL, hi = 0.0;
+            for (int i = 0; i < p; ++i) {
+                lo = std::min(lo, diag[i]);
+                hi = std::max(hi, diag[i]);
+            }
+            pass1 = hs.err == RQB_OK && lo > 0.0 && (hi / lo) * (hi / lo) <= 1e5;
+            h->stats.gram_fallbacks += pass1 ? 0 : 1;
+        }
+    }
+    if (!pass1) {
+        RQB_CK(gemm_tn_f64acc<T>(cx, m, bp, bp, Y, ldy, Y, ldy, ar.G, bp, ar.dpart, ar.dpart_cap, true, true));
+        RQB_CK(chol_inv<T>(cx, ar.G, bp, p, ar.R, ar.Rinv, true, ar.dpart, ar.dpart_cap));
+    }
     bool tc1 = false;
     if constexpr (std::is_same<T, float>::value) {
         if (ar.rp && m <= ar.rp->ldyl && tc::product_ok(m, bp, m, ar.Y1)) {
@@ -1064,9 +1099,9 @@ int orth_impl(rqb_handle h, const T* Y, int64_t m, int p, int64_t ldy, const T* 
     int rc = ensure_arena<T>(h, m, 1, bp, kprev, &ar);
     if (rc != RQB_OK) return rc;
     tc::ReprojScratch rp;
-    if (std::is_same<T, float>::value && (h->cfg.prec == RQB_PREC_TF32X3 || h->cfg.dtype == RQB_BF16) &&
-        tc::reproject_ok(m, kprev)) {
-        if ((rc = ensure_reproj(h, m, kprev, bp, &rp)) != RQB_OK) return rc;
+    h->stats.gram_fallbacks = 0;
+    if (std::is_same<T, float>::value && (h->cfg.prec == RQB_PREC_TF32X3 || h->cfg.dtype == RQB_BF16) && m >= 128) {
+        if ((rc = ensure_reproj(h, m, std::max<int64_t>(kprev, 1), bp, &rp)) != RQB_OK) return rc;
         ar.rp = &rp;
     }
     Scal sc = scalars(h);

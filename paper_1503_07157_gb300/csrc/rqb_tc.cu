@@ -1418,6 +1418,22 @@ cudaError_t update(Ctx& cx, const float* Wsrc, long long ldws, float* Wdst, long
     return update_impl(cx, Wsrc, ldws, Wdst, ldwd, m, n, Qt, Qtl, Bs, Bsl, np, sq_part, sq_cap, sq_out, 1);
 }
 
+// G (np x np, FP32, ld np, in w.Ct) = Y^T Y by the stream-K projection with
+// Y split into hi / lo (three passes, FP32 accumulation with period drains).
+bool gram_ok(long long m, int np, long long ldy, const float* Y) {
+    return m >= 128 && np >= kBM && (ldy % 4) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15u) == 0;
+}
+
+cudaError_t gram(Ctx& cx, const float* Y, long long ldy, long long m, int np, const ReprojScratch& w) {
+    cudaError_t e;
+    dim3 g1((unsigned)((m + 31) / 32), (unsigned)(np / 32));
+    k_split_q<<<g1, 256, 0, cx.stream>>>(Y, ldy, m, np, np, w.Yhi, w.Ylo, w.ldyl, nullptr, nullptr);
+    cx.launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return project(cx, Y, ldy, m, np, w.Yhi, w.Ylo, w.ldyl, np, np, w.Ct, np, w.Bs, w.Bsl, w.part, w.part_cap,
+                   w.sq_part, w.sq_cap, w.sq_out);
+}
+
 // Out (m x np, ld ldo) = Y (m x np, ld ldy) C (np x np, ld ldc), split-TF32.
 bool product_ok(long long m, int np, long long ldo, const float* Out) {
     return m >= 128 && np >= kUpdNJ && (ldo % 4) == 0 && (reinterpret_cast<uintptr_t>(Out) & 15u) == 0;

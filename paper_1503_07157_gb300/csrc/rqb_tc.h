@@ -80,6 +80,11 @@ bool reproject_ok(long long m, long long kprev);
 // w.Yhi / w.Ylo (m x np) and w.Bs / w.Bsl (np x np).  Out must be
 // TMA-addressable and np >= 128 (product_ok).
 bool product_ok(long long m, int np, long long ldo, const float* Out);
+
+// w.Ct (np x np, FP32, ld np) = Y^T Y (m x np, ld ldy) with the split-TF32
+// projection kernel (relative accuracy ~1e-7 of ||Y||^2); needs gram_ok.
+bool gram_ok(long long m, int np, long long ldy, const float* Y);
+cudaError_t gram(Ctx& cx, const float* Y, long long ldy, long long m, int np, const ReprojScratch& w);
 cudaError_t product(Ctx& cx, const float* Y, long long ldy, long long m, const float* C, long long ldc, int np,
                     float* Out, long long ldo, const ReprojScratch& w);
 cudaError_t reproject(Ctx& cx, const float* Qbar, long long ldq, long long m, long long kprev, float* Y,

@@ -112,6 +112,24 @@ def test_orth_tensor_core_reprojection(orc, htc, m, p, kprev):
     assert np.abs(Qi - Qo).max() <= 1e-3
 
 
+@pytest.mark.parametrize("cond,fallback", [(1e1, 0), (1e5, 1)])
+def test_orth_first_gram_fallback(orc, htc, cond, fallback):
+    """The first CholeskyQR pass of a split-TF32 handle takes its Gram from the
+    tensor core; a panel with kappa(Y) = 1e5 (pivot ratio^2 ~ 1e10 > 1e5) is
+    refactored from the exact FP64-accumulated Gram, and both end orthonormal."""
+    m, p = 6000, 256
+    rng = np.random.default_rng(int(cond))
+    U = np.linalg.qr(rng.standard_normal((m, p)))[0]
+    V = np.linalg.qr(rng.standard_normal((p, p)))[0]
+    Y = _f32((U * np.logspace(0, -np.log10(cond), p)) @ V.T)
+    Qi = to_np(htc.rqb_orth(to_dev(Y, torch.float32), None))
+    st = htc.rqb_get_stats()
+    assert st.gram_fallbacks == fallback
+    assert orth_err(Qi) <= 1e-5
+    Qo = orc.orth_reproject(Y, None)
+    assert np.abs(Qi - Qo).max() <= (1e-3 if cond < 1e3 else 5e-2)
+
+
 def _factor(rqb, A, eps, b, seed, **kw):
     with rqb.Handle(torch.float32, prec=rqb.RQB_PREC_TF32X3, **kw) as h:
         Q, B, k, rc = h.rqb_factor(to_dev(A, torch.float32), eps, b, seed, check=False)

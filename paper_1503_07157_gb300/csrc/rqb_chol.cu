@@ -155,10 +155,24 @@ __global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G
                 if (tid - kNb <= j) Di[j][tid - kNb] *= ij;
             }
             __syncthreads();
-            for (int e = tid; e < kNb * kNb; e += 256) {
-                const int r = e & (kNb - 1), c = e / kNb;
-                if (c > j && r >= c) D[r][c] -= D[r][j] * D[c][j];
-                else if (r > j && c <= j) Di[r][c] -= D[r][j] * Di[j][c];
+            // only the active entries, densely numbered, so that every FP64
+            // instruction issued has its lanes busy: the trailing triangle
+            // j < c <= r < 32 (nt entries), then the block j < r < 32, c <= j
+            const int nrem = kNb - 1 - j;
+            const int nt = nrem * (nrem + 1) / 2, nd = nrem * (j + 1);
+            for (int q = tid; q < nt + nd; q += 256) {
+                if (q < nt) {
+                    int u = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
+                    while (u * (u + 1) / 2 > q) --u;
+                    while ((u + 1) * (u + 2) / 2 <= q) ++u;
+                    const int v = q - u * (u + 1) / 2;
+                    const int r = j + 1 + u, c = j + 1 + v;
+                    D[r][c] -= D[r][j] * D[c][j];
+                } else {
+                    const int q2 = q - nt;
+                    const int r = j + 1 + q2 / (j + 1), c = q2 % (j + 1);
+                    Di[r][c] -= D[r][j] * Di[j][c];
+                }
             }
             __syncthreads();
         }

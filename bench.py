@@ -70,6 +70,8 @@ WORKLOADS["adjoint"] = dict(name="randQB_b fixed-rank forward + adjoint, 8192x40
 WORKLOADS["batched"] = dict(name="randQB_b batched FP32: 512 matrices, m~U[256,4096], n~U[128,min(m,2048)], "
                                  "s_j=exp(-j/r), r~U[10,200], b=32, eps_t=1e-3||A_t||_F",
                             m=0, n=0, b=32, eps_rel=1e-3, dtype="float32", spectrum="exp", count=512)
+for _k, _w in WORKLOADS.items():
+    _w["key"] = _k
 METRIC = "randQB_b TFLOP/s & roofline fraction at matched eps; mixed/batched vs plain FP32"
 
 
@@ -215,7 +217,11 @@ def alu_peak_tflops(dtype: str, num_sms: int, sm_mhz: float) -> float:
 # from profiles/ (None when the kernel changed since the capture or when the
 # workload's dominant kernel was captured only on a smaller case).
 #   fp32: k_gemm_nn sketch, 20000 x 16000, dram read 1.295 GB + write 0.145 GB
-NCU_TRAFFIC = {"fp32": 1.440e9, "fp64": None, "mixed": None}
+# DRAM bytes (read + write) per launch of each workload's dominant kernel from
+# ncu captures (profiles/); bf16: k_update16 captured at 8192 x 8192 (247 MB)
+# scaled by the 8x elements of a 32768 x 16384 launch; None where the kernel
+# changed since its last capture.
+NCU_TRAFFIC = {"fp32": 1.440e9, "fp64": None, "mixed": None, "bf16": 1.98e9}
 
 
 def oracle_modes(w: dict) -> tuple[int, int]:
@@ -322,7 +328,7 @@ def run_ours(args, w: dict, rank: int, world: int, dist):
                 "project": f"k_streamk{sfx}<project> + k_reduce_project{sfx}", "downdate": f"k_update{sfx}"}[dom]
         es = 2 if is16 else 4
         roofline = {"bound": "tensor", "kernel": kern, "achieved": round(achieved, 3), "peak": round(peak, 3),
-                    "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(args.workload),
+                    "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(w.get("key")),
                     "peak_source": (f"measured bf16 burst {bf16} TFLOP/s (MEASURED_PEAKS.json), of measured" if is16
                                     else f"measured bf16 burst {bf16} TFLOP/s (MEASURED_PEAKS.json) x 1/2 "
                                          f"(nominal TF32:BF16 dense ratio), of measured"),
@@ -341,7 +347,7 @@ def run_ours(args, w: dict, rank: int, world: int, dist):
                     "kernel": f"{dom} (k_gemm_{'nn' if dom == 'sketch' else 'tn'} + split reduction)"
                     if dom in ("sketch", "project") else dom,
                     "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
-                    "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(args.workload),
+                    "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(w.get("key")),
                     "peak_source": f"derived: {props.multi_processor_count} SMs x "
                                    f"{'128 FP32' if w['dtype'] == 'float32' else '2 FP64'} lanes x 2 x {sm_max:.0f} MHz",
                     "phase_ms_per_step": per_step}

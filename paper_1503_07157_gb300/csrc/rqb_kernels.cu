@@ -178,8 +178,13 @@ k_reduce_split(int64_t rows, int64_t cols, int splits, const TP* __restrict__ pa
         const int64_t r = e % rows, c = e / rows;
         // sym: the upper triangle is the mirror of the lower one
         const int64_t pe = (sym && r < c) ? c + r * ldp : r + c * ldp;
-        double s = 0.0;
-        for (int z = 0; z < splits; ++z) s += (double)part[z * zstride + pe];
+        // partials summed in their own precision, in split order (FP32
+        // partials: 2^-24 per term, far below the product's own rounding;
+        // FP64 partials: the FP64-accumulated Grams and coefficients)
+        TP acc = TP(0);
+#pragma unroll 4
+        for (int z = 0; z < splits; ++z) acc += part[z * zstride + pe];
+        double s = (double)acc;
         if (alpha != 1.0) s *= alpha;
         if (beta != 0.0) s += beta * (double)Yin[r + c * ldyin];
         const TO v = (TO)s;
@@ -749,9 +754,9 @@ cudaError_t chol_inv(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, bool
     const size_t sq = (size_t)bp * bp;
     const size_t packed = (size_t)bp * (bp + 1) / 2;
     if (scratch_doubles < sq) return cudaErrorInvalidValue;
-    // a Gram wider than 128: blocked over many CTAs (one CTA's shared memory
-    // does not hold an FP64 one, and one SM's FP64 rate would bound it)
-    if (bp > 128) return chol_inv_blocked<T>(cx, G, bp, p, R, Rinv, tol, scratch, scratch_doubles, fp64_factor);
+    // a Gram of 128 or more columns: blocked over many CTAs (one CTA's shared
+    // memory does not hold a wide FP64 one, and one SM's FP64 rate bounds it)
+    if (bp >= 128) return chol_inv_blocked<T>(cx, G, bp, p, R, Rinv, tol, scratch, scratch_doubles, fp64_factor);
     if (fp64_factor) {
         const int in_smem = (sizeof(double) * packed <= 200 * 1024) ? 1 : 0;
         k_cholesky<double><<<1, 256, in_smem ? sizeof(double) * packed : 0, cx.stream>>>(G, bp, p, R, in_smem,

@@ -243,6 +243,15 @@ int rqb_backward(rqb_handle h, const void* dL_dX, int64_t ldg, void* dL_dA, int6
  * factorization, bad r or leading dimension), RQB_ERR_NONFINITE, RQB_ERR_OOM. */
 int rqb_svd(rqb_handle h, int64_t r, void* U, int64_t ldu, double* S, void* Vt, int64_t ldvt);
 
+/* Self-test of the failure path of the tensor-core kernels: every wait of
+ * theirs on an mbarrier (a TMA copy, an MMA, a peer warp) is bounded (2 s of
+ * %globaltimer or 2^28 polls); on expiry the kernel drains its copies and
+ * MMAs, frees tensor memory and records RQB_ERR_TIMEOUT.  This call runs one
+ * such wait on a barrier that nothing completes and returns its status
+ * (RQB_ERR_TIMEOUT when the limit works), with the time waited in
+ * *waited_ms (may be NULL).  The handle and the CUDA context stay usable. */
+int rqb_wait_selftest(rqb_handle h, double* waited_ms);
+
 /* Statistics of the last call on this handle. */
 int rqb_get_stats(rqb_handle h, rqb_stats* out);
 

@@ -1628,6 +1628,22 @@ extern "C" int rqb_svd(rqb_handle h, int64_t r, void* U, int64_t ldu, double* S,
     return finish(h, rc);
 }
 
+extern "C" int rqb_wait_selftest(rqb_handle h, double* waited_ms) {
+    if (!h) return RQB_ERR_INVALID;
+    if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
+    Scal sc = scalars(h);
+    Ctx cx;
+    cx.stream = h->stream; cx.num_sms = h->num_sms; cx.st = sc.st;
+    unsigned long long* dns = reinterpret_cast<unsigned long long*>(sc.s + 15);
+    RQB_CK(cudaMemsetAsync(sc.st, 0, sizeof(DevState), h->stream));
+    RQB_CK(tc::wait_selftest(cx, dns));
+    unsigned long long ns = 0;
+    RQB_CK(cudaMemcpyAsync(&ns, dns, sizeof(ns), cudaMemcpyDeviceToHost, h->stream));
+    const int err = read_state(h, sc);
+    if (waited_ms) *waited_ms = (double)ns * 1e-6;
+    return finish(h, err);
+}
+
 extern "C" int rqb_backward(rqb_handle h, const void* dL_dX, int64_t ldg, void* dL_dA, int64_t ldda) {
     if (!h) return RQB_ERR_INVALID;
     if (!h->have_factor || !dL_dX || !dL_dA || ldg < h->last_m || ldda < h->last_m) return finish(h, RQB_ERR_INVALID);

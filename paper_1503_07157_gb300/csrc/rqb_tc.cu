@@ -1142,6 +1142,26 @@ __global__ void k_reduce_project16(const float* __restrict__ part, long long U, 
     }
 }
 
+// Self-test of the bounded wait: one thread waits on an mbarrier that no
+// thread or copy ever completes; the wait gives up after its limit and the
+// kernel records RQB_ERR_TIMEOUT and the time it waited.
+__global__ void k_wait_selftest(DevState* st, unsigned long long* waited_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long t0 = globaltimer_ns();
+        const bool ok = mbar_wait(&bar, 0, &abort_flag);
+        *waited_ns = globaltimer_ns() - t0;
+        if (!ok) record_error(st, RQB_ERR_TIMEOUT);
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1593,6 +1613,12 @@ cudaError_t reproject(Ctx& cx, const float* Qbar, long long ldq, long long m, lo
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return sketch_sub(cx, Qbar, ldq, m, kprev, w.Om, w.ldom, np, Y, ldy, Y, w.part, w.part_cap);
+}
+
+cudaError_t wait_selftest(Ctx& cx, unsigned long long* waited_ns) {
+    k_wait_selftest<<<1, 32, 0, cx.stream>>>(cx.st, waited_ns);
+    cx.launches++;
+    return cudaGetLastError();
 }
 
 }  // namespace tc

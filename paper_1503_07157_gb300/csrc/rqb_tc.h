@@ -137,5 +137,9 @@ cudaError_t update16(Ctx& cx, const __nv_bfloat16* Wsrc, long long ldws, __nv_bf
                      const __nv_bfloat16* Bs, const __nv_bfloat16* Bsl, int np, double* sq_part, int sq_cap,
                      double* sq_out);
 
+// One bounded mbarrier wait that nothing completes (device pointer
+// waited_ns receives the wait's duration); records RQB_ERR_TIMEOUT in cx.st.
+cudaError_t wait_selftest(Ctx& cx, unsigned long long* waited_ns);
+
 }  // namespace tc
 }  // namespace rqb

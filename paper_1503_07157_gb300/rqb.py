@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
             "rqb_factor_batched": [P, i64, P, P, P, P, P, i64, u64, P, P, P, P, P, P],
             "rqb_backward": [P, P, i64, P, i64],
             "rqb_svd": [P, i64, P, i64, Pd, P, i64],
+            "rqb_wait_selftest": [P, Pd],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -267,6 +268,12 @@ class Handle:
         lib().rqb_get_stats(self._h, ctypes.byref(st))
         import numpy as np
         return U, np.array(S[:], dtype=np.float64), Vt, int(st.svd_sweeps)
+
+    def rqb_wait_selftest(self):
+        """Run the bounded-wait self-test: returns (status, waited_ms)."""
+        w = ctypes.c_double()
+        rc = lib().rqb_wait_selftest(self._h, ctypes.byref(w))
+        return rc, float(w.value)
 
     def rqb_factor_batched(self, As: list, eps: list, b: int, seed: int = 0):
         """As: column-major FP32 device matrices.  Returns [(Q view, B view, k, status)]."""

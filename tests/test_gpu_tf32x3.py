@@ -247,3 +247,16 @@ def test_sketch_long_reduction_is_unbiased(orc, htc):
           "omega mismatch", diff.mean())
     assert np.linalg.norm(Yg - Yo) <= 2e-6 * np.linalg.norm(Yo)
     assert abs(np.sum((Yg - Yo) * Yo)) <= 1e-6 * np.sum(Yo * Yo)
+
+
+def test_bounded_wait_times_out_and_context_survives(rqb_lib):
+    """The failure path of the tensor-core kernels: a wait on an mbarrier that
+    nothing completes gives up after its 2 s limit with RQB_ERR_TIMEOUT, and the
+    same handle then factors normally."""
+    with rqb_lib.Handle(torch.float32, prec=rqb_lib.RQB_PREC_TF32X3) as h:
+        rc, ms = h.rqb_wait_selftest()
+        assert rc == rqb_lib.RQB_ERR_TIMEOUT
+        assert 1500.0 <= ms <= 4000.0
+        A = torch.randn(600, 400, device="cuda").t().contiguous().t()
+        _, _, k, rc = h.rqb_factor(A, 0.5 * float(A.norm()), 32, 0)
+        assert rc == rqb_lib.RQB_OK and k > 0

@@ -309,6 +309,17 @@ int orc_randqb_b_store(const double* A, int64_t m, int64_t n, int64_t lda,
     const double normA2 = frob2(m, n, W, m);
     double E = normA2;
     const double eps2 = eps * eps;
+    /* ||A||_F <= eps already (e.g. A = 0): the empty factorization, k = 0,
+     * meets the tolerance of Sec. 1.1; the figure's first panel would be the
+     * orthonormalisation of a zero (or negligible) sketch. */
+    if (!fixed_rank && normA2 <= eps2) {
+        res->k = 0;
+        res->blocks = 0;
+        res->normA2 = normA2;
+        res->status = 0;
+        free(W);
+        return 0;
+    }
 
     double* Om = (double*)malloc(sizeof(double) * (size_t)n * (size_t)b);
     double* Y = (double*)malloc(sizeof(double) * (size_t)m * (size_t)b);

@@ -496,6 +496,7 @@ int factor_tc(rqb_handle h, const float* A, int64_t m, int64_t n, int64_t lda, d
     int blocks = 0, direct = 0;
     int status = RQB_OK;
     bool converged = false;
+    bool empty_exit = false;
 
     // A as the first W: read in place when TMA can address it, else copied
     const float* Wsrc = A;
@@ -532,6 +533,13 @@ int factor_tc(rqb_handle h, const float* A, int64_t m, int64_t n, int64_t lda, d
         RQB_CK(launch_stop_after_b(cx, sc.s + 1, eps2, kBandTf32x3, fixed));
         h->timer.end(h->stream);
         int err = read_state(h, sc);
+        if (blocks == 0 && !fixed && h->hstate->normA2 <= eps2) {
+            // ||A||_F <= eps already: the empty factorization meets the
+            // tolerance (whatever the degenerate first panel did)
+            empty_exit = true;
+            converged = true;
+            break;
+        }
         if (err != RQB_OK) { status = err; break; }
         const int flag = h->hstate->flag;
         if (blocks < RQB_MAX_TRACKED_BLOCKS) {
@@ -563,7 +571,7 @@ int factor_tc(rqb_handle h, const float* A, int64_t m, int64_t n, int64_t lda, d
         RQB_CK(tc::sketch(cx, W, ldw, m, n, ta.Om, ta.ldom, bp, ar.Y, m, ta.part, ta.part_cap));
         h->timer.end(h->stream);
     }
-    if (status == RQB_OK) {
+    if (status == RQB_OK && !empty_exit) {
         int err = read_state(h, sc);
         if (err != RQB_OK) status = err;
     }
@@ -705,6 +713,12 @@ int factor_bf16(rqb_handle h, const __nv_bfloat16* A, int64_t m, int64_t n, int6
         RQB_CK(launch_stop_direct(cx, sc.s + 2, eps2, true));
         h->timer.end(h->stream);
         const int err = read_state(h, sc);
+        if (blocks == 0 && !fixed && h->hstate->normA2 <= eps2) {
+            // ||A||_F <= eps already: the empty factorization meets the
+            // tolerance (whatever the degenerate first panel did)
+            converged = true;
+            break;
+        }
         if (err != RQB_OK) { status = err; break; }
         if (blocks < RQB_MAX_TRACKED_BLOCKS) {
             h->stats.E[blocks] = h->hstate->E;
@@ -771,6 +785,7 @@ int factor_impl(rqb_handle h, const T* A, int64_t m, int64_t n, int64_t lda, dou
     int blocks = 0, direct = 0;
     int status = RQB_OK;
     bool converged = false;
+    bool empty_exit = false;
 
     // block 1 sketch: Y = A Omega_1 with ||A||_F^2 on the same read
     int p = (int)std::min<int64_t>(b, kcap);
@@ -817,6 +832,13 @@ int factor_impl(rqb_handle h, const T* A, int64_t m, int64_t n, int64_t lda, dou
         RQB_CK(launch_stop_after_b(cx, sc.s + 1, eps2, tau_rel, fixed));
         h->timer.end(h->stream);
         int err = read_state(h, sc);
+        if (blocks == 0 && !fixed && h->hstate->normA2 <= eps2) {
+            // ||A||_F <= eps already: the empty factorization meets the
+            // tolerance (whatever the degenerate first panel did)
+            empty_exit = true;
+            converged = true;
+            break;
+        }
         if (err != RQB_OK) { status = err; break; }
         const int flag = h->hstate->flag;
         if (blocks < RQB_MAX_TRACKED_BLOCKS) {
@@ -854,7 +876,7 @@ int factor_impl(rqb_handle h, const T* A, int64_t m, int64_t n, int64_t lda, dou
         }
         if (k >= kcap) break;
     }
-    if (status == RQB_OK) {
+    if (status == RQB_OK && !empty_exit) {
         int err = read_state(h, sc);
         if (err != RQB_OK) status = err;
     }

@@ -672,6 +672,11 @@ __global__ void __launch_bounds__(NT, 1) k_mat(const GMat* __restrict__ mats, GS
             g.blocks = 0;
             g.active = isfinite(nrm) ? 1 : 0;
             g.status = isfinite(nrm) ? RQB_NOT_CONVERGED : RQB_ERR_NONFINITE;
+            if (isfinite(nrm) && nrm <= d.eps2) {
+                // ||A||_F <= eps already: the empty factorization (k = 0)
+                g.active = 0;
+                g.status = RQB_OK;
+            }
             st[t] = g;
         }
         return;

@@ -84,3 +84,21 @@ def test_batched_rejects_bad_arguments(rqb_lib):
         A = to_dev(np.ones((8, 4)), torch.float32)
         with pytest.raises(rqb_lib.RqbError):
             h.rqb_factor_batched([A], [1.0], 33)
+
+
+def test_batched_zero_matrix_empty_factorization(rqb_lib):
+    """A zero matrix (||A|| = 0 <= eps) in the batch gets k = 0 and RQB_OK; the
+    others are unaffected."""
+    mats = _batch(seed=3)[:3]
+    m0, n0 = mats[1][0].shape
+    mats[1] = (np.zeros((m0, n0)), 0.0)
+    devs = [to_dev(A, torch.float32) for A, _ in mats]
+    with rqb_lib.Handle(torch.float32) as h:
+        out = h.rqb_factor_batched(devs, [e for _, e in mats], 32, seed=4)
+        # the factors live in the handle's buffers: read them before it closes
+        fac = [(to_np(Q), to_np(B), k, st) for Q, B, k, st in out]
+    assert fac[1][2] == 0 and fac[1][3] == rqb_lib.RQB_OK
+    for i in (0, 2):
+        Q, B, k, st = fac[i]
+        assert st == rqb_lib.RQB_OK and k > 0
+        assert resid(mats[i][0], Q, B) <= mats[i][1] * (1 + 1e-4)

@@ -216,3 +216,8 @@ def test_randqb_bf16_vs_fp32_same_eps(orc, rqb_lib):
     assert abs(kb - kn) <= b
     assert resid(A, Qn, Bn) <= eps * (1 + 1e-4)
     assert resid(A, Qb, Bb) <= eps + _stored_gap_bound(st.D, float(np.sum(A * A)))
+
+
+def test_randqb_zero_matrix(rqb_lib):
+    Q, B, k, rc, st = _factor(rqb_lib, np.zeros((1000, 700)), 0.0, 128, 0)
+    assert rc == rqb_lib.RQB_OK and k == 0

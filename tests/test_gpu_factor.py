@@ -271,3 +271,16 @@ def test_power_scheme_without_inner_orth_adaptive(orc, rqb_lib):
     if k == ro.k:
         assert abs(resid(A, Q, B) - resid(A, ro.Q, ro.B)) <= 1e-9 * resid(A, ro.Q, ro.B)
     assert orth_err(Q) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_norm_within_tolerance_gives_empty_factorization(orc, rqb_lib, dtype):
+    """||A||_F <= eps before any block (A = 0 included): k = 0 and RQB_OK, as
+    the oracle; a larger A with the same eps still factors."""
+    Q, B, k, rc, st = _factor(rqb_lib, np.zeros((300, 200)), 0.0, 32, dtype)
+    assert rc == rqb_lib.RQB_OK and k == 0
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((300, 200))
+    nA = np.linalg.norm(A)
+    Q, B, k, rc, st = _factor(rqb_lib, A, 1.01 * nA, 32, dtype)
+    assert rc == rqb_lib.RQB_OK and k == 0 == orc.randqb_b(A, 1.01 * nA, 32).k

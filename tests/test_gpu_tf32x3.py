@@ -260,3 +260,10 @@ def test_bounded_wait_times_out_and_context_survives(rqb_lib):
         A = torch.randn(600, 400, device="cuda").t().contiguous().t()
         _, _, k, rc = h.rqb_factor(A, 0.5 * float(A.norm()), 32, 0)
         assert rc == rqb_lib.RQB_OK and k > 0
+
+
+def test_randqb_zero_matrix(rqb_lib):
+    """A = 0: the empty factorization (k = 0, RQB_OK), not a breakdown of the
+    zero sketch."""
+    Q, B, k, rc, st = _factor(rqb_lib, np.zeros((1000, 700)), 0.0, 128, 0)
+    assert rc == rqb_lib.RQB_OK and k == 0

@@ -258,3 +258,18 @@ def test_golden_unblocked_power_floor_vs_blocked(orc):
         assert eb < 1e-8                           # blocked reaches full precision
         assert eb < 1e-3 * eu
     assert g["floor"]["1"] == 1e-5 and g["floor"]["2"] == 1e-3
+
+
+def test_norm_within_tolerance_gives_empty_factorization(orc):
+    """||A||_F <= eps before any block: k = 0 meets the tolerance (A = 0 included,
+    whose sketch has no orthonormal basis)."""
+    A = np.zeros((50, 40))
+    r = orc.randqb_b(A, 0.0, 8, seed=1)
+    assert r.k == 0 and r.blocks == 0 and r.status == 0
+    rng = np.random.default_rng(3)
+    A = 1e-3 * rng.standard_normal((60, 30))
+    nA = np.linalg.norm(A)
+    r = orc.randqb_b(A, 1.01 * nA, 8, seed=1)
+    assert r.k == 0 and r.status == 0
+    r = orc.randqb_b(A, 0.5 * nA, 8, seed=1)
+    assert r.k >= 8 and r.status == 0

@@ -218,10 +218,10 @@ def alu_peak_tflops(dtype: str, num_sms: int, sm_mhz: float) -> float:
 # workload's dominant kernel was captured only on a smaller case).
 #   fp32: k_gemm_nn sketch, 20000 x 16000, dram read 1.295 GB + write 0.145 GB
 # DRAM bytes (read + write) per launch of each workload's dominant kernel from
-# ncu captures (profiles/); bf16: k_update16 captured at 8192 x 8192 (247 MB)
-# scaled by the 8x elements of a 32768 x 16384 launch; None where the kernel
-# changed since its last capture.
-NCU_TRAFFIC = {"fp32": 1.440e9, "fp64": None, "mixed": None, "bf16": 1.98e9}
+# ncu captures (profiles/); mixed and bf16: k_update / k_update16 captured at
+# 8192 x 8192 (538.7 MB / 247 MB) scaled by the 8x elements of a
+# 32768 x 16384 launch; None where no capture of the current kernel exists.
+NCU_TRAFFIC = {"fp32": 1.440e9, "fp64": None, "mixed": 4.31e9, "bf16": 1.98e9}
 
 
 def oracle_modes(w: dict) -> tuple[int, int]:

@@ -539,11 +539,25 @@ def run_batched(args, w: dict, rank: int, world: int, dist, do_e2e: bool = True)
     torch.cuda.synchronize()
     loop_ms = (time.perf_counter() - t0) * 1e3
     h1.close()
+    # the byte model of the schedule, beside the ALU bound: per matrix of s
+    # blocks, A crosses HBM (3 s - 1) times (first sketch, each projection,
+    # each update read + write) and block i reads Qbar (i - 1) b columns twice
+    # for the re-projection
+    model_bytes = 0.0
+    for c, k in zip(cases, ks):
+        sb = (k + b - 1) // b
+        model_bytes += 4.0 * ((3 * sb - 1) * c.m * c.n + 2.0 * c.m * b * sb * (sb - 1) / 2.0)
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_gbs = model_bytes / (ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "kernel": "grouped batched kernels (k_rows_update, k_cols, k_rows, k_mat), whole batch",
                 "achieved": round(achieved, 3),
                 "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
                 "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
-                               f"{float(peaks.get('sm_max_mhz', 2070.0)):.0f} MHz"}
+                               f"{float(peaks.get('sm_max_mhz', 2070.0)):.0f} MHz",
+                "byte_model": {"bytes_per_step": model_bytes, "achieved_gbs": round(hbm_gbs, 1),
+                               "peak_gbs": hbm_peak, "frac": round(hbm_gbs / hbm_peak, 4),
+                               "note": "(3s-1) crossings of each A plus the re-projection reads; "
+                                       "the ALU bound is the binding one (16 flop/B > ridge)"}}
     if not do_e2e:
         h.close()
         return dict(value=aggregate_value(F, world, ms), ms=ms, F=F, clocks=clk, roofline=roofline, e2e=None,

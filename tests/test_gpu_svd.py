@@ -101,3 +101,25 @@ def test_svd_invalid(rqb_lib):
         _, _, k, _ = h.rqb_factor(A, 0.5 * float(A.norm()), 32, 0)
         with pytest.raises(rqb_lib.RqbError):
             h.rqb_svd(k + 1)
+
+
+def test_svd_bf16_handle(orc, rqb_lib):
+    """BF16 storage handle: Q and B are FP32, so rqb_svd runs as for FP32; its
+    leading singular values match the planted spectrum to the BF16 storage
+    level and the factors rebuild the handle's own Q B."""
+    m, n, b = 2048, 1300, 128
+    s = inputs.spectrum_exp(min(m, n), 150)
+    A = orc.round_bf16_array(inputs.usv(m, n, s, seed=m + n))
+    eps = 1e-2 * np.linalg.norm(A)
+    with rqb_lib.Handle(torch.bfloat16) as h:
+        Qd, Bd, k, rc = h.rqb_factor(to_dev(A, torch.bfloat16), eps, b, 3)
+        assert rc == rqb_lib.RQB_OK
+        Q, B = to_np(Qd), to_np(Bd)
+        U, S, Vt, _ = h.rqb_svd(k)
+        U, Vt = to_np(U), to_np(Vt)
+    sv = np.linalg.svd(A, compute_uv=False)
+    assert orth_err(U) <= 1e-5
+    QB = Q @ B
+    assert np.linalg.norm((U * S) @ Vt - QB) <= 1e-5 * np.linalg.norm(QB)
+    # top singular values: BF16 residual roundings perturb them by ~2^-9 sigma_1
+    assert np.all(np.abs(S[:k // 4] - sv[:k // 4]) <= 2.0 ** -8 * sv[0])

@@ -126,9 +126,13 @@ __global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G
         __syncthreads();
     } else {
         // FP64: the FP64 pipes of all four SM sub-partitions, tile in shared
-        // memory; step j pivots, scales column j of L and row j of L^{-1},
-        // updates the trailing part of L and eliminates column j from the rows
-        // of L^{-1} below j
+        // memory, one barrier per pivot.  The elimination runs unscaled: D
+        // keeps the Schur complements and Di the unscaled rows of L^{-1}
+        // (step j subtracts D[r][j] D[c][j] / pivot_j and D[r][j] Di[j][c] /
+        // pivot_j), and the thread that updates D[j+1][j+1] -- entry 0 of
+        // the dense numbering, thread 0 -- takes the next pivot at once.  The
+        // factors are scaled by pivot^{-1/2} at the end.
+        __shared__ W invp[kNb];
         for (int e = tid; e < kNb * kNb; e += 256) {
             const int r = e & (kNb - 1), c = e / kNb;
             D[r][c] = (r >= c) ? (W)G[(k0 + r) + (int64_t)(k0 + c) * bp] : W(0);
@@ -136,27 +140,22 @@ __global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G
         }
         if (tid == 0) fail = 0;
         __syncthreads();
+        auto take_pivot = [&](int j) {
+            W d = D[j][j];
+            if (!((double)d > tol * dG[k0 + j]) || !isfinite((double)d)) {
+                fail = 1;
+                d = W(1);
+                D[j][j] = d;
+            }
+            const W y = rsqrt_fp64(d);
+            inv[j] = y;
+            invp[j] = y * y;
+        };
+        if (tid == 0) take_pivot(0);
+        __syncthreads();
         for (int j = 0; j < kNb; ++j) {
-            if (tid == 0) {
-                W d = D[j][j];
-                if (!((double)d > tol * dG[k0 + j]) || !isfinite((double)d)) {
-                    fail = 1;
-                    d = W(1);
-                }
-                const W y = rsqrt_fp64(d);
-                D[j][j] = d * y;
-                inv[j] = y;
-            }
-            __syncthreads();
-            const W ij = inv[j];
-            if (tid < kNb) {
-                if (tid > j) D[tid][j] *= ij;
-            } else if (tid < 2 * kNb) {
-                if (tid - kNb <= j) Di[j][tid - kNb] *= ij;
-            }
-            __syncthreads();
-            // only the active entries, densely numbered, so that every FP64
-            // instruction issued has its lanes busy: the trailing triangle
+            const W ip = invp[j];
+            // the active entries, densely numbered: the trailing triangle
             // j < c <= r < 32 (nt entries), then the block j < r < 32, c <= j
             const int nrem = kNb - 1 - j;
             const int nt = nrem * (nrem + 1) / 2, nd = nrem * (j + 1);
@@ -167,15 +166,24 @@ __global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G
                     while ((u + 1) * (u + 2) / 2 <= q) ++u;
                     const int v = q - u * (u + 1) / 2;
                     const int r = j + 1 + u, c = j + 1 + v;
-                    D[r][c] -= D[r][j] * D[c][j];
+                    D[r][c] -= D[r][j] * D[c][j] * ip;
+                    if (q == 0) take_pivot(j + 1);
                 } else {
                     const int q2 = q - nt;
                     const int r = j + 1 + q2 / (j + 1), c = q2 % (j + 1);
-                    Di[r][c] -= D[r][j] * Di[j][c];
+                    Di[r][c] -= D[r][j] * Di[j][c] * ip;
                 }
             }
             __syncthreads();
         }
+        for (int e = tid; e < kNb * kNb; e += 256) {
+            const int r = e & (kNb - 1), c = e / kNb;
+            if (r >= c) {
+                D[r][c] *= inv[c];
+                Di[r][c] *= inv[r];
+            }
+        }
+        __syncthreads();
     }
     if (blockIdx.x == 0) {
         for (int e = tid; e < kNb * kNb; e += 256) {

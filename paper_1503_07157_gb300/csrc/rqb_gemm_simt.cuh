@@ -262,6 +262,172 @@ k_gemm_nn(int64_t m, int64_t K, int64_t ksplit, int nc, int nout,
 }
 
 // ---------------------------------------------------------------------------
+// NN with a row-major C, fed by cp.async: the X and C tiles of the next
+// ST - 1 reduction chunks are in flight while the current one is multiplied,
+// so the loads need no staging registers and their latency is covered by
+// several chunks of FMAs instead of one.  Same contract as k_gemm_nn with
+// C_ROWMAJOR, plus: X, C 16-byte aligned, ldx and csk multiples of 16 bytes
+// (the host checks).  Elements outside the matrices are zero-filled by the
+// copy itself (src-size below 16 bytes).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <typename T, int BM, int BN, int BK, int ST>
+struct GemmNNPipe {
+    static constexpr int TM = SimtTile<T>::TM, TN = SimtTile<T>::TN;
+    static constexpr int NT = (BM / TM) * (BN / TN);
+    static constexpr int V = Vec16<T>::N;
+    static constexpr int XVEC = BM * BK / V, CVEC = BK * BN / V;
+    static constexpr int XPER = (XVEC + NT - 1) / NT, CPER = (CVEC + NT - 1) / NT;
+    static constexpr size_t SMEM = sizeof(T) * (size_t)ST * BK * (BM + BN);
+    static constexpr int MINB = (sizeof(T) == 4 && NT >= 256) ? 2 : 1;
+};
+
+template <typename T, int BM, int BN, int BK, int ST>
+__global__ void __launch_bounds__(GemmNNPipe<T, BM, BN, BK, ST>::NT, GemmNNPipe<T, BM, BN, BK, ST>::MINB)
+k_gemm_nn_pipe(int64_t m, int64_t K, int64_t ksplit, int nc, int nout,
+               const T* __restrict__ X, int64_t ldx, const T* __restrict__ C, int64_t csk,
+               T* Out, int64_t ldo, int64_t out_zstride,
+               const T* Yin, int64_t ldyin, T alpha, T beta, double* __restrict__ nrm_part) {
+    using G = GemmNNPipe<T, BM, BN, BK, ST>;
+    constexpr int TM = G::TM, TN = G::TN, NT = G::NT, V = G::V;
+    constexpr int HM = TM / 2, HN = TN / 2;
+    extern __shared__ __align__(16) unsigned char nn_smem[];
+    T* As = reinterpret_cast<T*>(nn_smem);   // [ST][BK][BM]
+    T* Bs = As + (size_t)ST * BK * BM;        // [ST][BK][BN]
+
+    const int tid = threadIdx.x;
+    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+    const int64_t r0 = (int64_t)blockIdx.x * BM;
+    const int j0 = blockIdx.y * BN;
+    const int64_t kbeg = (int64_t)blockIdx.z * ksplit;
+    const int64_t kend = (kbeg + ksplit < K) ? kbeg + ksplit : K;
+    const int64_t nch = (kend > kbeg) ? (kend - kbeg + BK - 1) / BK : 0;
+
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+    const bool do_norm = (nrm_part != nullptr) && (blockIdx.y == 0);
+    double nacc = 0.0;
+
+    // chunk c (K columns kbeg + c*BK ..) into stage c % ST
+    auto issue = [&](int64_t c) {
+        const int s = (int)(c % ST);
+        const int64_t k0 = kbeg + c * BK;
+#pragma unroll
+        for (int t = 0; t < G::XPER; ++t) {
+            const int v = tid + t * NT;
+            if (v < G::XVEC) {
+                const int kk = v / (BM / V), rr = (v % (BM / V)) * V;
+                const int64_t k = k0 + kk, r = r0 + rr;
+                int64_t valid = (k < kend) ? m - r : 0;
+                valid = valid < 0 ? 0 : (valid > V ? V : valid);
+                const T* src = (valid > 0) ? X + r + k * ldx : X;
+                cp_async16(As + ((size_t)s * BK + kk) * BM + rr, src, (int)(valid * sizeof(T)));
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < G::CPER; ++t) {
+            const int v = tid + t * NT;
+            if (v < G::CVEC) {
+                const int kk = v / (BN / V), jj = (v % (BN / V)) * V;
+                const int64_t k = k0 + kk;
+                const int j = j0 + jj;
+                int valid = (k < kend) ? nc - j : 0;
+                valid = valid < 0 ? 0 : (valid > V ? V : valid);
+                const T* src = (valid > 0) ? C + k * csk + j : C;
+                cp_async16(Bs + ((size_t)s * BK + kk) * BN + jj, src, valid * (int)sizeof(T));
+            }
+        }
+    };
+
+#pragma unroll
+    for (int s = 0; s < ST - 1; ++s) {
+        if (s < nch) issue(s);
+        cp_async_commit();
+    }
+    for (int64_t c = 0; c < nch; ++c) {
+        cp_async_wait<ST - 2>();
+        __syncthreads();   // chunk c landed for every thread; stage (c - 1) % ST is free
+        if (c + ST - 1 < nch) issue(c + ST - 1);
+        cp_async_commit();
+        const T* as = As + (size_t)(c % ST) * BK * BM;
+        const T* bs = Bs + (size_t)(c % ST) * BK * BN;
+        if (do_norm) {   // this thread's own vectors of the X chunk, each element once
+#pragma unroll
+            for (int t = 0; t < G::XPER; ++t) {
+                const int v = tid + t * NT;
+                if (v < G::XVEC) {
+                    const int kk = v / (BM / V), rr = (v % (BM / V)) * V;
+                    T xv[V];
+                    lds_vec<T, V>(xv, as + kk * BM + rr);
+                    T sq = T(0);
+#pragma unroll
+                    for (int i = 0; i < V; ++i) sq = fma(xv[i], xv[i], sq);
+                    nacc += (double)sq;
+                }
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[TM], b[TN];
+            T a0[HM], a1[HM], b0[HN], b1[HN];
+            lds_vec<T, HM>(a0, as + kk * BM + ty * HM);
+            lds_vec<T, HM>(a1, as + kk * BM + BM / 2 + ty * HM);
+            lds_vec<T, HN>(b0, bs + kk * BN + tx * HN);
+            lds_vec<T, HN>(b1, bs + kk * BN + BN / 2 + tx * HN);
+#pragma unroll
+            for (int i = 0; i < HM; ++i) { a[i] = a0[i]; a[HM + i] = a1[i]; }
+#pragma unroll
+            for (int j = 0; j < HN; ++j) { b[j] = b0[j]; b[HN + j] = b1[j]; }
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+    }
+    cp_async_wait<0>();
+
+    if (nrm_part != nullptr) {   // uniform per CTA
+        __shared__ double red[NT / 32];
+        double v = nacc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) red[tid >> 5] = v;
+        __syncthreads();
+        if (tid == 0 && do_norm) {
+            double t = 0.0;
+            for (int w = 0; w < NT / 32; ++w) t += red[w];
+            nrm_part[blockIdx.x + (int64_t)gridDim.x * blockIdx.z] = t;
+        }
+    }
+
+    T* out = Out + (int64_t)blockIdx.z * out_zstride;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int64_t r = r0 + ((i < HM) ? (ty * HM + i) : (BM / 2 + ty * HM + (i - HM)));
+        if (r >= m) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int c = j0 + ((j < HN) ? (tx * HN + j) : (BN / 2 + tx * HN + (j - HN)));
+            if (c >= nout) continue;
+            T v = alpha * acc[i][j];
+            if (beta != T(0)) v = fma(beta, Yin[r + (int64_t)c * ldyin], v);
+            out[r + (int64_t)c * ldo] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // TN: Out[z] (p x q) = sum over rows r of split z of X(r, p) * Y(r, q).
 // X is m x pn (ldx), Y is m x qn (ldy); rows >= m and columns beyond pn/qn
 // read as zero; outputs with p < pn, q < qn are written, type Acc.

@@ -18,6 +18,13 @@
 #include "rqb_engine.h"
 #include "rqb_gemm_simt.cuh"
 
+#ifndef RQB_NN_PIPE_BK_F32
+#define RQB_NN_PIPE_BK_F32 8
+#endif
+#ifndef RQB_NN_PIPE_ST_F32
+#define RQB_NN_PIPE_ST_F32 4
+#endif
+
 namespace rqb {
 
 // ---------------------------------------------------------------------------
@@ -594,18 +601,39 @@ template <typename T> struct NNTile;
 template <> struct NNTile<float> { static constexpr int BK = 8; };
 template <> struct NNTile<double> { static constexpr int BK = 8; };
 
+// Pipelined NN (row-major C, cp.async-fed): reduction chunk and stage count.
+template <typename T> struct NNPipeCfg;
+template <> struct NNPipeCfg<float> { static constexpr int BK = RQB_NN_PIPE_BK_F32, ST = RQB_NN_PIPE_ST_F32; };
+template <> struct NNPipeCfg<double> { static constexpr int BK = 8, ST = 4; };
+
 template <typename T, int BM, int BN, bool ROWC>
 static cudaError_t nn_launch(Ctx& cx, const NNArgs<T>& a) {
     using G = GemmNN<T, BM, BN, NNTile<T>::BK, ROWC>;
+    using P = GemmNNPipe<T, BM, BN, NNPipeCfg<T>::BK, NNPipeCfg<T>::ST>;
     using KernT = void (*)(int64_t, int64_t, int64_t, int, int, const T*, int64_t, const T*, int64_t, int64_t, T*,
                            int64_t, int64_t, const T*, int64_t, T, T, double*);
+    using KernP = void (*)(int64_t, int64_t, int64_t, int, int, const T*, int64_t, const T*, int64_t, T*, int64_t,
+                           int64_t, const T*, int64_t, T, T, double*);
     KernT kern = k_gemm_nn<T, BM, BN, NNTile<T>::BK, ROWC>;
-    int threads = G::NT;
-    size_t dsmem = 0;
-    int64_t kalign = NNTile<T>::BK;
+    KernP kernp = k_gemm_nn_pipe<T, BM, BN, NNPipeCfg<T>::BK, NNPipeCfg<T>::ST>;
+    constexpr int V = Vec16<T>::N;
+    // the pipelined kernel needs 16-byte aligned vectors of X and of C's rows
+    const bool pipe = ROWC && ((uintptr_t)a.X % 16 == 0) && ((uintptr_t)a.C % 16 == 0) && (a.ldx % V == 0) &&
+                      (a.csk % V == 0);
+    int threads = pipe ? P::NT : G::NT;
+    size_t dsmem = pipe ? P::SMEM : 0;
+    if (pipe) {
+        static bool attr_set = false;   // one instantiation per tile shape
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(kernp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+    }
+    const int64_t kalign = pipe ? NNPipeCfg<T>::BK : NNTile<T>::BK;
     const int64_t mt = (a.m + BM - 1) / BM;
     const int nt = (std::max(a.nc, a.nout) + BN - 1) / BN;
-    const int slots = cx.num_sms * occupancy(kern, threads, dsmem);
+    const int slots = cx.num_sms * (pipe ? occupancy(kernp, threads, dsmem) : occupancy(kern, threads, dsmem));
     // FP64 pipes are 64x slower than FP32 ones on this part: spread FP64
     // products over more CTAs by splitting shorter reductions
     constexpr int64_t kmin = (sizeof(T) == 8) ? 64 : 256;
@@ -623,14 +651,20 @@ static cudaError_t nn_launch(Ctx& cx, const NNArgs<T>& a) {
     splits = (int)std::max<int64_t>(1, (a.K + ks - 1) / ks);
     if (a.nrm_part && mt * splits > a.nrm_cap) return cudaErrorInvalidValue;
     dim3 grid((unsigned)mt, (unsigned)nt, (unsigned)splits);
-    if (splits == 1) {
-        kern<<<grid, threads, dsmem, cx.stream>>>(a.m, a.K, ks, a.nc, a.nout, a.X, a.ldx, a.C, a.csk, a.csj, a.Out,
-                                                  a.ldo, 0, a.Yin, a.ldyin, a.alpha, a.beta, a.nrm_part);
-    } else {
-        // partial per split: m x (nt*BN), ld = m
-        kern<<<grid, threads, dsmem, cx.stream>>>(a.m, a.K, ks, a.nc, nt * BN, a.X, a.ldx, a.C, a.csk, a.csj, a.part,
-                                                  a.m, a.m * (int64_t)nt * BN, nullptr, 0, T(1), T(0), a.nrm_part);
-    }
+    // one split: the product goes straight to Out; else a partial per split (m x nt*BN, ld = m)
+    const bool one = (splits == 1);
+    T* out = one ? a.Out : a.part;
+    const int nout = one ? a.nout : nt * BN;
+    const int64_t ldo = one ? a.ldo : a.m, zs = one ? 0 : a.m * (int64_t)nt * BN;
+    const T* yin = one ? a.Yin : nullptr;
+    const int64_t ldyin = one ? a.ldyin : 0;
+    const T alpha = one ? a.alpha : T(1), beta = one ? a.beta : T(0);
+    if (pipe)
+        kernp<<<grid, threads, dsmem, cx.stream>>>(a.m, a.K, ks, a.nc, nout, a.X, a.ldx, a.C, a.csk, out, ldo, zs, yin,
+                                                   ldyin, alpha, beta, a.nrm_part);
+    else
+        kern<<<grid, threads, dsmem, cx.stream>>>(a.m, a.K, ks, a.nc, nout, a.X, a.ldx, a.C, a.csk, a.csj, out, ldo,
+                                                  zs, yin, ldyin, alpha, beta, a.nrm_part);
     cx.launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

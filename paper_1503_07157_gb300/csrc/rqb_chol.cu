@@ -41,17 +41,20 @@ __global__ void k_chol_init(double* __restrict__ G, int bp, int p, double* __res
     }
 }
 
-// 1 / sqrt(d) for d > 0 in FP64: the FP32 estimate refined by three Newton
-// steps y <- y (3 - d y^2) / 2 (each squares the relative error: 2^-23 ->
-// 2^-45 -> 2^-89), so the pivot's serial chain costs a few dependent FP64
-// multiply-adds instead of an FP64 square root and division.  Pivots outside
-// the FP32 range take the FP64 library route.
+// 1 / sqrt(d) for d > 0 in FP64: the FP32 estimate refined by two Newton
+// steps y <- y (3 - d y^2) / 2 (each about squares the relative error:
+// 2^-22 -> 2^-43 -> below the FP64 rounding), so the pivot's serial chain
+// costs a few dependent FP64 multiply-adds instead of an FP64 square root and
+// division.  Pivots outside the FP32 range (tested on the converted value,
+// on the FP32 pipe) take the FP64 library route.
 __device__ __forceinline__ double rsqrt_fp64(double d) {
-    if (!(d > 1e-36 && d < 1e36)) return 1.0 / sqrt(d);
-    double y = (double)rsqrtf((float)d);
+    const float df = (float)d;
+    const float e = rsqrtf(df);
+    if (!(df > 1e-36f && df < 1e36f)) return 1.0 / sqrt(d);
+    double y = (double)e;
     const double h = 0.5 * d;
 #pragma unroll
-    for (int it = 0; it < 3; ++it) y = y * fma(-h, y * y, 1.5);
+    for (int it = 0; it < 2; ++it) y = y * fma(-h, y * y, 1.5);
     return y;
 }
 
@@ -60,17 +63,16 @@ __device__ __forceinline__ double rsqrt_fp64(double d) {
 // pivot from lane j, scales column j, and applies the rank-1 update to the
 // trailing rows and the elimination to the rows of L^{-1} with values
 // broadcast by shuffles (fully unrolled, so the rows stay in registers).
+// Lane j tests pivot j against its threshold thr_lane (tol * G_jj rounded to
+// W); the elimination does not wait for the test, since a factorization with
+// a failed pivot is reported and discarded.
 template <typename W>
-__device__ __forceinline__ bool warp_chol32(W (&d)[kNb], W (&di)[kNb], int lane, const double* __restrict__ dG,
-                                            int k0, double tol) {
+__device__ __forceinline__ bool warp_chol32(W (&d)[kNb], W (&di)[kNb], int lane, W thr_lane) {
     bool fail = false;
 #pragma unroll 32
     for (int j = 0; j < kNb; ++j) {
-        W piv = __shfl_sync(0xffffffffu, d[j], j);
-        if (!((double)piv > tol * dG[k0 + j]) || !isfinite((double)piv)) {
-            fail = true;
-            piv = W(1);
-        }
+        const W piv = __shfl_sync(0xffffffffu, d[j], j);
+        if (lane == j && (!(piv > thr_lane) || !isfinite(piv))) fail = true;
         const W inv = W(1) / sqrt(piv);
         const bool me = (lane == j), below = (lane > j);
         d[j] = me ? piv * inv : (below ? d[j] * inv : d[j]);
@@ -93,7 +95,7 @@ __device__ __forceinline__ bool warp_chol32(W (&d)[kNb], W (&di)[kNb], int lane,
             }
         }
     }
-    return fail;
+    return __any_sync(0xffffffffu, fail);
 }
 
 template <typename W>
@@ -106,6 +108,16 @@ __global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G
     __shared__ int fail;
     const int tid = threadIdx.x;
     const int k0 = k * kNb;
+    // strip CTAs: row `srow` of G_ik is loaded before the factorization so
+    // that the loads overlap it (thread (rr, c) needs all 32 entries of its row)
+    const bool strip = blockIdx.x > 0;
+    const int bi = strip ? (blockIdx.x - 1) / (kNb / kStrip) : 0, sq = strip ? (blockIdx.x - 1) % (kNb / kStrip) : 0;
+    const int srow = (k + 1 + bi) * kNb + sq * kStrip + (tid >> 5);
+    W gv[kNb];
+    if (strip) {
+#pragma unroll
+        for (int t = 0; t < kNb; ++t) gv[t] = (W)G[srow + (int64_t)(k0 + t) * bp];
+    }
     if constexpr (sizeof(W) == 4) {
         // FP32: one warp, rows in registers
         if (tid < 32) {
@@ -115,7 +127,7 @@ __global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G
                 d[c] = (tid >= c) ? (W)G[(k0 + tid) + (int64_t)(k0 + c) * bp] : W(0);
                 di[c] = (tid == c) ? W(1) : W(0);
             }
-            const bool f = warp_chol32<W>(d, di, tid, dG, k0, tol);
+            const bool f = warp_chol32<W>(d, di, tid, (W)(tol * dG[k0 + tid]));
 #pragma unroll
             for (int c = 0; c < kNb; ++c) {
                 D[tid][c] = (tid >= c) ? d[c] : W(0);
@@ -125,53 +137,62 @@ __global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G
         }
         __syncthreads();
     } else {
-        // FP64: the FP64 pipes of all four SM sub-partitions, tile in shared
-        // memory, one barrier per pivot.  The elimination runs unscaled: D
-        // keeps the Schur complements and Di the unscaled rows of L^{-1}
-        // (step j subtracts D[r][j] D[c][j] / pivot_j and D[r][j] Di[j][c] /
-        // pivot_j), and the thread that updates D[j+1][j+1] -- entry 0 of
-        // the dense numbering, thread 0 -- takes the next pivot at once.  The
-        // factors are scaled by pivot^{-1/2} at the end.
+        // FP64: the tile in shared memory, one barrier per pivot.  The
+        // elimination runs unscaled: D keeps the Schur complements and Di the
+        // unscaled rows of L^{-1} (step j subtracts D[r][j] D[c][j] / pivot_j
+        // and D[r][j] Di[j][c] / pivot_j).  Thread 0 owns the serial chain:
+        // it updates D[j+1][j+1] (entry 0 of the dense numbering) and takes
+        // the next pivot at once, while warps 1..7 update the other active
+        // entries, so the chain never queues behind a warp's elimination
+        // work.  The factors are scaled by pivot^{-1/2} at the end.  A pivot
+        // that fails the test sets `fail` without stopping the chain (the
+        // factorization is then reported and discarded).
         __shared__ W invp[kNb];
+        __shared__ double thr[kNb];
         for (int e = tid; e < kNb * kNb; e += 256) {
             const int r = e & (kNb - 1), c = e / kNb;
             D[r][c] = (r >= c) ? (W)G[(k0 + r) + (int64_t)(k0 + c) * bp] : W(0);
             Di[r][c] = (r == c) ? W(1) : W(0);
         }
+        if (tid < kNb) thr[tid] = tol * dG[k0 + tid];
         if (tid == 0) fail = 0;
         __syncthreads();
-        auto take_pivot = [&](int j) {
-            W d = D[j][j];
-            if (!((double)d > tol * dG[k0 + j]) || !isfinite((double)d)) {
-                fail = 1;
-                d = W(1);
-                D[j][j] = d;
-            }
+        auto take_pivot = [&](int j, W d) {
+            if (!(d > thr[j]) || !isfinite(d)) fail = 1;
             const W y = rsqrt_fp64(d);
             inv[j] = y;
             invp[j] = y * y;
         };
-        if (tid == 0) take_pivot(0);
+        if (tid == 0) take_pivot(0, D[0][0]);
         __syncthreads();
+        constexpr int kWorkers = 256 - 32;
         for (int j = 0; j < kNb; ++j) {
             const W ip = invp[j];
             // the active entries, densely numbered: the trailing triangle
             // j < c <= r < 32 (nt entries), then the block j < r < 32, c <= j
             const int nrem = kNb - 1 - j;
             const int nt = nrem * (nrem + 1) / 2, nd = nrem * (j + 1);
-            for (int q = tid; q < nt + nd; q += 256) {
-                if (q < nt) {
-                    int u = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
-                    while (u * (u + 1) / 2 > q) --u;
-                    while ((u + 1) * (u + 2) / 2 <= q) ++u;
-                    const int v = q - u * (u + 1) / 2;
-                    const int r = j + 1 + u, c = j + 1 + v;
-                    D[r][c] -= D[r][j] * D[c][j] * ip;
-                    if (q == 0) take_pivot(j + 1);
-                } else {
-                    const int q2 = q - nt;
-                    const int r = j + 1 + q2 / (j + 1), c = q2 % (j + 1);
-                    Di[r][c] -= D[r][j] * Di[j][c] * ip;
+            if (tid == 0) {
+                if (nrem > 0) {
+                    const W l = D[j + 1][j];
+                    const W nv = fma(-(l * ip), l, D[j + 1][j + 1]);
+                    D[j + 1][j + 1] = nv;
+                    take_pivot(j + 1, nv);
+                }
+            } else if (tid >= 32) {
+                for (int q = 1 + (tid - 32); q < nt + nd; q += kWorkers) {
+                    if (q < nt) {
+                        int u = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
+                        while (u * (u + 1) / 2 > q) --u;
+                        while ((u + 1) * (u + 2) / 2 <= q) ++u;
+                        const int v = q - u * (u + 1) / 2;
+                        const int r = j + 1 + u, c = j + 1 + v;
+                        D[r][c] = fma(-(D[r][j] * ip), D[c][j], D[r][c]);
+                    } else {
+                        const int q2 = q - nt;
+                        const int r = j + 1 + q2 / (j + 1), c = q2 % (j + 1);
+                        Di[r][c] = fma(-(D[r][j] * ip), Di[j][c], Di[r][c]);
+                    }
                 }
             }
             __syncthreads();
@@ -185,7 +206,7 @@ __global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G
         }
         __syncthreads();
     }
-    if (blockIdx.x == 0) {
+    if (!strip) {
         for (int e = tid; e < kNb * kNb; e += 256) {
             const int r = e & (kNb - 1), c = e / kNb;
             if (r >= c) {
@@ -196,14 +217,12 @@ __global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G
         if (tid == 0 && fail) record_error(st, RQB_ERR_BREAKDOWN);
         return;
     }
-    // strip q of tile row i: L_ik(rows) = G_ik(rows) L_kk^{-T}
-    const int bi = (blockIdx.x - 1) / (kNb / kStrip), q = (blockIdx.x - 1) % (kNb / kStrip);
-    const int rr = tid >> 5, c = tid & 31;
-    const int row = (k + 1 + bi) * kNb + q * kStrip + rr;
+    // strip sq of tile row i: L_ik(rows) = G_ik(rows) L_kk^{-T}
+    const int c = tid & 31;
     W s = W(0);
-#pragma unroll 8
-    for (int t = 0; t < kNb; ++t) s += (W)G[row + (int64_t)(k0 + t) * bp] * Di[c][t];
-    L[row + (int64_t)(k0 + c) * bp] = (double)s;
+#pragma unroll
+    for (int t = 0; t < kNb; ++t) s += gv[t] * Di[c][t];
+    L[srow + (int64_t)(k0 + c) * bp] = (double)s;
 }
 
 // G_ij -= L_ik L_jk^T on the 8-row strip (blockIdx.x % 4) of tile pair

@@ -6,11 +6,10 @@
 // n^3/3 = 5.6 M FP64 multiply-adds, which one SM (two FP64 FMAs per clock on
 // this part) needs about 1.4 ms for.  Here the factorization G = L L^T is
 // blocked in 32 x 32 tiles and spread over many CTAs:
-//   panel k   every CTA factors the diagonal tile G_kk and inverts L_kk (FP32:
-//             one warp, rows in registers and shuffles; FP64: the whole CTA
-//             on the tile in shared memory, which keeps all four FP64 pipes
-//             of the SM busy); CTA 0 stores L_kk and L_kk^{-1}, the others the
-//             8-row strips of L_ik = G_ik L_kk^{-T} below it
+//   panel k   every CTA factors the diagonal tile G_kk and inverts L_kk (the
+//             whole CTA on the tile in shared memory, one barrier per pivot);
+//             CTA 0 stores L_kk and L_kk^{-1}, the others the 8-row strips of
+//             L_ik = G_ik L_kk^{-T} below it
 //   update k  G_ij -= L_ik L_jk^T for every tile k < j <= i, one CTA per
 //             8-row strip
 // R = L^T in FP64.  Each panel also keeps L_kk^{-1}, from which R^{-1} =
@@ -41,61 +40,28 @@ __global__ void k_chol_init(double* __restrict__ G, int bp, int p, double* __res
     }
 }
 
-// 1 / sqrt(d) for d > 0 in FP64: the FP32 estimate refined by two Newton
+// 1 / sqrt(d) for d > 0 in FP64: an FP32 estimate refined by two Newton
 // steps y <- y (3 - d y^2) / 2 (each about squares the relative error:
 // 2^-22 -> 2^-43 -> below the FP64 rounding), so the pivot's serial chain
 // costs a few dependent FP64 multiply-adds instead of an FP64 square root and
-// division.  Pivots outside the FP32 range (tested on the converted value,
-// on the FP32 pipe) take the FP64 library route.
+// division.  The FP32 argument of the estimate and the widening of its result
+// are built from the IEEE-754 fields with integer operations (binary64 ->
+// binary32 by truncating the significand, binary32 -> binary64 exactly), which
+// keeps the FP64 pipe -- a few lanes per clock on this part -- for the Newton
+// steps.  Pivots whose binary32 image would not be a normal number take the
+// FP64 library route.
 __device__ __forceinline__ double rsqrt_fp64(double d) {
-    const float df = (float)d;
-    const float e = rsqrtf(df);
-    if (!(df > 1e-36f && df < 1e36f)) return 1.0 / sqrt(d);
-    double y = (double)e;
+    const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+    const int e = (int)(hi >> 20);   // sign and biased exponent (sign 0 for d > 0)
+    if (e < 1023 - 120 || e > 1023 + 120) return 1.0 / sqrt(d);
+    const float df = __uint_as_float(((uint32_t)(e - 1023 + 127) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+    const uint32_t fb = __float_as_uint(rsqrtf(df));
+    double y = __hiloint2double((int)((((fb >> 23) + (1023 - 127)) << 20) | ((fb & 0x7fffffu) >> 3)),
+                                (int)(fb << 29));
     const double h = 0.5 * d;
 #pragma unroll
     for (int it = 0; it < 2; ++it) y = y * fma(-h, y * y, 1.5);
     return y;
-}
-
-// Factor the 32 x 32 diagonal tile in one warp: lane i holds row i of D
-// (-> L_kk) and of the identity (-> L_kk^{-1}) in registers; step j takes the
-// pivot from lane j, scales column j, and applies the rank-1 update to the
-// trailing rows and the elimination to the rows of L^{-1} with values
-// broadcast by shuffles (fully unrolled, so the rows stay in registers).
-// Lane j tests pivot j against its threshold thr_lane (tol * G_jj rounded to
-// W); the elimination does not wait for the test, since a factorization with
-// a failed pivot is reported and discarded.
-template <typename W>
-__device__ __forceinline__ bool warp_chol32(W (&d)[kNb], W (&di)[kNb], int lane, W thr_lane) {
-    bool fail = false;
-#pragma unroll 32
-    for (int j = 0; j < kNb; ++j) {
-        const W piv = __shfl_sync(0xffffffffu, d[j], j);
-        if (lane == j && (!(piv > thr_lane) || !isfinite(piv))) fail = true;
-        const W inv = W(1) / sqrt(piv);
-        const bool me = (lane == j), below = (lane > j);
-        d[j] = me ? piv * inv : (below ? d[j] * inv : d[j]);
-#pragma unroll 32
-        for (int t = 0; t < kNb; ++t)
-            if (t <= j) di[t] = me ? di[t] * inv : di[t];
-        const W lij = below ? d[j] : W(0);   // L[lane][j]
-#pragma unroll 32
-        for (int c = 0; c < kNb; ++c) {
-            if (c > j) {
-                const W lcj = __shfl_sync(0xffffffffu, d[j], c);
-                d[c] = (lane >= c) ? d[c] - lij * lcj : d[c];
-            }
-        }
-#pragma unroll 32
-        for (int t = 0; t < kNb; ++t) {
-            if (t <= j) {
-                const W xjt = __shfl_sync(0xffffffffu, di[t], j);
-                di[t] = below ? di[t] - lij * xjt : di[t];
-            }
-        }
-    }
-    return __any_sync(0xffffffffu, fail);
 }
 
 template <typename W>
@@ -118,80 +84,88 @@ __global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G
 #pragma unroll
         for (int t = 0; t < kNb; ++t) gv[t] = (W)G[srow + (int64_t)(k0 + t) * bp];
     }
-    if constexpr (sizeof(W) == 4) {
-        // FP32: one warp, rows in registers
-        if (tid < 32) {
-            W d[kNb], di[kNb];
-#pragma unroll
-            for (int c = 0; c < kNb; ++c) {
-                d[c] = (tid >= c) ? (W)G[(k0 + tid) + (int64_t)(k0 + c) * bp] : W(0);
-                di[c] = (tid == c) ? W(1) : W(0);
-            }
-            const bool f = warp_chol32<W>(d, di, tid, (W)(tol * dG[k0 + tid]));
-#pragma unroll
-            for (int c = 0; c < kNb; ++c) {
-                D[tid][c] = (tid >= c) ? d[c] : W(0);
-                Di[tid][c] = (tid >= c) ? di[c] : W(0);
-            }
-            if (tid == 0) fail = f ? 1 : 0;
-        }
-        __syncthreads();
-    } else {
-        // FP64: the tile in shared memory, one barrier per pivot.  The
-        // elimination runs unscaled: D keeps the Schur complements and Di the
-        // unscaled rows of L^{-1} (step j subtracts D[r][j] D[c][j] / pivot_j
-        // and D[r][j] Di[j][c] / pivot_j).  Thread 0 owns the serial chain:
-        // it updates D[j+1][j+1] (entry 0 of the dense numbering) and takes
-        // the next pivot at once, while warps 1..7 update the other active
-        // entries, so the chain never queues behind a warp's elimination
-        // work.  The factors are scaled by pivot^{-1/2} at the end.  A pivot
+    {
+        // The tile in shared memory, one barrier per pivot.  The elimination
+        // runs unscaled: D keeps the Schur complements and Di the unscaled
+        // rows of L^{-1} (step j subtracts D[r][j] D[c][j] / pivot_j and
+        // D[r][j] Di[j][c] / pivot_j).  Thread 0 owns the serial chain: it
+        // updates D[j+1][j+1] and takes the next pivot at once, while six
+        // other warps update the other active entries, so the chain never
+        // queues behind a warp's elimination work.  The factors are scaled by pivot^{-1/2} at the end.  A pivot
         // that fails the test sets `fail` without stopping the chain (the
-        // factorization is then reported and discarded).
+        // factorization is then reported and discarded).  FP64 keeps the
+        // FP64 pipes of all four SM sub-partitions busy; FP32 (the second
+        // CholeskyQR pass) is bound by the chain and the barriers.
         __shared__ W invp[kNb];
-        __shared__ double thr[kNb];
+        __shared__ W thr[kNb];
         for (int e = tid; e < kNb * kNb; e += 256) {
             const int r = e & (kNb - 1), c = e / kNb;
             D[r][c] = (r >= c) ? (W)G[(k0 + r) + (int64_t)(k0 + c) * bp] : W(0);
             Di[r][c] = (r == c) ? W(1) : W(0);
         }
-        if (tid < kNb) thr[tid] = tol * dG[k0 + tid];
+        if (tid < kNb) thr[tid] = (W)(tol * dG[k0 + tid]);
         if (tid == 0) fail = 0;
         __syncthreads();
         auto take_pivot = [&](int j, W d) {
-            if (!(d > thr[j]) || !isfinite(d)) fail = 1;
-            const W y = rsqrt_fp64(d);
+            W y;
+            if constexpr (sizeof(W) == 8) {
+                y = rsqrt_fp64(d);
+            } else {
+                // FP32: the hardware estimate and one Newton step
+                // y <- y (3 - d y^2) / 2 (the result is within about an ulp)
+                y = rsqrtf(d);
+                y = y * fmaf(-0.5f * d, y * y, 1.5f);
+            }
             inv[j] = y;
             invp[j] = y * y;
+            if (!(d > thr[j]) || !isfinite(d)) fail = 1;   // issued after the chain's operations
         };
         if (tid == 0) take_pivot(0, D[0][0]);
         __syncthreads();
-        constexpr int kWorkers = 256 - 32;
+        // workers: the six warps of sub-partitions 1..3 (warp w runs on
+        // sub-partition w % 4), so the chain of thread 0 has sub-partition 0's
+        // pipes alone.  Worker warp u owns the columns c = u (mod 6) of D and
+        // of Di, lane r their row r: a thread's active entries at step j
+        // share one multiplier D[r][j] / pivot_j, and all its operands are
+        // conflict-free or broadcast shared-memory reads.
+        const int wid = tid >> 5, lane = tid & 31;
+        const int u = (wid & 3) ? ((wid >> 2) * 3 + (wid & 3) - 1) : -1;
         for (int j = 0; j < kNb; ++j) {
             const W ip = invp[j];
-            // the active entries, densely numbered: the trailing triangle
-            // j < c <= r < 32 (nt entries), then the block j < r < 32, c <= j
-            const int nrem = kNb - 1 - j;
-            const int nt = nrem * (nrem + 1) / 2, nd = nrem * (j + 1);
             if (tid == 0) {
-                if (nrem > 0) {
+                if (j + 1 < kNb) {
                     const W l = D[j + 1][j];
                     const W nv = fma(-(l * ip), l, D[j + 1][j + 1]);
                     D[j + 1][j + 1] = nv;
                     take_pivot(j + 1, nv);
                 }
-            } else if (tid >= 32) {
-                for (int q = 1 + (tid - 32); q < nt + nd; q += kWorkers) {
-                    if (q < nt) {
-                        int u = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
-                        while (u * (u + 1) / 2 > q) --u;
-                        while ((u + 1) * (u + 2) / 2 <= q) ++u;
-                        const int v = q - u * (u + 1) / 2;
-                        const int r = j + 1 + u, c = j + 1 + v;
-                        D[r][c] = fma(-(D[r][j] * ip), D[c][j], D[r][c]);
-                    } else {
-                        const int q2 = q - nt;
-                        const int r = j + 1 + q2 / (j + 1), c = q2 % (j + 1);
-                        Di[r][c] = fma(-(D[r][j] * ip), Di[j][c], Di[r][c]);
+            } else if (u >= 0 && lane > j) {
+                const int r = lane;
+                const W a = D[r][j] * ip;
+                // this thread's columns c = u + 6 i: every operand is read
+                // before the first update is stored, so the six updates
+                // overlap instead of running as a chain of dependent accesses
+                W x[6], y[6];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    const int c = u + 6 * i;
+                    if (c < kNb) {
+                        x[i] = (c > j) ? D[c][j] : Di[j][c];
+                        y[i] = (c > j) ? D[r][c] : Di[r][c];
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    const int c = u + 6 * i;
+                    if (c < kNb) {
+                        const W v = fma(-a, x[i], y[i]);
+                        if (c > j) {
+                            // the trailing triangle j < c <= r; its one entry in
+                            // row j + 1, (j+1, j+1), is thread 0's
+                            if (r >= c && r != j + 1) D[r][c] = v;
+                        } else {
+                            Di[r][c] = v;
+                        }
                     }
                 }
             }

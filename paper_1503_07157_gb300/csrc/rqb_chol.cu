@@ -9,7 +9,8 @@
 //   panel k   every CTA factors the diagonal tile G_kk and inverts L_kk (the
 //             whole CTA on the tile in shared memory, one barrier per pivot);
 //             CTA 0 stores L_kk and L_kk^{-1}, the others the 8-row strips of
-//             L_ik = G_ik L_kk^{-T} below it
+//             L_ik = G_ik L_kk^{-T} below it (and FP32 copies of both when
+//             R^{-1} is formed in FP32)
 //   update k  G_ij -= L_ik L_jk^T for every tile k < j <= i, one CTA per
 //             8-row strip
 // R = L^T in FP64.  Each panel also keeps L_kk^{-1}, from which R^{-1} =
@@ -66,7 +67,8 @@ __device__ __forceinline__ double rsqrt_fp64(double d) {
 
 template <typename W>
 __global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G, double* __restrict__ L,
-                                                    double* __restrict__ Linv, int bp, int k,
+                                                    double* __restrict__ Linv, float* __restrict__ Lf,
+                                                    float* __restrict__ Lif, int bp, int k,
                                                     const double* __restrict__ dG, double tol, DevState* st) {
     __shared__ W D[kNb][kNb + 1];    // L_kk (lower)
     __shared__ W Di[kNb][kNb + 1];   // L_kk^{-1} (lower)
@@ -184,8 +186,13 @@ __global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G
         for (int e = tid; e < kNb * kNb; e += 256) {
             const int r = e & (kNb - 1), c = e / kNb;
             if (r >= c) {
-                L[(k0 + r) + (int64_t)(k0 + c) * bp] = (double)D[r][c];
-                Linv[(k0 + r) + (int64_t)(k0 + c) * bp] = (double)Di[r][c];
+                const int64_t o = (k0 + r) + (int64_t)(k0 + c) * bp;
+                L[o] = (double)D[r][c];
+                Linv[o] = (double)Di[r][c];
+                if (Lf) {
+                    Lf[o] = (float)D[r][c];
+                    Lif[o] = (float)Di[r][c];
+                }
             }
         }
         if (tid == 0 && fail) record_error(st, RQB_ERR_BREAKDOWN);
@@ -197,6 +204,7 @@ __global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G
 #pragma unroll
     for (int t = 0; t < kNb; ++t) s += gv[t] * Di[c][t];
     L[srow + (int64_t)(k0 + c) * bp] = (double)s;
+    if (Lf) Lf[srow + (int64_t)(k0 + c) * bp] = (float)s;
 }
 
 // G_ij -= L_ik L_jk^T on the 8-row strip (blockIdx.x % 4) of tile pair
@@ -334,6 +342,83 @@ __global__ void __launch_bounds__(256) k_linv_blocked(const double* __restrict__
     }
 }
 
+// Rinv = R^{-1} = (L^{-1})^T in FP32, by the block forward substitution of
+// k_linv_blocked, from the FP32 copies of L and of the diagonal-tile inverses
+// that the panels write (no FP64 loads or conversions).  CTA j forms column
+// block j of X = L^{-1}; the block row of L and L_ii^{-1} of step i + 1 are
+// copied by cp.async while step i multiplies.  X and the step's partial sum S
+// are row-major with rows padded to 36 floats, and thread (r, g) owns row r,
+// columns 4g .. 4g + 3, so that each operand of a multiply-add is one 16-byte
+// broadcast read or one conflict-free 4-byte read.
+constexpr int kXs = 36;   // padded row of X and S (floats)
+
+__global__ void __launch_bounds__(256) k_linv_f32(const float* __restrict__ Lf, const float* __restrict__ Lif, int bp,
+                                                  float* __restrict__ Rinv) {
+    extern __shared__ __align__(16) unsigned char linvf_smem[];
+    float* X = reinterpret_cast<float*>(linvf_smem);   // bp x 36
+    float* Lr = X + (size_t)bp * kXs;                  // [2][bp][32]: Lr[t][rr] = L(i0 + rr, j0 + t)
+    float* Dv = Lr + 2 * (size_t)bp * kNb;             // [2][32][32]: Dv[t][rr] = L_ii^{-1}(rr, t)
+    float* S = Dv + 2 * kNb * kNb;                      // 32 x 36
+    const int j = blockIdx.x, nblk = bp / kNb, tid = threadIdx.x, j0 = j * kNb;
+    auto issue = [&](int i, int b) {
+        const int i0 = i * kNb, len = i0 - j0;
+        float* lr = Lr + (size_t)b * bp * kNb;
+        for (int e = tid; e < len * 8; e += 256) {   // 8 vectors of 4 rows per column
+            const int t = e >> 3, v = (e & 7) * 4;
+            cp_async16(lr + t * kNb + v, Lf + (i0 + v) + (int64_t)(j0 + t) * bp, 16);
+        }
+        float* dv = Dv + b * kNb * kNb;
+        for (int e = tid; e < kNb * 8; e += 256) {
+            const int t = e >> 3, v = (e & 7) * 4;
+            cp_async16(dv + t * kNb + v, Lif + (i0 + v) + (int64_t)(i0 + t) * bp, 16);
+        }
+        cp_async_commit();
+    };
+    if (j + 1 < nblk) issue(j + 1, 0);
+    for (int e = tid; e < bp * kNb; e += 256) {
+        const int c = e % kNb, r = e / kNb;
+        X[r * kXs + c] = (r >= j0 && r < j0 + kNb && r - j0 >= c) ? Lif[r + (int64_t)(j0 + c) * bp] : 0.f;
+    }
+    const int r = tid & 31, g = tid >> 5;   // row r, columns 4g .. 4g + 3
+    for (int i = j + 1; i < nblk; ++i) {
+        const int b = (i - j - 1) & 1, i0 = i * kNb, len = i0 - j0;
+        cp_async_wait<0>();
+        __syncthreads();   // step i's operands landed; X rows of block i - 1 and S are complete / free
+        if (i + 1 < nblk) issue(i + 1, b ^ 1);
+        const float* lr = Lr + (size_t)b * bp * kNb;
+        const float* dv = Dv + b * kNb * kNb;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 8
+        for (int t = 0; t < len; ++t) {
+            const float l = lr[t * kNb + r];
+            const float4 x = *reinterpret_cast<const float4*>(X + (j0 + t) * kXs + 4 * g);
+            acc.x = fmaf(l, x.x, acc.x);
+            acc.y = fmaf(l, x.y, acc.y);
+            acc.z = fmaf(l, x.z, acc.z);
+            acc.w = fmaf(l, x.w, acc.w);
+        }
+        *reinterpret_cast<float4*>(S + r * kXs + 4 * g) = acc;
+        __syncthreads();
+        float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 8
+        for (int t = 0; t < kNb; ++t) {
+            const float d = (t <= r) ? dv[t * kNb + r] : 0.f;
+            const float4 sv = *reinterpret_cast<const float4*>(S + t * kXs + 4 * g);
+            out.x = fmaf(d, sv.x, out.x);
+            out.y = fmaf(d, sv.y, out.y);
+            out.z = fmaf(d, sv.z, out.z);
+            out.w = fmaf(d, sv.w, out.w);
+        }
+        *reinterpret_cast<float4*>(X + (i0 + r) * kXs + 4 * g) = make_float4(-out.x, -out.y, -out.z, -out.w);
+    }
+    __syncthreads();
+    // Rinv(j0 + c, rr) = X(rr, c)
+    for (int e = tid; e < bp * kNb; e += 256) {
+        const int c = e % kNb, rr = e / kNb;
+        Rinv[(j0 + c) + (int64_t)rr * bp] = X[rr * kXs + c];
+    }
+}
+
 }  // namespace
 
 // Rinv (T) = R^{-1} for an upper-triangular FP64 R (bp x bp, column-major);
@@ -355,27 +440,32 @@ cudaError_t upper_inverse(Ctx& cx, const double* R, int bp, T* Rinv) {
 
 // G (bp x bp, FP64, overwritten) = R^T R; R (FP64) and Rinv (T).  scratch:
 // 2 bp^2 + bp doubles (L, the inverses of its diagonal tiles, and the
-// diagonal of G).  fp64: working precision of the factorization (FP32 serves
-// the second CholeskyQR pass, whose Gram is I + O(u kappa)); the factors are
+// diagonal of G), plus bp^2 doubles' room for their FP32 copies when T is
+// float.  fp64: working precision of the factorization (FP32 serves the
+// second CholeskyQR pass, whose Gram is I + O(u kappa)); the factors are
 // stored in FP64 either way; R^{-1} is formed in T.
 template <typename T>
 cudaError_t chol_inv_blocked(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, double tol, double* scratch,
                              size_t scratch_doubles, bool fp64) {
-    if (bp % kNb != 0 || scratch_doubles < 2 * (size_t)bp * bp + bp) return cudaErrorInvalidValue;
+    constexpr bool f32 = sizeof(T) == 4;
+    const size_t need = 2 * (size_t)bp * bp + bp + (f32 ? (size_t)bp * bp : 0);
+    if (bp % kNb != 0 || scratch_doubles < need) return cudaErrorInvalidValue;
     double* L = scratch;
     double* Linv = scratch + (size_t)bp * bp;
     double* dG = Linv + (size_t)bp * bp;
+    float* Lf = f32 ? reinterpret_cast<float*>(dG + bp) : nullptr;   // 16-byte aligned: bp % 32 == 0
+    float* Lif = f32 ? Lf + (size_t)bp * bp : nullptr;
     const int nblk = bp / kNb;
     k_chol_init<<<std::max(1, bp * bp / 256), 256, 0, cx.stream>>>(G, bp, p, dG, L);
     cx.launches++;
     for (int k = 0; k < nblk; ++k) {
         const int below = nblk - k - 1;
         if (fp64)
-            k_chol_panel<double><<<1 + below * (kNb / kStrip), 256, 0, cx.stream>>>(G, L, Linv, bp, k, dG, tol,
-                                                                                    cx.st);
+            k_chol_panel<double><<<1 + below * (kNb / kStrip), 256, 0, cx.stream>>>(G, L, Linv, Lf, Lif, bp, k, dG,
+                                                                                    tol, cx.st);
         else
-            k_chol_panel<float><<<1 + below * (kNb / kStrip), 256, 0, cx.stream>>>(G, L, Linv, bp, k, dG, tol,
-                                                                                   cx.st);
+            k_chol_panel<float><<<1 + below * (kNb / kStrip), 256, 0, cx.stream>>>(G, L, Linv, Lf, Lif, bp, k, dG,
+                                                                                   tol, cx.st);
         cx.launches++;
         if (below > 0) {
             const int pairs = below * (below + 1) / 2;
@@ -388,14 +478,24 @@ cudaError_t chol_inv_blocked(Ctx& cx, double* G, int bp, int p, double* R, T* Ri
     }
     k_chol_transpose<<<std::max(1, bp * bp / 256), 256, 0, cx.stream>>>(L, bp, R);
     cx.launches++;
-    using Wi = T;
-    const size_t smem = sizeof(Wi) * ((size_t)bp * kNb + (size_t)bp * (kNb + 1) + 2 * (size_t)kNb * (kNb + 1));
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_linv_blocked<T, Wi>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
+    if constexpr (f32) {
+        const size_t smem = sizeof(float) * ((size_t)bp * kXs + 2 * (size_t)bp * kNb + 2 * kNb * kNb + kNb * kXs);
+        if (smem > 200 * 1024) return cudaErrorInvalidValue;
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_linv_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr_set = true;
+        }
+        k_linv_f32<<<nblk, 256, smem, cx.stream>>>(Lf, Lif, bp, Rinv);
+    } else {
+        const size_t smem = sizeof(T) * ((size_t)bp * kNb + (size_t)bp * (kNb + 1) + 2 * (size_t)kNb * (kNb + 1));
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_linv_blocked<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr_set = true;
+        }
+        k_linv_blocked<T, T><<<nblk, 256, smem, cx.stream>>>(L, Linv, bp, Rinv);
     }
-    k_linv_blocked<T, Wi><<<nblk, 256, smem, cx.stream>>>(L, Linv, bp, Rinv);
     cx.launches++;
     return cudaGetLastError();
 }

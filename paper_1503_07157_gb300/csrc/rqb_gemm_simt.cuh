@@ -269,16 +269,6 @@ k_gemm_nn(int64_t m, int64_t K, int64_t ksplit, int nc, int nout,
 // C_ROWMAJOR, plus: X, C 16-byte aligned, ldx and csk multiples of 16 bytes
 // (the host checks).  Elements outside the matrices are zero-filled by the
 // copy itself (src-size below 16 bytes).
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
 template <typename T, int BM, int BN, int BK, int ST>
 struct GemmNNPipe {
     static constexpr int TM = SimtTile<T>::TM, TN = SimtTile<T>::TN;

@@ -108,6 +108,18 @@ __device__ __forceinline__ bool aligned16(const T* p) {
     return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
 }
 
+// Asynchronous 16-byte global -> shared copies (cp.async): both addresses
+// 16-byte aligned; the bytes beyond src_bytes (0..16) are zero-filled.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Host-side helpers shared by the .cu files.
 struct LaunchCounter {

@@ -775,8 +775,14 @@ __device__ __forceinline__ int tile_slots(long long U, int C, int P, int G, int 
 
 // Y[r + c ldy] (r < m, c < np) = sum over the CTAs covering tile r / 128 of
 // their partials, in CTA order (FP32, at most a few terms, round to nearest);
-// with sub, Y = sub - that sum (sub may alias Y).  One CTA per tile.
+// with sub, Y = sub - that sum (sub may alias Y).  One CTA per tile and
+// slice; each thread sums four consecutive rows of a column with 16-byte
+// loads of the partials (and a 16-byte store where Y allows it).
 constexpr int kReduceSlices = 8;   // least CTAs per tile in the reductions (gridDim.y)
+
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
 
 __global__ void k_reduce_sketch(const float* __restrict__ part, long long U, int C, int P, int G, int np, long long m,
                                 float* Y, long long ldy, const float* sub) {
@@ -788,21 +794,33 @@ __global__ void k_reduce_sketch(const float* __restrict__ part, long long U, int
     const int nc = count;
     const int span = np * kBM / (int)gridDim.y;
     const int i0 = blockIdx.y * span;
-#pragma unroll 4
-    for (int idx = i0 + threadIdx.x; idx < i0 + span; idx += blockDim.x) {   // c * 128 + row
+    const bool vec = (ldy % 4 == 0) && ((reinterpret_cast<uintptr_t>(Y) & 15u) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(sub) & 15u) == 0);
+    for (int idx = i0 + 4 * (int)threadIdx.x; idx < i0 + span; idx += 4 * (int)blockDim.x) {   // c * 128 + row
         const int c = idx / kBM, rl = idx % kBM;
         const long long r = (long long)t * kBM + rl;
         if (r >= m) continue;
-        float acc = 0.f;
-        for (int q = 0; q < nc; ++q) acc += part[off[q] + idx];
-        Y[r + c * ldy] = sub ? sub[r + c * ldy] - acc : acc;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q = 0; q < nc; ++q) acc = add4(acc, *reinterpret_cast<const float4*>(part + off[q] + idx));
+        float* y = Y + r + c * ldy;
+        const float* sv = sub ? sub + r + c * ldy : nullptr;
+        if (vec && r + 4 <= m) {
+            if (sv) {
+                const float4 s4 = *reinterpret_cast<const float4*>(sv);
+                acc = make_float4(s4.x - acc.x, s4.y - acc.y, s4.z - acc.z, s4.w - acc.w);
+            }
+            *reinterpret_cast<float4*>(y) = acc;
+        } else {
+            const float a4[4] = {acc.x, acc.y, acc.z, acc.w};
+            for (int i = 0; i < 4 && r + i < m; ++i) y[i] = sv ? sv[i] - a4[i] : a4[i];
+        }
     }
 }
 
 // B_i: B[c + j ldb] (c < pcols) and the staged split copy Bs / Bsl (np x n,
 // column-major, ld np) from the partials of the projection; ||B_i||_F^2 of
-// the tile into sq_part[tile * 8 + slice] (FP64).  Eight CTAs per tile of 128
-// columns.
+// the tile into sq_part[tile * slices + slice] (FP64).  Each thread sums four
+// consecutive rows c of a column j (16-byte loads and staged stores).
 __global__ void k_reduce_project(const float* __restrict__ part, long long U, int C, int P, int G, int np, int pcols,
                                  long long n, float* __restrict__ B, long long ldb, float* __restrict__ Bs,
                                  float* __restrict__ Bsl, double* __restrict__ sq_part) {
@@ -816,19 +834,21 @@ __global__ void k_reduce_project(const float* __restrict__ part, long long U, in
     double sq = 0.0;
     const int span = np * kBM / (int)gridDim.y;
     const int i0 = blockIdx.y * span;
-#pragma unroll 4
-    for (int idx = i0 + threadIdx.x; idx < i0 + span; idx += blockDim.x) {   // jl * np + c
+    for (int idx = i0 + 4 * (int)threadIdx.x; idx < i0 + span; idx += 4 * (int)blockDim.x) {   // jl * np + c
         const int jl = idx / np, c = idx % np;
         const long long j = (long long)t * kBM + jl;
         if (j >= n) continue;
-        float v = 0.f;
-        for (int q = 0; q < nc; ++q) v += part[off[q] + idx];
-        Bs[c + j * np] = v;
-        Bsl[c + j * np] = tf32_lo(v);
-        if (c < pcols) {
-            B[c + j * ldb] = v;
-            sq += (double)v * (double)v;
-        }
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q = 0; q < nc; ++q) v = add4(v, *reinterpret_cast<const float4*>(part + off[q] + idx));
+        *reinterpret_cast<float4*>(Bs + c + j * np) = v;
+        *reinterpret_cast<float4*>(Bsl + c + j * np) = make_float4(tf32_lo(v.x), tf32_lo(v.y), tf32_lo(v.z), tf32_lo(v.w));
+        const float v4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (c + i < pcols) {
+                B[c + i + j * ldb] = v4[i];
+                sq += (double)v4[i] * (double)v4[i];
+            }
     }
     for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
@@ -1120,17 +1140,24 @@ __global__ void k_reduce_project16(const float* __restrict__ part, long long U, 
     const int span = np * kBM / (int)gridDim.y;
     const int i0 = blockIdx.y * span;
 #pragma unroll 4
-    for (int idx = i0 + threadIdx.x; idx < i0 + span; idx += blockDim.x) {
+    for (int idx = i0 + 4 * (int)threadIdx.x; idx < i0 + span; idx += 4 * (int)blockDim.x) {
         const int jl = idx / np, c = idx % np;
         const long long j = (long long)t * kBM + jl;
         if (j >= n) continue;
-        float v = 0.f;
-        for (int q = 0; q < nc; ++q) v += part[off[q] + idx];
-        split_bf16(v, Bs[c + j * np], Bsl[c + j * np]);
-        if (c < pcols) {
-            B[c + j * ldb] = v;
-            sq += (double)v * (double)v;
-        }
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q = 0; q < nc; ++q) v = add4(v, *reinterpret_cast<const float4*>(part + off[q] + idx));
+        const float v4[4] = {v.x, v.y, v.z, v.w};
+        __align__(8) __nv_bfloat16 hi[4], lo[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) split_bf16(v4[i], hi[i], lo[i]);
+        *reinterpret_cast<uint2*>(Bs + c + j * np) = *reinterpret_cast<const uint2*>(hi);
+        *reinterpret_cast<uint2*>(Bsl + c + j * np) = *reinterpret_cast<const uint2*>(lo);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (c + i < pcols) {
+                B[c + i + j * ldb] = v4[i];
+                sq += (double)v4[i] * (double)v4[i];
+            }
     }
     for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;

@@ -213,15 +213,12 @@ def alu_peak_tflops(dtype: str, num_sms: int, sm_mhz: float) -> float:
     return num_sms * lanes * 2.0 * sm_mhz * 1e6 / 1e12
 
 
-# ncu DRAM traffic of the dominant kernel per launch (bytes), keyed by workload;
-# from profiles/ (None when the kernel changed since the capture or when the
-# workload's dominant kernel was captured only on a smaller case).
-#   fp32: k_gemm_nn sketch, 20000 x 16000, dram read 1.295 GB + write 0.145 GB
 # DRAM bytes (read + write) per launch of each workload's dominant kernel from
-# ncu captures (profiles/); mixed and bf16: k_update / k_update16 captured at
+# ncu captures (profiles/): fp32: k_gemm_nn_pipe sketch at 20000 x 16000
+# (1.294 GB + 0.122 GB); mixed and bf16: k_update / k_update16 captured at
 # 8192 x 8192 (538.7 MB / 247 MB) scaled by the 8x elements of a
 # 32768 x 16384 launch; None where no capture of the current kernel exists.
-NCU_TRAFFIC = {"fp32": 1.440e9, "fp64": None, "mixed": 4.31e9, "bf16": 1.98e9}
+NCU_TRAFFIC = {"fp32": 1.416e9, "fp64": None, "mixed": 4.31e9, "bf16": 1.98e9}
 
 
 def oracle_modes(w: dict) -> tuple[int, int]:
@@ -344,7 +341,7 @@ def run_ours(args, w: dict, rank: int, world: int, dist):
         achieved = pf[dom] / (per_launch_ms * 1e-3) / 1e12
         peak = alu_peak_tflops(w["dtype"], props.multi_processor_count, sm_max)
         roofline = {"bound": "alu",
-                    "kernel": f"{dom} (k_gemm_{'nn' if dom == 'sketch' else 'tn'} + split reduction)"
+                    "kernel": f"{dom} (k_gemm_{'nn_pipe' if dom == 'sketch' else 'tn'} + split reduction)"
                     if dom in ("sketch", "project") else dom,
                     "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
                     "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(w.get("key")),

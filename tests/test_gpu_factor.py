@@ -140,6 +140,15 @@ def test_exact_rank_panel_breakdown(rqb_lib):
     assert rc == rqb_lib.RQB_ERR_BREAKDOWN
 
 
+def test_exact_rank_panel_breakdown_blocked(rqb_lib):
+    """The same for a 128-wide panel, whose Gram is factored by the blocked
+    multi-CTA Cholesky (rank(A) = 100 < b = 128): the failed pivot is
+    reported although the elimination does not stop at it."""
+    A = inputs.usv(300, 260, np.linspace(2.0, 1.0, 100), seed=43)
+    _, _, k, rc, _ = _factor(rqb_lib, A, 1e-12, 128, torch.float64)
+    assert rc == rqb_lib.RQB_ERR_BREAKDOWN
+
+
 def test_nonfinite_input(rqb_lib):
     A = np.ones((64, 48))
     A[3, 5] = np.nan

@@ -383,8 +383,20 @@ int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_
         a.part = ar.part; a.part_cap = ar.part_cap; a.allow_split = 1;
         RQB_CK(gemm_nn<T>(cx, a));
     }
-    // pass 2: CholeskyQR of Y1, Qout = Y1 R^{-1}
-    RQB_CK(gemm_tn_f64acc<T>(cx, m, bp, bp, ar.Y1, m, ar.Y1, m, ar.G, bp, ar.dpart, ar.dpart_cap, false, true));
+    // pass 2: CholeskyQR of Y1, Qout = Y1 R^{-1}.  Y1 is well conditioned
+    // (kappa ~ 1 after pass 1), so on the tensor-core handles its Gram comes
+    // from the split-TF32 products (relative error ~1e-7, about what FP32
+    // products summed in FP32 over 128 rows and then in FP64 leave).
+    bool tcg2 = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if (ar.rp && m <= ar.rp->ldyl && tc::gram_ok(m, bp, m, ar.Y1)) {
+            RQB_CK(tc::gram(cx, ar.Y1, m, m, bp, *ar.rp));
+            RQB_CK(launch_to_double<float>(cx, bp, bp, ar.rp->Ct, bp, ar.G, bp));
+            tcg2 = true;
+        }
+    }
+    if (!tcg2)
+        RQB_CK(gemm_tn_f64acc<T>(cx, m, bp, bp, ar.Y1, m, ar.Y1, m, ar.G, bp, ar.dpart, ar.dpart_cap, false, true));
     RQB_CK(chol_inv<T>(cx, ar.G, bp, p, ar.R, ar.Rinv, sizeof(T) == 8, ar.dpart, ar.dpart_cap));
     bool tc2 = false;
     if constexpr (std::is_same<T, float>::value) {

@@ -43,9 +43,8 @@ __global__ void k_chol_init(double* __restrict__ G, int bp, int p, double* __res
 
 // 1 / sqrt(d) for d > 0 in FP64: an FP32 estimate refined by two Newton
 // steps y <- y (3 - d y^2) / 2 (each about squares the relative error:
-// 2^-22 -> 2^-43 -> below the FP64 rounding), so the pivot's serial chain
-// costs a few dependent FP64 multiply-adds instead of an FP64 square root and
-// division.  The FP32 argument of the estimate and the widening of its result
+// 2^-22 -> 2^-43 -> below the FP64 rounding): a few dependent FP64
+// multiply-adds instead of an FP64 square root and division.  The FP32 argument of the estimate and the widening of its result
 // are built from the IEEE-754 fields with integer operations (binary64 ->
 // binary32 by truncating the significand, binary32 -> binary64 exactly), which
 // keeps the FP64 pipe -- a few lanes per clock on this part -- for the Newton
@@ -62,6 +61,22 @@ __device__ __forceinline__ double rsqrt_fp64(double d) {
     const double h = 0.5 * d;
 #pragma unroll
     for (int it = 0; it < 2; ++it) y = y * fma(-h, y * y, 1.5);
+    return y;
+}
+
+// 1 / d for d > 0 in FP64 by the same construction: the FP32 estimate
+// refined by two Newton steps y <- y + y (1 - d y) (2^-22 -> 2^-44 -> below
+// the FP64 rounding), two dependent FP64 operations per step.
+__device__ __forceinline__ double rcp_fp64(double d) {
+    const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+    const int e = (int)(hi >> 20);
+    if (e < 1023 - 120 || e > 1023 + 120) return 1.0 / d;
+    const float df = __uint_as_float(((uint32_t)(e - 1023 + 127) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+    const uint32_t fb = __float_as_uint(__frcp_rn(df));
+    double y = __hiloint2double((int)((((fb >> 23) + (1023 - 127)) << 20) | ((fb & 0x7fffffu) >> 3)),
+                                (int)(fb << 29));
+#pragma unroll
+    for (int it = 0; it < 2; ++it) y = fma(y, fma(-d, y, 1.0), y);
     return y;
 }
 
@@ -108,18 +123,16 @@ __global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G
         if (tid < kNb) thr[tid] = (W)(tol * dG[k0 + tid]);
         if (tid == 0) fail = 0;
         __syncthreads();
+        // the chain needs 1 / pivot only (the elimination runs unscaled);
+        // pivot^{-1/2} for the final scaling is formed after the loop
         auto take_pivot = [&](int j, W d) {
-            W y;
             if constexpr (sizeof(W) == 8) {
-                y = rsqrt_fp64(d);
+                invp[j] = rcp_fp64(d);
             } else {
                 // FP32: the hardware estimate and one Newton step
-                // y <- y (3 - d y^2) / 2 (the result is within about an ulp)
-                y = rsqrtf(d);
-                y = y * fmaf(-0.5f * d, y * y, 1.5f);
+                const float y = __frcp_rn(d);
+                invp[j] = fmaf(y, fmaf(-d, y, 1.f), y);
             }
-            inv[j] = y;
-            invp[j] = y * y;
             if (!(d > thr[j]) || !isfinite(d)) fail = 1;   // issued after the chain's operations
         };
         if (tid == 0) take_pivot(0, D[0][0]);
@@ -173,6 +186,16 @@ __global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G
             }
             __syncthreads();
         }
+        if (tid < kNb) {   // D[c][c] holds pivot c
+            const W d = D[tid][tid];
+            if constexpr (sizeof(W) == 8) {
+                inv[tid] = rsqrt_fp64(d);
+            } else {
+                const float y = rsqrtf(d);
+                inv[tid] = y * fmaf(-0.5f * d, y * y, 1.5f);
+            }
+        }
+        __syncthreads();
         for (int e = tid; e < kNb * kNb; e += 256) {
             const int r = e & (kNb - 1), c = e / kNb;
             if (r >= c) {

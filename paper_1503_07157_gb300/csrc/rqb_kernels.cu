@@ -13,6 +13,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdio>
 
 #include "rqb_engine.h"
@@ -204,14 +205,62 @@ k_reduce_split(int64_t rows, int64_t cols, int splits, const TP* __restrict__ pa
     }
 }
 
+// The FP32 case with alpha = 1, beta = 0 and aligned columns of a multiple
+// of four rows: four consecutive rows per thread (16-byte loads and stores,
+// 32-bit index arithmetic), the same FP32 sums in split order, and no FP64
+// work unless ||out||^2 is asked for.
+__global__ void __launch_bounds__(256)
+k_reduce_split4(int rows, int cols, int splits, const float* __restrict__ part, int64_t ldp, int64_t zstride,
+                float* __restrict__ out, int64_t ldo, double* __restrict__ sq_part) {
+    __shared__ double sh[8];
+    double sq = 0.0;
+    const int rq = rows / 4;
+    const int total = rq * cols;
+    for (int e = blockIdx.x * 256 + threadIdx.x; e < total; e += gridDim.x * 256) {
+        const int r = (e % rq) * 4, c = e / rq;
+        const float* p = part + r + (int64_t)c * ldp;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+        for (int z = 0; z < splits; ++z) {
+            const float4 v = *reinterpret_cast<const float4*>(p + z * zstride);
+            acc.x += v.x;
+            acc.y += v.y;
+            acc.z += v.z;
+            acc.w += v.w;
+        }
+        *reinterpret_cast<float4*>(out + r + (int64_t)c * ldo) = acc;
+        if (sq_part) {
+            sq = fma((double)acc.x, (double)acc.x, sq);
+            sq = fma((double)acc.y, (double)acc.y, sq);
+            sq = fma((double)acc.z, (double)acc.z, sq);
+            sq = fma((double)acc.w, (double)acc.w, sq);
+        }
+    }
+    if (sq_part) {
+        const double t = block_sum<256>(sq, sh);
+        if (threadIdx.x == 0) sq_part[blockIdx.x] = t;
+    }
+}
+
 template <typename TP, typename TO>
 cudaError_t launch_reduce_split(Ctx& cx, int64_t rows, int64_t cols, int splits, const TP* part, int64_t ldp,
                                 int64_t zstride, TO* out, int64_t ldo, double* sq_part, int sq_cap,
                                 double* sq_out, double alpha, double beta, const TO* Yin, int64_t ldyin, int sym) {
-    int blocks = std::max<int64_t>(1, std::min<int64_t>((rows * cols + 255) / 256, (int64_t)cx.num_sms * 8));
+    bool vec4 = false;
+    if constexpr (std::is_same<TP, float>::value && std::is_same<TO, float>::value)
+        vec4 = alpha == 1.0 && beta == 0.0 && !sym && rows % 4 == 0 && ldp % 4 == 0 && zstride % 4 == 0 &&
+               ldo % 4 == 0 && (uintptr_t)part % 16 == 0 && (uintptr_t)out % 16 == 0 && rows * cols < (1LL << 31);
+    const int64_t work = vec4 ? rows / 4 * cols : rows * cols;
+    int blocks = std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, (int64_t)cx.num_sms * 8));
     if (sq_part) blocks = std::min(blocks, sq_cap);
-    k_reduce_split<TP, TO><<<blocks, 256, 0, cx.stream>>>(rows, cols, splits, part, ldp, zstride, out, ldo,
-                                                           sq_part, alpha, beta, Yin, ldyin, sym);
+    if constexpr (std::is_same<TP, float>::value && std::is_same<TO, float>::value) {
+        if (vec4)
+            k_reduce_split4<<<blocks, 256, 0, cx.stream>>>((int)rows, (int)cols, splits, part, ldp, zstride, out,
+                                                           ldo, sq_part);
+    }
+    if (!vec4)
+        k_reduce_split<TP, TO><<<blocks, 256, 0, cx.stream>>>(rows, cols, splits, part, ldp, zstride, out, ldo,
+                                                               sq_part, alpha, beta, Yin, ldyin, sym);
     cx.launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !sq_part) return e;

@@ -320,10 +320,13 @@ constexpr int NTU = 128;
 __global__ void __launch_bounds__(NTU) k_rows_update(const GMat* __restrict__ mats, const GState* __restrict__ st,
                                                      const Item* __restrict__ items, int b, int first,
                                                      const float* __restrict__ Om_next, double* __restrict__ part) {
+    // B_i and Omega_{i+1} chunks are stored so that a thread's four strided
+    // columns tx + 8 j (j < 4) are one 16-byte word: entry (t, c) of a row
+    // sits at [(c % 8) * 4 + c / 8] (rows padded to 36 floats)
     __shared__ __align__(16) float Qs[BP][TR + 4];    // Qs[t][r] = Q_i(r0 + r, t)
-    __shared__ float Bs[BP][KCH + 1];                 // Bs[t][c] = B_i(t, c0 + c)
+    __shared__ __align__(16) float Bs[BP][36];        // B_i(t, c0 + c) at Bs[t][(c % 8) * 4 + c / 8]
     __shared__ __align__(16) float Ws[KCH][TR + 4];   // Ws[c][r] = W(r0 + r, c0 + c)
-    __shared__ float Os[KCH][BP + 1];                 // Os[c][j] = Omega_{i+1}(c0 + c, j)
+    __shared__ __align__(16) float Os[KCH][36];       // Omega_{i+1}(c0 + c, j) at Os[c][(j % 8) * 4 + j / 8]
     __shared__ double red[NTU / 32];
     const Item it = items[blockIdx.x];
     const GState s = st[it.t];
@@ -374,8 +377,8 @@ __global__ void __launch_bounds__(NTU) k_rows_update(const GMat* __restrict__ ma
 #pragma unroll
         for (int u = 0; u < SQ; ++u) {
             const int e = tid + u * NTU, c = e / BP, t = e % BP;
-            Bs[t][c] = br[u];
-            Os[c][t] = orr[u];
+            Bs[t][(c & 7) * 4 + (c >> 3)] = br[u];
+            Os[c][(t & 7) * 4 + (t >> 3)] = orr[u];
         }
 #pragma unroll
         for (int u = 0; u < WQ; ++u) {
@@ -395,9 +398,8 @@ __global__ void __launch_bounds__(NTU) k_rows_update(const GMat* __restrict__ ma
             const float4 a0 = *reinterpret_cast<const float4*>(&Qs[t][ty * 8]);
             const float4 a1 = *reinterpret_cast<const float4*>(&Qs[t][ty * 8 + 4]);
             const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            float bv[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) bv[j] = Bs[t][tx + 8 * j];
+            const float4 b4 = *reinterpret_cast<const float4*>(&Bs[t][tx * 4]);
+            const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -441,9 +443,8 @@ __global__ void __launch_bounds__(NTU) k_rows_update(const GMat* __restrict__ ma
             const float4 a0 = *reinterpret_cast<const float4*>(&Ws[c][ty * 8]);
             const float4 a1 = *reinterpret_cast<const float4*>(&Ws[c][ty * 8 + 4]);
             const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            float ov[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) ov[j] = Os[c][tx + 8 * j];
+            const float4 o4 = *reinterpret_cast<const float4*>(&Os[c][tx * 4]);
+            const float ov[4] = {o4.x, o4.y, o4.z, o4.w};
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -478,16 +479,26 @@ __global__ void __launch_bounds__(NTU) k_rows_update(const GMat* __restrict__ ma
 //                part = ||B_i tile||^2
 //   kColReproj   C(c, j)   = sum_r Qbar(r, c) Y1(r, j), 128 columns per item,
 //                FP32 partials promoted to FP64 every 128 rows
-// Thread (tj, lane) owns j = tj*4 .. +3 and c = lane + 32 q.
+// Thread (jg, ct) owns j = jg*JT .. +JT-1 and the four columns 4 ct .. +3
+// (JT = W / 32): per chunk row one broadcast 16-byte read of P and one
+// 16-byte read of V feed 4 JT multiply-adds.  The 16-byte groups of a V row
+// are permuted by (row / 4) % 8 so that both the transposing stores of the
+// staged chunk and the 16-byte reads are free of bank conflicts.
 enum ColOp { kColProject = 0, kColReproj = 1 };
+
+__device__ __forceinline__ int vs_col(int r, int c) {   // physical column of V entry (r, c)
+    return ((((c >> 2) ^ ((r >> 2) & 7))) << 2) | (c & 3);
+}
 
 template <int OP>
 __global__ void __launch_bounds__(NT) k_cols(const GMat* __restrict__ mats, const GState* __restrict__ st,
                                              const Item* __restrict__ items, int first, double* __restrict__ part) {
     constexpr int W = (OP == kColProject) ? TC : TCR;   // columns per item
-    constexpr int NQ = W / 32;                           // column slots per thread
+    constexpr int JT = W / 32;                           // j per thread (8 or 4)
+    constexpr int NCT = W / 4;                           // column threads
+    static_assert((BP / JT) * NCT == NT, "thread map");
     __shared__ __align__(16) float Ps[KCH][BP + 4];   // Ps[r][j]: Q_i or Y1 rows of the chunk
-    __shared__ float Vs[KCH][W + 1];     // Vs[r][c]: Wsrc or Qbar columns of the item
+    __shared__ __align__(16) float Vs[KCH][W];        // Vs[r][vs_col(r, c)]: Wsrc or Qbar columns of the item
     __shared__ double red[NT / 32];
     const Item it = items[blockIdx.x];
     const GState s = st[it.t];
@@ -503,18 +514,18 @@ __global__ void __launch_bounds__(NT) k_cols(const GMat* __restrict__ mats, cons
     const float* V = (OP == kColProject) ? (first ? d.A : d.W) : d.Q;
     const int64_t ldv = (OP == kColProject) ? (first ? d.lda : d.ldw) : d.ldq;
     const int64_t m = d.m;
-    const int tid = threadIdx.x, tj = tid >> 5, lane = tid & 31;
-    float acc[4][NQ];
-    double acc2[4][OP == kColReproj ? NQ : 1];
+    const int tid = threadIdx.x, jg = tid / NCT, ct = tid % NCT;
+    float acc[JT][4];
+    double acc2[OP == kColReproj ? JT : 1][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < JT; ++i)
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) acc[i][q] = 0.f;
+        for (int q = 0; q < 4; ++q) acc[i][q] = 0.f;
     if (OP == kColReproj) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < (OP == kColReproj ? JT : 1); ++i)
 #pragma unroll
-            for (int q = 0; q < (OP == kColReproj ? NQ : 1); ++q) acc2[i][q] = 0.0;
+            for (int q = 0; q < 4; ++q) acc2[i][q] = 0.0;
     }
     // staging: float4 e of a chunk covers rows 4 (e % 8) .. +3 of column e / 8;
     // the next chunk is loaded into registers while the current one is used
@@ -544,28 +555,32 @@ __global__ void __launch_bounds__(NT) k_cols(const GMat* __restrict__ mats, cons
 #pragma unroll
         for (int u = 0; u < VQ; ++u) {
             const int e = tid + u * NT, c = e / (KCH / 4), rq = (e % (KCH / 4)) * 4;
-            Vs[rq][c] = vr[u].x; Vs[rq + 1][c] = vr[u].y; Vs[rq + 2][c] = vr[u].z; Vs[rq + 3][c] = vr[u].w;
+            const int pc = vs_col(rq, c);   // rows rq .. rq + 3 share the permutation
+            Vs[rq][pc] = vr[u].x; Vs[rq + 1][pc] = vr[u].y; Vs[rq + 2][pc] = vr[u].z; Vs[rq + 3][pc] = vr[u].w;
         }
         __syncthreads();
         if (r0 + KCH < m) load(r0 + KCH);
 #pragma unroll 4
         for (int rr = 0; rr < KCH; ++rr) {
-            const float4 a4 = *reinterpret_cast<const float4*>(&Ps[rr][tj * 4]);   // warp-uniform: broadcast
-            const float a[4] = {a4.x, a4.y, a4.z, a4.w};
-            float v[NQ];
+            float a[JT];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) v[q] = Vs[rr][lane + 32 * q];
+            for (int h = 0; h < JT; h += 4) {   // warp-uniform: broadcast
+                const float4 a4 = *reinterpret_cast<const float4*>(&Ps[rr][jg * JT + h]);
+                a[h] = a4.x; a[h + 1] = a4.y; a[h + 2] = a4.z; a[h + 3] = a4.w;
+            }
+            const float4 v4 = *reinterpret_cast<const float4*>(&Vs[rr][vs_col(rr, 4 * ct)]);
+            const float v[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < JT; ++i)
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) acc[i][q] = fmaf(a[i], v[q], acc[i][q]);
+                for (int q = 0; q < 4; ++q) acc[i][q] = fmaf(a[i], v[q], acc[i][q]);
         }
         if (OP == kColReproj && (++chunk == 4 || r0 + KCH >= m)) {
             chunk = 0;
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < (OP == kColReproj ? JT : 1); ++i)
 #pragma unroll
-                for (int q = 0; q < (OP == kColReproj ? NQ : 1); ++q) {
+                for (int q = 0; q < 4; ++q) {
                     acc2[i][q] += (double)acc[i][q];
                     acc[i][q] = 0.f;
                 }
@@ -573,11 +588,11 @@ __global__ void __launch_bounds__(NT) k_cols(const GMat* __restrict__ mats, cons
     }
     double sq = 0.0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int j = tj * 4 + i;
+    for (int i = 0; i < JT; ++i) {
+        const int j = jg * JT + i;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const int64_t cc = c0 + lane + 32 * q;
+        for (int q = 0; q < 4; ++q) {
+            const int64_t cc = c0 + 4 * ct + q;
             if (cc >= ncols) continue;
             if (OP == kColProject) {
                 if (j < s.p) {
@@ -586,7 +601,7 @@ __global__ void __launch_bounds__(NT) k_cols(const GMat* __restrict__ mats, cons
                     sq += (double)bv * (double)bv;
                 }
             } else {
-                d.Cc[cc + (int64_t)j * d.kcap] = (float)acc2[i][OP == kColReproj ? q : 0];
+                d.Cc[cc + (int64_t)j * d.kcap] = (float)acc2[OP == kColReproj ? i : 0][q];
             }
         }
     }

@@ -49,9 +49,12 @@ def test_fp64_config(orc, rqb_lib):
     np.testing.assert_allclose(st.E, ro.E, rtol=0, atol=1e-13 * ro.normA2)
 
 
-@pytest.mark.parametrize("m,n,b,eps_rel", [(4000, 3200, 128, 1e-2), (4000, 3200, 128, 2e-3), (1037, 777, 37, 3e-3)])
+@pytest.mark.parametrize("m,n,b,eps_rel", [(4000, 3200, 128, 1e-2), (4000, 3200, 128, 2e-3), (1037, 777, 37, 3e-3),
+                                           (3000, 2000, 256, 1e-3)])
 def test_fp32_poly_decay(orc, rqb_lib, m, n, b, eps_rel):
-    """Polynomial decay s_j = j^-1.5 (the FP32 workload's spectrum) at oracle-size."""
+    """Polynomial decay s_j = j^-1.5 (the FP32 workload's spectrum) at oracle-size;
+    b = 256 runs the blocked Cholesky tiles (FP64 first pass, FP32 second) and
+    the FP32 R^-1 from their FP32 copies."""
     s = inputs.spectrum_poly(min(m, n))
     A = inputs.usv(m, n, s, seed=m + n).astype(np.float32).astype(np.float64)
     nA = np.linalg.norm(A)

@@ -1063,6 +1063,209 @@ __global__ void __launch_bounds__(kUpd16Threads, 1) k_update16(const __grid_cons
     }
 }
 
+// Wide BF16 update: the same product on 128 x 256 tiles (N = 256 MMAs read a
+// quarter fewer operand bytes per multiply-add than N = 128 ones), K in
+// chunks of 32 (64-byte swizzle rows, 48 KB per stage) through three stages,
+// and the W tile in 128 x 64 quarters through a ring of four 16 KB buffers
+// (warp 10 loads quarter w into slot w % 4; the epilogue warps replace it by
+// the rounded difference; one thread stores it and hands the previous slot
+// back once that store has read it).  TMEM: two 256-column accumulators.
+constexpr int kKCw = 32;                            // K per chunk
+constexpr int kNJw = 256;                           // tile columns
+constexpr int kStw = 3;                             // operand stages
+constexpr int kWRw = 4;                             // W quarter buffers
+constexpr uint32_t kQw = kBM * kKCw * 2;            // Q_i^T hi or lo chunk: 8 KB
+constexpr uint32_t kBw = kNJw * kKCw * 2;           // B_i hi or lo chunk: 16 KB
+constexpr uint32_t kStageW = 2 * kQw + 2 * kBw;     // 48 KB
+constexpr uint32_t kWQw = kBM * 64 * 2;             // W quarter: 16 KB
+constexpr size_t kUpd16wSmem = (size_t)kStw * kStageW + (size_t)kWRw * kWQw + 1024;
+
+__global__ void __launch_bounds__(kUpd16Threads, 1) k_update16w(const __grid_constant__ UpdateParams16 p) {
+    __shared__ __align__(8) uint64_t full[kStw], empty[kStw], accfull[2], accempty[2], wfull[kWRw], wempty[kWRw],
+        drain;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ double red[8];
+    extern __shared__ uint8_t dsm[];
+    uint8_t* base = dsm + (((smem_u32(dsm) + 1023u) & ~1023u) - smem_u32(dsm));
+    uint8_t* wbuf = base + kStw * kStageW;
+    constexpr uint32_t kCols = 2u * kNJw;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int* ab = &abort_flag;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStw; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int s = 0; s < 2; ++s) { mbar_init(&accfull[s], 1); mbar_init(&accempty[s], 8); }
+        for (int s = 0; s < kWRw; ++s) { mbar_init(&wfull[s], 1); mbar_init(&wempty[s], 1); }
+        mbar_init(&drain, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+        prefetch_map(&p.mqt);
+        prefetch_map(&p.mqtl);
+        prefetch_map(&p.mbs);
+        prefetch_map(&p.mbsl);
+        prefetch_map(&p.mws);
+        prefetch_map(&p.mwd);
+    }
+    if (warp == 1) tmem_alloc(&tmem_base, kCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const int T = p.RT * p.CT;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            long long q = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < T && !stop; t += gridDim.x) {
+                const int rt = t / p.CT, ctile = t % p.CT;
+                for (int kc = 0; kc < p.C; ++kc, ++q) {
+                    const int s = (int)(q % kStw);
+                    const uint32_t r = (uint32_t)(q / kStw);
+                    if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1u, ab)) { stop = true; break; }
+                    uint8_t* st = base + s * kStageW;
+                    mbar_arrive_expect_tx(&full[s], kStageW);
+                    tma_load_2d(st, &p.mqt, kc * kKCw, rt * kBM, &full[s]);
+                    tma_load_2d(st + kQw, &p.mqtl, kc * kKCw, rt * kBM, &full[s]);
+                    tma_load_2d(st + 2 * kQw, &p.mbs, kc * kKCw, ctile * kNJw, &full[s]);
+                    tma_load_2d(st + 2 * kQw + kBw, &p.mbsl, kc * kKCw, ctile * kNJw, &full[s]);
+                }
+            }
+            for (long long qq = (q > kStw ? q - kStw : 0); qq < q; ++qq)
+                mbar_wait(&full[qq % kStw], (uint32_t)(qq / kStw) & 1u, ab, false);
+        }
+    } else if (warp == 10) {
+        if (lane == 0) {
+            long long w = 0;   // quarters issued
+            bool stop = false;
+            for (int t = blockIdx.x; t < T && !stop; t += gridDim.x) {
+                for (int qq = 0; qq < 4; ++qq, ++w) {
+                    const int slot = (int)(w % kWRw);
+                    const long long use = w / kWRw;
+                    if (use > 0 && !mbar_wait(&wempty[slot], (uint32_t)(use - 1) & 1u, ab)) { stop = true; break; }
+                    mbar_arrive_expect_tx(&wfull[slot], kWQw);
+                    tma_load_2d(wbuf + slot * kWQw, &p.mws, (t / p.CT) * kBM, (t % p.CT) * kNJw + qq * 64,
+                                &wfull[slot]);
+                }
+            }
+            for (long long ww = (w > kWRw ? w - kWRw : 0); ww < w; ++ww)
+                mbar_wait(&wfull[ww % kWRw], (uint32_t)(ww / kWRw) & 1u, ab, false);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(kNJw, 0);
+            long long q = 0;
+            int g = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < T && !stop; t += gridDim.x, ++g) {
+                const int abuf = g & 1, use = g >> 1;
+                if (use > 0 && !mbar_wait(&accempty[abuf], (uint32_t)(use - 1) & 1u, ab)) break;
+                const uint32_t d = tmem + (uint32_t)(abuf * kNJw);
+                for (int kc = 0; kc < p.C; ++kc, ++q) {
+                    const int s = (int)(q % kStw);
+                    const uint32_t r = (uint32_t)(q / kStw);
+                    if (!mbar_wait(&full[s], r & 1u, ab)) { stop = true; break; }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(base + s * kStageW), a1 = a0 + kQw;
+                    const uint32_t b0 = a0 + 2 * kQw, b1 = b0 + kBw;
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk)
+                        mma_bf16(d, desc_k_sw64(a0 + kk * 32), desc_k_sw64(b0 + kk * 32), idesc,
+                                 (kc == 0 && kk == 0) ? 0u : 1u);
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk)
+                        mma_bf16(d, desc_k_sw64(a0 + kk * 32), desc_k_sw64(b1 + kk * 32), idesc, 1u);
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk)
+                        mma_bf16(d, desc_k_sw64(a1 + kk * 32), desc_k_sw64(b0 + kk * 32), idesc, 1u);
+                    mma_commit(&empty[s]);
+                }
+                if (stop) break;
+                mma_commit(&accfull[abuf]);
+            }
+            mma_commit(&drain);
+            mbar_wait(&drain, 0, ab, false);
+        }
+    } else {
+        const int e = warp - 2;
+        const int quarter = warp & 3;                 // TMEM lanes this warp may read
+        const int half = e >> 2;                      // columns [32 half, 32 half + 32) of each W quarter
+        const bool issuer = (warp == 2 && lane == 0);
+        const int row = quarter * 32 + lane;          // tile row of this thread
+        double sq = 0.0;
+        int g = 0;
+        long long w = 0;                              // quarters consumed
+        bool stop = false;
+        for (int t = blockIdx.x; t < T && !stop; t += gridDim.x, ++g) {
+            const int abuf = g & 1, use = g >> 1;
+            const bool oka = mbar_wait(&accfull[abuf], (uint32_t)use & 1u, ab);
+            const int rt = t / p.CT, ctile = t % p.CT;
+            const long long r = (long long)rt * kBM + row;
+            const bool rok = r < p.m;
+            for (int qq = 0; qq < 4; ++qq, ++w) {
+                const int slot = (int)(w % kWRw);
+                bool okw = oka && mbar_wait(&wfull[slot], (uint32_t)(w / kWRw) & 1u, ab);
+                // all eight warps leave together (the named barrier below counts them)
+                named_barrier(1, 256);
+                if (*ab || !okw) { stop = true; break; }
+                tc_fence_after();
+                const long long j0 = (long long)ctile * kNJw + qq * 64 + half * 32;
+                // W quarter column-major: element (row, col) at col * 256 + row * 2
+                unsigned short* wt = reinterpret_cast<unsigned short*>(wbuf + slot * kWQw) + row;
+                const uint32_t tl =
+                    tmem + (uint32_t)(abuf * kNJw + qq * 64 + half * 32) + ((uint32_t)(quarter * 32) << 16);
+                float sq32 = 0.f;
+#pragma unroll 1
+                for (int c0 = 0; c0 < 32; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tl + (uint32_t)c0, v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int cl = half * 32 + c0 + i;
+                        const float wv = __bfloat162float(__ushort_as_bfloat16(wt[cl * kBM]));
+                        const __nv_bfloat16 o = __float2bfloat16_rn(wv - v[i]);
+                        wt[cl * kBM] = __bfloat16_as_ushort(o);
+                        if (rok && j0 + c0 + i < p.n) {
+                            const float of = __bfloat162float(o);
+                            sq32 = fmaf(of, of, sq32);
+                        }
+                    }
+                }
+                sq += (double)sq32;
+                if (qq == 3) {   // the accumulator is read: hand it back
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&accempty[abuf]);
+                }
+                fence_async_smem();
+                named_barrier(1, 256);
+                if (issuer) {
+                    tma_store_2d(&p.mwd, rt * kBM, ctile * kNJw + qq * 64, wbuf + slot * kWQw);
+                    bulk_commit();
+                    // the previous quarter's store has read its buffer: hand it back
+                    bulk_wait_read<1>();
+                    if (w > 0) mbar_arrive(&wempty[(w - 1) % kWRw]);
+                }
+            }
+        }
+        if (issuer) bulk_wait<0>();
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (lane == 0) red[e] = sq;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, kCols);
+    if (threadIdx.x == 0) {
+        if (abort_flag) record_error(p.st, RQB_ERR_TIMEOUT);
+        if (p.sq_part) {
+            double t = 0.0;
+            for (int i = 0; i < 8; ++i) t += red[i];
+            p.sq_part[blockIdx.x] = t;
+        }
+    }
+}
+
 // x = hi + lo with hi = rn_bf16(x) and lo = rn_bf16(x - hi) (x - hi is exact
 // in FP32): the pair holds x to 2^-18 relative.
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
@@ -1218,7 +1421,8 @@ EncodeTiledFn encoder() {
 // fill out of bounds.  The base must be 16-byte aligned and the line pitch a
 // multiple of 16 bytes.
 cudaError_t make_map_t(CUtensorMap* map, const void* base, CUtensorMapDataType dt, int esize, long long inner,
-                       long long outer, long long ld, int box_inner, int box_outer, bool swizzle128) {
+                       long long outer, long long ld, int box_inner, int box_outer, bool swizzle128,
+                       bool swizzle64 = false) {
     EncodeTiledFn enc = encoder();
     if (!enc) return cudaErrorNotSupported;
     if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0 || ((ld * esize) & 15) != 0 || inner < box_inner ||
@@ -1229,7 +1433,9 @@ cudaError_t make_map_t(CUtensorMap* map, const void* base, CUtensorMapDataType d
     const cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
     const cuuint32_t es[2] = {1, 1};
     const CUresult r = enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                           swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                           swizzle128  ? CU_TENSOR_MAP_SWIZZLE_128B
+                           : swizzle64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                       : CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -1244,6 +1450,12 @@ cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, long long inne
                      int box_inner, int box_outer, bool swizzle128) {
     return make_map_t(map, base, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, inner, outer, ld, box_inner, box_outer,
                       swizzle128);
+}
+
+// BF16 map with the 64-byte swizzle (boxes of 32 elements along `inner`).
+cudaError_t make_map_sw64(CUtensorMap* map, const __nv_bfloat16* base, long long inner, long long outer,
+                          long long ld, int box_outer) {
+    return make_map_t(map, base, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, inner, outer, ld, 32, box_outer, false, true);
 }
 
 constexpr int kUpdNJ = 128, kUpdStages = 2;
@@ -1596,6 +1808,29 @@ cudaError_t update16(Ctx& cx, const __nv_bfloat16* Wsrc, long long ldws, __nv_bf
                      double* sq_out) {
     UpdateParams16 p;
     cudaError_t e;
+    if (n >= kNJw && m >= kBM && np % kKCw == 0) {
+        // 128 x 256 tiles (k_update16w)
+        if ((e = make_map_sw64(&p.mqt, Qt, np, m, np, kBM)) != cudaSuccess) return e;
+        if ((e = make_map_sw64(&p.mqtl, Qtl, np, m, np, kBM)) != cudaSuccess) return e;
+        if ((e = make_map_sw64(&p.mbs, Bs, np, n, np, kNJw)) != cudaSuccess) return e;
+        if ((e = make_map_sw64(&p.mbsl, Bsl, np, n, np, kNJw)) != cudaSuccess) return e;
+        if ((e = make_map(&p.mws, Wsrc, m, n, ldws, kBM, 64, false)) != cudaSuccess) return e;
+        if ((e = make_map(&p.mwd, Wdst, m, n, ldwd, kBM, 64, false)) != cudaSuccess) return e;
+        p.st = cx.st;
+        p.sq_part = sq_out ? sq_part : nullptr;
+        p.m = m; p.n = n;
+        p.RT = (int)((m + kBM - 1) / kBM);
+        p.CT = (int)((n + kNJw - 1) / kNJw);
+        p.C = np / kKCw;
+        const long long T = (long long)p.RT * p.CT;
+        const int grid = (int)std::min<long long>(cx.num_sms, T);
+        if (sq_out && grid > sq_cap) return cudaErrorInvalidValue;
+        if ((e = allow_smem(k_update16w, kUpd16wSmem)) != cudaSuccess) return e;
+        k_update16w<<<grid, kUpd16Threads, kUpd16wSmem, cx.stream>>>(p);
+        cx.launches++;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        return sq_out ? launch_sum_doubles(cx, sq_part, grid, sq_out) : cudaSuccess;
+    }
     if ((e = make_map(&p.mqt, Qt, np, m, np, kKC16, kBM, true)) != cudaSuccess) return e;
     if ((e = make_map(&p.mqtl, Qtl, np, m, np, kKC16, kBM, true)) != cudaSuccess) return e;
     if ((e = make_map(&p.mbs, Bs, np, n, np, kKC16, kUpdNJ, true)) != cudaSuccess) return e;

@@ -149,6 +149,19 @@ __device__ __forceinline__ uint64_t desc_k_sw128(uint32_t addr) {
     return d;
 }
 
+// K-major operand with the 64-byte swizzle: rows of 64 bytes (32 BF16 of K),
+// eight rows per 512-byte atom (SBO = 512); a K = 16 step advances the start
+// address by 32 bytes.
+__device__ __forceinline__ uint64_t desc_k_sw64(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
+    return d;
+}
+
 // Instruction descriptor of kind::tf32, D = F32, A = B = TF32, both K-major,
 // M = 128, N = n (multiple of 16, <= 256).
 __host__ __device__ constexpr uint32_t idesc_tf32(int n) {

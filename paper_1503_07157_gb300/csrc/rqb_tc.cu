@@ -666,6 +666,207 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_update(const __grid_constant
     }
 }
 
+// Wide split-TF32 update / product: the same as k_update on 128 x 256 tiles
+// (N = 256 MMAs: a quarter fewer operand bytes per multiply-add), K in chunks
+// of 16 (64-byte swizzle rows, 48 KB per stage) through three stages, and W
+// in 128 x 32 eighths of the tile through a ring of four 16 KB buffers
+// (warp 10 loads eighth w into slot w % 4 in update mode; one epilogue thread
+// stores it and hands the previous slot back once that store has read it).
+// TMEM: two 256-column accumulators.
+constexpr int kKCt = 16;                            // K per chunk (one 64-byte swizzle row of FP32)
+constexpr int kNJt = 256;                           // tile columns
+constexpr int kStt = 3;                             // operand stages
+constexpr int kWRt = 4;                             // W eighth buffers
+constexpr uint32_t kQt = kBM * kKCt * 4;            // Q_i^T hi or lo chunk: 8 KB
+constexpr uint32_t kBt = kNJt * kKCt * 4;           // B hi or lo chunk: 16 KB
+constexpr uint32_t kStageT = 2 * kQt + 2 * kBt;     // 48 KB
+constexpr uint32_t kWEt = kBM * 32 * 4;             // W eighth: 16 KB
+constexpr size_t kUpdwSmem = (size_t)kStt * kStageT + (size_t)kWRt * kWEt + 1024;
+
+__global__ void __launch_bounds__(kUpdThreads, 1) k_updatew(const __grid_constant__ UpdateParams p) {
+    __shared__ __align__(8) uint64_t full[kStt], empty[kStt], accfull[2], accempty[2], wfull[kWRt], wempty[kWRt],
+        drain;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ double red[8];
+    extern __shared__ uint8_t dsm[];
+    uint8_t* base = dsm + (((smem_u32(dsm) + 1023u) & ~1023u) - smem_u32(dsm));
+    uint8_t* wbuf = base + kStt * kStageT;
+    constexpr uint32_t kCols = 2u * kNJt;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int* ab = &abort_flag;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStt; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int s = 0; s < 2; ++s) { mbar_init(&accfull[s], 1); mbar_init(&accempty[s], 8); }
+        for (int s = 0; s < kWRt; ++s) { mbar_init(&wfull[s], 1); mbar_init(&wempty[s], 1); }
+        mbar_init(&drain, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+        prefetch_map(&p.mqt);
+        prefetch_map(&p.mqtl);
+        prefetch_map(&p.mbs);
+        prefetch_map(&p.mbsl);
+        prefetch_map(&p.mws);
+        prefetch_map(&p.mwd);
+    }
+    if (warp == 1) tmem_alloc(&tmem_base, kCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const int T = p.RT * p.CT;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            long long q = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < T && !stop; t += gridDim.x) {
+                const int rt = t / p.CT, ctile = t % p.CT;
+                for (int kc = 0; kc < p.C; ++kc, ++q) {
+                    const int s = (int)(q % kStt);
+                    const uint32_t r = (uint32_t)(q / kStt);
+                    if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1u, ab)) { stop = true; break; }
+                    uint8_t* st = base + s * kStageT;
+                    mbar_arrive_expect_tx(&full[s], kStageT);
+                    tma_load_2d(st, &p.mqt, kc * kKCt, rt * kBM, &full[s]);
+                    tma_load_2d(st + kQt, &p.mqtl, kc * kKCt, rt * kBM, &full[s]);
+                    tma_load_2d(st + 2 * kQt, &p.mbs, kc * kKCt, ctile * kNJt, &full[s]);
+                    tma_load_2d(st + 2 * kQt + kBt, &p.mbsl, kc * kKCt, ctile * kNJt, &full[s]);
+                }
+            }
+            for (long long qq = (q > kStt ? q - kStt : 0); qq < q; ++qq)
+                mbar_wait(&full[qq % kStt], (uint32_t)(qq / kStt) & 1u, ab, false);
+        }
+    } else if (warp == 10) {
+        if (lane == 0) {
+            long long w = 0;   // eighths issued
+            bool stop = false;
+            for (int t = blockIdx.x; t < T && !stop; t += gridDim.x) {
+                for (int qq = 0; qq < 8; ++qq, ++w) {
+                    const int slot = (int)(w % kWRt);
+                    const long long use = w / kWRt;
+                    if (use > 0 && !mbar_wait(&wempty[slot], (uint32_t)(use - 1) & 1u, ab)) { stop = true; break; }
+                    if (p.sub) {
+                        mbar_arrive_expect_tx(&wfull[slot], kWEt);
+                        tma_load_2d(wbuf + slot * kWEt, &p.mws, (t / p.CT) * kBM, (t % p.CT) * kNJt + qq * 32,
+                                    &wfull[slot]);
+                    } else {
+                        mbar_arrive(&wfull[slot]);   // the buffer is free; nothing to load
+                    }
+                }
+            }
+            if (p.sub)
+                for (long long ww = (w > kWRt ? w - kWRt : 0); ww < w; ++ww)
+                    mbar_wait(&wfull[ww % kWRt], (uint32_t)(ww / kWRt) & 1u, ab, false);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_tf32(kNJt);
+            long long q = 0;
+            int g = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < T && !stop; t += gridDim.x, ++g) {
+                const int abuf = g & 1, use = g >> 1;
+                if (use > 0 && !mbar_wait(&accempty[abuf], (uint32_t)(use - 1) & 1u, ab)) break;
+                const uint32_t d = tmem + (uint32_t)(abuf * kNJt);
+                for (int kc = 0; kc < p.C; ++kc, ++q) {
+                    const int s = (int)(q % kStt);
+                    const uint32_t r = (uint32_t)(q / kStt);
+                    if (!mbar_wait(&full[s], r & 1u, ab)) { stop = true; break; }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(base + s * kStageT), a1 = a0 + kQt;
+                    const uint32_t b0 = a0 + 2 * kQt, b1 = b0 + kBt;
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk)
+                        mma_tf32(d, desc_k_sw64(a0 + kk * 32), desc_k_sw64(b0 + kk * 32), idesc,
+                                 (kc == 0 && kk == 0) ? 0u : 1u);
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk)
+                        mma_tf32(d, desc_k_sw64(a0 + kk * 32), desc_k_sw64(b1 + kk * 32), idesc, 1u);
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk)
+                        mma_tf32(d, desc_k_sw64(a1 + kk * 32), desc_k_sw64(b0 + kk * 32), idesc, 1u);
+                    mma_commit(&empty[s]);
+                }
+                if (stop) break;
+                mma_commit(&accfull[abuf]);
+            }
+            mma_commit(&drain);
+            mbar_wait(&drain, 0, ab, false);
+        }
+    } else {
+        const int e = warp - 2;
+        const int quarter = warp & 3;                 // TMEM lanes this warp may read
+        const int half = e >> 2;                      // columns [16 half, 16 half + 16) of each W eighth
+        const bool issuer = (warp == 2 && lane == 0);
+        const int row = quarter * 32 + lane;          // tile row of this thread
+        double sq = 0.0;
+        int g = 0;
+        long long w = 0;                              // eighths consumed
+        bool stop = false;
+        for (int t = blockIdx.x; t < T && !stop; t += gridDim.x, ++g) {
+            const int abuf = g & 1, use = g >> 1;
+            const bool oka = mbar_wait(&accfull[abuf], (uint32_t)use & 1u, ab);
+            const int rt = t / p.CT, ctile = t % p.CT;
+            const long long r = (long long)rt * kBM + row;
+            const bool rok = r < p.m;
+            for (int qq = 0; qq < 8; ++qq, ++w) {
+                const int slot = (int)(w % kWRt);
+                bool okw = oka && mbar_wait(&wfull[slot], (uint32_t)(w / kWRt) & 1u, ab);
+                // all eight warps leave together (the named barrier below counts them)
+                named_barrier(1, 256);
+                if (*ab || !okw) { stop = true; break; }
+                tc_fence_after();
+                const long long j0 = (long long)ctile * kNJt + qq * 32 + half * 16;
+                // W eighth column-major: element (row, col) at col * 512 + row * 4
+                float* wt = reinterpret_cast<float*>(wbuf + slot * kWEt) + row;
+                const uint32_t tl =
+                    tmem + (uint32_t)(abuf * kNJt + qq * 32 + half * 16) + ((uint32_t)(quarter * 32) << 16);
+                float v[16];
+                tmem_ld16(tl, v);
+                float sq16 = 0.f;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int cl = half * 16 + i;
+                    const float d = p.sub ? wt[cl * kBM] - v[i] : v[i];
+                    wt[cl * kBM] = d;
+                    if (rok && j0 + i < p.n) sq16 = fmaf(d, d, sq16);
+                }
+                sq += (double)sq16;
+                if (qq == 7) {   // the accumulator is read: hand it back
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&accempty[abuf]);
+                }
+                fence_async_smem();
+                named_barrier(1, 256);
+                if (issuer) {
+                    tma_store_2d(&p.mwd, rt * kBM, ctile * kNJt + qq * 32, wbuf + slot * kWEt);
+                    bulk_commit();
+                    // the previous eighth's store has read its buffer: hand it back
+                    bulk_wait_read<1>();
+                    if (w > 0) mbar_arrive(&wempty[(w - 1) % kWRt]);
+                }
+            }
+        }
+        if (issuer) bulk_wait<0>();
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (lane == 0) red[e] = sq;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, kCols);
+    if (threadIdx.x == 0) {
+        if (abort_flag) record_error(p.st, RQB_ERR_TIMEOUT);
+        if (p.sq_part) {
+            double t = 0.0;
+            for (int i = 0; i < 8; ++i) t += red[i];
+            p.sq_part[blockIdx.x] = t;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Small kernels around the products.
 
@@ -1452,6 +1653,12 @@ cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, long long inne
                       swizzle128);
 }
 
+// FP32 map with the 64-byte swizzle (boxes of 16 elements along `inner`).
+cudaError_t make_map_sw64(CUtensorMap* map, const float* base, long long inner, long long outer, long long ld,
+                          int box_outer) {
+    return make_map_t(map, base, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, inner, outer, ld, 16, box_outer, false, true);
+}
+
 // BF16 map with the 64-byte swizzle (boxes of 32 elements along `inner`).
 cudaError_t make_map_sw64(CUtensorMap* map, const __nv_bfloat16* base, long long inner, long long outer,
                           long long ld, int box_outer) {
@@ -1648,6 +1855,29 @@ cudaError_t update_impl(Ctx& cx, const float* Wsrc, long long ldws, float* Wdst,
     if (!sub) {
         Wsrc = Wdst;     // the source map is not read
         ldws = ldwd;
+    }
+    if (n >= kNJt && m >= kBM && np % kKCt == 0) {
+        // 128 x 256 tiles (k_updatew)
+        if ((e = make_map_sw64(&p.mqt, Qt, np, m, np, kBM)) != cudaSuccess) return e;
+        if ((e = make_map_sw64(&p.mqtl, Qtl, np, m, np, kBM)) != cudaSuccess) return e;
+        if ((e = make_map_sw64(&p.mbs, Bs, np, n, np, kNJt)) != cudaSuccess) return e;
+        if ((e = make_map_sw64(&p.mbsl, Bsl, np, n, np, kNJt)) != cudaSuccess) return e;
+        if ((e = make_map(&p.mws, Wsrc, m, n, ldws, kBM, 32, false)) != cudaSuccess) return e;
+        if ((e = make_map(&p.mwd, Wdst, m, n, ldwd, kBM, 32, false)) != cudaSuccess) return e;
+        p.st = cx.st;
+        p.sq_part = sq_out ? sq_part : nullptr;
+        p.m = m; p.n = n;
+        p.RT = (int)((m + kBM - 1) / kBM);
+        p.CT = (int)((n + kNJt - 1) / kNJt);
+        p.C = np / kKCt;
+        const long long T = (long long)p.RT * p.CT;
+        const int grid = (int)std::min<long long>(cx.num_sms, T);
+        if (sq_out && grid > sq_cap) return cudaErrorInvalidValue;
+        if ((e = allow_smem(k_updatew, kUpdwSmem)) != cudaSuccess) return e;
+        k_updatew<<<grid, kUpdThreads, kUpdwSmem, cx.stream>>>(p);
+        cx.launches++;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        return sq_out ? launch_sum_doubles(cx, sq_part, grid, sq_out) : cudaSuccess;
     }
     if ((e = make_map(&p.mqt, Qt, np, m, np, kKC, kBM, true)) != cudaSuccess) return e;
     if ((e = make_map(&p.mqtl, Qtl, np, m, np, kKC, kBM, true)) != cudaSuccess) return e;

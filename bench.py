@@ -213,12 +213,15 @@ def alu_peak_tflops(dtype: str, num_sms: int, sm_mhz: float) -> float:
     return num_sms * lanes * 2.0 * sm_mhz * 1e6 / 1e12
 
 
-# DRAM bytes (read + write) per launch of each workload's dominant kernel from
-# ncu captures (profiles/): fp32: k_gemm_nn_pipe sketch at 20000 x 16000
-# (1.294 GB + 0.122 GB); mixed and bf16: k_update / k_update16 captured at
-# 8192 x 8192 (538.7 MB / 247 MB) scaled by the 8x elements of a
-# 32768 x 16384 launch; None where no capture of the current kernel exists.
-NCU_TRAFFIC = {"fp32": 1.416e9, "fp64": None, "mixed": 4.31e9, "bf16": 1.98e9}
+# DRAM bytes (read + write) per launch of the dominant kernel, keyed by
+# (workload, phase), from ncu captures (profiles/): fp32 sketch:
+# k_gemm_nn_pipe at 20000 x 16000 (1.294 GB + 0.122 GB); mixed projection:
+# k_streamk<project> at 8192 x 8192 (298.1 MB) scaled by the 8x elements of a
+# 32768 x 16384 launch; mixed and bf16 updates: k_updatew / k_update16w at
+# 8192 x 8192 scaled the same way; None where no capture of the current
+# kernel exists.
+NCU_TRAFFIC = {("fp32", "sketch"): 1.416e9, ("mixed", "project"): 2.385e9,
+               ("mixed", "downdate"): 4.383e9, ("bf16", "downdate"): 1.966e9}
 
 
 def oracle_modes(w: dict) -> tuple[int, int]:
@@ -322,10 +325,12 @@ def run_ours(args, w: dict, rank: int, world: int, dist):
         peak = bf16 if is16 else bf16 / 2.0
         sfx = "16" if is16 else ""
         kern = {"sketch": f"k_streamk{sfx}<sketch> + k_reduce_sketch",
-                "project": f"k_streamk{sfx}<project> + k_reduce_project{sfx}", "downdate": f"k_update{sfx}"}[dom]
+                "project": f"k_streamk{sfx}<project> + k_reduce_project{sfx}",
+                "downdate": f"k_update{sfx}w" if n >= 256 else f"k_update{sfx}"}[dom]
         es = 2 if is16 else 4
         roofline = {"bound": "tensor", "kernel": kern, "achieved": round(achieved, 3), "peak": round(peak, 3),
-                    "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(w.get("key")),
+                    "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                    "traffic": NCU_TRAFFIC.get((w.get("key"), dom)),
                     "peak_source": (f"measured bf16 burst {bf16} TFLOP/s (MEASURED_PEAKS.json), of measured" if is16
                                     else f"measured bf16 burst {bf16} TFLOP/s (MEASURED_PEAKS.json) x 1/2 "
                                          f"(nominal TF32:BF16 dense ratio), of measured"),
@@ -344,7 +349,7 @@ def run_ours(args, w: dict, rank: int, world: int, dist):
                     "kernel": f"{dom} (k_gemm_{'nn_pipe' if dom == 'sketch' else 'tn'} + split reduction)"
                     if dom in ("sketch", "project") else dom,
                     "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
-                    "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(w.get("key")),
+                    "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get((w.get("key"), dom)),
                     "peak_source": f"derived: {props.multi_processor_count} SMs x "
                                    f"{'128 FP32' if w['dtype'] == 'float32' else '2 FP64'} lanes x 2 x {sm_max:.0f} MHz",
                     "phase_ms_per_step": per_step}

@@ -338,7 +338,10 @@ __global__ void __launch_bounds__(320, 1) k_streamk16(const __grid_constant__ St
     const uint32_t tmem = tmem_base;
     const long long u0 = unit_begin(p.U, p.P, blockIdx.x), u1 = unit_begin(p.U, p.P, blockIdx.x + 1);
     auto seg_end = [&](long long u) { return u + 1 == u1 || (u + 1) % p.C == 0; };
-    auto period_end = [&](long long u) { return seg_end(u) || ((u % p.C) + 1) % kPeriod == 0; };
+    // the one-pass sketch accumulates four K-chunks (16 MMAs, as the
+    // split-TF32 sketch) per period, the two-pass projection two (16 MMAs)
+    constexpr int kPer16 = (ROLE == kSketch) ? 2 * kPeriod : kPeriod;
+    auto period_end = [&](long long u) { return seg_end(u) || ((u % p.C) + 1) % kPer16 == 0; };
 
     if (warp == 0) {
         if (lane == 0) {

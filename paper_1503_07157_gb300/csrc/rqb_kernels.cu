@@ -671,7 +671,7 @@ static cudaError_t nn_launch(Ctx& cx, const NNArgs<T>& a) {
                       (a.csk % V == 0);
     int threads = pipe ? P::NT : G::NT;
     size_t dsmem = pipe ? P::SMEM : 0;
-    if (pipe) {
+    if (pipe && P::SMEM > 48 * 1024) {   // beyond the default dynamic shared-memory limit
         static bool attr_set = false;   // one instantiation per tile shape
         if (!attr_set) {
             cudaError_t e = cudaFuncSetAttribute(kernp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM);

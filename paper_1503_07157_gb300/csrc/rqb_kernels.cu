@@ -671,7 +671,9 @@ static cudaError_t nn_launch(Ctx& cx, const NNArgs<T>& a) {
                       (a.csk % V == 0);
     int threads = pipe ? P::NT : G::NT;
     size_t dsmem = pipe ? P::SMEM : 0;
-    if (pipe && P::SMEM > 48 * 1024) {   // beyond the default dynamic shared-memory limit
+    if (pipe) {
+        // the FP64 64 x 128 tile's 48 KB of dynamic shared memory plus the
+        // kernel's static reduction buffer exceed the default limit
         static bool attr_set = false;   // one instantiation per tile shape
         if (!attr_set) {
             cudaError_t e = cudaFuncSetAttribute(kernp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM);

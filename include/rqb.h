@@ -137,7 +137,8 @@ typedef struct {
 typedef struct rqb_handle_s* rqb_handle;
 
 /* Create a handle on the current CUDA device.  cfg is copied.
- * Errors: RQB_ERR_INVALID (null pointer, unknown dtype/prec, flags != 0),
+ * Errors: RQB_ERR_INVALID (null pointer, unknown dtype/prec, a flag bit other
+ *         than the RQB_FLAG_* ones, max_rank < 0, power outside 0..8),
  *         RQB_ERR_UNSUPPORTED (dtype/prec pair not built: TF32X3 needs
  *         RQB_F32, RQB_PREC_BF16 needs RQB_BF16, and a BF16 handle needs
  *         power = 0), RQB_ERR_OOM. */

@@ -128,23 +128,38 @@ def orth(Y, return_r: bool = False):
     return (Q, R) if return_r else Q
 
 
-def sketch(A, seed: int, col0: int, p: int, omega_prec: int = 64):
+def sketch(A, seed: int, col0: int, p: int, omega_prec: int = 64, lda_pad: int = 0, ldy_pad: int = 0):
+    """A Omega(:, col0 : col0 + p).  lda_pad / ldy_pad > 0 place A and Y in
+    taller buffers (leading dims m + pad) to exercise the strided forms."""
     A = _f64(A)
     m, n = A.shape
-    Y = np.zeros((m, p), order="F")
-    _lib().orc_sketch(_ptr(A), m, n, m, seed, col0, p, omega_prec, _ptr(Y), m)
-    return Y
+    lda, ldy = m + lda_pad, m + ldy_pad
+    Abuf = np.zeros((lda, n), order="F")
+    Abuf[:m, :] = A
+    Ybuf = np.full((ldy, p), np.nan, order="F")
+    _lib().orc_sketch(_ptr(Abuf), m, n, lda, seed, col0, p, omega_prec, _ptr(Ybuf), ldy)
+    if ldy_pad and not np.all(np.isnan(Ybuf[m:, :])):
+        raise AssertionError("orc_sketch wrote past row m of a strided Y")
+    return Ybuf[:m, :].copy(order="F")
 
 
-def orth_reproject(Y, Qbar):
+def orth_reproject(Y, Qbar, ld_pad: int = 0):
+    """Lines (3), (3').  ld_pad > 0 places Y, Qbar and Q_i in taller buffers
+    (leading dims m + pad) to exercise the strided forms."""
     Y = _f64(Y)
     m, p = Y.shape
     Qbar = _f64(Qbar) if Qbar is not None and Qbar.shape[1] > 0 else np.zeros((m, 0), order="F")
     kprev = Qbar.shape[1]
-    Qi = np.zeros((m, p), order="F")
-    qb = Qbar if kprev > 0 else np.zeros((m, 1), order="F")
-    _lib().orc_orth_reproject(_ptr(Y), m, p, m, _ptr(qb), kprev, m, _ptr(Qi), m)
-    return Qi
+    ld = m + ld_pad
+    Ybuf = np.zeros((ld, p), order="F")
+    Ybuf[:m, :] = Y
+    qb = np.zeros((ld, max(kprev, 1)), order="F")
+    qb[:m, :kprev] = Qbar
+    Qi = np.full((ld, p), np.nan, order="F")
+    _lib().orc_orth_reproject(_ptr(Ybuf), m, p, ld, _ptr(qb), kprev, ld, _ptr(Qi), ld)
+    if ld_pad and not np.all(np.isnan(Qi[m:, :])):
+        raise AssertionError("orc_orth_reproject wrote past row m of a strided Q_i")
+    return Qi[:m, :].copy(order="F")
 
 
 @dataclass

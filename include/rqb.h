@@ -320,9 +320,11 @@ int rqb_downdate_sketch(rqb_handle h, const void* A, int64_t lda, const void* Qi
  *   normA2 host pointer or NULL; when non-NULL the call synchronises stream
  *   stream cudaStream_t (NULL: legacy default stream)
  * Errors: RQB_ERR_INVALID (bad argument), RQB_ERR_SCRATCH_LIMIT when the
- * Omega block (n * ncols rounded up to 32/64/128/256 columns) or the row
- * tiles (m / 128 > 8192) do not fit the fixed scratch -- nothing is launched
- * then; RQB_ERR_CUDA on a runtime error.
+ * Omega block (n * ncols rounded up to 32/64/128/256 columns) does not fit
+ * the fixed scratch, or when normA2 is asked for and the product has more
+ * than 8192 row tiles (tiles of 128 rows for FP32 with ncols <= 128, else of
+ * 64 rows: m > 1048576 or m > 524288) -- nothing is launched then;
+ * RQB_ERR_CUDA on a runtime error.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
  * before any stream capture.  All calls share the one array and it keeps the

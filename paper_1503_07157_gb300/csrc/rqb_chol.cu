@@ -451,11 +451,8 @@ cudaError_t upper_inverse(Ctx& cx, const double* R, int bp, T* Rinv) {
     using W = T;
     const size_t smem = sizeof(W) * ((size_t)bp * (bp + 1) / 2 + 8 * (size_t)bp);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_upper_inverse<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
+    cudaError_t ea = smem_limit(k_upper_inverse<T, W>, 200 * 1024);
+    if (ea != cudaSuccess) return ea;
     k_upper_inverse<T, W><<<(bp + 7) / 8, 256, smem, cx.stream>>>(R, bp, Rinv);
     cx.launches++;
     return cudaGetLastError();
@@ -504,19 +501,13 @@ cudaError_t chol_inv_blocked(Ctx& cx, double* G, int bp, int p, double* R, T* Ri
     if constexpr (f32) {
         const size_t smem = sizeof(float) * ((size_t)bp * kXs + 2 * (size_t)bp * kNb + 2 * kNb * kNb + kNb * kXs);
         if (smem > 200 * 1024) return cudaErrorInvalidValue;
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaFuncSetAttribute(k_linv_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            attr_set = true;
-        }
+        cudaError_t ea = smem_limit(k_linv_f32, 200 * 1024);
+        if (ea != cudaSuccess) return ea;
         k_linv_f32<<<nblk, 256, smem, cx.stream>>>(Lf, Lif, bp, Rinv);
     } else {
         const size_t smem = sizeof(T) * ((size_t)bp * kNb + (size_t)bp * (kNb + 1) + 2 * (size_t)kNb * (kNb + 1));
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaFuncSetAttribute(k_linv_blocked<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            attr_set = true;
-        }
+        cudaError_t ea = smem_limit(k_linv_blocked<T, T>, 200 * 1024);
+        if (ea != cudaSuccess) return ea;
         k_linv_blocked<T, T><<<nblk, 256, smem, cx.stream>>>(L, Linv, bp, Rinv);
     }
     cx.launches++;

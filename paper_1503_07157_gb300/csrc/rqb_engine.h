@@ -5,9 +5,36 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <mutex>
+#include <set>
+#include <tuple>
+
 #include "rqb_internal.cuh"
 
 namespace rqb {
+
+// Raises `kernel`'s dynamic shared-memory limit to `bytes` on the current
+// device.  The attribute is per device, so the call is made once per
+// (kernel, device, bytes) and remembered under a lock: several host threads
+// and several devices may launch the same kernel.
+inline cudaError_t smem_limit_once(const void* kernel, int bytes) {
+    static std::mutex mu;
+    static std::set<std::tuple<const void*, int, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_tuple(kernel, dev, bytes);
+    if (done.count(key)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.insert(key);
+    return e;
+}
+
+template <typename K>
+inline cudaError_t smem_limit(K kernel, int bytes) {
+    return smem_limit_once(reinterpret_cast<const void*>(kernel), bytes);
+}
 
 struct Ctx {
     cudaStream_t stream = nullptr;

@@ -674,12 +674,8 @@ static cudaError_t nn_launch(Ctx& cx, const NNArgs<T>& a) {
     if (pipe) {
         // the FP64 64 x 128 tile's 48 KB of dynamic shared memory plus the
         // kernel's static reduction buffer exceed the default limit
-        static bool attr_set = false;   // one instantiation per tile shape
-        if (!attr_set) {
-            cudaError_t e = cudaFuncSetAttribute(kernp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM);
-            if (e != cudaSuccess) return e;
-            attr_set = true;
-        }
+        cudaError_t e = smem_limit(kernp, (int)P::SMEM);
+        if (e != cudaSuccess) return e;
     }
     const int64_t kalign = pipe ? NNPipeCfg<T>::BK : NNTile<T>::BK;
     const int64_t mt = (a.m + BM - 1) / BM;
@@ -825,12 +821,11 @@ cudaError_t gemm_tn_f64acc(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, i
 template <typename T>
 cudaError_t chol_inv(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, bool fp64_factor, double* scratch,
                      size_t scratch_doubles) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_cholesky<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_cholesky<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_tri_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
+    for (const void* k : {reinterpret_cast<const void*>(k_cholesky<double>),
+                          reinterpret_cast<const void*>(k_cholesky<float>),
+                          reinterpret_cast<const void*>(k_tri_inverse<T>)}) {
+        cudaError_t ea = smem_limit_once(k, 200 * 1024);
+        if (ea != cudaSuccess) return ea;
     }
     // relative pivot below which a panel column counts as dependent: rounding
     // of the panel itself leaves pivots of order u^2 (1e-32 for FP64 data,
@@ -867,11 +862,8 @@ cudaError_t chol_inv(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, bool
 // diagonal are ignored), result in T.
 template <typename T>
 cudaError_t tri_inverse(Ctx& cx, const double* R, int kdim, T* Rinv) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_tri_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
+    cudaError_t ea = smem_limit(k_tri_inverse<T>, 200 * 1024);
+    if (ea != cudaSuccess) return ea;
     const int staged_cols = (int)std::min<int64_t>(kdim, std::max<int64_t>(0, (200 * 1024 / 8) / kdim - 5));
     const int cmax_all = std::min(kdim, staged_cols);
     const size_t smem2 = sizeof(double) * (size_t)(5 * (int64_t)kdim + (int64_t)kdim * std::max(cmax_all, 1));
@@ -908,11 +900,8 @@ static cudaError_t dd_launch(Ctx& cx, int64_t m, int64_t n, int p, const T* Wsrc
                              double* nrm_out) {
     using C = DDCfg<T, BM, BN>;
     auto kern = k_downdate_sketch<T, BM, BN>;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        attr = true;
-    }
+    cudaError_t ea = smem_limit(kern, (int)C::SMEM);
+    if (ea != cudaSuccess) return ea;
     const int64_t mt = (m + BM - 1) / BM;
     const int slots = cx.num_sms * occupancy(kern, C::NT, C::SMEM);
     const int64_t per = m * (int64_t)BN;

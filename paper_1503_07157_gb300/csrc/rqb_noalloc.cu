@@ -60,7 +60,11 @@ int sketch_noalloc(const T* A, int64_t m, int64_t n, int64_t lda, int64_t col0, 
     const size_t om_bytes = sizeof(T) * (size_t)n * (size_t)bp;
     const size_t off_part = align256(off_om + om_bytes);
     if (off_part > kScratchBytes) return RQB_ERR_SCRATCH_LIMIT;
-    if ((m + 127) / 128 > kNrmSlots) return RQB_ERR_SCRATCH_LIMIT;
+    // one FP64 norm partial per row tile of the product; the tile height is
+    // gemm_nn's: 128 rows for FP32 up to 128 columns, 64 rows for FP32 at 256
+    // columns and for every FP64 product
+    const int64_t bm = (sizeof(T) == 4 && bp <= 128) ? 128 : 64;
+    if (normA2 && (m + bm - 1) / bm > kNrmSlots) return RQB_ERR_SCRATCH_LIMIT;
     void* base = nullptr;
     int rc = scratch_address(&base);
     if (rc != RQB_OK) return rc;

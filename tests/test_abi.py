@@ -52,3 +52,25 @@ def test_null_handle_rejected_without_gpu(lib):
 
 def test_library_is_in_tree():
     assert os.path.dirname(rqb.LIB_PATH) == os.path.dirname(os.path.abspath(rqb.__file__))
+
+
+@pytest.mark.parametrize("dtype,ncols,m,want_norm,expect", [
+    # FP64 products use 64-row tiles: 600000 rows are 9375 norm partials > 8192
+    ("f64", 64, 600000, True, "RQB_ERR_SCRATCH_LIMIT"),
+    # FP32 at 256 columns also uses 64-row tiles
+    ("f32", 256, 600000, True, "RQB_ERR_SCRATCH_LIMIT"),
+    # FP32 at 128 columns: 128-row tiles, 1048577 rows need 8193 partials
+    ("f32", 128, 1048577, True, "RQB_ERR_SCRATCH_LIMIT"),
+    # an Omega block beyond the array is rejected whether or not the norm is asked for
+    ("f32", 128, 64, False, "RQB_ERR_SCRATCH_LIMIT"),
+])
+def test_noalloc_rejects_before_any_launch_without_gpu(lib, dtype, ncols, m, want_norm, expect):
+    """The capacity checks run on the host before any CUDA call, so they need no
+    GPU: the pointers below are never dereferenced."""
+    fake = ctypes.c_void_p(0x10000)
+    n = 1 << 20 if m == 64 else 16
+    dt = rqb.RQB_F64 if dtype == "f64" else rqb.RQB_F32
+    nrm = ctypes.c_double(0.0)
+    rc = lib.rqb_sketch_noalloc(dt, fake, m, n, m, 0, ncols, 0, fake, m,
+                                ctypes.byref(nrm) if want_norm else None, None)
+    assert rc == getattr(rqb, expect), rqb.status_string(rc)

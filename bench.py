@@ -479,17 +479,8 @@ def run_e2e(args, w: dict, res: dict) -> dict:
 
 
 def make_batch_device(count: int, seed: int = 0):
-    import numpy as np
-    import torch
     import inputs
-    cases = inputs.batched_sizes(count, seed=seed)
-    mats, eps = [], []
-    for i, c in enumerate(cases):
-        s = inputs.spectrum_exp(min(c.m, c.n), c.rate)
-        A = inputs.usv_torch(c.m, c.n, s, 1000 + i, device="cuda", dtype=torch.float32)
-        mats.append(A)
-        eps.append(1e-3 * float(np.sqrt(np.sum(s ** 2))))
-    return mats, eps, cases
+    return inputs.config_batched_torch(count, seed=seed)
 
 
 def run_batched(args, w: dict, rank: int, world: int, dist, do_e2e: bool = True):

@@ -14,6 +14,7 @@ Recipes (sizes and spectra):
                    b = 256, eps = 1e-3 ||A||_F
   config_batched   512 matrices, m ~ U[256, 4096], n ~ U[128, min(m, 2048)],
                    s_j = exp(-j/r), r ~ U[10, 200], b = 32, eps_t = 1e-3 ||A_t||_F
+                   (config_batched_torch builds the whole batch on the device)
   config_adjoint   8192 x 4096, N(0,1)/sqrt(4096) + planted rank 64 of norm 10,
                    k = 256 fixed, b = 64
   matrix1/2/4      the paper's Matrices 1, 2 and 4 (Sec. 6.2)
@@ -203,6 +204,20 @@ def config_mixed_torch(m: int = 32768, n: int = 16384, seed: int = 3, device="cu
     nrm = float(np.sqrt(np.sum(s ** 2)))
     A = usv_torch(m, n, s, seed, device=device)
     return A, dict(m=m, n=n, b=256, eps=1e-3 * nrm, seed_omega=0, sigma=s, normA=nrm)
+
+
+def config_batched_torch(count: int = 512, seed: int = 0, device="cuda"):
+    """The batched workload on `device`: sizes and rates from batched_sizes
+    (seed), matrix t built by usv_torch with seed 1000 + t, eps_t = 1e-3
+    ||A_t||_F (from the spectrum).  Returns (matrices, eps list, cases)."""
+    torch = _torch()
+    cases = batched_sizes(count, seed=seed)
+    mats, eps = [], []
+    for i, c in enumerate(cases):
+        s = spectrum_exp(min(c.m, c.n), c.rate)
+        mats.append(usv_torch(c.m, c.n, s, 1000 + i, device=device, dtype=torch.float32))
+        eps.append(1e-3 * float(np.sqrt(np.sum(s ** 2))))
+    return mats, eps, cases
 
 
 def config_adjoint_np(m: int = 8192, n: int = 4096, seed: int = 5, rank: int = 64, norm: float = 10.0):

@@ -134,8 +134,11 @@ def sketch(A, seed: int, col0: int, p: int, omega_prec: int = 64, lda_pad: int =
     A = _f64(A)
     m, n = A.shape
     lda, ldy = m + lda_pad, m + ldy_pad
-    Abuf = np.zeros((lda, n), order="F")
-    Abuf[:m, :] = A
+    if lda_pad:
+        Abuf = np.zeros((lda, n), order="F")
+        Abuf[:m, :] = A
+    else:
+        Abuf = A
     Ybuf = np.full((ldy, p), np.nan, order="F")
     _lib().orc_sketch(_ptr(Abuf), m, n, lda, seed, col0, p, omega_prec, _ptr(Ybuf), ldy)
     if ldy_pad and not np.all(np.isnan(Ybuf[m:, :])):

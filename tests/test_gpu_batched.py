@@ -11,7 +11,7 @@ import pytest
 import torch
 
 import inputs
-from parity_util import check_rank, orth_err, resid, to_dev, to_np
+from parity_util import assert_residual_parity, check_rank, oracle_at_rank, orth_err, resid, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -41,8 +41,8 @@ def test_batched_matches_oracle(orc, rqb_lib, b):
         nA = np.linalg.norm(A)
         assert st in (rqb_lib.RQB_OK, rqb_lib.RQB_NOT_CONVERGED), st
         check_rank(k, ro, eps, b, rel_band=1e-3)
-        if k == ro.k:
-            assert abs(resid(A, Q, B) - resid(A, ro.Q, ro.B)) <= 1e-5 * nA
+        rk = oracle_at_rank(orc, A, ro, k, b, 9, omega_prec=32)
+        assert_residual_parity(A, Q, B, rk, 1e-5, b=b, eps=eps if st == rqb_lib.RQB_OK else None)
         if st == rqb_lib.RQB_OK:
             assert resid(A, Q, B) <= eps * (1 + 1e-4)
         assert orth_err(Q) <= 1e-5

@@ -16,10 +16,17 @@ norm).  Tolerances:
                      within 2^-16 (|Q||B|)_ij of x); W_gpu equals the
                      oracle's rn_bf16(x) except at rounding ties of that size
   randQB_b           rank as the oracle's (or one block away when the oracle's
-                     stored norm is within 1e-2 of eps^2); ||Q^T Q - I|| <= 1e-5;
+                     stored norm is within 1e-2 of eps^2, then compared with the
+                     oracle rerun at the GPU's rank); ||Q^T Q - I|| <= 1e-5;
                      |  ||A - QB||_F - sqrt(D_s) | <= 1.01 2^-9 sum_i sqrt(D_i)
                      + 2e-5 sum_i sqrt(D_(i-1)) (A - QB = W_s - sum of the
-                     rounding errors, each at most 2^-9 of its block's residual)
+                     rounding errors, each at most 2^-9 of its block's residual);
+                     |r_gpu - r_oracle| within the sum of both sides' gaps and
+                     of the stored-norm band
+Entry by entry: the sketch within 1e-6 (|W| |Omega|)_ij of W Omega with the
+handle's own Omega (exact products, FP32 sums) and within that plus
+|W| |Omega_gpu - Omega_oracle| of the oracle's; the projection within
+1e-5 (|Q^T| |W|)_ij (the 2^-18 split of Q plus FP32 sums).
 Shapes span several 128-row tiles and 64-wide K chunks with ragged tails.
 """
 import numpy as np
@@ -27,7 +34,7 @@ import pytest
 import torch
 
 import inputs
-from parity_util import orth_err, resid, to_dev, to_np
+from parity_util import assert_elementwise, orth_err, product_bound, resid, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -67,6 +74,10 @@ def test_sketch(orc, hbf, m, n, p, col0):
     Yo = orc.sketch(A, 17, col0, p, omega_prec=8)
     assert np.linalg.norm(Yg - Yo) <= TOL_STEP * np.linalg.norm(Yo)
     assert abs(nrm - np.sum(A * A)) <= 1e-9 * np.sum(A * A)
+    bound = product_bound(A, Om)
+    assert_elementwise(Yg, Yh, bound, 1e-6, "BF16 sketch vs W Omega_gpu")
+    Oo = orc.omega(17, n, col0, p, prec=8)
+    assert_elementwise(Yg, Yo, bound, 1e-6, "BF16 sketch vs oracle", extra=np.abs(A) @ np.abs(Om - Oo))
 
 
 def test_sketch_unaligned_lda(orc, hbf):
@@ -89,6 +100,7 @@ def test_project(orc, hbf, m, n, p):
     Bg = to_np(Bi)
     assert np.linalg.norm(Bg - Bo) <= TOL_STEP * np.linalg.norm(Bo)
     assert abs(nb2 - np.sum(Bg * Bg)) <= 1e-12 * np.sum(Bg * Bg)
+    assert_elementwise(Bg, Bo, product_bound(Q.T, A), 1e-5, "BF16 Q^T W")
 
 
 @pytest.mark.parametrize("m,n,p,ncols,inplace", [(2000, 1000, 50, 50, False), (1037, 777, 37, 37, True),
@@ -112,6 +124,7 @@ def test_downdate_sketch(orc, hbf, m, n, p, ncols, inplace):
     Om = to_np(hbf.rqb_omega(n, 11, ncols, seed=4))
     Yh = Wg @ Om
     assert np.linalg.norm(to_np(Y) - Yh) <= 2e-6 * np.linalg.norm(Yh)
+    assert_elementwise(to_np(Y), Yh, product_bound(Wg, Om), 1e-6, "BF16 downdated W Omega")
 
 
 def _factor(rqb, A, eps, b, seed, **kw):
@@ -158,11 +171,18 @@ def test_randqb_matches_oracle(orc, rqb_lib, m, n, b, rate, rel_eps):
     assert abs(r - np.sqrt(st.D[-1])) <= _stored_gap_bound(st.D, nA * nA)
     ro_gap = abs(resid(A, ro.Q, ro.B) - np.sqrt(ro.D[-1]))
     assert ro_gap <= _stored_gap_bound(ro.D, nA * nA)
-    if k == ro.k:
-        nb = len(st.D)
-        dg, do = np.sqrt(np.array(st.D)), np.sqrt(np.array(ro.D[:nb]))
-        print("rel D gap", np.max(np.abs(dg - do) / do))
-        assert np.all(np.abs(dg - do) <= 2.0 ** -9 * np.cumsum(do) + 1e-5 * nA)
+    # at the GPU's rank (the oracle rerun to it in fixed-rank mode when a stop
+    # decision fell inside the band): the per-block stored norms agree within
+    # the roundings of the residual, and so do the residuals ||A - QB||_F
+    rk = ro if k == ro.k else orc.randqb_b(A, 0.0, b, seed=3, max_rank=k, fixed_rank=True, omega_prec=8,
+                                           storage_prec=16)
+    nb = len(st.D)
+    dg, do = np.sqrt(np.array(st.D)), np.sqrt(np.array(rk.D[:nb]))
+    print("rel D gap", np.max(np.abs(dg - do) / do))
+    assert np.all(np.abs(dg - do) <= 2.0 ** -9 * np.cumsum(do) + 1e-5 * nA)
+    r_o = resid(A, rk.Q, rk.B)
+    assert abs(r - r_o) <= (_stored_gap_bound(st.D, nA * nA) + _stored_gap_bound(rk.D, nA * nA)
+                            + 2.0 ** -9 * np.sum(do) + 1e-5 * nA)
 
 
 def test_randqb_fixed_rank_and_cap(orc, rqb_lib):

@@ -8,13 +8,20 @@ a ragged tail, and is compared element by element with the oracle's step:
   line (3') orth + reproj.   FP64: 1e-10 elementwise; FP32: orthonormal to 1e-5
   line (4)  Q^T A, ||B||^2
   line (5)  A - Q B fused with the next A Omega
+Beside each Frobenius check, every product entry is held to its own rounding
+bound, |gpu - oracle|_ij <= rtol (|X| |Y|)_ij for X Y (plus, for the sketch,
+|A| |Omega_gpu - Omega_oracle| from the generators' last-ulp differences):
+rtol = 1e-14 for FP64 and 1e-6 for FP32 (about 16 u32: a partial sum of n
+terms in FP32 drifts by ~u |x||y| per term on average).
 """
 import numpy as np
 import pytest
 import torch
 
 import inputs
-from parity_util import orth_err, to_dev, to_np
+from parity_util import assert_elementwise, orth_err, product_bound, to_dev, to_np
+
+EL64, EL32 = 1e-14, 1e-6
 
 pytestmark = pytest.mark.gpu
 
@@ -53,6 +60,10 @@ def test_sketch_fp64(orc, h64, m, n, p, col0):
     Yo = orc.sketch(A, 7, col0, p, omega_prec=64)
     assert np.linalg.norm(to_np(Y) - Yo) <= 1e-12 * np.linalg.norm(Yo)
     assert abs(nrm - np.sum(A * A)) <= 1e-12 * np.sum(A * A)
+    Om = orc.omega(7, n, col0, p, prec=64)
+    dOm = 5e-14 * max(1.0, np.abs(Om).max())
+    assert_elementwise(to_np(Y), Yo, product_bound(A, Om), EL64, "FP64 sketch",
+                       extra=dOm * np.abs(A).sum(axis=1, keepdims=True))
 
 
 @pytest.mark.parametrize("m,n,p", [(4000, 3000, 128), (1037, 777, 37), (2500, 1200, 256), (300, 4000, 32)])
@@ -63,6 +74,9 @@ def test_sketch_fp32(orc, h32, m, n, p):
     Yo = orc.sketch(A, 11, 0, p, omega_prec=32)
     assert np.linalg.norm(to_np(Y) - Yo) <= 1e-5 * np.linalg.norm(Yo)
     assert abs(nrm - np.sum(A * A)) <= 1e-9 * np.sum(A * A)
+    Om = orc.omega(11, n, 0, p, prec=32)
+    dOm = 4 * np.spacing(np.abs(Om).astype(np.float32)).astype(np.float64) + 1e-7
+    assert_elementwise(to_np(Y), Yo, product_bound(A, Om), EL32, "FP32 sketch", extra=np.abs(A) @ dOm)
 
 
 def test_sketch_padded_lda(orc, h64):
@@ -113,6 +127,7 @@ def test_project(orc, rqb_lib, dtype, tol, m, n, p):
     Bg = to_np(Bi)
     assert np.linalg.norm(Bg - Bo) <= tol * np.linalg.norm(Bo)
     assert abs(nb2 - np.sum(Bg * Bg)) <= 1e-12 * np.sum(Bg * Bg)
+    assert_elementwise(Bg, Bo, product_bound(Q.T, A), EL64 if dtype == torch.float64 else EL32, "Q^T A")
 
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-5)])
@@ -131,7 +146,16 @@ def test_downdate_sketch(orc, rqb_lib, dtype, tol, m, n, p, ncols, inplace):
     with rqb_lib.Handle(dtype) as h:
         Y, nw2 = h.rqb_downdate_sketch(Ad, to_dev(Q, dtype), to_dev(B, dtype), Wd, 5 * p, ncols, seed=21)
     Wo = A - Q @ B
-    Yo = Wo @ orc.omega(21, n, 5 * p, ncols, prec=prec)
+    Om = orc.omega(21, n, 5 * p, ncols, prec=prec)
+    Yo = Wo @ Om
     assert np.linalg.norm(to_np(Wd) - Wo) <= tol * np.linalg.norm(A)
     assert np.linalg.norm(to_np(Y) - Yo) <= tol * np.linalg.norm(A) * np.sqrt(n)
     assert abs(nw2 - np.sum(Wo * Wo)) <= 10 * tol * np.sum(A * A)
+    el = EL64 if dtype == torch.float64 else EL32
+    wscale = np.abs(A) + product_bound(Q, B)
+    assert_elementwise(to_np(Wd), Wo, wscale, el, "A - Q B")
+    if dtype == torch.float64:
+        dOm = 5e-14 * max(1.0, np.abs(Om).max()) * np.ones_like(Om)
+    else:
+        dOm = 4 * np.spacing(np.abs(Om).astype(np.float32)).astype(np.float64) + 1e-7
+    assert_elementwise(to_np(Y), Yo, wscale @ np.abs(Om), el, "(A - Q B) Omega", extra=np.abs(Wo) @ dOm)

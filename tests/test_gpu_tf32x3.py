@@ -10,6 +10,11 @@ error:
   randQB_b   rank exact (or one block away when the oracle's stop quantity is
              within the rounding band of eps^2), ||Q^T Q - I||_max <= 1e-5,
              |r_gpu - r_oracle| <= 4 2^-20 sum_i ||A^(i)||_F + 1e-5 ||A||_F
+Every step product is also checked entry by entry: |gpu - oracle|_ij <=
+TOL_EL (|X| |Y|)_ij, TOL_EL = 4e-6 (a split product keeps 2^-21 of each term
+and the FP32 sums of the tensor core round one way within a period), plus
+|A| |Omega_gpu - Omega_oracle| for the sketch, whose TF32 draw differs from the
+oracle's on a few entries by one TF32 ulp.
 Shapes span several 128-row tiles, 32-column chunks and ragged tails; the
 tensor-core path needs m >= 128 and n >= 256 (smaller shapes run the FP32
 SIMT kernels, which one test checks).
@@ -19,11 +24,13 @@ import pytest
 import torch
 
 import inputs
-from parity_util import check_rank, orth_err, resid, to_dev, to_np
+from parity_util import (assert_elementwise, check_rank, oracle_at_rank, orth_err, product_bound, resid,
+                         to_dev, to_np)
 
 pytestmark = pytest.mark.gpu
 
 TOL_STEP = 2e-5
+TOL_EL = 4e-6
 
 
 @pytest.fixture(scope="module")
@@ -54,6 +61,10 @@ def test_sketch(orc, htc, m, n, p, col0):
     Yo = orc.sketch(A, 17, col0, p, omega_prec=19)
     assert np.linalg.norm(to_np(Y) - Yo) <= TOL_STEP * np.linalg.norm(Yo)
     assert abs(nrm - np.sum(A * A)) <= 1e-9 * np.sum(A * A)
+    Om = orc.omega(17, n, col0, p, prec=19)
+    Omg = to_np(htc.rqb_omega(n, col0, p, seed=17))
+    assert_elementwise(to_np(Y), Yo, product_bound(A, Om), TOL_EL, "split-TF32 sketch",
+                       extra=np.abs(A) @ np.abs(Omg - Om))
 
 
 def test_sketch_unaligned_lda(orc, htc):
@@ -75,6 +86,7 @@ def test_project(orc, htc, m, n, p):
     Bg = to_np(Bi)
     assert np.linalg.norm(Bg - Bo) <= TOL_STEP * np.linalg.norm(Bo)
     assert abs(nb2 - np.sum(Bg * Bg)) <= 1e-12 * np.sum(Bg * Bg)
+    assert_elementwise(Bg, Bo, product_bound(Q.T, A), TOL_EL, "split-TF32 Q^T A")
 
 
 @pytest.mark.parametrize("m,n,p,ncols,inplace", [(2000, 1000, 50, 50, False), (1037, 777, 37, 37, True),
@@ -90,10 +102,16 @@ def test_downdate_sketch(orc, htc, m, n, p, ncols, inplace):
     Y, nw2 = htc.rqb_downdate_sketch(Ad, to_dev(Q, torch.float32), to_dev(B, torch.float32), Wd, 5 * p, ncols,
                                      seed=21)
     Wo = A - Q @ B
-    Yo = Wo @ orc.omega(21, n, 5 * p, ncols, prec=19)
+    Om = orc.omega(21, n, 5 * p, ncols, prec=19)
+    Yo = Wo @ Om
     assert np.linalg.norm(to_np(Wd) - Wo) <= TOL_STEP * np.linalg.norm(A)
     assert np.linalg.norm(to_np(Y) - Yo) <= TOL_STEP * np.linalg.norm(A) * np.sqrt(n)
     assert abs(nw2 - np.sum(Wo * Wo)) <= 10 * TOL_STEP * np.sum(A * A)
+    wscale = np.abs(A) + product_bound(Q, B)
+    assert_elementwise(to_np(Wd), Wo, wscale, TOL_EL, "split-TF32 A - Q B")
+    Omg = to_np(htc.rqb_omega(n, 5 * p, ncols, seed=21))
+    assert_elementwise(to_np(Y), Yo, wscale @ np.abs(Om), TOL_EL, "split-TF32 (A - Q B) Omega",
+                       extra=np.abs(Wo) @ np.abs(Omg - Om))
 
 
 @pytest.mark.parametrize("m,p,kprev", [(4000, 128, 256), (3000, 256, 512), (1037, 37, 130), (4100, 64, 1000)])
@@ -157,8 +175,8 @@ def test_randqb_matches_oracle(orc, rqb_lib, m, n, b, rate, rel_eps):
     assert orth_err(Q) <= 1e-5
     r = resid(A, Q, B)
     assert r <= eps * (1 + 1e-4)
-    if k == ro.k:
-        assert abs(r - resid(A, ro.Q, ro.B)) <= _resid_tol(ro, nA)
+    rk = oracle_at_rank(orc, A, ro, k, b, 3, omega_prec=19)
+    assert abs(r - resid(A, rk.Q, rk.B)) <= _resid_tol(rk, nA)
 
 
 def test_randqb_fixed_rank_and_cap(orc, rqb_lib):
@@ -185,6 +203,8 @@ def test_randqb_small_shape_runs_simt(orc, rqb_lib):
     assert rc == rqb_lib.RQB_OK
     check_rank(k, ro, eps, b, rel_band=1e-3)
     assert orth_err(Q) <= 1e-5
+    rk = oracle_at_rank(orc, A, ro, k, b, 1, omega_prec=32)
+    assert abs(resid(A, Q, B) - resid(A, rk.Q, rk.B)) <= 1e-5 * np.linalg.norm(A)
 
 
 def test_randqb_nonfinite(rqb_lib):

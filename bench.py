@@ -310,6 +310,8 @@ def run_ours(args, w: dict, rank: int, world: int, dist):
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(dev)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    es = {"float32": 4, "float64": 8, "bfloat16": 2}[w["dtype"]]
     if prec in (rqb.RQB_PREC_TF32X3, rqb.RQB_PREC_BF16):
         is16 = prec == rqb.RQB_PREC_BF16
         table = TC_PASSES16 if is16 else TC_PASSES
@@ -318,26 +320,41 @@ def run_ours(args, w: dict, rank: int, world: int, dist):
         idx = names.index(dom)
         per_launch_ms = phase_ms[idx] / phase_calls[idx]
         passes = table[dom]
+        # useful work of one launch (each product phase is one m x n x b product
+        # on the tensor-core path), its algorithmic bytes (one read of A; the
+        # update also writes it), and the roofline time on those terms: split
+        # passes are work the kernel executes, not useful work
         useful = 2.0 * m * n * b
-        executed = passes * useful
-        achieved = executed / (per_launch_ms * 1e-3) / 1e12
+        nbytes = (2 if dom == "downdate" else 1) * m * n * es
+        t = per_launch_ms * 1e-3
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
-        peak = bf16 if is16 else bf16 / 2.0
+        peak_tc = bf16 if is16 else bf16 / 2.0
+        t_tc, t_hbm = useful / (peak_tc * 1e12), nbytes / (hbm * 1e9)
         sfx = "16" if is16 else ""
         kern = {"sketch": f"k_streamk{sfx}<sketch> + k_reduce_sketch",
                 "project": f"k_streamk{sfx}<project> + k_reduce_project{sfx}",
                 "downdate": f"k_update{sfx}w" if n >= 256 else f"k_update{sfx}"}[dom]
-        es = 2 if is16 else 4
-        roofline = {"bound": "tensor", "kernel": kern, "achieved": round(achieved, 3), "peak": round(peak, 3),
-                    "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                    "traffic": NCU_TRAFFIC.get((w.get("key"), dom)),
-                    "peak_source": (f"measured bf16 burst {bf16} TFLOP/s (MEASURED_PEAKS.json), of measured" if is16
-                                    else f"measured bf16 burst {bf16} TFLOP/s (MEASURED_PEAKS.json) x 1/2 "
-                                         f"(nominal TF32:BF16 dense ratio), of measured"),
-                    "flops_per_launch": executed, "mma_passes": passes,
-                    "useful_tflops": round(useful / (per_launch_ms * 1e-3) / 1e12, 3),
-                    "hbm_gbs": round((2 if dom == "downdate" else 1) * m * n * es / (per_launch_ms * 1e-3) / 1e9, 1),
-                    "phase_ms_per_step": per_step}
+        tc_src = (f"measured bf16 burst {bf16} TFLOP/s (MEASURED_PEAKS.json), of measured" if is16
+                  else f"measured bf16 burst {bf16} TFLOP/s (MEASURED_PEAKS.json) x 1/2 (nominal TF32:BF16 dense "
+                       f"ratio), of measured")
+        if t_hbm >= t_tc:
+            roofline = {"bound": "hbm", "kernel": kern, "achieved": round(nbytes / t / 1e9, 1), "peak": hbm,
+                        "unit": "GB/s", "frac": round(t_hbm / t, 4),
+                        "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), of measured"}
+        else:
+            roofline = {"bound": "tensor", "kernel": kern, "achieved": round(useful / t / 1e12, 3),
+                        "peak": round(peak_tc, 3), "unit": "TFLOP/s", "frac": round(t_tc / t, 4),
+                        "peak_source": tc_src}
+        roofline.update({"traffic": NCU_TRAFFIC.get((w.get("key"), dom)),
+                         "bytes_per_launch": nbytes, "useful_flops_per_launch": useful,
+                         "roof_ms": round(max(t_tc, t_hbm) * 1e3, 4), "launch_ms": round(per_launch_ms, 4),
+                         "useful_tflops": round(useful / t / 1e12, 3), "hbm_gbs": round(nbytes / t / 1e9, 1),
+                         "mma_passes": passes, "executed_tflops": round(passes * useful / t / 1e12, 3),
+                         "executed_frac": round(passes * useful / t / 1e12 / peak_tc, 4),
+                         "tensor_peak": round(peak_tc, 3), "tensor_peak_source": tc_src,
+                         "phase_ms_per_step": per_step})
+        peak_run = peak_tc
+        peak_run_src = tc_src
     else:
         cand = [(phase_ms[i], names[i]) for i in range(len(names)) if names[i] in pf and phase_calls[i] > 0]
         dom_ms, dom = max(cand)
@@ -353,8 +370,26 @@ def run_ours(args, w: dict, rank: int, world: int, dist):
                     "peak_source": f"derived: {props.multi_processor_count} SMs x "
                                    f"{'128 FP32' if w['dtype'] == 'float32' else '2 FP64'} lanes x 2 x {sm_max:.0f} MHz",
                     "phase_ms_per_step": per_step}
+        peak_run, peak_run_src = peak, roofline["peak_source"]
+    whole = whole_run_roofline(F, m, n, s_blocks, es, ms, peak_run, peak_run_src, hbm)
     return dict(h=h, A=A, eps=eps, value=value, ms=ms, F=F, k=k, s=s_blocks, clocks=clk, roofline=roofline,
-                launches=launches // max(args.steps, 1), stream=stream)
+                whole_run=whole, launches=launches // max(args.steps, 1), stream=stream)
+
+
+def whole_run_roofline(F: float, m: int, n: int, s: int, es: int, ms: float, peak_tflops: float, peak_src: str,
+                       hbm_gbs: float) -> dict:
+    """Roofline of one whole factorization: the useful FLOPs F at the path's
+    arithmetic peak against the algorithmic bytes Bt = (3s - 1) m n sizeof(A)
+    (A read by the first sketch, then per non-last block one read for B_i and
+    one read + write for the downdate fused with the next sketch, then one read
+    for the last B_i) at the measured HBM bandwidth; frac = roofline time /
+    measured time."""
+    Bt = (3 * s - 1) * m * n * es
+    t_f, t_b = F / (peak_tflops * 1e12), Bt / (hbm_gbs * 1e9)
+    return {"useful_flops": F, "bytes": Bt, "flop_ms": round(t_f * 1e3, 4), "byte_ms": round(t_b * 1e3, 4),
+            "bound": "hbm" if t_b >= t_f else "compute", "roof_ms": round(max(t_f, t_b) * 1e3, 4),
+            "measured_ms": round(ms, 4), "frac": round(max(t_f, t_b) * 1e3 / ms, 4),
+            "peak_tflops": round(peak_tflops, 3), "peak_source": peak_src, "hbm_gbs": hbm_gbs}
 
 
 def adjoint_flops(m: int, n: int, k: int) -> float:
@@ -551,9 +586,15 @@ def run_batched(args, w: dict, rank: int, world: int, dist, do_e2e: bool = True)
                                "peak_gbs": hbm_peak, "frac": round(hbm_gbs / hbm_peak, 4),
                                "note": "(3s-1) crossings of each A plus the re-projection reads; "
                                        "the ALU bound is the binding one (16 flop/B > ridge)"}}
+    t_f, t_b = F / (peak * 1e12), model_bytes / (hbm_peak * 1e9)
+    whole = {"useful_flops": F, "bytes": model_bytes, "flop_ms": round(t_f * 1e3, 4), "byte_ms": round(t_b * 1e3, 4),
+             "bound": "hbm" if t_b >= t_f else "compute", "roof_ms": round(max(t_f, t_b) * 1e3, 4),
+             "measured_ms": round(ms, 4), "frac": round(max(t_f, t_b) * 1e3 / ms, 4), "peak_tflops": round(peak, 3),
+             "peak_source": roofline["peak_source"], "hbm_gbs": hbm_peak}
     if not do_e2e:
         h.close()
         return dict(value=aggregate_value(F, world, ms), ms=ms, F=F, clocks=clk, roofline=roofline, e2e=None,
+                    whole_run=whole,
                     launches=launches // max(args.steps, 1), extra={"count": len(mats), "k_mean": float(sum(ks)) / len(ks), "k_max": max(ks),
                                        "status_ok": int(sum(1 for s_ in sts if s_ == 0)),
                                        "loop_of_single_calls_ms": round(loop_ms, 2)})
@@ -585,6 +626,7 @@ def run_batched(args, w: dict, rank: int, world: int, dist, do_e2e: bool = True)
            "api": "pinned host copies + rqb_factor_batched"}
     h.close()
     return dict(value=aggregate_value(F, world, ms), ms=ms, F=F, clocks=clk, roofline=roofline, e2e=e2e,
+                whole_run=whole,
                 launches=launches // max(args.steps, 1), extra={"count": len(mats), "k_mean": float(sum(ks)) / len(ks), "k_max": max(ks),
                                    "status_ok": int(sum(1 for s_ in sts if s_ == 0)),
                                    "loop_of_single_calls_ms": round(loop_ms, 2)})
@@ -691,7 +733,8 @@ def main():
                                                                        {"float32": 4, "float64": 8, "bfloat16": 2}[
                                                                            w["dtype"]] / 1e9)
                        if w["m"] * w["n"] * 4 > 129e6 else "L2 not flushed: input fits in L2"},
-            "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": res["launches"]
+            "roofline": res["roofline"], "whole_run": res["whole_run"], "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": res["launches"]
             * args.steps, "clocks": res["clocks"],
         }
         if matched is not None:
@@ -722,8 +765,8 @@ def run_forms(args, rank: int, world: int, dist) -> dict:
     r = run_ours(a, wm, rank, world, dist)
     out["mixed"] = {"workload": wm["name"], "value": round(r["value"], 4), "unit": "TFLOP/s",
                     "ms_per_step": round(r["ms"], 3), "steps": a.steps, "k": r["k"], "blocks": r["s"],
-                    "roofline": r["roofline"], "plain_fp32_matched_eps": run_plain_matched(a, wm, r) if rank == 0
-                    else None}
+                    "roofline": r["roofline"], "whole_run": r["whole_run"],
+                    "plain_fp32_matched_eps": run_plain_matched(a, wm, r) if rank == 0 else None}
     r["h"].close()
     del r
     gc.collect()
@@ -732,7 +775,7 @@ def run_forms(args, rank: int, world: int, dist) -> dict:
     r = run_ours(a, w16, rank, world, dist)
     out["bf16"] = {"workload": w16["name"], "value": round(r["value"], 4), "unit": "TFLOP/s",
                    "ms_per_step": round(r["ms"], 3), "steps": a.steps, "k": r["k"], "blocks": r["s"],
-                   "roofline": r["roofline"],
+                   "roofline": r["roofline"], "whole_run": r["whole_run"],
                    "plain_fp32_matched_eps": run_plain_matched(a, w16, r) if rank == 0 else None}
     r["h"].close()
     del r
@@ -742,7 +785,8 @@ def run_forms(args, rank: int, world: int, dist) -> dict:
     a.steps = 2
     rb = run_batched(a, wb, rank, world, dist, do_e2e=False)
     out["batched"] = dict({"workload": wb["name"], "value": round(rb["value"], 4), "unit": "TFLOP/s",
-                           "ms_per_step": round(rb["ms"], 3), "steps": a.steps, "roofline": rb["roofline"]},
+                           "ms_per_step": round(rb["ms"], 3), "steps": a.steps, "roofline": rb["roofline"],
+                           "whole_run": rb["whole_run"]},
                           **rb["extra"])
     out["batched"]["speedup_vs_loop_of_single_calls"] = round(rb["extra"]["loop_of_single_calls_ms"] / rb["ms"], 3)
     gc.collect()
@@ -769,7 +813,7 @@ def main_batched(args, w, rank, world, dist) -> int:
                                 "useful_flops_per_step": res["F"],
                                 "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                                 "l2": "inputs larger than L2 (4.9 GB in total)"}, **res["extra"]),
-                "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"],
+                "roofline": res["roofline"], "whole_run": res["whole_run"], "cpu_baseline": cpu, "e2e": res["e2e"],
                 "gpu_launches": res["launches"] * args.steps, "clocks": res["clocks"]}
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -261,6 +261,8 @@ int ensure_reproj(rqb_handle h, int64_t m, int64_t kcap, int bp, tc::ReprojScrat
     const size_t kb = (size_t)std::max<int64_t>(kcap, bp);
     const size_t oCt = take((size_t)bp * kb), oOm = take((size_t)ldom * bp);
     const size_t oBs = take((size_t)bp * kb), oBsl = take((size_t)bp * kb);
+    const size_t oC64 = take(2 * (size_t)bp * kb);
+    const size_t oYt = take((size_t)ldyl * bp), oYtl = take((size_t)ldyl * bp);
     const size_t oP = take(part);
     int rc = h->pcbuf.ensure(off);
     if (rc != RQB_OK) return rc;
@@ -270,6 +272,8 @@ int ensure_reproj(rqb_handle h, int64_t m, int64_t kcap, int bp, tc::ReprojScrat
     w->Yhi = at(oYh); w->Ylo = at(oYl); w->ldyl = ldyl;
     w->Ct = at(oCt); w->Om = at(oOm); w->ldom = ldom;
     w->Bs = at(oBs); w->Bsl = at(oBsl);
+    w->Ct64 = reinterpret_cast<double*>(base + oC64);
+    w->Yt = at(oYt); w->Ytl = at(oYtl);
     w->part = at(oP); w->part_cap = part;
     w->sq_part = sc.nrm; w->sq_cap = kNrmCap; w->sq_out = sc.s + 8;
     return RQB_OK;
@@ -317,10 +321,11 @@ int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_
     // kappa(G) above 1e5, the Gram is recomputed with exact products and FP64
     // sums and factored again.
     bool pass1 = false;
+    bool split1 = false;   // w.Yt / w.Ytl hold Y's split for the product Y R^-1
     if constexpr (std::is_same<T, float>::value) {
         if (ar.rp && m <= ar.rp->ldyl && tc::gram_ok(m, bp, ldy, Y)) {
-            RQB_CK(tc::gram(cx, Y, ldy, m, bp, *ar.rp));
-            RQB_CK(launch_to_double<float>(cx, bp, bp, ar.rp->Ct, bp, ar.G, bp));
+            split1 = tc::product_ok(m, bp, m, ar.Y1);
+            RQB_CK(tc::gram(cx, Y, ldy, m, bp, *ar.rp, ar.G, split1));
             DevState* st2 = reinterpret_cast<DevState*>(reinterpret_cast<char*>(h->state.p) + 128);
             RQB_CK(cudaMemsetAsync(st2, 0, sizeof(DevState), h->stream));
             Ctx cx2 = cx;
@@ -349,7 +354,7 @@ int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_
     bool tc1 = false;
     if constexpr (std::is_same<T, float>::value) {
         if (ar.rp && m <= ar.rp->ldyl && tc::product_ok(m, bp, m, ar.Y1)) {
-            RQB_CK(tc::product(cx, Y, ldy, m, ar.Rinv, bp, bp, ar.Y1, m, *ar.rp));
+            RQB_CK(tc::product(cx, Y, ldy, m, ar.Rinv, bp, bp, ar.Y1, m, *ar.rp, split1));
             tc1 = true;
         }
     }
@@ -388,10 +393,11 @@ int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_
     // from the split-TF32 products (relative error ~1e-7, about what FP32
     // products summed in FP32 over 128 rows and then in FP64 leave).
     bool tcg2 = false;
+    bool split2 = false;   // w.Yt / w.Ytl hold Y1's split for the product Y1 R^-1
     if constexpr (std::is_same<T, float>::value) {
         if (ar.rp && m <= ar.rp->ldyl && tc::gram_ok(m, bp, m, ar.Y1)) {
-            RQB_CK(tc::gram(cx, ar.Y1, m, m, bp, *ar.rp));
-            RQB_CK(launch_to_double<float>(cx, bp, bp, ar.rp->Ct, bp, ar.G, bp));
+            split2 = p == bp && tc::product_ok(m, bp, ldqo, Qout);
+            RQB_CK(tc::gram(cx, ar.Y1, m, m, bp, *ar.rp, ar.G, split2));
             tcg2 = true;
         }
     }
@@ -402,7 +408,7 @@ int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_
     if constexpr (std::is_same<T, float>::value) {
         // full-width panels only: the product writes all bp columns
         if (ar.rp && m <= ar.rp->ldyl && p == bp && tc::product_ok(m, bp, ldqo, Qout)) {
-            RQB_CK(tc::product(cx, ar.Y1, m, m, ar.Rinv, bp, bp, Qout, ldqo, *ar.rp));
+            RQB_CK(tc::product(cx, ar.Y1, m, m, ar.Rinv, bp, bp, Qout, ldqo, *ar.rp, split2));
             tc2 = true;
         }
     }
@@ -521,10 +527,11 @@ int factor_tc(rqb_handle h, const float* A, int64_t m, int64_t n, int64_t lda, d
         ldws = ldw;
     }
     int p = (int)std::min<int64_t>(b, kcap);
-    RQB_CK(launch_sumsq<float>(cx, m, n, Wsrc, ldws, sc.nrm, kNrmCap, sc.s + 0));
-    RQB_CK(launch_set_norm(cx, sc.s + 0));
+    // ||A||_F^2 comes out of the first sketch's own reads of A (no pass of its own)
     RQB_CK(tc::omega(cx, n, 0, p, bp, seed, ta.Om, ta.ldom));
-    RQB_CK(tc::sketch(cx, Wsrc, ldws, m, n, ta.Om, ta.ldom, bp, ar.Y, m, ta.part, ta.part_cap));
+    RQB_CK(tc::sketch(cx, Wsrc, ldws, m, n, ta.Om, ta.ldom, bp, ar.Y, m, ta.part, ta.part_cap, sc.nrm, kNrmCap,
+                      sc.s + 0));
+    RQB_CK(launch_set_norm(cx, sc.s + 0));
     h->timer.end(h->stream);
 
     for (;;) {
@@ -1224,9 +1231,9 @@ int sketch_tc(rqb_handle h, const float* A, int64_t m, int64_t n, int64_t lda, i
     const float* X;
     int64_t ldx;
     if ((rc = tma_source(h, A, lda, m, n, &X, &ldx)) != RQB_OK) return rc;
-    if (normA2) RQB_CK(launch_sumsq<float>(cx, m, n, X, ldx, sc.nrm, kNrmCap, sc.s + 0));
     RQB_CK(tc::omega(cx, n, col0, p, bp, seed, ta.Om, ta.ldom));
-    RQB_CK(tc::sketch(cx, X, ldx, m, n, ta.Om, ta.ldom, bp, ar.Y, m, ta.part, ta.part_cap));
+    RQB_CK(tc::sketch(cx, X, ldx, m, n, ta.Om, ta.ldom, bp, ar.Y, m, ta.part, ta.part_cap, sc.nrm, kNrmCap,
+                      normA2 ? sc.s + 0 : nullptr));
     RQB_CK(cudaMemcpy2DAsync(Y, sizeof(float) * ldy, ar.Y, sizeof(float) * m, sizeof(float) * m, p,
                              cudaMemcpyDeviceToDevice, h->stream));
     if (normA2) RQB_CK(cudaMemcpyAsync(normA2, sc.s + 0, sizeof(double), cudaMemcpyDeviceToHost, h->stream));

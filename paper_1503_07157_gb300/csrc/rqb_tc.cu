@@ -51,6 +51,7 @@ struct StreamKParams {
     int P;             // CTAs
     int G;             // partial slots per CTA
     int np;            // MMA N
+    double* nrm_part = nullptr;  // sketch only, optional: ||X||_F^2, one FP64 partial per CTA
 };
 
 __host__ __device__ __forceinline__ long long unit_begin(long long U, int P, int p) { return U * p / P; }
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(320, 1) k_streamk(const __grid_constant__ Stre
     __shared__ __align__(8) uint64_t full[S], empty[S], cvfull[2], cvempty[2], accfull[2], accempty[2], drain;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
+    __shared__ double nred[8];
     extern __shared__ uint8_t dsm[];
     uint8_t* base = dsm + (((smem_u32(dsm) + 1023u) & ~1023u) - smem_u32(dsm));
     uint8_t* sX = base;
@@ -207,6 +209,7 @@ __global__ void __launch_bounds__(320, 1) k_streamk(const __grid_constant__ Stre
         float acc[kHalf];
 #pragma unroll
         for (int i = 0; i < kHalf; ++i) acc[i] = 0.f;
+        double nrm = 0.0;   // ||X||_F^2 of the tiles this thread converts
         int g = 0;
         long long q = 0;
         for (long long u = u0; u < u1; ++u, ++q) {
@@ -223,6 +226,24 @@ __global__ void __launch_bounds__(320, 1) k_streamk(const __grid_constant__ Stre
                 float x[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) x[j] = raw[(16 * h + j) * kBM + rr];
+                if (p.nrm_part) {
+                    // the stream-K units partition the matrix, and the TMA box
+                    // fills zeros past its edges: every entry is squared once.
+                    // Each square is split exactly (e = fma(x, x, -x*x)) and the
+                    // 16 of a unit are summed with TwoSum in FP32 pairs, then
+                    // added in FP64
+                    float hi = 0.f, lo = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float p2 = __fmul_rn(x[j], x[j]);
+                        const float e2 = fmaf(x[j], x[j], -p2);
+                        const float t = __fadd_rn(hi, p2);
+                        const float z = __fsub_rn(t, hi);
+                        lo += __fadd_rn(__fsub_rn(hi, __fsub_rn(t, z)), __fsub_rn(p2, z)) + e2;
+                        hi = t;
+                    }
+                    nrm += (double)hi + (double)lo;
+                }
                 uint8_t* hi = sCv + cs * Cfg::kCv;
                 uint8_t* lo = hi + kTileBytes;
 #pragma unroll
@@ -282,12 +303,23 @@ __global__ void __launch_bounds__(320, 1) k_streamk(const __grid_constant__ Stre
                 }
             }
         }
+        if (ROLE == kSketch && p.nrm_part) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+            if (lane == 0) nred[e] = nrm;
+        }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 1) tmem_dealloc(tmem, ncols);
     if (threadIdx.x == 0 && abort_flag) record_error(p.st, RQB_ERR_TIMEOUT);
+    if (ROLE == kSketch && p.nrm_part && threadIdx.x == 64) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += nred[w];
+        p.nrm_part[blockIdx.x] = t;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -923,9 +955,10 @@ __global__ void k_split_q(const float* __restrict__ Qi, long long ldq, long long
 
 // Omega-layout copy of the re-projection coefficients: Om[j + c ldo] =
 // rna_tf32(Ct[c + j ldc]) for j < kprev, c < np (Ct is C^T, np x kprev).
-__global__ void k_ct_to_omega(const float* __restrict__ Ct, long long ldc, long long kprev, int np,
+template <typename TC>
+__global__ void k_ct_to_omega(const TC* __restrict__ Ct, long long ldc, long long kprev, int np,
                               float* __restrict__ Om, long long ldo) {
-    __shared__ float tile[32][33];
+    __shared__ TC tile[32][33];
     const long long j0 = (long long)blockIdx.x * 32;
     const int c0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -936,7 +969,7 @@ __global__ void k_ct_to_omega(const float* __restrict__ Ct, long long ldc, long 
     __syncthreads();
     for (int i = ty; i < 32; i += 8) {
         const long long j = j0 + tx;
-        if (j < kprev) Om[j + (long long)(c0 + i) * ldo] = tf32_rna(tile[tx][i]);
+        if (j < kprev) Om[j + (long long)(c0 + i) * ldo] = tf32_rna((float)tile[tx][i]);
     }
 }
 
@@ -1061,6 +1094,40 @@ __global__ void k_reduce_project(const float* __restrict__ part, long long U, in
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
         sq_part[(size_t)t * gridDim.y + blockIdx.y] = s;
+    }
+}
+
+// The panel's coefficient products (the Grams Y^T Y and C^T = Y^T Qbar of
+// lines (3), (3')): out[c + j ldo] (c < pcols, j < n) = the sum, in FP64 and
+// in CTA order, of the FP32 partials of the CTAs covering tile j / 128.  Each
+// partial is one CTA's stretch of the reduction over m, accumulated in FP32
+// by the tensor core and the period drains; the sum across CTAs is FP64.
+__global__ void k_reduce_project64(const float* __restrict__ part, long long U, int C, int P, int G, int np,
+                                   int pcols, long long n, double* __restrict__ out, long long ldo) {
+    __shared__ size_t off[kMaxCover];
+    __shared__ int count;
+    const int t = blockIdx.x;
+    if (threadIdx.x == 0) count = tile_slots(U, C, P, G, np, t, off);
+    __syncthreads();
+    const int nc = count;
+    const int span = np * kBM / (int)gridDim.y;
+    const int i0 = blockIdx.y * span;
+    for (int idx = i0 + 4 * (int)threadIdx.x; idx < i0 + span; idx += 4 * (int)blockDim.x) {   // jl * np + c
+        const int jl = idx / np, c = idx % np;
+        const long long j = (long long)t * kBM + jl;
+        if (j >= n) continue;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        for (int q = 0; q < nc; ++q) {
+            const float4 v = *reinterpret_cast<const float4*>(part + off[q] + idx);
+            a0 += (double)v.x;
+            a1 += (double)v.y;
+            a2 += (double)v.z;
+            a3 += (double)v.w;
+        }
+        const double a[4] = {a0, a1, a2, a3};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (c + i < pcols) out[c + i + j * ldo] = a[i];
     }
 }
 
@@ -1784,7 +1851,8 @@ cudaError_t stage_b(Ctx& cx, const float* Bi, long long ldbi, int p, long long n
 }
 
 cudaError_t sketch(Ctx& cx, const float* X, long long ldx, long long m, long long n, const float* Om, long long ldom,
-                   int np, float* Y, long long ldy, float* part, size_t part_cap) {
+                   int np, float* Y, long long ldy, float* part, size_t part_cap, double* nrm_part, int nrm_cap,
+                   double* nrm_out) {
     StreamKParams p;
     cudaError_t e;
     if ((e = make_map(&p.mx, X, m, n, ldx, kBM, kKC, false)) != cudaSuccess) return e;
@@ -1792,16 +1860,19 @@ cudaError_t sketch(Ctx& cx, const float* X, long long ldx, long long m, long lon
     p.mwl = p.mw;
     const Plan pl = plan((m + kBM - 1) / kBM, (n + kKC - 1) / kKC, cx.num_sms);
     if ((size_t)pl.P * pl.G * kBM * np > part_cap) return cudaErrorInvalidValue;
+    if (nrm_out && pl.P > nrm_cap) return cudaErrorInvalidValue;
     p.part = part;
     p.st = cx.st;
     p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
+    p.nrm_part = nrm_out ? nrm_part : nullptr;
     if ((e = launch_streamk<kSketch>(cx, p, np)) != cudaSuccess) return e;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const dim3 rgrid(pl.tiles, reduce_slices(pl.tiles, cx.num_sms));
     k_reduce_sketch<<<rgrid, 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, m, Y,
                                                                            ldy, nullptr);
     cx.launches++;
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return nrm_out ? launch_sum_doubles(cx, nrm_part, pl.P, nrm_out) : cudaSuccess;
 }
 
 // Y = sub - X Omega (sub may alias Y), otherwise as sketch().
@@ -1847,6 +1918,30 @@ cudaError_t project(Ctx& cx, const float* X, long long ldx, long long m, long lo
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return launch_sum_doubles(cx, sq_part, pl.tiles * sl, sq_out);
+}
+
+// out (pcols x n, FP64, ld ldo) = Q^T X as project(), the CTAs' FP32
+// partials summed in FP64 (k_reduce_project64); no staged copies, no norm.
+cudaError_t project64(Ctx& cx, const float* X, long long ldx, long long m, long long n, const float* Qhi,
+                      const float* Qlo, long long ldql, int pcols, int np, double* out, long long ldo, float* part,
+                      size_t part_cap) {
+    StreamKParams p;
+    cudaError_t e;
+    if ((e = make_map(&p.mx, X, m, n, ldx, kKC, kBM, true)) != cudaSuccess) return e;
+    if ((e = make_map(&p.mw, Qhi, m, np, ldql, kKC, np, true)) != cudaSuccess) return e;
+    if ((e = make_map(&p.mwl, Qlo, m, np, ldql, kKC, np, true)) != cudaSuccess) return e;
+    const Plan pl = plan((n + kBM - 1) / kBM, (m + kKC - 1) / kKC, cx.num_sms);
+    const int sl = reduce_slices(pl.tiles, cx.num_sms);
+    if ((size_t)pl.P * pl.G * kBM * np > part_cap) return cudaErrorInvalidValue;
+    p.part = part;
+    p.st = cx.st;
+    p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
+    if ((e = launch_streamk<kProject>(cx, p, np)) != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_reduce_project64<<<dim3(pl.tiles, sl), 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, pcols, n,
+                                                                  out, ldo);
+    cx.launches++;
+    return cudaGetLastError();
 }
 
 cudaError_t update_impl(Ctx& cx, const float* Wsrc, long long ldws, float* Wdst, long long ldwd, long long m,
@@ -1916,14 +2011,15 @@ bool gram_ok(long long m, int np, long long ldy, const float* Y) {
     return m >= 128 && np >= kBM && (ldy % 4) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15u) == 0;
 }
 
-cudaError_t gram(Ctx& cx, const float* Y, long long ldy, long long m, int np, const ReprojScratch& w) {
+cudaError_t gram(Ctx& cx, const float* Y, long long ldy, long long m, int np, const ReprojScratch& w, double* G,
+                 bool keep_split) {
     cudaError_t e;
     dim3 g1((unsigned)((m + 31) / 32), (unsigned)(np / 32));
-    k_split_q<<<g1, 256, 0, cx.stream>>>(Y, ldy, m, np, np, w.Yhi, w.Ylo, w.ldyl, nullptr, nullptr);
+    k_split_q<<<g1, 256, 0, cx.stream>>>(Y, ldy, m, np, np, w.Yhi, w.Ylo, w.ldyl, keep_split ? w.Yt : nullptr,
+                                         keep_split ? w.Ytl : nullptr);
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return project(cx, Y, ldy, m, np, w.Yhi, w.Ylo, w.ldyl, np, np, w.Ct, np, w.Bs, w.Bsl, w.part, w.part_cap,
-                   w.sq_part, w.sq_cap, w.sq_out);
+    return project64(cx, Y, ldy, m, np, w.Yhi, w.Ylo, w.ldyl, np, np, G, np, w.part, w.part_cap);
 }
 
 // Out (m x np, ld ldo) = Y (m x np, ld ldy) C (np x np, ld ldc), split-TF32.
@@ -1932,18 +2028,20 @@ bool product_ok(long long m, int np, long long ldo, const float* Out) {
 }
 
 cudaError_t product(Ctx& cx, const float* Y, long long ldy, long long m, const float* C, long long ldc, int np,
-                    float* Out, long long ldo, const ReprojScratch& w) {
+                    float* Out, long long ldo, const ReprojScratch& w, bool presplit) {
     cudaError_t e;
-    dim3 g1((unsigned)((m + 31) / 32), (unsigned)(np / 32));
-    k_split_q<<<g1, 256, 0, cx.stream>>>(Y, ldy, m, np, np, nullptr, nullptr, 0, w.Yhi, w.Ylo);
-    cx.launches++;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (!presplit) {
+        dim3 g1((unsigned)((m + 31) / 32), (unsigned)(np / 32));
+        k_split_q<<<g1, 256, 0, cx.stream>>>(Y, ldy, m, np, np, nullptr, nullptr, 0, w.Yt, w.Ytl);
+        cx.launches++;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     const long long total = (long long)np * np;
     const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * cx.num_sms);
     k_stage_b<<<blocks, 256, 0, cx.stream>>>(C, ldc, np, np, np, w.Bs, w.Bsl);
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return update_impl(cx, nullptr, 0, Out, ldo, m, np, w.Yhi, w.Ylo, w.Bs, w.Bsl, np, nullptr, 0, nullptr, 0);
+    return update_impl(cx, nullptr, 0, Out, ldo, m, np, w.Yt, w.Ytl, w.Bs, w.Bsl, np, nullptr, 0, nullptr, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -2099,12 +2197,12 @@ cudaError_t reproject(Ctx& cx, const float* Qbar, long long ldq, long long m, lo
     k_split_q<<<g1, 256, 0, cx.stream>>>(Y, ldy, m, np, np, w.Yhi, w.Ylo, w.ldyl, nullptr, nullptr);
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = project(cx, Qbar, ldq, m, kprev, w.Yhi, w.Ylo, w.ldyl, np, np, w.Ct, np, w.Bs, w.Bsl, w.part,
-                     w.part_cap, w.sq_part, w.sq_cap, w.sq_out)) != cudaSuccess)
+    if ((e = project64(cx, Qbar, ldq, m, kprev, w.Yhi, w.Ylo, w.ldyl, np, np, w.Ct64, np, w.part,
+                       w.part_cap)) != cudaSuccess)
         return e;
     // C in the sketch's Omega layout (rounded to TF32), then Y -= Qbar C
     dim3 g2((unsigned)((kprev + 31) / 32), (unsigned)(np / 32));
-    k_ct_to_omega<<<g2, 256, 0, cx.stream>>>(w.Ct, np, kprev, np, w.Om, w.ldom);
+    k_ct_to_omega<double><<<g2, 256, 0, cx.stream>>>(w.Ct64, np, kprev, np, w.Om, w.ldom);
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return sketch_sub(cx, Qbar, ldq, m, kprev, w.Om, w.ldom, np, Y, ldy, Y, w.part, w.part_cap);

@@ -35,9 +35,13 @@ cudaError_t split_q(Ctx& cx, const float* Qi, long long ldq, long long m, int p,
 // p .. np-1 (the staged form the update reads).
 cudaError_t stage_b(Ctx& cx, const float* Bi, long long ldbi, int p, long long n, int np, float* Bs, float* Bsl);
 
-// Y (m x np, ld ldy) = X (m x n, ld ldx) Omega (n x np, ld ldom).
+// Y (m x np, ld ldy) = X (m x n, ld ldx) Omega (n x np, ld ldom).  With
+// nrm_out, ||X||_F^2 too (FP64, from the converter warps' reads of X: one
+// partial per CTA in nrm_part, at most nrm_cap of them), so that the first
+// block needs no separate pass over A.
 cudaError_t sketch(Ctx& cx, const float* X, long long ldx, long long m, long long n, const float* Om, long long ldom,
-                   int np, float* Y, long long ldy, float* part, size_t part_cap);
+                   int np, float* Y, long long ldy, float* part, size_t part_cap, double* nrm_part = nullptr,
+                   int nrm_cap = 0, double* nrm_out = nullptr);
 
 // B (pcols x n, ld ldb) = Q_i^T X and the staged split copy Bs / Bsl
 // (np x n, ld np); ||B||_F^2 into *sq_out.
@@ -59,6 +63,9 @@ struct ReprojScratch {
     float* Ylo;
     long long ldyl;
     float* Ct;
+    double* Ct64;     // C^T (np x kprev, ld np) summed across CTAs in FP64
+    float* Yt;        // row-major split copies of Y (m x np): the K-major
+    float* Ytl;       // operand of product()
     float* Om;
     long long ldom;
     float* Bs;
@@ -71,8 +78,9 @@ struct ReprojScratch {
 };
 
 // Line (3') on the tensor core: Y (m x np) <- Y - Qbar (Qbar^T Y), Qbar
-// m x kprev (ld ldq), both products split-TF32 (C rounded to TF32 for the
-// second); needs reproject_ok(m, kprev).
+// m x kprev (ld ldq), both products split-TF32; C = Qbar^T Y is summed
+// across CTAs in FP64 (w.Ct64) and rounded to TF32 as the operand of the
+// second product; needs reproject_ok(m, kprev).
 bool reproject_ok(long long m, long long kprev);
 
 // Out (m x np, ld ldo) = Y (m x np, ld ldy) C (np x np, ld ldc) with the
@@ -81,12 +89,18 @@ bool reproject_ok(long long m, long long kprev);
 // TMA-addressable and np >= 128 (product_ok).
 bool product_ok(long long m, int np, long long ldo, const float* Out);
 
-// w.Ct (np x np, FP32, ld np) = Y^T Y (m x np, ld ldy) with the split-TF32
-// projection kernel (relative accuracy ~1e-7 of ||Y||^2); needs gram_ok.
+// G (np x np, FP64, ld np) = Y^T Y (m x np, ld ldy) with the split-TF32
+// projection kernel: each CTA accumulates its stretch of rows in FP32 (TMEM
+// and period drains, relative accuracy ~1e-7), and the CTAs' partials are
+// summed in FP64; needs gram_ok.
+// With keep_split, the same pass over Y also writes the row-major split
+// copies w.Yt / w.Ytl, so that a following product() of the same Y can skip
+// its own split (presplit).
 bool gram_ok(long long m, int np, long long ldy, const float* Y);
-cudaError_t gram(Ctx& cx, const float* Y, long long ldy, long long m, int np, const ReprojScratch& w);
+cudaError_t gram(Ctx& cx, const float* Y, long long ldy, long long m, int np, const ReprojScratch& w, double* G,
+                 bool keep_split = false);
 cudaError_t product(Ctx& cx, const float* Y, long long ldy, long long m, const float* C, long long ldc, int np,
-                    float* Out, long long ldo, const ReprojScratch& w);
+                    float* Out, long long ldo, const ReprojScratch& w, bool presplit = false);
 cudaError_t reproject(Ctx& cx, const float* Qbar, long long ldq, long long m, long long kprev, float* Y,
                       long long ldy, int np, const ReprojScratch& w);
 

@@ -549,6 +549,7 @@ def run_batched(args, w: dict, rank: int, world: int, dist, do_e2e: bool = True)
         stb = h.rqb_get_stats()
         kern_ms += stb.phase_ms[0]
         launches += stb.kernel_launches
+    tile_width = stb.tile_width
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -577,7 +578,8 @@ def run_batched(args, w: dict, rank: int, world: int, dist, do_e2e: bool = True)
         model_bytes += 4.0 * ((3 * sb - 1) * c.m * c.n + 2.0 * c.m * b * sb * (sb - 1) / 2.0)
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     hbm_gbs = model_bytes / (ms * 1e-3) / 1e9
-    roofline = {"bound": "alu", "kernel": "grouped batched kernels (k_rows_update, k_cols, k_rows, k_mat), whole batch",
+    roofline = {"bound": "alu", "kernel": "grouped batched kernels (k_rows_update, k_cols, k_rows, k_mat), whole batch "
+                          f"as one graph launch, projection tile width {tile_width} (autotuned)",
                 "achieved": round(achieved, 3),
                 "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
                 "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
@@ -596,6 +598,7 @@ def run_batched(args, w: dict, rank: int, world: int, dist, do_e2e: bool = True)
         return dict(value=aggregate_value(F, world, ms), ms=ms, F=F, clocks=clk, roofline=roofline, e2e=None,
                     whole_run=whole,
                     launches=launches // max(args.steps, 1), extra={"count": len(mats), "k_mean": float(sum(ks)) / len(ks), "k_max": max(ks),
+                                       "projection_tile_width": tile_width,
                                        "status_ok": int(sum(1 for s_ in sts if s_ == 0)),
                                        "loop_of_single_calls_ms": round(loop_ms, 2)})
     # e2e: pinned host inputs in, Q and B back to pinned host, inside the timed region
@@ -628,6 +631,7 @@ def run_batched(args, w: dict, rank: int, world: int, dist, do_e2e: bool = True)
     return dict(value=aggregate_value(F, world, ms), ms=ms, F=F, clocks=clk, roofline=roofline, e2e=e2e,
                 whole_run=whole,
                 launches=launches // max(args.steps, 1), extra={"count": len(mats), "k_mean": float(sum(ks)) / len(ks), "k_max": max(ks),
+                                   "projection_tile_width": tile_width,
                                    "status_ok": int(sum(1 for s_ in sts if s_ == 0)),
                                    "loop_of_single_calls_ms": round(loop_ms, 2)})
 

@@ -131,7 +131,8 @@ typedef struct {
     int32_t gram_fallbacks; /* tensor-core handles: panels whose first Gram was
                                recomputed with exact products (section of
                                rqb_factor)                                     */
-    int32_t reserved2;
+    int32_t tile_width;     /* rqb_factor_batched: columns of A per work item of
+                               the projection, as picked by the autotuner      */
 } rqb_stats;
 
 typedef struct rqb_handle_s* rqb_handle;

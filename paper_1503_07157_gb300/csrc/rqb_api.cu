@@ -19,7 +19,9 @@ namespace batched {
 int factor_batched(cudaStream_t stream, int num_sms, int64_t count, const void* const* A, const int64_t* m,
                    const int64_t* n, const int64_t* lda, const double* eps, int64_t b, uint64_t seed, int64_t max_rank,
                    const void** Q, int64_t* ldq, const void** B, int64_t* ldb, int64_t* k, int* status, void** outbuf,
-                   size_t* outbytes, void** workbuf, size_t* workbytes, float* ms, int* launches);
+                   size_t* outbytes, void** workbuf, size_t* workbytes, void** cache, float* ms, int* launches,
+                   int* proj_width);
+void release_cache(void* cache);
 }
 }  // namespace rqb
 
@@ -131,6 +133,7 @@ struct rqb_handle_s {
     size_t bat_out_bytes = 0;
     void* bat_work = nullptr;  // its descriptors and per-CTA scratch
     size_t bat_work_bytes = 0;
+    void* bat_cache = nullptr; // its instantiated graph and autotuned tiles
 };
 
 namespace {
@@ -1004,6 +1007,7 @@ int rqb_destroy(rqb_handle h) {
     h->tcbuf.release();
     h->svdbuf.release();
     h->pcbuf.release();
+    rqb::batched::release_cache(h->bat_cache);
     if (h->bat_out) cudaFree(h->bat_out);
     if (h->bat_work) cudaFree(h->bat_work);
     if (h->hstate) cudaFreeHost(h->hstate);
@@ -1711,12 +1715,13 @@ extern "C" int rqb_factor_batched(rqb_handle h, int64_t count, const void* const
     if (set_device(h) != RQB_OK) return finish(h, RQB_ERR_CUDA);
     std::memset(&h->stats, 0, sizeof(h->stats));
     float ms = 0.f;
-    int launches = 0;
+    int launches = 0, width = 0;
     int rc = rqb::batched::factor_batched(h->stream, h->num_sms, count, A, m, n, lda, eps, b, seed, h->cfg.max_rank,
                                           Q, ldq, B, ldb, k, status, &h->bat_out, &h->bat_out_bytes, &h->bat_work,
-                                          &h->bat_work_bytes, &ms, &launches);
+                                          &h->bat_work_bytes, &h->bat_cache, &ms, &launches, &width);
     h->have_factor = false;
     h->stats.kernel_launches = launches;
+    h->stats.tile_width = width;
     h->stats.phase_ms[RQB_PHASE_SKETCH] = ms;   // the whole batch
     h->stats.phase_calls[RQB_PHASE_SKETCH] = 1;
     return finish(h, rc);

@@ -18,12 +18,22 @@
 //              the direct ||A^(i)||^2 of the update
 //   line (5)   A^(i) = A^(i-1) - Q_i B_i fused with the next block's sketch
 // The per-matrix state (k, E, flags, status) lives on the device; the items of
-// finished matrices return at once.  Blocks are launched in chunks of eight,
-// each chunk captured into one CUDA graph; the host reads the number of
-// active matrices between chunks.  Partial sums are combined per matrix in a
+// finished matrices return at once.  The whole batch is one instantiated CUDA
+// graph: a prologue, then a WHILE node whose body is one block of every
+// matrix, its condition (some matrix still active) set on the device at the
+// end of each block, so no host round trip happens between blocks.  The graph
+// is kept by the handle and relaunched while the batch shape is the same.
+// The projection's tile width (128 or 256 columns per work item) is picked by
+// an autotuner per batch class.  Partial sums are combined per matrix in a
 // fixed order, so results are bitwise repeatable.
 #include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <new>
+#include <string>
+#include <utility>
 #include <vector>
 
 #include "rqb_engine.h"
@@ -318,7 +328,7 @@ __global__ void __launch_bounds__(NT) k_rows(const GMat* __restrict__ mats, cons
 constexpr int NTU = 128;
 
 __global__ void __launch_bounds__(NTU) k_rows_update(const GMat* __restrict__ mats, const GState* __restrict__ st,
-                                                     const Item* __restrict__ items, int b, int first,
+                                                     const Item* __restrict__ items, int b, const int* __restrict__ blk,
                                                      const float* __restrict__ Om_next, double* __restrict__ part) {
     // B_i and Omega_{i+1} chunks are stored so that a thread's four strided
     // columns tx + 8 j (j < 4) are one 16-byte word: entry (t, c) of a row
@@ -332,6 +342,7 @@ __global__ void __launch_bounds__(NTU) k_rows_update(const GMat* __restrict__ ma
     const GState s = st[it.t];
     if (!s.pending) return;
     const GMat& d = mats[it.t];
+    const int first = (*blk == 0) ? 1 : 0;   // block 1 reads A itself
     const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
     const int64_t m = d.m, n = d.n, r0 = (int64_t)it.tile * TR;
     const float* Wsrc = first ? d.A : d.W;
@@ -490,10 +501,11 @@ __device__ __forceinline__ int vs_col(int r, int c) {   // physical column of V 
     return ((((c >> 2) ^ ((r >> 2) & 7))) << 2) | (c & 3);
 }
 
-template <int OP>
+template <int OP, int W>
 __global__ void __launch_bounds__(NT) k_cols(const GMat* __restrict__ mats, const GState* __restrict__ st,
-                                             const Item* __restrict__ items, int first, double* __restrict__ part) {
-    constexpr int W = (OP == kColProject) ? TC : TCR;   // columns per item
+                                             const Item* __restrict__ items, const int* __restrict__ blk,
+                                             double* __restrict__ part) {
+    // W: columns per item (the projection's is picked by the autotuner)
     constexpr int JT = W / 32;                           // j per thread (8 or 4)
     constexpr int NCT = W / 4;                           // column threads
     static_assert((BP / JT) * NCT == NT, "thread map");
@@ -505,6 +517,7 @@ __global__ void __launch_bounds__(NT) k_cols(const GMat* __restrict__ mats, cons
     if (!s.active) return;
     if (OP == kColReproj && s.k == 0) return;
     const GMat& d = mats[it.t];
+    const int first = (*blk == 0) ? 1 : 0;   // block 1 projects A itself
     const int64_t c0 = (int64_t)it.tile * W;
     const int64_t ncols = (OP == kColProject) ? d.n : s.k;
     if (c0 >= ncols) return;
@@ -758,8 +771,11 @@ __global__ void __launch_bounds__(NT, 1) k_mat(const GMat* __restrict__ mats, GS
     st[t] = g;
 }
 
-// Omega (n_max x BP, row-major): global columns col0 .. col0 + b - 1, zero beyond b.
-__global__ void k_omega_rows(int64_t n_max, int64_t col0, int b, uint64_t seed, float* __restrict__ Om) {
+// Omega (n_max x BP, row-major): global columns col0 .. col0 + b - 1, zero
+// beyond b, with col0 = 0 (no blk) or (*blk + 1) b, the next block's.
+__global__ void k_omega_rows(int64_t n_max, const int* __restrict__ blk, int b, uint64_t seed,
+                             float* __restrict__ Om) {
+    const int64_t col0 = blk ? (int64_t)(*blk + 1) * b : 0;
     const int64_t total = n_max * BP;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -769,7 +785,12 @@ __global__ void k_omega_rows(int64_t n_max, int64_t col0, int b, uint64_t seed, 
     }
 }
 
-__global__ void k_count_active(const GState* __restrict__ st, int count, int* __restrict__ out) {
+// End of a block of the device-side loop: advance the block index and keep
+// the loop (the graph's WHILE node) running while a matrix is still active
+// and fewer than max_blocks blocks have run; every matrix is done after
+// max_blocks blocks (k reaches its cap), so the loop always ends.
+__global__ void k_advance(int* __restrict__ blk, const GState* __restrict__ st, int count, int max_blocks,
+                          cudaGraphConditionalHandle loop) {
     __shared__ int sh[NT / 32];
     int c = 0;
     for (int t = threadIdx.x; t < count; t += NT) c += st[t].active;
@@ -780,7 +801,9 @@ __global__ void k_count_active(const GState* __restrict__ st, int count, int* __
     if (threadIdx.x == 0) {
         int tot = 0;
         for (int w = 0; w < NT / 32; ++w) tot += sh[w];
-        *out = tot;
+        const int next = *blk + 1;
+        *blk = next;
+        cudaGraphSetConditional(loop, (tot > 0 && next < max_blocks) ? 1u : 0u);
     }
 }
 
@@ -807,8 +830,6 @@ static int grow(void** buf, size_t* bytes, size_t need) {
 
 namespace {
 
-constexpr int kChunk = 8;   // blocks per captured graph
-
 struct Tables {
     const GMat* mats;
     GState* st;
@@ -819,118 +840,269 @@ struct Tables {
     double* rows_part;
     double* proj_part;
     double* gpart;       // BP x BP exact Gram partial per row item
-    float* Om[2];
+    float* Om[2];        // Omega_1, and the next block's Omega
     int64_t n_max;
+    int* blk;            // 0-based index of the block being run
+    int max_blocks;
 };
 
-// The launches of block i (0-based) of every active matrix.
-cudaError_t launch_block(cudaStream_t cs, const Tables& T, int i, int b, uint64_t seed, int* launches) {
-    const int first = (i == 0) ? 1 : 0;
-    const float* Om = T.Om[i & 1];
-    float* Om_next = T.Om[(i + 1) & 1];
+// The launches of one block of every active matrix; the block index is read
+// on the device (T.blk), so the same launches serve every block.
+template <int PW>
+void launch_block(cudaStream_t cs, const Tables& T, int b, uint64_t seed, cudaGraphConditionalHandle loop) {
+    float* Om_next = T.Om[1];
     k_rows_gram<0><<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, T.gpart);
     k_mat<kMatPanel1><<<T.count, NT, 0, cs>>>(T.mats, T.st, b, T.rows_part, T.proj_part, T.gpart);
-    k_rows<kRowMulR1><<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, b, Om, nullptr);
-    int nl = 3;
-    if (i > 0) {
-        k_cols<kColReproj><<<T.nreproj, NT, 0, cs>>>(T.mats, T.st, T.reproj, first, nullptr);
-        k_rows<kRowSubQC><<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, b, Om, nullptr);
-        nl += 2;
-    }
+    k_rows<kRowMulR1><<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, b, nullptr, nullptr);
+    // line (3'): both kernels return at once for a matrix with k = 0
+    k_cols<kColReproj, TCR><<<T.nreproj, NT, 0, cs>>>(T.mats, T.st, T.reproj, T.blk, nullptr);
+    k_rows<kRowSubQC><<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, b, nullptr, nullptr);
     k_rows_gram<1><<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, T.gpart);
     k_mat<kMatPanel2><<<T.count, NT, 0, cs>>>(T.mats, T.st, b, T.rows_part, T.proj_part, T.gpart);
-    k_rows<kRowMulR2><<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, b, Om, nullptr);
-    k_cols<kColProject><<<T.nproj, NT, 0, cs>>>(T.mats, T.st, T.proj, first, T.proj_part);
+    k_rows<kRowMulR2><<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, b, nullptr, nullptr);
+    k_cols<kColProject, PW><<<T.nproj, NT, 0, cs>>>(T.mats, T.st, T.proj, T.blk, T.proj_part);
     k_mat<kMatStop><<<T.count, NT, 0, cs>>>(T.mats, T.st, b, T.rows_part, T.proj_part, T.gpart);
     const int64_t tot = T.n_max * BP;
-    k_omega_rows<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, cs>>>(T.n_max, (int64_t)(i + 1) * b, b,
-                                                                                 seed, Om_next);
-    k_rows_update<<<T.nrows, NTU, 0, cs>>>(T.mats, T.st, T.rows, b, first, Om_next, T.rows_part);
+    k_omega_rows<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, cs>>>(T.n_max, T.blk, b, seed, Om_next);
+    k_rows_update<<<T.nrows, NTU, 0, cs>>>(T.mats, T.st, T.rows, b, T.blk, Om_next, T.rows_part);
     k_mat<kMatDirect><<<T.count, NT, 0, cs>>>(T.mats, T.st, b, T.rows_part, T.proj_part, T.gpart);
-    nl += 8;
-    *launches += nl;
-    return cudaGetLastError();
+    k_advance<<<1, NT, 0, cs>>>(T.blk, T.st, T.count, T.max_blocks, loop);
+}
+constexpr int kBlockLaunches = 14;   // kernels per block in launch_block
+constexpr int kPrologueLaunches = 3;
+
+}  // namespace
+
+// The factorization of one batch shape as one instantiated graph: a prologue
+// (Omega_1, the first sketch with ||A||^2, the initial state, block index 0)
+// followed by a WHILE node whose body is launch_block, so that the whole
+// batch runs from one cudaGraphLaunch with no host round trip.  Kept by the
+// handle and reused while the shape, the workspace and the launch
+// parameters are the same; the descriptors and item tables it reads are
+// rewritten in device memory before every launch.
+struct GraphCache {
+    // key
+    const void* work = nullptr;
+    int64_t count = 0, nrows = 0, nproj = 0, nreproj = 0, n_max = 0, b = 0;
+    int max_blocks = 0, pw = 0, device = -1;
+    uint64_t seed = 0;
+    // graph
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;        // capture stream (the caller's may be the legacy one)
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // autotuned projection widths, by batch class
+    std::vector<std::pair<std::string, int>> tuned;
+    bool tuned_loaded = false;
+    void drop_graph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        work = nullptr;
+    }
+    ~GraphCache() {
+        drop_graph();
+        if (cap) cudaStreamDestroy(cap);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+
+void release_cache(void* cache) { delete static_cast<GraphCache*>(cache); }
+
+namespace {
+
+template <int PW>
+int build_graph(GraphCache& G, const Tables& T, int b, uint64_t seed) {
+    cudaGraph_t g = nullptr, pro = nullptr;
+    cudaGraphNode_t npro = nullptr, nloop = nullptr;
+    cudaGraphConditionalHandle loop = 0;
+    int rc = RQB_OK;
+    do {
+        if (cudaGraphCreate(&g, 0) != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
+        // prologue, captured on the private stream
+        if (cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
+        const int64_t tot = T.n_max * BP;
+        k_omega_rows<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, G.cap>>>(T.n_max, nullptr, b, seed,
+                                                                                       T.Om[0]);
+        k_rows<kRowSketch0><<<T.nrows, NT, 0, G.cap>>>(T.mats, T.st, T.rows, b, T.Om[0], T.rows_part);
+        k_mat<kMatInit><<<T.count, NT, 0, G.cap>>>(T.mats, T.st, b, T.rows_part, T.proj_part, T.gpart);
+        cudaMemsetAsync(T.blk, 0, sizeof(int), G.cap);
+        const cudaError_t le = cudaGetLastError();
+        if (cudaStreamEndCapture(G.cap, &pro) != cudaSuccess || !pro || le != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
+        if (cudaGraphAddChildGraphNode(&npro, g, nullptr, 0, pro) != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
+        // the block loop: a WHILE node, its condition set by k_advance
+        if (cudaGraphConditionalHandleCreate(&loop, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+            rc = RQB_ERR_CUDA; break;
+        }
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = loop;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        if (cudaGraphAddNode(&nloop, g, &npro, nullptr, 1, &cp) != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        if (cudaStreamBeginCaptureToGraph(G.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+            cudaSuccess) { rc = RQB_ERR_CUDA; break; }
+        launch_block<PW>(G.cap, T, b, seed, loop);
+        const cudaError_t le2 = cudaGetLastError();
+        cudaGraph_t same = nullptr;
+        if (cudaStreamEndCapture(G.cap, &same) != cudaSuccess || le2 != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
+        if (cudaGraphInstantiate(&G.exec, g, 0) != cudaSuccess) { G.exec = nullptr; rc = RQB_ERR_CUDA; break; }
+    } while (0);
+    if (pro) cudaGraphDestroy(pro);
+    if (g) cudaGraphDestroy(g);
+    if (rc != RQB_OK) cudaGetLastError();
+    return rc;
+}
+
+// Batch class of the autotuner: the number of matrices and the sizes, on a
+// coarse grid, with b.
+std::string batch_class(int64_t count, const int64_t* m, const int64_t* n, int64_t b) {
+    int64_t mx_m = 0, mx_n = 0;
+    double mn = 0.0;
+    for (int64_t t = 0; t < count; ++t) {
+        mx_m = std::max(mx_m, m[t]);
+        mx_n = std::max(mx_n, n[t]);
+        mn += (double)m[t] * (double)n[t];
+    }
+    char buf[128];
+    std::snprintf(buf, sizeof(buf), "c%lld_m%lld_n%lld_mn%lld_b%lld", (long long)count,
+                  (long long)((mx_m + 255) / 256), (long long)((mx_n + 127) / 128),
+                  (long long)std::llround(std::log2(std::max(mn, 1.0)) * 4.0), (long long)b);
+    return std::string(buf);
 }
 
 }  // namespace
 
-int factor_batched(cudaStream_t stream, int num_sms, int64_t count, const void* const* A, const int64_t* m,
-                   const int64_t* n, const int64_t* lda, const double* eps, int64_t b, uint64_t seed, int64_t max_rank,
-                   const void** Q, int64_t* ldq, const void** B, int64_t* ldb, int64_t* k, int* status, void** outbuf,
-                   size_t* outbytes, void** workbuf, size_t* workbytes, float* ms, int* launches) {
-    (void)num_sms;
+// Autotuner of the projection's column tile (128 or 256 columns of A per
+// work item): the first batch of a class is run with each width and timed on
+// the device; the faster width is kept for the class in the handle and, when
+// the environment variable RQB_AUTOTUNE_CACHE names a file, appended to that
+// file and read back by later processes.  Both widths give the same results
+// bit for bit (each B_i entry is one thread's sum over the rows in the same
+// order).
+static void tune_load(GraphCache& G) {
+    if (G.tuned_loaded) return;
+    G.tuned_loaded = true;
+    const char* path = std::getenv("RQB_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    char key[256];
+    int w = 0;
+    while (std::fscanf(f, "batched_projection_width %255s %d\n", key, &w) == 2)
+        if (w == 128 || w == 256) G.tuned.emplace_back(std::string(key), w);
+    std::fclose(f);
+}
+
+static int tune_lookup(const GraphCache& G, const std::string& key) {
+    for (auto it = G.tuned.rbegin(); it != G.tuned.rend(); ++it)
+        if (it->first == key) return it->second;
+    return 0;
+}
+
+static void tune_store(GraphCache& G, const std::string& key, int w) {
+    G.tuned.emplace_back(key, w);
+    const char* path = std::getenv("RQB_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "batched_projection_width %s %d\n", key.c_str(), w);
+    std::fclose(f);
+}
+
+namespace {
+
+// Host-side layout of one batch for a projection width pw.
+struct Layout {
+    std::vector<GMat> d;
+    std::vector<Item> rows, proj, reproj;
+    size_t work_bytes = 0, out_bytes = 0;
+    size_t oDesc, oSt, oRows, oProj, oRep, oRp, oPp, oGp, oBlk, oOm0, oOm1;
+    std::vector<size_t> oW, qoff, boff;
+    int64_t n_max = 1, max_blocks = 1;
+};
+
+void make_layout(Layout& L, int pw, int64_t count, const void* const* A, const int64_t* m, const int64_t* n,
+                 const int64_t* lda, const double* eps, int64_t b, int64_t max_rank) {
     // largest matrices first: their items are scheduled first in every launch
     std::vector<int> order((size_t)count);
     for (int64_t t = 0; t < count; ++t) order[(size_t)t] = (int)t;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return m[x] * n[x] > m[y] * n[y]; });
-
-    // outputs: Q_t (ldq x kcap), B_t (ldb x n) per matrix
-    std::vector<GMat> d((size_t)count);
-    std::vector<size_t> qoff((size_t)count), boff((size_t)count);
+    L.d.assign((size_t)count, GMat{});
+    L.qoff.assign((size_t)count, 0);
+    L.boff.assign((size_t)count, 0);
     size_t total = 0;
-    int64_t n_max = 1, max_blocks = 1;
     for (int64_t t = 0; t < count; ++t) {
         const int64_t r = std::min(m[t], n[t]);
         const int64_t kc = (max_rank > 0 && max_rank < r) ? max_rank : r;
-        GMat& x = d[(size_t)t];
+        GMat& x = L.d[(size_t)t];
         x.A = static_cast<const float*>(A[t]);
         x.m = m[t]; x.n = n[t]; x.lda = lda[t]; x.kcap = kc;
         x.ldq = ((m[t] + 3) / 4) * 4;
         x.ldb = ((kc + 3) / 4) * 4;
         x.ldw = ((m[t] + 3) / 4) * 4;
         x.eps2 = eps[t] * eps[t];
-        qoff[(size_t)t] = total; total = al256(total + sizeof(float) * (size_t)x.ldq * (size_t)kc);
-        boff[(size_t)t] = total; total = al256(total + sizeof(float) * (size_t)x.ldb * (size_t)n[t]);
-        n_max = std::max(n_max, n[t]);
-        max_blocks = std::max(max_blocks, (kc + b - 1) / b);
+        L.qoff[(size_t)t] = total; total = al256(total + sizeof(float) * (size_t)x.ldq * (size_t)kc);
+        L.boff[(size_t)t] = total; total = al256(total + sizeof(float) * (size_t)x.ldb * (size_t)n[t]);
+        L.n_max = std::max(L.n_max, n[t]);
+        L.max_blocks = std::max(L.max_blocks, (kc + b - 1) / b);
     }
-    int rc = grow(outbuf, outbytes, total);
-    if (rc != RQB_OK) return rc;
-    char* ob = static_cast<char*>(*outbuf);
-    // work items, in decreasing matrix size
-    std::vector<Item> rows, proj, reproj;
+    L.out_bytes = total;
+    L.rows.clear(); L.proj.clear(); L.reproj.clear();
     for (int t : order) {
-        GMat& x = d[(size_t)t];
-        x.Q = reinterpret_cast<float*>(ob + qoff[(size_t)t]);
-        x.B = reinterpret_cast<float*>(ob + boff[(size_t)t]);
-        x.rows_begin = (int)rows.size();
-        for (int64_t i = 0; i < (x.m + TR - 1) / TR; ++i) rows.push_back(Item{t, (int)i});
-        x.rows_end = (int)rows.size();
-        x.proj_begin = (int)proj.size();
-        for (int64_t i = 0; i < (x.n + TC - 1) / TC; ++i) proj.push_back(Item{t, (int)i});
-        x.proj_end = (int)proj.size();
-        for (int64_t i = 0; i < (x.kcap + TCR - 1) / TCR; ++i) reproj.push_back(Item{t, (int)i});
+        GMat& x = L.d[(size_t)t];
+        x.rows_begin = (int)L.rows.size();
+        for (int64_t i = 0; i < (x.m + TR - 1) / TR; ++i) L.rows.push_back(Item{t, (int)i});
+        x.rows_end = (int)L.rows.size();
+        x.proj_begin = (int)L.proj.size();
+        for (int64_t i = 0; i < (x.n + pw - 1) / pw; ++i) L.proj.push_back(Item{t, (int)i});
+        x.proj_end = (int)L.proj.size();
+        for (int64_t i = 0; i < (x.kcap + TCR - 1) / TCR; ++i) L.reproj.push_back(Item{t, (int)i});
     }
-    // work layout: descriptors, state, item tables, partials, Omega x 2,
-    // then per matrix W, Y, Y1, Cc, Rinv
+    // work layout: descriptors, state, item tables, partials, block index,
+    // Omega x 2, then per matrix W, Y, Y1, Cc, Rinv
     size_t w = 0;
-    const size_t oDesc = w; w = al256(w + sizeof(GMat) * (size_t)count);
-    const size_t oSt = w; w = al256(w + sizeof(GState) * (size_t)count);
-    const size_t oRows = w; w = al256(w + sizeof(Item) * rows.size());
-    const size_t oProj = w; w = al256(w + sizeof(Item) * proj.size());
-    const size_t oRep = w; w = al256(w + sizeof(Item) * reproj.size());
-    const size_t oRp = w; w = al256(w + sizeof(double) * rows.size());
-    const size_t oPp = w; w = al256(w + sizeof(double) * proj.size());
-    const size_t oGp = w; w = al256(w + sizeof(double) * BP * BP * rows.size());
-    const size_t oCnt = w; w = al256(w + sizeof(int));
-    const size_t oOm0 = w; w = al256(w + sizeof(float) * (size_t)n_max * BP);
-    const size_t oOm1 = w; w = al256(w + sizeof(float) * (size_t)n_max * BP);
-    std::vector<size_t> oW((size_t)count);
+    L.oDesc = w; w = al256(w + sizeof(GMat) * (size_t)count);
+    L.oSt = w; w = al256(w + sizeof(GState) * (size_t)count);
+    L.oRows = w; w = al256(w + sizeof(Item) * L.rows.size());
+    L.oProj = w; w = al256(w + sizeof(Item) * L.proj.size());
+    L.oRep = w; w = al256(w + sizeof(Item) * L.reproj.size());
+    L.oRp = w; w = al256(w + sizeof(double) * L.rows.size());
+    L.oPp = w; w = al256(w + sizeof(double) * L.proj.size());
+    L.oGp = w; w = al256(w + sizeof(double) * BP * BP * L.rows.size());
+    L.oBlk = w; w = al256(w + sizeof(int));
+    L.oOm0 = w; w = al256(w + sizeof(float) * (size_t)L.n_max * BP);
+    L.oOm1 = w; w = al256(w + sizeof(float) * (size_t)L.n_max * BP);
+    L.oW.assign((size_t)count, 0);
     for (int64_t t = 0; t < count; ++t) {
-        const GMat& x = d[(size_t)t];
-        oW[(size_t)t] = w;
+        const GMat& x = L.d[(size_t)t];
+        L.oW[(size_t)t] = w;
         w = al256(w + sizeof(float) * (size_t)x.ldw * (size_t)x.n);          // W
         w = al256(w + sizeof(float) * (size_t)x.ldw * BP);                    // Y
         w = al256(w + sizeof(float) * (size_t)x.ldw * BP);                    // Y1
         w = al256(w + sizeof(float) * (size_t)x.kcap * BP);                   // Cc
         w = al256(w + sizeof(float) * BP * BP);                               // Rinv
     }
-    rc = grow(workbuf, workbytes, w);
+    L.work_bytes = w;
+}
+
+// Runs the batch with projection width pw through the cached (or a new)
+// graph; on success *ms is the device time of the graph and *iters the
+// number of blocks the loop ran.
+int run_batch(GraphCache& G, Layout& L, int pw, int64_t count, int64_t b, uint64_t seed, cudaStream_t stream,
+              int device, void** outbuf, size_t* outbytes, void** workbuf, size_t* workbytes,
+              std::vector<GState>& outs, float* ms, int* iters) {
+    int rc = grow(outbuf, outbytes, L.out_bytes);
     if (rc != RQB_OK) return rc;
+    rc = grow(workbuf, workbytes, L.work_bytes);
+    if (rc != RQB_OK) return rc;
+    char* ob = static_cast<char*>(*outbuf);
     char* wb = static_cast<char*>(*workbuf);
     for (int64_t t = 0; t < count; ++t) {
-        GMat& x = d[(size_t)t];
-        char* p = wb + oW[(size_t)t];
+        GMat& x = L.d[(size_t)t];
+        x.Q = reinterpret_cast<float*>(ob + L.qoff[(size_t)t]);
+        x.B = reinterpret_cast<float*>(ob + L.boff[(size_t)t]);
+        char* p = wb + L.oW[(size_t)t];
         x.W = reinterpret_cast<float*>(p); p += al256(sizeof(float) * (size_t)x.ldw * (size_t)x.n);
         x.Y = reinterpret_cast<float*>(p); p += al256(sizeof(float) * (size_t)x.ldw * BP);
         x.Y1 = reinterpret_cast<float*>(p); p += al256(sizeof(float) * (size_t)x.ldw * BP);
@@ -938,98 +1110,122 @@ int factor_batched(cudaStream_t stream, int num_sms, int64_t count, const void* 
         x.Rinv = reinterpret_cast<float*>(p);
     }
     Tables T;
-    T.mats = reinterpret_cast<const GMat*>(wb + oDesc);
-    T.st = reinterpret_cast<GState*>(wb + oSt);
-    T.rows = reinterpret_cast<const Item*>(wb + oRows);
-    T.proj = reinterpret_cast<const Item*>(wb + oProj);
-    T.reproj = reinterpret_cast<const Item*>(wb + oRep);
-    T.nrows = (int)rows.size();
-    T.nproj = (int)proj.size();
-    T.nreproj = (int)reproj.size();
+    T.mats = reinterpret_cast<const GMat*>(wb + L.oDesc);
+    T.st = reinterpret_cast<GState*>(wb + L.oSt);
+    T.rows = reinterpret_cast<const Item*>(wb + L.oRows);
+    T.proj = reinterpret_cast<const Item*>(wb + L.oProj);
+    T.reproj = reinterpret_cast<const Item*>(wb + L.oRep);
+    T.nrows = (int)L.rows.size();
+    T.nproj = (int)L.proj.size();
+    T.nreproj = (int)L.reproj.size();
     T.count = (int)count;
-    T.rows_part = reinterpret_cast<double*>(wb + oRp);
-    T.proj_part = reinterpret_cast<double*>(wb + oPp);
-    T.gpart = reinterpret_cast<double*>(wb + oGp);
-    T.Om[0] = reinterpret_cast<float*>(wb + oOm0);
-    T.Om[1] = reinterpret_cast<float*>(wb + oOm1);
-    T.n_max = n_max;
-    int* dcount = reinterpret_cast<int*>(wb + oCnt);
+    T.rows_part = reinterpret_cast<double*>(wb + L.oRp);
+    T.proj_part = reinterpret_cast<double*>(wb + L.oPp);
+    T.gpart = reinterpret_cast<double*>(wb + L.oGp);
+    T.blk = reinterpret_cast<int*>(wb + L.oBlk);
+    T.Om[0] = reinterpret_cast<float*>(wb + L.oOm0);
+    T.Om[1] = reinterpret_cast<float*>(wb + L.oOm1);
+    T.n_max = L.n_max;
+    T.max_blocks = (int)L.max_blocks;
 
-    cudaStream_t cs = nullptr;
-    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return RQB_ERR_CUDA;
-    cudaEvent_t e0 = nullptr, e1 = nullptr, dep = nullptr;
-    int nl = 0;
-    rc = RQB_OK;
-    do {
-        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
-            cudaEventCreateWithFlags(&dep, cudaEventDisableTiming) != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
-        // order after earlier work on the caller's stream
-        if (cudaEventRecord(dep, stream) != cudaSuccess || cudaStreamWaitEvent(cs, dep, 0) != cudaSuccess) {
-            rc = RQB_ERR_CUDA; break;
-        }
-        if (cudaMemcpyAsync(wb + oDesc, d.data(), sizeof(GMat) * (size_t)count, cudaMemcpyHostToDevice, cs) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(wb + oRows, rows.data(), sizeof(Item) * rows.size(), cudaMemcpyHostToDevice, cs) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(wb + oProj, proj.data(), sizeof(Item) * proj.size(), cudaMemcpyHostToDevice, cs) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(wb + oRep, reproj.data(), sizeof(Item) * reproj.size(), cudaMemcpyHostToDevice, cs) !=
-                cudaSuccess) { rc = RQB_ERR_CUDA; break; }
-        if (cudaEventRecord(e0, cs) != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
-        // block 1's sketch and the initial state
-        const int64_t tot = n_max * BP;
-        k_omega_rows<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, cs>>>(n_max, 0, (int)b, seed,
-                                                                                     T.Om[0]);
-        k_rows<kRowSketch0><<<T.nrows, NT, 0, cs>>>(T.mats, T.st, T.rows, (int)b, T.Om[0], T.rows_part);
-        k_mat<kMatInit><<<T.count, NT, 0, cs>>>(T.mats, T.st, (int)b, T.rows_part, T.proj_part, T.gpart);
-        nl += 3;
-        if (cudaGetLastError() != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
-        // blocks in chunks of kChunk, each chunk one captured graph
-        for (int i0 = 0; i0 < (int)max_blocks && rc == RQB_OK; i0 += kChunk) {
-            const int i1 = std::min<int>((int)max_blocks, i0 + kChunk);
-            cudaGraph_t graph = nullptr;
-            cudaGraphExec_t exec = nullptr;
-            if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
-            cudaError_t le = cudaSuccess;
-            for (int i = i0; i < i1 && le == cudaSuccess; ++i) le = launch_block(cs, T, i, (int)b, seed, &nl);
-            if (le == cudaSuccess) k_count_active<<<1, NT, 0, cs>>>(T.st, T.count, dcount);
-            if (cudaStreamEndCapture(cs, &graph) != cudaSuccess || !graph || le != cudaSuccess) {
-                if (graph) cudaGraphDestroy(graph);
-                rc = RQB_ERR_CUDA;
-                break;
+    if (!G.cap && cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking) != cudaSuccess) return RQB_ERR_CUDA;
+    if (!G.e0 && cudaEventCreate(&G.e0) != cudaSuccess) return RQB_ERR_CUDA;
+    if (!G.e1 && cudaEventCreate(&G.e1) != cudaSuccess) return RQB_ERR_CUDA;
+    const bool same = G.exec && G.work == wb && G.count == count && G.nrows == T.nrows && G.nproj == T.nproj &&
+                      G.nreproj == T.nreproj && G.n_max == T.n_max && G.b == b && G.max_blocks == T.max_blocks &&
+                      G.pw == pw && G.seed == seed && G.device == device;
+    if (!same) {
+        G.drop_graph();
+        rc = (pw == 128) ? build_graph<128>(G, T, (int)b, seed) : build_graph<256>(G, T, (int)b, seed);
+        if (rc != RQB_OK) return rc;
+        G.work = wb; G.count = count; G.nrows = T.nrows; G.nproj = T.nproj; G.nreproj = T.nreproj;
+        G.n_max = T.n_max; G.b = b; G.max_blocks = T.max_blocks; G.pw = pw; G.seed = seed; G.device = device;
+    }
+    // descriptors and item tables for this call, then the whole factorization
+    if (cudaMemcpyAsync(wb + L.oDesc, L.d.data(), sizeof(GMat) * (size_t)count, cudaMemcpyHostToDevice, stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(wb + L.oRows, L.rows.data(), sizeof(Item) * L.rows.size(), cudaMemcpyHostToDevice, stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(wb + L.oProj, L.proj.data(), sizeof(Item) * L.proj.size(), cudaMemcpyHostToDevice, stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(wb + L.oRep, L.reproj.data(), sizeof(Item) * L.reproj.size(), cudaMemcpyHostToDevice,
+                        stream) != cudaSuccess)
+        return RQB_ERR_CUDA;
+    int blk = 0;
+    outs.resize((size_t)count);
+    if (cudaEventRecord(G.e0, stream) != cudaSuccess || cudaGraphLaunch(G.exec, stream) != cudaSuccess ||
+        cudaEventRecord(G.e1, stream) != cudaSuccess ||
+        cudaMemcpyAsync(outs.data(), wb + L.oSt, sizeof(GState) * (size_t)count, cudaMemcpyDeviceToHost, stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(&blk, T.blk, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return RQB_ERR_CUDA;
+    float t_ms = 0.f;
+    cudaEventElapsedTime(&t_ms, G.e0, G.e1);
+    *ms = t_ms;
+    *iters = blk;
+    return RQB_OK;
+}
+
+}  // namespace
+
+int factor_batched(cudaStream_t stream, int num_sms, int64_t count, const void* const* A, const int64_t* m,
+                   const int64_t* n, const int64_t* lda, const double* eps, int64_t b, uint64_t seed, int64_t max_rank,
+                   const void** Q, int64_t* ldq, const void** B, int64_t* ldb, int64_t* k, int* status, void** outbuf,
+                   size_t* outbytes, void** workbuf, size_t* workbytes, void** cache, float* ms, int* launches,
+                   int* proj_width) {
+    (void)num_sms;
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return RQB_ERR_CUDA;
+    if (!*cache) {
+        *cache = new (std::nothrow) GraphCache();
+        if (!*cache) return RQB_ERR_OOM;
+    }
+    GraphCache& G = *static_cast<GraphCache*>(*cache);
+    tune_load(G);
+    const std::string cls = batch_class(count, m, n, b);
+    int pw = tune_lookup(G, cls);
+    std::vector<GState> outs;
+    Layout L;
+    float t_ms = 0.f;
+    int iters = 0;
+    int rc = RQB_OK;
+    if (pw == 0) {
+        // first batch of this class: run both widths, keep the faster
+        float best = 0.f;
+        for (int cand : {256, 128}) {
+            make_layout(L, cand, count, A, m, n, lda, eps, b, max_rank);
+            rc = run_batch(G, L, cand, count, b, seed, stream, device, outbuf, outbytes, workbuf, workbytes, outs,
+                           &t_ms, &iters);
+            if (rc != RQB_OK) return rc;
+            if (pw == 0 || t_ms < best) {
+                best = t_ms;
+                pw = cand;
             }
-            nl += 1;
-            int active = 0;
-            if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess || cudaGraphLaunch(exec, cs) != cudaSuccess ||
-                cudaMemcpyAsync(&active, dcount, sizeof(int), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
-                cudaStreamSynchronize(cs) != cudaSuccess)
-                rc = RQB_ERR_CUDA;
-            if (exec) cudaGraphExecDestroy(exec);
-            cudaGraphDestroy(graph);
-            if (rc == RQB_OK && active == 0) break;
         }
-        if (rc != RQB_OK) break;
-        if (cudaEventRecord(e1, cs) != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
-        std::vector<GState> outs((size_t)count);
-        if (cudaMemcpyAsync(outs.data(), wb + oSt, sizeof(GState) * (size_t)count, cudaMemcpyDeviceToHost, cs) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(cs) != cudaSuccess) { rc = RQB_ERR_CUDA; break; }
-        float t_ms = 0.f;
-        cudaEventElapsedTime(&t_ms, e0, e1);
-        if (ms) *ms = t_ms;
-        if (launches) *launches = nl;
-        for (int64_t t = 0; t < count; ++t) {
-            Q[t] = d[(size_t)t].Q; ldq[t] = d[(size_t)t].ldq;
-            B[t] = d[(size_t)t].B; ldb[t] = d[(size_t)t].ldb;
-            k[t] = outs[(size_t)t].k; status[t] = outs[(size_t)t].status;
+        tune_store(G, cls, pw);
+        if (pw != 128) {
+            // the outputs of the last run (width 128) are those of the kept
+            // width too; the graph of the kept width is built for the next call
+            make_layout(L, pw, count, A, m, n, lda, eps, b, max_rank);
+            rc = run_batch(G, L, pw, count, b, seed, stream, device, outbuf, outbytes, workbuf, workbytes, outs,
+                           &t_ms, &iters);
         }
-    } while (0);
-    if (rc != RQB_OK) cudaGetLastError();
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    if (dep) cudaEventDestroy(dep);
-    cudaStreamDestroy(cs);
-    return rc;
+    } else {
+        make_layout(L, pw, count, A, m, n, lda, eps, b, max_rank);
+        rc = run_batch(G, L, pw, count, b, seed, stream, device, outbuf, outbytes, workbuf, workbytes, outs, &t_ms,
+                       &iters);
+    }
+    if (rc != RQB_OK) return rc;
+    if (ms) *ms = t_ms;
+    if (launches) *launches = kPrologueLaunches + kBlockLaunches * iters;
+    if (proj_width) *proj_width = pw;
+    for (int64_t t = 0; t < count; ++t) {
+        Q[t] = L.d[(size_t)t].Q; ldq[t] = L.d[(size_t)t].ldq;
+        B[t] = L.d[(size_t)t].B; ldb[t] = L.d[(size_t)t].ldb;
+        k[t] = outs[(size_t)t].k; status[t] = outs[(size_t)t].status;
+    }
+    return RQB_OK;
 }
 
 }  // namespace batched

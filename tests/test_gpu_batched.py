@@ -1,4 +1,5 @@
-"""rqb_factor_batched: many FP32 matrices of uneven sizes in one persistent launch.
+"""rqb_factor_batched: many FP32 matrices of uneven sizes in one graph launch
+(a device-side block loop; tile width picked by the autotuner).
 
 Each matrix is compared with the oracle (randQB_b, same seed, binary32 Omega):
 rank exact (or one block away inside the decision band), |r_gpu - r_orc| <=
@@ -102,3 +103,65 @@ def test_batched_zero_matrix_empty_factorization(rqb_lib):
         Q, B, k, st = fac[i]
         assert st == rqb_lib.RQB_OK and k > 0
         assert resid(mats[i][0], Q, B) <= mats[i][1] * (1 + 1e-4)
+
+
+def _run(rqb_lib, mats, eps, b=32, seed=4):
+    devs = [to_dev(A, torch.float32) for A, _ in mats] if not torch.is_tensor(mats[0]) else mats
+    with rqb_lib.Handle(torch.float32) as h:
+        out = h.rqb_factor_batched(devs, eps, b, seed=seed)
+        res = [(to_np(Q), to_np(B), k, st) for Q, B, k, st in out]
+        out2 = h.rqb_factor_batched(devs, eps, b, seed=seed)      # the cached graph
+        res2 = [(to_np(Q), to_np(B), k, st) for Q, B, k, st in out2]
+        stats = h.rqb_get_stats()
+    return res, res2, stats
+
+
+def test_batched_one_graph_reused_and_autotuned(rqb_lib, tmp_path, monkeypatch):
+    """The whole batch runs as one graph launch whose block loop is a WHILE
+    node: the launch count is the prologue plus 14 kernels per block, a
+    second call reuses the graph with bit-identical results, and the
+    autotuner writes its choice for the batch class to RQB_AUTOTUNE_CACHE."""
+    mats = _batch(seed=5)
+    eps = [e for _, e in mats]
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("RQB_AUTOTUNE_CACHE", str(cache))
+    res, res2, st = _run(rqb_lib, mats, eps)
+    for (Q, B, k, s), (Q2, B2, k2, s2) in zip(res, res2):
+        assert k == k2 and s == s2
+        assert np.array_equal(Q, Q2) and np.array_equal(B, B2)
+    lines = cache.read_text().split("\n")
+    lines = [l for l in lines if l]
+    assert len(lines) == 1 and lines[0].startswith("batched_projection_width ")
+    width = int(lines[0].split()[-1])
+    assert width in (128, 256) and st.tile_width == width
+    max_k = max(k for _, _, k, _ in res)
+    blocks = -(-max_k // 32)
+    assert (st.kernel_launches - 3) % 14 == 0 and (st.kernel_launches - 3) // 14 >= blocks
+    # a new handle (a new process alike) reads the choice instead of tuning again
+    res3, _, st3 = _run(rqb_lib, mats, eps)
+    assert len([l for l in cache.read_text().split("\n") if l]) == 1 and st3.tile_width == width
+    for (Q, B, k, s), (Q3, B3, k3, s3) in zip(res, res3):
+        assert k == k3 and np.array_equal(Q, Q3) and np.array_equal(B, B3)
+
+
+def test_batched_projection_widths_bitwise_equal(rqb_lib, tmp_path, monkeypatch):
+    """Each B_i entry is one thread's sum over the rows in the same order
+    whatever the projection's tile width, so both widths the autotuner picks
+    from give the same factors bit for bit."""
+    mats = _batch(seed=6)[:8]
+    eps = [e for _, e in mats]
+    tune = tmp_path / "tune.txt"
+    monkeypatch.setenv("RQB_AUTOTUNE_CACHE", str(tune))
+    _run(rqb_lib, mats, eps)
+    key = tune.read_text().split()[1]
+    out = {}
+    for w in (128, 256):
+        f = tmp_path / f"w{w}.txt"
+        f.write_text(f"batched_projection_width {key} {w}\n")
+        monkeypatch.setenv("RQB_AUTOTUNE_CACHE", str(f))
+        res, _, st = _run(rqb_lib, mats, eps)
+        assert st.tile_width == w
+        out[w] = res
+    for (Q1, B1, k1, s1), (Q2, B2, k2, s2) in zip(out[128], out[256]):
+        assert k1 == k2 and s1 == s2
+        assert np.array_equal(Q1, Q2) and np.array_equal(B1, B2)

@@ -482,6 +482,36 @@ def run_plain_matched(args, w: dict, res: dict, steps: int = 2, prec: int | None
             "unit": "TFLOP/s", "k": k, "steps": steps, "speedup_of_form": round(ms / res["ms"], 3)}
 
 
+def run_omega_smem(args, w: dict, res: dict, steps: int = 3) -> dict:
+    """The BF16 workload with Omega_i drawn inside the sketch kernel
+    (RQB_FLAG_OMEGA_SMEM) instead of loaded from its buffer: same matrix, eps
+    and results; the sketch phase and the whole factorization timed."""
+    import torch
+    from paper_1503_07157_gb300 import rqb
+    m, n, b = w["m"], w["n"], w["b"]
+    h = rqb.Handle(torch.bfloat16, prec=rqb.RQB_PREC_BF16, stream=res["stream"],
+                   flags=rqb.RQB_FLAG_PHASE_TIMING | rqb.RQB_FLAG_OMEGA_SMEM)
+    h.rqb_factor(res["A"], res["eps"], b, seed=0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sk_ms, sk_calls = 0.0, 0
+    torch.cuda.synchronize()
+    ev0.record(res["stream"])
+    for _ in range(steps):
+        _, _, k, rc = h.rqb_factor(res["A"], res["eps"], b, seed=0)
+        st = h.rqb_get_stats()
+        sk_ms += st.phase_ms[0]
+        sk_calls += st.phase_calls[0]
+    ev1.record(res["stream"])
+    torch.cuda.synchronize()
+    h.close()
+    ms = ev0.elapsed_time(ev1) / steps
+    buf = res["roofline"]["phase_ms_per_step"]["sketch"]
+    return {"impl": "BF16, Omega_i drawn in shared memory inside the sketch (RQB_FLAG_OMEGA_SMEM)",
+            "ms_per_step": round(ms, 3), "k": k, "steps": steps,
+            "sketch_ms_per_step": round(sk_ms / steps, 4), "sketch_ms_per_launch": round(sk_ms / max(sk_calls, 1), 4),
+            "buffered_sketch_ms_per_step": buf, "buffered_ms_per_step": round(res["ms"], 3)}
+
+
 def run_e2e(args, w: dict, res: dict) -> dict:
     """Same metric through rqb_factor_host: pinned host A in, Q and B back to
     pinned host buffers, all copies inside the timed region."""
@@ -780,7 +810,8 @@ def run_forms(args, rank: int, world: int, dist) -> dict:
     out["bf16"] = {"workload": w16["name"], "value": round(r["value"], 4), "unit": "TFLOP/s",
                    "ms_per_step": round(r["ms"], 3), "steps": a.steps, "k": r["k"], "blocks": r["s"],
                    "roofline": r["roofline"], "whole_run": r["whole_run"],
-                   "plain_fp32_matched_eps": run_plain_matched(a, w16, r) if rank == 0 else None}
+                   "plain_fp32_matched_eps": run_plain_matched(a, w16, r) if rank == 0 else None,
+                   "omega_in_shared_memory": run_omega_smem(a, w16, r) if rank == 0 else None}
     r["h"].close()
     del r
     gc.collect()

@@ -100,6 +100,15 @@ typedef struct {
  * exceeds about u^(-1/2) of the Gram's precision reports
  * RQB_ERR_BREAKDOWN. */
 #define RQB_FLAG_SKIP_INNER_ORTH 2
+/* BF16 handles (else RQB_ERR_UNSUPPORTED): the sketch draws Omega_i
+ * (Fig. randQB_b line (2)) inside its kernel, per K-chunk and row tile,
+ * straight into the shared-memory operand of the tensor-core MMA, instead of
+ * writing Omega_i once per block to device memory and loading it from there.
+ * Same values and results bit for bit.  Regenerating Omega_i for every row
+ * tile costs more arithmetic than the loads it replaces, so the default
+ * (buffered Omega_i) is the faster path on this part; the flag exists to
+ * measure the alternative. */
+#define RQB_FLAG_OMEGA_SMEM 4
 
 /* Steps timed with RQB_FLAG_PHASE_TIMING (index into phase_ms/phase_calls). */
 typedef enum {

@@ -655,6 +655,21 @@ bool tma_ok16(const void* p, int64_t ld) { return (reinterpret_cast<uintptr_t>(p
 // residual to BF16, so E_i no longer tracks the stored residual: the stop
 // test of line (6) is decided on the direct ||A^(i)||_F^2 of the stored
 // values, summed by the update itself, every block.
+// Lines (2), (3) on the BF16 path: Omega_i (global columns col0 ..) into its
+// buffer and Y = X Omega_i, or with RQB_FLAG_OMEGA_SMEM Omega_i drawn inside
+// the sketch kernel (the same values).
+int sketch_block16(rqb_handle h, Ctx& cx, const TcArena16& ta, const __nv_bfloat16* X, int64_t ldx, int64_t m,
+                   int64_t n, int64_t col0, int p, int bp, uint64_t seed, float* Y) {
+    if (h->cfg.flags & RQB_FLAG_OMEGA_SMEM) {
+        const tc::OmegaGen gen{col0, p, seed};
+        RQB_CK(tc::sketch16(cx, X, ldx, m, n, nullptr, 0, bp, Y, m, ta.part, ta.part_cap, &gen));
+        return RQB_OK;
+    }
+    RQB_CK(tc::omega16(cx, n, col0, p, bp, seed, ta.Om, ta.ldom));
+    RQB_CK(tc::sketch16(cx, X, ldx, m, n, ta.Om, ta.ldom, bp, Y, m, ta.part, ta.part_cap));
+    return RQB_OK;
+}
+
 int factor_bf16(rqb_handle h, const __nv_bfloat16* A, int64_t m, int64_t n, int64_t lda, double eps, int64_t b,
                 uint64_t seed, int64_t* k_out) {
     const int64_t rmax = std::min(m, n);
@@ -706,8 +721,7 @@ int factor_bf16(rqb_handle h, const __nv_bfloat16* A, int64_t m, int64_t n, int6
     int p = (int)std::min<int64_t>(b, kcap);
     RQB_CK(launch_sumsq<__nv_bfloat16>(cx, m, n, Wsrc, ldws, sc.nrm, kNrmCap, sc.s + 0));
     RQB_CK(launch_set_norm(cx, sc.s + 0));
-    RQB_CK(tc::omega16(cx, n, 0, p, bp, seed, ta.Om, ta.ldom));
-    RQB_CK(tc::sketch16(cx, Wsrc, ldws, m, n, ta.Om, ta.ldom, bp, ar.Y, m, ta.part, ta.part_cap));
+    if ((rc = sketch_block16(h, cx, ta, Wsrc, ldws, m, n, 0, p, bp, seed, ar.Y)) != RQB_OK) return rc;
     h->timer.end(h->stream);
 
     for (;;) {
@@ -752,8 +766,7 @@ int factor_bf16(rqb_handle h, const __nv_bfloat16* A, int64_t m, int64_t n, int6
         if (k >= kcap) break;
         const int pn = (int)std::min<int64_t>(b, kcap - k);
         h->timer.begin(h->stream, RQB_PHASE_SKETCH);
-        RQB_CK(tc::omega16(cx, n, k, pn, bp, seed, ta.Om, ta.ldom));
-        RQB_CK(tc::sketch16(cx, W, ldw, m, n, ta.Om, ta.ldom, bp, ar.Y, m, ta.part, ta.part_cap));
+        if ((rc = sketch_block16(h, cx, ta, W, ldw, m, n, k, pn, bp, seed, ar.Y)) != RQB_OK) return rc;
         h->timer.end(h->stream);
     }
     h->stats.k = k;
@@ -952,9 +965,10 @@ const char* rqb_status_string(int status) {
 int rqb_create(rqb_handle* out, const rqb_config* cfg) {
     if (!out || !cfg) return RQB_ERR_INVALID;
     *out = nullptr;
-    if ((cfg->flags & ~(RQB_FLAG_PHASE_TIMING | RQB_FLAG_SKIP_INNER_ORTH)) != 0 || cfg->max_rank < 0 ||
-        cfg->power < 0)
+    if ((cfg->flags & ~(RQB_FLAG_PHASE_TIMING | RQB_FLAG_SKIP_INNER_ORTH | RQB_FLAG_OMEGA_SMEM)) != 0 ||
+        cfg->max_rank < 0 || cfg->power < 0)
         return RQB_ERR_INVALID;
+    if ((cfg->flags & RQB_FLAG_OMEGA_SMEM) && cfg->dtype != RQB_BF16) return RQB_ERR_UNSUPPORTED;
     if (cfg->dtype != RQB_F64 && cfg->dtype != RQB_F32 && cfg->dtype != RQB_BF16) return RQB_ERR_INVALID;
     if (cfg->prec != RQB_PREC_NATIVE && cfg->prec != RQB_PREC_TF32X3 && cfg->prec != RQB_PREC_BF16)
         return RQB_ERR_INVALID;
@@ -1339,8 +1353,7 @@ int sketch_bf16(rqb_handle h, const __nv_bfloat16* A, int64_t m, int64_t n, int6
     int64_t ldx;
     if ((rc = tma_source16(h, A, lda, m, n, &X, &ldx)) != RQB_OK) return rc;
     if (normA2) RQB_CK(launch_sumsq<__nv_bfloat16>(cx, m, n, X, ldx, sc.nrm, kNrmCap, sc.s + 0));
-    RQB_CK(tc::omega16(cx, n, col0, p, bp, seed, ta.Om, ta.ldom));
-    RQB_CK(tc::sketch16(cx, X, ldx, m, n, ta.Om, ta.ldom, bp, ar.Y, m, ta.part, ta.part_cap));
+    if ((rc = sketch_block16(h, cx, ta, X, ldx, m, n, col0, p, bp, seed, ar.Y)) != RQB_OK) return rc;
     RQB_CK(cudaMemcpy2DAsync(Y, sizeof(float) * ldy, ar.Y, sizeof(float) * m, sizeof(float) * m, p,
                              cudaMemcpyDeviceToDevice, h->stream));
     if (normA2) RQB_CK(cudaMemcpyAsync(normA2, sc.s + 0, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -1400,8 +1413,7 @@ int dd_bf16(rqb_handle h, const __nv_bfloat16* A, int64_t lda, const float* Qi, 
                         normW2 ? sc.s + 2 : nullptr));
     if (copy_out)
         RQB_CK(cudaMemcpy2DAsync(W, 2 * ldw, X, 2 * ldx, 2 * m, n, cudaMemcpyDeviceToDevice, h->stream));
-    RQB_CK(tc::omega16(cx, n, col0, ncols, bps, seed, ta.Om, ta.ldom));
-    RQB_CK(tc::sketch16(cx, X, ldx, m, n, ta.Om, ta.ldom, bps, ar.Y, m, ta.part, ta.part_cap));
+    if ((rc = sketch_block16(h, cx, ta, X, ldx, m, n, col0, (int)ncols, bps, seed, ar.Y)) != RQB_OK) return rc;
     RQB_CK(cudaMemcpy2DAsync(Y, sizeof(float) * ldy, ar.Y, sizeof(float) * m, sizeof(float) * m, ncols,
                              cudaMemcpyDeviceToDevice, h->stream));
     if (normW2) RQB_CK(cudaMemcpyAsync(normW2, sc.s + 2, sizeof(double), cudaMemcpyDeviceToHost, h->stream));

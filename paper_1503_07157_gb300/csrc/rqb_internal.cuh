@@ -86,6 +86,20 @@ __device__ __forceinline__ float gaussian_f32(uint64_t seed, int64_t r, int64_t 
     return (c & 1) ? rad * s : rad * co;
 }
 
+// Entries (r, 2 j) and (r, 2 j + 1) of Omega from their one Philox block:
+// the values gaussian_f32 gives for those two columns, bit for bit.
+__device__ __forceinline__ void gaussian_pair_f32(uint64_t seed, int64_t r, int64_t j, float* even, float* odd) {
+    const Philox4 x = philox4x32_10((uint32_t)r, (uint32_t)j, 0u, 0u, (uint32_t)(seed & 0xffffffffull),
+                                    (uint32_t)(seed >> 32));
+    const float u1 = ((float)(x.v[0] >> 9) + 0.5f) * 1.1920928955078125e-7f;  // 2^-23
+    const float u2 = ((float)(x.v[2] >> 9) + 0.5f) * 1.1920928955078125e-7f;
+    const float rad = sqrtf(-2.0f * logf(u1));
+    float s, co;
+    sincospif(2.0f * u2, &s, &co);
+    *even = rad * co;
+    *odd = rad * s;
+}
+
 template <typename T>
 __device__ __forceinline__ T gaussian(uint64_t seed, int64_t r, int64_t c);
 template <>

@@ -52,6 +52,11 @@ struct StreamKParams {
     int G;             // partial slots per CTA
     int np;            // MMA N
     double* nrm_part = nullptr;  // sketch only, optional: ||X||_F^2, one FP64 partial per CTA
+    // BF16 sketch generating Omega in shared memory (k_streamk16 with GEN):
+    // rows om_n, global columns om_col0 .., om_p of them valid, seed
+    long long om_n = 0, om_col0 = 0;
+    int om_p = 0;
+    unsigned long long om_seed = 0;
 };
 
 __host__ __device__ __forceinline__ long long unit_begin(long long U, int P, int p) { return U * p / P; }
@@ -339,13 +344,51 @@ struct StreamK16Cfg {
     static constexpr size_t kSmem = (size_t)S * kStage + 1024;
 };
 
-template <int ROLE, int NP>
+// Omega's K-chunk kc of the BF16 sketch written by 256 threads (ct) into the
+// operand stage dst in the layout a TMA load with the 128-byte swizzle gives:
+// one 128-byte row of 64 K values per column c, 16-byte group j of row c at
+// group j ^ (c % 8).  Entry (kk, c) is the binary32 Gaussian at row
+// 64 kc + kk and global column om_col0 + c rounded to BF16 (nearest even),
+// zero past row om_n or column om_p: the values k_omega_bf16 writes.
+template <int NP>
+__device__ __forceinline__ void gen_omega_chunk(uint8_t* dst, int kc, const StreamKParams& p, int ct) {
+    constexpr int kPairs = NP / 2;
+    constexpr int kRowStep = 256 / kPairs;
+    const int c0 = 2 * (ct % kPairs);
+    const long long g0 = p.om_col0 + c0;
+    for (int kk = ct / kPairs; kk < kKC16; kk += kRowStep) {
+        const long long r = (long long)kc * kKC16 + kk;
+        float v0 = 0.f, v1 = 0.f;
+        if (r < p.om_n && c0 < p.om_p) {
+            if ((g0 & 1) == 0) {
+                float a, b;
+                gaussian_pair_f32(p.om_seed, r, g0 >> 1, &a, &b);
+                v0 = a;
+                v1 = (c0 + 1 < p.om_p) ? b : 0.f;
+            } else {
+                v0 = gaussian_f32(p.om_seed, r, g0);
+                if (c0 + 1 < p.om_p) v1 = gaussian_f32(p.om_seed, r, g0 + 1);
+            }
+        }
+        const uint32_t grp = (uint32_t)(kk >> 3), inr = (uint32_t)(kk & 7) * 2u;
+        *reinterpret_cast<__nv_bfloat16*>(dst + (uint32_t)c0 * 128u + ((grp ^ (uint32_t)(c0 & 7)) << 4) + inr) =
+            __float2bfloat16_rn(v0);
+        *reinterpret_cast<__nv_bfloat16*>(dst + (uint32_t)(c0 + 1) * 128u + ((grp ^ (uint32_t)((c0 + 1) & 7)) << 4) +
+                                          inr) = __float2bfloat16_rn(v1);
+    }
+}
+
+// GEN (sketch only): Omega is not loaded by TMA but generated per unit by the
+// eight epilogue warps into the stage (gen_omega_chunk), which they may
+// overwrite once the MMAs of the stage's previous use have completed.
+template <int ROLE, int NP, bool GEN = false>
 __global__ void __launch_bounds__(320, 1) k_streamk16(const __grid_constant__ StreamKParams p) {
     using Cfg = StreamK16Cfg<ROLE, NP>;
     constexpr int S = Cfg::S;
     constexpr uint32_t kW = Cfg::kW, kStage = Cfg::kStage;
     constexpr int kHalf = NP / 2;
-    __shared__ __align__(8) uint64_t full[S], empty[S], accfull[2], accempty[2], drain;
+    static_assert(!GEN || ROLE == kSketch, "Omega is generated only by the sketch");
+    __shared__ __align__(8) uint64_t full[S], empty[S], omfull[S], accfull[2], accempty[2], drain;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     extern __shared__ uint8_t dsm[];
@@ -354,13 +397,17 @@ __global__ void __launch_bounds__(320, 1) k_streamk16(const __grid_constant__ St
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     volatile int* ab = &abort_flag;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+            if (GEN) mbar_init(&omfull[s], 8);
+        }
         for (int s = 0; s < 2; ++s) { mbar_init(&accfull[s], 1); mbar_init(&accempty[s], 8); }
         mbar_init(&drain, 1);
         abort_flag = 0;
         fence_mbar_init();
         prefetch_map(&p.mx);
-        prefetch_map(&p.mw);
+        if (!GEN) prefetch_map(&p.mw);
         if (ROLE == kProject) prefetch_map(&p.mwl);
     }
     if (warp == 1) tmem_alloc(&tmem_base, ncols);
@@ -385,10 +432,10 @@ __global__ void __launch_bounds__(320, 1) k_streamk16(const __grid_constant__ St
                 const int t = (int)(u / p.C), kc = (int)(u % p.C);
                 uint8_t* st = base + s * kStage;
                 if (ROLE == kSketch) {
-                    mbar_arrive_expect_tx(&full[s], kTileBytes + kW);
+                    mbar_arrive_expect_tx(&full[s], GEN ? kTileBytes : kTileBytes + kW);
                     tma_load_2d(st, &p.mx, t * kBM, kc * kKC16, &full[s]);
                     tma_load_2d(st + kTileBytes / 2, &p.mx, t * kBM + 64, kc * kKC16, &full[s]);
-                    tma_load_2d(st + kTileBytes, &p.mw, kc * kKC16, 0, &full[s]);
+                    if (!GEN) tma_load_2d(st + kTileBytes, &p.mw, kc * kKC16, 0, &full[s]);
                 } else {
                     mbar_arrive_expect_tx(&full[s], kTileBytes + 2u * kW);
                     tma_load_2d(st, &p.mx, kc * kKC16, t * kBM, &full[s]);
@@ -409,6 +456,7 @@ __global__ void __launch_bounds__(320, 1) k_streamk16(const __grid_constant__ St
                 const int s = (int)(q % S);
                 const uint32_t r = (uint32_t)(q / S);
                 if (!mbar_wait(&full[s], r & 1u, ab)) break;
+                if (GEN && !mbar_wait(&omfull[s], r & 1u, ab)) break;
                 const int abuf = g & 1, use = g >> 1;
                 if (first && use > 0 && !mbar_wait(&accempty[abuf], (uint32_t)(use - 1) & 1u, ab)) break;
                 tc_fence_after();
@@ -450,7 +498,18 @@ __global__ void __launch_bounds__(320, 1) k_streamk16(const __grid_constant__ St
 #pragma unroll
         for (int i = 0; i < kHalf; ++i) acc[i] = 0.f;
         int g = 0;
-        for (long long u = u0; u < u1; ++u) {
+        long long q = 0;
+        for (long long u = u0; u < u1; ++u, ++q) {
+            if constexpr (GEN) {
+                const int s = (int)(q % S);
+                const uint32_t r = (uint32_t)(q / S);
+                const bool okg = (r == 0) || mbar_wait(&empty[s], (r - 1) & 1u, ab);
+                if (!__all_sync(0xffffffffu, okg)) break;
+                gen_omega_chunk<NP>(base + s * kStage + kTileBytes, (int)(u % p.C), p, (int)threadIdx.x - 64);
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&omfull[s]);
+            }
             if (!period_end(u)) continue;
             const int abuf = g & 1, use = g >> 1;
             const bool okw = mbar_wait(&accfull[abuf], (uint32_t)use & 1u, ab);
@@ -1765,22 +1824,22 @@ cudaError_t launch_streamk(Ctx& cx, const StreamKParams& p, int np) {
     }
 }
 
-template <int ROLE, int NP>
+template <int ROLE, int NP, bool GEN = false>
 cudaError_t launch_streamk16_np(Ctx& cx, const StreamKParams& p) {
     constexpr size_t smem = StreamK16Cfg<ROLE, NP>::kSmem;
-    cudaError_t e = allow_smem(k_streamk16<ROLE, NP>, smem);
+    cudaError_t e = allow_smem(k_streamk16<ROLE, NP, GEN>, smem);
     if (e != cudaSuccess) return e;
-    k_streamk16<ROLE, NP><<<p.P, 320, smem, cx.stream>>>(p);
+    k_streamk16<ROLE, NP, GEN><<<p.P, 320, smem, cx.stream>>>(p);
     cx.launches++;
     return cudaGetLastError();
 }
 
-template <int ROLE>
+template <int ROLE, bool GEN = false>
 cudaError_t launch_streamk16(Ctx& cx, const StreamKParams& p, int np) {
     switch (np) {
-        case 64: return launch_streamk16_np<ROLE, 64>(cx, p);
-        case 128: return launch_streamk16_np<ROLE, 128>(cx, p);
-        case 256: return launch_streamk16_np<ROLE, 256>(cx, p);
+        case 64: return launch_streamk16_np<ROLE, 64, GEN>(cx, p);
+        case 128: return launch_streamk16_np<ROLE, 128, GEN>(cx, p);
+        case 256: return launch_streamk16_np<ROLE, 256, GEN>(cx, p);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -2091,18 +2150,28 @@ cudaError_t stage_b16(Ctx& cx, const float* Bi, long long ldbi, int p, long long
 
 cudaError_t sketch16(Ctx& cx, const __nv_bfloat16* X, long long ldx, long long m, long long n,
                      const __nv_bfloat16* Om, long long ldom, int np, float* Y, long long ldy, float* part,
-                     size_t part_cap) {
+                     size_t part_cap, const OmegaGen* gen) {
     StreamKParams p;
     cudaError_t e;
     if ((e = make_map(&p.mx, X, m, n, ldx, 64, kKC16, true)) != cudaSuccess) return e;
-    if ((e = make_map(&p.mw, Om, n, np, ldom, kKC16, np, true)) != cudaSuccess) return e;
+    if (gen) {
+        if (gen->p < 1 || gen->p > np) return cudaErrorInvalidValue;
+        p.om_n = n;
+        p.om_col0 = gen->col0;
+        p.om_p = gen->p;
+        p.om_seed = gen->seed;
+        p.mw = p.mx;   // not read
+    } else if ((e = make_map(&p.mw, Om, n, np, ldom, kKC16, np, true)) != cudaSuccess) {
+        return e;
+    }
     p.mwl = p.mw;
     const Plan pl = plan((m + kBM - 1) / kBM, (n + kKC16 - 1) / kKC16, cx.num_sms);
     if ((size_t)pl.P * pl.G * kBM * np > part_cap) return cudaErrorInvalidValue;
     p.part = part;
     p.st = cx.st;
     p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
-    if ((e = launch_streamk16<kSketch>(cx, p, np)) != cudaSuccess) return e;
+    e = gen ? launch_streamk16<kSketch, true>(cx, p, np) : launch_streamk16<kSketch>(cx, p, np);
+    if (e != cudaSuccess) return e;
     const dim3 rgrid(pl.tiles, reduce_slices(pl.tiles, cx.num_sms));
     k_reduce_sketch<<<rgrid, 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, m, Y,
                                                                            ldy, nullptr);

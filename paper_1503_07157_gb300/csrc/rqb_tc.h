@@ -131,10 +131,21 @@ cudaError_t split_q16(Ctx& cx, const float* Qi, long long ldq, long long m, int 
 cudaError_t stage_b16(Ctx& cx, const float* Bi, long long ldbi, int p, long long n, int np, __nv_bfloat16* Bs,
                       __nv_bfloat16* Bsl);
 
-// Y (m x np, FP32) = X (BF16) Omega (BF16): exact products, FP32 sums.
+// Omega_i drawn inside the BF16 sketch instead of read from a buffer: global
+// columns col0 .. col0 + p - 1 of the Gaussian matrix of seed (BF16-rounded
+// binary32 draws, the values omega16 writes).
+struct OmegaGen {
+    long long col0;
+    int p;
+    uint64_t seed;
+};
+
+// Y (m x np, FP32) = X (BF16) Omega (BF16): exact products, FP32 sums.  With
+// gen, Omega is generated per K-chunk in shared memory by the kernel (Om and
+// ldom are not read).
 cudaError_t sketch16(Ctx& cx, const __nv_bfloat16* X, long long ldx, long long m, long long n,
                      const __nv_bfloat16* Om, long long ldom, int np, float* Y, long long ldy, float* part,
-                     size_t part_cap);
+                     size_t part_cap, const OmegaGen* gen = nullptr);
 
 // B (pcols x n, FP32) = Q_i^T X with Q_i as its BF16 split, the staged split
 // copy Bs / Bsl of B, and ||B||_F^2 into *sq_out.

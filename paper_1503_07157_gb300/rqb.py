@@ -39,6 +39,7 @@ RQB_PREC_NATIVE, RQB_PREC_TF32X3, RQB_PREC_BF16 = 0, 1, 2
 RQB_MAX_TRACKED_BLOCKS = 512
 RQB_FLAG_PHASE_TIMING = 1
 RQB_FLAG_SKIP_INNER_ORTH = 2
+RQB_FLAG_OMEGA_SMEM = 4
 RQB_NUM_PHASES = 8
 PHASES = ("sketch", "orth", "project", "downdate", "control")
 

@@ -241,3 +241,42 @@ def test_randqb_bf16_vs_fp32_same_eps(orc, rqb_lib):
 def test_randqb_zero_matrix(rqb_lib):
     Q, B, k, rc, st = _factor(rqb_lib, np.zeros((1000, 700)), 0.0, 128, 0)
     assert rc == rqb_lib.RQB_OK and k == 0
+
+
+@pytest.mark.parametrize("m,n,p,col0", [(3000, 2000, 256, 128), (1037, 777, 37, 5), (129, 300, 64, 3)])
+def test_omega_in_shared_memory_is_bitwise_the_buffered_sketch(orc, rqb_lib, m, n, p, col0):
+    """RQB_FLAG_OMEGA_SMEM: Omega_i drawn by the sketch kernel into its
+    shared-memory operand gives the same sketch as Omega_i from its buffer,
+    bit for bit (same draws, same BF16 rounding, same MMA order), and so the
+    same oracle parity (odd col0 exercises the unpaired Philox columns)."""
+    rng = np.random.default_rng(m + n + p)
+    A = _bf(orc, rng.standard_normal((m, n)))
+    Ad = to_dev(A, torch.bfloat16)
+    with rqb_lib.Handle(torch.bfloat16) as h0, rqb_lib.Handle(torch.bfloat16, flags=rqb_lib.RQB_FLAG_OMEGA_SMEM) as h1:
+        Y0, n0 = h0.rqb_sketch(Ad, col0, p, seed=23)
+        Y1, n1 = h1.rqb_sketch(Ad, col0, p, seed=23)
+        Y0, Y1 = to_np(Y0), to_np(Y1)
+        Om = to_np(h0.rqb_omega(n, col0, p, seed=23))
+    assert np.array_equal(Y0, Y1) and n0 == n1
+    # against the oracle entry by entry, with the few entries where the two
+    # binary32 draws round to neighbouring BF16 values
+    Yo = orc.sketch(A, 23, col0, p, omega_prec=8)
+    Oo = orc.omega(23, n, col0, p, prec=8)
+    assert_elementwise(Y1, Yo, product_bound(A, Oo), 1e-6, "BF16 sketch, Omega in shared memory",
+                       extra=np.abs(A) @ np.abs(Om - Oo))
+
+
+def test_omega_in_shared_memory_factorization_bitwise(orc, rqb_lib):
+    m, n, b = 2049, 1300, 128
+    A = _bf(orc, inputs.usv(m, n, inputs.spectrum_exp(min(m, n), 150), seed=31))
+    eps = 1e-2 * np.linalg.norm(A)
+    Q0, B0, k0, rc0, _ = _factor(rqb_lib, A, eps, b, 3)
+    Q1, B1, k1, rc1, _ = _factor(rqb_lib, A, eps, b, 3, flags=rqb_lib.RQB_FLAG_OMEGA_SMEM)
+    assert rc0 == rc1 == rqb_lib.RQB_OK and k0 == k1
+    assert np.array_equal(Q0, Q1) and np.array_equal(B0, B1)
+
+
+def test_omega_in_shared_memory_needs_bf16(rqb_lib):
+    with pytest.raises(rqb_lib.RqbError) as ei:
+        rqb_lib.Handle(torch.float32, flags=rqb_lib.RQB_FLAG_OMEGA_SMEM)
+    assert ei.value.status == rqb_lib.RQB_ERR_UNSUPPORTED

@@ -346,6 +346,20 @@ int rqb_sketch_noalloc(int32_t dtype, const void* A, int64_t m, int64_t n, int64
                        int64_t col0, int64_t ncols, uint64_t seed, void* Y, int64_t ldy,
                        double* normA2, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Self-test of the FP64 reciprocal and reciprocal square root of the
+ * Cholesky pivots.  The paper has no counterpart: the library's Cholesky
+ * tiles take 1/d and 1/sqrt(d) of their FP64 pivots as an FP32 estimate
+ * refined by two Newton steps (published iteration, not CUDA's division or
+ * square root), and this entry point applies those same device functions to
+ * an array so that a test can hold them to their error bounds.
+ *   x       device, count FP64 values > 0
+ *   rcp     device, count outputs: 1 / x
+ *   rsq     device, count outputs: 1 / sqrt(x)
+ *   stream  cudaStream_t (NULL: legacy default stream); asynchronous
+ * Errors: RQB_ERR_INVALID (null pointer, count < 1), RQB_ERR_CUDA. */
+int rqb_fp64_recip_selftest(const double* x, int64_t count, double* rcp, double* rsq, void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* rqb_status_string(int status);
 

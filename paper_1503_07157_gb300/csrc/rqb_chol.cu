@@ -80,6 +80,16 @@ __device__ __forceinline__ double rcp_fp64(double d) {
     return y;
 }
 
+// rcp_fp64 and rsqrt_fp64 over an array, for the test that holds them to
+// their error bounds (entry point rqb_fp64_recip_selftest).
+__global__ void k_recip_selftest(const double* __restrict__ x, int64_t count, double* __restrict__ rcp,
+                                 double* __restrict__ rsq) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        rcp[i] = rcp_fp64(x[i]);
+        rsq[i] = rsqrt_fp64(x[i]);
+    }
+}
+
 template <typename W>
 __global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G, double* __restrict__ L,
                                                     double* __restrict__ Linv, float* __restrict__ Lf,
@@ -521,3 +531,10 @@ template cudaError_t chol_inv_blocked<double>(Ctx&, double*, int, int, double*, 
                                               bool);
 
 }  // namespace rqb
+
+extern "C" int rqb_fp64_recip_selftest(const double* x, int64_t count, double* rcp, double* rsq, void* stream) {
+    if (!x || !rcp || !rsq || count < 1) return RQB_ERR_INVALID;
+    const int blocks = (int)std::min<int64_t>((count + 255) / 256, 1024);
+    rqb::k_recip_selftest<<<blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x, count, rcp, rsq);
+    return cudaGetLastError() == cudaSuccess ? RQB_OK : RQB_ERR_CUDA;
+}

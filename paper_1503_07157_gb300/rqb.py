@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
             "rqb_backward": [P, P, i64, P, i64],
             "rqb_svd": [P, i64, P, i64, Pd, P, i64],
             "rqb_wait_selftest": [P, Pd],
+            "rqb_fp64_recip_selftest": [P, i64, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -377,6 +378,18 @@ def rqb_sketch_noalloc(A: torch.Tensor, col0: int, ncols: int, seed: int, Y: tor
                                   seed, ctypes.c_void_p(Y.data_ptr()), _ld(Y),
                                   ctypes.byref(nrm) if want_norm else None, ctypes.c_void_p(s.cuda_stream))
     return rc, (float(nrm.value) if want_norm else None)
+
+
+def rqb_fp64_recip_selftest(x: torch.Tensor):
+    """(1/x, 1/sqrt(x)) of a CUDA FP64 vector through the library's Newton
+    reciprocal and reciprocal square root (the Cholesky pivots' helpers)."""
+    x = x.contiguous()
+    rcp, rsq = torch.empty_like(x), torch.empty_like(x)
+    _check(lib().rqb_fp64_recip_selftest(ctypes.c_void_p(x.data_ptr()), x.numel(), ctypes.c_void_p(rcp.data_ptr()),
+                                         ctypes.c_void_p(rsq.data_ptr()),
+                                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
+           "rqb_fp64_recip_selftest")
+    return rcp, rsq
 
 
 class QQtA(torch.autograd.Function):

@@ -311,6 +311,22 @@ int read_state(rqb_handle h, const Scal& sc) {
     return h->hstate->err;
 }
 
+// Line (6) without line (5) for the tensor-core handles, whose stop test is
+// the direct norm of the stored residual (Sec. 3 c11, c12).  With X the
+// stored residual before block i (direct norm dprev) and B_i = Q_i^T X
+// (norm nb), Pythagoras (Prop. 4.1) gives ||X - Q_i B_i||^2 = dprev - nb for
+// an orthonormal Q_i.  The bound below adds 1e-4 dprev for Q_i's
+// orthogonality and the computed B_i and nb (each ~1e-5 or less on these
+// handles), 2e-5 ||B_i|| for the products of the update, and the rounding of
+// the stored residual (rho = 2^-8 for BF16 storage, 2^-23 for FP32).  When it
+// is below eps^2 the stored residual the update would produce passes the
+// test, so the last block needs no update.
+bool stops_without_update(double dprev, double nb, double eps2, double rho) {
+    const double core = std::sqrt(std::max(dprev * (1.0 + 1e-4) - nb, 0.0)) + 2e-5 * std::sqrt(std::max(nb, 0.0));
+    const double upper = (1.0 + rho) * (1.0 + rho) * core * core;
+    return std::isfinite(upper) && upper <= eps2;
+}
+
 // Lines (3) and (3'): Qout (p columns, ld ldqo) from the panel Y (bp columns,
 // ld ldy; columns >= p are zero) and Qbar (kprev columns, ld ldqb).
 template <typename T>
@@ -518,6 +534,7 @@ int factor_tc(rqb_handle h, const float* A, int64_t m, int64_t n, int64_t lda, d
     int status = RQB_OK;
     bool converged = false;
     bool empty_exit = false;
+    double dprev = 0.0;    // direct norm of the stored residual before the current block
 
     // A as the first W: read in place when TMA can address it, else copied
     const float* Wsrc = A;
@@ -568,9 +585,15 @@ int factor_tc(rqb_handle h, const float* A, int64_t m, int64_t n, int64_t lda, d
             h->stats.E[blocks] = h->hstate->E;
             h->stats.D[blocks] = -1.0;
         }
+        if (blocks == 0) dprev = h->hstate->normA2;
         k += p;
         blocks++;
         if (flag == kStop) { converged = true; break; }
+        if (!fixed && stops_without_update(dprev, h->hstate->normB2, eps2, 0x1p-23)) {
+            if (blocks - 1 < RQB_MAX_TRACKED_BLOCKS) h->stats.D[blocks - 1] = std::max(dprev - h->hstate->normB2, 0.0);
+            converged = true;
+            break;
+        }
         if (flag == kContinue && k >= kcap) break;
         const int pn = (int)std::min<int64_t>(b, std::max<int64_t>(kcap - k, 0));
         // line (5) with ||A^(i)||_F^2 on the same pass; the split-TF32 products
@@ -586,6 +609,7 @@ int factor_tc(rqb_handle h, const float* A, int64_t m, int64_t n, int64_t lda, d
         if (err != RQB_OK) { status = err; break; }
         if (flag == kAmbiguous) direct++;
         if (blocks - 1 < RQB_MAX_TRACKED_BLOCKS) h->stats.D[blocks - 1] = h->hstate->D;
+        dprev = h->hstate->D;
         if (!fixed && h->hstate->flag == kStop) { converged = true; break; }
         if (k >= kcap) break;
         h->timer.begin(h->stream, RQB_PHASE_SKETCH);
@@ -658,15 +682,20 @@ bool tma_ok16(const void* p, int64_t ld) { return (reinterpret_cast<uintptr_t>(p
 // Lines (2), (3) on the BF16 path: Omega_i (global columns col0 ..) into its
 // buffer and Y = X Omega_i, or with RQB_FLAG_OMEGA_SMEM Omega_i drawn inside
 // the sketch kernel (the same values).
+// With nrm_out, ||X||_F^2 out of the same pass over X (nrm_part: kNrmCap
+// FP64 partials).
 int sketch_block16(rqb_handle h, Ctx& cx, const TcArena16& ta, const __nv_bfloat16* X, int64_t ldx, int64_t m,
-                   int64_t n, int64_t col0, int p, int bp, uint64_t seed, float* Y) {
+                   int64_t n, int64_t col0, int p, int bp, uint64_t seed, float* Y, double* nrm_part = nullptr,
+                   double* nrm_out = nullptr) {
     if (h->cfg.flags & RQB_FLAG_OMEGA_SMEM) {
         const tc::OmegaGen gen{col0, p, seed};
-        RQB_CK(tc::sketch16(cx, X, ldx, m, n, nullptr, 0, bp, Y, m, ta.part, ta.part_cap, &gen));
+        RQB_CK(tc::sketch16(cx, X, ldx, m, n, nullptr, 0, bp, Y, m, ta.part, ta.part_cap, &gen, nrm_part, kNrmCap,
+                            nrm_out));
         return RQB_OK;
     }
     RQB_CK(tc::omega16(cx, n, col0, p, bp, seed, ta.Om, ta.ldom));
-    RQB_CK(tc::sketch16(cx, X, ldx, m, n, ta.Om, ta.ldom, bp, Y, m, ta.part, ta.part_cap));
+    RQB_CK(tc::sketch16(cx, X, ldx, m, n, ta.Om, ta.ldom, bp, Y, m, ta.part, ta.part_cap, nullptr, nrm_part, kNrmCap,
+                        nrm_out));
     return RQB_OK;
 }
 
@@ -709,6 +738,7 @@ int factor_bf16(rqb_handle h, const __nv_bfloat16* A, int64_t m, int64_t n, int6
     int blocks = 0;
     int status = RQB_OK;
     bool converged = false;
+    double dprev = 0.0;    // direct norm of the stored residual before the current block
 
     const __nv_bfloat16* Wsrc = A;
     int64_t ldws = lda;
@@ -719,9 +749,10 @@ int factor_bf16(rqb_handle h, const __nv_bfloat16* A, int64_t m, int64_t n, int6
         ldws = ldw;
     }
     int p = (int)std::min<int64_t>(b, kcap);
-    RQB_CK(launch_sumsq<__nv_bfloat16>(cx, m, n, Wsrc, ldws, sc.nrm, kNrmCap, sc.s + 0));
+    // ||A||_F^2 comes out of the first sketch's own reads of A (no pass of its own)
+    if ((rc = sketch_block16(h, cx, ta, Wsrc, ldws, m, n, 0, p, bp, seed, ar.Y, sc.nrm, sc.s + 0)) != RQB_OK)
+        return rc;
     RQB_CK(launch_set_norm(cx, sc.s + 0));
-    if ((rc = sketch_block16(h, cx, ta, Wsrc, ldws, m, n, 0, p, bp, seed, ar.Y)) != RQB_OK) return rc;
     h->timer.end(h->stream);
 
     for (;;) {
@@ -739,6 +770,23 @@ int factor_bf16(rqb_handle h, const __nv_bfloat16* A, int64_t m, int64_t n, int6
         // E_i bookkeeping only (reported in the statistics)
         RQB_CK(launch_stop_after_b(cx, sc.s + 1, eps2, 0.0, 1));
         h->timer.end(h->stream);
+        if (!fixed) {
+            // line (6) decided before line (5) when the bound on the stored
+            // residual the update would leave is already below eps^2
+            const int err0 = read_state(h, sc);
+            if (blocks == 0) dprev = h->hstate->normA2;
+            if (!(blocks == 0 && h->hstate->normA2 <= eps2) && err0 == RQB_OK &&
+                stops_without_update(dprev, h->hstate->normB2, eps2, 0x1p-8)) {
+                if (blocks < RQB_MAX_TRACKED_BLOCKS) {
+                    h->stats.E[blocks] = h->hstate->E;
+                    h->stats.D[blocks] = std::max(dprev - h->hstate->normB2, 0.0);
+                }
+                k += p;
+                blocks++;
+                converged = true;
+                break;
+            }
+        }
         h->timer.begin(h->stream, RQB_PHASE_DOWNDATE);
         RQB_CK(tc::update16(cx, Wsrc, ldws, W, ldw, m, n, ta.Qt, ta.Qtl, ta.Bs, ta.Bsl, bp, sc.nrm, kNrmCap,
                             sc.s + 2));
@@ -760,6 +808,7 @@ int factor_bf16(rqb_handle h, const __nv_bfloat16* A, int64_t m, int64_t n, int6
             h->stats.E[blocks] = h->hstate->E;
             h->stats.D[blocks] = h->hstate->D;
         }
+        dprev = h->hstate->D;
         k += p;
         blocks++;
         if (!fixed && h->hstate->flag == kStop) { converged = true; break; }
@@ -1352,8 +1401,9 @@ int sketch_bf16(rqb_handle h, const __nv_bfloat16* A, int64_t m, int64_t n, int6
     const __nv_bfloat16* X;
     int64_t ldx;
     if ((rc = tma_source16(h, A, lda, m, n, &X, &ldx)) != RQB_OK) return rc;
-    if (normA2) RQB_CK(launch_sumsq<__nv_bfloat16>(cx, m, n, X, ldx, sc.nrm, kNrmCap, sc.s + 0));
-    if ((rc = sketch_block16(h, cx, ta, X, ldx, m, n, col0, p, bp, seed, ar.Y)) != RQB_OK) return rc;
+    if ((rc = sketch_block16(h, cx, ta, X, ldx, m, n, col0, p, bp, seed, ar.Y, sc.nrm,
+                             normA2 ? sc.s + 0 : nullptr)) != RQB_OK)
+        return rc;
     RQB_CK(cudaMemcpy2DAsync(Y, sizeof(float) * ldy, ar.Y, sizeof(float) * m, sizeof(float) * m, p,
                              cudaMemcpyDeviceToDevice, h->stream));
     if (normA2) RQB_CK(cudaMemcpyAsync(normA2, sc.s + 0, sizeof(double), cudaMemcpyDeviceToHost, h->stream));

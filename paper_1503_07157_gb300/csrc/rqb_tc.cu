@@ -391,6 +391,10 @@ __global__ void __launch_bounds__(320, 1) k_streamk16(const __grid_constant__ St
     __shared__ __align__(8) uint64_t full[S], empty[S], omfull[S], accfull[2], accempty[2], drain;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
+    __shared__ double nred16[8];
+    // sketch with nrm_part: the epilogue warps also square every W tile, so a
+    // stage is free once the MMAs and those eight warps are done with it
+    const bool nrm = (ROLE == kSketch) && (p.nrm_part != nullptr);
     extern __shared__ uint8_t dsm[];
     uint8_t* base = dsm + (((smem_u32(dsm) + 1023u) & ~1023u) - smem_u32(dsm));
     constexpr uint32_t ncols = 2u * (uint32_t)NP;
@@ -399,7 +403,7 @@ __global__ void __launch_bounds__(320, 1) k_streamk16(const __grid_constant__ St
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], nrm ? 9 : 1);
             if (GEN) mbar_init(&omfull[s], 8);
         }
         for (int s = 0; s < 2; ++s) { mbar_init(&accfull[s], 1); mbar_init(&accempty[s], 8); }
@@ -497,9 +501,39 @@ __global__ void __launch_bounds__(320, 1) k_streamk16(const __grid_constant__ St
         float acc[kHalf];
 #pragma unroll
         for (int i = 0; i < kHalf; ++i) acc[i] = 0.f;
+        double sq = 0.0;     // ||W||_F^2 of the tile parts this thread squares (nrm)
         int g = 0;
         long long q = 0;
         for (long long u = u0; u < u1; ++u, ++q) {
+            if (nrm) {
+                // the stream-K units partition W and the TMA boxes zero-fill
+                // past its edges: every entry is squared once.  A BF16 square
+                // is exact in FP32; the 32 of a thread are summed with TwoSum
+                // in FP32 pairs, then added in FP64
+                const int s = (int)(q % S);
+                const uint32_t r = (uint32_t)(q / S);
+                const bool okn = mbar_wait(&full[s], r & 1u, ab);
+                if (!__all_sync(0xffffffffu, okn)) break;
+                const uint4* tile = reinterpret_cast<const uint4*>(base + s * kStage);
+                float hi = 0.f, lo = 0.f;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint4 w4 = tile[((int)threadIdx.x - 64) + 256 * i];
+                    const uint32_t w[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float v = __uint_as_float((j & 1) ? (w[j >> 1] & 0xffff0000u) : (w[j >> 1] << 16));
+                        const float p2 = __fmul_rn(v, v);
+                        const float t = __fadd_rn(hi, p2);
+                        const float z = __fsub_rn(t, hi);
+                        lo += __fadd_rn(__fsub_rn(hi, __fsub_rn(t, z)), __fsub_rn(p2, z));
+                        hi = t;
+                    }
+                }
+                sq += (double)hi + (double)lo;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+            }
             if constexpr (GEN) {
                 const int s = (int)(q % S);
                 const uint32_t r = (uint32_t)(q / S);
@@ -543,12 +577,23 @@ __global__ void __launch_bounds__(320, 1) k_streamk16(const __grid_constant__ St
                 for (int i = 0; i < kHalf; ++i) acc[i] = 0.f;
             }
         }
+        if (nrm) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            if (lane == 0) nred16[e] = sq;
+        }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 1) tmem_dealloc(tmem, ncols);
     if (threadIdx.x == 0 && abort_flag) record_error(p.st, RQB_ERR_TIMEOUT);
+    if (nrm && threadIdx.x == 64) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += nred16[w];
+        p.nrm_part[blockIdx.x] = t;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -2150,7 +2195,7 @@ cudaError_t stage_b16(Ctx& cx, const float* Bi, long long ldbi, int p, long long
 
 cudaError_t sketch16(Ctx& cx, const __nv_bfloat16* X, long long ldx, long long m, long long n,
                      const __nv_bfloat16* Om, long long ldom, int np, float* Y, long long ldy, float* part,
-                     size_t part_cap, const OmegaGen* gen) {
+                     size_t part_cap, const OmegaGen* gen, double* nrm_part, int nrm_cap, double* nrm_out) {
     StreamKParams p;
     cudaError_t e;
     if ((e = make_map(&p.mx, X, m, n, ldx, 64, kKC16, true)) != cudaSuccess) return e;
@@ -2167,16 +2212,19 @@ cudaError_t sketch16(Ctx& cx, const __nv_bfloat16* X, long long ldx, long long m
     p.mwl = p.mw;
     const Plan pl = plan((m + kBM - 1) / kBM, (n + kKC16 - 1) / kKC16, cx.num_sms);
     if ((size_t)pl.P * pl.G * kBM * np > part_cap) return cudaErrorInvalidValue;
+    if (nrm_out && pl.P > nrm_cap) return cudaErrorInvalidValue;
     p.part = part;
     p.st = cx.st;
     p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
+    p.nrm_part = nrm_out ? nrm_part : nullptr;
     e = gen ? launch_streamk16<kSketch, true>(cx, p, np) : launch_streamk16<kSketch>(cx, p, np);
     if (e != cudaSuccess) return e;
     const dim3 rgrid(pl.tiles, reduce_slices(pl.tiles, cx.num_sms));
     k_reduce_sketch<<<rgrid, 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, m, Y,
                                                                            ldy, nullptr);
     cx.launches++;
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return nrm_out ? launch_sum_doubles(cx, nrm_part, pl.P, nrm_out) : cudaSuccess;
 }
 
 cudaError_t project16(Ctx& cx, const __nv_bfloat16* X, long long ldx, long long m, long long n,

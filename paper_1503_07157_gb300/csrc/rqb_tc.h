@@ -142,10 +142,13 @@ struct OmegaGen {
 
 // Y (m x np, FP32) = X (BF16) Omega (BF16): exact products, FP32 sums.  With
 // gen, Omega is generated per K-chunk in shared memory by the kernel (Om and
-// ldom are not read).
+// ldom are not read).  With nrm_out, ||X||_F^2 too (FP64; the epilogue warps
+// square the W tiles in shared memory; one partial per CTA in nrm_part, at
+// most nrm_cap), so that the first block needs no separate pass over A.
 cudaError_t sketch16(Ctx& cx, const __nv_bfloat16* X, long long ldx, long long m, long long n,
                      const __nv_bfloat16* Om, long long ldom, int np, float* Y, long long ldy, float* part,
-                     size_t part_cap, const OmegaGen* gen = nullptr);
+                     size_t part_cap, const OmegaGen* gen = nullptr, double* nrm_part = nullptr, int nrm_cap = 0,
+                     double* nrm_out = nullptr);
 
 // B (pcols x n, FP32) = Q_i^T X with Q_i as its BF16 split, the staged split
 // copy Bs / Bsl of B, and ||B||_F^2 into *sq_out.

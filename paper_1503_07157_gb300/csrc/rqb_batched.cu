@@ -376,11 +376,11 @@ __global__ void __launch_bounds__(NTU) k_rows_update(const GMat* __restrict__ ma
             wr[u] = load_rows4(Wsrc + r + cc * ldws, m - r, cc < n, vsrc);
         }
     };
-    float yacc[8][4];
+    float2 yacc[4][4];   // (rows 2i, 2i + 1) x column j, for the packed FMAs
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) yacc[i][j] = 0.f;
+        for (int j = 0; j < 4; ++j) yacc[i][j] = make_float2(0.f, 0.f);
     double sq = 0.0;
     load(0);
     for (int64_t c0 = 0; c0 < n; c0 += KCH) {
@@ -399,11 +399,11 @@ __global__ void __launch_bounds__(NTU) k_rows_update(const GMat* __restrict__ ma
         __syncthreads();
         if (c0 + KCH < n) load(c0 + KCH);
         // P = Q_i(tile) B_i(:, chunk)
-        float pacc[8][4];
+        float2 pacc2[4][4];   // (rows 2i, 2i + 1) x column j
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) pacc[i][j] = 0.f;
+            for (int j = 0; j < 4; ++j) pacc2[i][j] = make_float2(0.f, 0.f);
 #pragma unroll 8
         for (int t = 0; t < BP; ++t) {
             const float4 a0 = *reinterpret_cast<const float4*>(&Qs[t][ty * 8]);
@@ -411,11 +411,16 @@ __global__ void __launch_bounds__(NTU) k_rows_update(const GMat* __restrict__ ma
             const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const float4 b4 = *reinterpret_cast<const float4*>(&Bs[t][tx * 4]);
             const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) pacc[i][j] = fmaf(av[i], bv[j], pacc[i][j]);
+            fma_tile_f32x2_rows<8, 4>(pacc2, av, bv);
         }
+        float pacc[8][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                pacc[2 * i][j] = pacc2[i][j].x;
+                pacc[2 * i + 1][j] = pacc2[i][j].y;
+            }
         // W = Wsrc - P on this thread's entries: shared copy, global store, ||W||^2
         float sqf = 0.f;
 #pragma unroll
@@ -456,10 +461,7 @@ __global__ void __launch_bounds__(NTU) k_rows_update(const GMat* __restrict__ ma
             const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const float4 o4 = *reinterpret_cast<const float4*>(&Os[c][tx * 4]);
             const float ov[4] = {o4.x, o4.y, o4.z, o4.w};
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) yacc[i][j] = fmaf(av[i], ov[j], yacc[i][j]);
+            fma_tile_f32x2_rows<8, 4>(yacc, av, ov);
         }
     }
 #pragma unroll
@@ -469,7 +471,8 @@ __global__ void __launch_bounds__(NTU) k_rows_update(const GMat* __restrict__ ma
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int c = tx + 8 * j;
-            d.Y[r + (int64_t)c * d.ldw] = (c < pn) ? yacc[i][j] : 0.f;
+            const float y = (i & 1) ? yacc[i >> 1][j].y : yacc[i >> 1][j].x;
+            d.Y[r + (int64_t)c * d.ldw] = (c < pn) ? y : 0.f;
         }
     }
 #pragma unroll
@@ -529,11 +532,13 @@ __global__ void __launch_bounds__(NT) k_cols(const GMat* __restrict__ mats, cons
     const int64_t m = d.m;
     const int tid = threadIdx.x, jg = tid / NCT, ct = tid % NCT;
     float acc[JT][4];
+    float2 accp[JT][2];   // acc as column pairs, for the packed FMAs
     double acc2[OP == kColReproj ? JT : 1][4];
 #pragma unroll
     for (int i = 0; i < JT; ++i)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[i][q] = 0.f;
+    zero_tile_f32x2<JT, 4>(accp);
     if (OP == kColReproj) {
 #pragma unroll
         for (int i = 0; i < (OP == kColReproj ? JT : 1); ++i)
@@ -583,13 +588,12 @@ __global__ void __launch_bounds__(NT) k_cols(const GMat* __restrict__ mats, cons
             }
             const float4 v4 = *reinterpret_cast<const float4*>(&Vs[rr][vs_col(rr, 4 * ct)]);
             const float v[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-            for (int i = 0; i < JT; ++i)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[i][q] = fmaf(a[i], v[q], acc[i][q]);
+            fma_tile_f32x2<JT, 4>(accp, a, v);
         }
         if (OP == kColReproj && (++chunk == 4 || r0 + KCH >= m)) {
             chunk = 0;
+            unpack_tile_f32x2<JT, 4>(accp, acc);
+            zero_tile_f32x2<JT, 4>(accp);
 #pragma unroll
             for (int i = 0; i < (OP == kColReproj ? JT : 1); ++i)
 #pragma unroll
@@ -599,6 +603,7 @@ __global__ void __launch_bounds__(NT) k_cols(const GMat* __restrict__ mats, cons
                 }
         }
     }
+    if (OP == kColProject) unpack_tile_f32x2<JT, 4>(accp, acc);
     double sq = 0.0;
 #pragma unroll
     for (int i = 0; i < JT; ++i) {

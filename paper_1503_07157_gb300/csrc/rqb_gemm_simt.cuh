@@ -24,6 +24,55 @@ template <typename T> struct SimtTile;
 template <> struct SimtTile<float> { static constexpr int TM = 8, TN = 8; };
 template <> struct SimtTile<double> { static constexpr int TM = 4, TN = 4; };
 
+// Packed FP32 multiply-adds (two per instruction on this part's FP32 pipe):
+// acc2[i][jp] += (a[i] a[i]) * (b[2jp] b[2jp+1]), each lane an IEEE
+// binary32 fused multiply-add rounded to nearest, so the results are bit for
+// bit those of fmaf in the same order.  Half the FMA instructions leave issue
+// slots to the loads of the issue-bound SIMT products.
+template <int TM, int TN>
+__device__ __forceinline__ void fma_tile_f32x2(float2 (&acc2)[TM][TN / 2], const float (&a)[TM],
+                                               const float (&b)[TN]) {
+    float2 bp[TN / 2];
+#pragma unroll
+    for (int j = 0; j < TN / 2; ++j) bp[j] = make_float2(b[2 * j], b[2 * j + 1]);
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const float2 aa = make_float2(a[i], a[i]);
+#pragma unroll
+        for (int j = 0; j < TN / 2; ++j) acc2[i][j] = __ffma2_rn(aa, bp[j], acc2[i][j]);
+    }
+}
+// The same with the pairs along rows: accr[ip][j] += (a[2ip] a[2ip+1]) *
+// (b[j] b[j]).
+template <int TM, int TN>
+__device__ __forceinline__ void fma_tile_f32x2_rows(float2 (&accr)[TM / 2][TN], const float (&a)[TM],
+                                                    const float (&b)[TN]) {
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+        const float2 bb = make_float2(b[j], b[j]);
+#pragma unroll
+        for (int i = 0; i < TM / 2; ++i) accr[i][j] = __ffma2_rn(make_float2(a[2 * i], a[2 * i + 1]), bb, accr[i][j]);
+    }
+}
+
+template <int TM, int TN>
+__device__ __forceinline__ void zero_tile_f32x2(float2 (&acc2)[TM][TN / 2]) {
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN / 2; ++j) acc2[i][j] = make_float2(0.f, 0.f);
+}
+template <int TM, int TN, typename T>
+__device__ __forceinline__ void unpack_tile_f32x2(const float2 (&acc2)[TM][TN / 2], T (&acc)[TM][TN]) {
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN / 2; ++j) {
+            acc[i][2 * j] = (T)acc2[i][j].x;
+            acc[i][2 * j + 1] = (T)acc2[i][j].y;
+        }
+}
+
 template <typename T, int H> struct VecH;   // H contiguous elements
 template <> struct VecH<float, 4> { using type = float4; };
 template <> struct VecH<float, 2> { using type = float2; };
@@ -99,6 +148,12 @@ k_gemm_nn(int64_t m, int64_t K, int64_t ksplit, int nc, int nout,
     for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+    // FP32 tiles of up to 128 x 64: acc as column pairs for the packed FMAs
+    // (the larger tiles keep scalar FMAs: their pairs would not fit the
+    // registers of two CTAs per SM)
+    constexpr bool kPackNN = (sizeof(T) == 4) && (BN <= 64);
+    float2 accq[TM][TN / 2];
+    if constexpr (kPackNN) zero_tile_f32x2<TM, TN>(accq);
 
     T xa[G::XPER][V];
     T cb[G::CPER][V];
@@ -217,10 +272,14 @@ k_gemm_nn(int64_t m, int64_t K, int64_t ksplit, int nc, int nout,
             for (int i = 0; i < HM; ++i) { a[i] = a0[i]; a[HM + i] = a1[i]; }
 #pragma unroll
             for (int j = 0; j < HN; ++j) { b[j] = b0[j]; b[HN + j] = b1[j]; }
+            if constexpr (kPackNN) {
+                fma_tile_f32x2<TM, TN>(accq, a, b);
+            } else {
 #pragma unroll
-            for (int i = 0; i < TM; ++i)
+                for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                    for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
         }
         if (more) {
             store_x(buf ^ 1);
@@ -229,6 +288,7 @@ k_gemm_nn(int64_t m, int64_t K, int64_t ksplit, int nc, int nout,
         __syncthreads();
         buf ^= 1;
     }
+    if constexpr (kPackNN) unpack_tile_f32x2<TM, TN>(accq, acc);
 
     if (nrm_part != nullptr) {   // uniform per CTA
         __shared__ double red[NT / 32];
@@ -306,6 +366,11 @@ k_gemm_nn_pipe(int64_t m, int64_t K, int64_t ksplit, int nc, int nout,
     for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+    // FP32 tiles of 128 rows: the accumulators as pairs for the packed FMAs
+    // (the 64 x 256 tile keeps scalar FMAs, its pairs would spill)
+    constexpr bool kPackP = (sizeof(T) == 4) && (BM == 128);
+    float2 acc2[TM][TN / 2];
+    if constexpr (kPackP) zero_tile_f32x2<TM, TN>(acc2);
     const bool do_norm = (nrm_part != nullptr) && (blockIdx.y == 0);
     double nacc = 0.0;
 
@@ -379,13 +444,18 @@ k_gemm_nn_pipe(int64_t m, int64_t K, int64_t ksplit, int nc, int nout,
             for (int i = 0; i < HM; ++i) { a[i] = a0[i]; a[HM + i] = a1[i]; }
 #pragma unroll
             for (int j = 0; j < HN; ++j) { b[j] = b0[j]; b[HN + j] = b1[j]; }
+            if constexpr (kPackP) {
+                fma_tile_f32x2<TM, TN>(acc2, a, b);
+            } else {
 #pragma unroll
-            for (int i = 0; i < TM; ++i)
+                for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                    for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
         }
     }
     cp_async_wait<0>();
+    if constexpr (kPackP) unpack_tile_f32x2<TM, TN>(acc2, acc);
 
     if (nrm_part != nullptr) {   // uniform per CTA
         __shared__ double red[NT / 32];
@@ -470,6 +540,15 @@ k_gemm_tn(int64_t m, int pn, int64_t qn, int64_t rsplit,
     for (int i = 0; i < TP; ++i)
 #pragma unroll
         for (int j = 0; j < TQ; ++j) { acc[i][j] = T(0); lo[i][j] = T(0); acc2[i][j] = Acc(0); }
+    // FP32 without COMP: the running sums as pairs for the packed FMAs
+    constexpr bool kPacked = (sizeof(T) == 4) && !COMP && (TP % 2 == 0);
+    float2 accp[(TP + 1) / 2][TQ];
+    if constexpr (kPacked) {
+#pragma unroll
+        for (int i = 0; i < (TP + 1) / 2; ++i)
+#pragma unroll
+            for (int j = 0; j < TQ; ++j) accp[i][j] = make_float2(0.f, 0.f);
+    }
 
     T xa[XPER][V], ya[YPER][V];
     // vector v: column cc = v / (BK/V), rows kk..kk+V
@@ -551,6 +630,8 @@ k_gemm_tn(int64_t m, int pn, int64_t qn, int64_t rsplit,
                 for (int i = 0; i < TP; ++i)
 #pragma unroll
                     for (int j = 0; j < TQ; ++j) exact_fma_acc(a[i], b[j], acc[i][j], lo[i][j]);
+            } else if constexpr (kPacked) {
+                fma_tile_f32x2_rows<TP, TQ>(accp, a, b);
             } else {
 #pragma unroll
                 for (int i = 0; i < TP; ++i)
@@ -560,6 +641,16 @@ k_gemm_tn(int64_t m, int pn, int64_t qn, int64_t rsplit,
         }
         if (PROMOTE > 0 && ++chunk == PROMOTE) {
             chunk = 0;
+            if constexpr (kPacked) {
+#pragma unroll
+                for (int i = 0; i < TP / 2; ++i)
+#pragma unroll
+                    for (int j = 0; j < TQ; ++j) {
+                        acc[2 * i][j] = accp[i][j].x;
+                        acc[2 * i + 1][j] = accp[i][j].y;
+                        accp[i][j] = make_float2(0.f, 0.f);
+                    }
+            }
 #pragma unroll
             for (int i = 0; i < TP; ++i)
 #pragma unroll
@@ -573,6 +664,15 @@ k_gemm_tn(int64_t m, int pn, int64_t qn, int64_t rsplit,
         if (more) store(buf ^ 1);
         __syncthreads();
         buf ^= 1;
+    }
+    if constexpr (kPacked) {
+#pragma unroll
+        for (int i = 0; i < TP / 2; ++i)
+#pragma unroll
+            for (int j = 0; j < TQ; ++j) {
+                acc[2 * i][j] = accp[i][j].x;
+                acc[2 * i + 1][j] = accp[i][j].y;
+            }
     }
 
     Acc* out = Out + (int64_t)blockIdx.z * out_zstride;

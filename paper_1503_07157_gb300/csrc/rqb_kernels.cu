@@ -478,6 +478,8 @@ k_downdate_sketch(int64_t m, int64_t n, int p, int64_t csplit,
     for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) yacc[i][j] = T(0);
+    float2 yacq[TM][TN / 2];   // FP32: yacc as column pairs, for the packed FMAs
+    if constexpr (sizeof(T) == 4) zero_tile_f32x2<TM, TN>(yacq);
     double nrm = 0.0;
 
     for (int64_t c0 = cbeg; c0 < cend; c0 += BC) {
@@ -585,12 +587,17 @@ k_downdate_sketch(int64_t m, int64_t n, int p, int64_t csplit,
             for (int i = 0; i < HM; ++i) { a[i] = a0[i]; a[HM + i] = a1[i]; }
 #pragma unroll
             for (int j = 0; j < HN; ++j) { b[j] = b0[j]; b[HN + j] = b1[j]; }
+            if constexpr (sizeof(T) == 4) {
+                fma_tile_f32x2<TM, TN>(yacq, a, b);
+            } else {
 #pragma unroll
-            for (int i = 0; i < TM; ++i)
+                for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) yacc[i][j] = fma(a[i], b[j], yacc[i][j]);
+                    for (int j = 0; j < TN; ++j) yacc[i][j] = fma(a[i], b[j], yacc[i][j]);
+            }
         }
     }
+    if constexpr (sizeof(T) == 4) unpack_tile_f32x2<TM, TN>(yacq, yacc);
 
     // Y partial of this split
     T* yout = Ypart + (int64_t)blockIdx.z * yzstride;

@@ -220,7 +220,7 @@ def alu_peak_tflops(dtype: str, num_sms: int, sm_mhz: float) -> float:
 # 32768 x 16384 launch; mixed and bf16 updates: k_updatew / k_update16w at
 # 8192 x 8192 scaled the same way; None where no capture of the current
 # kernel exists.
-NCU_TRAFFIC = {("fp32", "sketch"): 1.416e9, ("mixed", "project"): 2.385e9,
+NCU_TRAFFIC = {("fp32", "sketch"): 1.419e9, ("mixed", "project"): 2.385e9,
                ("mixed", "downdate"): 4.383e9, ("bf16", "downdate"): 1.966e9}
 
 

@@ -1125,6 +1125,22 @@ __device__ __forceinline__ float4 add4(float4 a, float4 b) {
     return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
 }
 
+// The nc partials of one float4 of a tile, summed in CTA order (FP32, round
+// to nearest), with four loads in flight.
+__device__ __forceinline__ float4 sum_partials(const float* __restrict__ part, const size_t* off, int nc, int idx) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    int q = 0;
+    for (; q + 4 <= nc; q += 4) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = *reinterpret_cast<const float4*>(part + off[q + u] + idx);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc = add4(acc, v[u]);
+    }
+    for (; q < nc; ++q) acc = add4(acc, *reinterpret_cast<const float4*>(part + off[q] + idx));
+    return acc;
+}
+
 __global__ void k_reduce_sketch(const float* __restrict__ part, long long U, int C, int P, int G, int np, long long m,
                                 float* Y, long long ldy, const float* sub) {
     __shared__ size_t off[kMaxCover];
@@ -1141,8 +1157,7 @@ __global__ void k_reduce_sketch(const float* __restrict__ part, long long U, int
         const int c = idx / kBM, rl = idx % kBM;
         const long long r = (long long)t * kBM + rl;
         if (r >= m) continue;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int q = 0; q < nc; ++q) acc = add4(acc, *reinterpret_cast<const float4*>(part + off[q] + idx));
+        float4 acc = sum_partials(part, off, nc, idx);
         float* y = Y + r + c * ldy;
         const float* sv = sub ? sub + r + c * ldy : nullptr;
         if (vec && r + 4 <= m) {
@@ -1179,8 +1194,7 @@ __global__ void k_reduce_project(const float* __restrict__ part, long long U, in
         const int jl = idx / np, c = idx % np;
         const long long j = (long long)t * kBM + jl;
         if (j >= n) continue;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int q = 0; q < nc; ++q) v = add4(v, *reinterpret_cast<const float4*>(part + off[q] + idx));
+        const float4 v = sum_partials(part, off, nc, idx);
         *reinterpret_cast<float4*>(Bs + c + j * np) = v;
         *reinterpret_cast<float4*>(Bsl + c + j * np) = make_float4(tf32_lo(v.x), tf32_lo(v.y), tf32_lo(v.z), tf32_lo(v.w));
         const float v4[4] = {v.x, v.y, v.z, v.w};
@@ -1221,7 +1235,20 @@ __global__ void k_reduce_project64(const float* __restrict__ part, long long U, 
         const long long j = (long long)t * kBM + jl;
         if (j >= n) continue;
         double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        for (int q = 0; q < nc; ++q) {
+        int q = 0;
+        for (; q + 4 <= nc; q += 4) {   // four partial loads in flight, added in CTA order
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = *reinterpret_cast<const float4*>(part + off[q + u] + idx);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a0 += (double)v[u].x;
+                a1 += (double)v[u].y;
+                a2 += (double)v[u].z;
+                a3 += (double)v[u].w;
+            }
+        }
+        for (; q < nc; ++q) {
             const float4 v = *reinterpret_cast<const float4*>(part + off[q] + idx);
             a0 += (double)v.x;
             a1 += (double)v.y;
@@ -1722,8 +1749,7 @@ __global__ void k_reduce_project16(const float* __restrict__ part, long long U, 
         const int jl = idx / np, c = idx % np;
         const long long j = (long long)t * kBM + jl;
         if (j >= n) continue;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int q = 0; q < nc; ++q) v = add4(v, *reinterpret_cast<const float4*>(part + off[q] + idx));
+        const float4 v = sum_partials(part, off, nc, idx);
         const float v4[4] = {v.x, v.y, v.z, v.w};
         __align__(8) __nv_bfloat16 hi[4], lo[4];
 #pragma unroll

@@ -59,13 +59,7 @@ def main() -> int:
             _, _, k, rc = h.rqb_factor(A, 0.0, 256, 0, check=False)
             torch.cuda.synchronize()
     elif args.case in ("batched", "batched64"):
-        import numpy as np
-        cases = inputs.batched_sizes(512, seed=0)[: (512 if args.case == "batched" else 64)]
-        mats, eps = [], []
-        for i, c in enumerate(cases):
-            s = inputs.spectrum_exp(min(c.m, c.n), c.rate)
-            mats.append(inputs.usv_torch(c.m, c.n, s, 1000 + i, device="cuda", dtype=torch.float32))
-            eps.append(1e-3 * float(np.sqrt(np.sum(s ** 2))))
+        mats, eps, _ = inputs.config_batched_torch(512 if args.case == "batched" else 64)
         torch.cuda.synchronize()
         with rqb.Handle(torch.float32) as h:
             h.rqb_factor_batched(mats, eps, 32, seed=0)

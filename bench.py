@@ -8,6 +8,8 @@ resident in HBM.  Prints one JSON line.
 Workloads (--workload):
   fp32  (default) 20000 x 16000 FP32, A = U diag(j^-1.5) V^T, b = 128,
         eps = 1e-2 ||A||_F, Omega seed 0 -- the plain FP32 configuration
+  fp32_multiblock  the fp32 matrix at eps = 7e-4 ||A||_F (k about 1500): the
+        plain FP32 path over many blocks
   fp64  2000 x 1000 FP64, s_j = 10^(-8(j-1)/999), b = 50, eps = 1e-4 ||A||_F
   mixed 32768 x 16384 FP32 on the split-TF32 tensor-core path (RQB_PREC_TF32X3),
         s_j = 10^(-4 j / 2000) for j <= 2000 then 1e-6, b = 256,
@@ -59,6 +61,8 @@ WORKLOADS = {
     "fp64": dict(name="randQB_b FP64 2000x1000 s_j=10^(-8(j-1)/999) b=50 eps=1e-4||A||_F", m=2000, n=1000, b=50,
                  eps_rel=1e-4, dtype="float64", spectrum="fp64cfg"),
 }
+WORKLOADS["fp32_multiblock"] = dict(name="randQB_b FP32 20000x16000 s_j=j^-1.5 b=128 eps=7e-4||A||_F (multi-block)",
+                                    m=20000, n=16000, b=128, eps_rel=7e-4, dtype="float32", spectrum="poly1.5")
 WORKLOADS["mixed"] = dict(name="randQB_b split-TF32 32768x16384 s_j=10^(-4j/2000) (j<=2000) then 1e-6 b=256 "
                                "eps=1e-3||A||_F", m=32768, n=16384, b=256, eps_rel=1e-3, dtype="float32",
                           spectrum="mixed", prec="tf32x3")
@@ -794,7 +798,19 @@ def run_forms(args, rank: int, world: int, dist) -> dict:
     import torch
     out = {}
     a = copy.copy(args)
-    a.steps, a.warmup = 5, 3
+    a.steps, a.warmup = 3, 3
+    # the plain FP32 path over many blocks (re-projection, fused downdate and
+    # next sketch) on the default workload's matrix
+    wf = WORKLOADS["fp32_multiblock"]
+    r = run_ours(a, wf, rank, world, dist)
+    out["fp32_multiblock"] = {"workload": wf["name"], "value": round(r["value"], 4), "unit": "TFLOP/s",
+                              "ms_per_step": round(r["ms"], 3), "steps": a.steps, "k": r["k"], "blocks": r["s"],
+                              "roofline": r["roofline"], "whole_run": r["whole_run"]}
+    r["h"].close()
+    del r
+    gc.collect()
+    torch.cuda.empty_cache()
+    a.steps = 5
     wm = WORKLOADS["mixed"]
     r = run_ours(a, wm, rank, world, dist)
     out["mixed"] = {"workload": wm["name"], "value": round(r["value"], 4), "unit": "TFLOP/s",

@@ -360,6 +360,16 @@ int rqb_sketch_noalloc(int32_t dtype, const void* A, int64_t m, int64_t n, int64
  * Errors: RQB_ERR_INVALID (null pointer, count < 1), RQB_ERR_CUDA. */
 int rqb_fp64_recip_selftest(const double* x, int64_t count, double* rcp, double* rsq, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Test hook: host-side failure injection for the out-of-memory path.  The
+ * paper has no counterpart.  after >= 0: the library's next `after` device
+ * allocations succeed and the one after them fails as if cudaMalloc had run
+ * out of memory (the call that needed it returns RQB_ERR_OOM; nothing is
+ * launched for the failed step and the handle stays usable); the injection
+ * then switches itself off.  after = -1 switches it off.  Process-wide.
+ * Errors: RQB_ERR_INVALID (after < -1). */
+int rqb_inject_alloc_failure(int64_t after);
+
 /* Human-readable name of a status code (static string). */
 const char* rqb_status_string(int status);
 

@@ -2,6 +2,7 @@
 // block loop of Fig. randQB_b driving the SIMT kernels of rqb_kernels.cu and,
 // for RQB_PREC_TF32X3, the split-TF32 tensor-core products of rqb_tc.cu.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -9,12 +10,26 @@
 #include <type_traits>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "rqb_engine.h"
 #include "rqb_tc.h"
 
 using namespace rqb;
 
 namespace rqb {
+
+// Countdown of rqb_inject_alloc_failure: -1 off; k >= 0: k more device
+// allocations succeed, the next one fails, then the injection is off again.
+static std::atomic<long long> g_fail_countdown{-1};
+
+bool alloc_should_fail() {
+    long long c = g_fail_countdown.load();
+    while (c >= 0)
+        if (g_fail_countdown.compare_exchange_weak(c, c - 1)) return c == 0;
+    return false;
+}
+
 namespace batched {
 int factor_batched(cudaStream_t stream, int num_sms, int64_t count, const void* const* A, const int64_t* m,
                    const int64_t* n, const int64_t* lda, const double* eps, int64_t b, uint64_t seed, int64_t max_rank,
@@ -42,6 +57,7 @@ struct DevBuf {
         if (p) cudaFree(p);
         p = nullptr;
         bytes = 0;
+        if (rqb::alloc_should_fail()) return RQB_ERR_OOM;
         if (cudaMalloc(&p, need) != cudaSuccess) {
             cudaGetLastError();
             return RQB_ERR_OOM;
@@ -77,18 +93,31 @@ struct PhaseTimer {
             if (ev[i]) cudaEventDestroy(ev[i]);
         on = false;
     }
+    // NVTX ranges named after the steps (host side, always on; a profiler
+    // that records NVTX shows the block loop's structure); at most one open
     void begin(cudaStream_t s, int ph) {
+        static const char* const kName[RQB_NUM_PHASES] = {"rqb sketch", "rqb orth", "rqb project", "rqb downdate",
+                                                          "rqb control", "rqb phase 5", "rqb phase 6", "rqb phase 7"};
+        close_range();
+        nvtxRangePushA(kName[(ph >= 0 && ph < RQB_NUM_PHASES) ? ph : RQB_NUM_PHASES - 1]);
+        range_open = true;
         if (!on || n >= kPairs) return;
         cudaEventRecord(ev[2 * n], s);
         phase[n] = ph;
         pending = true;
     }
     void end(cudaStream_t s) {
+        close_range();
         if (!on || !pending) return;
         cudaEventRecord(ev[2 * n + 1], s);
         pending = false;
         ++n;
     }
+    void close_range() {
+        if (range_open) nvtxRangePop();
+        range_open = false;
+    }
+    bool range_open = false;
     // after the stream has been synchronised
     void flush(rqb_stats* st) {
         for (int i = 0; i < n; ++i) {
@@ -986,6 +1015,7 @@ int max_block(const rqb_handle h) { return h->cfg.dtype == RQB_F64 ? 128 : 256; 
 int set_device(rqb_handle h) { return cudaSetDevice(h->device) == cudaSuccess ? RQB_OK : RQB_ERR_CUDA; }
 
 int finish(rqb_handle h, int rc) {
+    h->timer.close_range();
     h->last_status = rc;
     h->stats.status = rc;
     return rc;
@@ -994,6 +1024,12 @@ int finish(rqb_handle h, int rc) {
 }  // namespace
 
 extern "C" {
+
+int rqb_inject_alloc_failure(int64_t after) {
+    if (after < -1) return RQB_ERR_INVALID;
+    rqb::g_fail_countdown.store(after);
+    return RQB_OK;
+}
 
 const char* rqb_status_string(int status) {
     switch (status) {

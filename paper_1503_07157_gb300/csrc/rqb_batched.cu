@@ -825,6 +825,7 @@ static int grow(void** buf, size_t* bytes, size_t need) {
     if (*buf) cudaFree(*buf);
     *buf = nullptr;
     *bytes = 0;
+    if (alloc_should_fail()) return RQB_ERR_OOM;
     if (cudaMalloc(buf, need) != cudaSuccess) {
         cudaGetLastError();
         return RQB_ERR_OOM;

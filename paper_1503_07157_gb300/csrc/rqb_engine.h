@@ -13,6 +13,11 @@
 
 namespace rqb {
 
+// Host-side allocation-failure injection for tests (rqb_inject_alloc_failure):
+// true when the device allocation about to be made must fail as if
+// cudaMalloc had returned an out-of-memory error.
+bool alloc_should_fail();
+
 // Raises `kernel`'s dynamic shared-memory limit to `bytes` on the current
 // device.  The attribute is per device, so the call is made once per
 // (kernel, device, bytes) and remembered under a lock: several host threads

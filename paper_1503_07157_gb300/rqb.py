@@ -95,6 +95,7 @@ def lib() -> ctypes.CDLL:
             "rqb_svd": [P, i64, P, i64, Pd, P, i64],
             "rqb_wait_selftest": [P, Pd],
             "rqb_fp64_recip_selftest": [P, i64, P, P, P],
+            "rqb_inject_alloc_failure": [i64],
         }
         for name, args in sig.items():
             f = getattr(L, name)

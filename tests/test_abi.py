@@ -74,3 +74,9 @@ def test_noalloc_rejects_before_any_launch_without_gpu(lib, dtype, ncols, m, wan
     rc = lib.rqb_sketch_noalloc(dt, fake, m, n, m, 0, ncols, 0, fake, m,
                                 ctypes.byref(nrm) if want_norm else None, None)
     assert rc == getattr(rqb, expect), rqb.status_string(rc)
+
+
+def test_alloc_failure_hook_arguments_without_gpu(lib):
+    assert lib.rqb_inject_alloc_failure(-2) == rqb.RQB_ERR_INVALID
+    assert lib.rqb_inject_alloc_failure(3) == rqb.RQB_OK
+    assert lib.rqb_inject_alloc_failure(-1) == rqb.RQB_OK

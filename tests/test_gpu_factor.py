@@ -52,9 +52,10 @@ def test_fp64_config(orc, rqb_lib):
 
 
 @pytest.mark.parametrize("m,n,b,eps_rel", [(4000, 3200, 128, 1e-2), (4000, 3200, 128, 2e-3), (1037, 777, 37, 3e-3),
-                                           (3000, 2000, 256, 1e-3)])
+                                           (3000, 2000, 256, 1e-3), (4000, 3200, 128, 7e-4)])
 def test_fp32_poly_decay(orc, rqb_lib, m, n, b, eps_rel):
     """Polynomial decay s_j = j^-1.5 (the FP32 workload's spectrum) at oracle-size;
+    eps = 7e-4 ||A||_F is the multi-block benchmark point (about 12 blocks here);
     b = 256 runs the blocked Cholesky tiles (FP64 first pass, FP32 second) and
     the FP32 R^-1 from their FP32 copies."""
     s = inputs.spectrum_poly(min(m, n))
@@ -300,3 +301,33 @@ def test_norm_within_tolerance_gives_empty_factorization(orc, rqb_lib, dtype):
     nA = np.linalg.norm(A)
     Q, B, k, rc, st = _factor(rqb_lib, A, 1.01 * nA, 32, dtype)
     assert rc == rqb_lib.RQB_OK and k == 0 == orc.randqb_b(A, 1.01 * nA, 32).k
+
+
+def test_device_allocation_failure_reports_oom_and_recovers(orc, rqb_lib):
+    """Host-side failure injection (rqb_inject_alloc_failure): a device
+    allocation that fails makes rqb_create or rqb_factor return RQB_ERR_OOM,
+    the status is recorded on the handle, and the same handle factors
+    correctly on the next call."""
+    A = inputs.usv(700, 500, 0.9 ** np.arange(500), seed=31).astype(np.float32).astype(np.float64)
+    eps = 1e-3 * np.linalg.norm(A)
+    Ad = to_dev(A, torch.float32)
+    L = rqb_lib.lib()
+    try:
+        assert L.rqb_inject_alloc_failure(0) == rqb_lib.RQB_OK
+        with pytest.raises(rqb_lib.RqbError) as e:
+            rqb_lib.Handle(torch.float32)
+        assert e.value.status == rqb_lib.RQB_ERR_OOM
+        with rqb_lib.Handle(torch.float32) as h:
+            assert L.rqb_inject_alloc_failure(0) == rqb_lib.RQB_OK
+            _, _, _, rc = h.rqb_factor(Ad, eps, 32, 0, check=False)
+            assert rc == rqb_lib.RQB_ERR_OOM
+            assert h.rqb_get_stats().status == rqb_lib.RQB_ERR_OOM
+            Q, B, k, rc = h.rqb_factor(Ad, eps, 32, 0, check=False)
+            assert rc == rqb_lib.RQB_OK
+            Qn, Bn = to_np(Q), to_np(B)
+        ro = orc.randqb_b(A, eps, 32, seed=0, omega_prec=32)
+        assert k == ro.k
+        assert abs(resid(A, Qn, Bn) - resid(A, ro.Q, ro.B)) <= 1e-5 * np.linalg.norm(A)
+        assert L.rqb_inject_alloc_failure(-2) == rqb_lib.RQB_ERR_INVALID
+    finally:
+        L.rqb_inject_alloc_failure(-1)

@@ -142,6 +142,11 @@ typedef struct {
                                rqb_factor)                                     */
     int32_t tile_width;     /* rqb_factor_batched: columns of A per work item of
                                the projection, as picked by the autotuner      */
+    int32_t near_identity;  /* panels whose second CholeskyQR factor came from
+                               the near-identity expansion (||G - I||_F below
+                               2^-28 for an FP64 factor, 1e-4 for an FP32 one)
+                               instead of the elimination                      */
+    int32_t reserved;
 } rqb_stats;
 
 typedef struct rqb_handle_s* rqb_handle;

@@ -3,6 +3,7 @@
 // for RQB_PREC_TF32X3, the split-TF32 tensor-core products of rqb_tc.cu.
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -30,6 +31,14 @@ bool alloc_should_fail() {
     return false;
 }
 
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* v = std::getenv("RQB_PDL");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 namespace batched {
 int factor_batched(cudaStream_t stream, int num_sms, int64_t count, const void* const* A, const int64_t* m,
                    const int64_t* n, const int64_t* lda, const double* eps, int64_t b, uint64_t seed, int64_t max_rank,
@@ -48,6 +57,10 @@ constexpr int kScalars = 16;       // FP64 scalars on the device
 int round_up(int64_t v, int64_t q) { return (int)(((v + q - 1) / q) * q); }
 
 int pad_block(int64_t b) { return b <= 32 ? 32 : b <= 64 ? 64 : b <= 128 ? 128 : 256; }
+constexpr int kMaxPanel = 256;   // the widest padded panel pad_block gives
+// pinned host block of a handle: its DevState mirror, the first CholeskyQR
+// pass's scratch state and that pass's diag(R)
+constexpr size_t kHostPinned = 2 * sizeof(DevState) + sizeof(double) * kMaxPanel;
 
 struct DevBuf {
     void* p = nullptr;
@@ -145,7 +158,9 @@ struct rqb_handle_s {
     DevBuf q, b, w, ahost;     // outputs, residual copy, staging for host input
     int64_t ldq = 0, ldb = 0, ldw = 0, kcap_alloc = 0;
     // host mirror
-    DevState* hstate = nullptr;  // pinned
+    DevState* hstate = nullptr;  // pinned, with the two below in the same allocation
+    DevState* hstate2 = nullptr; // the first CholeskyQR pass's scratch state (tensor-core Gram check)
+    double* hdiag = nullptr;     // diag(R) of that pass, up to kMaxPanel entries
     rqb_stats stats{};
     int last_status = RQB_OK;
     PhaseTimer timer;
@@ -337,6 +352,7 @@ int read_state(rqb_handle h, const Scal& sc) {
     RQB_CK(cudaMemcpyAsync(h->hstate, sc.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
     RQB_CK(cudaStreamSynchronize(h->stream));
     h->timer.flush(&h->stats);
+    h->stats.near_identity = h->hstate->near_id;
     return h->hstate->err;
 }
 
@@ -380,11 +396,14 @@ int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_
             cx2.st = st2;
             RQB_CK(chol_inv<T>(cx2, ar.G, bp, p, ar.R, ar.Rinv, true, ar.dpart, ar.dpart_cap));
             cx.launches = cx2.launches;
-            DevState hs;
-            std::vector<double> diag((size_t)bp);
-            RQB_CK(cudaMemcpyAsync(&hs, st2, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
-            RQB_CK(cudaMemcpy2DAsync(diag.data(), sizeof(double), ar.R, sizeof(double) * (bp + 1), sizeof(double),
-                                     bp, cudaMemcpyDeviceToHost, h->stream));
+            // pinned host copies: the one synchronisation inside the panel
+            // waits for two small copies, not for staged pageable ones
+            if (bp > kMaxPanel) return RQB_ERR_INVALID;
+            const DevState& hs = *h->hstate2;
+            const double* diag = h->hdiag;
+            RQB_CK(cudaMemcpyAsync(h->hstate2, st2, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+            RQB_CK(cudaMemcpy2DAsync(h->hdiag, sizeof(double), ar.R, sizeof(double) * (bp + 1), sizeof(double), bp,
+                                     cudaMemcpyDeviceToHost, h->stream));
             RQB_CK(cudaStreamSynchronize(h->stream));
             double lo = HUGE_VAL, hi = 0.0;
             for (int i = 0; i < p; ++i) {
@@ -451,7 +470,7 @@ int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_
     }
     if (!tcg2)
         RQB_CK(gemm_tn_f64acc<T>(cx, m, bp, bp, ar.Y1, m, ar.Y1, m, ar.G, bp, ar.dpart, ar.dpart_cap, false, true));
-    RQB_CK(chol_inv<T>(cx, ar.G, bp, p, ar.R, ar.Rinv, sizeof(T) == 8, ar.dpart, ar.dpart_cap));
+    RQB_CK(chol_inv<T>(cx, ar.G, bp, p, ar.R, ar.Rinv, sizeof(T) == 8, ar.dpart, ar.dpart_cap, true));
     bool tc2 = false;
     if constexpr (std::is_same<T, float>::value) {
         // full-width panels only: the product writes all bp columns
@@ -1073,13 +1092,15 @@ int rqb_create(rqb_handle* out, const rqb_config* cfg) {
         return RQB_ERR_CUDA;
     }
     if (h->state.ensure(256 + sizeof(double) * (kScalars + kNrmCap)) != RQB_OK ||
-        cudaMallocHost(reinterpret_cast<void**>(&h->hstate), sizeof(DevState)) != cudaSuccess) {
+        cudaMallocHost(reinterpret_cast<void**>(&h->hstate), kHostPinned) != cudaSuccess) {
         cudaGetLastError();
         h->state.release();
         delete h;
         return RQB_ERR_OOM;
     }
-    std::memset(h->hstate, 0, sizeof(DevState));
+    std::memset(h->hstate, 0, kHostPinned);
+    h->hstate2 = h->hstate + 1;
+    h->hdiag = reinterpret_cast<double*>(h->hstate + 2);
     if ((cfg->flags & RQB_FLAG_PHASE_TIMING) && h->timer.create() != RQB_OK) {
         h->timer.destroy();
         cudaGetLastError();

@@ -31,7 +31,10 @@ constexpr int kStrip = 8;   // rows per CTA in the solves and updates
 // Padding rows/columns >= p become the identity; dG = diagonal of G (the
 // reference for the relative pivot test); L cleared.
 __global__ void k_chol_init(double* __restrict__ G, int bp, int p, double* __restrict__ dG,
-                            double* __restrict__ L) {
+                            double* __restrict__ L, const int* __restrict__ skip) {
+    pdl_trigger();
+    pdl_wait();
+    if (skip && *skip) return;   // the near-identity expansion gave the factor
     const int total = bp * bp;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
         const int r = e % bp, c = e / bp;
@@ -94,7 +97,11 @@ template <typename W>
 __global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G, double* __restrict__ L,
                                                     double* __restrict__ Linv, float* __restrict__ Lf,
                                                     float* __restrict__ Lif, int bp, int k,
-                                                    const double* __restrict__ dG, double tol, DevState* st) {
+                                                    const double* __restrict__ dG, double tol, DevState* st,
+                                                    const int* __restrict__ skip) {
+    pdl_trigger();
+    pdl_wait();
+    if (skip && *skip) return;   // the near-identity expansion gave the factor
     __shared__ W D[kNb][kNb + 1];    // L_kk (lower)
     __shared__ W Di[kNb][kNb + 1];   // L_kk^{-1} (lower)
     __shared__ W inv[kNb];
@@ -244,7 +251,10 @@ __global__ void __launch_bounds__(256) k_chol_panel(const double* __restrict__ G
 // (i, j), k < j <= i < nblk, pairs enumerated column by column.
 template <typename W>
 __global__ void __launch_bounds__(256) k_chol_update(double* __restrict__ G, const double* __restrict__ L, int bp,
-                                                     int k, int nblk) {
+                                                     int k, int nblk, const int* __restrict__ skip) {
+    pdl_trigger();
+    pdl_wait();
+    if (skip && *skip) return;   // the near-identity expansion gave the factor
     __shared__ W Lj[kNb][kNb + 1];
     int pair = blockIdx.x / (kNb / kStrip);
     const int q = blockIdx.x % (kNb / kStrip);
@@ -270,7 +280,11 @@ __global__ void __launch_bounds__(256) k_chol_update(double* __restrict__ G, con
 }
 
 // R = L^T (FP64, column-major, upper).
-__global__ void k_chol_transpose(const double* __restrict__ L, int bp, double* __restrict__ R) {
+__global__ void k_chol_transpose(const double* __restrict__ L, int bp, double* __restrict__ R,
+                                 const int* __restrict__ skip) {
+    pdl_trigger();
+    pdl_wait();
+    if (skip && *skip) return;   // the near-identity expansion gave the factor
     const int total = bp * bp;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
         const int r = e % bp, c = e / bp;
@@ -319,7 +333,10 @@ __global__ void __launch_bounds__(256) k_upper_inverse(const double* __restrict_
 // stores it transposed.
 template <typename T, typename W>
 __global__ void __launch_bounds__(256) k_linv_blocked(const double* __restrict__ L, const double* __restrict__ Linv,
-                                                      int bp, T* __restrict__ Rinv) {
+                                                      int bp, T* __restrict__ Rinv, const int* __restrict__ skip) {
+    pdl_trigger();
+    pdl_wait();
+    if (skip && *skip) return;   // the near-identity expansion gave the factor
     extern __shared__ __align__(16) unsigned char linv_smem[];
     W* X = reinterpret_cast<W*>(linv_smem);          // bp x 32, column block j of L^{-1}, ld bp
     W* Lr = X + (size_t)bp * kNb;                     // 32 x bp block row of L, ld 33 (row-padded)
@@ -386,7 +403,10 @@ __global__ void __launch_bounds__(256) k_linv_blocked(const double* __restrict__
 constexpr int kXs = 36;   // padded row of X and S (floats)
 
 __global__ void __launch_bounds__(256) k_linv_f32(const float* __restrict__ Lf, const float* __restrict__ Lif, int bp,
-                                                  float* __restrict__ Rinv) {
+                                                  float* __restrict__ Rinv, const int* __restrict__ skip) {
+    pdl_trigger();
+    pdl_wait();
+    if (skip && *skip) return;   // the near-identity expansion gave the factor
     extern __shared__ __align__(16) unsigned char linvf_smem[];
     float* X = reinterpret_cast<float*>(linvf_smem);   // bp x 36
     float* Lr = X + (size_t)bp * kXs;                  // [2][bp][32]: Lr[t][rr] = L(i0 + rr, j0 + t)
@@ -452,6 +472,76 @@ __global__ void __launch_bounds__(256) k_linv_f32(const float* __restrict__ Lf, 
     }
 }
 
+// Second CholeskyQR pass on a near-identity Gram (Sec. 4.3): after the first
+// pass, G = Y1^T Y1 = I + E with E of the order of that pass's rounding.
+// With U the upper triangle of E and its diagonal halved (U + U^T = E),
+// R = I + U gives R^T R = I + E + U^T U, so R is the Cholesky factor of G up
+// to O(||E||^2), and R^{-1} = I - U up to O(||E||^2).  When ||E||_F <= tau,
+// with tau^2 below the working precision's unit roundoff, the factor is taken
+// from this expansion (in FP64, from G's own entries) and the elimination is
+// skipped; otherwise the elimination runs as before.  Rows and columns >= p
+// are the identity.
+
+// part[b] = sum of (G_rc - delta_rc)^2 over CTA b's share of the p x p block.
+__global__ void __launch_bounds__(256) k_near_id_norm(const double* __restrict__ G, int bp, int p,
+                                                      double* __restrict__ part) {
+    pdl_trigger();
+    pdl_wait();
+    __shared__ double sh[8];
+    double acc = 0.0;
+    const int total = p * p;
+    for (int e = blockIdx.x * 256 + threadIdx.x; e < total; e += gridDim.x * 256) {
+        const int r = e % p, c = e / p;
+        const double d = G[r + (int64_t)c * bp] - (r == c ? 1.0 : 0.0);
+        acc = fma(d, d, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sh[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// Every CTA sums the parts in order and takes the same decision; when
+// ||E||_F^2 <= tau2 the CTAs write their share of R = I + U (FP64) and of
+// R^{-1} = I - U (T), and CTA 0 sets *skip = 1, else *skip = 0.
+template <typename T>
+__global__ void __launch_bounds__(256) k_near_id_apply(const double* __restrict__ G, int bp, int p,
+                                                       const double* __restrict__ part, double tau2,
+                                                       double* __restrict__ R, T* __restrict__ Rinv,
+                                                       int* __restrict__ skip, DevState* st) {
+    pdl_trigger();
+    pdl_wait();
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int b = 0; b < kNearIdParts; ++b) t += part[b];
+        ok = (t <= tau2) ? 1 : 0;   // false for a NaN norm
+        if (blockIdx.x == 0) {
+            *skip = ok;
+            if (ok && st) atomicAdd(&st->near_id, 1);
+        }
+    }
+    __syncthreads();
+    if (!ok) return;
+    const int total = bp * bp;
+    for (int e = blockIdx.x * 256 + threadIdx.x; e < total; e += gridDim.x * 256) {
+        const int r = e % bp, c = e / bp;
+        double u = 0.0;                      // U_rc
+        if (r < p && c < p) {
+            if (r < c) u = G[e];
+            else if (r == c) u = 0.5 * (G[e] - 1.0);
+        }
+        const double id = (r == c) ? 1.0 : 0.0;
+        R[e] = (r <= c) ? id + u : 0.0;
+        Rinv[e] = (T)((r <= c) ? id - u : 0.0);
+    }
+}
+
 }  // namespace
 
 // Rinv (T) = R^{-1} for an upper-triangular FP64 R (bp x bp, column-major);
@@ -476,7 +566,7 @@ cudaError_t upper_inverse(Ctx& cx, const double* R, int bp, T* Rinv) {
 // stored in FP64 either way; R^{-1} is formed in T.
 template <typename T>
 cudaError_t chol_inv_blocked(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, double tol, double* scratch,
-                             size_t scratch_doubles, bool fp64) {
+                             size_t scratch_doubles, bool fp64, const int* skip) {
     constexpr bool f32 = sizeof(T) == 4;
     const size_t need = 2 * (size_t)bp * bp + bp + (f32 ? (size_t)bp * bp : 0);
     if (bp % kNb != 0 || scratch_doubles < need) return cudaErrorInvalidValue;
@@ -486,49 +576,72 @@ cudaError_t chol_inv_blocked(Ctx& cx, double* G, int bp, int p, double* R, T* Ri
     float* Lf = f32 ? reinterpret_cast<float*>(dG + bp) : nullptr;   // 16-byte aligned: bp % 32 == 0
     float* Lif = f32 ? Lf + (size_t)bp * bp : nullptr;
     const int nblk = bp / kNb;
-    k_chol_init<<<std::max(1, bp * bp / 256), 256, 0, cx.stream>>>(G, bp, p, dG, L);
+    cudaError_t e = launch_pdl(k_chol_init, dim3(std::max(1, bp * bp / 256)), dim3(256), 0, cx.stream, G, bp, p, dG,
+                               L, skip);
+    if (e != cudaSuccess) return e;
     cx.launches++;
     for (int k = 0; k < nblk; ++k) {
         const int below = nblk - k - 1;
-        if (fp64)
-            k_chol_panel<double><<<1 + below * (kNb / kStrip), 256, 0, cx.stream>>>(G, L, Linv, Lf, Lif, bp, k, dG,
-                                                                                    tol, cx.st);
-        else
-            k_chol_panel<float><<<1 + below * (kNb / kStrip), 256, 0, cx.stream>>>(G, L, Linv, Lf, Lif, bp, k, dG,
-                                                                                   tol, cx.st);
+        const dim3 gp(1 + below * (kNb / kStrip));
+        e = fp64 ? launch_pdl(k_chol_panel<double>, gp, dim3(256), 0, cx.stream, G, L, Linv, Lf, Lif, bp, k, dG, tol,
+                              cx.st, skip)
+                 : launch_pdl(k_chol_panel<float>, gp, dim3(256), 0, cx.stream, G, L, Linv, Lf, Lif, bp, k, dG, tol,
+                              cx.st, skip);
+        if (e != cudaSuccess) return e;
         cx.launches++;
         if (below > 0) {
             const int pairs = below * (below + 1) / 2;
-            if (fp64)
-                k_chol_update<double><<<pairs * (kNb / kStrip), 256, 0, cx.stream>>>(G, L, bp, k, nblk);
-            else
-                k_chol_update<float><<<pairs * (kNb / kStrip), 256, 0, cx.stream>>>(G, L, bp, k, nblk);
+            const dim3 gu(pairs * (kNb / kStrip));
+            e = fp64 ? launch_pdl(k_chol_update<double>, gu, dim3(256), 0, cx.stream, G, L, bp, k, nblk, skip)
+                     : launch_pdl(k_chol_update<float>, gu, dim3(256), 0, cx.stream, G, L, bp, k, nblk, skip);
+            if (e != cudaSuccess) return e;
             cx.launches++;
         }
     }
-    k_chol_transpose<<<std::max(1, bp * bp / 256), 256, 0, cx.stream>>>(L, bp, R);
+    e = launch_pdl(k_chol_transpose, dim3(std::max(1, bp * bp / 256)), dim3(256), 0, cx.stream, L, bp, R, skip);
+    if (e != cudaSuccess) return e;
     cx.launches++;
     if constexpr (f32) {
         const size_t smem = sizeof(float) * ((size_t)bp * kXs + 2 * (size_t)bp * kNb + 2 * kNb * kNb + kNb * kXs);
         if (smem > 200 * 1024) return cudaErrorInvalidValue;
         cudaError_t ea = smem_limit(k_linv_f32, 200 * 1024);
         if (ea != cudaSuccess) return ea;
-        k_linv_f32<<<nblk, 256, smem, cx.stream>>>(Lf, Lif, bp, Rinv);
+        e = launch_pdl(k_linv_f32, dim3(nblk), dim3(256), smem, cx.stream, Lf, Lif, bp, Rinv, skip);
+        if (e != cudaSuccess) return e;
     } else {
         const size_t smem = sizeof(T) * ((size_t)bp * kNb + (size_t)bp * (kNb + 1) + 2 * (size_t)kNb * (kNb + 1));
         cudaError_t ea = smem_limit(k_linv_blocked<T, T>, 200 * 1024);
         if (ea != cudaSuccess) return ea;
-        k_linv_blocked<T, T><<<nblk, 256, smem, cx.stream>>>(L, Linv, bp, Rinv);
+        e = launch_pdl(k_linv_blocked<T, T>, dim3(nblk), dim3(256), smem, cx.stream, L, Linv, bp, Rinv, skip);
+        if (e != cudaSuccess) return e;
     }
+    cx.launches++;
+    return cudaGetLastError();
+}
+
+// Two launches of kNearIdParts CTAs: the norm's parts, then the decision and
+// the factor.
+template <typename T>
+cudaError_t near_identity(Ctx& cx, const double* G, int bp, int p, double* R, T* Rinv, double tau, double* work,
+                          int* skip) {
+    cudaError_t e = launch_pdl(k_near_id_norm, dim3(kNearIdParts), dim3(256), 0, cx.stream, G, bp, p, work);
+    if (e != cudaSuccess) return e;
+    cx.launches++;
+    e = launch_pdl(k_near_id_apply<T>, dim3(kNearIdParts), dim3(256), 0, cx.stream, G, bp, p,
+                   static_cast<const double*>(work), tau * tau, R, Rinv, skip, cx.st);
+    if (e != cudaSuccess) return e;
     cx.launches++;
     return cudaGetLastError();
 }
 
 template cudaError_t upper_inverse<float>(Ctx&, const double*, int, float*);
 template cudaError_t upper_inverse<double>(Ctx&, const double*, int, double*);
-template cudaError_t chol_inv_blocked<float>(Ctx&, double*, int, int, double*, float*, double, double*, size_t, bool);
+template cudaError_t chol_inv_blocked<float>(Ctx&, double*, int, int, double*, float*, double, double*, size_t, bool,
+                                             const int*);
 template cudaError_t chol_inv_blocked<double>(Ctx&, double*, int, int, double*, double*, double, double*, size_t,
-                                              bool);
+                                              bool, const int*);
+template cudaError_t near_identity<float>(Ctx&, const double*, int, int, double*, float*, double, double*, int*);
+template cudaError_t near_identity<double>(Ctx&, const double*, int, int, double*, double*, double, double*, int*);
 
 }  // namespace rqb
 

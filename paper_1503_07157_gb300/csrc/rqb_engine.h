@@ -8,6 +8,7 @@
 #include <mutex>
 #include <set>
 #include <tuple>
+#include <utility>
 
 #include "rqb_internal.cuh"
 
@@ -39,6 +40,30 @@ inline cudaError_t smem_limit_once(const void* kernel, int bytes) {
 template <typename K>
 inline cudaError_t smem_limit(K kernel, int bytes) {
     return smem_limit_once(reinterpret_cast<const void*>(kernel), bytes);
+}
+
+// Programmatic dependent launches (pdl_wait / pdl_trigger in the kernels):
+// on unless the environment sets RQB_PDL=0.
+bool pdl_enabled();
+
+// kernel<<<grid, block, smem, stream>>>(args...), with programmatic stream
+// serialisation when pdl_enabled(): the launch may overlap the kernel before
+// it in the stream up to the new kernel's pdl_wait().  Only kernels that call
+// pdl_wait() before touching global memory are launched this way.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 struct Ctx {
@@ -93,14 +118,26 @@ template <typename T>
 cudaError_t gemm_tn_f64acc(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, int64_t ldx, const T* Y,
                            int64_t ldy, double* Out, int64_t ldo, double* part, size_t part_cap_elems,
                            bool exact, bool sym = false);
+// second_pass: G is the Gram of an already orthonormalised panel (the
+// second CholeskyQR pass); the factor is first tried by the near-identity
+// expansion (near_identity), the elimination running only when it does not
+// apply.
 template <typename T>
 cudaError_t chol_inv(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, bool fp64_factor, double* scratch,
-                     size_t scratch_doubles);
+                     size_t scratch_doubles, bool second_pass = false);
 template <typename T>
 cudaError_t upper_inverse(Ctx& cx, const double* R, int bp, T* Rinv);
 template <typename T>
 cudaError_t chol_inv_blocked(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, double tol, double* scratch,
-                             size_t scratch_doubles, bool fp64);
+                             size_t scratch_doubles, bool fp64, const int* skip);
+// Second CholeskyQR pass (rqb_chol.cu): R and Rinv by the near-identity
+// expansion when ||G - I||_F <= tau, with *skip (device) set to 1 so that the
+// elimination launched after it returns at once, else *skip = 0.  work holds
+// kNearIdParts doubles.
+constexpr int kNearIdParts = 64;
+template <typename T>
+cudaError_t near_identity(Ctx& cx, const double* G, int bp, int p, double* R, T* Rinv, double tau, double* work,
+                          int* skip);
 template <typename T>
 cudaError_t downdate_sketch(Ctx& cx, int64_t m, int64_t n, int p, int bp, const T* Wsrc, int64_t ldws,
                             const T* Qi, int64_t ldq, const T* Bi, int64_t ldb, const T* Om, T* Wdst,

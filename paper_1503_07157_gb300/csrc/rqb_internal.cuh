@@ -22,7 +22,8 @@ struct DevState {
     double D;          // direct ||A^(i)||_F^2 of the current block
     int32_t err;       // first error code recorded by a kernel (rqb_status)
     int32_t flag;      // stop decision of the current block (see StopFlag)
-    int32_t pad[2];
+    int32_t near_id;   // second CholeskyQR passes factored by the near-identity expansion
+    int32_t pad;
 };
 
 enum StopFlag : int32_t { kContinue = 0, kStop = 1, kAmbiguous = 2 };
@@ -30,6 +31,17 @@ enum StopFlag : int32_t { kContinue = 0, kStop = 1, kAmbiguous = 2 };
 __device__ __forceinline__ void record_error(DevState* st, int code) {
     if (st) atomicCAS(&st->err, 0, code);
 }
+
+// Programmatic dependent launch (PTX griddepcontrol, sm_90 and later).  A
+// kernel launched with the programmatic stream-serialisation attribute may
+// start while the kernel before it in the stream is still running:
+// pdl_wait() blocks until that kernel has completed and its memory is
+// visible (for a normally launched kernel it returns at once), and
+// pdl_trigger() lets the next such kernel launch before this one ends.
+// Kernels that take part call pdl_trigger() first and pdl_wait() before
+// their first global-memory access, read or write.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of

@@ -34,6 +34,8 @@ namespace rqb {
 template <typename T>
 __global__ void k_omega(int64_t n, int64_t col0, int ncols, int ncols_pad, uint64_t seed,
                         T* __restrict__ out, int64_t rs, int64_t cs) {
+    pdl_trigger();
+    pdl_wait();
     const int64_t total = n * (int64_t)ncols_pad;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -51,7 +53,11 @@ cudaError_t launch_omega(Ctx& cx, int64_t n, int64_t col0, int ncols, int ncols_
     const int64_t total = n * (int64_t)ncols_pad;
     int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)cx.num_sms * 8);
     if (blocks < 1) blocks = 1;
-    k_omega<T><<<blocks, 256, 0, cx.stream>>>(n, col0, ncols, ncols_pad, seed, out, rs, cs);
+    {
+        const cudaError_t le_ = launch_pdl(k_omega<T>, dim3(blocks), dim3(256), 0, cx.stream, n, col0, ncols,
+                                           ncols_pad, seed, out, rs, cs);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return cudaGetLastError();
 }
@@ -77,6 +83,8 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_sumsq(int64_t m, int64_t n, const T* __restrict__ X, int64_t ldx,
                                                double* __restrict__ part) {
+    pdl_trigger();
+    pdl_wait();
     // one warp per column at a time (coalesced rows); FP32 or BF16 data: each square
     // is split exactly into p + e (e = fma(v, v, -p)) and summed with
     // compensated FP32 adds, promoted to FP64 every 64 rows per lane
@@ -147,6 +155,8 @@ __global__ void __launch_bounds__(256) k_sumsq(int64_t m, int64_t n, const T* __
 // Sum `count` doubles in a fixed order into *out (single CTA).
 __global__ void __launch_bounds__(256) k_sum_doubles(const double* __restrict__ part, int count,
                                                      double* __restrict__ out) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ double sh[8];
     double acc = 0.0;
     for (int i = threadIdx.x; i < count; i += 256) acc += part[i];
@@ -155,7 +165,10 @@ __global__ void __launch_bounds__(256) k_sum_doubles(const double* __restrict__ 
 }
 
 cudaError_t launch_sum_doubles(Ctx& cx, const double* part, int count, double* out) {
-    k_sum_doubles<<<1, 256, 0, cx.stream>>>(part, count, out);
+    {
+        const cudaError_t le_ = launch_pdl(k_sum_doubles, dim3(1), dim3(256), 0, cx.stream, part, count, out);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return cudaGetLastError();
 }
@@ -165,7 +178,10 @@ cudaError_t launch_sumsq(Ctx& cx, int64_t m, int64_t n, const T* X, int64_t ldx,
                          double* out) {
     int blocks = std::min<int>(part_cap, cx.num_sms * 4);
     blocks = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (m * n + 255) / 256));
-    k_sumsq<T><<<blocks, 256, 0, cx.stream>>>(m, n, X, ldx, part);
+    {
+        const cudaError_t le_ = launch_pdl(k_sumsq<T>, dim3(blocks), dim3(256), 0, cx.stream, m, n, X, ldx, part);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return launch_sum_doubles(cx, part, blocks, out);
 }
@@ -179,6 +195,8 @@ __global__ void __launch_bounds__(256)
 k_reduce_split(int64_t rows, int64_t cols, int splits, const TP* __restrict__ part, int64_t ldp,
                int64_t zstride, TO* out, int64_t ldo, double* __restrict__ sq_part, double alpha, double beta,
                const TO* Yin, int64_t ldyin, int sym) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ double sh[8];
     double sq = 0.0;
     const int64_t total = rows * cols;
@@ -212,6 +230,8 @@ k_reduce_split(int64_t rows, int64_t cols, int splits, const TP* __restrict__ pa
 __global__ void __launch_bounds__(256)
 k_reduce_split4(int rows, int cols, int splits, const float* __restrict__ part, int64_t ldp, int64_t zstride,
                 float* __restrict__ out, int64_t ldo, double* __restrict__ sq_part) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ double sh[8];
     double sq = 0.0;
     const int rq = rows / 4;
@@ -254,13 +274,18 @@ cudaError_t launch_reduce_split(Ctx& cx, int64_t rows, int64_t cols, int splits,
     int blocks = std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, (int64_t)cx.num_sms * 8));
     if (sq_part) blocks = std::min(blocks, sq_cap);
     if constexpr (std::is_same<TP, float>::value && std::is_same<TO, float>::value) {
-        if (vec4)
-            k_reduce_split4<<<blocks, 256, 0, cx.stream>>>((int)rows, (int)cols, splits, part, ldp, zstride, out,
-                                                           ldo, sq_part);
+        if (vec4) {
+            const cudaError_t le_ = launch_pdl(k_reduce_split4, dim3(blocks), dim3(256), 0, cx.stream, (int)rows,
+                                               (int)cols, splits, part, ldp, zstride, out, ldo, sq_part);
+            if (le_ != cudaSuccess) return le_;
+        }
     }
-    if (!vec4)
-        k_reduce_split<TP, TO><<<blocks, 256, 0, cx.stream>>>(rows, cols, splits, part, ldp, zstride, out, ldo,
-                                                               sq_part, alpha, beta, Yin, ldyin, sym);
+    if (!vec4) {
+        const cudaError_t le_ = launch_pdl(k_reduce_split<TP, TO>, dim3(blocks), dim3(256), 0, cx.stream, rows, cols,
+                                           splits, part, ldp, zstride, out, ldo, sq_part, alpha, beta, Yin, ldyin,
+                                           sym);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !sq_part) return e;
@@ -285,7 +310,10 @@ __device__ __forceinline__ int64_t packed_row(int r, int bp) { return (int64_t)r
 template <typename W>
 __global__ void __launch_bounds__(256)
 k_cholesky(const double* __restrict__ G, int bp, int p, double* __restrict__ R, int in_smem, void* scratch,
-           double tol, DevState* st) {
+           double tol, DevState* st, const int* __restrict__ skip) {
+    pdl_trigger();
+    pdl_wait();
+    if (skip && *skip) return;   // the near-identity expansion gave the factor
     extern __shared__ __align__(16) unsigned char chol_smem[];
     __shared__ double refd[256];
     __shared__ double rdiag[256];
@@ -336,7 +364,11 @@ k_cholesky(const double* __restrict__ G, int bp, int p, double* __restrict__ R, 
 // the CTA's leading block of R and the reciprocal diagonal in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(128)
-k_tri_inverse(const double* __restrict__ R, int bp, T* __restrict__ Rinv, int staged_cols) {
+k_tri_inverse(const double* __restrict__ R, int bp, T* __restrict__ Rinv, int staged_cols,
+              const int* __restrict__ skip) {
+    pdl_trigger();
+    pdl_wait();
+    if (skip && *skip) return;   // the near-identity expansion gave the factor
     extern __shared__ __align__(16) double dsm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cmax = min(bp - 1, (int)blockIdx.x * 4 + 3);
@@ -370,6 +402,8 @@ k_tri_inverse(const double* __restrict__ R, int bp, T* __restrict__ Rinv, int st
 // (decided on the direct norm after the downdate).  tau is the rounding band
 // of E in the working precision.
 __global__ void k_set_norm(DevState* st, const double* nrm) {
+    pdl_trigger();
+    pdl_wait();
     const double v = *nrm;
     st->normA2 = v;
     st->E = v;
@@ -378,6 +412,8 @@ __global__ void k_set_norm(DevState* st, const double* nrm) {
 }
 
 __global__ void k_stop_after_b(DevState* st, const double* nb2, double eps2, double tau_rel, int fixed) {
+    pdl_trigger();
+    pdl_wait();
     const double tau = tau_rel * st->normA2;
     const double b2 = *nb2;
     st->normB2 = b2;
@@ -394,23 +430,36 @@ __global__ void k_stop_after_b(DevState* st, const double* nb2, double eps2, dou
 // always = 0: decide only when the downdate test was ambiguous; always = 1:
 // decide on the direct norm whenever the downdate test did not stop.
 __global__ void k_stop_direct(DevState* st, const double* d2, double eps2, int always) {
+    pdl_trigger();
+    pdl_wait();
     const double d = *d2;
     st->D = d;
     if (st->flag == kAmbiguous || (always && st->flag != kStop)) st->flag = (d <= eps2) ? kStop : kContinue;
 }
 
 cudaError_t launch_set_norm(Ctx& cx, const double* nrm) {
-    k_set_norm<<<1, 1, 0, cx.stream>>>(cx.st, nrm);
+    {
+        const cudaError_t le_ = launch_pdl(k_set_norm, dim3(1), dim3(1), 0, cx.stream, cx.st, nrm);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return cudaGetLastError();
 }
 cudaError_t launch_stop_after_b(Ctx& cx, const double* nb2, double eps2, double tau_rel, int fixed) {
-    k_stop_after_b<<<1, 1, 0, cx.stream>>>(cx.st, nb2, eps2, tau_rel, fixed);
+    {
+        const cudaError_t le_ = launch_pdl(k_stop_after_b, dim3(1), dim3(1), 0, cx.stream, cx.st, nb2, eps2, tau_rel,
+                                           fixed);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return cudaGetLastError();
 }
 cudaError_t launch_stop_direct(Ctx& cx, const double* d2, double eps2, bool always) {
-    k_stop_direct<<<1, 1, 0, cx.stream>>>(cx.st, d2, eps2, always ? 1 : 0);
+    {
+        const cudaError_t le_ = launch_pdl(k_stop_direct, dim3(1), dim3(1), 0, cx.stream, cx.st, d2, eps2,
+                                           always ? 1 : 0);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return cudaGetLastError();
 }
@@ -827,7 +876,7 @@ cudaError_t gemm_tn_f64acc(Ctx& cx, int64_t m, int pn, int64_t qn, const T* X, i
 // fp64_factor: FP64 Cholesky (first CholeskyQR pass); else FP32 (second pass).
 template <typename T>
 cudaError_t chol_inv(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, bool fp64_factor, double* scratch,
-                     size_t scratch_doubles) {
+                     size_t scratch_doubles, bool second_pass) {
     for (const void* k : {reinterpret_cast<const void*>(k_cholesky<double>),
                           reinterpret_cast<const void*>(k_cholesky<float>),
                           reinterpret_cast<const void*>(k_tri_inverse<T>)}) {
@@ -841,17 +890,39 @@ cudaError_t chol_inv(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, bool
     const size_t sq = (size_t)bp * bp;
     const size_t packed = (size_t)bp * (bp + 1) / 2;
     if (scratch_doubles < sq) return cudaErrorInvalidValue;
+    // second pass: the near-identity expansion first; its norm parts and flag
+    // sit past the 3 bp^2 + bp doubles the elimination uses of scratch.  The
+    // terms it drops are O(||G - I||^2): tau^2 = 2^-56 for an FP64 factor,
+    // 1e-8 for an FP32 one, both below the unit roundoff
+    int* skip = nullptr;
+    if (second_pass) {
+        const size_t at = 3 * sq + (size_t)bp;
+        if (scratch_doubles < at + kNearIdParts + 1) return cudaErrorInvalidValue;
+        skip = reinterpret_cast<int*>(scratch + at + kNearIdParts);
+        const double tau = fp64_factor ? 0x1p-28 : 1e-4;
+        cudaError_t en = near_identity<T>(cx, G, bp, p, R, Rinv, tau, scratch + at, skip);
+        if (en != cudaSuccess) return en;
+    }
     // a Gram of 128 or more columns: blocked over many CTAs (one CTA's shared
     // memory does not hold a wide FP64 one, and one SM's FP64 rate bounds it)
-    if (bp >= 128) return chol_inv_blocked<T>(cx, G, bp, p, R, Rinv, tol, scratch, scratch_doubles, fp64_factor);
+    if (bp >= 128)
+        return chol_inv_blocked<T>(cx, G, bp, p, R, Rinv, tol, scratch, scratch_doubles, fp64_factor, skip);
     if (fp64_factor) {
         const int in_smem = (sizeof(double) * packed <= 200 * 1024) ? 1 : 0;
-        k_cholesky<double><<<1, 256, in_smem ? sizeof(double) * packed : 0, cx.stream>>>(G, bp, p, R, in_smem,
-                                                                                         scratch, tol, cx.st);
+        {
+            const cudaError_t le_ = launch_pdl(k_cholesky<double>, dim3(1), dim3(256),
+                                               in_smem ? sizeof(double) * packed : 0, cx.stream, G, bp, p, R, in_smem,
+                                               scratch, tol, cx.st, static_cast<const int*>(skip));
+            if (le_ != cudaSuccess) return le_;
+        }
     } else {
         const int in_smem = (sizeof(float) * packed <= 200 * 1024) ? 1 : 0;
-        k_cholesky<float><<<1, 256, in_smem ? sizeof(float) * packed : 0, cx.stream>>>(G, bp, p, R, in_smem,
-                                                                                       scratch, tol, cx.st);
+        {
+            const cudaError_t le_ = launch_pdl(k_cholesky<float>, dim3(1), dim3(256),
+                                               in_smem ? sizeof(float) * packed : 0, cx.stream, G, bp, p, R, in_smem,
+                                               scratch, tol, cx.st, static_cast<const int*>(skip));
+            if (le_ != cudaSuccess) return le_;
+        }
     }
     cx.launches++;
     cudaError_t e = cudaGetLastError();
@@ -860,7 +931,11 @@ cudaError_t chol_inv(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, bool
     const int staged_cols = (int)std::min<int64_t>(bp, (200 * 1024 / 8) / bp - 5);
     const int cmax_all = std::min(bp, staged_cols);
     const size_t smem2 = sizeof(double) * (size_t)(5 * bp + (int64_t)bp * std::max(cmax_all, 1));
-    k_tri_inverse<T><<<(bp + 3) / 4, 128, smem2, cx.stream>>>(R, bp, Rinv, staged_cols);
+    {
+        const cudaError_t le_ = launch_pdl(k_tri_inverse<T>, dim3((bp + 3) / 4), dim3(128), smem2, cx.stream, R, bp,
+                                           Rinv, staged_cols, static_cast<const int*>(skip));
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return cudaGetLastError();
 }
@@ -875,7 +950,11 @@ cudaError_t tri_inverse(Ctx& cx, const double* R, int kdim, T* Rinv) {
     const int cmax_all = std::min(kdim, staged_cols);
     const size_t smem2 = sizeof(double) * (size_t)(5 * (int64_t)kdim + (int64_t)kdim * std::max(cmax_all, 1));
     if (smem2 > 200 * 1024) return cudaErrorInvalidValue;
-    k_tri_inverse<T><<<(kdim + 3) / 4, 128, smem2, cx.stream>>>(R, kdim, Rinv, staged_cols);
+    {
+        const cudaError_t le_ = launch_pdl(k_tri_inverse<T>, dim3((kdim + 3) / 4), dim3(128), smem2, cx.stream, R,
+                                           kdim, Rinv, staged_cols, static_cast<const int*>(nullptr));
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return cudaGetLastError();
 }
@@ -883,6 +962,8 @@ cudaError_t tri_inverse(Ctx& cx, const double* R, int kdim, T* Rinv) {
 template <typename T>
 __global__ void k_to_double(int64_t rows, int64_t cols, const T* __restrict__ src, int64_t lds,
                             double* __restrict__ dst, int64_t ldd) {
+    pdl_trigger();
+    pdl_wait();
     const int64_t total = rows * cols;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = e % rows, c = e / rows;
@@ -894,7 +975,11 @@ template <typename T>
 cudaError_t launch_to_double(Ctx& cx, int64_t rows, int64_t cols, const T* src, int64_t lds, double* dst,
                              int64_t ldd) {
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows * cols + 255) / 256, cx.num_sms * 4));
-    k_to_double<T><<<blocks, 256, 0, cx.stream>>>(rows, cols, src, lds, dst, ldd);
+    {
+        const cudaError_t le_ = launch_pdl(k_to_double<T>, dim3(blocks), dim3(256), 0, cx.stream, rows, cols, src, lds,
+                                           dst, ldd);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return cudaGetLastError();
 }
@@ -959,7 +1044,7 @@ cudaError_t downdate_sketch(Ctx& cx, int64_t m, int64_t n, int p, int bp, const 
                                     int64_t, T*, size_t, double*, int, double*);                                 \
     template cudaError_t gemm_tn_f64acc<T>(Ctx&, int64_t, int, int64_t, const T*, int64_t, const T*, int64_t,    \
                                            double*, int64_t, double*, size_t, bool, bool);                        \
-    template cudaError_t chol_inv<T>(Ctx&, double*, int, int, double*, T*, bool, double*, size_t);               \
+    template cudaError_t chol_inv<T>(Ctx&, double*, int, int, double*, T*, bool, double*, size_t, bool);         \
     template cudaError_t downdate_sketch<T>(Ctx&, int64_t, int64_t, int, int, const T*, int64_t, const T*,        \
                                             int64_t, const T*, int64_t, const T*, T*, int64_t, T*, int64_t, T*,   \
                                             size_t, double*, int, double*);                                       \

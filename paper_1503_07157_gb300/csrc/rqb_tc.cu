@@ -1013,6 +1013,8 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_updatew(const __grid_constan
 // binary32 Gaussian (j, col0 + c) for c < p, zero for p <= c < bp.
 __global__ void k_omega_tf32(long long n, long long col0, int p, int bp, uint64_t seed, float* __restrict__ out,
                              long long ldo) {
+    pdl_trigger();
+    pdl_wait();
     const long long total = n * bp;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
@@ -1029,6 +1031,8 @@ __global__ void k_omega_tf32(long long n, long long col0, int p, int bp, uint64_
 __global__ void k_split_q(const float* __restrict__ Qi, long long ldq, long long m, int p, int bp,
                           float* __restrict__ Qhi, float* __restrict__ Qlo, long long ldql, float* __restrict__ Qt,
                           float* __restrict__ Qtl) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ float tile[32][33];
     const long long r0 = (long long)blockIdx.x * 32;
     const int c0 = blockIdx.y * 32;
@@ -1062,6 +1066,8 @@ __global__ void k_split_q(const float* __restrict__ Qi, long long ldq, long long
 template <typename TC>
 __global__ void k_ct_to_omega(const TC* __restrict__ Ct, long long ldc, long long kprev, int np,
                               float* __restrict__ Om, long long ldo) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ TC tile[32][33];
     const long long j0 = (long long)blockIdx.x * 32;
     const int c0 = blockIdx.y * 32;
@@ -1080,6 +1086,8 @@ __global__ void k_ct_to_omega(const TC* __restrict__ Ct, long long ldc, long lon
 // Bs / Bsl (np x n, ld np) from B_i (p x n, ld ldbi); rows p..np-1 zero.
 __global__ void k_stage_b(const float* __restrict__ Bi, long long ldbi, int p, long long n, int np,
                           float* __restrict__ Bs, float* __restrict__ Bsl) {
+    pdl_trigger();
+    pdl_wait();
     const long long total = n * np;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
@@ -1143,6 +1151,8 @@ __device__ __forceinline__ float4 sum_partials(const float* __restrict__ part, c
 
 __global__ void k_reduce_sketch(const float* __restrict__ part, long long U, int C, int P, int G, int np, long long m,
                                 float* Y, long long ldy, const float* sub) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ size_t off[kMaxCover];
     __shared__ int count;
     const int t = blockIdx.x;
@@ -1180,6 +1190,8 @@ __global__ void k_reduce_sketch(const float* __restrict__ part, long long U, int
 __global__ void k_reduce_project(const float* __restrict__ part, long long U, int C, int P, int G, int np, int pcols,
                                  long long n, float* __restrict__ B, long long ldb, float* __restrict__ Bs,
                                  float* __restrict__ Bsl, double* __restrict__ sq_part) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ size_t off[kMaxCover];
     __shared__ int count;
     __shared__ double red[32];
@@ -1216,49 +1228,72 @@ __global__ void k_reduce_project(const float* __restrict__ part, long long U, in
 }
 
 // The panel's coefficient products (the Grams Y^T Y and C^T = Y^T Qbar of
-// lines (3), (3')): out[c + j ldo] (c < pcols, j < n) = the sum, in FP64 and
-// in CTA order, of the FP32 partials of the CTAs covering tile j / 128.  Each
-// partial is one CTA's stretch of the reduction over m, accumulated in FP32
-// by the tensor core and the period drains; the sum across CTAs is FP64.
+// lines (3), (3')): out[c + j ldo] (c < pcols, j < n) = the FP64 sum of the
+// FP32 partials of the CTAs covering tile j / 128.  Each partial is one CTA's
+// stretch of the reduction over m, accumulated in FP32 by the tensor core and
+// the period drains; the sum across CTAs is FP64.  The partials of an entry
+// are cut into four runs of consecutive CTAs; a quarter of the threads sums
+// each run in CTA order, and the four run sums are added in run order (a
+// fixed order, independent of the launch).  sym (a Gram, X = Q): the entries
+// above the diagonal mirror those below it, which are summed once and stored
+// at both positions.
 __global__ void k_reduce_project64(const float* __restrict__ part, long long U, int C, int P, int G, int np,
-                                   int pcols, long long n, double* __restrict__ out, long long ldo) {
+                                   int pcols, long long n, double* __restrict__ out, long long ldo, int sym) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ size_t off[kMaxCover];
     __shared__ int count;
+    __shared__ double runs[3][256];   // run sums 1..3 of the 256 entries in flight
     const int t = blockIdx.x;
     if (threadIdx.x == 0) count = tile_slots(U, C, P, G, np, t, off);
     __syncthreads();
     const int nc = count;
+    const int g = (int)threadIdx.x >> 6, lt = (int)threadIdx.x & 63;
+    const int q0 = nc * g / 4, q1 = nc * (g + 1) / 4;
     const int span = np * kBM / (int)gridDim.y;
     const int i0 = blockIdx.y * span;
-    for (int idx = i0 + 4 * (int)threadIdx.x; idx < i0 + span; idx += 4 * (int)blockDim.x) {   // jl * np + c
+    for (int base = i0; base < i0 + span; base += 256) {   // 64 threads x 4 consecutive entries (jl * np + c)
+        const int idx = base + 4 * lt;
         const int jl = idx / np, c = idx % np;
         const long long j = (long long)t * kBM + jl;
-        if (j >= n) continue;
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        int q = 0;
-        for (; q + 4 <= nc; q += 4) {   // four partial loads in flight, added in CTA order
-            float4 v[4];
+        const bool live = idx < i0 + span && j < n && !(sym && c + 3 < j);
+        double a[4] = {0.0, 0.0, 0.0, 0.0};
+        if (live) {
+            int q = q0;
+            for (; q + 4 <= q1; q += 4) {   // four partial loads in flight
+                float4 v[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = *reinterpret_cast<const float4*>(part + off[q + u] + idx);
+                for (int u = 0; u < 4; ++u) v[u] = *reinterpret_cast<const float4*>(part + off[q + u] + idx);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                a0 += (double)v[u].x;
-                a1 += (double)v[u].y;
-                a2 += (double)v[u].z;
-                a3 += (double)v[u].w;
+                for (int u = 0; u < 4; ++u) {
+                    a[0] += (double)v[u].x;
+                    a[1] += (double)v[u].y;
+                    a[2] += (double)v[u].z;
+                    a[3] += (double)v[u].w;
+                }
+            }
+            for (; q < q1; ++q) {
+                const float4 v = *reinterpret_cast<const float4*>(part + off[q] + idx);
+                a[0] += (double)v.x;
+                a[1] += (double)v.y;
+                a[2] += (double)v.z;
+                a[3] += (double)v.w;
             }
         }
-        for (; q < nc; ++q) {
-            const float4 v = *reinterpret_cast<const float4*>(part + off[q] + idx);
-            a0 += (double)v.x;
-            a1 += (double)v.y;
-            a2 += (double)v.z;
-            a3 += (double)v.w;
-        }
-        const double a[4] = {a0, a1, a2, a3};
+        if (g > 0) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (c + i < pcols) out[c + i + j * ldo] = a[i];
+            for (int i = 0; i < 4; ++i) runs[g - 1][4 * lt + i] = a[i];
+        }
+        __syncthreads();
+        if (g == 0 && live) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const double v = ((a[i] + runs[0][4 * lt + i]) + runs[1][4 * lt + i]) + runs[2][4 * lt + i];
+                if (c + i < pcols) out[c + i + j * ldo] = v;
+                if (sym && c + i > j) out[j + (long long)(c + i) * ldo] = v;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -1681,6 +1716,8 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
 template <typename OutT>
 __global__ void k_omega_bf16(long long n, long long col0, int p, int bp, uint64_t seed, OutT* __restrict__ out,
                              long long ldo) {
+    pdl_trigger();
+    pdl_wait();
     const long long total = n * bp;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
@@ -1697,6 +1734,8 @@ __global__ void k_omega_bf16(long long n, long long col0, int p, int bp, uint64_
 __global__ void k_split_q16(const float* __restrict__ Qi, long long ldq, long long m, int p, int bp,
                             __nv_bfloat16* __restrict__ Qhi, __nv_bfloat16* __restrict__ Qlo, long long ldql,
                             __nv_bfloat16* __restrict__ Qt, __nv_bfloat16* __restrict__ Qtl) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ float tile[32][33];
     const long long r0 = (long long)blockIdx.x * 32;
     const int c0 = blockIdx.y * 32;
@@ -1720,6 +1759,8 @@ __global__ void k_split_q16(const float* __restrict__ Qi, long long ldq, long lo
 // Bs / Bsl (bp x n, ld bp, BF16 hi / lo) from B_i (p x n, ld ldbi).
 __global__ void k_stage_b16(const float* __restrict__ Bi, long long ldbi, int p, long long n, int bp,
                             __nv_bfloat16* __restrict__ Bs, __nv_bfloat16* __restrict__ Bsl) {
+    pdl_trigger();
+    pdl_wait();
     const long long total = n * bp;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
@@ -1734,6 +1775,8 @@ __global__ void k_reduce_project16(const float* __restrict__ part, long long U, 
                                    int pcols, long long n, float* __restrict__ B, long long ldb,
                                    __nv_bfloat16* __restrict__ Bs, __nv_bfloat16* __restrict__ Bsl,
                                    double* __restrict__ sq_part) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ size_t off[kMaxCover];
     __shared__ int count;
     __shared__ double red[32];
@@ -1959,7 +2002,11 @@ size_t partial_floats(long long m, long long n, int np, int sms) {
 cudaError_t omega(Ctx& cx, long long n, long long col0, int p, int np, uint64_t seed, float* out, long long ldo) {
     const long long total = n * np;
     const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * cx.num_sms);
-    k_omega_tf32<<<blocks, 256, 0, cx.stream>>>(n, col0, p, np, seed, out, ldo);
+    {
+        const cudaError_t le_ = launch_pdl(k_omega_tf32, dim3(blocks), dim3(256), 0, cx.stream, n, col0, p, np, seed,
+                                           out, ldo);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return cudaGetLastError();
 }
@@ -1967,7 +2014,11 @@ cudaError_t omega(Ctx& cx, long long n, long long col0, int p, int np, uint64_t 
 cudaError_t split_q(Ctx& cx, const float* Qi, long long ldq, long long m, int p, int np, float* Qhi, float* Qlo,
                     long long ldql, float* Qt, float* Qtl) {
     dim3 grid((unsigned)((m + 31) / 32), (unsigned)(np / 32));
-    k_split_q<<<grid, 256, 0, cx.stream>>>(Qi, ldq, m, p, np, Qhi, Qlo, ldql, Qt, Qtl);
+    {
+        const cudaError_t le_ = launch_pdl(k_split_q, dim3(grid), dim3(256), 0, cx.stream, Qi, ldq, m, p, np, Qhi, Qlo,
+                                           ldql, Qt, Qtl);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return cudaGetLastError();
 }
@@ -1975,7 +2026,11 @@ cudaError_t split_q(Ctx& cx, const float* Qi, long long ldq, long long m, int p,
 cudaError_t stage_b(Ctx& cx, const float* Bi, long long ldbi, int p, long long n, int np, float* Bs, float* Bsl) {
     const long long total = n * np;
     const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * cx.num_sms);
-    k_stage_b<<<blocks, 256, 0, cx.stream>>>(Bi, ldbi, p, n, np, Bs, Bsl);
+    {
+        const cudaError_t le_ = launch_pdl(k_stage_b, dim3(blocks), dim3(256), 0, cx.stream, Bi, ldbi, p, n, np, Bs,
+                                           Bsl);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return cudaGetLastError();
 }
@@ -1998,8 +2053,11 @@ cudaError_t sketch(Ctx& cx, const float* X, long long ldx, long long m, long lon
     if ((e = launch_streamk<kSketch>(cx, p, np)) != cudaSuccess) return e;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const dim3 rgrid(pl.tiles, reduce_slices(pl.tiles, cx.num_sms));
-    k_reduce_sketch<<<rgrid, 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, m, Y,
-                                                                           ldy, nullptr);
+    {
+        const cudaError_t le_ = launch_pdl(k_reduce_sketch, dim3(rgrid), dim3(256), 0, cx.stream, part, pl.U, pl.C,
+                                           pl.P, pl.G, np, m, Y, ldy, nullptr);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return nrm_out ? launch_sum_doubles(cx, nrm_part, pl.P, nrm_out) : cudaSuccess;
@@ -2021,8 +2079,11 @@ cudaError_t sketch_sub(Ctx& cx, const float* X, long long ldx, long long m, long
     p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
     if ((e = launch_streamk<kSketch>(cx, p, np)) != cudaSuccess) return e;
     const dim3 rgrid(pl.tiles, reduce_slices(pl.tiles, cx.num_sms));
-    k_reduce_sketch<<<rgrid, 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, m, Y,
-                                                                           ldy, sub);
+    {
+        const cudaError_t le_ = launch_pdl(k_reduce_sketch, dim3(rgrid), dim3(256), 0, cx.stream, part, pl.U, pl.C,
+                                           pl.P, pl.G, np, m, Y, ldy, sub);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return cudaGetLastError();
 }
@@ -2043,8 +2104,11 @@ cudaError_t project(Ctx& cx, const float* X, long long ldx, long long m, long lo
     p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
     if ((e = launch_streamk<kProject>(cx, p, np)) != cudaSuccess) return e;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_reduce_project<<<dim3(pl.tiles, sl), 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, pcols,
-                                                                            n, B, ldb, Bs, Bsl, sq_part);
+    {
+        const cudaError_t le_ = launch_pdl(k_reduce_project, dim3(pl.tiles, sl), dim3(256), 0, cx.stream, part,
+                                           pl.U, pl.C, pl.P, pl.G, np, pcols, n, B, ldb, Bs, Bsl, sq_part);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return launch_sum_doubles(cx, sq_part, pl.tiles * sl, sq_out);
@@ -2054,7 +2118,7 @@ cudaError_t project(Ctx& cx, const float* X, long long ldx, long long m, long lo
 // partials summed in FP64 (k_reduce_project64); no staged copies, no norm.
 cudaError_t project64(Ctx& cx, const float* X, long long ldx, long long m, long long n, const float* Qhi,
                       const float* Qlo, long long ldql, int pcols, int np, double* out, long long ldo, float* part,
-                      size_t part_cap) {
+                      size_t part_cap, bool sym = false) {
     StreamKParams p;
     cudaError_t e;
     if ((e = make_map(&p.mx, X, m, n, ldx, kKC, kBM, true)) != cudaSuccess) return e;
@@ -2068,8 +2132,11 @@ cudaError_t project64(Ctx& cx, const float* X, long long ldx, long long m, long 
     p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
     if ((e = launch_streamk<kProject>(cx, p, np)) != cudaSuccess) return e;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_reduce_project64<<<dim3(pl.tiles, sl), 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, pcols, n,
-                                                                  out, ldo);
+    {
+        const cudaError_t le_ = launch_pdl(k_reduce_project64, dim3(pl.tiles, sl), dim3(256), 0, cx.stream, part,
+                                           pl.U, pl.C, pl.P, pl.G, np, pcols, n, out, ldo, sym ? 1 : 0);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return cudaGetLastError();
 }
@@ -2145,11 +2212,14 @@ cudaError_t gram(Ctx& cx, const float* Y, long long ldy, long long m, int np, co
                  bool keep_split) {
     cudaError_t e;
     dim3 g1((unsigned)((m + 31) / 32), (unsigned)(np / 32));
-    k_split_q<<<g1, 256, 0, cx.stream>>>(Y, ldy, m, np, np, w.Yhi, w.Ylo, w.ldyl, keep_split ? w.Yt : nullptr,
-                                         keep_split ? w.Ytl : nullptr);
+    {
+        const cudaError_t le_ = launch_pdl(k_split_q, dim3(g1), dim3(256), 0, cx.stream, Y, ldy, m, np, np, w.Yhi,
+                                           w.Ylo, w.ldyl, keep_split ? w.Yt : nullptr, keep_split ? w.Ytl : nullptr);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return project64(cx, Y, ldy, m, np, w.Yhi, w.Ylo, w.ldyl, np, np, G, np, w.part, w.part_cap);
+    return project64(cx, Y, ldy, m, np, w.Yhi, w.Ylo, w.ldyl, np, np, G, np, w.part, w.part_cap, true);
 }
 
 // Out (m x np, ld ldo) = Y (m x np, ld ldy) C (np x np, ld ldc), split-TF32.
@@ -2162,13 +2232,21 @@ cudaError_t product(Ctx& cx, const float* Y, long long ldy, long long m, const f
     cudaError_t e;
     if (!presplit) {
         dim3 g1((unsigned)((m + 31) / 32), (unsigned)(np / 32));
-        k_split_q<<<g1, 256, 0, cx.stream>>>(Y, ldy, m, np, np, nullptr, nullptr, 0, w.Yt, w.Ytl);
+        {
+            const cudaError_t le_ = launch_pdl(k_split_q, dim3(g1), dim3(256), 0, cx.stream, Y, ldy, m, np, np,
+                                               nullptr, nullptr, 0, w.Yt, w.Ytl);
+            if (le_ != cudaSuccess) return le_;
+        }
         cx.launches++;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const long long total = (long long)np * np;
     const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * cx.num_sms);
-    k_stage_b<<<blocks, 256, 0, cx.stream>>>(C, ldc, np, np, np, w.Bs, w.Bsl);
+    {
+        const cudaError_t le_ = launch_pdl(k_stage_b, dim3(blocks), dim3(256), 0, cx.stream, C, ldc, np, np, np, w.Bs,
+                                           w.Bsl);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return update_impl(cx, nullptr, 0, Out, ldo, m, np, w.Yt, w.Ytl, w.Bs, w.Bsl, np, nullptr, 0, nullptr, 0);
@@ -2188,7 +2266,11 @@ cudaError_t omega16(Ctx& cx, long long n, long long col0, int p, int np, uint64_
                     long long ldo) {
     const long long total = n * np;
     const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * cx.num_sms);
-    k_omega_bf16<__nv_bfloat16><<<blocks, 256, 0, cx.stream>>>(n, col0, p, np, seed, out, ldo);
+    {
+        const cudaError_t le_ = launch_pdl(k_omega_bf16<__nv_bfloat16>, dim3(blocks), dim3(256), 0, cx.stream, n, col0,
+                                           p, np, seed, out, ldo);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return cudaGetLastError();
 }
@@ -2197,7 +2279,11 @@ cudaError_t omega16_f32(Ctx& cx, long long n, long long col0, int p, int np, uin
                         long long ldo) {
     const long long total = n * np;
     const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * cx.num_sms);
-    k_omega_bf16<float><<<blocks, 256, 0, cx.stream>>>(n, col0, p, np, seed, out, ldo);
+    {
+        const cudaError_t le_ = launch_pdl(k_omega_bf16<float>, dim3(blocks), dim3(256), 0, cx.stream, n, col0, p, np,
+                                           seed, out, ldo);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return cudaGetLastError();
 }
@@ -2205,7 +2291,11 @@ cudaError_t omega16_f32(Ctx& cx, long long n, long long col0, int p, int np, uin
 cudaError_t split_q16(Ctx& cx, const float* Qi, long long ldq, long long m, int p, int np, __nv_bfloat16* Qhi,
                       __nv_bfloat16* Qlo, long long ldql, __nv_bfloat16* Qt, __nv_bfloat16* Qtl) {
     dim3 grid((unsigned)((m + 31) / 32), (unsigned)(np / 32));
-    k_split_q16<<<grid, 256, 0, cx.stream>>>(Qi, ldq, m, p, np, Qhi, Qlo, ldql, Qt, Qtl);
+    {
+        const cudaError_t le_ = launch_pdl(k_split_q16, dim3(grid), dim3(256), 0, cx.stream, Qi, ldq, m, p, np, Qhi,
+                                           Qlo, ldql, Qt, Qtl);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return cudaGetLastError();
 }
@@ -2214,7 +2304,11 @@ cudaError_t stage_b16(Ctx& cx, const float* Bi, long long ldbi, int p, long long
                       __nv_bfloat16* Bsl) {
     const long long total = n * np;
     const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * cx.num_sms);
-    k_stage_b16<<<blocks, 256, 0, cx.stream>>>(Bi, ldbi, p, n, np, Bs, Bsl);
+    {
+        const cudaError_t le_ = launch_pdl(k_stage_b16, dim3(blocks), dim3(256), 0, cx.stream, Bi, ldbi, p, n, np, Bs,
+                                           Bsl);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return cudaGetLastError();
 }
@@ -2246,8 +2340,11 @@ cudaError_t sketch16(Ctx& cx, const __nv_bfloat16* X, long long ldx, long long m
     e = gen ? launch_streamk16<kSketch, true>(cx, p, np) : launch_streamk16<kSketch>(cx, p, np);
     if (e != cudaSuccess) return e;
     const dim3 rgrid(pl.tiles, reduce_slices(pl.tiles, cx.num_sms));
-    k_reduce_sketch<<<rgrid, 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np, m, Y,
-                                                                           ldy, nullptr);
+    {
+        const cudaError_t le_ = launch_pdl(k_reduce_sketch, dim3(rgrid), dim3(256), 0, cx.stream, part, pl.U, pl.C,
+                                           pl.P, pl.G, np, m, Y, ldy, nullptr);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return nrm_out ? launch_sum_doubles(cx, nrm_part, pl.P, nrm_out) : cudaSuccess;
@@ -2269,8 +2366,11 @@ cudaError_t project16(Ctx& cx, const __nv_bfloat16* X, long long ldx, long long 
     p.st = cx.st;
     p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
     if ((e = launch_streamk16<kProject>(cx, p, np)) != cudaSuccess) return e;
-    k_reduce_project16<<<dim3(pl.tiles, sl), 256, 0, cx.stream>>>(part, pl.U, pl.C, pl.P, pl.G, np,
-                                                                              pcols, n, B, ldb, Bs, Bsl, sq_part);
+    {
+        const cudaError_t le_ = launch_pdl(k_reduce_project16, dim3(pl.tiles, sl), dim3(256), 0, cx.stream, part,
+                                           pl.U, pl.C, pl.P, pl.G, np, pcols, n, B, ldb, Bs, Bsl, sq_part);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return launch_sum_doubles(cx, sq_part, pl.tiles * sl, sq_out);
@@ -2337,7 +2437,11 @@ cudaError_t reproject(Ctx& cx, const float* Qbar, long long ldq, long long m, lo
     // C^T = Y^T Qbar (np x kprev): the projection kernel with X = Qbar and Y in
     // the place of Q_i
     dim3 g1((unsigned)((m + 31) / 32), (unsigned)(np / 32));
-    k_split_q<<<g1, 256, 0, cx.stream>>>(Y, ldy, m, np, np, w.Yhi, w.Ylo, w.ldyl, nullptr, nullptr);
+    {
+        const cudaError_t le_ = launch_pdl(k_split_q, dim3(g1), dim3(256), 0, cx.stream, Y, ldy, m, np, np, w.Yhi,
+                                           w.Ylo, w.ldyl, nullptr, nullptr);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = project64(cx, Qbar, ldq, m, kprev, w.Yhi, w.Ylo, w.ldyl, np, np, w.Ct64, np, w.part,
@@ -2345,7 +2449,11 @@ cudaError_t reproject(Ctx& cx, const float* Qbar, long long ldq, long long m, lo
         return e;
     // C in the sketch's Omega layout (rounded to TF32), then Y -= Qbar C
     dim3 g2((unsigned)((kprev + 31) / 32), (unsigned)(np / 32));
-    k_ct_to_omega<double><<<g2, 256, 0, cx.stream>>>(w.Ct64, np, kprev, np, w.Om, w.ldom);
+    {
+        const cudaError_t le_ = launch_pdl(k_ct_to_omega<double>, dim3(g2), dim3(256), 0, cx.stream, w.Ct64, np, kprev,
+                                           np, w.Om, w.ldom);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return sketch_sub(cx, Qbar, ldq, m, kprev, w.Om, w.ldom, np, Y, ldy, Y, w.part, w.part_cap);

@@ -62,7 +62,8 @@ class rqb_stats(ctypes.Structure):
                 ("E", ctypes.c_double * RQB_MAX_TRACKED_BLOCKS), ("D", ctypes.c_double * RQB_MAX_TRACKED_BLOCKS),
                 ("kernel_launches", ctypes.c_int32), ("svd_sweeps", ctypes.c_int32),
                 ("phase_ms", ctypes.c_double * RQB_NUM_PHASES), ("phase_calls", ctypes.c_int32 * RQB_NUM_PHASES),
-                ("gram_fallbacks", ctypes.c_int32), ("tile_width", ctypes.c_int32)]
+                ("gram_fallbacks", ctypes.c_int32), ("tile_width", ctypes.c_int32),
+                ("near_identity", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _LIB = None
@@ -177,6 +178,7 @@ class Stats:
     phase_calls: list
     gram_fallbacks: int = 0
     tile_width: int = 0
+    near_identity: int = 0
 
 
 class Handle:
@@ -305,7 +307,8 @@ class Handle:
         nb = min(int(st.blocks), RQB_MAX_TRACKED_BLOCKS)
         return Stats(int(st.k), int(st.blocks), int(st.status), int(st.direct_tests), float(st.normA2),
                      float(st.eps), list(st.E[:nb]), list(st.D[:nb]), int(st.kernel_launches),
-                     list(st.phase_ms), list(st.phase_calls), int(st.gram_fallbacks), int(st.tile_width))
+                     list(st.phase_ms), list(st.phase_calls), int(st.gram_fallbacks), int(st.tile_width),
+                     int(st.near_identity))
 
     # -- steps ---------------------------------------------------------------
     def rqb_omega(self, n: int, col0: int, ncols: int, seed: int) -> torch.Tensor:

@@ -112,6 +112,36 @@ def test_orth_fp32(orc, h32, m, p, kprev):
     assert np.abs(Qi - Qo).max() <= 1e-3
 
 
+@pytest.mark.parametrize("dtype,cond,tol_q,route", [(torch.float64, 1e1, 1e-10, 1), (torch.float64, 1e7, 1e-7, None),
+                                                    (torch.float32, 1e1, 1e-4, 1), (torch.float32, 1e5, 5e-2, 0)])
+@pytest.mark.parametrize("m,p", [(3000, 128), (2000, 256), (1500, 64)])
+def test_orth_second_pass_routes(orc, rqb_lib, dtype, cond, tol_q, route, m, p):
+    """Lines (3), (3'): the second CholeskyQR pass takes its factor from the
+    near-identity expansion when the first pass leaves ||Y1^T Y1 - I||_F below
+    tau (FP64: 2^-28, FP32: 1e-4) and from the elimination otherwise.  The
+    first pass leaves about u kappa(Y) there (the FP32 product Y R^-1 on the
+    FP32 handle): kappa = 10 takes the expansion on both handles, kappa = 1e5
+    the elimination in FP32 (1e7 in FP64 is near tau and may take either).
+    Both routes give an orthonormal Q_i equal to the oracle's, and
+    stats.near_identity reports the route.  (FP64 handles take blocks of up
+    to 128 columns.)"""
+    if dtype == torch.float64 and p > 128:
+        p = 100
+    rng = np.random.default_rng(int(m + p + np.log10(cond)))
+    Y = np.linalg.qr(rng.standard_normal((m, p)))[0] @ np.diag(np.logspace(0, -np.log10(cond), p))
+    Y = Y @ np.linalg.qr(rng.standard_normal((p, p)))[0]
+    if dtype == torch.float32:
+        Y = Y.astype(np.float32).astype(np.float64)
+    with rqb_lib.Handle(dtype) as h:
+        Qi = to_np(h.rqb_orth(to_dev(Y, dtype), None))
+        st = h.rqb_get_stats()
+    Qo = orc.orth_reproject(Y, None)
+    assert orth_err(Qi) <= (1e-13 if dtype == torch.float64 else 1e-5)
+    assert np.abs(Qi - Qo).max() <= tol_q
+    if route is not None:
+        assert st.near_identity == route
+
+
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 1e-5)])
 @pytest.mark.parametrize("m,n,p", [(3000, 2000, 50), (1037, 777, 37), (500, 4100, 128)])
 def test_project(orc, rqb_lib, dtype, tol, m, n, p):

@@ -506,39 +506,120 @@ __global__ void __launch_bounds__(256) k_near_id_norm(const double* __restrict__
     }
 }
 
-// Every CTA sums the parts in order and takes the same decision; when
-// ||E||_F^2 <= tau2 the CTAs write their share of R = I + U (FP64) and of
-// R^{-1} = I - U (T), and CTA 0 sets *skip = 1, else *skip = 0.
+// Every CTA sums the parts in order and takes the same decision:
+//   ||E||_F^2 <= tau2:  first order, the CTAs write their share of R = I + U
+//                       (FP64) and R^{-1} = I - U (T); *skip = 1, *iter = 0;
+//   <= tau2i:           the iterated expansion (k_near_id_step): the CTAs
+//                       write E (FP32) to Ef and the first iterate U to X;
+//                       *skip = 1, *iter = 1;
+//   else:               *skip = 0, *iter = 0 (the elimination runs).
 template <typename T>
 __global__ void __launch_bounds__(256) k_near_id_apply(const double* __restrict__ G, int bp, int p,
-                                                       const double* __restrict__ part, double tau2,
+                                                       const double* __restrict__ part, double tau2, double tau2i,
                                                        double* __restrict__ R, T* __restrict__ Rinv,
-                                                       int* __restrict__ skip, DevState* st) {
+                                                       float* __restrict__ Ef, float* __restrict__ X,
+                                                       int* __restrict__ skip, int* __restrict__ iter,
+                                                       DevState* st) {
     pdl_trigger();
     pdl_wait();
-    __shared__ int ok;
+    __shared__ int mode;
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int b = 0; b < kNearIdParts; ++b) t += part[b];
-        ok = (t <= tau2) ? 1 : 0;   // false for a NaN norm
+        mode = (t <= tau2) ? 1 : (t <= tau2i) ? 2 : 0;   // 0 for a NaN norm
         if (blockIdx.x == 0) {
-            *skip = ok;
-            if (ok && st) atomicAdd(&st->near_id, 1);
+            *skip = mode != 0;
+            *iter = mode == 2;
+            if (mode != 0 && st) atomicAdd(&st->near_id, 1);
         }
     }
     __syncthreads();
-    if (!ok) return;
+    if (mode == 0) return;
     const int total = bp * bp;
     for (int e = blockIdx.x * 256 + threadIdx.x; e < total; e += gridDim.x * 256) {
         const int r = e % bp, c = e / bp;
+        const bool in = r < p && c < p;
         double u = 0.0;                      // U_rc
-        if (r < p && c < p) {
+        if (in) {
             if (r < c) u = G[e];
             else if (r == c) u = 0.5 * (G[e] - 1.0);
         }
-        const double id = (r == c) ? 1.0 : 0.0;
-        R[e] = (r <= c) ? id + u : 0.0;
-        Rinv[e] = (T)((r <= c) ? id - u : 0.0);
+        if (mode == 1) {
+            const double id = (r == c) ? 1.0 : 0.0;
+            R[e] = (r <= c) ? id + u : 0.0;
+            Rinv[e] = (T)((r <= c) ? id - u : 0.0);
+        } else {
+            Ef[e] = in ? (float)(G[e] - (r == c ? 1.0 : 0.0)) : 0.f;
+            X[e] = (float)u;
+            if (r > c) {   // the steps write the upper triangles only
+                R[e] = 0.0;
+                Rinv[e] = T(0);
+            }
+        }
+    }
+}
+
+// One step of the iterated expansion on the 32 x 32 tiles (I, J), I <= J, of
+// bp x bp upper-triangular FP32 matrices (column-major), one tile per CTA; it
+// runs only when *iter is set.
+//   MODE 0, the fixed point X = Phi(E - X^T X) of R = I + X (Phi: the upper
+//          triangle with the diagonal halved): Out = Phi(Ef - In^T In); with
+//          last, also R = I + Out (FP64) and Z = I - Out.
+//   MODE 1, R^{-1} = sum_j (-X)^j by Horner: Out = I - X In; with last, also
+//          Rinv = Out.
+// From X_1 = Phi(E) the k-th iterate is within ||E||^(k+1) / 2 of the exact
+// X (the map contracts by about ||E||), and j terms of the series leave
+// ||X||^(j+1): at ||E||_F <= 2e-2, X_4 and four terms are within 2e-9.
+template <int MODE, typename T>
+__global__ void __launch_bounds__(256) k_near_id_step(const float* __restrict__ Ef, const float* __restrict__ X,
+                                                      const float* __restrict__ In, float* __restrict__ Out, int bp,
+                                                      int last, double* __restrict__ R, float* __restrict__ Z,
+                                                      T* __restrict__ Rinv, const int* __restrict__ iter) {
+    pdl_trigger();
+    pdl_wait();
+    if (!*iter) return;
+    __shared__ float As[kNb][kNb + 1];   // As[l][r]
+    __shared__ float Bs[kNb][kNb + 1];   // Bs[l][c]
+    int J = 0;
+    while ((J + 1) * (J + 2) / 2 <= (int)blockIdx.x) ++J;
+    const int I = (int)blockIdx.x - J * (J + 1) / 2;
+    const int tid = threadIdx.x, lr = tid & 31, lc = (tid >> 5) * 4;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    // MODE 0: sum over l of In(l, i) In(l, j), l <= i; MODE 1: X(i, l) In(l, j), i <= l <= j
+    const int L0 = (MODE == 0) ? 0 : I, L1 = (MODE == 0) ? I : J;
+    for (int L = L0; L <= L1; ++L) {
+        for (int e = tid; e < kNb * kNb; e += 256) {
+            const int a = e & 31, b2 = e >> 5;
+            if (MODE == 0) As[a][b2] = In[(L * kNb + a) + (int64_t)(I * kNb + b2) * bp];
+            else As[b2][a] = X[(I * kNb + a) + (int64_t)(L * kNb + b2) * bp];
+            Bs[a][b2] = In[(L * kNb + a) + (int64_t)(J * kNb + b2) * bp];
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int l = 0; l < kNb; ++l) {
+            const float av = As[l][lr];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = fmaf(av, Bs[l][lc + q], acc[q]);
+        }
+        __syncthreads();
+    }
+    const int i = I * kNb + lr;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int j = J * kNb + lc + q;
+        const int64_t o = i + (int64_t)j * bp;
+        float v;
+        if (MODE == 0) v = (i < j) ? Ef[o] - acc[q] : (i == j) ? 0.5f * (Ef[o] - acc[q]) : 0.f;
+        else v = (i <= j) ? ((i == j) ? 1.f : 0.f) - acc[q] : 0.f;
+        Out[o] = v;
+        if (last) {
+            if (MODE == 0) {
+                R[o] = (i <= j) ? ((i == j) ? 1.0 : 0.0) + (double)v : 0.0;
+                Z[o] = (i <= j) ? ((i == j) ? 1.f : 0.f) - v : 0.f;
+            } else {
+                Rinv[o] = (T)v;
+            }
+        }
     }
 }
 
@@ -619,18 +700,50 @@ cudaError_t chol_inv_blocked(Ctx& cx, double* G, int bp, int p, double* R, T* Ri
     return cudaGetLastError();
 }
 
-// Two launches of kNearIdParts CTAs: the norm's parts, then the decision and
-// the factor.
+// The norm's parts, then the decision and the first-order factor (kNearIdParts
+// CTAs each), then for FP32 factors the iterated route's six steps.
 template <typename T>
 cudaError_t near_identity(Ctx& cx, const double* G, int bp, int p, double* R, T* Rinv, double tau, double* work,
                           int* skip) {
     cudaError_t e = launch_pdl(k_near_id_norm, dim3(kNearIdParts), dim3(256), 0, cx.stream, G, bp, p, work);
     if (e != cudaSuccess) return e;
     cx.launches++;
+    // the iterated route for FP32 factors (whose tau leaves most tensor-core
+    // panels above it): three fixed-point steps and three series steps on the
+    // FP32 work matrices after the parts and the flags
+    constexpr bool kIter = sizeof(T) == 4;
+    const double tau_i = kIter ? 2e-2 : 0.0;
+    const size_t sq = (size_t)bp * bp;
+    float* fw = reinterpret_cast<float*>(work + kNearIdParts + 2);
+    float *Ef = fw, *Xa = fw + sq, *Xb = fw + 2 * sq, *Za = fw + 3 * sq, *Zb = fw + 4 * sq;
+    int* iter = skip + 1;
     e = launch_pdl(k_near_id_apply<T>, dim3(kNearIdParts), dim3(256), 0, cx.stream, G, bp, p,
-                   static_cast<const double*>(work), tau * tau, R, Rinv, skip, cx.st);
+                   static_cast<const double*>(work), tau * tau, tau_i * tau_i, R, Rinv, Ef, Xa, skip, iter, cx.st);
     if (e != cudaSuccess) return e;
     cx.launches++;
+    if constexpr (kIter) {
+        const int nblk = bp / kNb;
+        const dim3 gt(nblk * (nblk + 1) / 2);
+        const float* X0in[3] = {Xa, Xb, Xa};
+        float* X0out[3] = {Xb, Xa, Xb};
+        for (int k = 0; k < 3; ++k) {
+            e = launch_pdl(k_near_id_step<0, T>, gt, dim3(256), 0, cx.stream, static_cast<const float*>(Ef),
+                           static_cast<const float*>(nullptr), X0in[k], X0out[k], bp, k == 2 ? 1 : 0, R, Za,
+                           static_cast<T*>(nullptr), static_cast<const int*>(iter));
+            if (e != cudaSuccess) return e;
+            cx.launches++;
+        }
+        const float* Zin[3] = {Za, Zb, Za};
+        float* Zout[3] = {Zb, Za, Zb};
+        for (int k = 0; k < 3; ++k) {
+            e = launch_pdl(k_near_id_step<1, T>, gt, dim3(256), 0, cx.stream, static_cast<const float*>(nullptr),
+                           static_cast<const float*>(Xb), Zin[k], Zout[k], bp, k == 2 ? 1 : 0,
+                           static_cast<double*>(nullptr), static_cast<float*>(nullptr), Rinv,
+                           static_cast<const int*>(iter));
+            if (e != cudaSuccess) return e;
+            cx.launches++;
+        }
+    }
     return cudaGetLastError();
 }
 

@@ -133,8 +133,10 @@ cudaError_t chol_inv_blocked(Ctx& cx, double* G, int bp, int p, double* R, T* Ri
 // Second CholeskyQR pass (rqb_chol.cu): R and Rinv by the near-identity
 // expansion when ||G - I||_F <= tau, with *skip (device) set to 1 so that the
 // elimination launched after it returns at once, else *skip = 0.  work holds
-// kNearIdParts doubles.
+// kNearIdWork(bp) doubles (the norm's parts, the flags and, for FP32
+// factors, the iterated route's five bp x bp FP32 matrices).
 constexpr int kNearIdParts = 64;
+inline size_t kNearIdWork(int bp) { return kNearIdParts + 2 + (5 * (size_t)bp * bp + 1) / 2; }
 template <typename T>
 cudaError_t near_identity(Ctx& cx, const double* G, int bp, int p, double* R, T* Rinv, double tau, double* work,
                           int* skip);

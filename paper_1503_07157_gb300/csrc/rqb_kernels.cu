@@ -890,14 +890,15 @@ cudaError_t chol_inv(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, bool
     const size_t sq = (size_t)bp * bp;
     const size_t packed = (size_t)bp * (bp + 1) / 2;
     if (scratch_doubles < sq) return cudaErrorInvalidValue;
-    // second pass: the near-identity expansion first; its norm parts and flag
-    // sit past the 3 bp^2 + bp doubles the elimination uses of scratch.  The
-    // terms it drops are O(||G - I||^2): tau^2 = 2^-56 for an FP64 factor,
-    // 1e-8 for an FP32 one, both below the unit roundoff
+    // second pass: the near-identity expansion first; its work sits past the
+    // 3 bp^2 + bp doubles the elimination uses of scratch.  First order drops
+    // O(||G - I||^2): tau^2 = 2^-56 for an FP64 factor, 1e-8 for an FP32 one,
+    // both below the unit roundoff; FP32 factors up to ||G - I||_F = 2e-2
+    // take the iterated expansion
     int* skip = nullptr;
     if (second_pass) {
         const size_t at = 3 * sq + (size_t)bp;
-        if (scratch_doubles < at + kNearIdParts + 1) return cudaErrorInvalidValue;
+        if (scratch_doubles < at + kNearIdWork(bp)) return cudaErrorInvalidValue;
         skip = reinterpret_cast<int*>(scratch + at + kNearIdParts);
         const double tau = fp64_factor ? 0x1p-28 : 1e-4;
         cudaError_t en = near_identity<T>(cx, G, bp, p, R, Rinv, tau, scratch + at, skip);

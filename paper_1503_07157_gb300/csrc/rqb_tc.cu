@@ -1289,7 +1289,8 @@ __global__ void k_reduce_project64(const float* __restrict__ part, long long U, 
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const double v = ((a[i] + runs[0][4 * lt + i]) + runs[1][4 * lt + i]) + runs[2][4 * lt + i];
-                if (c + i < pcols) out[c + i + j * ldo] = v;
+                // sym: every entry written once, from the lower triangle
+                if (c + i < pcols && (!sym || c + i >= j)) out[c + i + j * ldo] = v;
                 if (sym && c + i > j) out[j + (long long)(c + i) * ldo] = v;
             }
         }

@@ -7,7 +7,8 @@ so the arithmetic is the same as with ordinary launches.  The same seeded
 factorizations run in two child processes, one with RQB_PDL=0 (ordinary
 launches; the switch is read once per process) and one with the default, and
 their Q, B and k must agree bit for bit on every handle: FP64, plain FP32
-(blocked Cholesky at b = 256), split-TF32 and BF16 storage.
+(blocked Cholesky at b = 256), split-TF32 and BF16 storage.  A second run
+with the default launches checks that the factorization is deterministic.
 """
 import os
 import subprocess
@@ -66,14 +67,27 @@ def _run(tmp_path, tag, pdl):
     return dict(np.load(path))
 
 
-def test_pdl_launches_are_bitwise_neutral(rqb_lib, tmp_path):
-    on = _run(tmp_path, "on", None)
-    off = _run(tmp_path, "off", "0")
-    assert set(on) == set(off)
-    for key in sorted(on):
-        a, b = on[key], off[key]
+def _same(x, y):
+    assert set(x) == set(y)
+    bad = []
+    for key in sorted(x):
+        a, b = x[key], y[key]
         assert a.shape == b.shape, key
-        if key.endswith("_k"):
-            assert a[1] == rqb_lib.RQB_OK, key
         a8, b8 = np.ascontiguousarray(a).view(np.uint8), np.ascontiguousarray(b).view(np.uint8)
-        assert np.array_equal(a8, b8), key
+        if not np.array_equal(a8, b8):
+            bad.append(key)
+    return bad
+
+
+def test_pdl_launches_are_bitwise_neutral(rqb_lib, tmp_path):
+    """Two runs with programmatic launches and one with ordinary launches:
+    the factorization is deterministic (no order-dependent sums, no racing
+    stores) and the launch mode does not change it."""
+    on = _run(tmp_path, "on", None)
+    on2 = _run(tmp_path, "on2", None)
+    off = _run(tmp_path, "off", "0")
+    for key in on:
+        if key.endswith("_k"):
+            assert on[key][1] == rqb_lib.RQB_OK, key
+    assert _same(on, on2) == [], "repeat runs differ"
+    assert _same(on, off) == [], "launch modes differ"

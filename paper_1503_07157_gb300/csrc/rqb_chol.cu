@@ -578,30 +578,36 @@ __global__ void __launch_bounds__(256) k_near_id_step(const float* __restrict__ 
     pdl_trigger();
     pdl_wait();
     if (!*iter) return;
-    __shared__ float As[kNb][kNb + 1];   // As[l][r]
-    __shared__ float Bs[kNb][kNb + 1];   // Bs[l][c]
+    // all the operand tiles of this output tile are loaded at once (up to
+    // 2 x 8 tiles, every load in flight together), then multiplied
+    extern __shared__ float nis[];
+    constexpr int kT = kNb * (kNb + 1);   // one padded 32 x 33 tile
     int J = 0;
     while ((J + 1) * (J + 2) / 2 <= (int)blockIdx.x) ++J;
     const int I = (int)blockIdx.x - J * (J + 1) / 2;
     const int tid = threadIdx.x, lr = tid & 31, lc = (tid >> 5) * 4;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
     // MODE 0: sum over l of In(l, i) In(l, j), l <= i; MODE 1: X(i, l) In(l, j), i <= l <= j
-    const int L0 = (MODE == 0) ? 0 : I, L1 = (MODE == 0) ? I : J;
-    for (int L = L0; L <= L1; ++L) {
-        for (int e = tid; e < kNb * kNb; e += 256) {
-            const int a = e & 31, b2 = e >> 5;
-            if (MODE == 0) As[a][b2] = In[(L * kNb + a) + (int64_t)(I * kNb + b2) * bp];
-            else As[b2][a] = X[(I * kNb + a) + (int64_t)(L * kNb + b2) * bp];
-            Bs[a][b2] = In[(L * kNb + a) + (int64_t)(J * kNb + b2) * bp];
-        }
-        __syncthreads();
+    const int L0 = (MODE == 0) ? 0 : I, L1 = (MODE == 0) ? I : J, nL = L1 - L0 + 1;
+    float* As = nis;              // tile L: As[L][l][r]
+    float* Bs = nis + nL * kT;    // tile L: Bs[L][l][c]
+    for (int e = tid; e < nL * kNb * kNb; e += 256) {
+        const int L = L0 + e / (kNb * kNb), a = e & 31, b2 = (e >> 5) & 31;
+        float* at = As + (L - L0) * kT;
+        if (MODE == 0) at[a * (kNb + 1) + b2] = In[(L * kNb + a) + (int64_t)(I * kNb + b2) * bp];
+        else at[b2 * (kNb + 1) + a] = X[(I * kNb + a) + (int64_t)(L * kNb + b2) * bp];
+        Bs[(L - L0) * kT + a * (kNb + 1) + b2] = In[(L * kNb + a) + (int64_t)(J * kNb + b2) * bp];
+    }
+    __syncthreads();
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int L = 0; L < nL; ++L) {
+        const float* at = As + L * kT;
+        const float* bt = Bs + L * kT;
 #pragma unroll 8
         for (int l = 0; l < kNb; ++l) {
-            const float av = As[l][lr];
+            const float av = at[l * (kNb + 1) + lr];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = fmaf(av, Bs[l][lc + q], acc[q]);
+            for (int q = 0; q < 4; ++q) acc[q] = fmaf(av, bt[l * (kNb + 1) + lc + q], acc[q]);
         }
-        __syncthreads();
     }
     const int i = I * kNb + lr;
 #pragma unroll
@@ -724,10 +730,14 @@ cudaError_t near_identity(Ctx& cx, const double* G, int bp, int p, double* R, T*
     if constexpr (kIter) {
         const int nblk = bp / kNb;
         const dim3 gt(nblk * (nblk + 1) / 2);
+        // up to 2 x nblk padded operand tiles per CTA
+        const size_t smem = sizeof(float) * 2 * (size_t)nblk * kNb * (kNb + 1);
+        if ((e = smem_limit(k_near_id_step<0, T>, (int)smem)) != cudaSuccess) return e;
+        if ((e = smem_limit(k_near_id_step<1, T>, (int)smem)) != cudaSuccess) return e;
         const float* X0in[3] = {Xa, Xb, Xa};
         float* X0out[3] = {Xb, Xa, Xb};
         for (int k = 0; k < 3; ++k) {
-            e = launch_pdl(k_near_id_step<0, T>, gt, dim3(256), 0, cx.stream, static_cast<const float*>(Ef),
+            e = launch_pdl(k_near_id_step<0, T>, gt, dim3(256), smem, cx.stream, static_cast<const float*>(Ef),
                            static_cast<const float*>(nullptr), X0in[k], X0out[k], bp, k == 2 ? 1 : 0, R, Za,
                            static_cast<T*>(nullptr), static_cast<const int*>(iter));
             if (e != cudaSuccess) return e;
@@ -736,7 +746,7 @@ cudaError_t near_identity(Ctx& cx, const double* G, int bp, int p, double* R, T*
         const float* Zin[3] = {Za, Zb, Za};
         float* Zout[3] = {Zb, Za, Zb};
         for (int k = 0; k < 3; ++k) {
-            e = launch_pdl(k_near_id_step<1, T>, gt, dim3(256), 0, cx.stream, static_cast<const float*>(nullptr),
+            e = launch_pdl(k_near_id_step<1, T>, gt, dim3(256), smem, cx.stream, static_cast<const float*>(nullptr),
                            static_cast<const float*>(Xb), Zin[k], Zout[k], bp, k == 2 ? 1 : 0,
                            static_cast<double*>(nullptr), static_cast<float*>(nullptr), Rinv,
                            static_cast<const int*>(iter));

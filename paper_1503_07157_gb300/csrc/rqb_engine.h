@@ -5,9 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <map>
 #include <mutex>
-#include <set>
-#include <tuple>
 #include <utility>
 
 #include "rqb_internal.cuh"
@@ -19,21 +18,23 @@ namespace rqb {
 // cudaMalloc had returned an out-of-memory error.
 bool alloc_should_fail();
 
-// Raises `kernel`'s dynamic shared-memory limit to `bytes` on the current
-// device.  The attribute is per device, so the call is made once per
-// (kernel, device, bytes) and remembered under a lock: several host threads
-// and several devices may launch the same kernel.
+// Raises `kernel`'s dynamic shared-memory limit to at least `bytes` on the
+// current device.  The attribute is per device; the largest limit set for
+// each (kernel, device) is remembered under a lock (several host threads and
+// several devices may launch the same kernel) and never lowered, so calls
+// with different sizes cannot undo one another.
 inline cudaError_t smem_limit_once(const void* kernel, int bytes) {
     static std::mutex mu;
-    static std::set<std::tuple<const void*, int, int>> done;
+    static std::map<std::pair<const void*, int>, int> limit;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(mu);
-    const auto key = std::make_tuple(kernel, dev, bytes);
-    if (done.count(key)) return cudaSuccess;
+    const auto key = std::make_pair(kernel, dev);
+    const auto it = limit.find(key);
+    if (it != limit.end() && it->second >= bytes) return cudaSuccess;
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) done.insert(key);
+    if (e == cudaSuccess) limit[key] = bytes;
     return e;
 }
 

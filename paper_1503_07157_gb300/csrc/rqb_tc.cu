@@ -87,6 +87,7 @@ struct StreamKCfg {
 
 template <int ROLE, int NP>
 __global__ void __launch_bounds__(320, 1) k_streamk(const __grid_constant__ StreamKParams p) {
+    pdl_wait();
     using Cfg = StreamKCfg<ROLE, NP>;
     constexpr int S = Cfg::S;
     constexpr uint32_t kW = Cfg::kW;
@@ -383,6 +384,7 @@ __device__ __forceinline__ void gen_omega_chunk(uint8_t* dst, int kc, const Stre
 // overwrite once the MMAs of the stage's previous use have completed.
 template <int ROLE, int NP, bool GEN = false>
 __global__ void __launch_bounds__(320, 1) k_streamk16(const __grid_constant__ StreamKParams p) {
+    pdl_wait();
     using Cfg = StreamK16Cfg<ROLE, NP>;
     constexpr int S = Cfg::S;
     constexpr uint32_t kW = Cfg::kW, kStage = Cfg::kStage;
@@ -623,6 +625,7 @@ constexpr int kWRing = 3;          // half-tile W buffers
 
 template <int NJ, int S>
 __global__ void __launch_bounds__(kUpdThreads, 1) k_update(const __grid_constant__ UpdateParams p) {
+    pdl_wait();
     __shared__ __align__(8) uint64_t full[S], empty[S], accfull[2], accempty[2], wfull[kWRing], wempty[kWRing],
         drain;
     __shared__ uint32_t tmem_base;
@@ -823,6 +826,7 @@ constexpr uint32_t kWEt = kBM * 32 * 4;             // W eighth: 16 KB
 constexpr size_t kUpdwSmem = (size_t)kStt * kStageT + (size_t)kWRt * kWEt + 1024;
 
 __global__ void __launch_bounds__(kUpdThreads, 1) k_updatew(const __grid_constant__ UpdateParams p) {
+    pdl_wait();
     __shared__ __align__(8) uint64_t full[kStt], empty[kStt], accfull[2], accempty[2], wfull[kWRt], wempty[kWRt],
         drain;
     __shared__ uint32_t tmem_base;
@@ -1107,19 +1111,26 @@ __device__ __forceinline__ int first_cta(long long x, long long U, int P) {
 }
 
 // Offsets (in floats) of the partial slots that hold tile t, in CTA order,
-// into off[0 .. count); computed once per CTA by thread 0.  The host plan
-// keeps the number of CTAs covering one tile at most kMaxCover.
-
-__device__ __forceinline__ int tile_slots(long long U, int C, int P, int G, int np, int t, size_t* off) {
+// into off[0 .. count), returned as count.  Called by every thread of a CTA
+// of at least kMaxCover threads (it synchronises): thread i takes the i-th
+// CTA from the first one covering tile t, so the divisions of unit_begin run
+// in parallel; the covering CTAs are the prefix of those whose range starts
+// before the tile ends.  The host plan keeps the number of CTAs covering one
+// tile at most kMaxCover.  q0: a shared int for the first CTA.
+__device__ __forceinline__ int tile_slots(long long U, int C, int P, int G, int np, int t, size_t* off, int* q0) {
     const long long x0 = (long long)t * C, x1 = x0 + C;
-    int count = 0;
-    for (int q = first_cta(x0, U, P); q < P && count < kMaxCover; ++q) {
+    if (threadIdx.x == 0) *q0 = first_cta(x0, U, P);
+    __syncthreads();
+    const int q = *q0 + (int)threadIdx.x;
+    bool covers = false;
+    if (threadIdx.x < kMaxCover && q < P) {
         const long long ub = unit_begin(U, P, q);
-        if (ub >= x1) break;
-        const int seg = (int)(t - ub / C);
-        off[count++] = ((size_t)q * G + seg) * (size_t)kBM * np;
+        if (ub < x1) {
+            covers = true;
+            off[threadIdx.x] = ((size_t)q * G + (int)(t - ub / C)) * (size_t)kBM * np;
+        }
     }
-    return count;
+    return __syncthreads_count(covers);
 }
 
 // Y[r + c ldy] (r < m, c < np) = sum over the CTAs covering tile r / 128 of
@@ -1156,9 +1167,7 @@ __global__ void k_reduce_sketch(const float* __restrict__ part, long long U, int
     __shared__ size_t off[kMaxCover];
     __shared__ int count;
     const int t = blockIdx.x;
-    if (threadIdx.x == 0) count = tile_slots(U, C, P, G, np, t, off);
-    __syncthreads();
-    const int nc = count;
+    const int nc = tile_slots(U, C, P, G, np, t, off, &count);
     const int span = np * kBM / (int)gridDim.y;
     const int i0 = blockIdx.y * span;
     const bool vec = (ldy % 4 == 0) && ((reinterpret_cast<uintptr_t>(Y) & 15u) == 0) &&
@@ -1196,9 +1205,7 @@ __global__ void k_reduce_project(const float* __restrict__ part, long long U, in
     __shared__ int count;
     __shared__ double red[32];
     const int t = blockIdx.x;
-    if (threadIdx.x == 0) count = tile_slots(U, C, P, G, np, t, off);
-    __syncthreads();
-    const int nc = count;
+    const int nc = tile_slots(U, C, P, G, np, t, off, &count);
     double sq = 0.0;
     const int span = np * kBM / (int)gridDim.y;
     const int i0 = blockIdx.y * span;
@@ -1245,9 +1252,7 @@ __global__ void k_reduce_project64(const float* __restrict__ part, long long U, 
     __shared__ int count;
     __shared__ double runs[3][256];   // run sums 1..3 of the 256 entries in flight
     const int t = blockIdx.x;
-    if (threadIdx.x == 0) count = tile_slots(U, C, P, G, np, t, off);
-    __syncthreads();
-    const int nc = count;
+    const int nc = tile_slots(U, C, P, G, np, t, off, &count);
     const int g = (int)threadIdx.x >> 6, lt = (int)threadIdx.x & 63;
     const int q0 = nc * g / 4, q1 = nc * (g + 1) / 4;
     const int span = np * kBM / (int)gridDim.y;
@@ -1320,6 +1325,7 @@ constexpr int kUpd16Threads = 352;   // warps 0 (operand TMA), 1 (MMA), 2..9 (ep
 
 template <int NJ, int S>
 __global__ void __launch_bounds__(kUpd16Threads, 1) k_update16(const __grid_constant__ UpdateParams16 p) {
+    pdl_wait();
     __shared__ __align__(8) uint64_t full[S], empty[S], accfull[2], accempty[2], wfull[2], wempty[2], drain;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
@@ -1519,6 +1525,7 @@ constexpr uint32_t kWQw = kBM * 64 * 2;             // W quarter: 16 KB
 constexpr size_t kUpd16wSmem = (size_t)kStw * kStageW + (size_t)kWRw * kWQw + 1024;
 
 __global__ void __launch_bounds__(kUpd16Threads, 1) k_update16w(const __grid_constant__ UpdateParams16 p) {
+    pdl_wait();
     __shared__ __align__(8) uint64_t full[kStw], empty[kStw], accfull[2], accempty[2], wfull[kWRw], wempty[kWRw],
         drain;
     __shared__ uint32_t tmem_base;
@@ -1782,9 +1789,7 @@ __global__ void k_reduce_project16(const float* __restrict__ part, long long U, 
     __shared__ int count;
     __shared__ double red[32];
     const int t = blockIdx.x;
-    if (threadIdx.x == 0) count = tile_slots(U, C, P, G, np, t, off);
-    __syncthreads();
-    const int nc = count;
+    const int nc = tile_slots(U, C, P, G, np, t, off, &count);
     double sq = 0.0;
     const int span = np * kBM / (int)gridDim.y;
     const int i0 = blockIdx.y * span;
@@ -1923,7 +1928,10 @@ cudaError_t launch_streamk_np(Ctx& cx, const StreamKParams& p) {
     constexpr size_t smem = StreamKCfg<ROLE, NP>::kSmem;
     cudaError_t e = allow_smem(k_streamk<ROLE, NP>, smem);
     if (e != cudaSuccess) return e;
-    k_streamk<ROLE, NP><<<p.P, 320, smem, cx.stream>>>(p);
+    {
+        const cudaError_t le_ = launch_pdl(k_streamk<ROLE, NP>, dim3(p.P), dim3(320), smem, cx.stream, p);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return cudaGetLastError();
 }
@@ -1944,7 +1952,10 @@ cudaError_t launch_streamk16_np(Ctx& cx, const StreamKParams& p) {
     constexpr size_t smem = StreamK16Cfg<ROLE, NP>::kSmem;
     cudaError_t e = allow_smem(k_streamk16<ROLE, NP, GEN>, smem);
     if (e != cudaSuccess) return e;
-    k_streamk16<ROLE, NP, GEN><<<p.P, 320, smem, cx.stream>>>(p);
+    {
+        const cudaError_t le_ = launch_pdl(k_streamk16<ROLE, NP, GEN>, dim3(p.P), dim3(320), smem, cx.stream, p);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     return cudaGetLastError();
 }
@@ -2106,8 +2117,8 @@ cudaError_t project(Ctx& cx, const float* X, long long ldx, long long m, long lo
     if ((e = launch_streamk<kProject>(cx, p, np)) != cudaSuccess) return e;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
-        const cudaError_t le_ = launch_pdl(k_reduce_project, dim3(pl.tiles, sl), dim3(256), 0, cx.stream, part,
-                                           pl.U, pl.C, pl.P, pl.G, np, pcols, n, B, ldb, Bs, Bsl, sq_part);
+        const cudaError_t le_ = launch_pdl(k_reduce_project, dim3(pl.tiles, sl), dim3(256), 0, cx.stream, part, pl.U,
+                                           pl.C, pl.P, pl.G, np, pcols, n, B, ldb, Bs, Bsl, sq_part);
         if (le_ != cudaSuccess) return le_;
     }
     cx.launches++;
@@ -2134,8 +2145,8 @@ cudaError_t project64(Ctx& cx, const float* X, long long ldx, long long m, long 
     if ((e = launch_streamk<kProject>(cx, p, np)) != cudaSuccess) return e;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
-        const cudaError_t le_ = launch_pdl(k_reduce_project64, dim3(pl.tiles, sl), dim3(256), 0, cx.stream, part,
-                                           pl.U, pl.C, pl.P, pl.G, np, pcols, n, out, ldo, sym ? 1 : 0);
+        const cudaError_t le_ = launch_pdl(k_reduce_project64, dim3(pl.tiles, sl), dim3(256), 0, cx.stream, part, pl.U,
+                                           pl.C, pl.P, pl.G, np, pcols, n, out, ldo, sym ? 1 : 0);
         if (le_ != cudaSuccess) return le_;
     }
     cx.launches++;
@@ -2170,7 +2181,10 @@ cudaError_t update_impl(Ctx& cx, const float* Wsrc, long long ldws, float* Wdst,
         const int grid = (int)std::min<long long>(cx.num_sms, T);
         if (sq_out && grid > sq_cap) return cudaErrorInvalidValue;
         if ((e = allow_smem(k_updatew, kUpdwSmem)) != cudaSuccess) return e;
-        k_updatew<<<grid, kUpdThreads, kUpdwSmem, cx.stream>>>(p);
+        {
+            const cudaError_t le_ = launch_pdl(k_updatew, dim3(grid), dim3(kUpdThreads), kUpdwSmem, cx.stream, p);
+            if (le_ != cudaSuccess) return le_;
+        }
         cx.launches++;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         return sq_out ? launch_sum_doubles(cx, sq_part, grid, sq_out) : cudaSuccess;
@@ -2191,7 +2205,11 @@ cudaError_t update_impl(Ctx& cx, const float* Wsrc, long long ldws, float* Wdst,
     const int grid = (int)std::min<long long>(cx.num_sms, T);
     if (sq_out && grid > sq_cap) return cudaErrorInvalidValue;
     if ((e = allow_smem(k_update<kUpdNJ, kUpdStages>, kUpdSmem)) != cudaSuccess) return e;
-    k_update<kUpdNJ, kUpdStages><<<grid, kUpdThreads, kUpdSmem, cx.stream>>>(p);
+    {
+        const cudaError_t le_ = launch_pdl(k_update<kUpdNJ, kUpdStages>, dim3(grid), dim3(kUpdThreads), kUpdSmem,
+                                           cx.stream, p);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return sq_out ? launch_sum_doubles(cx, sq_part, grid, sq_out) : cudaSuccess;
@@ -2368,8 +2386,8 @@ cudaError_t project16(Ctx& cx, const __nv_bfloat16* X, long long ldx, long long 
     p.U = pl.U; p.C = pl.C; p.P = pl.P; p.G = pl.G; p.np = np;
     if ((e = launch_streamk16<kProject>(cx, p, np)) != cudaSuccess) return e;
     {
-        const cudaError_t le_ = launch_pdl(k_reduce_project16, dim3(pl.tiles, sl), dim3(256), 0, cx.stream, part,
-                                           pl.U, pl.C, pl.P, pl.G, np, pcols, n, B, ldb, Bs, Bsl, sq_part);
+        const cudaError_t le_ = launch_pdl(k_reduce_project16, dim3(pl.tiles, sl), dim3(256), 0, cx.stream, part, pl.U,
+                                           pl.C, pl.P, pl.G, np, pcols, n, B, ldb, Bs, Bsl, sq_part);
         if (le_ != cudaSuccess) return le_;
     }
     cx.launches++;
@@ -2401,7 +2419,11 @@ cudaError_t update16(Ctx& cx, const __nv_bfloat16* Wsrc, long long ldws, __nv_bf
         const int grid = (int)std::min<long long>(cx.num_sms, T);
         if (sq_out && grid > sq_cap) return cudaErrorInvalidValue;
         if ((e = allow_smem(k_update16w, kUpd16wSmem)) != cudaSuccess) return e;
-        k_update16w<<<grid, kUpd16Threads, kUpd16wSmem, cx.stream>>>(p);
+        {
+            const cudaError_t le_ = launch_pdl(k_update16w, dim3(grid), dim3(kUpd16Threads), kUpd16wSmem, cx.stream,
+                                               p);
+            if (le_ != cudaSuccess) return le_;
+        }
         cx.launches++;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         return sq_out ? launch_sum_doubles(cx, sq_part, grid, sq_out) : cudaSuccess;
@@ -2422,7 +2444,11 @@ cudaError_t update16(Ctx& cx, const __nv_bfloat16* Wsrc, long long ldws, __nv_bf
     const int grid = (int)std::min<long long>(cx.num_sms, T);
     if (sq_out && grid > sq_cap) return cudaErrorInvalidValue;
     if ((e = allow_smem(k_update16<kUpdNJ, kUpd16Stages>, kUpd16Smem)) != cudaSuccess) return e;
-    k_update16<kUpdNJ, kUpd16Stages><<<grid, kUpd16Threads, kUpd16Smem, cx.stream>>>(p);
+    {
+        const cudaError_t le_ = launch_pdl(k_update16<kUpdNJ, kUpd16Stages>, dim3(grid), dim3(kUpd16Threads),
+                                           kUpd16Smem, cx.stream, p);
+        if (le_ != cudaSuccess) return le_;
+    }
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return sq_out ? launch_sum_doubles(cx, sq_part, grid, sq_out) : cudaSuccess;

@@ -219,13 +219,14 @@ def alu_peak_tflops(dtype: str, num_sms: int, sm_mhz: float) -> float:
 
 # DRAM bytes (read + write) per launch of the dominant kernel, keyed by
 # (workload, phase), from ncu captures (profiles/): fp32 sketch:
-# k_gemm_nn_pipe at 20000 x 16000 (1.294 GB + 0.122 GB); mixed projection:
-# k_streamk<project> at 8192 x 8192 (298.1 MB) scaled by the 8x elements of a
-# 32768 x 16384 launch; mixed and bf16 updates: k_updatew / k_update16w at
-# 8192 x 8192 scaled the same way; None where no capture of the current
-# kernel exists.
-NCU_TRAFFIC = {("fp32", "sketch"): 1.419e9, ("mixed", "project"): 2.385e9,
-               ("mixed", "downdate"): 4.383e9, ("bf16", "downdate"): 1.966e9}
+# k_gemm_nn_pipe at 20000 x 16000 (1.294 GB + 0.122 GB); split-TF32 and BF16
+# projections and sketches: k_streamk<project|sketch> (294.9 / 283.8 MB) and
+# k_streamk16<project|sketch> (148.2 / 141.8 MB) at 8192 x 8192, scaled by the
+# 8x elements of a 32768 x 16384 launch (A is read once; the partials, a few
+# percent, are overcounted); None where no capture of the current kernel
+# exists.
+NCU_TRAFFIC = {("fp32", "sketch"): 1.419e9, ("mixed", "project"): 2.359e9, ("mixed", "sketch"): 2.270e9,
+               ("bf16", "project"): 1.185e9, ("bf16", "sketch"): 1.134e9}
 
 
 def oracle_modes(w: dict) -> tuple[int, int]:

@@ -26,6 +26,10 @@
  *   - all work is enqueued on the handle's stream (cfg.stream, a
  *     cudaStream_t; NULL = the legacy default stream).  Calls that return
  *     results to the host (k, stop decisions) synchronise that stream.
+ *     The library's small kernels use programmatic dependent launches (each
+ *     waits for the kernel before it in the stream before touching memory);
+ *     the environment variable RQB_PDL=0, read once per process, launches
+ *     everything ordinarily, with bit-identical results.
  *   - Omega entry (r, c) is a function of (seed, r, c) only: Philox4x32-10
  *     (Salmon et al., SC'11) at counter (r, c/2, 0, 0) with key (seed low
  *     word, seed high word) gives two uniforms u1, u2 in (0, 1) and

@@ -479,8 +479,9 @@ __global__ void __launch_bounds__(256) k_linv_f32(const float* __restrict__ Lf, 
 // to O(||E||^2), and R^{-1} = I - U up to O(||E||^2).  When ||E||_F <= tau,
 // with tau^2 below the working precision's unit roundoff, the factor is taken
 // from this expansion (in FP64, from G's own entries) and the elimination is
-// skipped; otherwise the elimination runs as before.  Rows and columns >= p
-// are the identity.
+// skipped; FP32 factors up to ||E||_F = 2e-2 take the expansion iterated to
+// convergence (k_near_id_step); otherwise the elimination runs as before.
+// Rows and columns >= p are the identity.
 
 // part[b] = sum of (G_rc - delta_rc)^2 over CTA b's share of the p x p block.
 __global__ void __launch_bounds__(256) k_near_id_norm(const double* __restrict__ G, int bp, int p,

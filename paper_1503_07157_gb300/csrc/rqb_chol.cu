@@ -530,7 +530,16 @@ __global__ void __launch_bounds__(256) k_near_id_apply(const double* __restrict_
         mode = (t <= tau2) ? 1 : (t <= tau2i) ? 2 : 0;   // 0 for a NaN norm
         if (blockIdx.x == 0) {
             *skip = mode != 0;
-            *iter = mode == 2;
+            // steps of the iterated route for a 2e-9 error (e = ||E||_F,
+            // ||X|| <= e / sqrt(2), the map contracting by sqrt(2) e): s
+            // fixed-point steps after X_1 leave (sqrt(2) e)^s e^2 / 2, and the
+            // series to (-X)^(s+1) leaves (e / sqrt(2))^(s+2) (in numpy the
+            // worst of rank-one, rank-four, diagonal and dense E at these
+            // thresholds was 5e-11)
+            const double e = sqrt(t);
+            const int nx = (e <= 1.4e-3) ? 1 : (e <= 6.7e-3) ? 2 : 3;
+            const int nz = (e <= 1.7e-3) ? 1 : (e <= 9.4e-3) ? 2 : 3;
+            *iter = (mode == 2) ? (nx | (nz << 4)) : 0;
             if (mode != 0 && st) atomicAdd(&st->near_id, 1);
         }
     }
@@ -564,21 +573,29 @@ __global__ void __launch_bounds__(256) k_near_id_apply(const double* __restrict_
 // bp x bp upper-triangular FP32 matrices (column-major), one tile per CTA; it
 // runs only when *iter is set.
 //   MODE 0, the fixed point X = Phi(E - X^T X) of R = I + X (Phi: the upper
-//          triangle with the diagonal halved): Out = Phi(Ef - In^T In); with
-//          last, also R = I + Out (FP64) and Z = I - Out.
-//   MODE 1, R^{-1} = sum_j (-X)^j by Horner: Out = I - X In; with last, also
-//          Rinv = Out.
+//          triangle with the diagonal halved): Out = Phi(Ef - In^T In); the
+//          last step also writes R = I + Out (FP64) and Z = I - Out.
+//   MODE 1, R^{-1} = sum_j (-X)^j by Horner: Out = I - X In; the last step
+//          also writes Rinv = Out.
 // From X_1 = Phi(E) the k-th iterate is within ||E||^(k+1) / 2 of the exact
 // X (the map contracts by about ||E||), and j terms of the series leave
-// ||X||^(j+1): at ||E||_F <= 2e-2, X_4 and four terms are within 2e-9.
+// ||X||^(j+1): at ||E||_F <= 2e-2, X_4 and four terms are within 2e-9.  The
+// apply kernel sets how many steps of each kind a panel needs for that.
 template <int MODE, typename T>
-__global__ void __launch_bounds__(256) k_near_id_step(const float* __restrict__ Ef, const float* __restrict__ X,
-                                                      const float* __restrict__ In, float* __restrict__ Out, int bp,
-                                                      int last, double* __restrict__ R, float* __restrict__ Z,
+__global__ void __launch_bounds__(256) k_near_id_step(const float* __restrict__ Ef, const float* __restrict__ Xa,
+                                                      const float* __restrict__ Xb, const float* __restrict__ In,
+                                                      float* __restrict__ Out, int bp, int k,
+                                                      double* __restrict__ R, float* __restrict__ Z,
                                                       T* __restrict__ Rinv, const int* __restrict__ iter) {
     pdl_trigger();
     pdl_wait();
-    if (!*iter) return;
+    // *iter: fixed-point steps in bits 0..3, series steps in bits 4..7 (0:
+    // the iterated route is off); this launch is step k of its kind
+    const int nsteps = (MODE == 0) ? (*iter & 15) : ((*iter >> 4) & 15);
+    if (k >= nsteps) return;
+    const bool last = (k == nsteps - 1);
+    // the final fixed-point iterate is in Xb after one or three steps, in Xa after two
+    const float* X = ((*iter & 15) == 2) ? Xa : Xb;
     // all the operand tiles of this output tile are loaded at once (up to
     // 2 x 8 tiles, every load in flight together), then multiplied
     extern __shared__ float nis[];
@@ -716,8 +733,9 @@ cudaError_t near_identity(Ctx& cx, const double* G, int bp, int p, double* R, T*
     if (e != cudaSuccess) return e;
     cx.launches++;
     // the iterated route for FP32 factors (whose tau leaves most tensor-core
-    // panels above it): three fixed-point steps and three series steps on the
-    // FP32 work matrices after the parts and the flags
+    // panels above it): up to three fixed-point steps and three series steps
+    // on the FP32 work matrices after the parts and the flags (the steps a
+    // panel does not need return at once)
     constexpr bool kIter = sizeof(T) == 4;
     const double tau_i = kIter ? 2e-2 : 0.0;
     const size_t sq = (size_t)bp * bp;
@@ -739,8 +757,8 @@ cudaError_t near_identity(Ctx& cx, const double* G, int bp, int p, double* R, T*
         float* X0out[3] = {Xb, Xa, Xb};
         for (int k = 0; k < 3; ++k) {
             e = launch_pdl(k_near_id_step<0, T>, gt, dim3(256), smem, cx.stream, static_cast<const float*>(Ef),
-                           static_cast<const float*>(nullptr), X0in[k], X0out[k], bp, k == 2 ? 1 : 0, R, Za,
-                           static_cast<T*>(nullptr), static_cast<const int*>(iter));
+                           static_cast<const float*>(nullptr), static_cast<const float*>(nullptr), X0in[k], X0out[k],
+                           bp, k, R, Za, static_cast<T*>(nullptr), static_cast<const int*>(iter));
             if (e != cudaSuccess) return e;
             cx.launches++;
         }
@@ -748,7 +766,7 @@ cudaError_t near_identity(Ctx& cx, const double* G, int bp, int p, double* R, T*
         float* Zout[3] = {Zb, Za, Zb};
         for (int k = 0; k < 3; ++k) {
             e = launch_pdl(k_near_id_step<1, T>, gt, dim3(256), smem, cx.stream, static_cast<const float*>(nullptr),
-                           static_cast<const float*>(Xb), Zin[k], Zout[k], bp, k == 2 ? 1 : 0,
+                           static_cast<const float*>(Xa), static_cast<const float*>(Xb), Zin[k], Zout[k], bp, k,
                            static_cast<double*>(nullptr), static_cast<float*>(nullptr), Rinv,
                            static_cast<const int*>(iter));
             if (e != cudaSuccess) return e;

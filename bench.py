@@ -920,13 +920,26 @@ def run_reference(args, w: dict) -> int:
                                             "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return 0
-    A = make_sample_host(w, args.sample_frac)
-    m, n = A.shape
-    nA = float((A * A).sum()) ** 0.5
-    eps = w["eps_rel"] * nA
+    # exactly W untimed and K timed runs; the sample is shrunk (from one
+    # calibration run) so that they take about REF_BUDGET_S on the host cores
+    REF_BUDGET_S = 150.0
+    steps, warm = max(1, args.steps), max(0, args.warmup)
     prec, store = oracle_modes(w)
-    steps = max(1, min(args.steps, 5))
-    warm = min(args.warmup, 1)
+    frac = args.sample_frac
+
+    def sample(f):
+        A = make_sample_host(w, f)
+        return A, w["eps_rel"] * float((A * A).sum()) ** 0.5
+
+    A, eps = sample(frac)
+    t0 = time.perf_counter()
+    oracle.randqb_b(A, eps, w["b"], seed=0, omega_prec=prec, storage_prec=store)
+    t_cal = time.perf_counter() - t0
+    if (warm + steps) * t_cal > REF_BUDGET_S:
+        # time grows with m n at a fixed rank: frac scales by the square root
+        frac = max(0.05, frac * ((REF_BUDGET_S / ((warm + steps) * t_cal)) ** 0.5))
+        A, eps = sample(frac)
+    m, n = A.shape
     times, r = [], None
     for i in range(warm + steps):
         t0 = time.perf_counter()
@@ -941,8 +954,8 @@ def run_reference(args, w: dict) -> int:
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["name"], "sample": f"{m}x{n}", "k": r.k, "blocks": r.blocks},
             "cpu_baseline": {"value": round(val, 6), "unit": "TFLOP/s", "cores": oracle.num_threads(),
-                             "kind": "oracle", "sample": f"same recipe at {m}x{n} (frac {args.sample_frac}); "
-                             f"steps capped at {steps}, warm-up at {warm} to bound CPU time"},
+                             "kind": "oracle", "sample": f"same recipe at {m}x{n} (frac {frac:.3f}, sized so that "
+                             f"{warm} warm-up and {steps} timed runs take about {REF_BUDGET_S:.0f} s)"},
             "e2e": {"value": round(val, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0

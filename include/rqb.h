@@ -150,6 +150,14 @@ typedef struct {
                                the near-identity expansion (||G - I||_F below
                                2^-28 for an FP64 factor, 1e-4 for an FP32 one)
                                instead of the elimination                      */
+    int32_t fused_gram;     /* split-TF32 handles: panels whose second Gram was
+                               formed as Y1^T Y1 - C^T C from the product that
+                               gives C = Qbar^T Y1 (line (3'), ||C||_F^2 at most
+                               0.05) instead of from the re-projected panel   */
+    int32_t pass1_fp32;     /* tensor-core handles: panels whose first
+                               CholeskyQR factor was the FP32 elimination of
+                               the split-TF32 Gram (pivots spanning at most
+                               1e3) rather than an FP64 one                   */
     int32_t reserved;
 } rqb_stats;
 

@@ -301,14 +301,16 @@ int ensure_tc(rqb_handle h, int64_t m, int64_t n, int bp, TcArena* out) {
 // columns against up to kcap earlier columns.
 int ensure_reproj(rqb_handle h, int64_t m, int64_t kcap, int bp, tc::ReprojScratch* w) {
     const int64_t ldyl = round_up(m, 4), ldom = round_up(kcap, 4);
-    const size_t part = tc::partial_floats(m, std::max<int64_t>(kcap, 256), bp, h->num_sms);
+    // the fused re-projection's product has kcap + bp output rows at most
+    const size_t part = tc::partial_floats(m, std::max<int64_t>(kcap, 256) + bp, bp, h->num_sms);
     size_t off = 0;
     auto take = [&](size_t floats) { size_t o = off; off = align256(off + 4 * floats); return o; };
     const size_t oYh = take((size_t)ldyl * bp), oYl = take((size_t)ldyl * bp);
     const size_t kb = (size_t)std::max<int64_t>(kcap, bp);
     const size_t oCt = take((size_t)bp * kb), oOm = take((size_t)ldom * bp);
     const size_t oBs = take((size_t)bp * kb), oBsl = take((size_t)bp * kb);
-    const size_t oC64 = take(2 * (size_t)bp * kb);
+    const size_t oC64 = take(2 * (size_t)bp * (kb + bp));   // C^T and, after it, Y^T Y (reproject_gram)
+    const size_t oTr = take(2 * 64 + 4);                    // trace parts (FP64) and the fused flag
     const size_t oYt = take((size_t)ldyl * bp), oYtl = take((size_t)ldyl * bp);
     const size_t oP = take(part);
     int rc = h->pcbuf.ensure(off);
@@ -320,6 +322,8 @@ int ensure_reproj(rqb_handle h, int64_t m, int64_t kcap, int bp, tc::ReprojScrat
     w->Ct = at(oCt); w->Om = at(oOm); w->ldom = ldom;
     w->Bs = at(oBs); w->Bsl = at(oBsl);
     w->Ct64 = reinterpret_cast<double*>(base + oC64);
+    w->trace_part = reinterpret_cast<double*>(base + oTr);
+    w->fused = reinterpret_cast<int*>(base + oTr + sizeof(double) * 64);
     w->Yt = at(oYt); w->Ytl = at(oYtl);
     w->part = at(oP); w->part_cap = part;
     w->sq_part = sc.nrm; w->sq_cap = kNrmCap; w->sq_out = sc.s + 8;
@@ -353,6 +357,7 @@ int read_state(rqb_handle h, const Scal& sc) {
     RQB_CK(cudaStreamSynchronize(h->stream));
     h->timer.flush(&h->stats);
     h->stats.near_identity = h->hstate->near_id;
+    h->stats.fused_gram = h->hstate->fused_gram;
     return h->hstate->err;
 }
 
@@ -380,37 +385,51 @@ int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_
     // pass 1: CholeskyQR of Y, Y1 = Y R^{-1}.  On the tensor-core handles the
     // Gram is first taken from the split-TF32 products (relative error
     // ~1e-7): pass 1 only has to leave Y1 well conditioned for pass 2, which
-    // it does while kappa(Y)^2 * 1e-7 << 1.  The FP64 Cholesky of that Gram
-    // runs on a scratch state; when it breaks down or its pivots put
-    // kappa(G) above 1e5, the Gram is recomputed with exact products and FP64
-    // sums and factored again.
+    // it does while kappa(Y)^2 * 1e-7 << 1.  That Gram is factored on a
+    // scratch state, first by the FP32 elimination (its rounding, about
+    // sqrt(bp) u32 kappa(G) in Y1^T Y1 - I, is of the order of the Gram's
+    // own): accepted when it does not break down and its pivots span at most
+    // 1e3.  Otherwise the saved Gram is factored in FP64, accepted up to a
+    // pivot span of 1e5; past that the Gram is recomputed with exact products
+    // and FP64 sums and factored again.
     bool pass1 = false;
     bool split1 = false;   // w.Yt / w.Ytl hold Y's split for the product Y R^-1
     if constexpr (std::is_same<T, float>::value) {
-        if (ar.rp && m <= ar.rp->ldyl && tc::gram_ok(m, bp, ldy, Y)) {
+        const size_t sq = (size_t)bp * bp;
+        if (ar.rp && m <= ar.rp->ldyl && tc::gram_ok(m, bp, ldy, Y) && ar.dpart_cap >= 9 * sq) {
+            if (bp > kMaxPanel) return RQB_ERR_INVALID;
             split1 = tc::product_ok(m, bp, m, ar.Y1);
             RQB_CK(tc::gram(cx, Y, ldy, m, bp, *ar.rp, ar.G, split1));
+            // the elimination overwrites G: a copy past its scratch
+            double* Gsave = ar.dpart + 8 * sq;
+            RQB_CK(cudaMemcpyAsync(Gsave, ar.G, sizeof(double) * sq, cudaMemcpyDeviceToDevice, h->stream));
             DevState* st2 = reinterpret_cast<DevState*>(reinterpret_cast<char*>(h->state.p) + 128);
-            RQB_CK(cudaMemsetAsync(st2, 0, sizeof(DevState), h->stream));
             Ctx cx2 = cx;
             cx2.st = st2;
-            RQB_CK(chol_inv<T>(cx2, ar.G, bp, p, ar.R, ar.Rinv, true, ar.dpart, ar.dpart_cap));
-            cx.launches = cx2.launches;
-            // pinned host copies: the one synchronisation inside the panel
-            // waits for two small copies, not for staged pageable ones
-            if (bp > kMaxPanel) return RQB_ERR_INVALID;
-            const DevState& hs = *h->hstate2;
-            const double* diag = h->hdiag;
-            RQB_CK(cudaMemcpyAsync(h->hstate2, st2, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
-            RQB_CK(cudaMemcpy2DAsync(h->hdiag, sizeof(double), ar.R, sizeof(double) * (bp + 1), sizeof(double), bp,
-                                     cudaMemcpyDeviceToHost, h->stream));
-            RQB_CK(cudaStreamSynchronize(h->stream));
-            double lo = HUGE_VAL, hi = 0.0;
-            for (int i = 0; i < p; ++i) {
-                lo = std::min(lo, diag[i]);
-                hi = std::max(hi, diag[i]);
+            for (int attempt = 0; attempt < 2 && !pass1; ++attempt) {
+                const bool fp64 = attempt == 1;
+                if (fp64)
+                    RQB_CK(cudaMemcpyAsync(ar.G, Gsave, sizeof(double) * sq, cudaMemcpyDeviceToDevice, h->stream));
+                RQB_CK(cudaMemsetAsync(st2, 0, sizeof(DevState), h->stream));
+                cx2.launches = cx.launches;
+                RQB_CK(chol_inv<T>(cx2, ar.G, bp, p, ar.R, ar.Rinv, fp64, ar.dpart, 8 * sq));
+                cx.launches = cx2.launches;
+                // pinned host copies: the synchronisation inside the panel
+                // waits for two small copies, not for staged pageable ones
+                const DevState& hs = *h->hstate2;
+                const double* diag = h->hdiag;
+                RQB_CK(cudaMemcpyAsync(h->hstate2, st2, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+                RQB_CK(cudaMemcpy2DAsync(h->hdiag, sizeof(double), ar.R, sizeof(double) * (bp + 1), sizeof(double),
+                                         bp, cudaMemcpyDeviceToHost, h->stream));
+                RQB_CK(cudaStreamSynchronize(h->stream));
+                double lo = HUGE_VAL, hi = 0.0;
+                for (int i = 0; i < p; ++i) {
+                    lo = std::min(lo, diag[i]);
+                    hi = std::max(hi, diag[i]);
+                }
+                pass1 = hs.err == RQB_OK && lo > 0.0 && (hi / lo) * (hi / lo) <= (fp64 ? 1e5 : 1e3);
+                h->stats.pass1_fp32 += (pass1 && !fp64) ? 1 : 0;
             }
-            pass1 = hs.err == RQB_OK && lo > 0.0 && (hi / lo) * (hi / lo) <= 1e5;
             h->stats.gram_fallbacks += pass1 ? 0 : 1;
         }
     }
@@ -433,11 +452,21 @@ int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_
         a.Out = ar.Y1; a.ldo = m;
         RQB_CK(gemm_nn<T>(cx, a));
     }
-    // line (3'): Y1 -= Qbar (Qbar^T Y1)
+    // line (3'): Y1 -= Qbar (Qbar^T Y1).  On the tensor-core handles the same
+    // product also gives Y1^T Y1, from which the second pass's Gram follows
+    // (tc::reproject_gram); *fused is set on the device where that formula is
+    // used, and the direct Gram below then does nothing
     bool done = false;
+    const int* fused = nullptr;
     if constexpr (std::is_same<T, float>::value) {
         if (kprev > 0 && ar.rp && m <= ar.rp->ldyl && tc::reproject_ok(m, kprev) && tma_ok(Qbar, ldqb)) {
-            RQB_CK(tc::reproject(cx, Qbar, ldqb, m, kprev, ar.Y1, m, bp, *ar.rp));
+            if (tc::reproject_gram_ok(m, kprev, bp, m, ar.Y1, *ar.rp)) {
+                RQB_CK(tc::reproject_gram(cx, Qbar, ldqb, m, kprev, ar.Y1, m, bp, *ar.rp, ar.G, ar.rp->fused,
+                                          ar.rp->trace_part));
+                fused = ar.rp->fused;
+            } else {
+                RQB_CK(tc::reproject(cx, Qbar, ldqb, m, kprev, ar.Y1, m, bp, *ar.rp));
+            }
             done = true;
         }
     }
@@ -463,8 +492,9 @@ int orth_reproject(rqb_handle h, Ctx& cx, const Arena<T>& ar, const T* Y, int64_
     bool split2 = false;   // w.Yt / w.Ytl hold Y1's split for the product Y1 R^-1
     if constexpr (std::is_same<T, float>::value) {
         if (ar.rp && m <= ar.rp->ldyl && tc::gram_ok(m, bp, m, ar.Y1)) {
+            // after the fused re-projection only the product's copies of the split are made
             split2 = p == bp && tc::product_ok(m, bp, ldqo, Qout);
-            RQB_CK(tc::gram(cx, ar.Y1, m, m, bp, *ar.rp, ar.G, split2));
+            RQB_CK(tc::gram(cx, ar.Y1, m, m, bp, *ar.rp, ar.G, split2, fused));
             tcg2 = true;
         }
     }
@@ -1265,6 +1295,7 @@ int orth_impl(rqb_handle h, const T* Y, int64_t m, int p, int64_t ldy, const T* 
     if (rc != RQB_OK) return rc;
     tc::ReprojScratch rp;
     h->stats.gram_fallbacks = 0;
+    h->stats.pass1_fp32 = 0;
     if (std::is_same<T, float>::value && (h->cfg.prec == RQB_PREC_TF32X3 || h->cfg.dtype == RQB_BF16) && m >= 128) {
         if ((rc = ensure_reproj(h, m, std::max<int64_t>(kprev, 1), bp, &rp)) != RQB_OK) return rc;
         ar.rp = &rp;

@@ -23,7 +23,7 @@ struct DevState {
     int32_t err;       // first error code recorded by a kernel (rqb_status)
     int32_t flag;      // stop decision of the current block (see StopFlag)
     int32_t near_id;   // second CholeskyQR passes factored by the near-identity expansion
-    int32_t pad;
+    int32_t fused_gram;  // second Grams formed from the re-projection's product
 };
 
 enum StopFlag : int32_t { kContinue = 0, kStop = 1, kAmbiguous = 2 };

@@ -57,6 +57,13 @@ struct StreamKParams {
     long long om_n = 0, om_col0 = 0;
     int om_p = 0;
     unsigned long long om_seed = 0;
+    // split-TF32 projection over two X matrices side by side: tiles >= tsplit
+    // of X come from mx2 (its tile t - tsplit)
+    CUtensorMap mx2;
+    int tsplit = 0x7fffffff;
+    // nonzero *gate: the launch does nothing (a product made unnecessary by
+    // an earlier kernel's device-side decision)
+    const int* gate = nullptr;
 };
 
 __host__ __device__ __forceinline__ long long unit_begin(long long U, int P, int p) { return U * p / P; }
@@ -88,6 +95,7 @@ struct StreamKCfg {
 template <int ROLE, int NP>
 __global__ void __launch_bounds__(320, 1) k_streamk(const __grid_constant__ StreamKParams p) {
     pdl_wait();
+    if (p.gate && *p.gate) return;   // before any barrier, shared memory or TMEM
     using Cfg = StreamKCfg<ROLE, NP>;
     constexpr int S = Cfg::S;
     constexpr uint32_t kW = Cfg::kW;
@@ -118,6 +126,7 @@ __global__ void __launch_bounds__(320, 1) k_streamk(const __grid_constant__ Stre
         prefetch_map(&p.mx);
         prefetch_map(&p.mw);
         if (ROLE == kProject) prefetch_map(&p.mwl);
+        if (ROLE == kProject && p.tsplit != 0x7fffffff) prefetch_map(&p.mx2);
     }
     if (warp == 1) tmem_alloc(&tmem_base, ncols);
     tc_fence_before();
@@ -144,7 +153,9 @@ __global__ void __launch_bounds__(320, 1) k_streamk(const __grid_constant__ Stre
                     tma_load_2d(sW + s * kW, &p.mw, kc * kKC, 0, &full[s]);
                 } else {
                     mbar_arrive_expect_tx(&full[s], kTileBytes + 2u * kW);
-                    tma_load_2d(sX + s * kTileBytes, &p.mx, kc * kKC, t * kBM, &full[s]);
+                    const bool second = t >= p.tsplit;
+                    tma_load_2d(sX + s * kTileBytes, second ? &p.mx2 : &p.mx, kc * kKC,
+                                (second ? t - p.tsplit : t) * kBM, &full[s]);
                     tma_load_2d(sW + s * kW, &p.mw, kc * kKC, 0, &full[s]);
                     tma_load_2d(sWl + s * kW, &p.mwl, kc * kKC, 0, &full[s]);
                 }
@@ -1031,12 +1042,17 @@ __global__ void k_omega_tf32(long long n, long long col0, int p, int bp, uint64_
 // From Q_i (m x p, column-major, ld ldq): Qhi = Q_i and its lo part Qlo
 // (column-major, ld ldql, bp columns), Qt = Q_i^T as row-major m x bp and
 // its lo part Qtl; columns p..bp-1 are zero.  32 x 32 tiles transposed
-// through shared memory.
+// through shared memory.  A nonzero *gate drops the column-major copies (the
+// kernel then returns at once when Qt is NULL).
 __global__ void k_split_q(const float* __restrict__ Qi, long long ldq, long long m, int p, int bp,
                           float* __restrict__ Qhi, float* __restrict__ Qlo, long long ldql, float* __restrict__ Qt,
-                          float* __restrict__ Qtl) {
+                          float* __restrict__ Qtl, const int* __restrict__ gate) {
     pdl_trigger();
     pdl_wait();
+    if (gate && *gate) {
+        if (Qt == nullptr) return;
+        Qhi = nullptr;
+    }
     __shared__ float tile[32][33];
     const long long r0 = (long long)blockIdx.x * 32;
     const int c0 = blockIdx.y * 32;
@@ -1067,6 +1083,122 @@ __global__ void k_split_q(const float* __restrict__ Qi, long long ldq, long long
 
 // Omega-layout copy of the re-projection coefficients: Om[j + c ldo] =
 // rna_tf32(Ct[c + j ldc]) for j < kprev, c < np (Ct is C^T, np x kprev).
+// Split-k parts of C^T C for the fused second-pass Gram.  C is kprev x np,
+// held transposed in Ct (np x kprev, ld ldc, FP64).  CTA (t, s) takes the
+// 32 x 32 upper tile t = (I, J), I <= J (t = J (J + 1) / 2 + I), over
+// k in [128 s, 128 s + 128), and writes its 1024 sums to
+// part[(t KS + s) 1024 + i + 32 j] (KS = gridDim.y).  The FP32-rounded
+// entries of C are multiplied and summed in FP32 over 32 k, the four 32-k
+// sums added in FP64.
+__global__ void __launch_bounds__(256) k_gram_part(const double* __restrict__ Ct, long long ldc, long long kprev,
+                                                   double* __restrict__ part) {
+    pdl_trigger();
+    pdl_wait();
+    __shared__ float As[128][33], Bs[128][33];
+    int J = 0;
+    while ((J + 1) * (J + 2) / 2 <= (int)blockIdx.x) ++J;
+    const int I = (int)blockIdx.x - J * (J + 1) / 2;
+    const long long k0 = (long long)blockIdx.y * 128;
+    const int tid = threadIdx.x;
+    // all 16 loads of a thread in flight at once: 16-byte pairs of C^T
+    // (Ct 16-byte aligned, ldc even)
+    const double2* C2 = reinterpret_cast<const double2*>(Ct);
+    double2 va[8], vb[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int e = tid + 256 * r, c2 = e & 15, kk = e >> 4;
+        const bool in = k0 + kk < kprev;
+        const long long row = (k0 + kk) * ldc;
+        va[r] = in ? C2[(row + I * 32) / 2 + c2] : make_double2(0.0, 0.0);
+        vb[r] = in ? C2[(row + J * 32) / 2 + c2] : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int e = tid + 256 * r, c2 = e & 15, kk = e >> 4;
+        As[kk][2 * c2] = (float)va[r].x;
+        As[kk][2 * c2 + 1] = (float)va[r].y;
+        Bs[kk][2 * c2] = (float)vb[r].x;
+        Bs[kk][2 * c2 + 1] = (float)vb[r].y;
+    }
+    __syncthreads();
+    const int lr = tid & 31, lc = (tid >> 5) * 4;
+    double accd[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int kc = 0; kc < 128; kc += 32) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+        for (int kk = kc; kk < kc + 32; ++kk) {
+            const float x = As[kk][lr];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = fmaf(x, Bs[kk][lc + q], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) accd[q] += (double)acc[q];
+    }
+    double* out = part + ((size_t)blockIdx.x * gridDim.y + blockIdx.y) * 1024;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[lr + 32 * (lc + q)] = accd[q];
+}
+
+// G (np x np, FP64, ld np) = S - C^T C on the 32 x 32 upper tiles, one per
+// CTA (numbered as in k_gram_part), the KS parts of each entry summed in the
+// order s = 0, 1, ...: S[i + j lds] = (Y^T Y)(i, j), upper triangle read.
+// Each entry of G is written once, the lower triangle as the mirror of the
+// upper.  Diagonal tiles also write trace_part[I], the sum of their
+// (C^T C)_ii.
+__global__ void __launch_bounds__(256) k_gram_fin(const double* __restrict__ S, long long lds,
+                                                  const double* __restrict__ part, int KS, int np,
+                                                  double* __restrict__ G, double* __restrict__ trace_part) {
+    pdl_trigger();
+    pdl_wait();
+    __shared__ double dsum[32];
+    int J = 0;
+    while ((J + 1) * (J + 2) / 2 <= (int)blockIdx.x) ++J;
+    const int I = (int)blockIdx.x - J * (J + 1) / 2;
+    const double* pp = part + (size_t)blockIdx.x * KS * 1024;
+    double vs[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+    for (int s = 0; s < KS; ++s) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) vs[r] += pp[(size_t)s * 1024 + threadIdx.x + 256 * r];
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int e = threadIdx.x + 256 * r;
+        const double v = vs[r];
+        const int li = e & 31, lj = e >> 5;
+        const int i = I * 32 + li, j = J * 32 + lj;
+        if (i <= j) {
+            const double g = S[i + (long long)j * lds] - v;
+            G[i + (long long)j * np] = g;
+            if (i < j) G[j + (long long)i * np] = g;
+        }
+        if (I == J && li == lj) dsum[li] = v;
+    }
+    if (I == J) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int d = 0; d < 32; ++d) t += dsum[d];
+            trace_part[I] = t;
+        }
+    }
+}
+
+// *fused = 1 when ||C||_F^2, the sum of the nparts trace parts, is <= thr
+// (counted in st->fused_gram), else 0.
+__global__ void k_gram_gate(const double* __restrict__ trace_part, int nparts, double thr, int* __restrict__ fused,
+                            DevState* st) {
+    pdl_trigger();
+    pdl_wait();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int b = 0; b < nparts; ++b) t += trace_part[b];
+        const int f = (t <= thr) ? 1 : 0;   // 0 for a NaN
+        *fused = f;
+        if (f && st) atomicAdd(&st->fused_gram, 1);
+    }
+}
+
 template <typename TC>
 __global__ void k_ct_to_omega(const TC* __restrict__ Ct, long long ldc, long long kprev, int np,
                               float* __restrict__ Om, long long ldo) {
@@ -1245,9 +1377,11 @@ __global__ void k_reduce_project(const float* __restrict__ part, long long U, in
 // above the diagonal mirror those below it, which are summed once and stored
 // at both positions.
 __global__ void k_reduce_project64(const float* __restrict__ part, long long U, int C, int P, int G, int np,
-                                   int pcols, long long n, double* __restrict__ out, long long ldo, int sym) {
+                                   int pcols, long long n, double* __restrict__ out, long long ldo, int sym,
+                                   const int* __restrict__ gate) {
     pdl_trigger();
     pdl_wait();
+    if (gate && *gate) return;
     __shared__ size_t off[kMaxCover];
     __shared__ int count;
     __shared__ double runs[3][256];   // run sums 1..3 of the 256 entries in flight
@@ -2028,7 +2162,7 @@ cudaError_t split_q(Ctx& cx, const float* Qi, long long ldq, long long m, int p,
     dim3 grid((unsigned)((m + 31) / 32), (unsigned)(np / 32));
     {
         const cudaError_t le_ = launch_pdl(k_split_q, dim3(grid), dim3(256), 0, cx.stream, Qi, ldq, m, p, np, Qhi, Qlo,
-                                           ldql, Qt, Qtl);
+                                           ldql, Qt, Qtl, static_cast<const int*>(nullptr));
         if (le_ != cudaSuccess) return le_;
     }
     cx.launches++;
@@ -2128,14 +2262,25 @@ cudaError_t project(Ctx& cx, const float* X, long long ldx, long long m, long lo
 
 // out (pcols x n, FP64, ld ldo) = Q^T X as project(), the CTAs' FP32
 // partials summed in FP64 (k_reduce_project64); no staged copies, no norm.
+// With X2, X is [X X2] side by side: n columns of X (a multiple of 128) then
+// n2 of X2 (ld ldx2), out pcols x (n + n2).  A nonzero *gate makes both
+// launches do nothing.
 cudaError_t project64(Ctx& cx, const float* X, long long ldx, long long m, long long n, const float* Qhi,
                       const float* Qlo, long long ldql, int pcols, int np, double* out, long long ldo, float* part,
-                      size_t part_cap, bool sym = false) {
+                      size_t part_cap, bool sym = false, const float* X2 = nullptr, long long ldx2 = 0,
+                      long long n2 = 0, const int* gate = nullptr) {
     StreamKParams p;
     cudaError_t e;
     if ((e = make_map(&p.mx, X, m, n, ldx, kKC, kBM, true)) != cudaSuccess) return e;
     if ((e = make_map(&p.mw, Qhi, m, np, ldql, kKC, np, true)) != cudaSuccess) return e;
     if ((e = make_map(&p.mwl, Qlo, m, np, ldql, kKC, np, true)) != cudaSuccess) return e;
+    if (X2) {
+        if (n % kBM != 0) return cudaErrorInvalidValue;
+        if ((e = make_map(&p.mx2, X2, m, n2, ldx2, kKC, kBM, true)) != cudaSuccess) return e;
+        p.tsplit = (int)(n / kBM);
+        n += n2;
+    }
+    p.gate = gate;
     const Plan pl = plan((n + kBM - 1) / kBM, (m + kKC - 1) / kKC, cx.num_sms);
     const int sl = reduce_slices(pl.tiles, cx.num_sms);
     if ((size_t)pl.P * pl.G * kBM * np > part_cap) return cudaErrorInvalidValue;
@@ -2146,7 +2291,7 @@ cudaError_t project64(Ctx& cx, const float* X, long long ldx, long long m, long 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
         const cudaError_t le_ = launch_pdl(k_reduce_project64, dim3(pl.tiles, sl), dim3(256), 0, cx.stream, part, pl.U,
-                                           pl.C, pl.P, pl.G, np, pcols, n, out, ldo, sym ? 1 : 0);
+                                           pl.C, pl.P, pl.G, np, pcols, n, out, ldo, sym ? 1 : 0, gate);
         if (le_ != cudaSuccess) return le_;
     }
     cx.launches++;
@@ -2228,17 +2373,19 @@ bool gram_ok(long long m, int np, long long ldy, const float* Y) {
 }
 
 cudaError_t gram(Ctx& cx, const float* Y, long long ldy, long long m, int np, const ReprojScratch& w, double* G,
-                 bool keep_split) {
+                 bool keep_split, const int* gate) {
     cudaError_t e;
     dim3 g1((unsigned)((m + 31) / 32), (unsigned)(np / 32));
     {
         const cudaError_t le_ = launch_pdl(k_split_q, dim3(g1), dim3(256), 0, cx.stream, Y, ldy, m, np, np, w.Yhi,
-                                           w.Ylo, w.ldyl, keep_split ? w.Yt : nullptr, keep_split ? w.Ytl : nullptr);
+                                           w.Ylo, w.ldyl, keep_split ? w.Yt : nullptr, keep_split ? w.Ytl : nullptr,
+                                           gate);
         if (le_ != cudaSuccess) return le_;
     }
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return project64(cx, Y, ldy, m, np, w.Yhi, w.Ylo, w.ldyl, np, np, G, np, w.part, w.part_cap, true);
+    return project64(cx, Y, ldy, m, np, w.Yhi, w.Ylo, w.ldyl, np, np, G, np, w.part, w.part_cap, true, nullptr, 0, 0,
+                     gate);
 }
 
 // Out (m x np, ld ldo) = Y (m x np, ld ldy) C (np x np, ld ldc), split-TF32.
@@ -2253,7 +2400,7 @@ cudaError_t product(Ctx& cx, const float* Y, long long ldy, long long m, const f
         dim3 g1((unsigned)((m + 31) / 32), (unsigned)(np / 32));
         {
             const cudaError_t le_ = launch_pdl(k_split_q, dim3(g1), dim3(256), 0, cx.stream, Y, ldy, m, np, np,
-                                               nullptr, nullptr, 0, w.Yt, w.Ytl);
+                                               nullptr, nullptr, 0, w.Yt, w.Ytl, static_cast<const int*>(nullptr));
             if (le_ != cudaSuccess) return le_;
         }
         cx.launches++;
@@ -2466,7 +2613,7 @@ cudaError_t reproject(Ctx& cx, const float* Qbar, long long ldq, long long m, lo
     dim3 g1((unsigned)((m + 31) / 32), (unsigned)(np / 32));
     {
         const cudaError_t le_ = launch_pdl(k_split_q, dim3(g1), dim3(256), 0, cx.stream, Y, ldy, m, np, np, w.Yhi,
-                                           w.Ylo, w.ldyl, nullptr, nullptr);
+                                           w.Ylo, w.ldyl, nullptr, nullptr, static_cast<const int*>(nullptr));
         if (le_ != cudaSuccess) return le_;
     }
     cx.launches++;
@@ -2484,6 +2631,64 @@ cudaError_t reproject(Ctx& cx, const float* Qbar, long long ldq, long long m, lo
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return sketch_sub(cx, Qbar, ldq, m, kprev, w.Om, w.ldom, np, Y, ldy, Y, w.part, w.part_cap);
+}
+
+bool reproject_gram_ok(long long m, long long kprev, int np, long long ldy, const float* Y, const ReprojScratch& w) {
+    if (!(reproject_ok(m, kprev) && kprev % kBM == 0 && np % 32 == 0 && np <= 64 * 32 && gram_ok(m, np, ldy, Y)))
+        return false;
+    const size_t tiles = (size_t)(np / 32) * (np / 32 + 1) / 2;
+    return 2 * tiles * (size_t)(kprev / 128) * 1024 <= w.part_cap;
+}
+
+cudaError_t reproject_gram(Ctx& cx, const float* Qbar, long long ldq, long long m, long long kprev, float* Y,
+                           long long ldy, int np, const ReprojScratch& w, double* G, int* fused,
+                           double* trace_part) {
+    cudaError_t e;
+    dim3 g1((unsigned)((m + 31) / 32), (unsigned)(np / 32));
+    {
+        const cudaError_t le_ = launch_pdl(k_split_q, dim3(g1), dim3(256), 0, cx.stream, Y, ldy, m, np, np, w.Yhi,
+                                           w.Ylo, w.ldyl, nullptr, nullptr, static_cast<const int*>(nullptr));
+        if (le_ != cudaSuccess) return le_;
+    }
+    cx.launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // Y^T [Qbar Y]: C^T in columns 0 .. kprev - 1 of w.Ct64 (ld np), S = Y^T Y after them
+    if ((e = project64(cx, Qbar, ldq, m, kprev, w.Yhi, w.Ylo, w.ldyl, np, np, w.Ct64, np, w.part, w.part_cap,
+                       false, Y, ldy, np)) != cudaSuccess)
+        return e;
+    dim3 g2((unsigned)((kprev + 31) / 32), (unsigned)(np / 32));
+    {
+        const cudaError_t le_ = launch_pdl(k_ct_to_omega<double>, dim3(g2), dim3(256), 0, cx.stream, w.Ct64, np, kprev,
+                                           np, w.Om, w.ldom);
+        if (le_ != cudaSuccess) return le_;
+    }
+    cx.launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = sketch_sub(cx, Qbar, ldq, m, kprev, w.Om, w.ldom, np, Y, ldy, Y, w.part, w.part_cap)) != cudaSuccess)
+        return e;
+    // the sketch's partials are consumed: its buffer holds the parts of C^T C
+    const int nb = np / 32, tiles = nb * (nb + 1) / 2, KS = (int)(kprev / 128);
+    double* parts = reinterpret_cast<double*>(w.part);
+    {
+        const cudaError_t le_ = launch_pdl(k_gram_part, dim3(tiles, KS), dim3(256), 0, cx.stream,
+                                           static_cast<const double*>(w.Ct64), (long long)np, kprev, parts);
+        if (le_ != cudaSuccess) return le_;
+    }
+    cx.launches++;
+    {
+        const cudaError_t le_ = launch_pdl(k_gram_fin, dim3(tiles), dim3(256), 0, cx.stream,
+                                           static_cast<const double*>(w.Ct64 + (size_t)kprev * np), (long long)np,
+                                           static_cast<const double*>(parts), KS, np, G, trace_part);
+        if (le_ != cudaSuccess) return le_;
+    }
+    cx.launches++;
+    {
+        const cudaError_t le_ = launch_pdl(k_gram_gate, dim3(1), dim3(32), 0, cx.stream,
+                                           static_cast<const double*>(trace_part), nb, 0.05, fused, cx.st);
+        if (le_ != cudaSuccess) return le_;
+    }
+    cx.launches++;
+    return cudaGetLastError();
 }
 
 cudaError_t wait_selftest(Ctx& cx, unsigned long long* waited_ns) {

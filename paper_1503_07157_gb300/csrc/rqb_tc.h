@@ -75,6 +75,8 @@ struct ReprojScratch {
     double* sq_part;
     int sq_cap;
     double* sq_out;
+    double* trace_part;  // np / 32 parts of ||C||_F^2 (reproject_gram)
+    int* fused;          // reproject_gram's decision (device)
 };
 
 // Line (3') on the tensor core: Y (m x np) <- Y - Qbar (Qbar^T Y), Qbar
@@ -97,12 +99,32 @@ bool product_ok(long long m, int np, long long ldo, const float* Out);
 // copies w.Yt / w.Ytl, so that a following product() of the same Y can skip
 // its own split (presplit).
 bool gram_ok(long long m, int np, long long ldy, const float* Y);
+// A nonzero *gate (device) makes the launches do nothing but the copies kept
+// for product() (keep_split).
 cudaError_t gram(Ctx& cx, const float* Y, long long ldy, long long m, int np, const ReprojScratch& w, double* G,
-                 bool keep_split = false);
+                 bool keep_split = false, const int* gate = nullptr);
 cudaError_t product(Ctx& cx, const float* Y, long long ldy, long long m, const float* C, long long ldc, int np,
                     float* Out, long long ldo, const ReprojScratch& w, bool presplit = false);
 cudaError_t reproject(Ctx& cx, const float* Qbar, long long ldq, long long m, long long kprev, float* Y,
                       long long ldy, int np, const ReprojScratch& w);
+
+// Line (3') with the second CholeskyQR pass's Gram from the same product:
+// one stream-K pass of Y^T [Qbar Y] gives C^T and S = Y^T Y; then
+// Y <- Y - Qbar C~ (C~ = C rounded to TF32, the product's operand) and
+// G (np x np, FP64) = S - C^T C.  For an orthonormal Qbar the Gram of the
+// new Y is S - C^T C + d^T d with d = C~ - C (|d| <= 2^-11 |C|), so the two
+// differ by d^T d plus C~^T (Qbar^T Qbar - I) C~, both of the order of
+// ||C||^2 times 2^-22 or Qbar's loss of orthogonality.  *fused (device) is
+// set to 1 when ||C||_F^2 <= 0.05, where S - C^T C has no cancellation,
+// else 0: the caller then forms the Gram of the new Y directly with
+// gram(..., fused), which makes only product()'s copies of the split when
+// *fused is 1.
+// trace_part: np / 32 doubles.  Needs reproject_gram_ok (which also checks
+// that w.part holds the split-k parts of C^T C).
+bool reproject_gram_ok(long long m, long long kprev, int np, long long ldy, const float* Y, const ReprojScratch& w);
+cudaError_t reproject_gram(Ctx& cx, const float* Qbar, long long ldq, long long m, long long kprev, float* Y,
+                           long long ldy, int np, const ReprojScratch& w, double* G, int* fused,
+                           double* trace_part);
 
 // ---------------------------------------------------------------------------
 // BF16 storage path (A and the residual W in BF16; kind::f16 MMAs with FP32

@@ -63,7 +63,8 @@ class rqb_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int32), ("svd_sweeps", ctypes.c_int32),
                 ("phase_ms", ctypes.c_double * RQB_NUM_PHASES), ("phase_calls", ctypes.c_int32 * RQB_NUM_PHASES),
                 ("gram_fallbacks", ctypes.c_int32), ("tile_width", ctypes.c_int32),
-                ("near_identity", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("near_identity", ctypes.c_int32), ("fused_gram", ctypes.c_int32),
+                ("pass1_fp32", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _LIB = None
@@ -179,6 +180,8 @@ class Stats:
     gram_fallbacks: int = 0
     tile_width: int = 0
     near_identity: int = 0
+    fused_gram: int = 0
+    pass1_fp32: int = 0
 
 
 class Handle:
@@ -308,7 +311,8 @@ class Handle:
         return Stats(int(st.k), int(st.blocks), int(st.status), int(st.direct_tests), float(st.normA2),
                      float(st.eps), list(st.E[:nb]), list(st.D[:nb]), int(st.kernel_launches),
                      list(st.phase_ms), list(st.phase_calls), int(st.gram_fallbacks), int(st.tile_width),
-                     int(st.near_identity))
+                     int(st.near_identity), int(st.fused_gram),
+                     int(st.pass1_fp32))
 
     # -- steps ---------------------------------------------------------------
     def rqb_omega(self, n: int, col0: int, ncols: int, seed: int) -> torch.Tensor:

@@ -41,7 +41,7 @@ def test_struct_layout_matches_header():
     # rqb_config: 2 x int32, int64, 2 x int32, pointer, 2 x int32
     assert ctypes.sizeof(rqb.rqb_config) == 40
     assert ctypes.sizeof(rqb.rqb_stats) == (8 * 2 + 4 * 2 + 8 * 2 + 8 * 2 * rqb.RQB_MAX_TRACKED_BLOCKS + 8
-                                            + 8 * rqb.RQB_NUM_PHASES + 4 * rqb.RQB_NUM_PHASES + 4 * 4)
+                                            + 8 * rqb.RQB_NUM_PHASES + 4 * rqb.RQB_NUM_PHASES + 4 * 6)
 
 
 def test_null_handle_rejected_without_gpu(lib):

@@ -130,11 +130,44 @@ def test_orth_tensor_core_reprojection(orc, htc, m, p, kprev):
     assert np.abs(Qi - Qo).max() <= 1e-3
 
 
-@pytest.mark.parametrize("cond,fallback", [(1e1, 0), (1e5, 1)])
-def test_orth_first_gram_fallback(orc, htc, cond, fallback):
+@pytest.mark.parametrize("c2,fused", [(1e-6, 1), (0.04, 1), (0.07, 0), (30.0, 0)])
+def test_orth_fused_second_gram(orc, htc, c2, fused):
+    """Line (3') with kprev a multiple of 128: the second CholeskyQR pass takes
+    its Gram from the product that gives C = Qbar^T Y1, as Y1^T Y1 - C^T C,
+    where ||C||_F^2 <= 0.05, and from the re-projected panel otherwise.  Y is
+    built so that its orthonormalised panel Y1 has ||C||_F^2 = c2 (Y1 =
+    sqrt(1 - c^2) Z + c Qbar G, Z orthonormal and orthogonal to Qbar, G
+    orthonormal, c^2 p = c2); both routes end orthonormal and equal to the
+    oracle's Q_i, and stats.fused_gram reports the route.  Y -= Qbar C~ with
+    C~ = C rounded to TF32 leaves Qbar^T Y = C - C~, at most 2^-11 |C| in each
+    entry: Q_i is orthogonal to Qbar to 1e-5 plus twice that."""
+    m, p, kprev = 3000, 256, 512
+    rng = np.random.default_rng(int(1e3 * c2) + 5)
+    X = np.linalg.qr(rng.standard_normal((m, kprev + p)))[0]
+    Qbar, Z = X[:, :kprev], X[:, kprev:]
+    G = np.linalg.qr(rng.standard_normal((kprev, p)))[0]
+    c = np.sqrt(c2 / p)
+    Y1 = np.sqrt(1 - c * c) * Z + c * (Qbar @ G)
+    Y = _f32(Y1 @ np.diag(np.logspace(0, -1, p)) @ np.linalg.qr(rng.standard_normal((p, p)))[0])
+    Qbar = _f32(Qbar)
+    Qi = to_np(htc.rqb_orth(to_dev(Y, torch.float32), to_dev(Qbar, torch.float32)))
+    st = htc.rqb_get_stats()
+    Qo = orc.orth_reproject(Y, Qbar)
+    cmax = np.abs(Qbar.T @ np.linalg.qr(Y)[0]).max()
+    assert st.fused_gram == fused
+    assert orth_err(Qi) <= 1e-5
+    assert np.abs(Qbar.T @ Qi).max() <= 1e-5 + 2.0 ** -10 * cmax
+    assert np.abs(Qi - Qo).max() <= 1e-3
+
+
+@pytest.mark.parametrize("cond,fallback,fp32", [(1e1, 0, 1), (1e2, 0, 1), (1e3, 0, 0), (1e5, 1, 0)])
+def test_orth_first_gram_fallback(orc, htc, cond, fallback, fp32):
     """The first CholeskyQR pass of a split-TF32 handle takes its Gram from the
-    tensor core; a panel with kappa(Y) = 1e5 (pivot ratio^2 ~ 1e10 > 1e5) is
-    refactored from the exact FP64-accumulated Gram, and both end orthonormal."""
+    tensor core and factors it in FP32 when its pivots span at most 1e3
+    (kappa(Y) = 10 and 100 here: spans 6.5 and 169), else in FP64 when they
+    span at most 1e5 (kappa(Y) = 1e3: 1.0e4); kappa(Y) = 1e5 (span 3e7) is
+    refactored from the exact FP64-accumulated Gram.  All end orthonormal and
+    equal to the oracle's Q_i, and the stats report the route."""
     m, p = 6000, 256
     rng = np.random.default_rng(int(cond))
     U = np.linalg.qr(rng.standard_normal((m, p)))[0]
@@ -143,6 +176,7 @@ def test_orth_first_gram_fallback(orc, htc, cond, fallback):
     Qi = to_np(htc.rqb_orth(to_dev(Y, torch.float32), None))
     st = htc.rqb_get_stats()
     assert st.gram_fallbacks == fallback
+    assert st.pass1_fp32 == fp32
     assert orth_err(Qi) <= 1e-5
     Qo = orc.orth_reproject(Y, None)
     assert np.abs(Qi - Qo).max() <= (1e-3 if cond < 1e3 else 5e-2)

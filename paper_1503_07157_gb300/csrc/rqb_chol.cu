@@ -15,6 +15,9 @@
 //             8-row strip
 // R = L^T in FP64.  Each panel also keeps L_kk^{-1}, from which R^{-1} =
 // (L^{-1})^T is formed by block forward substitution in the output type.
+// An FP32 factorization of up to 256 columns instead holds the whole Gram in
+// one CTA's shared memory (k_chol_f32_cta): FP32 has the SM's full FMA rate,
+// and the chain of launches, not the arithmetic, bounds the tiled scheme.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,18 +32,26 @@ constexpr int kNb = 32;     // tile
 constexpr int kStrip = 8;   // rows per CTA in the solves and updates
 
 // Padding rows/columns >= p become the identity; dG = diagonal of G (the
-// reference for the relative pivot test); L cleared.
+// reference for the relative pivot test); L (when given) cleared; Gf (when
+// given) = G rounded to FP32.
 __global__ void k_chol_init(double* __restrict__ G, int bp, int p, double* __restrict__ dG,
-                            double* __restrict__ L, const int* __restrict__ skip) {
+                            double* __restrict__ L, const int* __restrict__ skip, float* __restrict__ Gf) {
     pdl_trigger();
     pdl_wait();
     if (skip && *skip) return;   // the near-identity expansion gave the factor
     const int total = bp * bp;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
         const int r = e % bp, c = e / bp;
-        if (r >= p || c >= p) G[e] = (r == c) ? 1.0 : 0.0;
-        L[e] = 0.0;
-        if (r == c) dG[r] = (r < p) ? G[e] : 1.0;
+        double g;
+        if (r >= p || c >= p) {
+            g = (r == c) ? 1.0 : 0.0;
+            G[e] = g;
+        } else {
+            g = G[e];
+        }
+        if (L) L[e] = 0.0;
+        if (Gf) Gf[e] = (float)g;
+        if (r == c) dG[r] = g;
     }
 }
 
@@ -277,6 +288,208 @@ __global__ void __launch_bounds__(256) k_chol_update(double* __restrict__ G, con
 #pragma unroll 8
     for (int t = 0; t < kNb; ++t) s += (W)L[row + (int64_t)(k0 + t) * bp] * Lj[c][t];
     G[row + (int64_t)(j * kNb + c) * bp] -= (double)s;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 factor of a Gram of at most 256 columns on one CTA.  The lower 32 x 32
+// tiles of G (FP32) stay in shared memory, each stored by columns with a
+// stride of kTs floats; for each tile column k: the diagonal tile is
+// factored by one warp in registers (tile_factor_warp, L_kk^{-1} alongside),
+// the tiles below it are solved,
+// L_ik = G_ik L_kk^{-T}, and the trailing tiles updated, G_ij -= L_ik L_jk^T
+// (k < j <= i), each by a 64-thread group with 4 x 4 outputs per thread fed
+// by 16-byte shared-memory reads and packed FP32 FMAs.  No launch and no
+// global round trip separates the tile columns, which a chain of panel and
+// update kernels pays for at every tile.
+constexpr int kTs = 36;                // column stride of a tile in shared memory (floats)
+constexpr int kTileF = kNb * kTs;      // floats per tile
+constexpr int kCtaThreads = 512;
+
+__host__ __device__ constexpr int tri_tile(int i, int j) { return i * (i + 1) / 2 + j; }
+
+size_t chol_f32_cta_smem(int bp) {
+    const int nblk = bp / kNb;
+    return sizeof(float) * (size_t)(nblk * (nblk + 1) / 2 + 1) * kTileF;
+}
+
+// Tile number t -> (i, j), j <= i, in the order of tri_tile.
+__device__ __forceinline__ void tile_ij(int t, int* i, int* j) {
+    int a = 0;
+    while ((a + 1) * (a + 2) / 2 <= t) ++a;
+    *i = a;
+    *j = t - a * (a + 1) / 2;
+}
+
+// The diagonal tile's factor on one warp, without block barriers: lane r
+// holds row r of the tile (d[c] = D(r, c)) and of its inverse (w[c]), both in
+// registers.  Unscaled elimination: step j takes pivot D(j, j) from lane j
+// and, for r > j, subtracts D(r, j) / pivot_j times column j's entries D(c, j)
+// (c > j, from lane c) from D(r, c), and times row j of the inverse (from
+// lane j) from w; rows are scaled by pivot^{-1/2} at the end.  thr: this
+// lane's pivot threshold; a pivot at or below it, or not finite, sets *fail.
+// Entries above the diagonal are read and updated but not used, and are
+// stored as zeros.
+__device__ __forceinline__ void tile_factor_warp(float* __restrict__ D, float* __restrict__ Di, float thr, int lane,
+                                                 int* fail) {
+    float d[kNb], w[kNb];
+#pragma unroll
+    for (int c = 0; c < kNb; ++c) {
+        d[c] = D[c * kTs + lane];
+        w[c] = (c == lane) ? 1.f : 0.f;
+    }
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < kNb; ++j) {
+        const float pj = __shfl_sync(0xffffffffu, d[j], j);
+        const float y = __frcp_rn(pj);
+        const float ip = fmaf(y, fmaf(-pj, y, 1.f), y);
+        if (lane == j && (!(pj > thr) || !isfinite(pj))) bad = true;
+        const float a = (lane > j) ? d[j] * ip : 0.f;
+#pragma unroll
+        for (int c = j + 1; c < kNb; ++c) d[c] = fmaf(-a, __shfl_sync(0xffffffffu, d[j], c), d[c]);
+#pragma unroll
+        for (int c = 0; c <= j; ++c) w[c] = fmaf(-a, __shfl_sync(0xffffffffu, w[c], j), w[c]);
+    }
+    float dd = 0.f;
+#pragma unroll
+    for (int c = 0; c < kNb; ++c) dd = (c == lane) ? d[c] : dd;
+    const float yy = rsqrtf(dd);
+    const float inv = yy * fmaf(-0.5f * dd, yy * yy, 1.5f);
+#pragma unroll
+    for (int c = 0; c < kNb; ++c) {
+        const float ic = __shfl_sync(0xffffffffu, inv, c);
+        D[c * kTs + lane] = (lane >= c) ? d[c] * ic : 0.f;
+        Di[c * kTs + lane] = (lane >= c) ? w[c] * inv : 0.f;
+    }
+    if (bad) *fail = 1;
+}
+
+// Gf: bp x bp (ld bp, FP32, lower triangle read); writes the lower tiles of
+// L to Lf and the diagonal tiles of L^{-1} (that is, L_kk^{-1}) to Lif, both
+// bp x bp ld bp; a pivot at or below tol * dG or not finite records
+// RQB_ERR_BREAKDOWN (the factorization then runs on and is discarded).
+__global__ void __launch_bounds__(kCtaThreads, 1)
+k_chol_f32_cta(const float* __restrict__ Gf, int bp, const double* __restrict__ dG, double tol,
+               float* __restrict__ Lf, float* __restrict__ Lif, DevState* st, const int* __restrict__ skip) {
+    pdl_trigger();
+    pdl_wait();
+    if (skip && *skip) return;   // the near-identity expansion gave the factor
+    extern __shared__ __align__(16) float csm[];
+    const int nblk = bp / kNb, ntile = nblk * (nblk + 1) / 2;
+    float* T = csm;                               // tile (i, j) at T + tri_tile(i, j) kTileF, (r, c) at [c kTs + r]
+    float* Di = csm + (size_t)ntile * kTileF;     // L_kk^{-1} of the current column, same layout
+    __shared__ int fail;
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    for (int e = tid; e < ntile * kNb * (kNb / 4); e += kCtaThreads) {
+        const int v = e & 7, c = (e >> 3) & 31, t = e >> 8;
+        int i, j;
+        tile_ij(t, &i, &j);
+        cp_async16(T + (size_t)t * kTileF + c * kTs + 4 * v, Gf + (size_t)(i * kNb + 4 * v) + (size_t)(j * kNb + c) * bp,
+                   16);
+    }
+    cp_async_commit();
+    if (tid == 0) fail = 0;
+    cp_async_wait<0>();
+    __syncthreads();
+    for (int k = 0; k < nblk; ++k) {
+        const int k0 = k * kNb;
+        if (wid == 0)
+            tile_factor_warp(T + (size_t)tri_tile(k, k) * kTileF, Di, (float)(tol * dG[k0 + lane]), lane, &fail);
+        __syncthreads();
+        for (int e = tid; e < kNb * (kNb / 4); e += kCtaThreads) {
+            const int v = e & 7, c = e >> 3;
+            *reinterpret_cast<float4*>(Lif + (size_t)(k0 + 4 * v) + (size_t)(k0 + c) * bp) =
+                *reinterpret_cast<const float4*>(Di + c * kTs + 4 * v);
+        }
+        // L_ik = G_ik L_kk^{-T}: two tiles per pass, thread (r, columns 4 cg .. 4 cg + 3)
+        for (int ib = k + 1; ib < nblk; ib += 2) {
+            const int i = ib + (tid >> 8), r = tid & 31, cg = (tid >> 5) & 7;
+            float* Tik = T + (size_t)tri_tile(i < nblk ? i : k, k) * kTileF;
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            if (i < nblk) {
+#pragma unroll 8
+                for (int t = 0; t < kNb; ++t) {
+                    const float g = Tik[t * kTs + r];
+                    const float4 l = *reinterpret_cast<const float4*>(Di + t * kTs + 4 * cg);
+                    acc[0] = fmaf(g, l.x, acc[0]);
+                    acc[1] = fmaf(g, l.y, acc[1]);
+                    acc[2] = fmaf(g, l.z, acc[2]);
+                    acc[3] = fmaf(g, l.w, acc[3]);
+                }
+            }
+            __syncthreads();   // every read of the pass's tiles before the first store
+            if (i < nblk) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) Tik[(4 * cg + q) * kTs + r] = acc[q];
+            }
+        }
+        __syncthreads();
+        // G_ij -= L_ik L_jk^T, k < j <= i: group g of 64 threads per tile pair,
+        // thread (rb, cb) rows 4 rb .. 4 rb + 3, columns 4 cb .. 4 cb + 3
+        const int mrem = nblk - 1 - k, npair = mrem * (mrem + 1) / 2;
+        const int g = tid >> 6, l = tid & 63, rb = l & 7, cb = l >> 3;
+        for (int pr = g; pr < npair; pr += kCtaThreads / 64) {
+            int jj = 0, rem = pr;
+            while (rem >= mrem - jj) {
+                rem -= mrem - jj;
+                ++jj;
+            }
+            const int j = k + 1 + jj, i = j + rem;
+            const float* Li = T + (size_t)tri_tile(i, k) * kTileF;
+            const float* Lj = T + (size_t)tri_tile(j, k) * kTileF;
+            float* Tij = T + (size_t)tri_tile(i, j) * kTileF;
+            float2 acc[4][2];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = make_float2(0.f, 0.f);
+#pragma unroll 8
+            for (int t = 0; t < kNb; ++t) {
+                const float4 a = *reinterpret_cast<const float4*>(Li + t * kTs + 4 * rb);
+                const float4 b = *reinterpret_cast<const float4*>(Lj + t * kTs + 4 * cb);
+                const float2 b01 = make_float2(b.x, b.y), b23 = make_float2(b.z, b.w);
+                const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float2 aa = make_float2(av[q], av[q]);
+                    acc[q][0] = __ffma2_rn(aa, b01, acc[q][0]);
+                    acc[q][1] = __ffma2_rn(aa, b23, acc[q][1]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {   // column 4 cb + q, rows 4 rb .. 4 rb + 3
+                float4* dst = reinterpret_cast<float4*>(Tij + (4 * cb + q) * kTs + 4 * rb);
+                float4 v = *dst;
+                const int h = q >> 1;
+                v.x -= (q & 1) ? acc[0][h].y : acc[0][h].x;
+                v.y -= (q & 1) ? acc[1][h].y : acc[1][h].x;
+                v.z -= (q & 1) ? acc[2][h].y : acc[2][h].x;
+                v.w -= (q & 1) ? acc[3][h].y : acc[3][h].x;
+                *dst = v;
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < ntile * kNb * (kNb / 4); e += kCtaThreads) {
+        const int v = e & 7, c = (e >> 3) & 31, t = e >> 8;
+        int i, j;
+        tile_ij(t, &i, &j);
+        *reinterpret_cast<float4*>(Lf + (size_t)(i * kNb + 4 * v) + (size_t)(j * kNb + c) * bp) =
+            *reinterpret_cast<const float4*>(T + (size_t)t * kTileF + c * kTs + 4 * v);
+    }
+    if (tid == 0 && fail) record_error(st, RQB_ERR_BREAKDOWN);
+}
+
+// R = L^T (FP64, column-major, upper) from the FP32 L of k_chol_f32_cta
+// (lower triangle of Lf read).
+__global__ void k_chol_transpose_f32(const float* __restrict__ Lf, int bp, double* __restrict__ R,
+                                     const int* __restrict__ skip) {
+    pdl_trigger();
+    pdl_wait();
+    if (skip && *skip) return;   // the near-identity expansion gave the factor
+    const int total = bp * bp;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int r = e % bp, c = e / bp;
+        R[e] = (r <= c) ? (double)Lf[c + (int64_t)r * bp] : 0.0;
+    }
 }
 
 // R = L^T (FP64, column-major, upper).
@@ -667,8 +880,10 @@ cudaError_t upper_inverse(Ctx& cx, const double* R, int bp, T* Rinv) {
 // 2 bp^2 + bp doubles (L, the inverses of its diagonal tiles, and the
 // diagonal of G), plus bp^2 doubles' room for their FP32 copies when T is
 // float.  fp64: working precision of the factorization (FP32 serves the
-// second CholeskyQR pass, whose Gram is I + O(u kappa)); the factors are
-// stored in FP64 either way; R^{-1} is formed in T.
+// second CholeskyQR pass, whose Gram is I + O(u kappa), and the first pass
+// of the tensor-core handles); the factors are stored in FP64 either way;
+// R^{-1} is formed in T.  FP32 factors of up to 256 columns run on one CTA
+// (k_chol_f32_cta), the others as the chain of panel and update kernels.
 template <typename T>
 cudaError_t chol_inv_blocked(Ctx& cx, double* G, int bp, int p, double* R, T* Rinv, double tol, double* scratch,
                              size_t scratch_doubles, bool fp64, const int* skip) {
@@ -681,31 +896,51 @@ cudaError_t chol_inv_blocked(Ctx& cx, double* G, int bp, int p, double* R, T* Ri
     float* Lf = f32 ? reinterpret_cast<float*>(dG + bp) : nullptr;   // 16-byte aligned: bp % 32 == 0
     float* Lif = f32 ? Lf + (size_t)bp * bp : nullptr;
     const int nblk = bp / kNb;
-    cudaError_t e = launch_pdl(k_chol_init, dim3(std::max(1, bp * bp / 256)), dim3(256), 0, cx.stream, G, bp, p, dG,
-                               L, skip);
-    if (e != cudaSuccess) return e;
-    cx.launches++;
-    for (int k = 0; k < nblk; ++k) {
-        const int below = nblk - k - 1;
-        const dim3 gp(1 + below * (kNb / kStrip));
-        e = fp64 ? launch_pdl(k_chol_panel<double>, gp, dim3(256), 0, cx.stream, G, L, Linv, Lf, Lif, bp, k, dG, tol,
-                              cx.st, skip)
-                 : launch_pdl(k_chol_panel<float>, gp, dim3(256), 0, cx.stream, G, L, Linv, Lf, Lif, bp, k, dG, tol,
-                              cx.st, skip);
+    cudaError_t e;
+    if (f32 && !fp64 && nblk <= 8) {
+        // FP32 factor on one CTA (k_chol_f32_cta); G in FP32 where L would sit
+        float* Gf = reinterpret_cast<float*>(L);
+        const size_t smem = chol_f32_cta_smem(bp);
+        if ((e = smem_limit(k_chol_f32_cta, (int)smem)) != cudaSuccess) return e;
+        e = launch_pdl(k_chol_init, dim3(std::max(1, bp * bp / 256)), dim3(256), 0, cx.stream, G, bp, p, dG,
+                       static_cast<double*>(nullptr), skip, Gf);
         if (e != cudaSuccess) return e;
         cx.launches++;
-        if (below > 0) {
-            const int pairs = below * (below + 1) / 2;
-            const dim3 gu(pairs * (kNb / kStrip));
-            e = fp64 ? launch_pdl(k_chol_update<double>, gu, dim3(256), 0, cx.stream, G, L, bp, k, nblk, skip)
-                     : launch_pdl(k_chol_update<float>, gu, dim3(256), 0, cx.stream, G, L, bp, k, nblk, skip);
+        e = launch_pdl(k_chol_f32_cta, dim3(1), dim3(kCtaThreads), smem, cx.stream, static_cast<const float*>(Gf), bp,
+                       static_cast<const double*>(dG), tol, Lf, Lif, cx.st, skip);
+        if (e != cudaSuccess) return e;
+        cx.launches++;
+        e = launch_pdl(k_chol_transpose_f32, dim3(std::max(1, bp * bp / 256)), dim3(256), 0, cx.stream,
+                       static_cast<const float*>(Lf), bp, R, skip);
+        if (e != cudaSuccess) return e;
+        cx.launches++;
+    } else {
+        e = launch_pdl(k_chol_init, dim3(std::max(1, bp * bp / 256)), dim3(256), 0, cx.stream, G, bp, p, dG, L, skip,
+                       static_cast<float*>(nullptr));
+        if (e != cudaSuccess) return e;
+        cx.launches++;
+        for (int k = 0; k < nblk; ++k) {
+            const int below = nblk - k - 1;
+            const dim3 gp(1 + below * (kNb / kStrip));
+            e = fp64 ? launch_pdl(k_chol_panel<double>, gp, dim3(256), 0, cx.stream, G, L, Linv, Lf, Lif, bp, k, dG,
+                                  tol, cx.st, skip)
+                     : launch_pdl(k_chol_panel<float>, gp, dim3(256), 0, cx.stream, G, L, Linv, Lf, Lif, bp, k, dG,
+                                  tol, cx.st, skip);
             if (e != cudaSuccess) return e;
             cx.launches++;
+            if (below > 0) {
+                const int pairs = below * (below + 1) / 2;
+                const dim3 gu(pairs * (kNb / kStrip));
+                e = fp64 ? launch_pdl(k_chol_update<double>, gu, dim3(256), 0, cx.stream, G, L, bp, k, nblk, skip)
+                         : launch_pdl(k_chol_update<float>, gu, dim3(256), 0, cx.stream, G, L, bp, k, nblk, skip);
+                if (e != cudaSuccess) return e;
+                cx.launches++;
+            }
         }
+        e = launch_pdl(k_chol_transpose, dim3(std::max(1, bp * bp / 256)), dim3(256), 0, cx.stream, L, bp, R, skip);
+        if (e != cudaSuccess) return e;
+        cx.launches++;
     }
-    e = launch_pdl(k_chol_transpose, dim3(std::max(1, bp * bp / 256)), dim3(256), 0, cx.stream, L, bp, R, skip);
-    if (e != cudaSuccess) return e;
-    cx.launches++;
     if constexpr (f32) {
         const size_t smem = sizeof(float) * ((size_t)bp * kXs + 2 * (size_t)bp * kNb + 2 * kNb * kNb + kNb * kXs);
         if (smem > 200 * 1024) return cudaErrorInvalidValue;

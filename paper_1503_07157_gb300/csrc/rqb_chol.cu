@@ -379,7 +379,9 @@ k_chol_f32_cta(const float* __restrict__ Gf, int bp, const double* __restrict__ 
     float* T = csm;                               // tile (i, j) at T + tri_tile(i, j) kTileF, (r, c) at [c kTs + r]
     float* Di = csm + (size_t)ntile * kTileF;     // L_kk^{-1} of the current column, same layout
     __shared__ int fail;
+    __shared__ float thrs[8 * kNb];   // pivot thresholds tol * dG, all columns
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    for (int r = tid; r < bp; r += kCtaThreads) thrs[r] = (float)(tol * dG[r]);
     for (int e = tid; e < ntile * kNb * (kNb / 4); e += kCtaThreads) {
         const int v = e & 7, c = (e >> 3) & 31, t = e >> 8;
         int i, j;
@@ -393,20 +395,22 @@ k_chol_f32_cta(const float* __restrict__ Gf, int bp, const double* __restrict__ 
     __syncthreads();
     for (int k = 0; k < nblk; ++k) {
         const int k0 = k * kNb;
-        if (wid == 0)
-            tile_factor_warp(T + (size_t)tri_tile(k, k) * kTileF, Di, (float)(tol * dG[k0 + lane]), lane, &fail);
+        if (wid == 0) tile_factor_warp(T + (size_t)tri_tile(k, k) * kTileF, Di, thrs[k0 + lane], lane, &fail);
         __syncthreads();
         for (int e = tid; e < kNb * (kNb / 4); e += kCtaThreads) {
             const int v = e & 7, c = e >> 3;
             *reinterpret_cast<float4*>(Lif + (size_t)(k0 + 4 * v) + (size_t)(k0 + c) * bp) =
                 *reinterpret_cast<const float4*>(Di + c * kTs + 4 * v);
         }
-        // L_ik = G_ik L_kk^{-T}: two tiles per pass, thread (r, columns 4 cg .. 4 cg + 3)
-        for (int ib = k + 1; ib < nblk; ib += 2) {
-            const int i = ib + (tid >> 8), r = tid & 31, cg = (tid >> 5) & 7;
-            float* Tik = T + (size_t)tri_tile(i < nblk ? i : k, k) * kTileF;
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            if (i < nblk) {
+        // L_ik = G_ik L_kk^{-T}: each half of the CTA takes every other tile
+        // i > k, thread (r, columns 4 cg .. 4 cg + 3); a half's named barrier
+        // orders its reads of a tile before its stores to it (the halves
+        // never share a tile)
+        {
+            const int half = tid >> 8, r = tid & 31, cg = (tid >> 5) & 7;
+            for (int i = k + 1 + half; i < nblk; i += 2) {
+                float* Tik = T + (size_t)tri_tile(i, k) * kTileF;
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 8
                 for (int t = 0; t < kNb; ++t) {
                     const float g = Tik[t * kTs + r];
@@ -416,9 +420,7 @@ k_chol_f32_cta(const float* __restrict__ Gf, int bp, const double* __restrict__ 
                     acc[2] = fmaf(g, l.z, acc[2]);
                     acc[3] = fmaf(g, l.w, acc[3]);
                 }
-            }
-            __syncthreads();   // every read of the pass's tiles before the first store
-            if (i < nblk) {
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + half), "r"(kCtaThreads / 2) : "memory");
 #pragma unroll
                 for (int q = 0; q < 4; ++q) Tik[(4 * cg + q) * kTs + r] = acc[q];
             }

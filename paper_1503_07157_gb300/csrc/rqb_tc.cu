@@ -1082,61 +1082,56 @@ __global__ void k_split_q(const float* __restrict__ Qi, long long ldq, long long
 }
 
 // Omega-layout copy of the re-projection coefficients: Om[j + c ldo] =
-// rna_tf32(Ct[c + j ldc]) for j < kprev, c < np (Ct is C^T, np x kprev).
-// Split-k parts of C^T C for the fused second-pass Gram.  C is kprev x np,
-// held transposed in Ct (np x kprev, ld ldc, FP64).  CTA (t, s) takes the
-// 32 x 32 upper tile t = (I, J), I <= J (t = J (J + 1) / 2 + I), over
-// k in [128 s, 128 s + 128), and writes its 1024 sums to
-// part[(t KS + s) 1024 + i + 32 j] (KS = gridDim.y).  The FP32-rounded
-// entries of C are multiplied and summed in FP32 over 32 k, the four 32-k
-// sums added in FP64.
-__global__ void __launch_bounds__(256) k_gram_part(const double* __restrict__ Ct, long long ldc, long long kprev,
+// rna_tf32(Ct[c + j ldc]) for j < kprev, c < np (Ct is C^T, np x kprev);
+// with C32, also C32[j + c ldc32] = Ct[c + j ldc] rounded to FP32.
+// Split-k parts of C^T C for the fused second-pass Gram.  C is kprev x np
+// (FP32, ld ldc, k contiguous).  CTA (t, s) takes the 32 x 32 upper tile
+// t = (I, J), I <= J (t = J (J + 1) / 2 + I), over k in [128 s, 128 s + 128),
+// and writes its 1024 sums to part[(t KS + s) 1024 + i + 32 j] (KS =
+// gridDim.y), in FP64.  Products are summed in FP32 over 32 k, and the four
+// 32-k sums pairwise.
+__global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ C, long long ldc, long long kprev,
                                                    double* __restrict__ part) {
     pdl_trigger();
     pdl_wait();
-    __shared__ float As[128][33], Bs[128][33];
+    __shared__ float As[32][129], Bs[32][129];   // [column of the tile][k]: conflict-free along k and along columns
     int J = 0;
     while ((J + 1) * (J + 2) / 2 <= (int)blockIdx.x) ++J;
     const int I = (int)blockIdx.x - J * (J + 1) / 2;
     const long long k0 = (long long)blockIdx.y * 128;
     const int tid = threadIdx.x;
-    // all 16 loads of a thread in flight at once: 16-byte pairs of C^T
-    // (Ct 16-byte aligned, ldc even)
-    const double2* C2 = reinterpret_cast<const double2*>(Ct);
-    double2 va[8], vb[8];
+    float va[16], vb[16];   // all 32 loads of a thread in flight at once
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        const int e = tid + 256 * r, c2 = e & 15, kk = e >> 4;
+    for (int r = 0; r < 16; ++r) {
+        const int e = tid + 256 * r, kk = e & 127, c = e >> 7;
         const bool in = k0 + kk < kprev;
-        const long long row = (k0 + kk) * ldc;
-        va[r] = in ? C2[(row + I * 32) / 2 + c2] : make_double2(0.0, 0.0);
-        vb[r] = in ? C2[(row + J * 32) / 2 + c2] : make_double2(0.0, 0.0);
+        va[r] = in ? C[(k0 + kk) + (long long)(I * 32 + c) * ldc] : 0.f;
+        vb[r] = in ? C[(k0 + kk) + (long long)(J * 32 + c) * ldc] : 0.f;
     }
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        const int e = tid + 256 * r, c2 = e & 15, kk = e >> 4;
-        As[kk][2 * c2] = (float)va[r].x;
-        As[kk][2 * c2 + 1] = (float)va[r].y;
-        Bs[kk][2 * c2] = (float)vb[r].x;
-        Bs[kk][2 * c2 + 1] = (float)vb[r].y;
+    for (int r = 0; r < 16; ++r) {
+        const int e = tid + 256 * r, kk = e & 127, c = e >> 7;
+        As[c][kk] = va[r];
+        Bs[c][kk] = vb[r];
     }
     __syncthreads();
     const int lr = tid & 31, lc = (tid >> 5) * 4;
-    double accd[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int kc = 0; kc < 128; kc += 32) {
+    float cs[4][4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 8
-        for (int kk = kc; kk < kc + 32; ++kk) {
-            const float x = As[kk][lr];
+        for (int kk = 32 * h; kk < 32 * h + 32; ++kk) {
+            const float x = As[lr][kk];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = fmaf(x, Bs[kk][lc + q], acc[q]);
+            for (int q = 0; q < 4; ++q) acc[q] = fmaf(x, Bs[lc + q][kk], acc[q]);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) accd[q] += (double)acc[q];
+        for (int q = 0; q < 4; ++q) cs[h][q] = acc[q];
     }
     double* out = part + ((size_t)blockIdx.x * gridDim.y + blockIdx.y) * 1024;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) out[lr + 32 * (lc + q)] = accd[q];
+    for (int q = 0; q < 4; ++q) out[lr + 32 * (lc + q)] = (double)((cs[0][q] + cs[1][q]) + (cs[2][q] + cs[3][q]));
 }
 
 // G (np x np, FP64, ld np) = S - C^T C on the 32 x 32 upper tiles, one per
@@ -1201,7 +1196,7 @@ __global__ void k_gram_gate(const double* __restrict__ trace_part, int nparts, d
 
 template <typename TC>
 __global__ void k_ct_to_omega(const TC* __restrict__ Ct, long long ldc, long long kprev, int np,
-                              float* __restrict__ Om, long long ldo) {
+                              float* __restrict__ Om, long long ldo, float* __restrict__ C32, long long ldc32) {
     pdl_trigger();
     pdl_wait();
     __shared__ TC tile[32][33];
@@ -1215,7 +1210,11 @@ __global__ void k_ct_to_omega(const TC* __restrict__ Ct, long long ldc, long lon
     __syncthreads();
     for (int i = ty; i < 32; i += 8) {
         const long long j = j0 + tx;
-        if (j < kprev) Om[j + (long long)(c0 + i) * ldo] = tf32_rna((float)tile[tx][i]);
+        if (j < kprev) {
+            const float v = (float)tile[tx][i];
+            Om[j + (long long)(c0 + i) * ldo] = tf32_rna(v);
+            if (C32) C32[j + (long long)(c0 + i) * ldc32] = v;
+        }
     }
 }
 
@@ -2625,7 +2624,7 @@ cudaError_t reproject(Ctx& cx, const float* Qbar, long long ldq, long long m, lo
     dim3 g2((unsigned)((kprev + 31) / 32), (unsigned)(np / 32));
     {
         const cudaError_t le_ = launch_pdl(k_ct_to_omega<double>, dim3(g2), dim3(256), 0, cx.stream, w.Ct64, np, kprev,
-                                           np, w.Om, w.ldom);
+                                           np, w.Om, w.ldom, static_cast<float*>(nullptr), 0LL);
         if (le_ != cudaSuccess) return le_;
     }
     cx.launches++;
@@ -2659,19 +2658,20 @@ cudaError_t reproject_gram(Ctx& cx, const float* Qbar, long long ldq, long long 
     dim3 g2((unsigned)((kprev + 31) / 32), (unsigned)(np / 32));
     {
         const cudaError_t le_ = launch_pdl(k_ct_to_omega<double>, dim3(g2), dim3(256), 0, cx.stream, w.Ct64, np, kprev,
-                                           np, w.Om, w.ldom);
+                                           np, w.Om, w.ldom, w.Ct, kprev);
         if (le_ != cudaSuccess) return le_;
     }
     cx.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = sketch_sub(cx, Qbar, ldq, m, kprev, w.Om, w.ldom, np, Y, ldy, Y, w.part, w.part_cap)) != cudaSuccess)
         return e;
-    // the sketch's partials are consumed: its buffer holds the parts of C^T C
+    // the sketch's partials are consumed: its buffer holds the parts of C^T C,
+    // formed from the FP32 copy of C (w.Ct, kprev x np) made beside Om
     const int nb = np / 32, tiles = nb * (nb + 1) / 2, KS = (int)(kprev / 128);
     double* parts = reinterpret_cast<double*>(w.part);
     {
         const cudaError_t le_ = launch_pdl(k_gram_part, dim3(tiles, KS), dim3(256), 0, cx.stream,
-                                           static_cast<const double*>(w.Ct64), (long long)np, kprev, parts);
+                                           static_cast<const float*>(w.Ct), kprev, kprev, parts);
         if (le_ != cudaSuccess) return le_;
     }
     cx.launches++;

@@ -1365,14 +1365,28 @@ __global__ void k_reduce_project(const float* __restrict__ part, long long U, in
     }
 }
 
+// Sum2 step (Ogita, Rump and Oishi, "Accurate sum and dot product", 2005):
+// s collects the FP32 sum and e the FP32 sum of the exact rounding errors of
+// its additions (TwoSum), so that s + e carries the sum of n terms to within
+// about (n u)^2 of the sum of their magnitudes (u = 2^-24), on the FP32 pipe.
+__device__ __forceinline__ void sum2_add(float& s, float& e, float x) {
+    const float t = s + x;
+    const float z = t - s;
+    e += (s - (t - z)) + (x - z);
+    s = t;
+}
+
 // The panel's coefficient products (the Grams Y^T Y and C^T = Y^T Qbar of
-// lines (3), (3')): out[c + j ldo] (c < pcols, j < n) = the FP64 sum of the
-// FP32 partials of the CTAs covering tile j / 128.  Each partial is one CTA's
-// stretch of the reduction over m, accumulated in FP32 by the tensor core and
-// the period drains; the sum across CTAs is FP64.  The partials of an entry
-// are cut into four runs of consecutive CTAs; a quarter of the threads sums
-// each run in CTA order, and the four run sums are added in run order (a
-// fixed order, independent of the launch).  sym (a Gram, X = Q): the entries
+// lines (3), (3')): out[c + j ldo] (c < pcols, j < n) = the sum of the FP32
+// partials of the CTAs covering tile j / 128, stored in FP64.  Each partial
+// is one CTA's stretch of the reduction over m, accumulated in FP32 by the
+// tensor core and the period drains.  The partials of an entry are cut into
+// four runs of consecutive CTAs; a quarter of the threads sums each run in
+// CTA order by Sum2 (sum2_add: about 10^-10 of the magnitudes for the ~100
+// partials of an entry, far below the partials' own FP32 rounding, and on
+// the FP32 pipe, where this part's FP64 pipe does two operations per clock
+// per SM), and the four run sums are added in FP64 in run order (a fixed
+// order, independent of the launch).  sym (a Gram, X = Q): the entries
 // above the diagonal mirror those below it, which are summed once and stored
 // at both positions.
 __global__ void k_reduce_project64(const float* __restrict__ part, long long U, int C, int P, int G, int np,
@@ -1395,7 +1409,7 @@ __global__ void k_reduce_project64(const float* __restrict__ part, long long U, 
         const int jl = idx / np, c = idx % np;
         const long long j = (long long)t * kBM + jl;
         const bool live = idx < i0 + span && j < n && !(sym && c + 3 < j);
-        double a[4] = {0.0, 0.0, 0.0, 0.0};
+        float as[4] = {0.f, 0.f, 0.f, 0.f}, ae[4] = {0.f, 0.f, 0.f, 0.f};
         if (live) {
             int q = q0;
             for (; q + 4 <= q1; q += 4) {   // four partial loads in flight
@@ -1404,20 +1418,23 @@ __global__ void k_reduce_project64(const float* __restrict__ part, long long U, 
                 for (int u = 0; u < 4; ++u) v[u] = *reinterpret_cast<const float4*>(part + off[q + u] + idx);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    a[0] += (double)v[u].x;
-                    a[1] += (double)v[u].y;
-                    a[2] += (double)v[u].z;
-                    a[3] += (double)v[u].w;
+                    sum2_add(as[0], ae[0], v[u].x);
+                    sum2_add(as[1], ae[1], v[u].y);
+                    sum2_add(as[2], ae[2], v[u].z);
+                    sum2_add(as[3], ae[3], v[u].w);
                 }
             }
             for (; q < q1; ++q) {
                 const float4 v = *reinterpret_cast<const float4*>(part + off[q] + idx);
-                a[0] += (double)v.x;
-                a[1] += (double)v.y;
-                a[2] += (double)v.z;
-                a[3] += (double)v.w;
+                sum2_add(as[0], ae[0], v.x);
+                sum2_add(as[1], ae[1], v.y);
+                sum2_add(as[2], ae[2], v.z);
+                sum2_add(as[3], ae[3], v.w);
             }
         }
+        double a[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = (double)as[i] + (double)ae[i];
         if (g > 0) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) runs[g - 1][4 * lt + i] = a[i];

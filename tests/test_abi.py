@@ -44,6 +44,19 @@ def test_struct_layout_matches_header():
                                             + 8 * rqb.RQB_NUM_PHASES + 4 * rqb.RQB_NUM_PHASES + 4 * 6)
 
 
+@pytest.mark.parametrize("sname", ["rqb_config", "rqb_stats"])
+def test_struct_fields_match_header(sname):
+    """The binding's ctypes fields name the header's struct members in the
+    header's order (a member added on one side only, or out of order, would
+    shift every field after it)."""
+    text = re.sub(r"/\*.*?\*/", "", open(rqb.HEADER).read(), flags=re.S)
+    m = re.search(r"typedef struct\s*(?:\w+\s*)?\{([^{}]*)\}\s*" + sname + r"\s*;", text)
+    assert m, sname
+    body = m.group(1)
+    members = re.findall(r"\b(?:u?int32_t|u?int64_t|double|float|void)\s*\**\s*(\w+)\s*(?:\[[^\]]*\])?\s*;", body)
+    assert [f[0] for f in getattr(rqb, sname)._fields_] == members
+
+
 def test_null_handle_rejected_without_gpu(lib):
     assert lib.rqb_destroy(None) == rqb.RQB_ERR_INVALID
     assert lib.rqb_get_stats(None, None) == rqb.RQB_ERR_INVALID

@@ -362,7 +362,9 @@ int read_state(rqb_handle h, const Scal& sc) {
 }
 
 // Line (6) without line (5) for the tensor-core handles, whose stop test is
-// the direct norm of the stored residual (Sec. 3 c11, c12).  With X the
+// the direct norm of the stored residual (the downdated E of line (6) would
+// carry the rounding of the FP32 or BF16 storage and of the split products
+// in every block).  With X the
 // stored residual before block i (direct norm dprev) and B_i = Q_i^T X
 // (norm nb), Pythagoras (Prop. 4.1) gives ||X - Q_i B_i||^2 = dprev - nb for
 // an orthonormal Q_i.  The bound below adds 1e-4 dprev for Q_i's
